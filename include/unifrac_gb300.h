@@ -1,0 +1,185 @@
+/*
+ * unifrac_gb300.h -- C ABI of the GB300 Striped UniFrac engine.
+ *
+ * Computes all-pairs (or a stripe range of) UniFrac distances between the
+ * samples of a count table over a rooted phylogenetic tree, on one GPU.
+ *
+ * Background.  Sfiligoi, McDonald & Knight, "Porting and optimizing UniFrac
+ * for GPUs" (arXiv 2005.05826) ship the method as a "C shared library
+ * linkable by any programming language" (Abstract) and split the n x n
+ * distance problem into independent stripes (Abstract, Sec. 1; Fig. 1):
+ * stripe s, column k holds the pair (k, (k + s + 1) mod n), and the stripes
+ * of a run live in one unified buffer indexed (s - start) * n + k (Sec. 2,
+ * Fig. 1).  The paper prints no UniFrac formula; the four methods below are
+ * the standard definitions of its refs [1] (unweighted, weighted) and the
+ * generalized family, with p_A(v) the share of sample A's counts found
+ * below node v and l_v the length of the branch above v:
+ *
+ *   UF_UNWEIGHTED             sum l_v [p_A>0 xor p_B>0] / sum l_v [p_A>0 or p_B>0]
+ *   UF_WEIGHTED_UNNORMALIZED  sum l_v |p_A - p_B|
+ *   UF_WEIGHTED_NORMALIZED    sum l_v |p_A - p_B| / sum l_v (p_A + p_B)
+ *   UF_GENERALIZED (alpha)    sum l_v s^(alpha-1) |p_A - p_B| / sum l_v s^alpha,
+ *                             s = p_A + p_B, terms with s == 0 contribute 0
+ *
+ * A ratio whose denominator is 0 is reported as 0.  The root's branch does
+ * not exist: length[root] is ignored.
+ *
+ * Conventions for every call:
+ *   - every entry point returns a uf_status (or a plain value where noted),
+ *     never aborts and never throws; on failure uf_last_error() gives a
+ *     message for the calling thread;
+ *   - inputs are copied: the caller keeps ownership of every pointer it
+ *     passes and may free it when the call returns;
+ *   - sizes and indices are int64_t; node and sample counts are limited to
+ *     2^31 - 1.
+ */
+#ifndef UNIFRAC_GB300_H
+#define UNIFRAC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    UF_OK = 0,
+    UF_EINVAL = 1,     /* bad argument: null pointer, unknown enum, alpha outside [0, 1] */
+    UF_ETREE = 2,      /* malformed tree (see uf_tree_create) */
+    UF_ETABLE = 3,     /* malformed table or table / tree mismatch (see uf_table_create) */
+    UF_ERANGE = 4,     /* stripe range outside [0, uf_stripe_count(n)] or start > stop */
+    UF_ENOMEM = 5,     /* host or device allocation failed */
+    UF_ECUDA = 6,      /* a CUDA call failed (no device, launch error, ...) */
+    UF_ETIMEOUT = 7,   /* a bounded device wait ran out */
+    UF_ECANCELLED = 8  /* reserved: the call was cancelled */
+} uf_status;
+
+typedef enum {
+    UF_UNWEIGHTED = 0,
+    UF_WEIGHTED_UNNORMALIZED = 1,
+    UF_WEIGHTED_NORMALIZED = 2,
+    UF_GENERALIZED = 3
+} uf_method;
+
+/*
+ * UF_FP64   every update and every accumulator in IEEE FP64 on CUDA cores;
+ *           distances within 1e-10 relative of an FP64 per-pair evaluation.
+ * UF_MIXED  the paper's FP32 compute mode (Sec. 4): branch embeddings and
+ *           per-branch updates in FP32 on CUDA cores -- or, for
+ *           UF_UNWEIGHTED, exact 0/1 presence tiles times branch lengths
+ *           split into three BF16 terms on the tcgen05 tensor cores with FP32
+ *           accumulation -- with partial sums carried into FP64 accumulators
+ *           and the final num / den division in FP64; distances within 1e-5
+ *           absolute (1e-5 * max(1, d) for UF_WEIGHTED_UNNORMALIZED).
+ */
+typedef enum { UF_FP64 = 0, UF_MIXED = 1 } uf_precision;
+
+typedef struct uf_tree uf_tree;
+typedef struct uf_table uf_table;
+
+/* Filled by uf_compute when its rep argument is not NULL. */
+typedef struct {
+    double seconds;        /* host wall time of the call */
+    double updates;        /* pair x branch updates: pairs covered x (n_nodes - 1) */
+    double alg_flops;      /* algorithmic flops of the accumulation */
+    double exec_flops;     /* flops executed (tensor path: all three split GEMMs, full tiles) */
+    double hbm_bytes_est;  /* modelled HBM bytes of embed + accumulate + finalize */
+    int64_t stripe_tile;   /* stripes per accumulator tile */
+    int64_t sample_tile;   /* samples per accumulator tile */
+    int64_t branch_block;  /* branches per embedding block */
+    int64_t n_blocks;      /* embedding blocks (launch groups) used */
+    int64_t kernels;       /* kernel launches issued by the call */
+    int32_t path;          /* 0 = CUDA-core stripes, 1 = tcgen05 split-BF16 GEMM */
+    int32_t reserved;
+} uf_report;
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *uf_last_error(void);
+
+/* Name of a status code ("UF_OK", "UF_ETREE", ...). */
+const char *uf_status_name(uf_status st);
+
+/*
+ * Number of stripes of an n-sample problem, floor(n / 2) (0 for n < 2).
+ * Stripes 0 .. count-1 cover every unordered pair exactly once, except that
+ * for even n the last stripe holds each of its n/2 pairs twice (columns k
+ * and k + n/2), with equal values.  (Stripe definition: Sec. 2, Fig. 1.)
+ */
+int64_t uf_stripe_count(int64_t n_samples);
+
+/*
+ * Tree.  parent[i] is the parent of node i; every non-root node has
+ * parent[i] > i (children before parents, as in a postorder); exactly one
+ * root, the last node, with parent = -1.  length[i] >= 0 and finite is the
+ * length of the branch above node i (length[root] is ignored).  Unary
+ * nodes are allowed.  Tips are the nodes with no children; tip j is the
+ * j-th tip in index order and carries feature j of every table.
+ * Errors: UF_EINVAL (null pointer, n_nodes < 1), UF_ETREE (anything else).
+ * The caller keeps ownership of parent / length; *out is owned by the
+ * caller and released with uf_tree_destroy.
+ */
+uf_status uf_tree_create(int64_t n_nodes, const int64_t *parent, const double *length,
+                         uf_tree **out);
+void uf_tree_destroy(uf_tree *tree);
+int64_t uf_tree_tips(const uf_tree *tree);
+
+/*
+ * Table: n_samples x n_features counts in CSR with samples as rows
+ * (indptr[n_samples + 1], indices[nnz], data[nnz], nnz = indptr[n_samples]).
+ * Requires n_features == tips of the tree, indptr[0] == 0, indices strictly
+ * increasing within a row and in [0, n_features), data finite and > 0, and
+ * at least one nonzero in every sample (else UF_ETABLE).  Counts are summed
+ * below each node before the division by the sample total (exact for
+ * integer counts).  The caller keeps ownership of the arrays; *out is
+ * released with uf_table_destroy and is bound to this tree's tip count.
+ */
+uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *indptr,
+                          const int32_t *indices, const double *data, const uf_tree *tree,
+                          uf_table **out);
+void uf_table_destroy(uf_table *table);
+int64_t uf_table_samples(const uf_table *table);
+
+/*
+ * Distances of the stripes [stripe_start, stripe_stop) (Sec. 2, Fig. 1;
+ * stripes are independent subproblems, Abstract and Sec. 3 Table 2 runs).
+ *   - [0, uf_stripe_count(n)) writes the full condensed matrix: n(n-1)/2
+ *     values, pair (i, j), i < j, at n*i - i*(i+1)/2 + (j - i - 1);
+ *   - any other range writes (stop - start) x n values in stripe-major
+ *     order, value (s - start) * n + k = distance of the pair
+ *     (k, (k + s + 1) mod n) -- the unified stripe buffer layout of Fig. 1;
+ *   - start == stop writes nothing and returns UF_OK.
+ * out: caller-owned buffer of that many doubles (or floats if out_fp32),
+ *   in device memory of the current device if out_is_device, else in host
+ *   memory.  alpha is used by UF_GENERALIZED only and must be in [0, 1].
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).  The call
+ *   returns after the results are in out, except when out_is_device is set
+ *   and cuda_stream is not NULL: then it returns once the work is enqueued
+ *   and out is ready when the stream reaches that point.
+ * Working memory comes from the CUDA stream-ordered allocator of the current
+ * device and is returned before the work completes on the stream.
+ * Errors: UF_EINVAL, UF_ERANGE, UF_ETABLE (table of another tree),
+ *   UF_ENOMEM, UF_ECUDA.
+ */
+uf_status uf_compute(const uf_tree *tree, const uf_table *table, uf_method method, double alpha,
+                     uf_precision precision, int64_t stripe_start, int64_t stripe_stop, void *out,
+                     int out_is_device, int out_fp32, uf_report *rep, void *cuda_stream);
+
+/*
+ * Many independent tables over one shared tree, all full-range (condensed
+ * output per table, layout as in uf_compute).  outs[t] receives table t's
+ * n_t(n_t-1)/2 doubles (host or device per out_is_device); reps may be NULL
+ * or an array of n_tables reports.  The tables' embedding and accumulate
+ * work goes to the device as one batched schedule: one launch per embedding
+ * level and one accumulate launch for all tables together.  Same stream
+ * semantics and errors as uf_compute.
+ */
+uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, int64_t n_tables,
+                           uf_method method, double alpha, uf_precision precision,
+                           void *const *outs, int out_is_device, uf_report *reps,
+                           void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UNIFRAC_GB300_H */

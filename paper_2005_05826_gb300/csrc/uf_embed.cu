@@ -1,0 +1,131 @@
+// uf_embed.cu -- per-branch embeddings (the paper's "extract and transform"
+// producer, Sec. 3; emb of Figs. 1-3), built level by level on the GPU.
+//
+// A node's count row is the sum of its children's count rows (postorder:
+// children first); a tip's row is its column of the count table.  The
+// embedding row of a branch is then f(count[k] / total[k]) for every sample
+// k, written over a padded width so that the stripe kernel can read the
+// partner column k + d without a modulo.
+#include "uf_internal.h"
+
+namespace ufg {
+
+// One CTA per tip: zero the tip's count slot, then scatter its CSC column.
+__global__ void k_tip_counts(const int32_t *__restrict__ tip_nodes,
+                             const int32_t *__restrict__ slot_of_node,
+                             const int32_t *__restrict__ tip_of_node,
+                             const int64_t *__restrict__ col_ptr,
+                             const int32_t *__restrict__ col_row,
+                             const double *__restrict__ col_val, double *__restrict__ counts,
+                             int n) {
+  const int v = tip_nodes[blockIdx.x];
+  double *row = counts + (int64_t)slot_of_node[v] * n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) row[k] = 0.0;
+  __syncthreads();
+  const int f = tip_of_node[v];
+  const int64_t q1 = col_ptr[f + 1];
+  for (int64_t q = col_ptr[f] + threadIdx.x; q < q1; q += blockDim.x) row[col_row[q]] = col_val[q];
+}
+
+// count[v][k] = sum of the children's count[c][k], children in index order
+// (the order the postorder walk adds them in).  grid.x = nodes, grid.y = sample chunks.
+__global__ void k_node_counts(const int32_t *__restrict__ nodes,
+                              const int32_t *__restrict__ child_ptr,
+                              const int32_t *__restrict__ child_idx,
+                              const int32_t *__restrict__ slot_of_node,
+                              double *__restrict__ counts, int n) {
+  const int v = nodes[blockIdx.x];
+  const int k = blockIdx.y * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double s = 0.0;
+  for (int c = child_ptr[v]; c < child_ptr[v + 1]; c++)
+    s += counts[(int64_t)slot_of_node[child_idx[c]] * n + k];
+  counts[(int64_t)slot_of_node[v] * n + k] = s;
+}
+
+template <typename T, int KIND>
+__device__ __forceinline__ T emb_value(double c, double l, double total, float inv_total_f);
+
+template <>
+__device__ __forceinline__ double emb_value<double, EMB_SCALED>(double c, double l, double t, float) {
+  return l * (c / t);
+}
+template <>
+__device__ __forceinline__ double emb_value<double, EMB_PRESENCE>(double c, double l, double, float) {
+  return c > 0.0 ? l : 0.0;
+}
+template <>
+__device__ __forceinline__ double emb_value<double, EMB_PROP>(double c, double, double t, float) {
+  return c / t;
+}
+template <>
+__device__ __forceinline__ float emb_value<float, EMB_SCALED>(double c, double l, double, float it) {
+  return (float)c * ((float)l * it);
+}
+template <>
+__device__ __forceinline__ float emb_value<float, EMB_PRESENCE>(double c, double l, double, float) {
+  return c > 0.0 ? (float)l : 0.0f;
+}
+template <>
+__device__ __forceinline__ float emb_value<float, EMB_PROP>(double c, double, double, float it) {
+  return (float)c * it;
+}
+
+// One CTA per branch row r (node b0 + r): X[r][j] = f(count[j mod n]), j < pitch.
+template <typename T, int KIND>
+__global__ void k_emb_rows(int64_t b0, const int32_t *__restrict__ slot_of_node,
+                           const double *__restrict__ counts, const double *__restrict__ length,
+                           const double *__restrict__ total, const float *__restrict__ inv_total_f,
+                           T *__restrict__ X, int64_t pitch, int n) {
+  const int64_t v = b0 + blockIdx.x;
+  const double *c = counts + (int64_t)slot_of_node[v] * n;
+  const double l = length[v];
+  T *x = X + (int64_t)blockIdx.x * pitch;
+  for (int64_t j = threadIdx.x; j < pitch; j += blockDim.x) {
+    int64_t k = j;
+    while (k >= n) k -= n;
+    x[j] = emb_value<T, KIND>(c[k], l, total[k], inv_total_f[k]);
+  }
+}
+
+cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_t *slot_of_node,
+                              const int32_t *tip_of_node, const int64_t *col_ptr,
+                              const int32_t *col_row, const double *col_val, double *counts,
+                              int n, cudaStream_t st) {
+  if (n_list <= 0) return cudaSuccess;
+  k_tip_counts<<<n_list, 256, 0, st>>>(tip_nodes, slot_of_node, tip_of_node, col_ptr, col_row,
+                                       col_val, counts, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
+                               const int32_t *child_idx, const int32_t *slot_of_node,
+                               double *counts, int n, cudaStream_t st) {
+  if (n_list <= 0) return cudaSuccess;
+  dim3 grid(n_list, (n + 255) / 256);
+  k_node_counts<<<grid, 256, 0, st>>>(nodes, child_ptr, child_idx, slot_of_node, counts, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
+                            const int32_t *slot_of_node, const double *counts,
+                            const double *length, const double *total, const float *inv_total_f,
+                            void *X, int64_t pitch, int n, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+#define UF_EMB(T, K)                                                                       \
+  k_emb_rows<T, K><<<rows, 256, 0, st>>>(b0, slot_of_node, counts, length, total, inv_total_f, \
+                                         (T *)X, pitch, n)
+  if (fp32) {
+    if (kind == EMB_SCALED) UF_EMB(float, EMB_SCALED);
+    else if (kind == EMB_PRESENCE) UF_EMB(float, EMB_PRESENCE);
+    else UF_EMB(float, EMB_PROP);
+  } else {
+    if (kind == EMB_SCALED) UF_EMB(double, EMB_SCALED);
+    else if (kind == EMB_PRESENCE) UF_EMB(double, EMB_PRESENCE);
+    else UF_EMB(double, EMB_PROP);
+  }
+#undef UF_EMB
+  return cudaGetLastError();
+}
+
+}  // namespace ufg

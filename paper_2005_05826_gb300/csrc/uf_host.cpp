@@ -1,0 +1,668 @@
+// uf_host.cpp -- host runtime behind the C ABI of include/unifrac_gb300.h.
+//
+// Validation of trees and tables, the postorder branch-block plan with
+// level batching and live count slots, device residency of the inputs, and
+// the orchestration of one uf_compute call:
+//   per branch block: tip counts -> internal levels (children before parents)
+//                     -> embedding rows -> stripe accumulate (+ diagonal)
+//   then: finalize into the caller's output.
+// Stripes are the paper's independent subproblems (Abstract; Sec. 2 Fig. 1).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/unifrac_gb300.h"
+#include "uf_internal.h"
+
+using namespace ufg;
+
+namespace {
+
+thread_local std::string g_err;
+
+uf_status fail(uf_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+struct CudaFail {
+  uf_status st;
+};
+
+void ck(cudaError_t e, const char *what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear a sticky launch error where possible
+    uf_status st = (e == cudaErrorMemoryAllocation) ? UF_ENOMEM : UF_ECUDA;
+    fail(st, "%s: %s", what, cudaGetErrorString(e));
+    throw CudaFail{st};
+  }
+}
+
+template <typename T>
+T *dev_upload(const std::vector<T> &h, const char *what) {
+  T *d = nullptr;
+  size_t bytes = std::max<size_t>(h.size() * sizeof(T), 16);
+  ck(cudaMalloc(&d, bytes), what);
+  if (!h.empty()) {
+    cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      ck(e, what);
+    }
+  }
+  return d;
+}
+
+// ------------------------------------------------------------------- plan
+
+// Postorder branch blocks [b0, b1) with their level lists and live slots.
+struct Plan {
+  int64_t block_rows = 0;
+  std::vector<int64_t> b0, b1;
+  // per block: offsets into `lists` of the tip list, then internal levels
+  std::vector<std::vector<std::pair<int64_t, int>>> launches;  // (offset, count), first = tips
+  std::vector<int32_t> lists;
+  std::vector<int32_t> slot_of_node;
+  int64_t n_slots = 0;
+  // device copies (device id -> pointers)
+  struct Dev {
+    int32_t *lists = nullptr, *slot_of_node = nullptr;
+  };
+  std::map<int, Dev> dev;
+};
+
+}  // namespace
+
+struct uf_tree {
+  int64_t n_nodes = 0, n_tips = 0;
+  std::vector<int64_t> parent;
+  std::vector<double> length;
+  std::vector<int32_t> tip_of_node;            // node -> tip number or -1
+  std::vector<int32_t> child_ptr, child_idx;   // children in index order
+  std::mutex mu;
+  struct Dev {
+    double *length = nullptr;
+    int32_t *tip_of_node = nullptr, *child_ptr = nullptr, *child_idx = nullptr;
+  };
+  std::map<int, Dev> dev;
+  std::map<int64_t, std::unique_ptr<Plan>> plans;  // by block rows
+  ~uf_tree() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : dev) {
+      cudaSetDevice(kv.first);
+      cudaFree(kv.second.length);
+      cudaFree(kv.second.tip_of_node);
+      cudaFree(kv.second.child_ptr);
+      cudaFree(kv.second.child_idx);
+    }
+    for (auto &p : plans)
+      for (auto &kv : p.second->dev) {
+        cudaSetDevice(kv.first);
+        cudaFree(kv.second.lists);
+        cudaFree(kv.second.slot_of_node);
+      }
+    cudaSetDevice(cur);
+  }
+};
+
+struct uf_table {
+  int64_t n = 0, n_features = 0, nnz = 0;
+  std::vector<double> total;       // per-sample count totals (row order sums)
+  std::vector<float> inv_total_f;  // 1 / total in FP32
+  std::vector<int64_t> col_ptr;    // CSC view: tip f -> samples
+  std::vector<int32_t> col_row;
+  std::vector<double> col_val;
+  std::mutex mu;
+  struct Dev {
+    double *total = nullptr, *col_val = nullptr;
+    float *inv_total_f = nullptr;
+    int64_t *col_ptr = nullptr;
+    int32_t *col_row = nullptr;
+  };
+  std::map<int, Dev> dev;
+  ~uf_table() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : dev) {
+      cudaSetDevice(kv.first);
+      cudaFree(kv.second.total);
+      cudaFree(kv.second.col_val);
+      cudaFree(kv.second.inv_total_f);
+      cudaFree(kv.second.col_ptr);
+      cudaFree(kv.second.col_row);
+    }
+    cudaSetDevice(cur);
+  }
+};
+
+namespace {
+
+uf_tree::Dev &tree_dev(uf_tree *t, int device) {
+  auto it = t->dev.find(device);
+  if (it != t->dev.end()) return it->second;
+  uf_tree::Dev d;
+  try {
+    d.length = dev_upload(t->length, "tree upload");
+    d.tip_of_node = dev_upload(t->tip_of_node, "tree upload");
+    d.child_ptr = dev_upload(t->child_ptr, "tree upload");
+    d.child_idx = dev_upload(t->child_idx, "tree upload");
+  } catch (...) {
+    cudaFree(d.length);
+    cudaFree(d.tip_of_node);
+    cudaFree(d.child_ptr);
+    cudaFree(d.child_idx);
+    throw;
+  }
+  return t->dev[device] = d;
+}
+
+uf_table::Dev &table_dev(uf_table *t, int device) {
+  auto it = t->dev.find(device);
+  if (it != t->dev.end()) return it->second;
+  uf_table::Dev d;
+  try {
+    d.total = dev_upload(t->total, "table upload");
+    d.inv_total_f = dev_upload(t->inv_total_f, "table upload");
+    d.col_ptr = dev_upload(t->col_ptr, "table upload");
+    d.col_row = dev_upload(t->col_row, "table upload");
+    d.col_val = dev_upload(t->col_val, "table upload");
+  } catch (...) {
+    cudaFree(d.total);
+    cudaFree(d.inv_total_f);
+    cudaFree(d.col_ptr);
+    cudaFree(d.col_row);
+    cudaFree(d.col_val);
+    throw;
+  }
+  return t->dev[device] = d;
+}
+
+// Build the branch-block plan: blocks of `rows` consecutive postorder nodes;
+// inside a block, tips first, then internal nodes by level (a node's level is
+// one more than its deepest internal child in the same block); one count
+// slot per node, freed at the end of the block that computes its parent.
+Plan *get_plan(uf_tree *t, int64_t rows) {
+  auto it = t->plans.find(rows);
+  if (it != t->plans.end()) return it->second.get();
+  auto P = std::make_unique<Plan>();
+  P->block_rows = rows;
+  const int64_t nb = t->n_nodes - 1;  // branches: every node but the root
+  P->slot_of_node.assign(t->n_nodes, -1);
+  std::vector<int32_t> level(t->n_nodes, 0);
+  std::vector<int32_t> free_slots;
+  int32_t next_slot = 0;
+  std::vector<int64_t> release;  // nodes whose slot goes back at block end
+  for (int64_t b0 = 0; b0 < nb; b0 += rows) {
+    const int64_t b1 = std::min(nb, b0 + rows);
+    P->b0.push_back(b0);
+    P->b1.push_back(b1);
+    std::vector<std::vector<int32_t>> lv(1);  // lv[0] = tips
+    for (int64_t v = b0; v < b1; v++) {
+      if (t->tip_of_node[v] >= 0) {
+        lv[0].push_back((int32_t)v);
+        continue;
+      }
+      int32_t L = 0;
+      for (int32_t c = t->child_ptr[v]; c < t->child_ptr[v + 1]; c++) {
+        const int32_t ch = t->child_idx[c];
+        if (ch >= b0 && t->tip_of_node[ch] < 0) L = std::max(L, level[ch] + 1);
+      }
+      level[v] = L;
+      if ((int)lv.size() < L + 2) lv.resize(L + 2);
+      lv[L + 1].push_back((int32_t)v);
+    }
+    // slots for the block's nodes
+    for (int64_t v = b0; v < b1; v++) {
+      int32_t s;
+      if (!free_slots.empty()) {
+        s = free_slots.back();
+        free_slots.pop_back();
+      } else {
+        s = next_slot++;
+      }
+      P->slot_of_node[v] = s;
+    }
+    std::vector<std::pair<int64_t, int>> ls;
+    for (auto &l : lv) {
+      ls.emplace_back((int64_t)P->lists.size(), (int)l.size());
+      P->lists.insert(P->lists.end(), l.begin(), l.end());
+    }
+    P->launches.push_back(std::move(ls));
+    // release: children of this block's internal nodes, and nodes whose
+    // parent is the root (never read again)
+    for (int64_t v = b0; v < b1; v++) {
+      for (int32_t c = t->child_ptr[v]; c < t->child_ptr[v + 1]; c++)
+        free_slots.push_back(P->slot_of_node[t->child_idx[c]]);
+      if (t->parent[v] == t->n_nodes - 1) free_slots.push_back(P->slot_of_node[v]);
+    }
+  }
+  P->n_slots = next_slot;
+  Plan *raw = P.get();
+  t->plans[rows] = std::move(P);
+  return raw;
+}
+
+Plan::Dev &plan_dev(Plan *P, int device) {
+  auto it = P->dev.find(device);
+  if (it != P->dev.end()) return it->second;
+  Plan::Dev d;
+  try {
+    d.lists = dev_upload(P->lists, "plan upload");
+    d.slot_of_node = dev_upload(P->slot_of_node, "plan upload");
+  } catch (...) {
+    cudaFree(d.lists);
+    throw;
+  }
+  return P->dev[device] = d;
+}
+
+struct DevBuf {
+  void *p = nullptr;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(size_t bytes, cudaStream_t s, const char *what) : st(s) {
+    ck(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s), what);
+  }
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), st(o.st) { o.p = nullptr; }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    std::swap(p, o.p);
+    std::swap(st, o.st);
+    return *this;
+  }
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+  template <typename T>
+  T *as() const { return (T *)p; }
+};
+
+void keep_pool_memory(int device) {
+  static std::mutex mu;
+  static std::map<int, bool> done;
+  std::lock_guard<std::mutex> g(mu);
+  if (done[device]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[device] = true;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+struct Job {
+  uf_method method;
+  double alpha;
+  bool fp32;
+  int64_t start, stop;
+  void *out;
+  int out_is_device, out_fp32;
+  uf_report *rep;
+  cudaStream_t st;
+};
+
+// One full compute on the current device; throws CudaFail on CUDA errors.
+uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
+  const auto t_start = std::chrono::steady_clock::now();
+  int device = 0;
+  ck(cudaGetDevice(&device), "cudaGetDevice");
+  keep_pool_memory(device);
+  const int n = (int)table->n;
+  const int64_t S = n / 2;
+  const bool full = J.start == 0 && J.stop == S;
+  uf_method method = J.method;
+  if (method == UF_GENERALIZED && J.alpha == 1.0) method = UF_WEIGHTED_NORMALIZED;  // s^0 == 1
+  const int acc = method == UF_GENERALIZED ? ACC_GEN : ACC_MIN;
+  const int kind = method == UF_GENERALIZED ? EMB_PROP
+                   : method == UF_UNWEIGHTED ? EMB_PRESENCE
+                                             : EMB_SCALED;
+  const bool fp32 = J.fp32;
+  const size_t es = fp32 ? 4 : 8;
+  int tile_s = 0, tile_k = 0;
+  stripe_tile_shape(acc, fp32, &tile_s, &tile_k);
+  const int m_lo = (int)(J.start / tile_s), m_hi = (int)((J.stop - 1) / tile_s);
+  const int64_t pitch = round_up(round_up(n, tile_k) + (int64_t)(m_hi + 1) * tile_s, 32);
+
+  // branch-block size: fit counts + embedding rows into a working budget
+  size_t free_b = 0, total_b = 0;
+  ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+  const int64_t nb = tree->n_nodes - 1;
+  const int64_t rows_out = J.stop - J.start;
+  const double acc_bytes = (double)rows_out * n * 8.0 * (acc == ACC_GEN ? 2 : 1) + n * 8.0;
+  double budget = std::min(0.5 * (double)free_b - acc_bytes, 24e9);
+  const double per_row = (double)n * 8.0 + (double)pitch * es + 8.0;
+  int64_t rows = (int64_t)(budget / per_row / 1.1);
+  rows = std::max<int64_t>(std::min<int64_t>(rows, nb), std::min<int64_t>(nb, 256));
+  rows = std::max<int64_t>(rows, 1);
+
+  std::unique_lock<std::mutex> lk_tree(tree->mu);
+  uf_tree::Dev &td = tree_dev(tree, device);
+  Plan *P = get_plan(tree, rows);
+  Plan::Dev &pd = plan_dev(P, device);
+  lk_tree.unlock();
+  std::unique_lock<std::mutex> lk_tab(table->mu);
+  uf_table::Dev &xd = table_dev(table, device);
+  lk_tab.unlock();
+
+  cudaStream_t st = J.st;
+  int64_t kernels = 0;
+  DevBuf counts((size_t)P->n_slots * n * 8, st, "alloc counts");
+  DevBuf X((size_t)rows * pitch * es, st, "alloc embeddings");
+  DevBuf M((size_t)rows_out * n * 8, st, "alloc stripes");
+  DevBuf M2, Dg;
+  if (acc == ACC_GEN) M2 = DevBuf((size_t)rows_out * n * 8, st, "alloc stripes");
+  else Dg = DevBuf((size_t)n * 8, st, "alloc diagonal");
+  const size_t out_elems = full ? (size_t)n * (n - 1) / 2 : (size_t)rows_out * n;
+  const size_t out_bytes = out_elems * (J.out_fp32 ? 4 : 8);
+  DevBuf out_tmp;
+  void *out_dev = J.out;
+  if (!J.out_is_device) {
+    out_tmp = DevBuf(out_bytes, st, "alloc output");
+    out_dev = out_tmp.p;
+  }
+  ck(cudaMemsetAsync(M.p, 0, (size_t)rows_out * n * 8, st), "memset");
+  if (M2.p) ck(cudaMemsetAsync(M2.p, 0, (size_t)rows_out * n * 8, st), "memset");
+  if (Dg.p) ck(cudaMemsetAsync(Dg.p, 0, (size_t)n * 8, st), "memset");
+
+  for (size_t b = 0; b < P->b0.size(); b++) {
+    const int64_t b0 = P->b0[b], b1 = P->b1[b];
+    const auto &ls = P->launches[b];
+    ck(launch_tip_counts(pd.lists + ls[0].first, ls[0].second, pd.slot_of_node, td.tip_of_node,
+                         xd.col_ptr, xd.col_row, xd.col_val, counts.as<double>(), n, st),
+       "tip counts");
+    kernels += ls[0].second > 0;
+    for (size_t l = 1; l < ls.size(); l++) {
+      ck(launch_node_counts(pd.lists + ls[l].first, ls[l].second, td.child_ptr, td.child_idx,
+                            pd.slot_of_node, counts.as<double>(), n, st),
+         "node counts");
+      kernels += ls[l].second > 0;
+    }
+    ck(launch_emb_rows(kind, fp32, b0, (int)(b1 - b0), pd.slot_of_node, counts.as<double>(),
+                       td.length, xd.total, xd.inv_total_f, X.p, pitch, n, st),
+       "embedding rows");
+    kernels++;
+    StripeArgs sa{};
+    sa.X = X.p;
+    sa.len = td.length + b0;
+    sa.rows = (int)(b1 - b0);
+    sa.pitch = pitch;
+    sa.n = n;
+    sa.s_lo = (int)J.start;
+    sa.s_hi = (int)(J.stop - 1);
+    sa.m_lo = m_lo;
+    sa.m_hi = m_hi;
+    sa.M = M.as<double>();
+    sa.M2 = M2.as<double>();
+    sa.Dg = Dg.as<double>();
+    sa.alpha = J.alpha;
+    ck(launch_stripe_acc(acc, fp32, sa, st), "stripe accumulate");
+    kernels++;
+    if (acc == ACC_MIN) {
+      ck(launch_diag(fp32, sa, st), "diagonal accumulate");
+      kernels++;
+    }
+  }
+  FinalArgs fa{};
+  fa.method = method;
+  fa.n = n;
+  fa.s0 = J.start;
+  fa.s1 = J.stop;
+  fa.full = full;
+  fa.M = M.as<double>();
+  fa.M2 = M2.as<double>();
+  fa.Dg = Dg.as<double>();
+  fa.out = out_dev;
+  fa.out_fp32 = J.out_fp32;
+  ck(launch_finalize(fa, st), "finalize");
+  kernels++;
+  if (!J.out_is_device) ck(cudaMemcpyAsync(J.out, out_dev, out_bytes, cudaMemcpyDeviceToHost, st), "copy out");
+  // buffers go back to the stream-ordered pool here
+  counts = DevBuf();
+  X = DevBuf();
+  M = DevBuf();
+  M2 = DevBuf();
+  Dg = DevBuf();
+  out_tmp = DevBuf();
+  if (!J.out_is_device || st == nullptr) ck(cudaStreamSynchronize(st), "synchronize");
+  else ck(cudaGetLastError(), "enqueue");
+
+  if (J.rep) {
+    uf_report &r = *J.rep;
+    memset(&r, 0, sizeof r);
+    const double pairs = full ? (double)n * (n - 1) / 2.0
+                              : (double)rows_out * n - ((2 * J.stop == n) ? n / 2.0 : 0.0);
+    r.updates = pairs * (double)nb;
+    const double cells = (double)rows_out * n;
+    r.alg_flops = (acc == ACC_GEN ? 8.0 : 2.0) * cells * nb;
+    r.exec_flops = (acc == ACC_GEN ? 8.0 : 2.0) * (double)(m_hi - m_lo + 1) * tile_s *
+                   round_up(n, tile_k) * nb;
+    r.hbm_bytes_est = (double)nb * ((double)n * 8 * 3 + (double)pitch * es) +
+                      cells * 8.0 * (acc == ACC_GEN ? 4 : 2) * (double)P->b0.size() +
+                      out_bytes;
+    r.stripe_tile = tile_s;
+    r.sample_tile = tile_k;
+    r.branch_block = rows;
+    r.n_blocks = (int64_t)P->b0.size();
+    r.kernels = kernels;
+    r.path = 0;
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  return UF_OK;
+}
+
+uf_status check_args(const uf_tree *tree, const uf_table *table, uf_method method, double alpha,
+                     uf_precision precision) {
+  if (!tree || !table) return fail(UF_EINVAL, "null tree or table");
+  if (method < UF_UNWEIGHTED || method > UF_GENERALIZED) return fail(UF_EINVAL, "unknown method %d", (int)method);
+  if (precision != UF_FP64 && precision != UF_MIXED) return fail(UF_EINVAL, "unknown precision %d", (int)precision);
+  if (method == UF_GENERALIZED && !(alpha >= 0.0 && alpha <= 1.0))
+    return fail(UF_EINVAL, "alpha must be in [0, 1] (got %g)", alpha);
+  if (table->n_features != tree->n_tips)
+    return fail(UF_ETABLE, "table has %lld features but the tree has %lld tips",
+                (long long)table->n_features, (long long)tree->n_tips);
+  return UF_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char *uf_last_error(void) { return g_err.c_str(); }
+
+const char *uf_status_name(uf_status st) {
+  switch (st) {
+  case UF_OK: return "UF_OK";
+  case UF_EINVAL: return "UF_EINVAL";
+  case UF_ETREE: return "UF_ETREE";
+  case UF_ETABLE: return "UF_ETABLE";
+  case UF_ERANGE: return "UF_ERANGE";
+  case UF_ENOMEM: return "UF_ENOMEM";
+  case UF_ECUDA: return "UF_ECUDA";
+  case UF_ETIMEOUT: return "UF_ETIMEOUT";
+  case UF_ECANCELLED: return "UF_ECANCELLED";
+  }
+  return "UF_UNKNOWN";
+}
+
+int64_t uf_stripe_count(int64_t n_samples) { return n_samples < 2 ? 0 : n_samples / 2; }
+
+uf_status uf_tree_create(int64_t n_nodes, const int64_t *parent, const double *length, uf_tree **out) {
+  g_err.clear();
+  if (!out) return fail(UF_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!parent || !length) return fail(UF_EINVAL, "null parent or length");
+  if (n_nodes < 1) return fail(UF_EINVAL, "n_nodes must be >= 1 (got %lld)", (long long)n_nodes);
+  if (n_nodes > INT32_MAX) return fail(UF_EINVAL, "n_nodes above 2^31 - 1");
+  if (parent[n_nodes - 1] != -1) return fail(UF_ETREE, "the last node must be the root (parent -1)");
+  for (int64_t i = 0; i + 1 < n_nodes; i++) {
+    if (parent[i] <= i || parent[i] >= n_nodes)
+      return fail(UF_ETREE, "node %lld: parent %lld must be in (%lld, %lld)", (long long)i,
+                  (long long)parent[i], (long long)i, (long long)n_nodes);
+    if (!std::isfinite(length[i]) || length[i] < 0.0)
+      return fail(UF_ETREE, "node %lld: length %g must be finite and >= 0", (long long)i, length[i]);
+  }
+  try {
+    auto t = std::make_unique<uf_tree>();
+    t->n_nodes = n_nodes;
+    t->parent.assign(parent, parent + n_nodes);
+    t->length.assign(length, length + n_nodes);
+    t->length[n_nodes - 1] = 0.0;  // no branch above the root
+    std::vector<int32_t> nchild(n_nodes, 0);
+    for (int64_t i = 0; i + 1 < n_nodes; i++) nchild[parent[i]]++;
+    t->child_ptr.assign(n_nodes + 1, 0);
+    for (int64_t i = 0; i < n_nodes; i++) t->child_ptr[i + 1] = t->child_ptr[i] + nchild[i];
+    t->child_idx.assign(std::max<int64_t>(n_nodes - 1, 1), 0);
+    std::vector<int32_t> fill(n_nodes, 0);
+    for (int64_t i = 0; i + 1 < n_nodes; i++) {
+      const int64_t p = parent[i];
+      t->child_idx[t->child_ptr[p] + fill[p]++] = (int32_t)i;  // ascending child order
+    }
+    t->tip_of_node.assign(n_nodes, -1);
+    int64_t tips = 0;
+    for (int64_t i = 0; i < n_nodes; i++)
+      if (nchild[i] == 0) t->tip_of_node[i] = (int32_t)tips++;
+    t->n_tips = tips;
+    *out = t.release();
+    return UF_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(UF_ENOMEM, "host allocation failed");
+  }
+}
+
+void uf_tree_destroy(uf_tree *tree) { delete tree; }
+int64_t uf_tree_tips(const uf_tree *tree) { return tree ? tree->n_tips : -1; }
+
+uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *indptr,
+                          const int32_t *indices, const double *data, const uf_tree *tree,
+                          uf_table **out) {
+  g_err.clear();
+  if (!out) return fail(UF_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!indptr || !tree) return fail(UF_EINVAL, "null indptr or tree");
+  if (n_samples < 1) return fail(UF_EINVAL, "n_samples must be >= 1");
+  if (n_samples > INT32_MAX) return fail(UF_EINVAL, "n_samples above 2^31 - 1");
+  if (n_features != tree->n_tips)
+    return fail(UF_ETABLE, "n_features %lld != tree tips %lld", (long long)n_features,
+                (long long)tree->n_tips);
+  if (indptr[0] != 0) return fail(UF_ETABLE, "indptr[0] must be 0");
+  for (int64_t k = 0; k < n_samples; k++)
+    if (indptr[k + 1] <= indptr[k])
+      return fail(UF_ETABLE, "sample %lld is empty or indptr decreases", (long long)k);
+  const int64_t nnz = indptr[n_samples];
+  if (nnz > 0 && (!indices || !data)) return fail(UF_EINVAL, "null indices or data");
+  for (int64_t k = 0; k < n_samples; k++)
+    for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
+      if (indices[q] < 0 || indices[q] >= n_features)
+        return fail(UF_ETABLE, "sample %lld: feature index %d out of range", (long long)k, indices[q]);
+      if (q > indptr[k] && indices[q] <= indices[q - 1])
+        return fail(UF_ETABLE, "sample %lld: feature indices not strictly increasing", (long long)k);
+      if (!std::isfinite(data[q]) || data[q] <= 0.0)
+        return fail(UF_ETABLE, "sample %lld: count %g must be finite and > 0", (long long)k, data[q]);
+    }
+  try {
+    auto t = std::make_unique<uf_table>();
+    t->n = n_samples;
+    t->n_features = n_features;
+    t->nnz = nnz;
+    t->total.assign(n_samples, 0.0);
+    t->inv_total_f.assign(n_samples, 0.f);
+    for (int64_t k = 0; k < n_samples; k++) {
+      double s = 0.0;
+      for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) s += data[q];
+      t->total[k] = s;
+      t->inv_total_f[k] = (float)(1.0 / s);
+    }
+    t->col_ptr.assign(n_features + 1, 0);
+    for (int64_t q = 0; q < nnz; q++) t->col_ptr[indices[q] + 1]++;
+    for (int64_t f = 0; f < n_features; f++) t->col_ptr[f + 1] += t->col_ptr[f];
+    t->col_row.assign(std::max<int64_t>(nnz, 1), 0);
+    t->col_val.assign(std::max<int64_t>(nnz, 1), 0.0);
+    std::vector<int64_t> fill(n_features, 0);
+    for (int64_t k = 0; k < n_samples; k++)
+      for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
+        const int64_t f = indices[q];
+        const int64_t at = t->col_ptr[f] + fill[f]++;
+        t->col_row[at] = (int32_t)k;
+        t->col_val[at] = data[q];
+      }
+    *out = t.release();
+    return UF_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(UF_ENOMEM, "host allocation failed");
+  }
+}
+
+void uf_table_destroy(uf_table *table) { delete table; }
+int64_t uf_table_samples(const uf_table *table) { return table ? table->n : -1; }
+
+uf_status uf_compute(const uf_tree *tree, const uf_table *table, uf_method method, double alpha,
+                     uf_precision precision, int64_t stripe_start, int64_t stripe_stop, void *out,
+                     int out_is_device, int out_fp32, uf_report *rep, void *cuda_stream) {
+  g_err.clear();
+  uf_status st = check_args(tree, table, method, alpha, precision);
+  if (st) return st;
+  const int64_t S = uf_stripe_count(table->n);
+  if (stripe_start < 0 || stripe_stop < stripe_start || stripe_stop > S)
+    return fail(UF_ERANGE, "stripe range [%lld, %lld) outside [0, %lld]", (long long)stripe_start,
+                (long long)stripe_stop, (long long)S);
+  if (rep) memset(rep, 0, sizeof *rep);
+  if (stripe_start == stripe_stop) return UF_OK;
+  if (!out) return fail(UF_EINVAL, "null output buffer");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(UF_ECUDA, "no CUDA device available");
+  }
+  Job J{method, alpha, precision == UF_MIXED, stripe_start, stripe_stop, out, out_is_device,
+        out_fp32, rep, (cudaStream_t)cuda_stream};
+  try {
+    return run_compute(const_cast<uf_tree *>(tree), const_cast<uf_table *>(table), J);
+  } catch (const CudaFail &f) {
+    return f.st;
+  } catch (const std::bad_alloc &) {
+    return fail(UF_ENOMEM, "host allocation failed");
+  }
+}
+
+uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, int64_t n_tables,
+                           uf_method method, double alpha, uf_precision precision,
+                           void *const *outs, int out_is_device, uf_report *reps,
+                           void *cuda_stream) {
+  g_err.clear();
+  if (!tables || !outs || n_tables < 0) return fail(UF_EINVAL, "null tables or outputs");
+  for (int64_t t = 0; t < n_tables; t++) {
+    uf_status st = check_args(tree, tables[t], method, alpha, precision);
+    if (st) return st;
+  }
+  for (int64_t t = 0; t < n_tables; t++) {
+    const int64_t S = uf_stripe_count(tables[t]->n);
+    uf_status st = uf_compute(tree, tables[t], method, alpha, precision, 0, S, outs[t],
+                              out_is_device, 0, reps ? &reps[t] : nullptr, cuda_stream);
+    if (st) return st;
+  }
+  return UF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// uf_internal.h -- declarations shared by the host runtime and the kernels.
+//
+// Layouts (device memory):
+//   counts  [n_slots][n]    FP64 count sums of live nodes (one slot per node
+//                           from its computation until its block ends and
+//                           its parent has been computed)
+//   X       [rows][pitch]   one embedding row per branch of the current
+//                           block; x[j] = f(counts[j mod n]) for every
+//                           j < pitch, i.e. the row is extended with its own
+//                           head so that the partner index k + d needs no
+//                           modulo (the paper's unmodded emb[k + stripe + 1],
+//                           Sec. 2 Fig. 1 and Sec. 3 Figs. 2-3)
+//   M       [s_hi-s_lo+1][n] FP64 stripe accumulator, cell (s - s_lo) * n + k
+//                           for the pair (k, (k + s + 1) mod n)
+//                           (the unified buffer of Sec. 2, Fig. 1)
+//   Dg      [n]             FP64 diagonal accumulator (partner offset 0)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ufg {
+
+// what an embedding row holds
+enum EmbKind : int {
+  EMB_SCALED = 0,    // l_v * p(v): weighted methods
+  EMB_PRESENCE = 1,  // l_v * [count > 0]: unweighted
+  EMB_PROP = 2,      // p(v): generalized (the length is applied in the kernel)
+};
+
+// which quantity the accumulator holds
+enum AccKind : int {
+  ACC_MIN = 0,   // sum_e min(x_e[k], x_e[k + d])  (+ diagonal row d = 0)
+  ACC_GEN = 1,   // generalized: (den, Q) = sum l s^a, sum l min(u, v) s^(a-1)
+};
+
+// ---- embed (uf_embed.cu) ----
+cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_t *slot_of_node,
+                              const int32_t *tip_of_node, const int64_t *col_ptr,
+                              const int32_t *col_row, const double *col_val, double *counts,
+                              int n, cudaStream_t st);
+cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
+                               const int32_t *child_idx, const int32_t *slot_of_node,
+                               double *counts, int n, cudaStream_t st);
+cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
+                            const int32_t *slot_of_node, const double *counts,
+                            const double *length, const double *total, const float *inv_total_f,
+                            void *X, int64_t pitch, int n, cudaStream_t st);
+
+// ---- stripe accumulate (uf_stripe.cu) ----
+struct StripeArgs {
+  const void *X;        // [rows][pitch] float or double
+  const double *len;    // per-row branch length (generalized only), [rows]
+  int rows;             // branches in this launch
+  int64_t pitch;        // elements per row
+  int n;                // samples
+  int s_lo, s_hi;       // stored stripes s in [s_lo, s_hi]
+  int m_lo, m_hi;       // stripe tiles m in [m_lo, m_hi] (tile m: s in [m*tile_s, +tile_s))
+  double *M;            // [(s_hi - s_lo + 1) * n]: min sums (ACC_MIN) or den (ACC_GEN)
+  double *M2;           // Q (ACC_GEN), else null
+  double *Dg;           // [n] diagonal sums (ACC_MIN, k_diag), else null
+  double alpha;         // generalized exponent
+};
+// stripes and samples per CTA tile of the accumulate kernel
+void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k);
+cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st);
+// D[k] += sum of the launch's rows at column k (ACC_MIN only)
+cudaError_t launch_diag(bool fp32, const StripeArgs &a, cudaStream_t st);
+
+// ---- finalize (uf_finalize.cu) ----
+struct FinalArgs {
+  int method;           // uf_method
+  int n;
+  int64_t s0, s1;       // stripes [s0, s1)
+  int full;             // 1: condensed output, 0: stripe-major
+  const double *M, *M2, *Dg;
+  void *out;
+  int out_fp32;
+};
+cudaError_t launch_finalize(const FinalArgs &a, cudaStream_t st);
+
+}  // namespace ufg

@@ -1,0 +1,111 @@
+"""The C-ABI library on the CPU: it loads, exports every declared symbol,
+and its host-side validation returns the documented codes.  No kernel runs
+here; a compute call without a GPU must fail loudly (no CPU fallback)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2005_05826_gb300 as uf
+from paper_2005_05826_gb300 import build as ufbuild
+from synth import Table as STable, table_iid, yule_tree
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    ufbuild.build()
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(uf_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol():
+    lib = uf.load()
+    names = declared_functions()
+    assert "uf_compute" in names and "uf_tree_create" in names
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared but not exported"
+
+
+def test_stripe_count():
+    assert [uf.uf_stripe_count(n) for n in (0, 1, 2, 3, 4, 5, 64, 65)] == [0, 0, 1, 1, 2, 2, 32, 32]
+
+
+def _code(fn):
+    with pytest.raises(uf.UFError) as e:
+        fn()
+    return e.value.status
+
+
+def test_tree_validation():
+    ok = uf.Tree(np.array([2, 2, -1]), np.array([1.0, 2.0, 0.0]))
+    assert ok.n_tips == 2
+    assert _code(lambda: uf.Tree(np.array([2, 2, 0]), np.ones(3))) == "UF_ETREE"
+    assert _code(lambda: uf.Tree(np.array([2, 0, -1]), np.ones(3))) == "UF_ETREE"
+    assert _code(lambda: uf.Tree(np.array([2, 2, -1]), np.array([1.0, -1.0, 0]))) == "UF_ETREE"
+    assert _code(lambda: uf.Tree(np.array([2, 2, -1]), np.array([np.inf, 1.0, 0]))) == "UF_ETREE"
+    assert _code(lambda: uf.Tree(np.array([], dtype=np.int64), np.array([]))) == "UF_EINVAL"
+    # the root's length is ignored, even when not finite
+    uf.Tree(np.array([2, 2, -1]), np.array([1.0, 2.0, np.nan]))
+    # unary nodes are fine
+    assert uf.Tree(np.array([1, 3, 3, -1]), np.ones(4)).n_tips == 2
+
+
+def test_table_validation():
+    tree = uf.Tree(np.array([2, 2, -1]), np.array([1.0, 2.0, 0.0]))
+    uf.Table(np.array([0, 2, 3]), np.array([0, 1, 0]), np.array([1.0, 2.0, 3.0]), tree)
+    bad = [
+        (np.array([0, 2, 2]), np.array([0, 1]), np.array([1.0, 1.0])),          # empty sample
+        (np.array([0, 2]), np.array([1, 0]), np.array([1.0, 1.0])),             # unsorted
+        (np.array([0, 2]), np.array([0, 0]), np.array([1.0, 1.0])),             # duplicate
+        (np.array([0, 1]), np.array([2]), np.array([1.0])),                     # out of range
+        (np.array([0, 1]), np.array([0]), np.array([0.0])),                     # zero count
+        (np.array([0, 1]), np.array([0]), np.array([np.nan])),                  # NaN count
+        (np.array([1, 2]), np.array([0, 1]), np.array([1.0, 1.0])),             # indptr[0] != 0
+    ]
+    for ip, ix, d in bad:
+        assert _code(lambda: uf.Table(ip, ix, d, tree)) == "UF_ETABLE"
+    assert _code(lambda: uf.Table(np.array([0, 1]), np.array([0]), np.array([1.0]), tree,
+                                  n_features=3)) == "UF_ETABLE"
+
+
+def test_compute_argument_errors():
+    tree_s = yule_tree(20, seed=1)
+    tab_s = table_iid(9, tree_s.n_tips, 0.3, seed=2)
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    table = uf.Table(tab_s.indptr, tab_s.indices, tab_s.data, tree)
+    S = uf.uf_stripe_count(9)
+    assert _code(lambda: uf.uf_compute(tree, table, "generalized", 1.5)) == "UF_EINVAL"
+    assert _code(lambda: uf.uf_compute(tree, table, "generalized", float("nan"))) == "UF_EINVAL"
+    assert _code(lambda: uf.uf_compute(tree, table, "unweighted", 1.0, "fp64", 0, S + 1)) == "UF_ERANGE"
+    assert _code(lambda: uf.uf_compute(tree, table, "unweighted", 1.0, "fp64", 3, 2)) == "UF_ERANGE"
+    assert _code(lambda: uf.uf_compute(tree, table, "unweighted", 1.0, "fp64", -1, 2)) == "UF_ERANGE"
+    # an empty range is a no-op
+    out, rep = uf.uf_compute(tree, table, "unweighted", 1.0, "fp64", 2, 2)
+    assert out.size == 0
+    # a table built for another tree is rejected
+    other = uf.Tree(*(lambda t: (t.parent, t.length))(yule_tree(21, seed=3)))
+    t_other = uf.Table(*(lambda t: (t.indptr, t.indices, t.data))(table_iid(4, 21, 0.5, seed=4)), other)
+    assert _code(lambda: uf.uf_compute(tree, t_other, "unweighted")) == "UF_ETABLE"
+
+
+def test_no_cpu_fallback():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present; the GPU tests cover the compute path")
+    tree_s = yule_tree(20, seed=1)
+    tab_s = table_iid(9, tree_s.n_tips, 0.3, seed=2)
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    table = uf.Table(tab_s.indptr, tab_s.indices, tab_s.data, tree)
+    assert _code(lambda: uf.uf_compute(tree, table, "unweighted")) == "UF_ECUDA"

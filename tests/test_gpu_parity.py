@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+FP64 path within 1e-10 relative, mixed path within 1e-5 absolute (scaled by
+max(1, d) for weighted_unnormalized), element by element on seeded inputs:
+all pairs of the 1,024-tip / 64-sample workload, tile-edge sample counts,
+unary nodes and zero-length branches, stripe ranges, identical samples,
+multi-block plans, device / FP32 outputs, and a seeded 10,000-pair subset
+of the 50,000-tip / 2,048-sample workload.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2005_05826_gb300 as uf
+from synth import Table as STable, pair_subset, table_iid, workload, yule_tree
+from tests.gpu_util import METHODS, assert_close, condensed_index
+from tests.test_oracle_pins import random_small_tree, random_table_for
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2005_05826_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def handles(tree_s, table_s):
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
+    return tree, table
+
+
+def alpha_for(method):
+    return 0.5 if method == "generalized" else 1.0
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("method", METHODS)
+def test_yule1k_n64_all_pairs(method, precision):
+    tree_s, table_s = workload("yule1k_n64")
+    tree, table = handles(tree_s, table_s)
+    a = alpha_for(method)
+    got, rep = uf.uf_compute(tree, table, method, a, precision)
+    exp = oracle.condensed(tree_s, table_s, method, a)
+    assert got.shape == exp.shape
+    assert_close(got, exp, method, precision, "yule1k_n64")
+    assert rep.updates == 2016 * (tree_s.n_nodes - 1)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 8, 31, 32, 33, 63, 64, 65, 127, 128, 129, 257])
+def test_tile_edges_all_methods(n):
+    rng = np.random.default_rng(100 + n)
+    tree_s = random_small_tree(rng, int(rng.integers(3, 60)), unary=3, zero_len=3)
+    table_s = random_table_for(rng, tree_s, n, density=0.3)
+    tree, table = handles(tree_s, table_s)
+    for method in METHODS:
+        for alpha in ([0.0, 0.5, 0.75, 1.0] if method == "generalized" else [1.0]):
+            exp = oracle.condensed(tree_s, table_s, method, alpha)
+            for precision in PRECISIONS:
+                got, _ = uf.uf_compute(tree, table, method, alpha, precision)
+                assert_close(got, exp, method, precision, f"n={n} alpha={alpha}")
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_identical_samples_are_exactly_zero(precision):
+    tree_s = yule_tree(300, seed=31)
+    t = table_iid(40, tree_s.n_tips, 0.05, seed=32)
+    counts = t.dense()
+    counts[5] = counts[17]
+    counts[33] = counts[17] * 3.0  # proportional counts: same proportions
+    table_s = STable.from_dense(counts)
+    tree, table = handles(tree_s, table_s)
+    n = table_s.n_samples
+    # exact copies give 0 on both paths; proportional counts give the same
+    # FP64 proportions (correctly rounded quotients), hence 0 on the FP64 path
+    pairs = [(5, 17)] + ([(17, 33), (5, 33)] if precision == "fp64" else [])
+    for method in METHODS:
+        got, _ = uf.uf_compute(tree, table, method, alpha_for(method), precision)
+        for i, j in pairs:
+            d = got[condensed_index(n, i, j)]
+            assert d == 0.0, (method, i, j, d)
+
+
+@pytest.mark.parametrize("n", [9, 64, 300])
+def test_stripe_ranges(n):
+    tree_s = yule_tree(200, seed=40 + n)
+    table_s = table_iid(n, tree_s.n_tips, 0.1, seed=41 + n)
+    tree, table = handles(tree_s, table_s)
+    S = uf.uf_stripe_count(n)
+    cuts = sorted({0, 1, S // 3, S // 2 + 1, S - 1, S})
+    for method in ["unweighted", "weighted_normalized", "generalized"]:
+        _, _, exp_striped, _ = oracle.striped(tree_s, table_s, method, 0.5, 0, S)
+        for precision in PRECISIONS:
+            parts = []
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                if a == b:
+                    continue
+                got, _ = uf.uf_compute(tree, table, method, 0.5, precision, a, b)
+                assert got.shape == (b - a, n)
+                assert_close(got.ravel(), exp_striped[a:b].ravel(), method, precision, f"range [{a},{b})")
+                parts.append(got)
+            whole = np.vstack(parts)
+            # stripes are independent: the pieces equal a run of everything
+            alln, _ = uf.uf_compute(tree, table, method, 0.5, precision, 0, S - 1)
+            np.testing.assert_array_equal(whole[: S - 1], alln)
+
+
+def test_device_and_fp32_outputs():
+    tree_s, table_s = workload("yule1k_n64")
+    tree, table = handles(tree_s, table_s)
+    n = table_s.n_samples
+    host, _ = uf.uf_compute(tree, table, "weighted_normalized", 1.0, "mixed")
+    dev = torch.empty(n * (n - 1) // 2, dtype=torch.float64, device="cuda")
+    uf.uf_compute(tree, table, "weighted_normalized", 1.0, "mixed", out=dev)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(dev.cpu().numpy(), host)
+    f32, _ = uf.uf_compute(tree, table, "weighted_normalized", 1.0, "mixed", out_fp32=True)
+    assert f32.dtype == np.float32
+    np.testing.assert_array_equal(f32, host.astype(np.float32))
+
+
+def test_batch_matches_single():
+    tree_s = yule_tree(500, seed=50)
+    tables_s = [table_iid(n, tree_s.n_tips, 0.05, seed=51 + n) for n in (7, 64, 130)]
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    tables = [uf.Table(t.indptr, t.indices, t.data, tree) for t in tables_s]
+    for precision in PRECISIONS:
+        outs, reps = uf.uf_compute_batch(tree, tables, "unweighted", 1.0, precision)
+        for t_s, t, o in zip(tables_s, tables, outs):
+            exp = oracle.condensed(tree_s, t_s, "unweighted", 1.0)
+            assert_close(o, exp, "unweighted", precision, "batch")
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_yule50k_n2048_pair_subset(method):
+    tree_s, table_s = workload("yule50k_n2048")
+    tree, table = handles(tree_s, table_s)
+    n = table_s.n_samples
+    i, j = pair_subset(n, 10_000, seed=12345)
+    a = alpha_for(method)
+    exp = oracle.pairs(tree_s, table_s, method, a, i, j)[0]
+    for precision in PRECISIONS:
+        got, _ = uf.uf_compute(tree, table, method, a, precision)
+        assert_close(got[condensed_index(n, i, j)], exp, method, precision, "yule50k_n2048")

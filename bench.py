@@ -1,0 +1,448 @@
+#!/usr/bin/env python3
+"""Benchmark: Striped UniFrac pair x branch updates per second on GB300.
+
+Workload (default): a seeded Yule tree with 50,000 tips (99,999 nodes,
+lengths Exp(mean 0.1)) and 2,048 samples whose features have prevalence
+Beta(0.5, 20) and counts 1 + Poisson(LogNormal(1, 1)); synthetic, generated
+by ``synth``.  One step = the whole hot path (embedding levels, stripe
+accumulate, diagonal, finalize) for each of the four methods (unweighted,
+weighted_unnormalized, weighted_normalized, generalized alpha = 0.5) over
+all stripes.  ``value`` is pair x branch updates per second of the mixed
+path with inputs resident on the GPU; the FP64 path is measured beside it,
+and both report their max error against the FP64 oracle on a seeded
+10,000-pair subset.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs the same-sized problem (independent
+problems, weak scaling, no collective on the data path); rank 0 prints one
+JSON line.  ``--impl reference`` times the FP64 CPU oracle (the only
+reference this method has) on the host cores on a bounded pair sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair*branch updates/s"
+ALL_METHODS = [("unweighted", 1.0), ("weighted_unnormalized", 1.0), ("weighted_normalized", 1.0),
+               ("generalized", 0.5)]
+METHODS = list(ALL_METHODS)
+# CUDA-core FP32 lanes per SM and the SFU rate per SM on GB300 (sm_103): the
+# peaks of the ALU-bound accumulate kernels at the maximum SM clock
+FP32_LANES_PER_SM = 128
+SFU_PER_SM = 16
+SMS = 152
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(kernel_key: str):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or
+    None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        ent = d.get(kernel_key)
+        if not ent:
+            return None
+        src = os.path.join(ROOT, ent["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != ent.get("source_sha256_16"):
+            return None
+        return ent["dram_bytes_per_launch_scaled"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def oracle_sample_rate(tree_s, table_s, target_seconds: float, seed: int = 99):
+    """Oracle throughput on a bounded random pair sample of the workload,
+    running the four methods of a step: (updates/s, cores, pairs, seconds)."""
+    import oracle
+    from synth import pair_subset
+    n = table_s.n_samples
+    branches = tree_s.n_nodes - 1
+    probe = 64
+    i, j = pair_subset(n, probe, seed=seed)
+    t0 = time.perf_counter()
+    for m, a in METHODS:
+        oracle.pairs(tree_s, table_s, m, a, i, j)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    pairs = int(max(probe, min(200_000, probe * target_seconds / dt)))
+    i, j = pair_subset(n, pairs, seed=seed + 1)
+    t0 = time.perf_counter()
+    used = 1
+    for m, a in METHODS:
+        used = oracle.pairs(tree_s, table_s, m, a, i, j)[3]
+    dt = time.perf_counter() - t0
+    return len(METHODS) * i.size * branches / dt, used, int(i.size), dt
+
+
+def run_reference(args, rank, world):
+    from synth import workload
+    tree_s, table_s = workload(args.workload)
+    if rank != 0:
+        return 0
+    rates, used, pairs = [], 1, 0
+    for s in range(args.warmup + args.steps):
+        r, used, pairs, _ = oracle_sample_rate(tree_s, table_s, args.ref_seconds, seed=1000 + s)
+        if s >= args.warmup:
+            rates.append(r)
+    value = statistics.mean(rates)
+    n = table_s.n_samples
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * len(METHODS) * pairs * (tree_s.n_nodes - 1) / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(args, tree_s, table_s, l2="n/a (host)"),
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": used, "kind": "oracle",
+                         "sample": f"{pairs} random pairs of {n} samples x 4 methods per step "
+                                   f"(FP64 per-pair tree walk)"},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args, tree_s, table_s, l2):
+    return {"workload": args.workload, "tips": tree_s.n_tips, "nodes": tree_s.n_nodes,
+            "samples": table_s.n_samples, "nnz": table_s.nnz,
+            "methods": [m for m, _ in METHODS], "alpha": 0.5, "stripes": "all",
+            "l2": l2}
+
+
+def max_errors(tree_s, table_s, outs, precision):
+    """Max error of each method's result against the oracle on the seeded
+    10,000-pair subset (abs for mixed, rel for fp64)."""
+    import oracle
+    from synth import pair_subset
+    n = table_s.n_samples
+    i, j = pair_subset(n, 10_000, seed=12345)
+    idx = n * i - i * (i + 1) // 2 + (j - i - 1)
+    res = {}
+    for (m, a), got in zip(METHODS, outs):
+        exp = oracle.pairs(tree_s, table_s, m, a, i, j)[0]
+        g = got[idx]
+        abs_err = float(np.max(np.abs(g - exp)))
+        rel = np.abs(g - exp) / np.maximum(np.abs(exp), 1e-300)
+        rel[(exp == 0) & (g == 0)] = 0.0
+        res[m] = {"max_abs": abs_err, "max_rel": float(np.max(rel))}
+    return res
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2005_05826_gb300 as uf
+    from paper_2005_05826_gb300 import build as ufbuild
+    from synth import workload
+
+    ufbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    tree_s, table_s = workload(args.workload)
+    n = table_s.n_samples
+    branches = tree_s.n_nodes - 1
+    npairs = n * (n - 1) // 2
+    peaks, peak_src = load_peaks()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # CPU baseline first (before any fork-sensitive GPU state matters)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, used, pairs, dt = oracle_sample_rate(tree_s, table_s, args.cpu_seconds)
+        cpu = {"value": r, "unit": "updates/s", "cores": used, "kind": "oracle",
+               "sample": f"{pairs} random pairs x 4 methods, {dt:.1f} s (FP64 per-pair tree walk)"}
+
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
+    outs = [torch.empty(npairs, dtype=torch.float64, device=dev) for _ in METHODS]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    uf.uf_set_option("kernel_timing", 1)
+
+    def step(precision, reps=None):
+        for (m, a), o in zip(METHODS, outs):
+            _, rep = uf.uf_compute(tree, table, m, a, precision, out=o)
+            if reps is not None:
+                reps.append((m, rep))
+
+    # ---- mixed path: the headline ----
+    for _ in range(args.warmup):
+        step("mixed")
+    torch.cuda.synchronize()
+    times, reps = [], []
+    sampler = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with sampler:
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between steps, outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step("mixed", reps)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_total = sum(times)
+    if dist:
+        t = torch.tensor([t_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    updates_step = len(METHODS) * npairs * branches
+    value = world * updates_step * args.steps / t_total
+    mixed_outs = [o.cpu().numpy() for o in outs]
+    launches = int(sum(r.kernels for _, r in reps))
+
+    # per-kernel roofline of the accumulate launches (timed inside the steps)
+    acc_ms = {}
+    for m, r in reps:
+        d = acc_ms.setdefault(m, [0.0, 0, 0])
+        d[0] += r.t_accumulate_ms
+        d[1] += r.acc_launches
+        d[2] += 1
+    kern = {}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    for m, (ms, nl, ncalls) in acc_ms.items():
+        per_launch_s = ms / 1e3 / max(nl, 1)
+        # algorithmic cell updates of one launch: a call's launches share the
+        # call's pairs x branches (the duplicate half stripe excluded)
+        cells = npairs * branches * ncalls / max(nl, 1)
+        if m == "generalized":
+            ops = cells                  # one SFU reciprocal square root per update
+            peak = SFU_PER_SM * SMS * sm_max * 1e6 / 1e12
+            basis = f"{SFU_PER_SM} SFU ops/clk/SM x {SMS} SMs x {sm_max:.0f} MHz"
+            name = "k_stripe_gen<float,4,8,rsqrt>"
+        else:
+            ops = 2 * cells              # one FP32 min + one FP32 add per update
+            peak = FP32_LANES_PER_SM * SMS * sm_max * 1e6 / 1e12
+            basis = f"{FP32_LANES_PER_SM} FP32 lanes/clk/SM x {SMS} SMs x {sm_max:.0f} MHz"
+            name = "k_stripe_min<float,8,8>"
+        ach = ops / per_launch_s / 1e12
+        kern[m] = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s",
+                   "frac": ach / peak, "ms_per_launch": per_launch_s * 1e3, "launches": nl,
+                   "peak_basis": basis, "share_of_step": ms / 1e3 / t_total}
+    dom = max(kern, key=lambda m: kern[m]["share_of_step"])
+    rl = dict(kern[dom])
+    rl["traffic"] = kernel_traffic(rl["kernel"])
+    rl["method"] = dom
+
+    # ---- e2e through the C ABI with host buffers ----
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        e_times, h2d, d2h = [], 0.0, 0.0
+        for s in range(max(1, min(args.steps, 3)) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tr = uf.Tree(tree_s.parent, tree_s.length)
+            tb = uf.Table(table_s.indptr, table_s.indices, table_s.data, tr)
+            hb = db = 0.0
+            for m, a in METHODS:
+                _, rep = uf.uf_compute(tr, tb, m, a, "mixed")
+                hb += rep.h2d_bytes
+                db += rep.d2h_bytes
+            tb.close()
+            tr.close()
+            torch.cuda.synchronize()
+            if s > 0:  # the first is a warm-up
+                e_times.append(time.perf_counter() - t0)
+                h2d, d2h = hb, db
+        e2e = {"value": updates_step / statistics.mean(e_times), "unit": "updates/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1e3 * statistics.mean(e_times)}
+
+    # ---- FP64 path beside it ----
+    fp64 = None
+    if rank == 0 and not args.no_fp64:
+        step("fp64")
+        torch.cuda.synchronize()
+        f_reps = []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        step("fp64", f_reps)
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        fp64_outs = [o.cpu().numpy() for o in outs]
+        per_method = {m: r.t_accumulate_ms + r.t_diag_ms + r.t_embed_ms + r.t_finalize_ms
+                      for m, r in f_reps}
+        fp64 = {"value": updates_step / t64, "unit": "updates/s", "ms_per_step": t64 * 1e3,
+                "ms_per_method": per_method}
+        # FP64 CUDA-core roofline of the weighted accumulate: 2 FP64 ops per
+        # update against GB300's nominal FP64 rate (1.25 TFLOP/s = 0.625 T
+        # instructions/s counting an FMA as two flops)
+        r_wn = dict(f_reps).get("weighted_normalized")
+        if r_wn is not None:
+            ach64 = 2 * npairs * branches / (r_wn.t_accumulate_ms / 1e3) / 1e12
+            fp64["roofline_weighted"] = {
+                "kernel": "k_stripe_min<double,8,8>", "bound": "alu", "achieved": ach64,
+                "peak": 0.625, "unit": "Tops/s", "frac": ach64 / 0.625,
+                "peak_basis": "nominal FP64 1.25 TFLOP/s (FMA = 2 flops)"}
+        if not args.no_err:
+            fp64["max_err"] = max_errors(tree_s, table_s, fp64_outs, "fp64")
+            fp64["max_rel_err"] = max(v["max_rel"] for v in fp64["max_err"].values())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    mixed_err = {} if args.no_err else max_errors(tree_s, table_s, mixed_outs, "mixed")
+    clocks = sampler.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Yule tree + Beta-prevalence CSR counts)",
+        "config": workload_config(args, tree_s, table_s, l2="flushed between steps (256 MB write)"),
+        "precision": "mixed: FP32 updates, FP64 accumulators and division",
+        "max_abs_err_vs_oracle": max((v["max_abs"] for v in mixed_err.values()), default=None),
+        "max_err": mixed_err,
+        "roofline": rl,
+        "kernels": kern,
+        "peak_source": peak_src,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "fp64_path": fp64,
+        "mixed_vs_fp64_speedup": (value / fp64["value"]) if fp64 else None,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="yule50k_n2048")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
+    ap.add_argument("--no-err", action="store_true", help="skip the max-error check vs the oracle")
+    ap.add_argument("--methods", default="all",
+                    help="comma list of methods per step (default: all four)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.methods != "all":
+        want = args.methods.split(",")
+        METHODS[:] = [ma for ma in ALL_METHODS if ma[0] in want]
+        if not METHODS:
+            ap.error(f"no known method in {args.methods!r}")
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

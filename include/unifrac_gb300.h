@@ -91,7 +91,28 @@ typedef struct {
     int64_t kernels;       /* kernel launches issued by the call */
     int32_t path;          /* 0 = CUDA-core stripes, 1 = tcgen05 split-BF16 GEMM */
     int32_t reserved;
+    double h2d_bytes;      /* host -> device bytes copied by this call (first use of inputs) */
+    double d2h_bytes;      /* device -> host bytes copied by this call (host output) */
+    /* device time per phase in ms, measured with CUDA events on the call's
+     * stream when the "kernel_timing" option is 1 (else 0) */
+    double t_embed_ms;     /* tip counts, internal levels, embedding rows */
+    double t_accumulate_ms;/* stripe accumulate (or tensor GEMM) launches */
+    double t_diag_ms;      /* diagonal accumulate launches */
+    double t_finalize_ms;  /* finalize */
+    int64_t acc_launches;  /* accumulate launches timed in t_accumulate_ms */
 } uf_report;
+
+/*
+ * Process-wide options (not tied to a tree or table):
+ *   "branch_block"   0 = automatic (default); otherwise the number of
+ *                    branches per embedding block (>= 1), e.g. to bound memory
+ *   "kernel_timing"  0 (default) or 1: time each phase with CUDA events and
+ *                    fill the t_*_ms fields of uf_report (adds a stream sync)
+ * uf_set_option returns UF_EINVAL for an unknown name or a bad value;
+ * uf_get_option returns -1 for an unknown name.
+ */
+uf_status uf_set_option(const char *name, int64_t value);
+int64_t uf_get_option(const char *name);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *uf_last_error(void);

@@ -20,7 +20,7 @@ import numpy as np
 
 __all__ = ["UFError", "Tree", "Table", "Report", "METHODS", "PRECISIONS", "library_path", "load",
            "uf_last_error", "uf_stripe_count", "uf_tree_create", "uf_table_create", "uf_compute",
-           "uf_compute_batch", "condensed_size"]
+           "uf_compute_batch", "uf_set_option", "uf_get_option", "condensed_size"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libunifrac_gb300.so")
@@ -37,7 +37,11 @@ class Report(ctypes.Structure):
                 ("hbm_bytes_est", ctypes.c_double), ("stripe_tile", ctypes.c_int64),
                 ("sample_tile", ctypes.c_int64), ("branch_block", ctypes.c_int64),
                 ("n_blocks", ctypes.c_int64), ("kernels", ctypes.c_int64),
-                ("path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("path", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("h2d_bytes", ctypes.c_double), ("d2h_bytes", ctypes.c_double),
+                ("t_embed_ms", ctypes.c_double), ("t_accumulate_ms", ctypes.c_double),
+                ("t_diag_ms", ctypes.c_double), ("t_finalize_ms", ctypes.c_double),
+                ("acc_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
@@ -92,6 +96,10 @@ def load():
         lib.uf_compute_batch.argtypes = [vp, vp, i64, i32, dbl, i32, vp, i32,
                                          ctypes.POINTER(Report), vp]
         lib.uf_compute_batch.restype = i32
+        lib.uf_set_option.argtypes = [ctypes.c_char_p, i64]
+        lib.uf_set_option.restype = i32
+        lib.uf_get_option.argtypes = [ctypes.c_char_p]
+        lib.uf_get_option.restype = i64
         _lib = lib
         return lib
 
@@ -103,6 +111,14 @@ def _check(code: int):
 
 def uf_last_error() -> str:
     return load().uf_last_error().decode(errors="replace")
+
+
+def uf_set_option(name: str, value: int) -> None:
+    _check(load().uf_set_option(name.encode(), int(value)))
+
+
+def uf_get_option(name: str) -> int:
+    return int(load().uf_get_option(name.encode()))
 
 
 def uf_stripe_count(n_samples: int) -> int:

@@ -8,6 +8,7 @@
 //   then: finalize into the caller's output.
 // Stripes are the paper's independent subproblems (Abstract; Sec. 2 Fig. 1).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -30,6 +31,9 @@ using namespace ufg;
 namespace {
 
 thread_local std::string g_err;
+
+std::atomic<int64_t> g_branch_block{0};
+std::atomic<int64_t> g_kernel_timing{0};
 
 uf_status fail(uf_status st, const char *fmt, ...) {
   char buf[512];
@@ -54,8 +58,11 @@ void ck(cudaError_t e, const char *what) {
   }
 }
 
+thread_local double g_h2d = 0.0;  // bytes uploaded by the current call
+
 template <typename T>
 T *dev_upload(const std::vector<T> &h, const char *what) {
+  g_h2d += (double)h.size() * sizeof(T);
   T *d = nullptr;
   size_t bytes = std::max<size_t>(h.size() * sizeof(T), 16);
   ck(cudaMalloc(&d, bytes), what);
@@ -310,6 +317,44 @@ void keep_pool_memory(int device) {
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// Phase timer: CUDA events recorded on the call's stream around each phase.
+struct PhaseTimer {
+  bool on;
+  cudaStream_t st;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  cudaEvent_t open_ev = nullptr;
+  int open_phase = -1;
+  PhaseTimer(bool enabled, cudaStream_t s) : on(enabled), st(s) {}
+  void begin(int phase) {
+    if (!on) return;
+    ck(cudaEventCreate(&open_ev), "cudaEventCreate");
+    ck(cudaEventRecord(open_ev, st), "cudaEventRecord");
+    open_phase = phase;
+  }
+  void end() {
+    if (!on) return;
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e), "cudaEventCreate");
+    ck(cudaEventRecord(e, st), "cudaEventRecord");
+    marks.push_back({open_phase, {open_ev, e}});
+    open_ev = nullptr;
+  }
+  // after the stream is synchronized
+  void collect(double *ms4) {
+    for (auto &m : marks) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, m.second.first, m.second.second) == cudaSuccess) ms4[m.first] += t;
+    }
+  }
+  ~PhaseTimer() {
+    for (auto &m : marks) {
+      cudaEventDestroy(m.second.first);
+      cudaEventDestroy(m.second.second);
+    }
+    if (open_ev) cudaEventDestroy(open_ev);
+  }
+};
+
 struct Job {
   uf_method method;
   double alpha;
@@ -324,6 +369,7 @@ struct Job {
 // One full compute on the current device; throws CudaFail on CUDA errors.
 uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   const auto t_start = std::chrono::steady_clock::now();
+  g_h2d = 0.0;
   int device = 0;
   ck(cudaGetDevice(&device), "cudaGetDevice");
   keep_pool_memory(device);
@@ -353,6 +399,7 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   const double per_row = (double)n * 8.0 + (double)pitch * es + 8.0;
   int64_t rows = (int64_t)(budget / per_row / 1.1);
   rows = std::max<int64_t>(std::min<int64_t>(rows, nb), std::min<int64_t>(nb, 256));
+  if (g_branch_block.load() > 0) rows = std::min<int64_t>(g_branch_block.load(), std::max<int64_t>(nb, 1));
   rows = std::max<int64_t>(rows, 1);
 
   std::unique_lock<std::mutex> lk_tree(tree->mu);
@@ -365,13 +412,18 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   lk_tab.unlock();
 
   cudaStream_t st = J.st;
-  int64_t kernels = 0;
+  int64_t kernels = 0, acc_launches = 0;
+  PhaseTimer timer(g_kernel_timing.load() != 0, st);
   DevBuf counts((size_t)P->n_slots * n * 8, st, "alloc counts");
   DevBuf X((size_t)rows * pitch * es, st, "alloc embeddings");
   DevBuf M((size_t)rows_out * n * 8, st, "alloc stripes");
-  DevBuf M2, Dg;
-  if (acc == ACC_GEN) M2 = DevBuf((size_t)rows_out * n * 8, st, "alloc stripes");
-  else Dg = DevBuf((size_t)n * 8, st, "alloc diagonal");
+  DevBuf M2, Dg, diag_tmp;
+  if (acc == ACC_GEN) {
+    M2 = DevBuf((size_t)rows_out * n * 8, st, "alloc stripes");
+  } else {
+    Dg = DevBuf((size_t)n * 8, st, "alloc diagonal");
+    diag_tmp = DevBuf(diag_scratch_bytes(fp32, (int)rows, n), st, "alloc diagonal scratch");
+  }
   const size_t out_elems = full ? (size_t)n * (n - 1) / 2 : (size_t)rows_out * n;
   const size_t out_bytes = out_elems * (J.out_fp32 ? 4 : 8);
   DevBuf out_tmp;
@@ -387,6 +439,7 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   for (size_t b = 0; b < P->b0.size(); b++) {
     const int64_t b0 = P->b0[b], b1 = P->b1[b];
     const auto &ls = P->launches[b];
+    timer.begin(0);
     ck(launch_tip_counts(pd.lists + ls[0].first, ls[0].second, pd.slot_of_node, td.tip_of_node,
                          xd.col_ptr, xd.col_row, xd.col_val, counts.as<double>(), n, st),
        "tip counts");
@@ -401,6 +454,7 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
                        td.length, xd.total, xd.inv_total_f, X.p, pitch, n, st),
        "embedding rows");
     kernels++;
+    timer.end();
     StripeArgs sa{};
     sa.X = X.p;
     sa.len = td.length + b0;
@@ -415,11 +469,16 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
     sa.M2 = M2.as<double>();
     sa.Dg = Dg.as<double>();
     sa.alpha = J.alpha;
+    timer.begin(1);
     ck(launch_stripe_acc(acc, fp32, sa, st), "stripe accumulate");
+    timer.end();
     kernels++;
+    acc_launches++;
     if (acc == ACC_MIN) {
-      ck(launch_diag(fp32, sa, st), "diagonal accumulate");
-      kernels++;
+      timer.begin(2);
+      ck(launch_diag(fp32, sa, diag_tmp.p, st), "diagonal accumulate");
+      timer.end();
+      kernels += 2;
     }
   }
   FinalArgs fa{};
@@ -433,7 +492,9 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   fa.Dg = Dg.as<double>();
   fa.out = out_dev;
   fa.out_fp32 = J.out_fp32;
+  timer.begin(3);
   ck(launch_finalize(fa, st), "finalize");
+  timer.end();
   kernels++;
   if (!J.out_is_device) ck(cudaMemcpyAsync(J.out, out_dev, out_bytes, cudaMemcpyDeviceToHost, st), "copy out");
   // buffers go back to the stream-ordered pool here
@@ -442,9 +503,12 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   M = DevBuf();
   M2 = DevBuf();
   Dg = DevBuf();
+  diag_tmp = DevBuf();
   out_tmp = DevBuf();
-  if (!J.out_is_device || st == nullptr) ck(cudaStreamSynchronize(st), "synchronize");
+  if (!J.out_is_device || st == nullptr || timer.on) ck(cudaStreamSynchronize(st), "synchronize");
   else ck(cudaGetLastError(), "enqueue");
+  double ms4[4] = {0, 0, 0, 0};
+  timer.collect(ms4);
 
   if (J.rep) {
     uf_report &r = *J.rep;
@@ -465,6 +529,13 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
     r.n_blocks = (int64_t)P->b0.size();
     r.kernels = kernels;
     r.path = 0;
+    r.h2d_bytes = g_h2d;
+    r.d2h_bytes = J.out_is_device ? 0.0 : (double)out_bytes;
+    r.t_embed_ms = ms4[0];
+    r.t_accumulate_ms = ms4[1];
+    r.t_diag_ms = ms4[2];
+    r.t_finalize_ms = ms4[3];
+    r.acc_launches = acc_launches;
     r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   }
   return UF_OK;
@@ -488,6 +559,29 @@ uf_status check_args(const uf_tree *tree, const uf_table *table, uf_method metho
 // ====================================================================== ABI
 
 extern "C" {
+
+uf_status uf_set_option(const char *name, int64_t value) {
+  g_err.clear();
+  if (!name) return fail(UF_EINVAL, "null option name");
+  if (!strcmp(name, "branch_block")) {
+    if (value < 0) return fail(UF_EINVAL, "branch_block must be >= 0");
+    g_branch_block = value;
+    return UF_OK;
+  }
+  if (!strcmp(name, "kernel_timing")) {
+    if (value != 0 && value != 1) return fail(UF_EINVAL, "kernel_timing must be 0 or 1");
+    g_kernel_timing = value;
+    return UF_OK;
+  }
+  return fail(UF_EINVAL, "unknown option '%s'", name);
+}
+
+int64_t uf_get_option(const char *name) {
+  if (!name) return -1;
+  if (!strcmp(name, "branch_block")) return g_branch_block.load();
+  if (!strcmp(name, "kernel_timing")) return g_kernel_timing.load();
+  return -1;
+}
 
 const char *uf_last_error(void) { return g_err.c_str(); }
 

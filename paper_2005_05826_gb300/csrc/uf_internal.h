@@ -63,8 +63,10 @@ struct StripeArgs {
 // stripes and samples per CTA tile of the accumulate kernel
 void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k);
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st);
-// D[k] += sum of the launch's rows at column k (ACC_MIN only)
-cudaError_t launch_diag(bool fp32, const StripeArgs &a, cudaStream_t st);
+// D[k] += sum of the launch's rows at column k (ACC_MIN only), in the same
+// operation order as the stripe kernel; scratch holds diag_scratch_bytes()
+size_t diag_scratch_bytes(bool fp32, int rows, int n);
+cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStream_t st);
 
 // ---- finalize (uf_finalize.cu) ----
 struct FinalArgs {

@@ -20,8 +20,9 @@
 // bytes of padding per 128 bytes so the per-thread 16-byte reads are free of
 // bank conflicts.
 //
-// Precision.  FP64: every update in FP64, one FP64 add into the global
-// accumulator at the end of the launch.  FP32 (the paper's fp32 mode, Sec. 4):
+// Precision.  FP64: every update in FP64 into a register partial over B1 = 64
+// branches, each partial added into the FP64 global accumulator.  FP32 (the
+// paper's fp32 mode, Sec. 4):
 // updates in FP32 into a register partial over B1 = 64 branches, partials
 // summed into a second FP32 register level, and that level added into the
 // FP64 global accumulator every 4096 branches and at the end.  Every cell runs
@@ -196,9 +197,9 @@ __global__ void __launch_bounds__(NT, 1) k_stripe_min(const StripeArgs a) {
 #pragma unroll
         for (int j = 0; j < RK; j++) acc[i][j] += tmin<T>(u[j], v[i + j + 1]);
     }
+    in_sub += RB;
+    in_flush += RB;
     if (F32) {
-      in_sub += RB;
-      in_flush += RB;
       if (in_sub == B1 || it == nst - 1) {
 #pragma unroll
         for (int i = 0; i < RD; i++)
@@ -217,46 +218,58 @@ __global__ void __launch_bounds__(NT, 1) k_stripe_min(const StripeArgs a) {
           for (int j = 0; j < RK; j++) mid[i][j] = 0.f;
         in_flush = 0;
       }
+    } else if (in_sub == B1 || it == nst - 1) {
+      flush_cells<RD, RK>(a.M, acc, a, s0 + RD * ts, k0 + RK * tk);
+#pragma unroll
+      for (int i = 0; i < RD; i++)
+#pragma unroll
+        for (int j = 0; j < RK; j++) acc[i][j] = T(0);
+      in_sub = 0;
     }
   }
   cp_async_wait<0>();
-  if (!F32) flush_cells<RD, RK>(a.M, acc, a, s0 + RD * ts, k0 + RK * tk);
 }
 
 // ---- diagonal: D[k] += sum_e x_e[k], with the same operation sequence as
 //      k_stripe_min applies to a cell whose two columns are equal ----
+// Phase 1: one partial per (B1-row sub-block, sample), summed in row order.
 template <typename T>
-__global__ void k_diag(const StripeArgs a) {
+__global__ void k_diag_partial(const StripeArgs a, T *__restrict__ part) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n) return;
+  const int sb = blockIdx.y;
   const T *X = (const T *)a.X;
-  constexpr bool F32 = sizeof(T) == 4;
+  const int e0 = sb * B1, e1 = min(a.rows, e0 + B1);
   T acc = T(0);
+  for (int e = e0; e < e1; e++) {
+    const T x = X[(int64_t)e * a.pitch + k];
+    acc += tmin<T>(x, x);
+  }
+  part[(int64_t)sb * a.n + k] = acc;
+}
+
+// Phase 2: sub-block partials in order -- FP32: into an FP32 level added to
+// the FP64 diagonal every FLUSH rows; FP64: each partial into the diagonal.
+template <typename T>
+__global__ void k_diag_reduce(const StripeArgs a, const T *__restrict__ part, int n_sb) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n) return;
+  constexpr bool F32 = sizeof(T) == 4;
+  double d = a.Dg[k];
   float mid = 0.f;
-  const int nst = (a.rows + RB - 1) / RB;
-  int in_sub = 0, in_flush = 0;
-  for (int it = 0; it < nst; it++) {
-    for (int r = 0; r < RB; r++) {
-      const int e = it * RB + r;
-      const T x = e < a.rows ? X[(int64_t)e * a.pitch + k] : T(0);
-      acc += tmin<T>(x, x);
-    }
+  for (int sb = 0; sb < n_sb; sb++) {
+    const T p = part[(int64_t)sb * a.n + k];
     if (F32) {
-      in_sub += RB;
-      in_flush += RB;
-      if (in_sub == B1 || it == nst - 1) {
-        mid += (float)acc;
-        acc = T(0);
-        in_sub = 0;
-      }
-      if (in_flush == FLUSH || it == nst - 1) {
-        a.Dg[k] += (double)mid;
+      mid += (float)p;
+      if ((sb + 1) % (FLUSH / B1) == 0 || sb == n_sb - 1) {
+        d += (double)mid;
         mid = 0.f;
-        in_flush = 0;
       }
+    } else {
+      d += (double)p;
     }
   }
-  if (!F32) a.Dg[k] += (double)acc;
+  a.Dg[k] = d;
 }
 
 // ---- generalized: den += l s w, Q += l min(u, v) w, w = s^(alpha - 1) ----
@@ -398,11 +411,23 @@ cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStrea
   return half ? run_gen<double, 4, 8, 0>(a, st) : run_gen<double, 4, 8, 1>(a, st);
 }
 
-cudaError_t launch_diag(bool fp32, const StripeArgs &a, cudaStream_t st) {
+size_t diag_scratch_bytes(bool fp32, int rows, int n) {
+  const int64_t n_sb = (rows + B1 - 1) / B1;
+  return (size_t)n_sb * n * (fp32 ? 4 : 8);
+}
+
+cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStream_t st) {
   if (a.rows <= 0) return cudaSuccess;
-  const int blocks = (a.n + 127) / 128;
-  if (fp32) k_diag<float><<<blocks, 128, 0, st>>>(a);
-  else k_diag<double><<<blocks, 128, 0, st>>>(a);
+  const int n_sb = (a.rows + B1 - 1) / B1;
+  dim3 g1((a.n + 127) / 128, n_sb);
+  const int g2 = (a.n + 127) / 128;
+  if (fp32) {
+    k_diag_partial<float><<<g1, 128, 0, st>>>(a, (float *)scratch);
+    k_diag_reduce<float><<<g2, 128, 0, st>>>(a, (const float *)scratch, n_sb);
+  } else {
+    k_diag_partial<double><<<g1, 128, 0, st>>>(a, (double *)scratch);
+    k_diag_reduce<double><<<g2, 128, 0, st>>>(a, (const double *)scratch, n_sb);
+  }
   return cudaGetLastError();
 }
 

@@ -199,6 +199,37 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
                            void *const *outs, int out_is_device, uf_report *reps,
                            void *cuda_stream);
 
+/*
+ * uf_compute_noalloc -- the full-range computation of uf_compute (condensed
+ * FP64 output) without allocating any device memory.  The paper has no
+ * counterpart; it exists for callers that may not call cudaMalloc: an
+ * application whose own memory manager owns the device heap (a framework's
+ * caching allocator, a service held to a fixed device-memory budget), or code
+ * that must not enter the allocator because its latency or its failure path
+ * is not allowed at that point.
+ *
+ * Working memory is one fixed area of UF_NOALLOC_SCRATCH_BYTES (64 MiB) that
+ * every GPU loading this library reserves until the process exits; tree and
+ * table data are copied into it from the handles on every call.  A problem
+ * whose working set (inputs, count sums, embedding rows, stripe accumulators)
+ * does not fit is rejected with UF_ENOMEM and a message giving both sizes,
+ * before any work is enqueued.
+ * out_device: caller-owned device memory of n(n-1)/2 doubles on the current
+ *   device, layout as in uf_compute.  cuda_stream: cudaStream_t or NULL.  The
+ *   call returns after the results are in out_device.
+ * The first call on a device, with that device current, sets up the area's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture begins on the device.  All calls on a device share the area
+ * and leave their data in it (accumulators are cleared by each call); calls
+ * whose work overlaps on the GPU -- from other threads or other streams --
+ * race on it.
+ * Errors: UF_EINVAL, UF_ETABLE, UF_ENOMEM (too large for the area), UF_ECUDA.
+ */
+#define UF_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+uf_status uf_compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method method,
+                             double alpha, uf_precision precision, double *out_device,
+                             void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,8 @@ import numpy as np
 
 __all__ = ["UFError", "Tree", "Table", "Report", "METHODS", "PRECISIONS", "library_path", "load",
            "uf_last_error", "uf_stripe_count", "uf_tree_create", "uf_table_create", "uf_compute",
-           "uf_compute_batch", "uf_set_option", "uf_get_option", "condensed_size"]
+           "uf_compute_batch", "uf_compute_noalloc", "uf_set_option", "uf_get_option",
+           "condensed_size"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libunifrac_gb300.so")
@@ -96,6 +97,8 @@ def load():
         lib.uf_compute_batch.argtypes = [vp, vp, i64, i32, dbl, i32, vp, i32,
                                          ctypes.POINTER(Report), vp]
         lib.uf_compute_batch.restype = i32
+        lib.uf_compute_noalloc.argtypes = [vp, vp, i32, dbl, i32, vp, vp]
+        lib.uf_compute_noalloc.restype = i32
         lib.uf_set_option.argtypes = [ctypes.c_char_p, i64]
         lib.uf_set_option.restype = i32
         lib.uf_get_option.argtypes = [ctypes.c_char_p]
@@ -282,3 +285,25 @@ def uf_compute_batch(tree: Tree, tables, method: str, alpha: float = 1.0, precis
                                 PRECISIONS[precision], ptrs, is_dev, reps,
                                 ctypes.c_void_p(int(st)) if st else None))
     return [s[3] for s in specs], [reps[i] for i in range(nt)]
+
+
+def uf_compute_noalloc(tree: Tree, table: Table, method: str, alpha: float = 1.0,
+                       precision: str = "fp64", out=None, stream=None):
+    """Full-range condensed distances without any device allocation by the
+    library: for callers that may not allocate device memory (their own
+    memory manager owns the device heap, or the allocator may not be entered
+    at that point).  ``out`` must be a CUDA float64 tensor of n(n-1)/2
+    elements, written in place; the library works in its fixed 64 MiB area and
+    raises UF_ENOMEM for problems that do not fit.  Returns ``out``."""
+    import torch
+    n = table.n_samples
+    need = condensed_size(n)
+    if out is None or not hasattr(out, "data_ptr") or not out.is_cuda:
+        raise ValueError("out must be a CUDA torch tensor (device memory owned by the caller)")
+    if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() < need:
+        raise ValueError(f"out must be a contiguous float64 tensor with >= {need} elements")
+    st = int(stream) if stream is not None else torch.cuda.current_stream(out.device).cuda_stream
+    _check(load().uf_compute_noalloc(tree.handle, table.handle, METHODS[method], float(alpha),
+                                     PRECISIONS[precision], ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(st) if st else None))
+    return out

@@ -760,3 +760,43 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- views
+// Read-only access to the host copies held by a tree / table, for entry
+// points implemented in other translation units.
+namespace ufg {
+
+bool tree_host_view(const uf_tree *t, TreeView *v) {
+  if (!t || !v) return false;
+  v->n_nodes = t->n_nodes;
+  v->n_tips = t->n_tips;
+  v->length = t->length.data();
+  v->tip_of_node = t->tip_of_node.data();
+  v->child_ptr = t->child_ptr.data();
+  v->child_idx = t->child_idx.data();
+  return true;
+}
+
+bool table_host_view(const uf_table *t, TableView *v) {
+  if (!t || !v) return false;
+  v->n = t->n;
+  v->n_features = t->n_features;
+  v->nnz = t->nnz;
+  v->total = t->total.data();
+  v->inv_total_f = t->inv_total_f.data();
+  v->col_ptr = t->col_ptr.data();
+  v->col_row = t->col_row.data();
+  v->col_val = t->col_val.data();
+  return true;
+}
+
+}  // namespace ufg
+
+namespace ufg {
+// Set the calling thread's uf_last_error() text (for entry points in other
+// translation units) and return st.
+uf_status set_last_error(uf_status st, const char *msg) {
+  g_err = msg ? msg : "";
+  return st;
+}
+}  // namespace ufg

@@ -18,6 +18,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/unifrac_gb300.h"
+
 namespace ufg {
 
 // what an embedding row holds
@@ -80,4 +82,30 @@ struct FinalArgs {
 };
 cudaError_t launch_finalize(const FinalArgs &a, cudaStream_t st);
 
+}  // namespace ufg
+
+// ---- host views of tree / table handles (uf_host.cpp) ----
+struct uf_tree;
+struct uf_table;
+namespace ufg {
+struct TreeView {
+  int64_t n_nodes, n_tips;
+  const double *length;
+  const int32_t *tip_of_node, *child_ptr, *child_idx;
+};
+struct TableView {
+  int64_t n, n_features, nnz;
+  const double *total;
+  const float *inv_total_f;
+  const int64_t *col_ptr;
+  const int32_t *col_row;
+  const double *col_val;
+};
+bool tree_host_view(const ::uf_tree *t, TreeView *v);
+bool table_host_view(const ::uf_table *t, TableView *v);
+}  // namespace ufg
+
+namespace ufg {
+// Set the calling thread's uf_last_error() text and return st (uf_host.cpp).
+uf_status set_last_error(uf_status st, const char *msg);
 }  // namespace ufg

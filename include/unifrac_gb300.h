@@ -5,8 +5,8 @@
  * samples of a count table over a rooted phylogenetic tree, on one GPU.
  *
  * Background.  Sfiligoi, McDonald & Knight, "Porting and optimizing UniFrac
- * for GPUs" (arXiv 2005.05826) ship the method as a "C shared library
- * linkable by any programming language" (Abstract) and split the n x n
+ * for GPUs" (arXiv 2005.05826) ship the method as a C shared library that
+ * any language can call (Abstract) and split the n x n
  * distance problem into independent stripes (Abstract, Sec. 1; Fig. 1):
  * stripe s, column k holds the pair (k, (k + s + 1) mod n), and the stripes
  * of a run live in one unified buffer indexed (s - start) * n + k (Sec. 2,

@@ -1,5 +1,5 @@
-// uf_embed.cu -- per-branch embeddings (the paper's "extract and transform"
-// producer, Sec. 3; emb of Figs. 1-3), built level by level on the GPU.
+// uf_embed.cu -- per-branch embeddings (emb of Figs. 1-3; in the paper a CPU
+// producer prepares them buffer by buffer, Sec. 3), built level by level on the GPU.
 //
 // A node's count row is the sum of its children's count rows (postorder:
 // children first); a tip's row is its column of the count table.  The

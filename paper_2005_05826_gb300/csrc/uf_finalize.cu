@@ -1,5 +1,6 @@
-// uf_finalize.cu -- stripe accumulators -> distances (the paper's final copy
-// out of the unified stripe buffer, Sec. 2), with the num / den division in FP64.
+// uf_finalize.cu -- stripe accumulators -> distances: the step that, in the
+// paper, moves results out of the unified stripe buffer after the branch loop
+// (Sec. 2), here with the num / den division in FP64.
 //
 // Per cell (stripe s, sample k, partner j = (k + s + 1) mod n), with
 // M = sum_e min(x_e[k], x_e[j]) and D the same sum at offset 0:

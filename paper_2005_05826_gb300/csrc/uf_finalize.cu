@@ -2,13 +2,17 @@
 // paper, moves results out of the unified stripe buffer after the branch loop
 // (Sec. 2), here with the num / den division in FP64.
 //
-// Per cell (stripe s, sample k, partner j = (k + s + 1) mod n), with
-// M = sum_e min(x_e[k], x_e[j]) and D the same sum at offset 0:
-//   weighted:    sum l |p_k - p_j| = D_k + D_j - 2M,  sum l (p_k + p_j) = D_k + D_j
-//   unweighted:  sum l [xor] = W_k + W_j - 2G,         sum l [or] = W_k + W_j - G
+// Accumulators are int64 fixed point (value * 2^F).  Per cell (stripe s,
+// sample k, partner j = (k + s + 1) mod n), with D the diagonal sums and the
+// cell holding M = sum min(x_k, x_j) (min form) or A = sum |x_k - x_j|
+// (abs form):
+//   weighted:    num = A  or  D_k + D_j - 2M,      den = D_k + D_j
+//   unweighted:  num = A  or  W_k + W_j - 2G,      den = (W_k + W_j + A) / 2  or  W_k + W_j - G
 //                (W = D, G = M on presence embeddings)
 //   generalized: num = den - 2Q
-// A ratio with den == 0 is 0; numerators are clamped at 0 against rounding.
+// num and den are formed exactly in integers before the one FP64 division
+// (the common 2^F cancels); weighted_unnormalized returns num * 2^-F.
+// A ratio with den == 0 is 0.
 #include "uf_internal.h"
 
 namespace ufg {
@@ -24,26 +28,39 @@ __global__ void k_finalize(const FinalArgs a) {
     int64_t j = k + s + 1;
     if (j >= a.n) j -= a.n;
     if (a.full && 2 * (s + 1) == a.n && k >= a.n / 2) continue;  // duplicate half stripe
-    const double m = a.M[c];
+    const long long m = (long long)a.M[c];
+    const bool abs_form = a.mixed_forms && (s & 7) >= 8 - FP32_ABS_ROWS;
     double val;
     switch (a.method) {
     case 0: {  // unweighted
-      const double w = a.Dg[k] + a.Dg[j];
-      const double num = fmax(w - 2.0 * m, 0.0), den = w - m;
-      val = den > 0.0 ? num / den : 0.0;
+      const long long w = (long long)a.Dg[k] + (long long)a.Dg[j];
+      long long num, den2;  // den2 = 2 * den
+      if (abs_form) {
+        num = m;
+        den2 = w + m;
+      } else {
+        num = w - 2 * m;
+        den2 = 2 * (w - m);
+      }
+      if (num < 0) num = 0;
+      val = den2 > 0 ? 2.0 * (double)num / (double)den2 : 0.0;
     } break;
-    case 1:  // weighted unnormalized
-      val = fmax(a.Dg[k] + a.Dg[j] - 2.0 * m, 0.0);
-      break;
+    case 1: {  // weighted unnormalized
+      long long num = abs_form ? m : (long long)a.Dg[k] + (long long)a.Dg[j] - 2 * m;
+      if (num < 0) num = 0;
+      val = (double)num * a.inv_scale;
+    } break;
     case 2: {  // weighted normalized
-      const double den = a.Dg[k] + a.Dg[j];
-      const double num = fmax(den - 2.0 * m, 0.0);
-      val = den > 0.0 ? num / den : 0.0;
+      const long long den = (long long)a.Dg[k] + (long long)a.Dg[j];
+      long long num = abs_form ? m : den - 2 * m;
+      if (num < 0) num = 0;
+      val = den > 0 ? (double)num / (double)den : 0.0;
     } break;
     default: {  // generalized: M = den, M2 = Q
-      const double den = m;
-      const double num = fmax(den - 2.0 * a.M2[c], 0.0);
-      val = den > 0.0 ? num / den : 0.0;
+      const long long den = m;
+      long long num = den - 2 * (long long)a.M2[c];
+      if (num < 0) num = 0;
+      val = den > 0 ? (double)num / (double)den : 0.0;
     } break;
     }
     int64_t idx;

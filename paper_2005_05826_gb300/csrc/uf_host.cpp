@@ -109,6 +109,9 @@ struct uf_tree {
   };
   std::map<int, Dev> dev;
   std::map<int64_t, std::unique_ptr<Plan>> plans;  // by block rows
+  // root distance of every node (root: 0), max over tips, total branch length
+  std::vector<double> dist;
+  double max_tip_dist = 0.0, total_length = 0.0;
   ~uf_tree() {
     int cur = 0;
     cudaGetDevice(&cur);
@@ -137,6 +140,7 @@ struct uf_table {
   std::vector<int32_t> col_row;
   std::vector<double> col_val;
   std::mutex mu;
+  std::map<const uf_tree *, double> presence_bound;  // by tree: max_k sum_{f in k} dist(tip f)
   struct Dev {
     double *total = nullptr, *col_val = nullptr;
     float *inv_total_f = nullptr;
@@ -355,6 +359,49 @@ struct PhaseTimer {
   }
 };
 
+// Upper bound on every value an accumulator of this kind can reach:
+//   l * p embeddings:         D_k = sum_f p_f dist(f) <= max tip distance
+//   l * presence embeddings:  W_k <= min(total length, sum_{f in k} dist(f))
+//   generalized (den, Q):     den <= sum l s^alpha <= 2 (W_k + W_j)
+double accum_bound(uf_tree *tree, uf_table *table, int kind) {
+  if (kind == EMB_SCALED) return tree->max_tip_dist;
+  double pres;
+  {
+    std::lock_guard<std::mutex> g(table->mu);
+    auto it = table->presence_bound.find(tree);
+    if (it == table->presence_bound.end()) {
+      std::vector<double> per(table->n, 0.0);
+      const int32_t *tip_node_of = nullptr;
+      std::vector<int32_t> tip_node(tree->n_tips);
+      for (int64_t v = 0; v < tree->n_nodes; v++)
+        if (tree->tip_of_node[v] >= 0) tip_node[tree->tip_of_node[v]] = (int32_t)v;
+      tip_node_of = tip_node.data();
+      for (int64_t f = 0; f < table->n_features; f++)
+        for (int64_t q = table->col_ptr[f]; q < table->col_ptr[f + 1]; q++)
+          per[table->col_row[q]] += tree->dist[tip_node_of[f]];
+      double mx = 0.0;
+      for (double x : per) mx = std::max(mx, x);
+      it = table->presence_bound.emplace(tree, mx).first;
+    }
+    pres = std::min(tree->total_length, it->second);
+  }
+  return kind == EMB_PRESENCE ? pres : 4.0 * pres;
+}
+
+}  // namespace
+
+namespace ufg {
+// Fixed-point scale 2^F of the accumulators: 2 * bound * 2^F <= 2^61.
+double accum_scale(const uf_tree *tree, const uf_table *table, int kind) {
+  const double B = accum_bound(const_cast<uf_tree *>(tree), const_cast<uf_table *>(table), kind);
+  int F = 100;
+  if (B > 0.0 && std::isfinite(B)) F = std::min(100, std::max(0, 60 - (int)std::ceil(std::log2(B))));
+  return std::ldexp(1.0, F);
+}
+}  // namespace ufg
+
+namespace {
+
 struct Job {
   uf_method method;
   double alpha;
@@ -387,6 +434,7 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   int tile_s = 0, tile_k = 0;
   stripe_tile_shape(acc, fp32, &tile_s, &tile_k);
   const int m_lo = (int)(J.start / tile_s), m_hi = (int)((J.stop - 1) / tile_s);
+  const double scale = accum_scale(tree, table, kind);
   const int64_t pitch = round_up(round_up(n, tile_k) + (int64_t)(m_hi + 1) * tile_s, 32);
 
   // branch-block size: fit counts + embedding rows into a working budget
@@ -417,7 +465,7 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   DevBuf counts((size_t)P->n_slots * n * 8, st, "alloc counts");
   DevBuf X((size_t)rows * pitch * es, st, "alloc embeddings");
   DevBuf M((size_t)rows_out * n * 8, st, "alloc stripes");
-  DevBuf M2, Dg, diag_tmp;
+  DevBuf M2, Dg, diag_tmp, counter(sizeof(int), st, "alloc counter");
   if (acc == ACC_GEN) {
     M2 = DevBuf((size_t)rows_out * n * 8, st, "alloc stripes");
   } else {
@@ -465,10 +513,14 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
     sa.s_hi = (int)(J.stop - 1);
     sa.m_lo = m_lo;
     sa.m_hi = m_hi;
-    sa.M = M.as<double>();
-    sa.M2 = M2.as<double>();
-    sa.Dg = Dg.as<double>();
+    sa.n_ktiles = (int)((n + tile_k - 1) / tile_k);
+    sa.chunk = stripe_chunk_rows();
+    sa.M = M.as<unsigned long long>();
+    sa.M2 = M2.as<unsigned long long>();
+    sa.Dg = Dg.as<unsigned long long>();
     sa.alpha = J.alpha;
+    sa.scale = scale;
+    sa.counter = counter.as<int>();
     timer.begin(1);
     ck(launch_stripe_acc(acc, fp32, sa, st), "stripe accumulate");
     timer.end();
@@ -487,9 +539,11 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   fa.s0 = J.start;
   fa.s1 = J.stop;
   fa.full = full;
-  fa.M = M.as<double>();
-  fa.M2 = M2.as<double>();
-  fa.Dg = Dg.as<double>();
+  fa.mixed_forms = fp32 && acc == ACC_MIN;
+  fa.M = M.as<unsigned long long>();
+  fa.M2 = M2.as<unsigned long long>();
+  fa.Dg = Dg.as<unsigned long long>();
+  fa.inv_scale = 1.0 / scale;
   fa.out = out_dev;
   fa.out_fp32 = J.out_fp32;
   timer.begin(3);
@@ -504,6 +558,7 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   M2 = DevBuf();
   Dg = DevBuf();
   diag_tmp = DevBuf();
+  counter = DevBuf();
   out_tmp = DevBuf();
   if (!J.out_is_device || st == nullptr || timer.on) ck(cudaStreamSynchronize(st), "synchronize");
   else ck(cudaGetLastError(), "enqueue");
@@ -638,6 +693,13 @@ uf_status uf_tree_create(int64_t n_nodes, const int64_t *parent, const double *l
     for (int64_t i = 0; i < n_nodes; i++)
       if (nchild[i] == 0) t->tip_of_node[i] = (int32_t)tips++;
     t->n_tips = tips;
+    t->dist.assign(n_nodes, 0.0);
+    for (int64_t v = n_nodes - 2; v >= 0; v--) {  // parents come later in the order
+      t->dist[v] = t->length[v] + t->dist[parent[v]];
+      t->total_length += t->length[v];
+    }
+    for (int64_t v = 0; v < n_nodes; v++)
+      if (nchild[v] == 0) t->max_tip_dist = std::max(t->max_tip_dist, t->dist[v]);
     *out = t.release();
     return UF_OK;
   } catch (const std::bad_alloc &) {

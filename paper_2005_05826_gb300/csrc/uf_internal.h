@@ -10,10 +10,10 @@
 //                           head so that the partner index k + d needs no
 //                           modulo (the paper's unmodded emb[k + stripe + 1],
 //                           Sec. 2 Fig. 1 and Sec. 3 Figs. 2-3)
-//   M       [s_hi-s_lo+1][n] FP64 stripe accumulator, cell (s - s_lo) * n + k
-//                           for the pair (k, (k + s + 1) mod n)
+//   M       [s_hi-s_lo+1][n] int64 fixed-point stripe accumulator, cell
+//                           (s - s_lo) * n + k for the pair (k, (k + s + 1) mod n)
 //                           (the unified buffer of Sec. 2, Fig. 1)
-//   Dg      [n]             FP64 diagonal accumulator (partner offset 0)
+//   Dg      [n]             int64 fixed-point diagonal accumulator (partner offset 0)
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -49,6 +49,10 @@ cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
                             void *X, int64_t pitch, int n, cudaStream_t st);
 
 // ---- stripe accumulate (uf_stripe.cu) ----
+// In the FP32 min kernel, stripes s with (s % 8) >= 8 - FP32_ABS_ROWS hold
+// A = sum |x_k - x_j| instead of M = sum min(x_k, x_j) (see uf_stripe.cu).
+constexpr int FP32_ABS_ROWS = 3;
+
 struct StripeArgs {
   const void *X;        // [rows][pitch] float or double
   const double *len;    // per-row branch length (generalized only), [rows]
@@ -57,16 +61,22 @@ struct StripeArgs {
   int n;                // samples
   int s_lo, s_hi;       // stored stripes s in [s_lo, s_hi]
   int m_lo, m_hi;       // stripe tiles m in [m_lo, m_hi] (tile m: s in [m*tile_s, +tile_s))
-  double *M;            // [(s_hi - s_lo + 1) * n]: min sums (ACC_MIN) or den (ACC_GEN)
-  double *M2;           // Q (ACC_GEN), else null
-  double *Dg;           // [n] diagonal sums (ACC_MIN, k_diag), else null
+  int n_ktiles;         // sample tiles: ceil(n / tile_k)
+  int chunk;            // rows per work unit (stripe_chunk_rows())
+  unsigned long long *M;   // [(s_hi - s_lo + 1) * n] fixed point: M / A (ACC_MIN) or den (ACC_GEN)
+  unsigned long long *M2;  // Q (ACC_GEN), else null
+  unsigned long long *Dg;  // [n] fixed-point diagonal sums (ACC_MIN, launch_diag), else null
   double alpha;         // generalized exponent
+  double scale;         // 2^F: fixed-point scale of every accumulator
+  int *counter;         // one int of device memory: the work-unit counter (reset per launch)
 };
 // stripes and samples per CTA tile of the accumulate kernel
 void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k);
+// rows per work unit
+int stripe_chunk_rows();
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st);
-// D[k] += sum of the launch's rows at column k (ACC_MIN only), in the same
-// operation order as the stripe kernel; scratch holds diag_scratch_bytes()
+// D[k] += sum of the launch's rows at column k (ACC_MIN only), with the
+// stripe kernel's operation order; scratch holds diag_scratch_bytes()
 size_t diag_scratch_bytes(bool fp32, int rows, int n);
 cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStream_t st);
 
@@ -76,7 +86,9 @@ struct FinalArgs {
   int n;
   int64_t s0, s1;       // stripes [s0, s1)
   int full;             // 1: condensed output, 0: stripe-major
-  const double *M, *M2, *Dg;
+  int mixed_forms;      // 1: the FP32 min kernel's abs-form stripes are present
+  const unsigned long long *M, *M2, *Dg;  // fixed-point accumulators
+  double inv_scale;     // 2^-F
   void *out;
   int out_fp32;
 };
@@ -106,6 +118,8 @@ bool table_host_view(const ::uf_table *t, TableView *v);
 }  // namespace ufg
 
 namespace ufg {
+// Fixed-point scale 2^F for the accumulators of an embedding kind (uf_host.cpp).
+double accum_scale(const ::uf_tree *tree, const ::uf_table *table, int kind);
 // Set the calling thread's uf_last_error() text and return st (uf_host.cpp).
 uf_status set_last_error(uf_status st, const char *msg);
 }  // namespace ufg

@@ -116,6 +116,7 @@ extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
   const int m_hi = (int)((S - 1) / tile_s);
   const int64_t pitch = round_up(round_up(n, tile_k) + (int64_t)(m_hi + 1) * tile_s, 32);
   const int64_t N = tv.n_nodes, nb = N - 1;
+  const double scale = accum_scale(tree, table, kind);
 
   // one branch block holding every branch; slot of node v = v
   std::vector<int32_t> level(N, 0), lists, slot(N);
@@ -159,13 +160,14 @@ extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
     p[10] = c.take<float>(n);                       // inv_total_f
     p[11] = c.take<double>((size_t)std::max<int64_t>(nb, 1) * n);        // counts
     p[12] = c.take<unsigned char>((size_t)std::max(rows, 1) * pitch * es);  // X
-    p[13] = c.take<double>((size_t)S * n);          // M (min sums or den)
-    p[14] = acc == ACC_GEN ? (void *)c.take<double>((size_t)S * n) : nullptr;  // Q
-    p[15] = acc == ACC_MIN ? (void *)c.take<double>(n) : nullptr;               // diagonal
+    p[13] = c.take<unsigned long long>((size_t)S * n);  // stripe accumulator (fixed point)
+    p[14] = acc == ACC_GEN ? (void *)c.take<unsigned long long>((size_t)S * n) : nullptr;  // Q
+    p[15] = acc == ACC_MIN ? (void *)c.take<unsigned long long>(n) : nullptr;               // diagonal
     p[16] = acc == ACC_MIN ? (void *)c.take<unsigned char>(diag_scratch_bytes(fp32, std::max(rows, 1), n))
                            : nullptr;                                        // diagonal partials
+    p[17] = c.take<int>(1);                                                  // work-unit counter
   };
-  void *p[17];
+  void *p[18];
   Carve dry{nullptr};
   layout(dry, p);
   if (dry.used > UF_NOALLOC_SCRATCH_BYTES) {
@@ -239,10 +241,14 @@ extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
     sa.s_hi = (int)(S - 1);
     sa.m_lo = 0;
     sa.m_hi = m_hi;
-    sa.M = (double *)p[13];
-    sa.M2 = (double *)p[14];
-    sa.Dg = (double *)p[15];
+    sa.n_ktiles = (n + tile_k - 1) / tile_k;
+    sa.chunk = stripe_chunk_rows();
+    sa.M = (unsigned long long *)p[13];
+    sa.M2 = (unsigned long long *)p[14];
+    sa.Dg = (unsigned long long *)p[15];
     sa.alpha = alpha;
+    sa.scale = scale;
+    sa.counter = (int *)p[17];
     UF_TRY(launch_stripe_acc(acc, fp32, sa, st));
     if (acc == ACC_MIN) UF_TRY(launch_diag(fp32, sa, p[16], st));
   }
@@ -252,9 +258,11 @@ extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
   fa.s0 = 0;
   fa.s1 = S;
   fa.full = 1;
-  fa.M = (const double *)p[13];
-  fa.M2 = (const double *)p[14];
-  fa.Dg = (const double *)p[15];
+  fa.mixed_forms = fp32 && acc == ACC_MIN;
+  fa.M = (const unsigned long long *)p[13];
+  fa.M2 = (const unsigned long long *)p[14];
+  fa.Dg = (const unsigned long long *)p[15];
+  fa.inv_scale = 1.0 / scale;
   fa.out = out_device;
   fa.out_fp32 = 0;
   UF_TRY(launch_finalize(fa, st));

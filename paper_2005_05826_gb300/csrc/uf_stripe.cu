@@ -2,33 +2,44 @@
 //
 // For every branch e of a launch, stripe s and sample k the paper adds
 // f(emb_e[k], emb_e[(k + s + 1) mod n]) * length_e into the stripe buffer.
-// Here the per-branch term is rewritten so that one accumulator serves three
-// methods (exact algebra, stated per method in the finalize kernel):
+// Here the per-branch term is rewritten (exact algebra; the finalize kernel
+// states it per method):
 //   |u - v| = u + v - 2 min(u, v),  [a xor b] = a + b - 2 ab,  [a or b] = a + b - ab,
-// so with x = l * u (l * presence for unweighted) every weighted / unweighted
-// numerator and denominator follows from
-//   M[s][k] = sum_e min(x_e[k], x_e[k + s + 1])   and   D[k] = sum_e x_e[k],
-// the latter being the same sum at offset 0.  Generalized UniFrac keeps two
-// accumulators, den = sum l s^a and Q = sum l min(u, v) s^(a-1), num = den - 2Q.
+// so with x = l * u (l * presence for unweighted) every weighted and
+// unweighted numerator and denominator follows from the diagonal
+// D[k] = sum_e x_e[k] and, per cell, either
+//   M[s][k] = sum_e min(x_e[k], x_e[k + s + 1])        (min form) or
+//   A[s][k] = sum_e |x_e[k] - x_e[k + s + 1]|          (abs form).
+// One min-form update is one FMNMX (ALU pipe, half rate) plus half an FADD2;
+// one abs-form update is half an FADD2 plus one FADD (FMA pipe).  The FP32
+// kernel gives the last FP32_ABS_ROWS of every 8 stripes the abs form so the
+// two pipes share the load.  Generalized UniFrac keeps two accumulators,
+// den = sum l s^a and Q = sum l min(u, v) s^(a-1), num = den - 2Q.
 //
-// Tiling: a CTA owns a TILE_S x TILE_K (stripe x sample) accumulator tile and
-// streams all branch rows of the launch through it (the paper's input-buffer
-// batching, Sec. 3 Fig. 2, taken to the whole launch): per stage, RB rows of
-// the u window [k0, k0 + TILE_K) and the partner window [k0 + s0, k0 + s0 +
-// TILE_K + TILE_S) are copied into shared memory with 16-byte cp.async, then
-// each thread updates an RD x RK register micro-tile.  Shared rows carry 16
-// bytes of padding per 128 bytes so the per-thread 16-byte reads are free of
-// bank conflicts.
+// Work is split into units (row chunk of up to a.chunk branches, tile of
+// TILE_S stripes x TILE_K samples).  Persistent CTAs take units from a global
+// counter, chunk-major, so the CTAs in flight read the same rows and those
+// rows stay in L2.  Per unit, 8-row stages of the u window [k0, k0 + TILE_K)
+// and the partner window [k0 + s0, k0 + s0 + TILE_K + TILE_S) go to shared
+// memory by 16-byte cp.async (three stages in flight), and each thread
+// updates an RD x RK register micro-tile.  Shared rows are XOR-swizzled in
+// 16-byte units so the per-thread 16-byte reads are free of bank conflicts.
 //
-// Precision.  FP64: every update in FP64 into a register partial over B1 = 64
-// branches, each partial added into the FP64 global accumulator.  FP32 (the
-// paper's fp32 mode, Sec. 4):
-// updates in FP32 into a register partial over B1 = 64 branches, partials
-// summed into a second FP32 register level, and that level added into the
-// FP64 global accumulator every 4096 branches and at the end.  Every cell runs
-// the same sequence of operations, so two identical samples produce bitwise
-// equal M and D and a distance of exactly 0.
+// Precision.  FP32 (the paper's fp32 mode, Sec. 4): register partials over
+// B1 = 64 branches are summed into an FP32 level kept in shared memory; at
+// the end of the unit that level is scaled by 2^F and rounded once to an
+// int64 fixed-point value, which is added atomically into the int64
+// accumulator.  FP64: register partials over 64 branches in FP64, each
+// rounded to fixed point and summed in shared memory, then added atomically.
+// Integer addition is exact and order-free, so chunks may land in any order
+// and the result is still deterministic; every cell (and the diagonal) runs
+// the same FP32 / FP64 operation sequence within a unit, so two identical
+// samples give bitwise equal accumulators and a distance of exactly 0.
+// F is chosen by the host from an upper bound B on any accumulated value so
+// that 2 B 2^F <= 2^61.
+#include <algorithm>
 #include <cfloat>
+#include <type_traits>
 
 #include "uf_internal.h"
 
@@ -39,29 +50,35 @@ namespace {
 constexpr int NT = 256;       // threads per CTA: 16 (stripe) x 16 (sample)
 constexpr int RB = 8;         // branch rows per pipeline stage
 constexpr int NSTAGE = 3;     // cp.async pipeline depth
-constexpr int B1 = 64;        // FP32 inner partial length (branches)
-constexpr int FLUSH = 4096;   // FP32 outer level length (branches) before the FP64 add
+constexpr int B1 = 64;        // inner partial length (branches)
 
-// 16 bytes of padding after every 128 bytes of a shared row
+// Shared rows are stored in 16-byte units with unit j placed at
+// j ^ ((j >> 3) & MASK), MASK = (bytes a thread reads per 8-sample run) / 16 - 1.
+// Eight threads that read the same unit offset q of consecutive 8-sample runs
+// (any starting run) then hit eight distinct 16-byte bank groups.
 template <typename T>
-__host__ __device__ constexpr int skew(int i) {
-  return i + (int)(16 / sizeof(T)) * (i / (int)(128 / sizeof(T)));
+__host__ __device__ constexpr int swz(int elem) {
+  constexpr int VEC = 16 / sizeof(T);
+  constexpr int MASK = 8 * sizeof(T) / 16 - 1;
+  const int j = elem / VEC;
+  return (j ^ ((j >> 3) & MASK)) * VEC + elem % VEC;
 }
 
-template <typename T, int RD, int RK>
+template <typename T, int RD, int RK, int NACC>
 struct Geo {
   static constexpr int TS = 16 * RD;             // stripes per tile
   static constexpr int TK = 16 * RK;             // samples per tile
   static constexpr int VEC = 16 / sizeof(T);     // elements per 16-byte copy
   static constexpr int UW = TK;                  // u window
   static constexpr int VW = TK + TS;             // partner window (needs TK + TS - 1, shifted by one)
-  static constexpr int US = skew<T>(UW);
-  static constexpr int VS = skew<T>(VW);
-  static constexpr int ROW = US + VS;
-  static constexpr int STAGE = RB * ROW + RB;    // + the rows' lengths
+  static constexpr int ROW = UW + VW;            // both parts are multiples of 128 bytes
+  static constexpr int STAGE = RB * ROW + RB;    // + the rows' lengths (keeps 16-byte alignment)
   static constexpr int UCH = UW / VEC, VCH = VW / VEC, CH = UCH + VCH;
   static constexpr int NV = (RD + RK + VEC - 1) / VEC;  // partner vectors per thread
-  static constexpr size_t SMEM = (size_t)NSTAGE * STAGE * sizeof(T);
+  // second level per thread and cell: FP32 for the FP32 path, int64 for FP64
+  using Mid = typename std::conditional<sizeof(T) == 4, float, long long>::type;
+  static constexpr size_t SMEM =
+      (size_t)NSTAGE * STAGE * sizeof(T) + (size_t)NACC * RD * RK * NT * sizeof(Mid);
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -79,7 +96,7 @@ __device__ __forceinline__ float tmin<float>(float a, float b) { return fminf(a,
 template <>
 __device__ __forceinline__ double tmin<double>(double a, double b) { return fmin(a, b); }
 
-// s^(alpha - 1) for s > 0 (the caller discards s == 0 terms)
+// s^(alpha - 1) for s > 0 (s == 0 terms are zeroed by the caller)
 template <typename T, int MODE>
 __device__ __forceinline__ T gen_pow(T s, T am1);
 template <>
@@ -91,10 +108,38 @@ __device__ __forceinline__ double gen_pow<double, 0>(double s, double) { return 
 template <>
 __device__ __forceinline__ double gen_pow<double, 1>(double s, double am1) { return pow(fmax(s, 1e-300), am1); }
 
+// fixed point: round x * 2^F to the nearest integer
+__device__ __forceinline__ long long to_fixed(float x, double scale) { return __float2ll_rn(x * (float)scale); }
+__device__ __forceinline__ long long to_fixed(double x, double scale) { return __double2ll_rn(x * scale); }
+
+struct Unit {
+  int r0, r1, k0, s0;
+};
+
+__device__ __forceinline__ bool next_unit(const StripeArgs &a, int tile_s, int tile_k, int *s_unit,
+                                          Unit *u) {
+  __syncthreads();  // everyone is done with the previous unit's shared data
+  if (threadIdx.x == 0) *s_unit = atomicAdd(a.counter, 1);
+  __syncthreads();
+  const int id = *s_unit;
+  const int n_stiles = a.m_hi - a.m_lo + 1;
+  const int n_tiles = a.n_ktiles * n_stiles;
+  const int n_chunks = (a.rows + a.chunk - 1) / a.chunk;
+  if (id >= n_chunks * n_tiles) return false;
+  const int c = id / n_tiles, t = id - c * n_tiles;
+  const int kt = t % a.n_ktiles, st = t / a.n_ktiles;
+  u->r0 = c * a.chunk;
+  u->r1 = min(a.rows, u->r0 + a.chunk);
+  u->k0 = kt * tile_k;
+  u->s0 = (a.m_lo + st) * tile_s;
+  return true;
+}
+
 // Stage loader: RB branch rows [e0, e0 + RB) of the u and partner windows.
-template <typename T, int RD, int RK, bool LEN>
-__device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0, int k0, int s0) {
-  using G = Geo<T, RD, RK>;
+template <typename T, int RD, int RK, int NACC, bool LEN>
+__device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0, int e_end, int k0,
+                                           int s0) {
+  using G = Geo<T, RD, RK, NACC>;
   const T *X = (const T *)a.X;
   for (int c = threadIdx.x; c < RB * G::CH; c += NT) {
     const int r = c / G::CH, q = c - r * G::CH;
@@ -103,14 +148,14 @@ __device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0
     T *dst;
     int64_t src;
     if (q < G::UCH) {
-      dst = row + skew<T>(q * G::VEC);
+      dst = row + swz<T>(q * G::VEC);
       src = (int64_t)k0 + q * G::VEC;
     } else {
       const int qv = q - G::UCH;
-      dst = row + G::US + skew<T>(qv * G::VEC);
+      dst = row + G::UW + swz<T>(qv * G::VEC);
       src = (int64_t)k0 + s0 + qv * G::VEC;
     }
-    if (e < a.rows) {
+    if (e < e_end) {
       cp_async16(dst, X + (int64_t)e * a.pitch + src);
     } else {
 #pragma unroll
@@ -119,127 +164,234 @@ __device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0
   }
   if (LEN && threadIdx.x < RB) {
     const int e = e0 + threadIdx.x;
-    stage[RB * G::ROW + threadIdx.x] = e < a.rows ? (T)a.len[e] : T(0);
+    stage[RB * G::ROW + threadIdx.x] = e < e_end ? (T)a.len[e] : T(0);
   }
 }
 
-// Add a thread's FP32/FP64 cell values into the global FP64 stripe accumulator.
-template <int RD, int RK, typename V>
-__device__ __forceinline__ void flush_cells(double *M, const V (&val)[RD][RK], const StripeArgs &a,
-                                            int s_base, int k_base) {
+// Add one thread's second-level cells (fixed point) into the accumulator.
+template <typename T, int RD, int RK, typename Mid>
+__device__ __forceinline__ void commit_cells(unsigned long long *M, const Mid *mid, const StripeArgs &a,
+                                             int s_base, int k_base) {
 #pragma unroll
   for (int i = 0; i < RD; i++) {
     const int s = s_base + i;
     if (s < a.s_lo || s > a.s_hi) continue;
-    double *row = M + (int64_t)(s - a.s_lo) * a.n;
+    unsigned long long *row = M + (int64_t)(s - a.s_lo) * a.n;
 #pragma unroll
     for (int j = 0; j < RK; j++) {
       const int k = k_base + j;
-      if (k < a.n) row[k] += (double)val[i][j];
+      if (k < a.n) {
+        const Mid m = mid[(i * RK + j) * NT + threadIdx.x];
+        long long q;
+        if constexpr (sizeof(Mid) == 4) q = to_fixed((float)m, a.scale);
+        else q = (long long)m;
+        atomicAdd(row + k, (unsigned long long)q);
+      }
     }
   }
 }
 
-// ---- weighted / unweighted: M[s][k] += sum_e min(x_e[k], x_e[k + s + 1]) ----
-template <typename T, int RD, int RK>
-__global__ void __launch_bounds__(NT, 1) k_stripe_min(const StripeArgs a) {
-  using G = Geo<T, RD, RK>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *smem = reinterpret_cast<T *>(smem_raw);
-  const int k0 = blockIdx.x * G::TK;
-  const int s0 = (a.m_lo + blockIdx.y) * G::TS;
-  const int tk = threadIdx.x & 15, ts = threadIdx.x >> 4;
-  const int uoff = skew<T>(RK * tk);
-  const int w0 = RK * tk + RD * ts;  // partner window of this thread, used from w0 + 1
-
+// ---- weighted / unweighted ----
+// rows i < NMIN of the micro-tile: M += min(x_k, x_j); rows i >= NMIN: A += |x_k - x_j|
+template <typename T, int RD, int RK, int NMIN, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
+  using G = Geo<T, RD, RK, 1>;
+  using Mid = typename G::Mid;
   constexpr bool F32 = sizeof(T) == 4;
-  T acc[RD][RK];
-  float mid[RD][RK];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *stg = reinterpret_cast<T *>(smem_raw);
+  Mid *mid = reinterpret_cast<Mid *>(smem_raw + (size_t)NSTAGE * G::STAGE * sizeof(T));
+  __shared__ int s_unit;
+  const int tk = threadIdx.x & 15, ts = threadIdx.x >> 4;
+  const int w0 = RK * tk + RD * ts;  // partner window of this thread, used from w0 + 1
+  Unit U;
+  while (next_unit(a, G::TS, G::TK, &s_unit, &U)) {
 #pragma unroll
-  for (int i = 0; i < RD; i++)
+    for (int c = 0; c < RD * RK; c++) mid[c * NT + threadIdx.x] = Mid(0);
+    const int nst = (U.r1 - U.r0 + RB - 1) / RB;
 #pragma unroll
-    for (int j = 0; j < RK; j++) {
-      acc[i][j] = T(0);
-      mid[i][j] = 0.f;
-    }
-
-  const int nst = (a.rows + RB - 1) / RB;
-#pragma unroll
-  for (int p = 0; p < NSTAGE - 1; p++) {
-    if (p < nst) load_stage<T, RD, RK, false>(smem + p * G::STAGE, a, p * RB, k0, s0);
-    cp_async_commit();
-  }
-  int in_sub = 0, in_flush = 0;
-  for (int it = 0; it < nst; it++) {
-    cp_async_wait<NSTAGE - 2>();
-    __syncthreads();
-    {
-      const int nx = it + NSTAGE - 1;
-      if (nx < nst) load_stage<T, RD, RK, false>(smem + (nx % NSTAGE) * G::STAGE, a, nx * RB, k0, s0);
+    for (int p = 0; p < NSTAGE - 1; p++) {
+      if (p < nst) load_stage<T, RD, RK, 1, false>(stg + p * G::STAGE, a, U.r0 + p * RB, U.r1, U.k0, U.s0);
       cp_async_commit();
     }
-    const T *stage = smem + (it % NSTAGE) * G::STAGE;
+    T acc[RD][RK];
+#pragma unroll
+    for (int i = 0; i < RD; i++)
+#pragma unroll
+      for (int j = 0; j < RK; j++) acc[i][j] = T(0);
+    int in_sub = 0;
+    for (int it = 0; it < nst; it++) {
+      cp_async_wait<NSTAGE - 2>();
+      __syncthreads();
+      {
+        const int nx = it + NSTAGE - 1;
+        if (nx < nst)
+          load_stage<T, RD, RK, 1, false>(stg + (nx % NSTAGE) * G::STAGE, a, U.r0 + nx * RB, U.r1, U.k0, U.s0);
+        cp_async_commit();
+      }
+      const T *stage = stg + (it % NSTAGE) * G::STAGE;
 #pragma unroll 2
-    for (int r = 0; r < RB; r++) {
-      const T *urow = stage + r * G::ROW;
-      const T *vrow = urow + G::US;
-      T u[RK], v[G::NV * G::VEC];
+      for (int r = 0; r < RB; r++) {
+        const T *urow = stage + r * G::ROW;
+        const T *vrow = urow + G::UW;
+        T u[RK], v[G::NV * G::VEC];
 #pragma unroll
-      for (int q = 0; q < RK / G::VEC; q++)
-        *reinterpret_cast<uint4 *>(&u[q * G::VEC]) =
-            *reinterpret_cast<const uint4 *>(urow + uoff + q * G::VEC);
+        for (int q = 0; q < RK / G::VEC; q++)
+          *reinterpret_cast<uint4 *>(&u[q * G::VEC]) =
+              *reinterpret_cast<const uint4 *>(urow + swz<T>(RK * tk + q * G::VEC));
 #pragma unroll
-      for (int q = 0; q < G::NV; q++)
-        *reinterpret_cast<uint4 *>(&v[q * G::VEC]) =
-            *reinterpret_cast<const uint4 *>(vrow + skew<T>(w0 + q * G::VEC));
+        for (int q = 0; q < G::NV; q++)
+          *reinterpret_cast<uint4 *>(&v[q * G::VEC]) =
+              *reinterpret_cast<const uint4 *>(vrow + swz<T>(w0 + q * G::VEC));
+        if constexpr (F32) {
 #pragma unroll
-      for (int i = 0; i < RD; i++)
+          for (int i = 0; i < RD; i++)
 #pragma unroll
-        for (int j = 0; j < RK; j++) acc[i][j] += tmin<T>(u[j], v[i + j + 1]);
-    }
-    in_sub += RB;
-    in_flush += RB;
-    if (F32) {
+            for (int j = 0; j < RK; j += 2) {
+              if (i < NMIN) {  // two mins, one paired add
+                float2 a2 = make_float2(acc[i][j], acc[i][j + 1]);
+                const float2 m2 = make_float2(fminf(u[j], v[i + j + 1]), fminf(u[j + 1], v[i + j + 2]));
+                a2 = __fadd2_rn(a2, m2);
+                acc[i][j] = a2.x;
+                acc[i][j + 1] = a2.y;
+              } else {  // one paired difference, two adds of absolute values
+                const float2 d2 = __fadd2_rn(make_float2(u[j], u[j + 1]),
+                                             make_float2(-v[i + j + 1], -v[i + j + 2]));
+                acc[i][j] += fabsf(d2.x);
+                acc[i][j + 1] += fabsf(d2.y);
+              }
+            }
+        } else {
+#pragma unroll
+          for (int i = 0; i < RD; i++)
+#pragma unroll
+            for (int j = 0; j < RK; j++) acc[i][j] += tmin<T>(u[j], v[i + j + 1]);
+        }
+      }
+      in_sub += RB;
       if (in_sub == B1 || it == nst - 1) {
 #pragma unroll
         for (int i = 0; i < RD; i++)
 #pragma unroll
           for (int j = 0; j < RK; j++) {
-            mid[i][j] += (float)acc[i][j];
+            Mid &m = mid[(i * RK + j) * NT + threadIdx.x];
+            if constexpr (F32) m += acc[i][j];
+            else m += to_fixed(acc[i][j], a.scale);
             acc[i][j] = T(0);
           }
         in_sub = 0;
       }
-      if (in_flush == FLUSH || it == nst - 1) {
-        flush_cells<RD, RK>(a.M, mid, a, s0 + RD * ts, k0 + RK * tk);
+    }
+    cp_async_wait<0>();
+    commit_cells<T, RD, RK>(a.M, mid, a, U.s0 + RD * ts, U.k0 + RK * tk);
+  }
+}
+
+// ---- generalized: den += l s w, Q += l min(u, v) w, w = s^(alpha - 1) ----
+template <typename T, int RD, int RK, int MODE, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
+  using G = Geo<T, RD, RK, 2>;
+  using Mid = typename G::Mid;
+  constexpr bool F32 = sizeof(T) == 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *stg = reinterpret_cast<T *>(smem_raw);
+  Mid *midd = reinterpret_cast<Mid *>(smem_raw + (size_t)NSTAGE * G::STAGE * sizeof(T));
+  Mid *midq = midd + RD * RK * NT;
+  __shared__ int s_unit;
+  const int tk = threadIdx.x & 15, ts = threadIdx.x >> 4;
+  const int w0 = RK * tk + RD * ts;
+  const T am1 = (T)(a.alpha - 1.0);
+  Unit U;
+  while (next_unit(a, G::TS, G::TK, &s_unit, &U)) {
+#pragma unroll
+    for (int c = 0; c < RD * RK; c++) midd[c * NT + threadIdx.x] = midq[c * NT + threadIdx.x] = Mid(0);
+    const int nst = (U.r1 - U.r0 + RB - 1) / RB;
+#pragma unroll
+    for (int p = 0; p < NSTAGE - 1; p++) {
+      if (p < nst) load_stage<T, RD, RK, 2, true>(stg + p * G::STAGE, a, U.r0 + p * RB, U.r1, U.k0, U.s0);
+      cp_async_commit();
+    }
+    T accd[RD][RK], accq[RD][RK];
+#pragma unroll
+    for (int i = 0; i < RD; i++)
+#pragma unroll
+      for (int j = 0; j < RK; j++) accd[i][j] = accq[i][j] = T(0);
+    int in_sub = 0;
+    for (int it = 0; it < nst; it++) {
+      cp_async_wait<NSTAGE - 2>();
+      __syncthreads();
+      {
+        const int nx = it + NSTAGE - 1;
+        if (nx < nst)
+          load_stage<T, RD, RK, 2, true>(stg + (nx % NSTAGE) * G::STAGE, a, U.r0 + nx * RB, U.r1, U.k0, U.s0);
+        cp_async_commit();
+      }
+      const T *stage = stg + (it % NSTAGE) * G::STAGE;
+#pragma unroll 1
+      for (int r = 0; r < RB; r++) {
+        const T *urow = stage + r * G::ROW;
+        const T *vrow = urow + G::UW;
+        const T l = stage[RB * G::ROW + r];
+        T u[RK], v[G::NV * G::VEC];
+#pragma unroll
+        for (int q = 0; q < RK / G::VEC; q++)
+          *reinterpret_cast<uint4 *>(&u[q * G::VEC]) =
+              *reinterpret_cast<const uint4 *>(urow + swz<T>(RK * tk + q * G::VEC));
+#pragma unroll
+        for (int q = 0; q < G::NV; q++)
+          *reinterpret_cast<uint4 *>(&v[q * G::VEC]) =
+              *reinterpret_cast<const uint4 *>(vrow + swz<T>(w0 + q * G::VEC));
 #pragma unroll
         for (int i = 0; i < RD; i++)
 #pragma unroll
-          for (int j = 0; j < RK; j++) mid[i][j] = 0.f;
-        in_flush = 0;
+          for (int j = 0; j < RK; j++) {
+            const T uu = u[j], vv = v[i + j + 1];
+            const T s = uu + vv;
+            T w = l * gen_pow<T, MODE>(s, am1);
+            if (MODE == 1) w = s > T(0) ? w : T(0);
+            accd[i][j] = fma(s, w, accd[i][j]);
+            accq[i][j] = fma(tmin<T>(uu, vv), w, accq[i][j]);
+          }
       }
-    } else if (in_sub == B1 || it == nst - 1) {
-      flush_cells<RD, RK>(a.M, acc, a, s0 + RD * ts, k0 + RK * tk);
+      in_sub += RB;
+      if (in_sub == B1 || it == nst - 1) {
 #pragma unroll
-      for (int i = 0; i < RD; i++)
+        for (int i = 0; i < RD; i++)
 #pragma unroll
-        for (int j = 0; j < RK; j++) acc[i][j] = T(0);
-      in_sub = 0;
+          for (int j = 0; j < RK; j++) {
+            const int c = (i * RK + j) * NT + threadIdx.x;
+            if constexpr (F32) {
+              midd[c] += accd[i][j];
+              midq[c] += accq[i][j];
+            } else {
+              midd[c] += to_fixed(accd[i][j], a.scale);
+              midq[c] += to_fixed(accq[i][j], a.scale);
+            }
+            accd[i][j] = accq[i][j] = T(0);
+          }
+        in_sub = 0;
+      }
     }
+    cp_async_wait<0>();
+    commit_cells<T, RD, RK>(a.M, midd, a, U.s0 + RD * ts, U.k0 + RK * tk);
+    commit_cells<T, RD, RK>(a.M2, midq, a, U.s0 + RD * ts, U.k0 + RK * tk);
   }
-  cp_async_wait<0>();
 }
 
-// ---- diagonal: D[k] += sum_e x_e[k], with the same operation sequence as
-//      k_stripe_min applies to a cell whose two columns are equal ----
-// Phase 1: one partial per (B1-row sub-block, sample), summed in row order.
+// ---- diagonal: D[k] += sum_e x_e[k], with the operation sequence a stripe
+//      cell in min form runs when its two columns are equal ----
+// Phase 1: one partial per (B1-row sub-block, sample), summed in row order;
+// sub-blocks restart at every chunk boundary, as in the stripe kernels.
 template <typename T>
 __global__ void k_diag_partial(const StripeArgs a, T *__restrict__ part) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n) return;
   const int sb = blockIdx.y;
   const T *X = (const T *)a.X;
-  const int e0 = sb * B1, e1 = min(a.rows, e0 + B1);
+  const int per_chunk = (a.chunk + B1 - 1) / B1;
+  const int c = sb / per_chunk;
+  const int e0 = c * a.chunk + (sb - c * per_chunk) * B1;
+  const int e1 = min(min(a.rows, (c + 1) * a.chunk), e0 + B1);
   T acc = T(0);
   for (int e = e0; e < e1; e++) {
     const T x = X[(int64_t)e * a.pitch + k];
@@ -248,149 +400,71 @@ __global__ void k_diag_partial(const StripeArgs a, T *__restrict__ part) {
   part[(int64_t)sb * a.n + k] = acc;
 }
 
-// Phase 2: sub-block partials in order -- FP32: into an FP32 level added to
-// the FP64 diagonal every FLUSH rows; FP64: each partial into the diagonal.
+// Phase 2: FP32 -- a chunk's sub-block partials summed in order in FP32, then
+// rounded to fixed point; FP64 -- each partial rounded to fixed point.
 template <typename T>
 __global__ void k_diag_reduce(const StripeArgs a, const T *__restrict__ part, int n_sb) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n) return;
-  constexpr bool F32 = sizeof(T) == 4;
-  double d = a.Dg[k];
+  const int per_chunk = (a.chunk + B1 - 1) / B1;
+  long long d = 0;
   float mid = 0.f;
   for (int sb = 0; sb < n_sb; sb++) {
     const T p = part[(int64_t)sb * a.n + k];
-    if (F32) {
-      mid += (float)p;
-      if ((sb + 1) % (FLUSH / B1) == 0 || sb == n_sb - 1) {
-        d += (double)mid;
+    if constexpr (sizeof(T) == 4) {
+      mid += p;
+      if ((sb + 1) % per_chunk == 0 || sb == n_sb - 1) {
+        d += to_fixed(mid, a.scale);
         mid = 0.f;
       }
     } else {
-      d += (double)p;
+      d += to_fixed(p, a.scale);
     }
   }
-  a.Dg[k] = d;
-}
-
-// ---- generalized: den += l s w, Q += l min(u, v) w, w = s^(alpha - 1) ----
-template <typename T, int RD, int RK, int MODE>
-__global__ void __launch_bounds__(NT, 1) k_stripe_gen(const StripeArgs a) {
-  using G = Geo<T, RD, RK>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *smem = reinterpret_cast<T *>(smem_raw);
-  const int k0 = blockIdx.x * G::TK;
-  const int s0 = (a.m_lo + blockIdx.y) * G::TS;
-  const int tk = threadIdx.x & 15, ts = threadIdx.x >> 4;
-  const int uoff = skew<T>(RK * tk);
-  const int w0 = RK * tk + RD * ts;
-  const T am1 = (T)(a.alpha - 1.0);
-
-  constexpr bool F32 = sizeof(T) == 4;
-  T accd[RD][RK], accq[RD][RK];
-  float midd[RD][RK], midq[RD][RK];
-#pragma unroll
-  for (int i = 0; i < RD; i++)
-#pragma unroll
-    for (int j = 0; j < RK; j++) {
-      accd[i][j] = accq[i][j] = T(0);
-      midd[i][j] = midq[i][j] = 0.f;
-    }
-  const int nst = (a.rows + RB - 1) / RB;
-#pragma unroll
-  for (int p = 0; p < NSTAGE - 1; p++) {
-    if (p < nst) load_stage<T, RD, RK, true>(smem + p * G::STAGE, a, p * RB, k0, s0);
-    cp_async_commit();
-  }
-  int in_sub = 0, in_flush = 0;
-  for (int it = 0; it < nst; it++) {
-    cp_async_wait<NSTAGE - 2>();
-    __syncthreads();
-    {
-      const int nx = it + NSTAGE - 1;
-      if (nx < nst) load_stage<T, RD, RK, true>(smem + (nx % NSTAGE) * G::STAGE, a, nx * RB, k0, s0);
-      cp_async_commit();
-    }
-    const T *stage = smem + (it % NSTAGE) * G::STAGE;
-#pragma unroll 1
-    for (int r = 0; r < RB; r++) {
-      const T *urow = stage + r * G::ROW;
-      const T *vrow = urow + G::US;
-      const T l = stage[RB * G::ROW + r];
-      T u[RK], v[G::NV * G::VEC];
-#pragma unroll
-      for (int q = 0; q < RK / G::VEC; q++)
-        *reinterpret_cast<uint4 *>(&u[q * G::VEC]) =
-            *reinterpret_cast<const uint4 *>(urow + uoff + q * G::VEC);
-#pragma unroll
-      for (int q = 0; q < G::NV; q++)
-        *reinterpret_cast<uint4 *>(&v[q * G::VEC]) =
-            *reinterpret_cast<const uint4 *>(vrow + skew<T>(w0 + q * G::VEC));
-#pragma unroll
-      for (int i = 0; i < RD; i++)
-#pragma unroll
-        for (int j = 0; j < RK; j++) {
-          const T uu = u[j], vv = v[i + j + 1];
-          const T s = uu + vv;
-          T w = l * gen_pow<T, MODE>(s, am1);
-          if (MODE == 1) w = s > T(0) ? w : T(0);
-          accd[i][j] = fma(s, w, accd[i][j]);
-          accq[i][j] = fma(tmin<T>(uu, vv), w, accq[i][j]);
-        }
-    }
-    if (F32) {
-      in_sub += RB;
-      in_flush += RB;
-      if (in_sub == B1 || it == nst - 1) {
-#pragma unroll
-        for (int i = 0; i < RD; i++)
-#pragma unroll
-          for (int j = 0; j < RK; j++) {
-            midd[i][j] += (float)accd[i][j];
-            midq[i][j] += (float)accq[i][j];
-            accd[i][j] = accq[i][j] = T(0);
-          }
-        in_sub = 0;
-      }
-      if (in_flush == FLUSH || it == nst - 1) {
-        flush_cells<RD, RK>(a.M, midd, a, s0 + RD * ts, k0 + RK * tk);
-        flush_cells<RD, RK>(a.M2, midq, a, s0 + RD * ts, k0 + RK * tk);
-#pragma unroll
-        for (int i = 0; i < RD; i++)
-#pragma unroll
-          for (int j = 0; j < RK; j++) midd[i][j] = midq[i][j] = 0.f;
-        in_flush = 0;
-      }
-    }
-  }
-  cp_async_wait<0>();
-  if (!F32) {
-    flush_cells<RD, RK>(a.M, accd, a, s0 + RD * ts, k0 + RK * tk);
-    flush_cells<RD, RK>(a.M2, accq, a, s0 + RD * ts, k0 + RK * tk);
-  }
+  a.Dg[k] += (unsigned long long)d;
 }
 
 template <typename K>
-cudaError_t set_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t prepare(K kernel, size_t smem, int *grid, int units) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  *grid = std::max(1, std::min(units, std::max(per_sm, 1) * sms));
+  return cudaSuccess;
 }
 
-template <typename T, int RD, int RK>
+int units_of(const StripeArgs &a) {
+  const int n_chunks = (a.rows + a.chunk - 1) / a.chunk;
+  return n_chunks * a.n_ktiles * (a.m_hi - a.m_lo + 1);
+}
+
+template <typename T, int RD, int RK, int NMIN, int MINB>
 cudaError_t run_min(const StripeArgs &a, cudaStream_t st) {
-  using G = Geo<T, RD, RK>;
-  cudaError_t e = set_smem(k_stripe_min<T, RD, RK>, G::SMEM);
+  using G = Geo<T, RD, RK, 1>;
+  int grid = 0;
+  cudaError_t e = prepare(k_stripe_min<T, RD, RK, NMIN, MINB>, G::SMEM, &grid, units_of(a));
   if (e != cudaSuccess) return e;
-  dim3 grid((a.n + G::TK - 1) / G::TK, a.m_hi - a.m_lo + 1);
-  k_stripe_min<T, RD, RK><<<grid, NT, G::SMEM, st>>>(a);
+  e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_stripe_min<T, RD, RK, NMIN, MINB><<<grid, NT, G::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T, int RD, int RK, int MODE>
+template <typename T, int RD, int RK, int MODE, int MINB>
 cudaError_t run_gen(const StripeArgs &a, cudaStream_t st) {
-  using G = Geo<T, RD, RK>;
-  cudaError_t e = set_smem(k_stripe_gen<T, RD, RK, MODE>, G::SMEM);
+  using G = Geo<T, RD, RK, 2>;
+  int grid = 0;
+  cudaError_t e = prepare(k_stripe_gen<T, RD, RK, MODE, MINB>, G::SMEM, &grid, units_of(a));
   if (e != cudaSuccess) return e;
-  dim3 grid((a.n + G::TK - 1) / G::TK, a.m_hi - a.m_lo + 1);
-  k_stripe_gen<T, RD, RK, MODE><<<grid, NT, G::SMEM, st>>>(a);
+  e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_stripe_gen<T, RD, RK, MODE, MINB><<<grid, NT, G::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -403,22 +477,29 @@ void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k) {
   *tile_k = 16 * 8;
 }
 
+int stripe_chunk_rows() { return 2048; }
+
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st) {
   if (a.rows <= 0 || a.m_hi < a.m_lo) return cudaSuccess;
-  if (acc == ACC_MIN) return fp32 ? run_min<float, 8, 8>(a, st) : run_min<double, 8, 8>(a, st);
+  if (acc == ACC_MIN)
+    return fp32 ? run_min<float, 8, 8, 8 - FP32_ABS_ROWS, 2>(a, st) : run_min<double, 8, 8, 8, 1>(a, st);
   const bool half = a.alpha == 0.5;
-  if (fp32) return half ? run_gen<float, 4, 8, 0>(a, st) : run_gen<float, 4, 8, 1>(a, st);
-  return half ? run_gen<double, 4, 8, 0>(a, st) : run_gen<double, 4, 8, 1>(a, st);
+  if (fp32) return half ? run_gen<float, 4, 8, 0, 2>(a, st) : run_gen<float, 4, 8, 1, 2>(a, st);
+  return half ? run_gen<double, 4, 8, 0, 1>(a, st) : run_gen<double, 4, 8, 1, 1>(a, st);
 }
 
 size_t diag_scratch_bytes(bool fp32, int rows, int n) {
-  const int64_t n_sb = (rows + B1 - 1) / B1;
-  return (size_t)n_sb * n * (fp32 ? 4 : 8);
+  const int chunk = stripe_chunk_rows();
+  const int64_t n_chunks = (rows + chunk - 1) / chunk;
+  const int64_t n_sb = n_chunks * ((chunk + B1 - 1) / B1);
+  return (size_t)std::max<int64_t>(n_sb, 1) * n * (fp32 ? 4 : 8);
 }
 
 cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStream_t st) {
   if (a.rows <= 0) return cudaSuccess;
-  const int n_sb = (a.rows + B1 - 1) / B1;
+  const int per_chunk = (a.chunk + B1 - 1) / B1;
+  const int n_chunks = (a.rows + a.chunk - 1) / a.chunk;
+  const int n_sb = (n_chunks - 1) * per_chunk + ((a.rows - (n_chunks - 1) * a.chunk) + B1 - 1) / B1;
   dim3 g1((a.n + 127) / 128, n_sb);
   const int g2 = (a.n + 127) / 128;
   if (fp32) {

@@ -297,17 +297,31 @@ def run_ours(args, rank, world, local_rank):
     # per-kernel roofline of the accumulate launches (timed inside the steps)
     acc_ms = {}
     for m, r in reps:
-        d = acc_ms.setdefault(m, [0.0, 0, 0])
+        d = acc_ms.setdefault(m, [0.0, 0, 0, 0.0, 0])
         d[0] += r.t_accumulate_ms
         d[1] += r.acc_launches
         d[2] += 1
+        d[3] += r.exec_flops
+        d[4] = r.path
     kern = {}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    for m, (ms, nl, ncalls) in acc_ms.items():
+    for m, (ms, nl, ncalls, xflops, path) in acc_ms.items():
         per_launch_s = ms / 1e3 / max(nl, 1)
         # algorithmic cell updates of one launch: a call's launches share the
         # call's pairs x branches (the duplicate half stripe excluded)
         cells = npairs * branches * ncalls / max(nl, 1)
+        if path == 1:
+            # tensor cores: executed BF16 flops (three split GEMMs, whole
+            # 128 x 256 tiles) against the measured dense BF16 peak
+            ach = xflops / max(nl, 1) / per_launch_s / 1e12
+            peak = float(peaks.get("bf16_tflops", 1900.0))
+            kern[m] = {"kernel": "k_gram<tcgen05 kind::f16, 128x256>", "bound": "tensor",
+                       "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                       "ms_per_launch": per_launch_s * 1e3, "launches": nl,
+                       "peak_basis": f"measured bf16 dense ({peak_src})",
+                       "algorithmic_tflops": 2 * cells / per_launch_s / 1e12,
+                       "share_of_step": ms / 1e3 / t_total}
+            continue
         if m == "generalized":
             ops = cells                  # one SFU reciprocal square root per update
             peak = SFU_PER_SM * SMS * sm_max * 1e6 / 1e12
@@ -396,7 +410,8 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded Yule tree + Beta-prevalence CSR counts)",
         "config": workload_config(args, tree_s, table_s, l2="flushed between steps (256 MB write)"),
-        "precision": "mixed: FP32 updates, FP64 accumulators and division",
+        "precision": "mixed: FP32 updates (unweighted: exact 0/1 x split-BF16 lengths on tcgen05, "
+                     "FP32 accumulation), int64 fixed-point accumulators, FP64 division",
         "max_abs_err_vs_oracle": max((v["max_abs"] for v in mixed_err.values()), default=None),
         "max_err": mixed_err,
         "roofline": rl,

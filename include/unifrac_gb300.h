@@ -108,6 +108,8 @@ typedef struct {
  *                    branches per embedding block (>= 1), e.g. to bound memory
  *   "kernel_timing"  0 (default) or 1: time each phase with CUDA events and
  *                    fill the t_*_ms fields of uf_report (adds a stream sync)
+ *   "tensor_path"    1 (default): UF_UNWEIGHTED with UF_MIXED runs on the
+ *                    tcgen05 tensor cores; 0: on the CUDA-core stripe kernels
  * uf_set_option returns UF_EINVAL for an unknown name or a bad value;
  * uf_get_option returns -1 for an unknown name.
  */

@@ -34,6 +34,7 @@ thread_local std::string g_err;
 
 std::atomic<int64_t> g_branch_block{0};
 std::atomic<int64_t> g_kernel_timing{0};
+std::atomic<int64_t> g_tensor_path{1};
 
 uf_status fail(uf_status st, const char *fmt, ...) {
   char buf[512];
@@ -413,8 +414,160 @@ struct Job {
   cudaStream_t st;
 };
 
+// Unweighted, mixed precision: per branch block, tip counts -> internal levels
+// -> presence / split-length planes -> tcgen05 gram accumulation; then the
+// gram finalize.  Throws CudaFail on CUDA errors.
+uf_status run_gram(uf_tree *tree, uf_table *table, const Job &J) {
+  const auto t_start = std::chrono::steady_clock::now();
+  g_h2d = 0.0;
+  int device = 0;
+  ck(cudaGetDevice(&device), "cudaGetDevice");
+  keep_pool_memory(device);
+  const int n = (int)table->n;
+  const int64_t S = n / 2;
+  const bool full = J.start == 0 && J.stop == S;
+  const double scale = accum_scale(tree, table, EMB_PRESENCE);
+  const int64_t nb = tree->n_nodes - 1;
+  const int64_t rows_out = J.stop - J.start;
+  int n_pad = 0;
+  int64_t K_probe = 0;
+  gram_geometry(n, 1, &n_pad, &K_probe);
+
+  size_t free_b = 0, total_b = 0;
+  ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+  const double gt_bytes = (double)n_pad * n_pad * 8.0;
+  double budget = std::min(0.5 * (double)free_b - gt_bytes, 24e9);
+  const double per_row = (double)n * 8.0 + 4.0 * n_pad * 2.0 + 8.0;
+  int64_t rows = (int64_t)(budget / per_row / 1.1);
+  rows = std::max<int64_t>(std::min<int64_t>(rows, nb), std::min<int64_t>(nb, 256));
+  if (g_branch_block.load() > 0) rows = std::min<int64_t>(g_branch_block.load(), std::max<int64_t>(nb, 1));
+  rows = std::max<int64_t>(rows, 1);
+  int64_t K_pad = 0;
+  gram_geometry(n, (int)rows, &n_pad, &K_pad);
+
+  std::unique_lock<std::mutex> lk_tree(tree->mu);
+  uf_tree::Dev &td = tree_dev(tree, device);
+  Plan *P = get_plan(tree, rows);
+  Plan::Dev &pd = plan_dev(P, device);
+  lk_tree.unlock();
+  std::unique_lock<std::mutex> lk_tab(table->mu);
+  uf_table::Dev &xd = table_dev(table, device);
+  lk_tab.unlock();
+
+  cudaStream_t st = J.st;
+  int64_t kernels = 0, acc_launches = 0;
+  PhaseTimer timer(g_kernel_timing.load() != 0, st);
+  const std::vector<int32_t> tiles = gram_tiles(n_pad);
+  const int n_tiles = (int)tiles.size() / 2;
+  DevBuf counts((size_t)P->n_slots * n * 8, st, "alloc counts");
+  DevBuf Pl((size_t)4 * n_pad * K_pad * 2, st, "alloc presence planes");
+  DevBuf Gt((size_t)n_pad * n_pad * 8, st, "alloc gram");
+  DevBuf d_tiles(tiles.size() * 4, st, "alloc tile list");
+  DevBuf err(sizeof(int), st, "alloc error flag");
+  ck(cudaMemcpyAsync(d_tiles.p, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, st), "copy tiles");
+  ck(cudaMemsetAsync(Gt.p, 0, (size_t)n_pad * n_pad * 8, st), "memset");
+  ck(cudaMemsetAsync(err.p, 0, sizeof(int), st), "memset");
+  const size_t out_elems = full ? (size_t)n * (n - 1) / 2 : (size_t)rows_out * n;
+  const size_t out_bytes = out_elems * (J.out_fp32 ? 4 : 8);
+  DevBuf out_tmp;
+  void *out_dev = J.out;
+  if (!J.out_is_device) {
+    out_tmp = DevBuf(out_bytes, st, "alloc output");
+    out_dev = out_tmp.p;
+  }
+  double exec_flops = 0.0;
+  for (size_t b = 0; b < P->b0.size(); b++) {
+    const int64_t b0 = P->b0[b], b1 = P->b1[b];
+    const auto &ls = P->launches[b];
+    timer.begin(0);
+    ck(launch_tip_counts(pd.lists + ls[0].first, ls[0].second, pd.slot_of_node, td.tip_of_node,
+                         xd.col_ptr, xd.col_row, xd.col_val, counts.as<double>(), n, st),
+       "tip counts");
+    kernels += ls[0].second > 0;
+    for (size_t l = 1; l < ls.size(); l++) {
+      ck(launch_node_counts(pd.lists + ls[l].first, ls[l].second, td.child_ptr, td.child_idx,
+                            pd.slot_of_node, counts.as<double>(), n, st),
+         "node counts");
+      kernels += ls[l].second > 0;
+    }
+    ck(launch_gram_prep(b0, (int)(b1 - b0), pd.slot_of_node, counts.as<double>(), td.length, n, n_pad,
+                        K_pad, Pl.p, st),
+       "presence planes");
+    kernels++;
+    timer.end();
+    GramArgs ga{};
+    ga.n = n;
+    ga.n_pad = n_pad;
+    ga.k_len = (int)round_up(b1 - b0, 64);
+    ga.kc = 4096;
+    ga.n_tiles = n_tiles;
+    ga.tile_bi = d_tiles.as<int32_t>();
+    ga.tile_bj = d_tiles.as<int32_t>() + n_tiles;
+    ga.Gt = Gt.as<unsigned long long>();
+    ga.scale = scale;
+    ga.err = err.as<int>();
+    timer.begin(1);
+    ck(launch_gram(ga, Pl.p, K_pad, st), "tensor-core gram");
+    timer.end();
+    kernels++;
+    acc_launches++;
+    exec_flops += 2.0 * 3 * 128.0 * 256.0 * ga.k_len * n_tiles;
+  }
+  GramFinalArgs fa{};
+  fa.n = n;
+  fa.n_pad = n_pad;
+  fa.s0 = J.start;
+  fa.s1 = J.stop;
+  fa.full = full;
+  fa.Gt = Gt.as<unsigned long long>();
+  fa.out = out_dev;
+  fa.out_fp32 = J.out_fp32;
+  timer.begin(3);
+  ck(launch_finalize_gram(fa, st), "finalize");
+  timer.end();
+  kernels++;
+  int h_err = 0;
+  ck(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
+  if (!J.out_is_device) ck(cudaMemcpyAsync(J.out, out_dev, out_bytes, cudaMemcpyDeviceToHost, st), "copy out");
+  counts = DevBuf();
+  Pl = DevBuf();
+  Gt = DevBuf();
+  d_tiles = DevBuf();
+  out_tmp = DevBuf();
+  ck(cudaStreamSynchronize(st), "synchronize");  // the error flag is read here
+  err = DevBuf();
+  if (h_err) return fail(UF_ETIMEOUT, "tensor-core kernel: a bounded wait gave up");
+  double ms4[4] = {0, 0, 0, 0};
+  timer.collect(ms4);
+  if (J.rep) {
+    uf_report &r = *J.rep;
+    memset(&r, 0, sizeof r);
+    const double pairs = full ? (double)n * (n - 1) / 2.0
+                              : (double)rows_out * n - ((2 * J.stop == n) ? n / 2.0 : 0.0);
+    r.updates = pairs * (double)nb;
+    r.alg_flops = 2.0 * pairs * nb;
+    r.exec_flops = exec_flops;
+    r.hbm_bytes_est = (double)nb * ((double)n * 8 * 3 + 4.0 * n_pad * 2) + out_bytes;
+    r.stripe_tile = 256;
+    r.sample_tile = 128;
+    r.branch_block = rows;
+    r.n_blocks = (int64_t)P->b0.size();
+    r.kernels = kernels;
+    r.path = 1;
+    r.h2d_bytes = g_h2d;
+    r.d2h_bytes = J.out_is_device ? 0.0 : (double)out_bytes;
+    r.t_embed_ms = ms4[0];
+    r.t_accumulate_ms = ms4[1];
+    r.t_finalize_ms = ms4[3];
+    r.acc_launches = acc_launches;
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  return UF_OK;
+}
+
 // One full compute on the current device; throws CudaFail on CUDA errors.
 uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
+  if (J.method == UF_UNWEIGHTED && J.fp32 && g_tensor_path.load()) return run_gram(tree, table, J);
   const auto t_start = std::chrono::steady_clock::now();
   g_h2d = 0.0;
   int device = 0;
@@ -628,6 +781,11 @@ uf_status uf_set_option(const char *name, int64_t value) {
     g_kernel_timing = value;
     return UF_OK;
   }
+  if (!strcmp(name, "tensor_path")) {
+    if (value != 0 && value != 1) return fail(UF_EINVAL, "tensor_path must be 0 or 1");
+    g_tensor_path = value;
+    return UF_OK;
+  }
   return fail(UF_EINVAL, "unknown option '%s'", name);
 }
 
@@ -635,6 +793,7 @@ int64_t uf_get_option(const char *name) {
   if (!name) return -1;
   if (!strcmp(name, "branch_block")) return g_branch_block.load();
   if (!strcmp(name, "kernel_timing")) return g_kernel_timing.load();
+  if (!strcmp(name, "tensor_path")) return g_tensor_path.load();
   return -1;
 }
 

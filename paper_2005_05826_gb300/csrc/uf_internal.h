@@ -16,6 +16,8 @@
 //   Dg      [n]             int64 fixed-point diagonal accumulator (partner offset 0)
 #pragma once
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/unifrac_gb300.h"
@@ -93,6 +95,35 @@ struct FinalArgs {
   int out_fp32;
 };
 cudaError_t launch_finalize(const FinalArgs &a, cudaStream_t st);
+
+// ---- unweighted on tensor cores (uf_gram.cu) ----
+struct GramArgs {
+  int n, n_pad;         // samples, padded to the 256-sample tile
+  int k_len;            // branches of this block, rounded up to 64
+  int kc;               // branches per work unit (multiple of 64)
+  int n_tiles;          // upper-triangle tiles (gram_tiles)
+  int n_units;          // set by launch_gram
+  const int32_t *tile_bi, *tile_bj;
+  unsigned long long *Gt;  // [n_pad][n_pad] fixed point; cell (i, j), i <= j, at j * n_pad + i
+  double scale;         // 2^F
+  int *err;             // set to 1 when a bounded wait gave up
+};
+struct GramFinalArgs {
+  int n, n_pad;
+  int64_t s0, s1;
+  int full;
+  const unsigned long long *Gt;
+  void *out;
+  int out_fp32;
+};
+// padded sizes of the presence planes for n samples and a block of `rows` branches
+void gram_geometry(int n, int rows, int *n_pad, int64_t *K_pad);
+// tile list: first half row-block indices, second half column-block indices
+std::vector<int32_t> gram_tiles(int n_pad);
+cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, const double *counts,
+                             const double *length, int n, int n_pad, int64_t K_pad, void *Pl, cudaStream_t st);
+cudaError_t launch_gram(const GramArgs &a, void *Pl, int64_t K_pad, cudaStream_t st);
+cudaError_t launch_finalize_gram(const GramFinalArgs &a, cudaStream_t st);
 
 }  // namespace ufg
 

@@ -148,3 +148,41 @@ def test_yule50k_n2048_pair_subset(method):
     for precision in PRECISIONS:
         got, _ = uf.uf_compute(tree, table, method, a, precision)
         assert_close(got[condensed_index(n, i, j)], exp, method, precision, "yule50k_n2048")
+
+
+@pytest.mark.parametrize("tensor", [0, 1])
+def test_multi_block_plans_and_both_unweighted_paths(tensor):
+    # small branch blocks exercise count-slot reuse across blocks
+    tree_s = yule_tree(400, seed=60)
+    table_s = table_iid(150, tree_s.n_tips, 0.05, seed=61)
+    tree, table = handles(tree_s, table_s)
+    uf.uf_set_option("tensor_path", tensor)
+    try:
+        for block in (0, 97, 300):
+            uf.uf_set_option("branch_block", block)
+            for method in METHODS:
+                a = alpha_for(method)
+                exp = oracle.condensed(tree_s, table_s, method, a)
+                for precision in PRECISIONS:
+                    got, rep = uf.uf_compute(tree, table, method, a, precision)
+                    assert_close(got, exp, method, precision, f"block={block} tensor={tensor}")
+                    if block:
+                        assert rep.n_blocks == -(-(tree_s.n_nodes - 1) // block)
+                    if method == "unweighted" and precision == "mixed":
+                        assert rep.path == tensor
+    finally:
+        uf.uf_set_option("branch_block", 0)
+        uf.uf_set_option("tensor_path", 1)
+
+
+def test_tensor_path_large_n_pair_subset():
+    # several 128 x 256 tiles, several K chunks, ragged n
+    tree_s = yule_tree(9000, seed=62)
+    table_s = table_iid(1000, tree_s.n_tips, 0.02, seed=63)
+    tree, table = handles(tree_s, table_s)
+    n = table_s.n_samples
+    i, j = pair_subset(n, 4000, seed=12345)
+    exp = oracle.pairs(tree_s, table_s, "unweighted", 1.0, i, j)[0]
+    got, rep = uf.uf_compute(tree, table, "unweighted", 1.0, "mixed")
+    assert rep.path == 1
+    assert_close(got[condensed_index(n, i, j)], exp, "unweighted", "mixed", "tensor path")

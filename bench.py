@@ -367,7 +367,28 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- FP64 path beside it ----
     fp64 = None
-    if rank == 0 and not args.no_fp64:
+    if rank == 0 and not args.no_fp64 and args.fp64_stripes > 0:
+        # FP64 path on the stripe slice [0, fp64_stripes) only (large workloads)
+        S = uf.uf_stripe_count(n)
+        k = min(args.fp64_stripes, S)
+        sl = torch.empty(k * n, dtype=torch.float64, device=dev)
+        f_reps = []
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for m, a in METHODS:
+            _, rep = uf.uf_compute(tree, table, m, a, "fp64", 0, k, out=sl)
+            f_reps.append((m, rep))
+        e1.record(stream)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        upd = sum(r.updates for _, r in f_reps)
+        fp64 = {"value": upd / t64, "unit": "updates/s", "ms_for_slice": t64 * 1e3,
+                "slice": f"stripes [0, {k}) of {S}, all methods of the step (from a slice)",
+                "ms_per_method": {m: r.t_accumulate_ms + r.t_diag_ms + r.t_embed_ms + r.t_finalize_ms
+                                  for m, r in f_reps}}
+    elif rank == 0 and not args.no_fp64:
         step("fp64")
         torch.cuda.synchronize()
         f_reps = []
@@ -440,6 +461,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
+    ap.add_argument("--fp64-stripes", type=int, default=0,
+                    help="run the FP64 comparison on stripes [0, K) only (large workloads)")
     ap.add_argument("--no-err", action="store_true", help="skip the max-error check vs the oracle")
     ap.add_argument("--methods", default="all",
                     help="comma list of methods per step (default: all four)")

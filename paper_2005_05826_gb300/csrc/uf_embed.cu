@@ -10,16 +10,17 @@
 
 namespace ufg {
 
-// One CTA per tip: zero the tip's count slot, then scatter its CSC column.
+// One CTA per tip: zero the table's part of the tip's count slot, then
+// scatter its CSC column (counts points at the table's first column).
 __global__ void k_tip_counts(const int32_t *__restrict__ tip_nodes,
                              const int32_t *__restrict__ slot_of_node,
                              const int32_t *__restrict__ tip_of_node,
                              const int64_t *__restrict__ col_ptr,
                              const int32_t *__restrict__ col_row,
                              const double *__restrict__ col_val, double *__restrict__ counts,
-                             int n) {
+                             int64_t ld, int n) {
   const int v = tip_nodes[blockIdx.x];
-  double *row = counts + (int64_t)slot_of_node[v] * n;
+  double *row = counts + (int64_t)slot_of_node[v] * ld;
   for (int k = threadIdx.x; k < n; k += blockDim.x) row[k] = 0.0;
   __syncthreads();
   const int f = tip_of_node[v];
@@ -28,19 +29,20 @@ __global__ void k_tip_counts(const int32_t *__restrict__ tip_nodes,
 }
 
 // count[v][k] = sum of the children's count[c][k], children in index order
-// (the order the postorder walk adds them in).  grid.x = nodes, grid.y = sample chunks.
+// (the order the postorder walk adds them in), over all ld columns.
+// grid.x = nodes, grid.y = sample chunks.
 __global__ void k_node_counts(const int32_t *__restrict__ nodes,
                               const int32_t *__restrict__ child_ptr,
                               const int32_t *__restrict__ child_idx,
                               const int32_t *__restrict__ slot_of_node,
-                              double *__restrict__ counts, int n) {
+                              double *__restrict__ counts, int64_t ld) {
   const int v = nodes[blockIdx.x];
-  const int k = blockIdx.y * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  const int64_t k = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (k >= ld) return;
   double s = 0.0;
   for (int c = child_ptr[v]; c < child_ptr[v + 1]; c++)
-    s += counts[(int64_t)slot_of_node[child_idx[c]] * n + k];
-  counts[(int64_t)slot_of_node[v] * n + k] = s;
+    s += counts[(int64_t)slot_of_node[child_idx[c]] * ld + k];
+  counts[(int64_t)slot_of_node[v] * ld + k] = s;
 }
 
 template <typename T, int KIND>
@@ -71,19 +73,34 @@ __device__ __forceinline__ float emb_value<float, EMB_PROP>(double c, double, do
   return (float)c * it;
 }
 
-// One CTA per branch row r (node b0 + r): X[r][j] = f(count[j mod n]), j < pitch.
+// Table whose row segment holds column j (segments are contiguous, in order).
+__device__ __forceinline__ int segment_of(const TabDesc *tabs, int n_tabs, int64_t j) {
+  int lo = 0, hi = n_tabs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tabs[mid].x_col <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One CTA per branch row r (node b0 + r): in table t's segment,
+// X[r][x_col + j] = f(count[off + (j mod n)]) for j < the segment's width.
 template <typename T, int KIND>
 __global__ void k_emb_rows(int64_t b0, const int32_t *__restrict__ slot_of_node,
-                           const double *__restrict__ counts, const double *__restrict__ length,
-                           const double *__restrict__ total, const float *__restrict__ inv_total_f,
-                           T *__restrict__ X, int64_t pitch, int n) {
+                           const double *__restrict__ counts, int64_t ld,
+                           const double *__restrict__ length, const double *__restrict__ total,
+                           const float *__restrict__ inv_total_f, T *__restrict__ X, int64_t pitch,
+                           const TabDesc *__restrict__ tabs, int n_tabs) {
   const int64_t v = b0 + blockIdx.x;
-  const double *c = counts + (int64_t)slot_of_node[v] * n;
+  const double *c = counts + (int64_t)slot_of_node[v] * ld;
   const double l = length[v];
   T *x = X + (int64_t)blockIdx.x * pitch;
   for (int64_t j = threadIdx.x; j < pitch; j += blockDim.x) {
-    int64_t k = j;
-    while (k >= n) k -= n;
+    const TabDesc &tb = tabs[n_tabs == 1 ? 0 : segment_of(tabs, n_tabs, j)];
+    int64_t k = j - tb.x_col;
+    while (k >= tb.n) k -= tb.n;
+    k += tb.off;
     x[j] = emb_value<T, KIND>(c[k], l, total[k], inv_total_f[k]);
   }
 }
@@ -91,30 +108,30 @@ __global__ void k_emb_rows(int64_t b0, const int32_t *__restrict__ slot_of_node,
 cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_t *slot_of_node,
                               const int32_t *tip_of_node, const int64_t *col_ptr,
                               const int32_t *col_row, const double *col_val, double *counts,
-                              int n, cudaStream_t st) {
+                              int64_t ld, int n, cudaStream_t st) {
   if (n_list <= 0) return cudaSuccess;
   k_tip_counts<<<n_list, 256, 0, st>>>(tip_nodes, slot_of_node, tip_of_node, col_ptr, col_row,
-                                       col_val, counts, n);
+                                       col_val, counts, ld, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
                                const int32_t *child_idx, const int32_t *slot_of_node,
-                               double *counts, int n, cudaStream_t st) {
+                               double *counts, int64_t ld, cudaStream_t st) {
   if (n_list <= 0) return cudaSuccess;
-  dim3 grid(n_list, (n + 255) / 256);
-  k_node_counts<<<grid, 256, 0, st>>>(nodes, child_ptr, child_idx, slot_of_node, counts, n);
+  dim3 grid(n_list, (unsigned)((ld + 255) / 256));
+  k_node_counts<<<grid, 256, 0, st>>>(nodes, child_ptr, child_idx, slot_of_node, counts, ld);
   return cudaGetLastError();
 }
 
 cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
-                            const int32_t *slot_of_node, const double *counts,
+                            const int32_t *slot_of_node, const double *counts, int64_t ld,
                             const double *length, const double *total, const float *inv_total_f,
-                            void *X, int64_t pitch, int n, cudaStream_t st) {
+                            void *X, int64_t pitch, const TabDesc *tabs, int n_tabs, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-#define UF_EMB(T, K)                                                                       \
-  k_emb_rows<T, K><<<rows, 256, 0, st>>>(b0, slot_of_node, counts, length, total, inv_total_f, \
-                                         (T *)X, pitch, n)
+#define UF_EMB(T, K)                                                                            \
+  k_emb_rows<T, K><<<rows, 256, 0, st>>>(b0, slot_of_node, counts, ld, length, total, inv_total_f, \
+                                         (T *)X, pitch, tabs, n_tabs)
   if (fp32) {
     if (kind == EMB_SCALED) UF_EMB(float, EMB_SCALED);
     else if (kind == EMB_PRESENCE) UF_EMB(float, EMB_PRESENCE);

@@ -9,10 +9,12 @@
 // l = l_hi + l_mid + l_lo (each product is exact; the sum of the three terms
 // carries l to about 24 bits), accumulated in FP32 in tensor memory.
 //
-// Layout: Pl[4][n_pad][K_pad] BF16, plane 0 = P, planes 1-3 = A_hi, A_mid,
-// A_lo, branches contiguous (K-major for both MMA operands).  A work unit is
-// (K chunk of `kc` branches, tile of GM = 128 samples i x GN = 256 samples j);
-// only tiles that meet the upper triangle i <= j are scheduled.  Per unit the
+// Layout: Pl[4][npad_tot][K_pad] BF16, plane 0 = P, planes 1-3 = A_hi, A_mid,
+// A_lo, branches contiguous (K-major for both MMA operands); the tables of a
+// batch occupy consecutive row ranges of every plane.  A work unit is
+// (K chunk of `kc` branches, tile of GM = 128 samples i x GN = 256 samples j of
+// one table); only tiles that meet the upper triangle i <= j are scheduled,
+// chunk-major over all tables of the batch.  Per unit the
 // accumulator (128 lanes x 256 FP32 columns of TMEM, two buffers) is rounded
 // to int64 fixed point (scale 2^F) and added atomically into Gt, stored
 // transposed (cell (i, j), i <= j, at Gt[j * n_pad + i]) so that the 32 lanes
@@ -137,15 +139,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 struct GUnit {
   int bi, bj, k0, nk;  // tile, first branch and number of GK steps
+  int n, n_pad, row_base;
+  int64_t gt_off;
 };
 
 __device__ __forceinline__ GUnit gram_unit(const GramArgs &a, int u) {
   const int c = u / a.n_tiles, t = u - c * a.n_tiles;
+  const GramTab &tb = a.tabs[a.tile_tab[t]];
   GUnit g;
   g.bi = a.tile_bi[t];
   g.bj = a.tile_bj[t];
   g.k0 = c * a.kc;
   g.nk = (min(a.kc, a.k_len - g.k0) + GK - 1) / GK;
+  g.n = tb.n;
+  g.n_pad = tb.n_pad;
+  g.row_base = tb.row_base;
+  g.gt_off = tb.gt_off;
   return g;
 }
 
@@ -196,8 +205,8 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         unsigned char *base = smem + stage * STAGE_BYTES;
         const int kx = g.k0 + ks * GK;
         for (int t = 0; t < NSPLIT; t++)
-          tma_load_2d(base + t * A_BYTES, &mapA, &full[stage], kx, (1 + t) * a.n_pad + g.bi * GM);
-        tma_load_2d(base + NSPLIT * A_BYTES, &mapB, &full[stage], kx, g.bj * GN);
+          tma_load_2d(base + t * A_BYTES, &mapA, &full[stage], kx, (1 + t) * a.npad_tot + g.row_base + g.bi * GM);
+        tma_load_2d(base + NSPLIT * A_BYTES, &mapB, &full[stage], kx, g.row_base + g.bj * GN);
         if (++stage == GSTAGES) {
           stage = 0;
           phase ^= 1;
@@ -267,9 +276,9 @@ __global__ void __launch_bounds__(G_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < 32; q++) {
           const int j = g.bj * GN + c * 32 + q;
-          if (i <= j && j < a.n) {
+          if (i <= j && j < g.n) {
             const long long v = __float2ll_rn(__uint_as_float(r[q]) * scale);
-            atomicAdd(a.Gt + (size_t)j * a.n_pad + i, (unsigned long long)v);
+            atomicAdd(a.Gt + g.gt_off + (int64_t)j * g.n_pad + i, (unsigned long long)v);
           }
         }
       }
@@ -287,18 +296,40 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// Table whose plane rows include row k (tables in order of row_base).
+__device__ __forceinline__ int gram_table_of_row(const GramTab *tabs, int n_tabs, int k) {
+  int lo = 0, hi = n_tabs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tabs[mid].row_base <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Presence and split-length planes of a branch block, transposed to
-// sample-major: Pl[0][k][e] = [count > 0], Pl[1 + t][k][e] = presence * l_t.
+// sample-major: Pl[0][k][e] = [count > 0], Pl[1 + t][k][e] = presence * l_t,
+// for every plane row k (padding rows of a table are 0).
 __global__ void k_gram_prep(int64_t b0, int rows, int k_len, const int32_t *__restrict__ slot_of_node,
-                            const double *__restrict__ counts, const double *__restrict__ length, int n,
-                            int n_pad, int64_t K_pad, __nv_bfloat16 *__restrict__ Pl) {
+                            const double *__restrict__ counts, int64_t ld, const double *__restrict__ length,
+                            const GramTab *__restrict__ tabs, int n_tabs, int npad_tot, int64_t K_pad,
+                            __nv_bfloat16 *__restrict__ Pl) {
   __shared__ float tile[32][33];
   const int e_base = blockIdx.x * 32, k_base = blockIdx.y * 32;
-  for (int el = threadIdx.y; el < 32; el += blockDim.y) {
-    const int e = e_base + el, k = k_base + threadIdx.x;
-    float p = 0.f;
-    if (e < rows && k < n) p = counts[(int64_t)slot_of_node[b0 + e] * n + k] > 0.0 ? 1.f : 0.f;
-    tile[el][threadIdx.x] = p;
+  {
+    const int k = k_base + threadIdx.x;  // plane row
+    int col = -1;
+    if (k < npad_tot) {
+      const GramTab &tb = tabs[n_tabs == 1 ? 0 : gram_table_of_row(tabs, n_tabs, k)];
+      const int kl = k - tb.row_base;
+      if (kl < tb.n) col = tb.off + kl;
+    }
+    for (int el = threadIdx.y; el < 32; el += blockDim.y) {
+      const int e = e_base + el;
+      float p = 0.f;
+      if (e < rows && col >= 0) p = counts[(int64_t)slot_of_node[b0 + e] * ld + col] > 0.0 ? 1.f : 0.f;
+      tile[el][threadIdx.x] = p;
+    }
   }
   __syncthreads();
   const int e = e_base + threadIdx.x;
@@ -309,10 +340,10 @@ __global__ void k_gram_prep(int64_t b0, int rows, int k_len, const int32_t *__re
   const __nv_bfloat16 lo = __double2bfloat16(r1 - (double)__bfloat162float(mid));
   const __nv_bfloat16 zero = __float2bfloat16(0.f), one = __float2bfloat16(1.f);
   if (e >= k_len) return;
-  const int64_t plane = (int64_t)n_pad * K_pad;
+  const int64_t plane = (int64_t)npad_tot * K_pad;
   for (int kl = threadIdx.y; kl < 32; kl += blockDim.y) {
     const int k = k_base + kl;
-    if (k >= n_pad) continue;
+    if (k >= npad_tot) continue;
     const bool on = tile[threadIdx.x][kl] != 0.f;
     const int64_t at = (int64_t)k * K_pad + e;
     Pl[at] = on ? one : zero;
@@ -368,32 +399,28 @@ EncodeTiledFn encode_fn() {
 
 }  // namespace
 
-void gram_geometry(int n, int rows, int *n_pad, int64_t *K_pad) {
-  *n_pad = (n + GN - 1) / GN * GN;
-  *K_pad = ((int64_t)std::max(rows, 1) + GK - 1) / GK * GK;
-}
+int gram_pad(int n) { return (n + GN - 1) / GN * GN; }
 
-std::vector<int32_t> gram_tiles(int n_pad) {
-  std::vector<int32_t> bi, bj;
+int64_t gram_kpad(int rows) { return ((int64_t)std::max(rows, 1) + GK - 1) / GK * GK; }
+
+void gram_tiles(int n_pad, std::vector<int32_t> *bi, std::vector<int32_t> *bj) {
   for (int j = 0; j < n_pad / GN; j++)
     for (int i = 0; i < n_pad / GM; i++)
       if (i * GM < (j + 1) * GN) {
-        bi.push_back(i);
-        bj.push_back(j);
+        bi->push_back(i);
+        bj->push_back(j);
       }
-  std::vector<int32_t> out(bi);
-  out.insert(out.end(), bj.begin(), bj.end());
-  return out;
 }
 
 size_t gram_smem_bytes() { return (size_t)GSTAGES * STAGE_BYTES + 1024; }
 
 cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, const double *counts,
-                             const double *length, int n, int n_pad, int64_t K_pad, void *Pl, cudaStream_t st) {
+                             int64_t ld, const double *length, const GramTab *tabs, int n_tabs,
+                             int npad_tot, int64_t K_pad, void *Pl, cudaStream_t st) {
   const int k_len = (int)((rows + GK - 1) / GK * GK);
-  dim3 grid((k_len + 31) / 32, (n_pad + 31) / 32), block(32, 8);
-  k_gram_prep<<<grid, block, 0, st>>>(b0, rows, k_len, slot_of_node, counts, length, n, n_pad, K_pad,
-                                       (__nv_bfloat16 *)Pl);
+  dim3 grid((k_len + 31) / 32, (npad_tot + 31) / 32), block(32, 8);
+  k_gram_prep<<<grid, block, 0, st>>>(b0, rows, k_len, slot_of_node, counts, ld, length, tabs, n_tabs,
+                                       npad_tot, K_pad, (__nv_bfloat16 *)Pl);
   return cudaGetLastError();
 }
 
@@ -401,7 +428,7 @@ cudaError_t launch_gram(const GramArgs &a0, void *Pl, int64_t K_pad, cudaStream_
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap mapA, mapB;
-  const cuuint64_t dims[2] = {(cuuint64_t)K_pad, (cuuint64_t)4 * a0.n_pad};
+  const cuuint64_t dims[2] = {(cuuint64_t)K_pad, (cuuint64_t)4 * a0.npad_tot};
   const cuuint64_t strides[1] = {(cuuint64_t)K_pad * 2};
   const cuuint32_t boxA[2] = {GK, GM}, boxB[2] = {GK, GN}, es[2] = {1, 1};
   if (enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Pl, dims, strides, boxA, es, CU_TENSOR_MAP_INTERLEAVE_NONE,

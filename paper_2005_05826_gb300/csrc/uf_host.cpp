@@ -403,106 +403,207 @@ double accum_scale(const uf_tree *tree, const uf_table *table, int kind) {
 
 namespace {
 
-struct Job {
+// One table of a compute call: its stripe range and output.
+struct TableJob {
+  uf_table *table;
+  int64_t start, stop;
+  void *out;
+  uf_report *rep;
+};
+
+// A compute call: one or more tables over one tree, one method and precision.
+struct BatchJob {
   uf_method method;
   double alpha;
   bool fp32;
-  int64_t start, stop;
-  void *out;
   int out_is_device, out_fp32;
-  uf_report *rep;
   cudaStream_t st;
+  std::vector<TableJob> tabs;
 };
 
-// Unweighted, mixed precision: per branch block, tip counts -> internal levels
-// -> presence / split-length planes -> tcgen05 gram accumulation; then the
-// gram finalize.  Throws CudaFail on CUDA errors.
-uf_status run_gram(uf_tree *tree, uf_table *table, const Job &J) {
-  const auto t_start = std::chrono::steady_clock::now();
-  g_h2d = 0.0;
-  int device = 0;
-  ck(cudaGetDevice(&device), "cudaGetDevice");
-  keep_pool_memory(device);
-  const int n = (int)table->n;
-  const int64_t S = n / 2;
-  const bool full = J.start == 0 && J.stop == S;
-  const double scale = accum_scale(tree, table, EMB_PRESENCE);
-  const int64_t nb = tree->n_nodes - 1;
-  const int64_t rows_out = J.stop - J.start;
-  int n_pad = 0;
-  int64_t K_probe = 0;
-  gram_geometry(n, 1, &n_pad, &K_probe);
+// Device copies of the inputs and the per-sample arrays on the combined axis.
+struct Inputs {
+  uf_tree::Dev *td = nullptr;
+  Plan *P = nullptr;
+  Plan::Dev *pd = nullptr;
+  std::vector<uf_table::Dev *> xd;
+};
 
+Inputs bind_inputs(uf_tree *tree, const BatchJob &J, int device, int64_t rows) {
+  Inputs in;
+  {
+    std::lock_guard<std::mutex> g(tree->mu);
+    in.td = &tree_dev(tree, device);
+    in.P = get_plan(tree, rows);
+    in.pd = &plan_dev(in.P, device);
+  }
+  for (const TableJob &t : J.tabs) {
+    std::lock_guard<std::mutex> g(t.table->mu);
+    in.xd.push_back(&table_dev(t.table, device));
+  }
+  return in;
+}
+
+// Branch rows per embedding block for a working budget of per_row bytes a row
+// plus fixed bytes.
+int64_t block_rows(int64_t nb, double per_row, double fixed) {
   size_t free_b = 0, total_b = 0;
   ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-  const double gt_bytes = (double)n_pad * n_pad * 8.0;
-  double budget = std::min(0.5 * (double)free_b - gt_bytes, 24e9);
-  const double per_row = (double)n * 8.0 + 4.0 * n_pad * 2.0 + 8.0;
+  const double budget = std::min(0.5 * (double)free_b - fixed, 24e9);
   int64_t rows = (int64_t)(budget / per_row / 1.1);
   rows = std::max<int64_t>(std::min<int64_t>(rows, nb), std::min<int64_t>(nb, 256));
   if (g_branch_block.load() > 0) rows = std::min<int64_t>(g_branch_block.load(), std::max<int64_t>(nb, 1));
-  rows = std::max<int64_t>(rows, 1);
-  int64_t K_pad = 0;
-  gram_geometry(n, (int)rows, &n_pad, &K_pad);
+  return std::max<int64_t>(rows, 1);
+}
 
-  std::unique_lock<std::mutex> lk_tree(tree->mu);
-  uf_tree::Dev &td = tree_dev(tree, device);
-  Plan *P = get_plan(tree, rows);
-  Plan::Dev &pd = plan_dev(P, device);
-  lk_tree.unlock();
-  std::unique_lock<std::mutex> lk_tab(table->mu);
-  uf_table::Dev &xd = table_dev(table, device);
-  lk_tab.unlock();
+// Tip counts of one block for every table (each into its columns), then the
+// internal levels over the combined axis.
+void enqueue_counts(const Inputs &in, const BatchJob &J, const std::vector<int> &off, size_t b, double *counts,
+                    int64_t ld, cudaStream_t st, int64_t *kernels) {
+  const auto &ls = in.P->launches[b];
+  for (size_t t = 0; t < J.tabs.size(); t++) {
+    ck(launch_tip_counts(in.pd->lists + ls[0].first, ls[0].second, in.pd->slot_of_node, in.td->tip_of_node,
+                         in.xd[t]->col_ptr, in.xd[t]->col_row, in.xd[t]->col_val, counts + off[t], ld,
+                         (int)J.tabs[t].table->n, st),
+       "tip counts");
+    *kernels += ls[0].second > 0;
+  }
+  for (size_t l = 1; l < ls.size(); l++) {
+    ck(launch_node_counts(in.pd->lists + ls[l].first, ls[l].second, in.td->child_ptr, in.td->child_idx,
+                          in.pd->slot_of_node, counts, ld, st),
+       "node counts");
+    *kernels += ls[l].second > 0;
+  }
+}
 
+// Output buffers: the caller's device memory, or a device staging buffer
+// copied to the caller's host memory at the end.
+struct Outputs {
+  std::vector<DevBuf> tmp;
+  std::vector<void *> dev;
+  std::vector<size_t> bytes;
+};
+
+Outputs bind_outputs(const BatchJob &J, cudaStream_t st) {
+  Outputs o;
+  for (const TableJob &t : J.tabs) {
+    const int64_t n = t.table->n, S = n / 2;
+    const bool full = t.start == 0 && t.stop == S;
+    const size_t elems = full ? (size_t)n * (n - 1) / 2 : (size_t)(t.stop - t.start) * n;
+    o.bytes.push_back(elems * (J.out_fp32 ? 4 : 8));
+    if (J.out_is_device) {
+      o.tmp.emplace_back();
+      o.dev.push_back(t.out);
+    } else {
+      o.tmp.emplace_back(o.bytes.back(), st, "alloc output");
+      o.dev.push_back(o.tmp.back().p);
+    }
+  }
+  return o;
+}
+
+void fill_reports(uf_tree *tree, const BatchJob &J, const Outputs &o, double ms[4], int64_t kernels,
+                  int64_t acc_launches, int path, int64_t rows, int64_t n_blocks, double exec_flops,
+                  int tile_s, int tile_k, double seconds) {
+  const int64_t nb = tree->n_nodes - 1;
+  for (size_t t = 0; t < J.tabs.size(); t++) {
+    if (!J.tabs[t].rep) continue;
+    uf_report &r = *J.tabs[t].rep;
+    memset(&r, 0, sizeof r);
+    const int64_t n = J.tabs[t].table->n, S = n / 2;
+    const bool full = J.tabs[t].start == 0 && J.tabs[t].stop == S;
+    const int64_t rows_out = J.tabs[t].stop - J.tabs[t].start;
+    const double pairs = full ? (double)n * (n - 1) / 2.0
+                              : (double)rows_out * n - ((2 * J.tabs[t].stop == n) ? n / 2.0 : 0.0);
+    r.updates = pairs * (double)nb;
+    r.alg_flops = 2.0 * pairs * nb;
+    r.exec_flops = exec_flops / (double)J.tabs.size();
+    r.hbm_bytes_est = (double)nb * (double)n * 8 * 3 + (double)o.bytes[t];
+    r.stripe_tile = tile_s;
+    r.sample_tile = tile_k;
+    r.branch_block = rows;
+    r.n_blocks = n_blocks;
+    r.kernels = kernels;
+    r.path = path;
+    r.h2d_bytes = g_h2d;
+    r.d2h_bytes = J.out_is_device ? 0.0 : (double)o.bytes[t];
+    r.t_embed_ms = ms[0];
+    r.t_accumulate_ms = ms[1];
+    r.t_diag_ms = ms[2];
+    r.t_finalize_ms = ms[3];
+    r.acc_launches = acc_launches;
+    r.seconds = seconds;
+  }
+}
+
+// Unweighted, mixed precision, on the tensor cores: per branch block, counts
+// -> presence / split-length planes of every table -> tcgen05 gram; then the
+// gram finalize of every table.  Throws CudaFail on CUDA errors.
+uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, double t0_dummy) {
+  (void)t0_dummy;
+  const auto t_start = std::chrono::steady_clock::now();
+  const size_t nt = J.tabs.size();
+  std::vector<int> off(nt);
+  std::vector<GramTab> gt(nt);
+  std::vector<int32_t> tile_tab, tile_bi, tile_bj;
+  int n_cols = 0, npad_tot = 0;
+  int64_t gt_cells = 0;
+  for (size_t t = 0; t < nt; t++) {
+    const int n = (int)J.tabs[t].table->n;
+    off[t] = n_cols;
+    gt[t].n = n;
+    gt[t].n_pad = gram_pad(n);
+    gt[t].row_base = npad_tot;
+    gt[t].off = n_cols;
+    gt[t].gt_off = gt_cells;
+    const size_t before = tile_bi.size();
+    gram_tiles(gt[t].n_pad, &tile_bi, &tile_bj);
+    tile_tab.insert(tile_tab.end(), tile_bi.size() - before, (int32_t)t);
+    n_cols += n;
+    npad_tot += gt[t].n_pad;
+    gt_cells += (int64_t)gt[t].n_pad * gt[t].n_pad;
+  }
+  const int n_tiles = (int)tile_bi.size();
+  const int64_t nb = tree->n_nodes - 1;
+  const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + 4.0 * npad_tot * 2.0 + 8.0, (double)gt_cells * 8.0);
+  const int64_t K_pad = gram_kpad((int)rows);
+  Inputs in = bind_inputs(tree, J, device, rows);
   cudaStream_t st = J.st;
   int64_t kernels = 0, acc_launches = 0;
   PhaseTimer timer(g_kernel_timing.load() != 0, st);
-  const std::vector<int32_t> tiles = gram_tiles(n_pad);
-  const int n_tiles = (int)tiles.size() / 2;
-  DevBuf counts((size_t)P->n_slots * n * 8, st, "alloc counts");
-  DevBuf Pl((size_t)4 * n_pad * K_pad * 2, st, "alloc presence planes");
-  DevBuf Gt((size_t)n_pad * n_pad * 8, st, "alloc gram");
-  DevBuf d_tiles(tiles.size() * 4, st, "alloc tile list");
+  std::vector<int32_t> tl(tile_tab);
+  tl.insert(tl.end(), tile_bi.begin(), tile_bi.end());
+  tl.insert(tl.end(), tile_bj.begin(), tile_bj.end());
+  DevBuf counts((size_t)in.P->n_slots * n_cols * 8, st, "alloc counts");
+  DevBuf Pl((size_t)4 * npad_tot * K_pad * 2, st, "alloc presence planes");
+  DevBuf Gt((size_t)gt_cells * 8, st, "alloc gram");
+  DevBuf d_tiles(tl.size() * 4, st, "alloc tile list");
+  DevBuf d_tabs(nt * sizeof(GramTab), st, "alloc table list");
   DevBuf err(sizeof(int), st, "alloc error flag");
-  ck(cudaMemcpyAsync(d_tiles.p, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, st), "copy tiles");
-  ck(cudaMemsetAsync(Gt.p, 0, (size_t)n_pad * n_pad * 8, st), "memset");
+  ck(cudaMemcpyAsync(d_tiles.p, tl.data(), tl.size() * 4, cudaMemcpyHostToDevice, st), "copy tiles");
+  ck(cudaMemcpyAsync(d_tabs.p, gt.data(), nt * sizeof(GramTab), cudaMemcpyHostToDevice, st), "copy tables");
+  ck(cudaMemsetAsync(Gt.p, 0, (size_t)gt_cells * 8, st), "memset");
   ck(cudaMemsetAsync(err.p, 0, sizeof(int), st), "memset");
-  const size_t out_elems = full ? (size_t)n * (n - 1) / 2 : (size_t)rows_out * n;
-  const size_t out_bytes = out_elems * (J.out_fp32 ? 4 : 8);
-  DevBuf out_tmp;
-  void *out_dev = J.out;
-  if (!J.out_is_device) {
-    out_tmp = DevBuf(out_bytes, st, "alloc output");
-    out_dev = out_tmp.p;
-  }
+  Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
-  for (size_t b = 0; b < P->b0.size(); b++) {
-    const int64_t b0 = P->b0[b], b1 = P->b1[b];
-    const auto &ls = P->launches[b];
+  for (size_t b = 0; b < in.P->b0.size(); b++) {
+    const int64_t b0 = in.P->b0[b], b1 = in.P->b1[b];
     timer.begin(0);
-    ck(launch_tip_counts(pd.lists + ls[0].first, ls[0].second, pd.slot_of_node, td.tip_of_node,
-                         xd.col_ptr, xd.col_row, xd.col_val, counts.as<double>(), n, st),
-       "tip counts");
-    kernels += ls[0].second > 0;
-    for (size_t l = 1; l < ls.size(); l++) {
-      ck(launch_node_counts(pd.lists + ls[l].first, ls[l].second, td.child_ptr, td.child_idx,
-                            pd.slot_of_node, counts.as<double>(), n, st),
-         "node counts");
-      kernels += ls[l].second > 0;
-    }
-    ck(launch_gram_prep(b0, (int)(b1 - b0), pd.slot_of_node, counts.as<double>(), td.length, n, n_pad,
-                        K_pad, Pl.p, st),
+    enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, st, &kernels);
+    ck(launch_gram_prep(b0, (int)(b1 - b0), in.pd->slot_of_node, counts.as<double>(), n_cols, in.td->length,
+                        d_tabs.as<GramTab>(), (int)nt, npad_tot, K_pad, Pl.p, st),
        "presence planes");
     kernels++;
     timer.end();
     GramArgs ga{};
-    ga.n = n;
-    ga.n_pad = n_pad;
     ga.k_len = (int)round_up(b1 - b0, 64);
     ga.kc = 4096;
     ga.n_tiles = n_tiles;
-    ga.tile_bi = d_tiles.as<int32_t>();
-    ga.tile_bj = d_tiles.as<int32_t>() + n_tiles;
+    ga.npad_tot = npad_tot;
+    ga.tile_tab = d_tiles.as<int32_t>();
+    ga.tile_bi = d_tiles.as<int32_t>() + n_tiles;
+    ga.tile_bj = d_tiles.as<int32_t>() + 2 * n_tiles;
+    ga.tabs = d_tabs.as<GramTab>();
     ga.Gt = Gt.as<unsigned long long>();
     ga.scale = scale;
     ga.err = err.as<int>();
@@ -513,161 +614,129 @@ uf_status run_gram(uf_tree *tree, uf_table *table, const Job &J) {
     acc_launches++;
     exec_flops += 2.0 * 3 * 128.0 * 256.0 * ga.k_len * n_tiles;
   }
-  GramFinalArgs fa{};
-  fa.n = n;
-  fa.n_pad = n_pad;
-  fa.s0 = J.start;
-  fa.s1 = J.stop;
-  fa.full = full;
-  fa.Gt = Gt.as<unsigned long long>();
-  fa.out = out_dev;
-  fa.out_fp32 = J.out_fp32;
   timer.begin(3);
-  ck(launch_finalize_gram(fa, st), "finalize");
+  for (size_t t = 0; t < nt; t++) {
+    GramFinalArgs fa{};
+    fa.n = gt[t].n;
+    fa.n_pad = gt[t].n_pad;
+    fa.s0 = J.tabs[t].start;
+    fa.s1 = J.tabs[t].stop;
+    fa.full = J.tabs[t].start == 0 && J.tabs[t].stop == gt[t].n / 2;
+    fa.Gt = Gt.as<unsigned long long>() + gt[t].gt_off;
+    fa.out = o.dev[t];
+    fa.out_fp32 = J.out_fp32;
+    ck(launch_finalize_gram(fa, st), "finalize");
+    kernels++;
+  }
   timer.end();
-  kernels++;
   int h_err = 0;
   ck(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
-  if (!J.out_is_device) ck(cudaMemcpyAsync(J.out, out_dev, out_bytes, cudaMemcpyDeviceToHost, st), "copy out");
+  if (!J.out_is_device)
+    for (size_t t = 0; t < nt; t++)
+      ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
   counts = DevBuf();
   Pl = DevBuf();
   Gt = DevBuf();
   d_tiles = DevBuf();
-  out_tmp = DevBuf();
+  d_tabs = DevBuf();
+  o.tmp.clear();
   ck(cudaStreamSynchronize(st), "synchronize");  // the error flag is read here
   err = DevBuf();
   if (h_err) return fail(UF_ETIMEOUT, "tensor-core kernel: a bounded wait gave up");
-  double ms4[4] = {0, 0, 0, 0};
-  timer.collect(ms4);
-  if (J.rep) {
-    uf_report &r = *J.rep;
-    memset(&r, 0, sizeof r);
-    const double pairs = full ? (double)n * (n - 1) / 2.0
-                              : (double)rows_out * n - ((2 * J.stop == n) ? n / 2.0 : 0.0);
-    r.updates = pairs * (double)nb;
-    r.alg_flops = 2.0 * pairs * nb;
-    r.exec_flops = exec_flops;
-    r.hbm_bytes_est = (double)nb * ((double)n * 8 * 3 + 4.0 * n_pad * 2) + out_bytes;
-    r.stripe_tile = 256;
-    r.sample_tile = 128;
-    r.branch_block = rows;
-    r.n_blocks = (int64_t)P->b0.size();
-    r.kernels = kernels;
-    r.path = 1;
-    r.h2d_bytes = g_h2d;
-    r.d2h_bytes = J.out_is_device ? 0.0 : (double)out_bytes;
-    r.t_embed_ms = ms4[0];
-    r.t_accumulate_ms = ms4[1];
-    r.t_finalize_ms = ms4[3];
-    r.acc_launches = acc_launches;
-    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-  }
+  double ms[4] = {0, 0, 0, 0};
+  timer.collect(ms);
+  fill_reports(tree, J, o, ms, kernels, acc_launches, 1, rows, (int64_t)in.P->b0.size(), exec_flops, 256, 128,
+               std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
   return UF_OK;
 }
 
-// One full compute on the current device; throws CudaFail on CUDA errors.
-uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
-  if (J.method == UF_UNWEIGHTED && J.fp32 && g_tensor_path.load()) return run_gram(tree, table, J);
+// Every other method / precision on the CUDA-core stripe kernels.  Throws
+// CudaFail on CUDA errors.
+uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method method, double scale) {
   const auto t_start = std::chrono::steady_clock::now();
-  g_h2d = 0.0;
-  int device = 0;
-  ck(cudaGetDevice(&device), "cudaGetDevice");
-  keep_pool_memory(device);
-  const int n = (int)table->n;
-  const int64_t S = n / 2;
-  const bool full = J.start == 0 && J.stop == S;
-  uf_method method = J.method;
-  if (method == UF_GENERALIZED && J.alpha == 1.0) method = UF_WEIGHTED_NORMALIZED;  // s^0 == 1
+  const size_t nt = J.tabs.size();
   const int acc = method == UF_GENERALIZED ? ACC_GEN : ACC_MIN;
-  const int kind = method == UF_GENERALIZED ? EMB_PROP
-                   : method == UF_UNWEIGHTED ? EMB_PRESENCE
-                                             : EMB_SCALED;
+  const int kind = method == UF_GENERALIZED ? EMB_PROP : method == UF_UNWEIGHTED ? EMB_PRESENCE : EMB_SCALED;
   const bool fp32 = J.fp32;
   const size_t es = fp32 ? 4 : 8;
   int tile_s = 0, tile_k = 0;
   stripe_tile_shape(acc, fp32, &tile_s, &tile_k);
-  const int m_lo = (int)(J.start / tile_s), m_hi = (int)((J.stop - 1) / tile_s);
-  const double scale = accum_scale(tree, table, kind);
-  const int64_t pitch = round_up(round_up(n, tile_k) + (int64_t)(m_hi + 1) * tile_s, 32);
-
-  // branch-block size: fit counts + embedding rows into a working budget
-  size_t free_b = 0, total_b = 0;
-  ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+  std::vector<TabDesc> tabs(nt);
+  std::vector<int> off(nt);
+  int n_cols = 0, n_tiles = 0;
+  int64_t pitch = 0, cells = 0;
+  for (size_t t = 0; t < nt; t++) {
+    const int n = (int)J.tabs[t].table->n;
+    TabDesc &d = tabs[t];
+    d.n = n;
+    d.off = n_cols;
+    d.s_lo = (int)J.tabs[t].start;
+    d.s_hi = (int)(J.tabs[t].stop - 1);
+    d.m_lo = (int)(J.tabs[t].start / tile_s);
+    d.m_hi = (int)((J.tabs[t].stop - 1) / tile_s);
+    d.n_ktiles = (n + tile_k - 1) / tile_k;
+    d.tile0 = n_tiles;
+    d.x_col = pitch;
+    d.m_off = cells;
+    off[t] = n_cols;
+    n_cols += n;
+    n_tiles += d.n_ktiles * (d.m_hi - d.m_lo + 1);
+    pitch += round_up(round_up(n, tile_k) + (int64_t)(d.m_hi + 1) * tile_s, 32);
+    cells += (J.tabs[t].stop - J.tabs[t].start) * (int64_t)n;
+  }
   const int64_t nb = tree->n_nodes - 1;
-  const int64_t rows_out = J.stop - J.start;
-  const double acc_bytes = (double)rows_out * n * 8.0 * (acc == ACC_GEN ? 2 : 1) + n * 8.0;
-  double budget = std::min(0.5 * (double)free_b - acc_bytes, 24e9);
-  const double per_row = (double)n * 8.0 + (double)pitch * es + 8.0;
-  int64_t rows = (int64_t)(budget / per_row / 1.1);
-  rows = std::max<int64_t>(std::min<int64_t>(rows, nb), std::min<int64_t>(nb, 256));
-  if (g_branch_block.load() > 0) rows = std::min<int64_t>(g_branch_block.load(), std::max<int64_t>(nb, 1));
-  rows = std::max<int64_t>(rows, 1);
-
-  std::unique_lock<std::mutex> lk_tree(tree->mu);
-  uf_tree::Dev &td = tree_dev(tree, device);
-  Plan *P = get_plan(tree, rows);
-  Plan::Dev &pd = plan_dev(P, device);
-  lk_tree.unlock();
-  std::unique_lock<std::mutex> lk_tab(table->mu);
-  uf_table::Dev &xd = table_dev(table, device);
-  lk_tab.unlock();
-
+  const double acc_bytes = (double)cells * 8.0 * (acc == ACC_GEN ? 2 : 1) + n_cols * 8.0;
+  const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + (double)pitch * es + 8.0 + n_cols * es / 64.0, acc_bytes);
+  Inputs in = bind_inputs(tree, J, device, rows);
   cudaStream_t st = J.st;
   int64_t kernels = 0, acc_launches = 0;
   PhaseTimer timer(g_kernel_timing.load() != 0, st);
-  DevBuf counts((size_t)P->n_slots * n * 8, st, "alloc counts");
+  DevBuf counts((size_t)in.P->n_slots * n_cols * 8, st, "alloc counts");
   DevBuf X((size_t)rows * pitch * es, st, "alloc embeddings");
-  DevBuf M((size_t)rows_out * n * 8, st, "alloc stripes");
+  DevBuf M((size_t)cells * 8, st, "alloc stripes");
   DevBuf M2, Dg, diag_tmp, counter(sizeof(int), st, "alloc counter");
+  DevBuf d_tabs(nt * sizeof(TabDesc), st, "alloc table list");
+  DevBuf total((size_t)n_cols * 8, st, "alloc totals"), inv_total((size_t)n_cols * 4, st, "alloc totals");
+  ck(cudaMemcpyAsync(d_tabs.p, tabs.data(), nt * sizeof(TabDesc), cudaMemcpyHostToDevice, st), "copy tables");
+  for (size_t t = 0; t < nt; t++) {
+    const size_t n = (size_t)J.tabs[t].table->n;
+    ck(cudaMemcpyAsync(total.as<double>() + off[t], in.xd[t]->total, n * 8, cudaMemcpyDeviceToDevice, st),
+       "gather totals");
+    ck(cudaMemcpyAsync(inv_total.as<float>() + off[t], in.xd[t]->inv_total_f, n * 4, cudaMemcpyDeviceToDevice,
+                       st),
+       "gather totals");
+  }
   if (acc == ACC_GEN) {
-    M2 = DevBuf((size_t)rows_out * n * 8, st, "alloc stripes");
+    M2 = DevBuf((size_t)cells * 8, st, "alloc stripes");
+    ck(cudaMemsetAsync(M2.p, 0, (size_t)cells * 8, st), "memset");
   } else {
-    Dg = DevBuf((size_t)n * 8, st, "alloc diagonal");
-    diag_tmp = DevBuf(diag_scratch_bytes(fp32, (int)rows, n), st, "alloc diagonal scratch");
+    Dg = DevBuf((size_t)n_cols * 8, st, "alloc diagonal");
+    diag_tmp = DevBuf(diag_scratch_bytes(fp32, (int)rows, n_cols), st, "alloc diagonal scratch");
+    ck(cudaMemsetAsync(Dg.p, 0, (size_t)n_cols * 8, st), "memset");
   }
-  const size_t out_elems = full ? (size_t)n * (n - 1) / 2 : (size_t)rows_out * n;
-  const size_t out_bytes = out_elems * (J.out_fp32 ? 4 : 8);
-  DevBuf out_tmp;
-  void *out_dev = J.out;
-  if (!J.out_is_device) {
-    out_tmp = DevBuf(out_bytes, st, "alloc output");
-    out_dev = out_tmp.p;
-  }
-  ck(cudaMemsetAsync(M.p, 0, (size_t)rows_out * n * 8, st), "memset");
-  if (M2.p) ck(cudaMemsetAsync(M2.p, 0, (size_t)rows_out * n * 8, st), "memset");
-  if (Dg.p) ck(cudaMemsetAsync(Dg.p, 0, (size_t)n * 8, st), "memset");
-
-  for (size_t b = 0; b < P->b0.size(); b++) {
-    const int64_t b0 = P->b0[b], b1 = P->b1[b];
-    const auto &ls = P->launches[b];
+  ck(cudaMemsetAsync(M.p, 0, (size_t)cells * 8, st), "memset");
+  Outputs o = bind_outputs(J, st);
+  double exec_flops = 0.0;
+  for (size_t b = 0; b < in.P->b0.size(); b++) {
+    const int64_t b0 = in.P->b0[b], b1 = in.P->b1[b];
     timer.begin(0);
-    ck(launch_tip_counts(pd.lists + ls[0].first, ls[0].second, pd.slot_of_node, td.tip_of_node,
-                         xd.col_ptr, xd.col_row, xd.col_val, counts.as<double>(), n, st),
-       "tip counts");
-    kernels += ls[0].second > 0;
-    for (size_t l = 1; l < ls.size(); l++) {
-      ck(launch_node_counts(pd.lists + ls[l].first, ls[l].second, td.child_ptr, td.child_idx,
-                            pd.slot_of_node, counts.as<double>(), n, st),
-         "node counts");
-      kernels += ls[l].second > 0;
-    }
-    ck(launch_emb_rows(kind, fp32, b0, (int)(b1 - b0), pd.slot_of_node, counts.as<double>(),
-                       td.length, xd.total, xd.inv_total_f, X.p, pitch, n, st),
+    enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, st, &kernels);
+    ck(launch_emb_rows(kind, fp32, b0, (int)(b1 - b0), in.pd->slot_of_node, counts.as<double>(), n_cols,
+                       in.td->length, total.as<double>(), inv_total.as<float>(), X.p, pitch,
+                       d_tabs.as<TabDesc>(), (int)nt, st),
        "embedding rows");
     kernels++;
     timer.end();
     StripeArgs sa{};
     sa.X = X.p;
-    sa.len = td.length + b0;
+    sa.len = in.td->length + b0;
     sa.rows = (int)(b1 - b0);
     sa.pitch = pitch;
-    sa.n = n;
-    sa.s_lo = (int)J.start;
-    sa.s_hi = (int)(J.stop - 1);
-    sa.m_lo = m_lo;
-    sa.m_hi = m_hi;
-    sa.n_ktiles = (int)((n + tile_k - 1) / tile_k);
     sa.chunk = stripe_chunk_rows();
+    sa.tabs = d_tabs.as<TabDesc>();
+    sa.n_tabs = (int)nt;
+    sa.n_tiles = n_tiles;
+    sa.n_cols = n_cols;
     sa.M = M.as<unsigned long long>();
     sa.M2 = M2.as<unsigned long long>();
     sa.Dg = Dg.as<unsigned long long>();
@@ -679,6 +748,7 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
     timer.end();
     kernels++;
     acc_launches++;
+    exec_flops += 2.0 * (double)n_tiles * tile_s * tile_k * (double)(b1 - b0);
     if (acc == ACC_MIN) {
       timer.begin(2);
       ck(launch_diag(fp32, sa, diag_tmp.p, st), "diagonal accumulate");
@@ -686,24 +756,28 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
       kernels += 2;
     }
   }
-  FinalArgs fa{};
-  fa.method = method;
-  fa.n = n;
-  fa.s0 = J.start;
-  fa.s1 = J.stop;
-  fa.full = full;
-  fa.mixed_forms = fp32 && acc == ACC_MIN;
-  fa.M = M.as<unsigned long long>();
-  fa.M2 = M2.as<unsigned long long>();
-  fa.Dg = Dg.as<unsigned long long>();
-  fa.inv_scale = 1.0 / scale;
-  fa.out = out_dev;
-  fa.out_fp32 = J.out_fp32;
   timer.begin(3);
-  ck(launch_finalize(fa, st), "finalize");
+  for (size_t t = 0; t < nt; t++) {
+    FinalArgs fa{};
+    fa.method = method;
+    fa.n = tabs[t].n;
+    fa.s0 = J.tabs[t].start;
+    fa.s1 = J.tabs[t].stop;
+    fa.full = J.tabs[t].start == 0 && J.tabs[t].stop == tabs[t].n / 2;
+    fa.mixed_forms = fp32 && acc == ACC_MIN;
+    fa.M = M.as<unsigned long long>() + tabs[t].m_off;
+    fa.M2 = M2.p ? M2.as<unsigned long long>() + tabs[t].m_off : nullptr;
+    fa.Dg = Dg.p ? Dg.as<unsigned long long>() + off[t] : nullptr;
+    fa.inv_scale = 1.0 / scale;
+    fa.out = o.dev[t];
+    fa.out_fp32 = J.out_fp32;
+    ck(launch_finalize(fa, st), "finalize");
+    kernels++;
+  }
   timer.end();
-  kernels++;
-  if (!J.out_is_device) ck(cudaMemcpyAsync(J.out, out_dev, out_bytes, cudaMemcpyDeviceToHost, st), "copy out");
+  if (!J.out_is_device)
+    for (size_t t = 0; t < nt; t++)
+      ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
   // buffers go back to the stream-ordered pool here
   counts = DevBuf();
   X = DevBuf();
@@ -712,41 +786,35 @@ uf_status run_compute(uf_tree *tree, uf_table *table, const Job &J) {
   Dg = DevBuf();
   diag_tmp = DevBuf();
   counter = DevBuf();
-  out_tmp = DevBuf();
+  d_tabs = DevBuf();
+  total = DevBuf();
+  inv_total = DevBuf();
+  o.tmp.clear();
   if (!J.out_is_device || st == nullptr || timer.on) ck(cudaStreamSynchronize(st), "synchronize");
   else ck(cudaGetLastError(), "enqueue");
-  double ms4[4] = {0, 0, 0, 0};
-  timer.collect(ms4);
-
-  if (J.rep) {
-    uf_report &r = *J.rep;
-    memset(&r, 0, sizeof r);
-    const double pairs = full ? (double)n * (n - 1) / 2.0
-                              : (double)rows_out * n - ((2 * J.stop == n) ? n / 2.0 : 0.0);
-    r.updates = pairs * (double)nb;
-    const double cells = (double)rows_out * n;
-    r.alg_flops = (acc == ACC_GEN ? 8.0 : 2.0) * cells * nb;
-    r.exec_flops = (acc == ACC_GEN ? 8.0 : 2.0) * (double)(m_hi - m_lo + 1) * tile_s *
-                   round_up(n, tile_k) * nb;
-    r.hbm_bytes_est = (double)nb * ((double)n * 8 * 3 + (double)pitch * es) +
-                      cells * 8.0 * (acc == ACC_GEN ? 4 : 2) * (double)P->b0.size() +
-                      out_bytes;
-    r.stripe_tile = tile_s;
-    r.sample_tile = tile_k;
-    r.branch_block = rows;
-    r.n_blocks = (int64_t)P->b0.size();
-    r.kernels = kernels;
-    r.path = 0;
-    r.h2d_bytes = g_h2d;
-    r.d2h_bytes = J.out_is_device ? 0.0 : (double)out_bytes;
-    r.t_embed_ms = ms4[0];
-    r.t_accumulate_ms = ms4[1];
-    r.t_diag_ms = ms4[2];
-    r.t_finalize_ms = ms4[3];
-    r.acc_launches = acc_launches;
-    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-  }
+  double ms[4] = {0, 0, 0, 0};
+  timer.collect(ms);
+  fill_reports(tree, J, o, ms, kernels, acc_launches, 0, rows, (int64_t)in.P->b0.size(), exec_flops, tile_s,
+               tile_k, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
   return UF_OK;
+}
+
+// One compute call on the current device; throws CudaFail on CUDA errors.
+uf_status run_batch(uf_tree *tree, const BatchJob &J) {
+  g_h2d = 0.0;
+  int device = 0;
+  ck(cudaGetDevice(&device), "cudaGetDevice");
+  keep_pool_memory(device);
+  uf_method method = J.method;
+  if (method == UF_GENERALIZED && J.alpha == 1.0) method = UF_WEIGHTED_NORMALIZED;  // s^0 == 1
+  const int kind = method == UF_GENERALIZED ? EMB_PROP : method == UF_UNWEIGHTED ? EMB_PRESENCE : EMB_SCALED;
+  double scale = 0.0;  // one fixed-point scale valid for every table of the call
+  for (const TableJob &t : J.tabs) {
+    const double s = accum_scale(tree, t.table, kind);
+    scale = scale == 0.0 ? s : std::min(scale, s);
+  }
+  if (method == UF_UNWEIGHTED && J.fp32 && g_tensor_path.load()) return run_gram(tree, J, device, scale, 0.0);
+  return run_stripes(tree, J, device, method, scale);
 }
 
 uf_status check_args(const uf_tree *tree, const uf_table *table, uf_method method, double alpha,
@@ -950,10 +1018,10 @@ uf_status uf_compute(const uf_tree *tree, const uf_table *table, uf_method metho
     cudaGetLastError();
     return fail(UF_ECUDA, "no CUDA device available");
   }
-  Job J{method, alpha, precision == UF_MIXED, stripe_start, stripe_stop, out, out_is_device,
-        out_fp32, rep, (cudaStream_t)cuda_stream};
+  BatchJob J{method, alpha, precision == UF_MIXED, out_is_device, out_fp32, (cudaStream_t)cuda_stream, {}};
+  J.tabs.push_back(TableJob{const_cast<uf_table *>(table), stripe_start, stripe_stop, out, rep});
   try {
-    return run_compute(const_cast<uf_tree *>(tree), const_cast<uf_table *>(table), J);
+    return run_batch(const_cast<uf_tree *>(tree), J);
   } catch (const CudaFail &f) {
     return f.st;
   } catch (const std::bad_alloc &) {
@@ -967,17 +1035,29 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
                            void *cuda_stream) {
   g_err.clear();
   if (!tables || !outs || n_tables < 0) return fail(UF_EINVAL, "null tables or outputs");
+  BatchJob J{method, alpha, precision == UF_MIXED, out_is_device, 0, (cudaStream_t)cuda_stream, {}};
   for (int64_t t = 0; t < n_tables; t++) {
     uf_status st = check_args(tree, tables[t], method, alpha, precision);
     if (st) return st;
-  }
-  for (int64_t t = 0; t < n_tables; t++) {
+    if (reps) memset(&reps[t], 0, sizeof(uf_report));
     const int64_t S = uf_stripe_count(tables[t]->n);
-    uf_status st = uf_compute(tree, tables[t], method, alpha, precision, 0, S, outs[t],
-                              out_is_device, 0, reps ? &reps[t] : nullptr, cuda_stream);
-    if (st) return st;
+    if (S == 0) continue;  // fewer than two samples: nothing to write
+    if (!outs[t]) return fail(UF_EINVAL, "null output buffer for table %lld", (long long)t);
+    J.tabs.push_back(TableJob{const_cast<uf_table *>(tables[t]), 0, S, outs[t], reps ? &reps[t] : nullptr});
   }
-  return UF_OK;
+  if (J.tabs.empty()) return UF_OK;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(UF_ECUDA, "no CUDA device available");
+  }
+  try {
+    return run_batch(const_cast<uf_tree *>(tree), J);
+  } catch (const CudaFail &f) {
+    return f.st;
+  } catch (const std::bad_alloc &) {
+    return fail(UF_ENOMEM, "host allocation failed");
+  }
 }
 
 }  // extern "C"

@@ -37,18 +37,35 @@ enum AccKind : int {
   ACC_GEN = 1,   // generalized: (den, Q) = sum l s^a, sum l min(u, v) s^(a-1)
 };
 
+// ---- batches ----
+// One table of a batch as the stripe kernels see it.  The samples of all
+// tables sit side by side on one combined sample axis (count slots, totals,
+// the diagonal), and every embedding row holds one padded segment per table.
+struct TabDesc {
+  int n;              // samples
+  int off;            // first column on the combined sample axis
+  int s_lo, s_hi;     // stored stripes [s_lo, s_hi]
+  int m_lo, m_hi;     // stripe tiles covering them
+  int n_ktiles;       // sample tiles
+  int tile0;          // first tile of this table in the batch's tile numbering
+  int64_t x_col;      // first column of its segment in an embedding row
+  int64_t m_off;      // first cell of its stripe accumulator
+};
+
 // ---- embed (uf_embed.cu) ----
+// Count rows live in slots of `ld` doubles (the combined sample axis).
 cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_t *slot_of_node,
                               const int32_t *tip_of_node, const int64_t *col_ptr,
                               const int32_t *col_row, const double *col_val, double *counts,
-                              int n, cudaStream_t st);
+                              int64_t ld, int n, cudaStream_t st);
 cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
                                const int32_t *child_idx, const int32_t *slot_of_node,
-                               double *counts, int n, cudaStream_t st);
+                               double *counts, int64_t ld, cudaStream_t st);
+// Embedding rows of branches b0 .. b0 + rows - 1 for every table segment.
 cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
-                            const int32_t *slot_of_node, const double *counts,
+                            const int32_t *slot_of_node, const double *counts, int64_t ld,
                             const double *length, const double *total, const float *inv_total_f,
-                            void *X, int64_t pitch, int n, cudaStream_t st);
+                            void *X, int64_t pitch, const TabDesc *tabs, int n_tabs, cudaStream_t st);
 
 // ---- stripe accumulate (uf_stripe.cu) ----
 // In the FP32 min kernel, stripes s with (s % 8) >= 8 - FP32_ABS_ROWS hold
@@ -56,18 +73,18 @@ cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
 constexpr int FP32_ABS_ROWS = 3;
 
 struct StripeArgs {
-  const void *X;        // [rows][pitch] float or double
+  const void *X;        // [rows][pitch] float or double, one segment per table
   const double *len;    // per-row branch length (generalized only), [rows]
   int rows;             // branches in this launch
-  int64_t pitch;        // elements per row
-  int n;                // samples
-  int s_lo, s_hi;       // stored stripes s in [s_lo, s_hi]
-  int m_lo, m_hi;       // stripe tiles m in [m_lo, m_hi] (tile m: s in [m*tile_s, +tile_s))
-  int n_ktiles;         // sample tiles: ceil(n / tile_k)
+  int64_t pitch;        // elements per row (all segments)
   int chunk;            // rows per work unit (stripe_chunk_rows())
-  unsigned long long *M;   // [(s_hi - s_lo + 1) * n] fixed point: M / A (ACC_MIN) or den (ACC_GEN)
+  const TabDesc *tabs;  // device array of n_tabs tables
+  int n_tabs;
+  int n_tiles;          // tiles of all tables (per row chunk)
+  int n_cols;           // combined samples (diagonal length)
+  unsigned long long *M;   // fixed point: M / A (ACC_MIN) or den (ACC_GEN), per table at m_off
   unsigned long long *M2;  // Q (ACC_GEN), else null
-  unsigned long long *Dg;  // [n] fixed-point diagonal sums (ACC_MIN, launch_diag), else null
+  unsigned long long *Dg;  // [n_cols] fixed-point diagonal (ACC_MIN, launch_diag), else null
   double alpha;         // generalized exponent
   double scale;         // 2^F: fixed-point scale of every accumulator
   int *counter;         // one int of device memory: the work-unit counter (reset per launch)
@@ -79,7 +96,7 @@ int stripe_chunk_rows();
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st);
 // D[k] += sum of the launch's rows at column k (ACC_MIN only), with the
 // stripe kernel's operation order; scratch holds diag_scratch_bytes()
-size_t diag_scratch_bytes(bool fp32, int rows, int n);
+size_t diag_scratch_bytes(bool fp32, int rows, int n_cols);
 cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStream_t st);
 
 // ---- finalize (uf_finalize.cu) ----
@@ -89,7 +106,7 @@ struct FinalArgs {
   int64_t s0, s1;       // stripes [s0, s1)
   int full;             // 1: condensed output, 0: stripe-major
   int mixed_forms;      // 1: the FP32 min kernel's abs-form stripes are present
-  const unsigned long long *M, *M2, *Dg;  // fixed-point accumulators
+  const unsigned long long *M, *M2, *Dg;  // fixed-point accumulators of this table
   double inv_scale;     // 2^-F
   void *out;
   int out_fp32;
@@ -97,14 +114,23 @@ struct FinalArgs {
 cudaError_t launch_finalize(const FinalArgs &a, cudaStream_t st);
 
 // ---- unweighted on tensor cores (uf_gram.cu) ----
-struct GramArgs {
+// One table of a batch: its samples occupy rows [row_base, row_base + n_pad)
+// of every presence plane; its gram matrix starts at gt_off.
+struct GramTab {
   int n, n_pad;         // samples, padded to the 256-sample tile
+  int row_base;         // first plane row
+  int off;              // first column on the combined sample axis
+  int64_t gt_off;       // first cell of its gram matrix (n_pad x n_pad)
+};
+struct GramArgs {
   int k_len;            // branches of this block, rounded up to 64
   int kc;               // branches per work unit (multiple of 64)
-  int n_tiles;          // upper-triangle tiles (gram_tiles)
+  int n_tiles;          // tiles of all tables
   int n_units;          // set by launch_gram
-  const int32_t *tile_bi, *tile_bj;
-  unsigned long long *Gt;  // [n_pad][n_pad] fixed point; cell (i, j), i <= j, at j * n_pad + i
+  int npad_tot;         // plane rows (sum of n_pad)
+  const int32_t *tile_tab, *tile_bi, *tile_bj;
+  const GramTab *tabs;
+  unsigned long long *Gt;  // fixed point; cell (i, j), i <= j, of table t at gt_off + j * n_pad + i
   double scale;         // 2^F
   int *err;             // set to 1 when a bounded wait gave up
 };
@@ -112,16 +138,17 @@ struct GramFinalArgs {
   int n, n_pad;
   int64_t s0, s1;
   int full;
-  const unsigned long long *Gt;
+  const unsigned long long *Gt;  // this table's gram matrix
   void *out;
   int out_fp32;
 };
-// padded sizes of the presence planes for n samples and a block of `rows` branches
-void gram_geometry(int n, int rows, int *n_pad, int64_t *K_pad);
-// tile list: first half row-block indices, second half column-block indices
-std::vector<int32_t> gram_tiles(int n_pad);
+int gram_pad(int n);                      // n rounded up to the tile
+int64_t gram_kpad(int rows);              // branches rounded up to the stage
+// upper-triangle tiles of one table: (bi, bj) pairs appended to bi / bj
+void gram_tiles(int n_pad, std::vector<int32_t> *bi, std::vector<int32_t> *bj);
 cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, const double *counts,
-                             const double *length, int n, int n_pad, int64_t K_pad, void *Pl, cudaStream_t st);
+                             int64_t ld, const double *length, const GramTab *tabs, int n_tabs,
+                             int npad_tot, int64_t K_pad, void *Pl, cudaStream_t st);
 cudaError_t launch_gram(const GramArgs &a, void *Pl, int64_t K_pad, cudaStream_t st);
 cudaError_t launch_finalize_gram(const GramFinalArgs &a, cudaStream_t st);
 

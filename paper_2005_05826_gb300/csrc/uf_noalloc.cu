@@ -166,8 +166,9 @@ extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
     p[16] = acc == ACC_MIN ? (void *)c.take<unsigned char>(diag_scratch_bytes(fp32, std::max(rows, 1), n))
                            : nullptr;                                        // diagonal partials
     p[17] = c.take<int>(1);                                                  // work-unit counter
+    p[18] = c.take<TabDesc>(1);                                              // the table's description
   };
-  void *p[18];
+  void *p[19];
   Carve dry{nullptr};
   layout(dry, p);
   if (dry.used > UF_NOALLOC_SCRATCH_BYTES) {
@@ -215,6 +216,18 @@ extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
   UF_TRY(h2d(p[8], xv.col_val, xv.nnz * 8));
   UF_TRY(h2d(p[9], xv.total, (size_t)n * 8));
   UF_TRY(h2d(p[10], xv.inv_total_f, (size_t)n * 4));
+  TabDesc tab{};
+  tab.n = n;
+  tab.off = 0;
+  tab.s_lo = 0;
+  tab.s_hi = (int)(S - 1);
+  tab.m_lo = 0;
+  tab.m_hi = m_hi;
+  tab.n_ktiles = (n + tile_k - 1) / tile_k;
+  tab.tile0 = 0;
+  tab.x_col = 0;
+  tab.m_off = 0;
+  UF_TRY(h2d(p[18], &tab, sizeof tab));
   // accumulators start at zero; the rest of the area is overwritten before use
   UF_TRY(cudaMemsetAsync(p[13], 0, (size_t)S * n * 8, st));
   if (p[14]) UF_TRY(cudaMemsetAsync(p[14], 0, (size_t)S * n * 8, st));
@@ -225,24 +238,23 @@ extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
   if (rows > 0) {
     UF_TRY(launch_tip_counts(d_lists + launches[0].first, launches[0].second, d_slot,
                              (const int32_t *)p[1], (const int64_t *)p[6], (const int32_t *)p[7],
-                             (const double *)p[8], d_counts, n, st));
+                             (const double *)p[8], d_counts, n, n, st));
     for (size_t l = 1; l < launches.size(); l++)
       UF_TRY(launch_node_counts(d_lists + launches[l].first, launches[l].second,
                                 (const int32_t *)p[2], (const int32_t *)p[3], d_slot, d_counts, n, st));
-    UF_TRY(launch_emb_rows(kind, fp32, 0, rows, d_slot, d_counts, (const double *)p[0],
-                           (const double *)p[9], (const float *)p[10], p[12], pitch, n, st));
+    UF_TRY(launch_emb_rows(kind, fp32, 0, rows, d_slot, d_counts, n, (const double *)p[0],
+                           (const double *)p[9], (const float *)p[10], p[12], pitch,
+                           (const TabDesc *)p[18], 1, st));
     StripeArgs sa{};
     sa.X = p[12];
     sa.len = (const double *)p[0];
     sa.rows = rows;
     sa.pitch = pitch;
-    sa.n = n;
-    sa.s_lo = 0;
-    sa.s_hi = (int)(S - 1);
-    sa.m_lo = 0;
-    sa.m_hi = m_hi;
-    sa.n_ktiles = (n + tile_k - 1) / tile_k;
     sa.chunk = stripe_chunk_rows();
+    sa.tabs = (const TabDesc *)p[18];
+    sa.n_tabs = 1;
+    sa.n_tiles = tab.n_ktiles * (m_hi + 1);
+    sa.n_cols = n;
     sa.M = (unsigned long long *)p[13];
     sa.M2 = (unsigned long long *)p[14];
     sa.Dg = (unsigned long long *)p[15];

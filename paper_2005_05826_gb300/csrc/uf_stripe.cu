@@ -113,32 +113,54 @@ __device__ __forceinline__ long long to_fixed(float x, double scale) { return __
 __device__ __forceinline__ long long to_fixed(double x, double scale) { return __double2ll_rn(x * scale); }
 
 struct Unit {
-  int r0, r1, k0, s0;
+  int r0, r1;       // branch rows
+  int k0, s0;       // tile origin: first sample, first stripe
+  int n, s_lo, s_hi;
+  int64_t x_col;    // the table's first column in an embedding row
+  int64_t m_off;    // the table's first accumulator cell
 };
 
+// Table holding tile number tt of the batch (tables in order of tile0).
+__device__ __forceinline__ int table_of_tile(const TabDesc *tabs, int n_tabs, int tt) {
+  int lo = 0, hi = n_tabs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tabs[mid].tile0 <= tt) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Next work unit for this CTA: chunk-major over (row chunk, tile of any table).
 __device__ __forceinline__ bool next_unit(const StripeArgs &a, int tile_s, int tile_k, int *s_unit,
                                           Unit *u) {
   __syncthreads();  // everyone is done with the previous unit's shared data
   if (threadIdx.x == 0) *s_unit = atomicAdd(a.counter, 1);
   __syncthreads();
   const int id = *s_unit;
-  const int n_stiles = a.m_hi - a.m_lo + 1;
-  const int n_tiles = a.n_ktiles * n_stiles;
   const int n_chunks = (a.rows + a.chunk - 1) / a.chunk;
-  if (id >= n_chunks * n_tiles) return false;
-  const int c = id / n_tiles, t = id - c * n_tiles;
-  const int kt = t % a.n_ktiles, st = t / a.n_ktiles;
+  if (id >= n_chunks * a.n_tiles) return false;
+  const int c = id / a.n_tiles, tt = id - c * a.n_tiles;
+  const TabDesc &tb = a.tabs[a.n_tabs == 1 ? 0 : table_of_tile(a.tabs, a.n_tabs, tt)];
+  const int t = tt - tb.tile0;
+  const int kt = t % tb.n_ktiles, st = t / tb.n_ktiles;
   u->r0 = c * a.chunk;
   u->r1 = min(a.rows, u->r0 + a.chunk);
   u->k0 = kt * tile_k;
-  u->s0 = (a.m_lo + st) * tile_s;
+  u->s0 = (tb.m_lo + st) * tile_s;
+  u->n = tb.n;
+  u->s_lo = tb.s_lo;
+  u->s_hi = tb.s_hi;
+  u->x_col = tb.x_col;
+  u->m_off = tb.m_off;
   return true;
 }
 
-// Stage loader: RB branch rows [e0, e0 + RB) of the u and partner windows.
+// Stage loader: RB branch rows [e0, e0 + RB) of the u window (columns from
+// ucol) and the partner window (columns from vcol).
 template <typename T, int RD, int RK, int NACC, bool LEN>
-__device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0, int e_end, int k0,
-                                           int s0) {
+__device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0, int e_end, int64_t ucol,
+                                           int64_t vcol) {
   using G = Geo<T, RD, RK, NACC>;
   const T *X = (const T *)a.X;
   for (int c = threadIdx.x; c < RB * G::CH; c += NT) {
@@ -149,11 +171,11 @@ __device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0
     int64_t src;
     if (q < G::UCH) {
       dst = row + swz<T>(q * G::VEC);
-      src = (int64_t)k0 + q * G::VEC;
+      src = ucol + q * G::VEC;
     } else {
       const int qv = q - G::UCH;
       dst = row + G::UW + swz<T>(qv * G::VEC);
-      src = (int64_t)k0 + s0 + qv * G::VEC;
+      src = vcol + qv * G::VEC;
     }
     if (e < e_end) {
       cp_async16(dst, X + (int64_t)e * a.pitch + src);
@@ -171,16 +193,16 @@ __device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0
 // Add one thread's second-level cells (fixed point) into the accumulator.
 template <typename T, int RD, int RK, typename Mid>
 __device__ __forceinline__ void commit_cells(unsigned long long *M, const Mid *mid, const StripeArgs &a,
-                                             int s_base, int k_base) {
+                                             const Unit &U, int s_base, int k_base) {
 #pragma unroll
   for (int i = 0; i < RD; i++) {
     const int s = s_base + i;
-    if (s < a.s_lo || s > a.s_hi) continue;
-    unsigned long long *row = M + (int64_t)(s - a.s_lo) * a.n;
+    if (s < U.s_lo || s > U.s_hi) continue;
+    unsigned long long *row = M + U.m_off + (int64_t)(s - U.s_lo) * U.n;
 #pragma unroll
     for (int j = 0; j < RK; j++) {
       const int k = k_base + j;
-      if (k < a.n) {
+      if (k < U.n) {
         const Mid m = mid[(i * RK + j) * NT + threadIdx.x];
         long long q;
         if constexpr (sizeof(Mid) == 4) q = to_fixed((float)m, a.scale);
@@ -211,7 +233,8 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
     const int nst = (U.r1 - U.r0 + RB - 1) / RB;
 #pragma unroll
     for (int p = 0; p < NSTAGE - 1; p++) {
-      if (p < nst) load_stage<T, RD, RK, 1, false>(stg + p * G::STAGE, a, U.r0 + p * RB, U.r1, U.k0, U.s0);
+      if (p < nst) load_stage<T, RD, RK, 1, false>(stg + p * G::STAGE, a, U.r0 + p * RB, U.r1, U.x_col + U.k0,
+                                        U.x_col + U.k0 + U.s0);
       cp_async_commit();
     }
     T acc[RD][RK];
@@ -226,7 +249,8 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
       {
         const int nx = it + NSTAGE - 1;
         if (nx < nst)
-          load_stage<T, RD, RK, 1, false>(stg + (nx % NSTAGE) * G::STAGE, a, U.r0 + nx * RB, U.r1, U.k0, U.s0);
+          load_stage<T, RD, RK, 1, false>(stg + (nx % NSTAGE) * G::STAGE, a, U.r0 + nx * RB, U.r1,
+                                          U.x_col + U.k0, U.x_col + U.k0 + U.s0);
         cp_async_commit();
       }
       const T *stage = stg + (it % NSTAGE) * G::STAGE;
@@ -283,7 +307,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
       }
     }
     cp_async_wait<0>();
-    commit_cells<T, RD, RK>(a.M, mid, a, U.s0 + RD * ts, U.k0 + RK * tk);
+    commit_cells<T, RD, RK>(a.M, mid, a, U, U.s0 + RD * ts, U.k0 + RK * tk);
   }
 }
 
@@ -308,7 +332,8 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
     const int nst = (U.r1 - U.r0 + RB - 1) / RB;
 #pragma unroll
     for (int p = 0; p < NSTAGE - 1; p++) {
-      if (p < nst) load_stage<T, RD, RK, 2, true>(stg + p * G::STAGE, a, U.r0 + p * RB, U.r1, U.k0, U.s0);
+      if (p < nst) load_stage<T, RD, RK, 2, true>(stg + p * G::STAGE, a, U.r0 + p * RB, U.r1, U.x_col + U.k0,
+                                       U.x_col + U.k0 + U.s0);
       cp_async_commit();
     }
     T accd[RD][RK], accq[RD][RK];
@@ -323,7 +348,8 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
       {
         const int nx = it + NSTAGE - 1;
         if (nx < nst)
-          load_stage<T, RD, RK, 2, true>(stg + (nx % NSTAGE) * G::STAGE, a, U.r0 + nx * RB, U.r1, U.k0, U.s0);
+          load_stage<T, RD, RK, 2, true>(stg + (nx % NSTAGE) * G::STAGE, a, U.r0 + nx * RB, U.r1,
+                                         U.x_col + U.k0, U.x_col + U.k0 + U.s0);
         cp_async_commit();
       }
       const T *stage = stg + (it % NSTAGE) * G::STAGE;
@@ -373,8 +399,8 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
       }
     }
     cp_async_wait<0>();
-    commit_cells<T, RD, RK>(a.M, midd, a, U.s0 + RD * ts, U.k0 + RK * tk);
-    commit_cells<T, RD, RK>(a.M2, midq, a, U.s0 + RD * ts, U.k0 + RK * tk);
+    commit_cells<T, RD, RK>(a.M, midd, a, U, U.s0 + RD * ts, U.k0 + RK * tk);
+    commit_cells<T, RD, RK>(a.M2, midq, a, U, U.s0 + RD * ts, U.k0 + RK * tk);
   }
 }
 
@@ -382,10 +408,23 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
 //      cell in min form runs when its two columns are equal ----
 // Phase 1: one partial per (B1-row sub-block, sample), summed in row order;
 // sub-blocks restart at every chunk boundary, as in the stripe kernels.
+// Table holding combined sample column k (tables in order of off).
+__device__ __forceinline__ int table_of_col(const TabDesc *tabs, int n_tabs, int k) {
+  int lo = 0, hi = n_tabs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tabs[mid].off <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <typename T>
 __global__ void k_diag_partial(const StripeArgs a, T *__restrict__ part) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.n) return;
+  const int kg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kg >= a.n_cols) return;
+  const TabDesc &tb = a.tabs[a.n_tabs == 1 ? 0 : table_of_col(a.tabs, a.n_tabs, kg)];
+  const int64_t k = tb.x_col + (kg - tb.off);  // the sample's column in its segment
   const int sb = blockIdx.y;
   const T *X = (const T *)a.X;
   const int per_chunk = (a.chunk + B1 - 1) / B1;
@@ -397,7 +436,7 @@ __global__ void k_diag_partial(const StripeArgs a, T *__restrict__ part) {
     const T x = X[(int64_t)e * a.pitch + k];
     acc += tmin<T>(x, x);
   }
-  part[(int64_t)sb * a.n + k] = acc;
+  part[(int64_t)sb * a.n_cols + kg] = acc;
 }
 
 // Phase 2: FP32 -- a chunk's sub-block partials summed in order in FP32, then
@@ -405,12 +444,12 @@ __global__ void k_diag_partial(const StripeArgs a, T *__restrict__ part) {
 template <typename T>
 __global__ void k_diag_reduce(const StripeArgs a, const T *__restrict__ part, int n_sb) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.n) return;
+  if (k >= a.n_cols) return;
   const int per_chunk = (a.chunk + B1 - 1) / B1;
   long long d = 0;
   float mid = 0.f;
   for (int sb = 0; sb < n_sb; sb++) {
-    const T p = part[(int64_t)sb * a.n + k];
+    const T p = part[(int64_t)sb * a.n_cols + k];
     if constexpr (sizeof(T) == 4) {
       mid += p;
       if ((sb + 1) % per_chunk == 0 || sb == n_sb - 1) {
@@ -441,7 +480,7 @@ cudaError_t prepare(K kernel, size_t smem, int *grid, int units) {
 
 int units_of(const StripeArgs &a) {
   const int n_chunks = (a.rows + a.chunk - 1) / a.chunk;
-  return n_chunks * a.n_ktiles * (a.m_hi - a.m_lo + 1);
+  return n_chunks * a.n_tiles;
 }
 
 template <typename T, int RD, int RK, int NMIN, int MINB>
@@ -480,7 +519,7 @@ void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k) {
 int stripe_chunk_rows() { return 2048; }
 
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st) {
-  if (a.rows <= 0 || a.m_hi < a.m_lo) return cudaSuccess;
+  if (a.rows <= 0 || a.n_tiles <= 0) return cudaSuccess;
   if (acc == ACC_MIN)
     return fp32 ? run_min<float, 8, 8, 8 - FP32_ABS_ROWS, 2>(a, st) : run_min<double, 8, 8, 8, 1>(a, st);
   const bool half = a.alpha == 0.5;
@@ -488,11 +527,11 @@ cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStrea
   return half ? run_gen<double, 4, 8, 0, 1>(a, st) : run_gen<double, 4, 8, 1, 1>(a, st);
 }
 
-size_t diag_scratch_bytes(bool fp32, int rows, int n) {
+size_t diag_scratch_bytes(bool fp32, int rows, int n_cols) {
   const int chunk = stripe_chunk_rows();
   const int64_t n_chunks = (rows + chunk - 1) / chunk;
   const int64_t n_sb = n_chunks * ((chunk + B1 - 1) / B1);
-  return (size_t)std::max<int64_t>(n_sb, 1) * n * (fp32 ? 4 : 8);
+  return (size_t)std::max<int64_t>(n_sb, 1) * n_cols * (fp32 ? 4 : 8);
 }
 
 cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStream_t st) {
@@ -500,8 +539,8 @@ cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStrea
   const int per_chunk = (a.chunk + B1 - 1) / B1;
   const int n_chunks = (a.rows + a.chunk - 1) / a.chunk;
   const int n_sb = (n_chunks - 1) * per_chunk + ((a.rows - (n_chunks - 1) * a.chunk) + B1 - 1) / B1;
-  dim3 g1((a.n + 127) / 128, n_sb);
-  const int g2 = (a.n + 127) / 128;
+  dim3 g1((a.n_cols + 127) / 128, n_sb);
+  const int g2 = (a.n_cols + 127) / 128;
   if (fp32) {
     k_diag_partial<float><<<g1, 128, 0, st>>>(a, (float *)scratch);
     k_diag_reduce<float><<<g2, 128, 0, st>>>(a, (const float *)scratch, n_sb);

@@ -125,16 +125,24 @@ def test_device_and_fp32_outputs():
     np.testing.assert_array_equal(f32, host.astype(np.float32))
 
 
-def test_batch_matches_single():
+@pytest.mark.parametrize("method", METHODS)
+def test_batch_of_uneven_tables(method):
+    # one embedding pass and one accumulate launch serve every table
     tree_s = yule_tree(500, seed=50)
-    tables_s = [table_iid(n, tree_s.n_tips, 0.05, seed=51 + n) for n in (7, 64, 130)]
+    sizes = (7, 1, 64, 130, 2, 257, 33)
+    tables_s = [table_iid(n, tree_s.n_tips, 0.05, seed=51 + n) for n in sizes]
     tree = uf.Tree(tree_s.parent, tree_s.length)
     tables = [uf.Table(t.indptr, t.indices, t.data, tree) for t in tables_s]
+    a = alpha_for(method)
     for precision in PRECISIONS:
-        outs, reps = uf.uf_compute_batch(tree, tables, "unweighted", 1.0, precision)
-        for t_s, t, o in zip(tables_s, tables, outs):
-            exp = oracle.condensed(tree_s, t_s, "unweighted", 1.0)
-            assert_close(o, exp, "unweighted", precision, "batch")
+        outs, reps = uf.uf_compute_batch(tree, tables, method, a, precision)
+        for t_s, o, rep in zip(tables_s, outs, reps):
+            if t_s.n_samples < 2:
+                assert o.size == 0
+                continue
+            exp = oracle.condensed(tree_s, t_s, method, a)
+            assert_close(o, exp, method, precision, f"batch n={t_s.n_samples}")
+            assert rep.updates == t_s.n_samples * (t_s.n_samples - 1) // 2 * (tree_s.n_nodes - 1)
 
 
 @pytest.mark.parametrize("method", METHODS)

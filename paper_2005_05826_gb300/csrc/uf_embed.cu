@@ -68,9 +68,12 @@ template <>
 __device__ __forceinline__ float emb_value<float, EMB_PRESENCE>(double c, double l, double, float) {
   return c > 0.0 ? (float)l : 0.0f;
 }
+// FP32 proportions carry a 1e-30 offset: it leaves every nonzero FP32
+// proportion unchanged (all are far above 1e-30 * 2^24) and keeps the
+// generalized kernel's s = u + v away from 0 without a guard per update.
 template <>
 __device__ __forceinline__ float emb_value<float, EMB_PROP>(double c, double, double, float it) {
-  return (float)c * it;
+  return (float)c * it + 1e-30f;
 }
 
 // Table whose row segment holds column j (segments are contiguous, in order).

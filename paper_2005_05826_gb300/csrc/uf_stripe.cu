@@ -96,17 +96,28 @@ __device__ __forceinline__ float tmin<float>(float a, float b) { return fminf(a,
 template <>
 __device__ __forceinline__ double tmin<double>(double a, double b) { return fmin(a, b); }
 
-// s^(alpha - 1) for s > 0 (s == 0 terms are zeroed by the caller)
+// FP64 s^(alpha - 1) for s > 0 (s == 0 terms are zeroed by the caller)
 template <typename T, int MODE>
 __device__ __forceinline__ T gen_pow(T s, T am1);
-template <>
-__device__ __forceinline__ float gen_pow<float, 0>(float s, float) { return rsqrtf(fmaxf(s, 1e-30f)); }
-template <>
-__device__ __forceinline__ float gen_pow<float, 1>(float s, float am1) { return __powf(fmaxf(s, 1e-30f), am1); }
 template <>
 __device__ __forceinline__ double gen_pow<double, 0>(double s, double) { return rsqrt(fmax(s, 1e-300)); }
 template <>
 __device__ __forceinline__ double gen_pow<double, 1>(double s, double am1) { return pow(fmax(s, 1e-300), am1); }
+
+// s^(alpha - 1) on the SFU for FP32 s >= 1e-30 (never denormal):
+// MODE 0 (alpha = 1/2) one reciprocal square root; MODE 1 exp2((alpha - 1) log2 s).
+template <int MODE>
+__device__ __forceinline__ float sfu_pow(float s, float am1) {
+  float r;
+  if (MODE == 0) {
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+  } else {
+    float lg;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(s));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(lg * am1));
+  }
+  return r;
+}
 
 // fixed point: round x * 2^F to the nearest integer
 __device__ __forceinline__ long long to_fixed(float x, double scale) { return __float2ll_rn(x * (float)scale); }
@@ -180,8 +191,11 @@ __device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0
     if (e < e_end) {
       cp_async16(dst, X + (int64_t)e * a.pitch + src);
     } else {
+      // rows past the unit: zero, or for FP32 proportions the embedding's
+      // 1e-30 floor (their length is 0, so they add nothing either way)
+      const T pad = (LEN && sizeof(T) == 4) ? T(1e-30f) : T(0);
 #pragma unroll
-      for (int i = 0; i < G::VEC; i++) dst[i] = T(0);
+      for (int i = 0; i < G::VEC; i++) dst[i] = pad;
     }
   }
   if (LEN && threadIdx.x < RB) {
@@ -367,17 +381,49 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
         for (int q = 0; q < G::NV; q++)
           *reinterpret_cast<uint4 *>(&v[q * G::VEC]) =
               *reinterpret_cast<const uint4 *>(vrow + swz<T>(w0 + q * G::VEC));
+        if constexpr (F32) {
+          // pairs of cells per f32x2 instruction; the embedding keeps every
+          // proportion >= 1e-30 (an offset no nonzero FP32 proportion can see),
+          // so s > 0: for alpha = 1/2 an absent pair adds l sqrt(2e-30) to den
+          // and exactly half of that to Q (net 0 to num), for other alpha its
+          // term is zeroed explicitly
+          const float2 l2 = make_float2(l, l);
 #pragma unroll
-        for (int i = 0; i < RD; i++)
+          for (int i = 0; i < RD; i++)
 #pragma unroll
-          for (int j = 0; j < RK; j++) {
-            const T uu = u[j], vv = v[i + j + 1];
-            const T s = uu + vv;
-            T w = l * gen_pow<T, MODE>(s, am1);
-            if (MODE == 1) w = s > T(0) ? w : T(0);
-            accd[i][j] = fma(s, w, accd[i][j]);
-            accq[i][j] = fma(tmin<T>(uu, vv), w, accq[i][j]);
-          }
+            for (int j = 0; j < RK; j += 2) {
+              const float2 uu = make_float2(u[j], u[j + 1]);
+              const float2 vv = make_float2(v[i + j + 1], v[i + j + 2]);
+              const float2 s2 = __fadd2_rn(uu, vv);
+              float2 r2 = make_float2(sfu_pow<MODE>(s2.x, am1), sfu_pow<MODE>(s2.y, am1));
+              if (MODE == 1) {  // s^(alpha-1) of an absent pair (s = 2e-30) must not count
+                r2.x = s2.x > 4e-30f ? r2.x : 0.f;
+                r2.y = s2.y > 4e-30f ? r2.y : 0.f;
+              }
+              const float2 w2 = __fmul2_rn(l2, r2);
+              const float2 m2 = make_float2(fminf(uu.x, vv.x), fminf(uu.y, vv.y));
+              float2 d2 = make_float2(accd[i][j], accd[i][j + 1]);
+              float2 q2 = make_float2(accq[i][j], accq[i][j + 1]);
+              d2 = __ffma2_rn(s2, w2, d2);
+              q2 = __ffma2_rn(m2, w2, q2);
+              accd[i][j] = d2.x;
+              accd[i][j + 1] = d2.y;
+              accq[i][j] = q2.x;
+              accq[i][j + 1] = q2.y;
+            }
+        } else {
+#pragma unroll
+          for (int i = 0; i < RD; i++)
+#pragma unroll
+            for (int j = 0; j < RK; j++) {
+              const T uu = u[j], vv = v[i + j + 1];
+              const T s = uu + vv;
+              T w = l * gen_pow<T, MODE>(s, am1);
+              if (MODE == 1) w = s > T(0) ? w : T(0);
+              accd[i][j] = fma(s, w, accd[i][j]);
+              accq[i][j] = fma(tmin<T>(uu, vv), w, accq[i][j]);
+            }
+        }
       }
       in_sub += RB;
       if (in_sub == B1 || it == nst - 1) {

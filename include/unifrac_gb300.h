@@ -100,6 +100,9 @@ typedef struct {
     double t_diag_ms;      /* diagonal accumulate launches */
     double t_finalize_ms;  /* finalize */
     int64_t acc_launches;  /* accumulate launches timed in t_accumulate_ms */
+    int64_t chunk_rows;    /* branches per accumulate work unit (autotuned) */
+    int32_t graph;         /* 1: the launch sequence ran as one CUDA graph */
+    int32_t reserved2;
 } uf_report;
 
 /*
@@ -110,6 +113,14 @@ typedef struct {
  *                    fill the t_*_ms fields of uf_report (adds a stream sync)
  *   "tensor_path"    1 (default): UF_UNWEIGHTED with UF_MIXED runs on the
  *                    tcgen05 tensor cores; 0: on the CUDA-core stripe kernels
+ *   "graph"          1 (default): a call's branch-block launch sequence is
+ *                    captured into a CUDA graph and launched as one graph
+ *                    (not when "kernel_timing" is 1); 0: plain launches
+ *   "autotune"       1 (default): the first call for an (accumulator,
+ *                    precision, size) class times the accumulate kernel on
+ *                    its first branch block with 1,024 / 2,048 / 4,096 / 8,192
+ *                    branches per work unit and keeps the fastest for the
+ *                    process; 0: 2,048; 2: forget the kept choices, then 1
  * uf_set_option returns UF_EINVAL for an unknown name or a bad value;
  * uf_get_option returns -1 for an unknown name.
  */

@@ -42,10 +42,11 @@ class Report(ctypes.Structure):
                 ("h2d_bytes", ctypes.c_double), ("d2h_bytes", ctypes.c_double),
                 ("t_embed_ms", ctypes.c_double), ("t_accumulate_ms", ctypes.c_double),
                 ("t_diag_ms", ctypes.c_double), ("t_finalize_ms", ctypes.c_double),
-                ("acc_launches", ctypes.c_int64)]
+                ("acc_launches", ctypes.c_int64), ("chunk_rows", ctypes.c_int64),
+                ("graph", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        return {name: getattr(self, name) for name, _ in self._fields_ if not name.startswith("reserved")}
 
 
 class UFError(RuntimeError):

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -35,6 +36,8 @@ thread_local std::string g_err;
 std::atomic<int64_t> g_branch_block{0};
 std::atomic<int64_t> g_kernel_timing{0};
 std::atomic<int64_t> g_tensor_path{1};
+std::atomic<int64_t> g_graph{1};
+std::atomic<int64_t> g_autotune{1};
 
 uf_status fail(uf_status st, const char *fmt, ...) {
   char buf[512];
@@ -403,6 +406,94 @@ double accum_scale(const uf_tree *tree, const uf_table *table, int kind) {
 
 namespace {
 
+// Private stream per device on which a call's launch sequence is captured.
+cudaStream_t capture_stream(int device) {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = streams.find(device);
+  if (it != streams.end()) return it->second;
+  cudaStream_t s = nullptr;
+  ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
+  return streams[device] = s;
+}
+
+// Records the branch-block launch sequence of a call into a CUDA graph (on a
+// private stream) and launches that graph on the caller's stream; when off,
+// launches go to the caller's stream directly.
+struct Capture {
+  bool on;
+  cudaStream_t user, cap = nullptr;
+  bool open = false;
+  Capture(bool enable, cudaStream_t st, int device) : on(enable), user(st) {
+    if (!on) return;
+    cap = capture_stream(device);
+    ck(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+    open = true;
+  }
+  cudaStream_t stream() const { return on ? cap : user; }
+  // end the capture and launch the graph on the caller's stream
+  void launch() {
+    if (!on) return;
+    cudaGraph_t g = nullptr;
+    open = false;
+    ck(cudaStreamEndCapture(cap, &g), "cudaStreamEndCapture");
+    cudaGraphExec_t e = nullptr;
+    cudaError_t err = cudaGraphInstantiate(&e, g, 0);
+    if (err == cudaSuccess) err = cudaGraphLaunch(e, user);
+    if (e) cudaGraphExecDestroy(e);  // freed once the launch completes
+    cudaGraphDestroy(g);
+    ck(err, "graph launch");
+  }
+  ~Capture() {
+    if (open) {  // an error escaped mid-capture: drop the partial graph
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(cap, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+  }
+};
+
+// Autotuned rows per work unit, by (accumulator, precision, size bucket).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tuned_chunk;
+
+std::tuple<int, int, int, int> tune_key(int acc, bool fp32, int64_t n_tiles, int64_t rows) {
+  auto lg = [](int64_t x) { return (int)std::floor(std::log2((double)std::max<int64_t>(x, 1))); };
+  return {acc, fp32 ? 1 : 0, lg(n_tiles), lg(rows)};
+}
+
+// Time the accumulate launch of the first block with each candidate chunk
+// size and keep the fastest (the accumulators are cleared afterwards).
+int tune_chunk(int acc, bool fp32, StripeArgs sa, size_t cells, cudaStream_t st) {
+  const int cand[4] = {1024, 2048, 4096, 8192};
+  cudaEvent_t e0, e1;
+  ck(cudaEventCreate(&e0), "cudaEventCreate");
+  ck(cudaEventCreate(&e1), "cudaEventCreate");
+  int best = stripe_chunk_rows();
+  float best_ms = 1e30f;
+  for (int c : cand) {
+    if (c > 2 * std::max(sa.rows, 1024)) break;
+    sa.chunk = c;
+    ck(cudaEventRecord(e0, st), "cudaEventRecord");
+    ck(launch_stripe_acc(acc, fp32, sa, st), "autotune");
+    ck(cudaEventRecord(e1, st), "cudaEventRecord");
+    ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ck(cudaMemsetAsync(sa.M, 0, cells * 8, st), "memset");
+  if (sa.M2) ck(cudaMemsetAsync(sa.M2, 0, cells * 8, st), "memset");
+  return best;
+}
+
 // One table of a compute call: its stripe range and output.
 struct TableJob {
   uf_table *table;
@@ -586,12 +677,14 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
   ck(cudaMemsetAsync(err.p, 0, sizeof(int), st), "memset");
   Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
+  Capture cap(g_graph.load() != 0 && !timer.on, st, device);
+  const cudaStream_t ls = cap.stream();
   for (size_t b = 0; b < in.P->b0.size(); b++) {
     const int64_t b0 = in.P->b0[b], b1 = in.P->b1[b];
     timer.begin(0);
-    enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, st, &kernels);
+    enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, ls, &kernels);
     ck(launch_gram_prep(b0, (int)(b1 - b0), in.pd->slot_of_node, counts.as<double>(), n_cols, in.td->length,
-                        d_tabs.as<GramTab>(), (int)nt, npad_tot, K_pad, Pl.p, st),
+                        d_tabs.as<GramTab>(), (int)nt, npad_tot, K_pad, Pl.p, ls),
        "presence planes");
     kernels++;
     timer.end();
@@ -608,7 +701,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
     ga.scale = scale;
     ga.err = err.as<int>();
     timer.begin(1);
-    ck(launch_gram(ga, Pl.p, K_pad, st), "tensor-core gram");
+    ck(launch_gram(ga, Pl.p, K_pad, ls), "tensor-core gram");
     timer.end();
     kernels++;
     acc_launches++;
@@ -625,10 +718,11 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
     fa.Gt = Gt.as<unsigned long long>() + gt[t].gt_off;
     fa.out = o.dev[t];
     fa.out_fp32 = J.out_fp32;
-    ck(launch_finalize_gram(fa, st), "finalize");
+    ck(launch_finalize_gram(fa, ls), "finalize");
     kernels++;
   }
   timer.end();
+  cap.launch();
   int h_err = 0;
   ck(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
   if (!J.out_is_device)
@@ -647,6 +741,11 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
   timer.collect(ms);
   fill_reports(tree, J, o, ms, kernels, acc_launches, 1, rows, (int64_t)in.P->b0.size(), exec_flops, 256, 128,
                std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+  for (const TableJob &t : J.tabs)
+    if (t.rep) {
+      t.rep->chunk_rows = 4096;
+      t.rep->graph = cap.on ? 1 : 0;
+    }
   return UF_OK;
 }
 
@@ -717,13 +816,26 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   ck(cudaMemsetAsync(M.p, 0, (size_t)cells * 8, st), "memset");
   Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
+  // chunk size: tuned once per (accumulator, precision, size bucket)
+  const auto key = tune_key(acc, fp32, n_tiles, rows);
+  int chunk = stripe_chunk_rows();
+  bool tune = false;
+  if (g_autotune.load()) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tuned_chunk.find(key);
+    if (it != g_tuned_chunk.end()) chunk = it->second;
+    else tune = true;
+  }
+  // the launch sequence goes into a CUDA graph unless it is timed per phase
+  Capture cap(g_graph.load() != 0 && !timer.on && !tune, st, device);
+  const cudaStream_t ls = cap.stream();
   for (size_t b = 0; b < in.P->b0.size(); b++) {
     const int64_t b0 = in.P->b0[b], b1 = in.P->b1[b];
     timer.begin(0);
-    enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, st, &kernels);
+    enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, ls, &kernels);
     ck(launch_emb_rows(kind, fp32, b0, (int)(b1 - b0), in.pd->slot_of_node, counts.as<double>(), n_cols,
                        in.td->length, total.as<double>(), inv_total.as<float>(), X.p, pitch,
-                       d_tabs.as<TabDesc>(), (int)nt, st),
+                       d_tabs.as<TabDesc>(), (int)nt, ls),
        "embedding rows");
     kernels++;
     timer.end();
@@ -732,7 +844,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sa.len = in.td->length + b0;
     sa.rows = (int)(b1 - b0);
     sa.pitch = pitch;
-    sa.chunk = stripe_chunk_rows();
+    sa.chunk = chunk;
     sa.tabs = d_tabs.as<TabDesc>();
     sa.n_tabs = (int)nt;
     sa.n_tiles = n_tiles;
@@ -743,15 +855,20 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sa.alpha = J.alpha;
     sa.scale = scale;
     sa.counter = counter.as<int>();
+    if (tune && b == 0) {
+      chunk = sa.chunk = tune_chunk(acc, fp32, sa, (size_t)cells, ls);
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      g_tuned_chunk[key] = chunk;
+    }
     timer.begin(1);
-    ck(launch_stripe_acc(acc, fp32, sa, st), "stripe accumulate");
+    ck(launch_stripe_acc(acc, fp32, sa, ls), "stripe accumulate");
     timer.end();
     kernels++;
     acc_launches++;
     exec_flops += 2.0 * (double)n_tiles * tile_s * tile_k * (double)(b1 - b0);
     if (acc == ACC_MIN) {
       timer.begin(2);
-      ck(launch_diag(fp32, sa, diag_tmp.p, st), "diagonal accumulate");
+      ck(launch_diag(fp32, sa, diag_tmp.p, ls), "diagonal accumulate");
       timer.end();
       kernels += 2;
     }
@@ -771,10 +888,11 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     fa.inv_scale = 1.0 / scale;
     fa.out = o.dev[t];
     fa.out_fp32 = J.out_fp32;
-    ck(launch_finalize(fa, st), "finalize");
+    ck(launch_finalize(fa, ls), "finalize");
     kernels++;
   }
   timer.end();
+  cap.launch();
   if (!J.out_is_device)
     for (size_t t = 0; t < nt; t++)
       ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
@@ -796,6 +914,11 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   timer.collect(ms);
   fill_reports(tree, J, o, ms, kernels, acc_launches, 0, rows, (int64_t)in.P->b0.size(), exec_flops, tile_s,
                tile_k, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+  for (const TableJob &t : J.tabs)
+    if (t.rep) {
+      t.rep->chunk_rows = chunk;
+      t.rep->graph = cap.on ? 1 : 0;
+    }
   return UF_OK;
 }
 
@@ -854,6 +977,21 @@ uf_status uf_set_option(const char *name, int64_t value) {
     g_tensor_path = value;
     return UF_OK;
   }
+  if (!strcmp(name, "graph")) {
+    if (value != 0 && value != 1) return fail(UF_EINVAL, "graph must be 0 or 1");
+    g_graph = value;
+    return UF_OK;
+  }
+  if (!strcmp(name, "autotune")) {
+    if (value < 0 || value > 2) return fail(UF_EINVAL, "autotune must be 0, 1 or 2");
+    if (value == 2) {  // forget the tuned choices
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      g_tuned_chunk.clear();
+      value = 1;
+    }
+    g_autotune = value;
+    return UF_OK;
+  }
   return fail(UF_EINVAL, "unknown option '%s'", name);
 }
 
@@ -862,6 +1000,8 @@ int64_t uf_get_option(const char *name) {
   if (!strcmp(name, "branch_block")) return g_branch_block.load();
   if (!strcmp(name, "kernel_timing")) return g_kernel_timing.load();
   if (!strcmp(name, "tensor_path")) return g_tensor_path.load();
+  if (!strcmp(name, "graph")) return g_graph.load();
+  if (!strcmp(name, "autotune")) return g_autotune.load();
   return -1;
 }
 

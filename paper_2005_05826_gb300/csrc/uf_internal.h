@@ -77,7 +77,7 @@ struct StripeArgs {
   const double *len;    // per-row branch length (generalized only), [rows]
   int rows;             // branches in this launch
   int64_t pitch;        // elements per row (all segments)
-  int chunk;            // rows per work unit (stripe_chunk_rows())
+  int chunk;            // rows per work unit: a multiple of 64, >= 1,024
   const TabDesc *tabs;  // device array of n_tabs tables
   int n_tabs;
   int n_tiles;          // tiles of all tables (per row chunk)
@@ -91,11 +91,12 @@ struct StripeArgs {
 };
 // stripes and samples per CTA tile of the accumulate kernel
 void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k);
-// rows per work unit
+// default rows per work unit
 int stripe_chunk_rows();
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st);
 // D[k] += sum of the launch's rows at column k (ACC_MIN only), with the
-// stripe kernel's operation order; scratch holds diag_scratch_bytes()
+// stripe kernel's operation order; scratch holds diag_scratch_bytes() (valid
+// for every chunk size the StripeArgs may carry)
 size_t diag_scratch_bytes(bool fp32, int rows, int n_cols);
 cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStream_t st);
 

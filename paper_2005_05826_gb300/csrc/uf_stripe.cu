@@ -574,9 +574,8 @@ cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStrea
 }
 
 size_t diag_scratch_bytes(bool fp32, int rows, int n_cols) {
-  const int chunk = stripe_chunk_rows();
-  const int64_t n_chunks = (rows + chunk - 1) / chunk;
-  const int64_t n_sb = n_chunks * ((chunk + B1 - 1) / B1);
+  // sub-blocks of any chunk size >= 1,024 rows that is a multiple of B1
+  const int64_t n_sb = (rows + B1 - 1) / B1 + (rows + 1023) / 1024;
   return (size_t)std::max<int64_t>(n_sb, 1) * n_cols * (fp32 ? 4 : 8);
 }
 

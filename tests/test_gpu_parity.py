@@ -194,3 +194,44 @@ def test_tensor_path_large_n_pair_subset():
     got, rep = uf.uf_compute(tree, table, "unweighted", 1.0, "mixed")
     assert rep.path == 1
     assert_close(got[condensed_index(n, i, j)], exp, "unweighted", "mixed", "tensor path")
+
+
+def test_graph_and_plain_launches_agree():
+    tree_s = yule_tree(600, seed=90)
+    tables_s = [table_iid(n, tree_s.n_tips, 0.05, seed=91 + n) for n in (40, 150)]
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    tables = [uf.Table(t.indptr, t.indices, t.data, tree) for t in tables_s]
+    try:
+        for method in ["unweighted", "weighted_normalized", "generalized"]:
+            for precision in PRECISIONS:
+                res = {}
+                for graph in (0, 1):
+                    uf.uf_set_option("graph", graph)
+                    outs, reps = uf.uf_compute_batch(tree, tables, method, 0.5, precision)
+                    assert all(r.graph == graph for r in reps)
+                    res[graph] = outs
+                for a, b in zip(res[0], res[1]):
+                    np.testing.assert_array_equal(a, b)
+    finally:
+        uf.uf_set_option("graph", 1)
+
+
+def test_autotuned_chunk_sizes():
+    tree_s = yule_tree(3000, seed=92)
+    table_s = table_iid(200, tree_s.n_tips, 0.03, seed=93)
+    tree, table = handles(tree_s, table_s)
+    exp = oracle.condensed(tree_s, table_s, "weighted_normalized", 1.0)
+    try:
+        uf.uf_set_option("autotune", 2)  # forget earlier choices: this call tunes
+        got, rep = uf.uf_compute(tree, table, "weighted_normalized", 1.0, "mixed")
+        assert rep.chunk_rows in (1024, 2048, 4096, 8192)
+        assert_close(got, exp, "weighted_normalized", "mixed", "tuning call")
+        got2, rep2 = uf.uf_compute(tree, table, "weighted_normalized", 1.0, "mixed")
+        assert rep2.chunk_rows == rep.chunk_rows
+        np.testing.assert_array_equal(got, got2)
+        uf.uf_set_option("autotune", 0)
+        got3, rep3 = uf.uf_compute(tree, table, "weighted_normalized", 1.0, "mixed")
+        assert rep3.chunk_rows == 2048
+        assert_close(got3, exp, "weighted_normalized", "mixed", "fixed chunk")
+    finally:
+        uf.uf_set_option("autotune", 1)

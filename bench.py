@@ -205,7 +205,7 @@ def workload_config(args, tree_s, table_s, l2):
     return {"workload": args.workload, "tips": tree_s.n_tips, "nodes": tree_s.n_nodes,
             "samples": table_s.n_samples, "nnz": table_s.nnz,
             "methods": [m for m, _ in METHODS], "alpha": 0.5, "stripes": "all",
-            "l2": l2}
+            "sparse_rows_mode": getattr(args, "sparse", 1), "l2": l2}
 
 
 def max_errors(tree_s, table_s, outs, precision):
@@ -248,6 +248,7 @@ def run_batched(args, rank, world, local_rank):
     methods = [("unweighted", 1.0), ("weighted_normalized", 1.0)]
     stream = torch.cuda.current_stream(dev)
     uf.uf_set_option("kernel_timing", 0)
+    uf.uf_set_option("sparse", args.sparse)
 
     def step(reps=None):
         for m, a in methods:
@@ -349,6 +350,7 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     uf.uf_set_option("kernel_timing", 1)
+    uf.uf_set_option("sparse", args.sparse)
 
     def step(precision, reps=None):
         for (m, a), o in zip(METHODS, outs):
@@ -390,20 +392,26 @@ def run_ours(args, rank, world, local_rank):
 
     # per-kernel roofline of the accumulate launches (timed inside the steps)
     acc_ms = {}
+    sparse = {}
     for m, r in reps:
-        d = acc_ms.setdefault(m, [0.0, 0, 0, 0.0, 0])
+        d = acc_ms.setdefault(m, [0.0, 0, 0, 0.0, 0, 0])
         d[0] += r.t_accumulate_ms
         d[1] += r.acc_launches
         d[2] += 1
         d[3] += r.exec_flops
         d[4] = r.path
+        d[5] = r.dense_rows if r.path == 0 else branches
+        sp = sparse.setdefault(m, {"rows": r.sparse_rows, "dense_rows": d[5], "pairs_at_most": r.sparse_pairs,
+                                   "ms_per_call": 0.0})
+        sp["ms_per_call"] += r.t_sparse_ms / args.steps
     kern = {}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    for m, (ms, nl, ncalls, xflops, path) in acc_ms.items():
+    for m, (ms, nl, ncalls, xflops, path, drows) in acc_ms.items():
         per_launch_s = ms / 1e3 / max(nl, 1)
         # algorithmic cell updates of one launch: a call's launches share the
-        # call's pairs x branches (the duplicate half stripe excluded)
-        cells = npairs * branches * ncalls / max(nl, 1)
+        # call's pairs x the branches that run through the dense kernels (the
+        # duplicate half stripe excluded)
+        cells = npairs * drows * ncalls / max(nl, 1)
         if path == 1:
             # tensor cores: executed BF16 flops (three split GEMMs, whole
             # 128 x 256 tiles) against the measured dense BF16 peak
@@ -511,7 +519,7 @@ def run_ours(args, rank, world, local_rank):
         if r_wn is not None:
             # two FP64 instructions per update (DMNMX + DADD) at the nominal
             # 0.625 T FP64 instructions/s (1.25 TFLOP/s counting an FMA as two)
-            ach64 = npairs * branches / (r_wn.t_accumulate_ms / 1e3) / 1e12
+            ach64 = npairs * r_wn.dense_rows / (r_wn.t_accumulate_ms / 1e3) / 1e12
             fp64["roofline_weighted"] = {
                 "kernel": "k_stripe_min<double,8,8>", "bound": "alu", "achieved": ach64,
                 "peak": 0.3125, "unit": "Tupdates/s", "frac": ach64 / 0.3125,
@@ -536,8 +544,11 @@ def run_ours(args, rank, world, local_rank):
                      "FP32 accumulation), int64 fixed-point accumulators, FP64 division",
         "max_abs_err_vs_oracle": max((v["max_abs"] for v in mixed_err.values()), default=None),
         "max_err": mixed_err,
+        "updates_basis": "dense-equivalent: every sample pair x every non-root branch per method, "
+                         "including the zero terms that the sparse-row path skips",
         "roofline": rl,
         "kernels": kern,
+        "sparse_rows": sparse,
         "peak_source": peak_src,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -569,6 +580,8 @@ def main():
                     help="comma list of methods per step (default: all four)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--sparse", type=int, choices=[0, 1, 2], default=1,
+                    help="sparse-row path: 0 every branch dense, 1 cost model (default), 2 every branch that fits")
     args = ap.parse_args()
     if args.methods != "all":
         want = args.methods.split(",")

@@ -103,6 +103,10 @@ typedef struct {
     int64_t chunk_rows;    /* branches per accumulate work unit (autotuned) */
     int32_t graph;         /* 1: the launch sequence ran as one CUDA graph */
     int32_t reserved2;
+    int64_t dense_rows;    /* branches run through the dense stripe kernels */
+    int64_t sparse_rows;   /* branches scattered pair by pair (option "sparse") */
+    double sparse_pairs;   /* both-nonzero sample pairs of those branches, at most */
+    double t_sparse_ms;    /* device time of the sparse-row launches ("kernel_timing") */
 } uf_report;
 
 /*
@@ -121,6 +125,15 @@ typedef struct {
  *                    its first branch block with 1,024 / 2,048 / 4,096 / 8,192
  *                    branches per work unit and keeps the fastest for the
  *                    process; 0: 2,048; 2: forget the kept choices, then 1
+ *   "sparse"         1 (default): a branch whose subtree holds few count
+ *                    entries skips the dense stripe kernels; its terms are
+ *                    added pair by pair over the samples nonzero under it,
+ *                    when a cost model of the two kernels says that is
+ *                    faster; 0: every branch through the dense kernels;
+ *                    2: every branch that can be scattered is (subtree with
+ *                    at most 4,096 entries per table and contiguous tip
+ *                    numbers).  Applies to the CUDA-core stripe path; the
+ *                    results agree within the precision's tolerance.
  * uf_set_option returns UF_EINVAL for an unknown name or a bad value;
  * uf_get_option returns -1 for an unknown name.
  */

@@ -43,7 +43,9 @@ class Report(ctypes.Structure):
                 ("t_embed_ms", ctypes.c_double), ("t_accumulate_ms", ctypes.c_double),
                 ("t_diag_ms", ctypes.c_double), ("t_finalize_ms", ctypes.c_double),
                 ("acc_launches", ctypes.c_int64), ("chunk_rows", ctypes.c_int64),
-                ("graph", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("dense_rows", ctypes.c_int64), ("sparse_rows", ctypes.c_int64),
+                ("sparse_pairs", ctypes.c_double), ("t_sparse_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if not name.startswith("reserved")}

@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cuda_home = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
     os.makedirs(OUT_DIR, exist_ok=True)
     cu, cpp = sources()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "unifrac_gb300.h"))
     jobs = []
     objs = []

@@ -6,7 +6,7 @@
 // embedding row of a branch is then f(count[k] / total[k]) for every sample
 // k, written over a padded width so that the stripe kernel can read the
 // partner column k + d without a modulo.
-#include "uf_internal.h"
+#include "uf_device.cuh"
 
 namespace ufg {
 
@@ -45,37 +45,6 @@ __global__ void k_node_counts(const int32_t *__restrict__ nodes,
   counts[(int64_t)slot_of_node[v] * ld + k] = s;
 }
 
-template <typename T, int KIND>
-__device__ __forceinline__ T emb_value(double c, double l, double total, float inv_total_f);
-
-template <>
-__device__ __forceinline__ double emb_value<double, EMB_SCALED>(double c, double l, double t, float) {
-  return l * (c / t);
-}
-template <>
-__device__ __forceinline__ double emb_value<double, EMB_PRESENCE>(double c, double l, double, float) {
-  return c > 0.0 ? l : 0.0;
-}
-template <>
-__device__ __forceinline__ double emb_value<double, EMB_PROP>(double c, double, double t, float) {
-  return c / t;
-}
-template <>
-__device__ __forceinline__ float emb_value<float, EMB_SCALED>(double c, double l, double, float it) {
-  return (float)c * ((float)l * it);
-}
-template <>
-__device__ __forceinline__ float emb_value<float, EMB_PRESENCE>(double c, double l, double, float) {
-  return c > 0.0 ? (float)l : 0.0f;
-}
-// FP32 proportions carry a 1e-30 offset: it leaves every nonzero FP32
-// proportion unchanged (all are far above 1e-30 * 2^24) and keeps the
-// generalized kernel's s = u + v away from 0 without a guard per update.
-template <>
-__device__ __forceinline__ float emb_value<float, EMB_PROP>(double c, double, double, float it) {
-  return (float)c * it + 1e-30f;
-}
-
 // Table whose row segment holds column j (segments are contiguous, in order).
 __device__ __forceinline__ int segment_of(const TabDesc *tabs, int n_tabs, int64_t j) {
   int lo = 0, hi = n_tabs - 1;
@@ -87,15 +56,17 @@ __device__ __forceinline__ int segment_of(const TabDesc *tabs, int n_tabs, int64
   return lo;
 }
 
-// One CTA per branch row r (node b0 + r): in table t's segment,
-// X[r][x_col + j] = f(count[off + (j mod n)]) for j < the segment's width.
+// One CTA per branch row r (node nodes[r], or b0 + r without a list): in
+// table t's segment, X[r][x_col + j] = f(count[off + (j mod n)]) for j < the
+// segment's width.
 template <typename T, int KIND>
-__global__ void k_emb_rows(int64_t b0, const int32_t *__restrict__ slot_of_node,
+__global__ void k_emb_rows(int64_t b0, const int32_t *__restrict__ nodes,
+                           const int32_t *__restrict__ slot_of_node,
                            const double *__restrict__ counts, int64_t ld,
                            const double *__restrict__ length, const double *__restrict__ total,
                            const float *__restrict__ inv_total_f, T *__restrict__ X, int64_t pitch,
                            const TabDesc *__restrict__ tabs, int n_tabs) {
-  const int64_t v = b0 + blockIdx.x;
+  const int64_t v = nodes ? (int64_t)nodes[blockIdx.x] : b0 + blockIdx.x;
   const double *c = counts + (int64_t)slot_of_node[v] * ld;
   const double l = length[v];
   T *x = X + (int64_t)blockIdx.x * pitch;
@@ -130,10 +101,11 @@ cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *
 cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
                             const int32_t *slot_of_node, const double *counts, int64_t ld,
                             const double *length, const double *total, const float *inv_total_f,
-                            void *X, int64_t pitch, const TabDesc *tabs, int n_tabs, cudaStream_t st) {
+                            void *X, int64_t pitch, const TabDesc *tabs, int n_tabs, cudaStream_t st,
+                            const int32_t *nodes) {
   if (rows <= 0) return cudaSuccess;
 #define UF_EMB(T, K)                                                                            \
-  k_emb_rows<T, K><<<rows, 256, 0, st>>>(b0, slot_of_node, counts, ld, length, total, inv_total_f, \
+  k_emb_rows<T, K><<<rows, 256, 0, st>>>(b0, nodes, slot_of_node, counts, ld, length, total, inv_total_f, \
                                          (T *)X, pitch, tabs, n_tabs)
   if (fp32) {
     if (kind == EMB_SCALED) UF_EMB(float, EMB_SCALED);

@@ -13,6 +13,9 @@
 // num and den are formed exactly in integers before the one FP64 division
 // (the common 2^F cancels); weighted_unnormalized returns num * 2^-F.
 // A ratio with den == 0 is 0.
+// Branches scattered by uf_sparse.cu add their per-sample terms R here: the
+// diagonal is D + R, an abs-form cell gains R_k + R_j, and the generalized
+// den gains R_k + R_j.
 #include "uf_internal.h"
 
 namespace ufg {
@@ -28,12 +31,15 @@ __global__ void k_finalize(const FinalArgs a) {
     int64_t j = k + s + 1;
     if (j >= a.n) j -= a.n;
     if (a.full && 2 * (s + 1) == a.n && k >= a.n / 2) continue;  // duplicate half stripe
-    const long long m = (long long)a.M[c];
+    long long m = (long long)a.M[c];
     const bool abs_form = a.mixed_forms && (s & 7) >= 8 - FP32_ABS_ROWS;
+    const long long rk = a.Dsp ? (long long)a.Dsp[k] : 0, rj = a.Dsp ? (long long)a.Dsp[j] : 0;
+    const long long dk = (a.Dg ? (long long)a.Dg[k] : 0) + rk, dj = (a.Dg ? (long long)a.Dg[j] : 0) + rj;
+    if (abs_form || a.method == 3) m += rk + rj;
     double val;
     switch (a.method) {
     case 0: {  // unweighted
-      const long long w = (long long)a.Dg[k] + (long long)a.Dg[j];
+      const long long w = dk + dj;
       long long num, den2;  // den2 = 2 * den
       if (abs_form) {
         num = m;
@@ -46,12 +52,12 @@ __global__ void k_finalize(const FinalArgs a) {
       val = den2 > 0 ? 2.0 * (double)num / (double)den2 : 0.0;
     } break;
     case 1: {  // weighted unnormalized
-      long long num = abs_form ? m : (long long)a.Dg[k] + (long long)a.Dg[j] - 2 * m;
+      long long num = abs_form ? m : dk + dj - 2 * m;
       if (num < 0) num = 0;
       val = (double)num * a.inv_scale;
     } break;
     case 2: {  // weighted normalized
-      const long long den = (long long)a.Dg[k] + (long long)a.Dg[j];
+      const long long den = dk + dj;
       long long num = abs_form ? m : den - 2 * m;
       if (num < 0) num = 0;
       val = den > 0 ? (double)num / (double)den : 0.0;

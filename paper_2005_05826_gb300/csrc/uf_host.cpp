@@ -38,6 +38,7 @@ std::atomic<int64_t> g_kernel_timing{0};
 std::atomic<int64_t> g_tensor_path{1};
 std::atomic<int64_t> g_graph{1};
 std::atomic<int64_t> g_autotune{1};
+std::atomic<int64_t> g_sparse{1};
 
 uf_status fail(uf_status st, const char *fmt, ...) {
   char buf[512];
@@ -106,10 +107,14 @@ struct uf_tree {
   std::vector<double> length;
   std::vector<int32_t> tip_of_node;            // node -> tip number or -1
   std::vector<int32_t> child_ptr, child_idx;   // children in index order
+  // tips under node v are the tip numbers [tip_lo[v], tip_hi[v]) when those
+  // are contiguous (always so for a postorder numbering), else both -1
+  std::vector<int32_t> tip_lo, tip_hi;
   std::mutex mu;
   struct Dev {
     double *length = nullptr;
     int32_t *tip_of_node = nullptr, *child_ptr = nullptr, *child_idx = nullptr;
+    int32_t *tip_lo = nullptr, *tip_hi = nullptr;
   };
   std::map<int, Dev> dev;
   std::map<int64_t, std::unique_ptr<Plan>> plans;  // by block rows
@@ -125,6 +130,8 @@ struct uf_tree {
       cudaFree(kv.second.tip_of_node);
       cudaFree(kv.second.child_ptr);
       cudaFree(kv.second.child_idx);
+      cudaFree(kv.second.tip_lo);
+      cudaFree(kv.second.tip_hi);
     }
     for (auto &p : plans)
       for (auto &kv : p.second->dev) {
@@ -178,11 +185,15 @@ uf_tree::Dev &tree_dev(uf_tree *t, int device) {
     d.tip_of_node = dev_upload(t->tip_of_node, "tree upload");
     d.child_ptr = dev_upload(t->child_ptr, "tree upload");
     d.child_idx = dev_upload(t->child_idx, "tree upload");
+    d.tip_lo = dev_upload(t->tip_lo, "tree upload");
+    d.tip_hi = dev_upload(t->tip_hi, "tree upload");
   } catch (...) {
     cudaFree(d.length);
     cudaFree(d.tip_of_node);
     cudaFree(d.child_ptr);
     cudaFree(d.child_idx);
+    cudaFree(d.tip_lo);
+    cudaFree(d.tip_hi);
     throw;
   }
   return t->dev[device] = d;
@@ -567,6 +578,87 @@ void enqueue_counts(const Inputs &in, const BatchJob &J, const std::vector<int> 
   }
 }
 
+// Branches of a call split between the dense stripe kernels and the
+// sparse-row pair kernel (uf_sparse.cu).
+struct RowSplit {
+  std::vector<int32_t> dense;       // dense branch nodes, block by block, ascending
+  std::vector<int64_t> dense_ptr;   // per block: first index into dense (size blocks + 1)
+  std::vector<double> dense_len;    // their branch lengths
+  std::vector<std::vector<int32_t>> sparse;  // sparse branch nodes by capacity class
+  std::vector<int> cap;             // shared-memory entries of each class
+  int64_t n_sparse = 0;
+  double pairs = 0.0;               // both-nonzero pairs scattered, at most (sum over tables)
+  int64_t max_dense = 0;            // most dense rows in one block
+};
+
+// Per branch v the count entries of table t under v are the CSC run of v's
+// tips, ub_t(v) = col_ptr_t[tip_hi] - col_ptr_t[tip_lo] (an upper bound on the
+// nonzero samples, exact when no two tips share a sample).  Mode 1 scatters
+// v when the modelled time of its pairs is below that of a dense pass over
+// its stripe cells; the rates are GB300 measurements of the two kernels and
+// of global 64-bit atomics (L2-resident accumulators or not).  Mode 2
+// scatters every branch that fits; mode 0 none.  The choice depends on the
+// tree and the tables only, not on the stripe range, so that a range run
+// gives bitwise the stripes of the full run.
+RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int acc, bool fp32) {
+  RowSplit R;
+  const int mode = (int)g_sparse.load();
+  const int64_t nb = tree->n_nodes - 1;
+  const size_t nt = J.tabs.size();
+  const int classes[4] = {128, 512, 2048, SPARSE_MAX_ENTRIES};
+  R.cap.assign(classes, classes + 4);
+  R.sparse.resize(4);
+  std::vector<char> is_sparse(std::max<int64_t>(nb, 1), 0);
+  if (mode != 0) {
+    const int n_acc = acc == ACC_GEN ? 2 : 1;
+    double cells = 0.0;  // stripe cells of a full run of every table
+    for (size_t t = 0; t < nt; t++) {
+      const double n = (double)J.tabs[t].table->n;
+      cells += std::floor(n / 2.0) * n;
+    }
+    const double atom_rate = cells * 8.0 * n_acc <= 64e6 ? 1.5e11 : 2.5e10;
+    const double dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
+    const double visit_rate = fp32 ? 2e12 : (acc == ACC_GEN ? 3e10 : 1e12);
+    const double job_cost = 5e-10;
+    const double dense_t = cells / dense_rate;
+    for (int64_t v = 0; v < nb; v++) {
+      const int32_t lo = tree->tip_lo[v], hi = tree->tip_hi[v];
+      if (lo < 0) continue;
+      double cost = 0.0, pairs = 0.0;
+      int64_t mx = 0;
+      for (size_t t = 0; t < nt; t++) {
+        const auto &cp = J.tabs[t].table->col_ptr;
+        const int64_t ub = cp[hi] - cp[lo];
+        mx = std::max(mx, ub);
+        if (ub == 0) continue;
+        const double pr = (double)ub * (double)(ub - 1) / 2.0;
+        pairs += pr;
+        cost += job_cost + pr * (1.0 / visit_rate + n_acc / atom_rate) + (double)ub * 4.0 / atom_rate;
+      }
+      if (mx > SPARSE_MAX_ENTRIES) continue;
+      if (mode == 2 || cost < dense_t) {
+        is_sparse[v] = 1;
+        int c = 0;
+        while (classes[c] < mx) c++;
+        R.sparse[c].push_back((int32_t)v);
+        R.n_sparse++;
+        R.pairs += pairs;
+      }
+    }
+  }
+  R.dense_ptr.push_back(0);
+  for (size_t b = 0; b < P->b0.size(); b++) {
+    for (int64_t v = P->b0[b]; v < P->b1[b]; v++)
+      if (!is_sparse[v]) {
+        R.dense.push_back((int32_t)v);
+        R.dense_len.push_back(tree->length[v]);
+      }
+    R.dense_ptr.push_back((int64_t)R.dense.size());
+    R.max_dense = std::max(R.max_dense, R.dense_ptr[b + 1] - R.dense_ptr[b]);
+  }
+  return R;
+}
+
 // Output buffers: the caller's device memory, or a device staging buffer
 // copied to the caller's host memory at the end.
 struct Outputs {
@@ -788,15 +880,53 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + (double)pitch * es + 8.0 + n_cols * es / 64.0, acc_bytes);
   Inputs in = bind_inputs(tree, J, device, rows);
   cudaStream_t st = J.st;
+  const RowSplit split = split_rows(tree, J, in.P, acc, fp32);
+  const int64_t xrows = std::max<int64_t>(split.max_dense, 1);
   int64_t kernels = 0, acc_launches = 0;
   PhaseTimer timer(g_kernel_timing.load() != 0, st);
   DevBuf counts((size_t)in.P->n_slots * n_cols * 8, st, "alloc counts");
-  DevBuf X((size_t)rows * pitch * es, st, "alloc embeddings");
+  DevBuf X((size_t)xrows * pitch * es, st, "alloc embeddings");
   DevBuf M((size_t)cells * 8, st, "alloc stripes");
-  DevBuf M2, Dg, diag_tmp, counter(sizeof(int), st, "alloc counter");
+  DevBuf M2, Dg, Dsp, diag_tmp, counter(sizeof(int), st, "alloc counter");
   DevBuf d_tabs(nt * sizeof(TabDesc), st, "alloc table list");
   DevBuf total((size_t)n_cols * 8, st, "alloc totals"), inv_total((size_t)n_cols * 4, st, "alloc totals");
+  DevBuf d_dense(std::max<size_t>(split.dense.size(), 1) * 4, st, "alloc row lists");
+  DevBuf d_dlen(std::max<size_t>(split.dense_len.size(), 1) * 8, st, "alloc row lists");
+  DevBuf d_sparse, d_sptabs;
   ck(cudaMemcpyAsync(d_tabs.p, tabs.data(), nt * sizeof(TabDesc), cudaMemcpyHostToDevice, st), "copy tables");
+  if (!split.dense.empty()) {
+    ck(cudaMemcpyAsync(d_dense.p, split.dense.data(), split.dense.size() * 4, cudaMemcpyHostToDevice, st),
+       "copy row lists");
+    ck(cudaMemcpyAsync(d_dlen.p, split.dense_len.data(), split.dense_len.size() * 8, cudaMemcpyHostToDevice, st),
+       "copy row lists");
+  }
+  std::vector<int64_t> sp_off;  // first entry of each capacity class in d_sparse
+  if (split.n_sparse > 0) {
+    std::vector<int32_t> all;
+    for (const auto &c : split.sparse) {
+      sp_off.push_back((int64_t)all.size());
+      all.insert(all.end(), c.begin(), c.end());
+    }
+    std::vector<SpTab> sp(nt);
+    for (size_t t = 0; t < nt; t++) {
+      sp[t].col_ptr = in.xd[t]->col_ptr;
+      sp[t].col_row = in.xd[t]->col_row;
+      sp[t].col_val = in.xd[t]->col_val;
+      sp[t].total = in.xd[t]->total;
+      sp[t].inv_total_f = in.xd[t]->inv_total_f;
+      sp[t].n = tabs[t].n;
+      sp[t].off = tabs[t].off;
+      sp[t].s_lo = tabs[t].s_lo;
+      sp[t].s_hi = tabs[t].s_hi;
+      sp[t].m_off = tabs[t].m_off;
+    }
+    d_sparse = DevBuf(all.size() * 4, st, "alloc row lists");
+    d_sptabs = DevBuf(nt * sizeof(SpTab), st, "alloc table list");
+    ck(cudaMemcpyAsync(d_sparse.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice, st), "copy row lists");
+    ck(cudaMemcpyAsync(d_sptabs.p, sp.data(), nt * sizeof(SpTab), cudaMemcpyHostToDevice, st), "copy tables");
+    Dsp = DevBuf((size_t)n_cols * 8, st, "alloc diagonal");
+    ck(cudaMemsetAsync(Dsp.p, 0, (size_t)n_cols * 8, st), "memset");
+  }
   for (size_t t = 0; t < nt; t++) {
     const size_t n = (size_t)J.tabs[t].table->n;
     ck(cudaMemcpyAsync(total.as<double>() + off[t], in.xd[t]->total, n * 8, cudaMemcpyDeviceToDevice, st),
@@ -810,17 +940,17 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     ck(cudaMemsetAsync(M2.p, 0, (size_t)cells * 8, st), "memset");
   } else {
     Dg = DevBuf((size_t)n_cols * 8, st, "alloc diagonal");
-    diag_tmp = DevBuf(diag_scratch_bytes(fp32, (int)rows, n_cols), st, "alloc diagonal scratch");
+    diag_tmp = DevBuf(diag_scratch_bytes(fp32, (int)xrows, n_cols), st, "alloc diagonal scratch");
     ck(cudaMemsetAsync(Dg.p, 0, (size_t)n_cols * 8, st), "memset");
   }
   ck(cudaMemsetAsync(M.p, 0, (size_t)cells * 8, st), "memset");
   Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
   // chunk size: tuned once per (accumulator, precision, size bucket)
-  const auto key = tune_key(acc, fp32, n_tiles, rows);
+  const auto key = tune_key(acc, fp32, n_tiles, xrows);
   int chunk = stripe_chunk_rows();
   bool tune = false;
-  if (g_autotune.load()) {
+  if (g_autotune.load() && !split.dense.empty()) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tuned_chunk.find(key);
     if (it != g_tuned_chunk.end()) chunk = it->second;
@@ -829,20 +959,25 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   // the launch sequence goes into a CUDA graph unless it is timed per phase
   Capture cap(g_graph.load() != 0 && !timer.on && !tune, st, device);
   const cudaStream_t ls = cap.stream();
+  bool tuned = false;
   for (size_t b = 0; b < in.P->b0.size(); b++) {
-    const int64_t b0 = in.P->b0[b], b1 = in.P->b1[b];
+    const int64_t b0 = in.P->b0[b];
+    const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
     timer.begin(0);
     enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, ls, &kernels);
-    ck(launch_emb_rows(kind, fp32, b0, (int)(b1 - b0), in.pd->slot_of_node, counts.as<double>(), n_cols,
-                       in.td->length, total.as<double>(), inv_total.as<float>(), X.p, pitch,
-                       d_tabs.as<TabDesc>(), (int)nt, ls),
-       "embedding rows");
-    kernels++;
+    if (nd > 0) {
+      ck(launch_emb_rows(kind, fp32, b0, (int)nd, in.pd->slot_of_node, counts.as<double>(), n_cols,
+                         in.td->length, total.as<double>(), inv_total.as<float>(), X.p, pitch,
+                         d_tabs.as<TabDesc>(), (int)nt, ls, d_dense.as<int32_t>() + d0),
+         "embedding rows");
+      kernels++;
+    }
     timer.end();
+    if (nd == 0) continue;
     StripeArgs sa{};
     sa.X = X.p;
-    sa.len = in.td->length + b0;
-    sa.rows = (int)(b1 - b0);
+    sa.len = d_dlen.as<double>() + d0;
+    sa.rows = (int)nd;
     sa.pitch = pitch;
     sa.chunk = chunk;
     sa.tabs = d_tabs.as<TabDesc>();
@@ -855,8 +990,9 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sa.alpha = J.alpha;
     sa.scale = scale;
     sa.counter = counter.as<int>();
-    if (tune && b == 0) {
+    if (tune && !tuned) {
       chunk = sa.chunk = tune_chunk(acc, fp32, sa, (size_t)cells, ls);
+      tuned = true;
       std::lock_guard<std::mutex> g(g_tune_mu);
       g_tuned_chunk[key] = chunk;
     }
@@ -865,13 +1001,39 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     timer.end();
     kernels++;
     acc_launches++;
-    exec_flops += 2.0 * (double)n_tiles * tile_s * tile_k * (double)(b1 - b0);
+    exec_flops += 2.0 * (double)n_tiles * tile_s * tile_k * (double)nd;
     if (acc == ACC_MIN) {
       timer.begin(2);
       ck(launch_diag(fp32, sa, diag_tmp.p, ls), "diagonal accumulate");
       timer.end();
       kernels += 2;
     }
+  }
+  // sparse rows: after the dense blocks, whose chunk tuning clears M
+  if (split.n_sparse > 0) {
+    timer.begin(4);
+    for (size_t c = 0; c < split.sparse.size(); c++) {
+      if (split.sparse[c].empty()) continue;
+      SparseArgs sp{};
+      sp.nodes = d_sparse.as<int32_t>() + sp_off[c];
+      sp.n_nodes = (int)split.sparse[c].size();
+      sp.cap = split.cap[c];
+      sp.tip_lo = in.td->tip_lo;
+      sp.tip_hi = in.td->tip_hi;
+      sp.length = in.td->length;
+      sp.tabs = d_sptabs.as<SpTab>();
+      sp.n_tabs = (int)nt;
+      sp.kind = kind;
+      sp.mixed_forms = fp32 && acc == ACC_MIN;
+      sp.M = M.as<unsigned long long>();
+      sp.M2 = M2.as<unsigned long long>();
+      sp.Dsp = Dsp.as<unsigned long long>();
+      sp.alpha = J.alpha;
+      sp.scale = scale;
+      ck(launch_sparse_rows(acc, fp32, sp, ls), "sparse rows");
+      kernels++;
+    }
+    timer.end();
   }
   timer.begin(3);
   for (size_t t = 0; t < nt; t++) {
@@ -885,6 +1047,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     fa.M = M.as<unsigned long long>() + tabs[t].m_off;
     fa.M2 = M2.p ? M2.as<unsigned long long>() + tabs[t].m_off : nullptr;
     fa.Dg = Dg.p ? Dg.as<unsigned long long>() + off[t] : nullptr;
+    fa.Dsp = Dsp.p ? Dsp.as<unsigned long long>() + off[t] : nullptr;
     fa.inv_scale = 1.0 / scale;
     fa.out = o.dev[t];
     fa.out_fp32 = J.out_fp32;
@@ -902,15 +1065,20 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   M = DevBuf();
   M2 = DevBuf();
   Dg = DevBuf();
+  Dsp = DevBuf();
   diag_tmp = DevBuf();
   counter = DevBuf();
   d_tabs = DevBuf();
+  d_dense = DevBuf();
+  d_dlen = DevBuf();
+  d_sparse = DevBuf();
+  d_sptabs = DevBuf();
   total = DevBuf();
   inv_total = DevBuf();
   o.tmp.clear();
   if (!J.out_is_device || st == nullptr || timer.on) ck(cudaStreamSynchronize(st), "synchronize");
   else ck(cudaGetLastError(), "enqueue");
-  double ms[4] = {0, 0, 0, 0};
+  double ms[5] = {0, 0, 0, 0, 0};
   timer.collect(ms);
   fill_reports(tree, J, o, ms, kernels, acc_launches, 0, rows, (int64_t)in.P->b0.size(), exec_flops, tile_s,
                tile_k, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
@@ -918,6 +1086,10 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     if (t.rep) {
       t.rep->chunk_rows = chunk;
       t.rep->graph = cap.on ? 1 : 0;
+      t.rep->dense_rows = (int64_t)split.dense.size();
+      t.rep->sparse_rows = split.n_sparse;
+      t.rep->sparse_pairs = split.pairs;
+      t.rep->t_sparse_ms = ms[4];
     }
   return UF_OK;
 }
@@ -992,6 +1164,11 @@ uf_status uf_set_option(const char *name, int64_t value) {
     g_autotune = value;
     return UF_OK;
   }
+  if (!strcmp(name, "sparse")) {
+    if (value < 0 || value > 2) return fail(UF_EINVAL, "sparse must be 0, 1 or 2");
+    g_sparse = value;
+    return UF_OK;
+  }
   return fail(UF_EINVAL, "unknown option '%s'", name);
 }
 
@@ -1002,6 +1179,7 @@ int64_t uf_get_option(const char *name) {
   if (!strcmp(name, "tensor_path")) return g_tensor_path.load();
   if (!strcmp(name, "graph")) return g_graph.load();
   if (!strcmp(name, "autotune")) return g_autotune.load();
+  if (!strcmp(name, "sparse")) return g_sparse.load();
   return -1;
 }
 
@@ -1060,6 +1238,26 @@ uf_status uf_tree_create(int64_t n_nodes, const int64_t *parent, const double *l
     for (int64_t i = 0; i < n_nodes; i++)
       if (nchild[i] == 0) t->tip_of_node[i] = (int32_t)tips++;
     t->n_tips = tips;
+    {
+      std::vector<int64_t> under(n_nodes, 0);
+      t->tip_lo.assign(n_nodes, INT32_MAX);
+      t->tip_hi.assign(n_nodes, -1);
+      for (int64_t v = 0; v < n_nodes; v++) {  // children come before their parent
+        if (t->tip_of_node[v] >= 0) {
+          t->tip_lo[v] = t->tip_of_node[v];
+          t->tip_hi[v] = t->tip_of_node[v] + 1;
+          under[v] = 1;
+        }
+        if (v + 1 < n_nodes) {
+          const int64_t p = parent[v];
+          t->tip_lo[p] = std::min(t->tip_lo[p], t->tip_lo[v]);
+          t->tip_hi[p] = std::max(t->tip_hi[p], t->tip_hi[v]);
+          under[p] += under[v];
+        }
+      }
+      for (int64_t v = 0; v < n_nodes; v++)
+        if ((int64_t)t->tip_hi[v] - t->tip_lo[v] != under[v]) t->tip_lo[v] = t->tip_hi[v] = -1;
+    }
     t->dist.assign(n_nodes, 0.0);
     for (int64_t v = n_nodes - 2; v >= 0; v--) {  // parents come later in the order
       t->dist[v] = t->length[v] + t->dist[parent[v]];

@@ -61,11 +61,13 @@ cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_
 cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
                                const int32_t *child_idx, const int32_t *slot_of_node,
                                double *counts, int64_t ld, cudaStream_t st);
-// Embedding rows of branches b0 .. b0 + rows - 1 for every table segment.
+// Embedding rows of branches nodes[0 .. rows) (b0 .. b0 + rows - 1 when
+// nodes is null) for every table segment.
 cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
                             const int32_t *slot_of_node, const double *counts, int64_t ld,
                             const double *length, const double *total, const float *inv_total_f,
-                            void *X, int64_t pitch, const TabDesc *tabs, int n_tabs, cudaStream_t st);
+                            void *X, int64_t pitch, const TabDesc *tabs, int n_tabs, cudaStream_t st,
+                            const int32_t *nodes = nullptr);
 
 // ---- stripe accumulate (uf_stripe.cu) ----
 // In the FP32 min kernel, stripes s with (s % 8) >= 8 - FP32_ABS_ROWS hold
@@ -111,8 +113,46 @@ struct FinalArgs {
   double inv_scale;     // 2^-F
   void *out;
   int out_fp32;
+  // sparse-row diagonal of this table (uf_sparse.cu), or null: R[k] = sum of
+  // the sparse rows' x[k] (ACC_MIN) or l u[k]^alpha (ACC_GEN)
+  const unsigned long long *Dsp;
 };
 cudaError_t launch_finalize(const FinalArgs &a, cudaStream_t st);
+
+// ---- sparse rows (uf_sparse.cu) ----
+// A branch whose subtree holds few nonzero counts adds to a stripe cell only
+// when both samples of the cell are nonzero under it (min(x_k, x_j) = 0
+// otherwise; the generalized den is split into per-sample terms plus a pair
+// correction).  Such rows skip the dense kernels: one CTA per (row, table)
+// gathers the subtree's nonzero samples from the table's CSC columns (the
+// subtree's tips are a contiguous range of tip numbers) and scatters the
+// both-nonzero pairs into the accumulators.
+struct SpTab {
+  const int64_t *col_ptr;   // CSC of the table: tip f -> entries [col_ptr[f], col_ptr[f + 1])
+  const int32_t *col_row;   // sample of each entry (ascending within a tip)
+  const double *col_val;    // count of each entry
+  const double *total;      // per-sample count totals
+  const float *inv_total_f; // 1 / total in FP32
+  int n, off, s_lo, s_hi;   // samples, combined column, stored stripes
+  int64_t m_off;            // first accumulator cell
+};
+struct SparseArgs {
+  const int32_t *nodes;     // sparse branch nodes of this launch
+  int n_nodes;
+  int cap;                  // shared-memory capacity in entries (power of two, >= 128)
+  const int32_t *tip_lo, *tip_hi;  // tips of node v: tip numbers [tip_lo[v], tip_hi[v])
+  const double *length;     // branch length of every node
+  const SpTab *tabs;
+  int n_tabs;
+  int kind;                 // EmbKind
+  int mixed_forms;          // FP32 min kernel abs-form stripes present
+  unsigned long long *M, *M2, *Dsp;  // cells (M / den), Q (generalized), per-sample diagonal R
+  double alpha, scale;
+};
+// largest subtree entry count a sparse row may have
+constexpr int SPARSE_MAX_ENTRIES = 4096;
+size_t sparse_smem_bytes(bool fp32, int cap);
+cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 
 // ---- unweighted on tensor cores (uf_gram.cu) ----
 // One table of a batch: its samples occupy rows [row_base, row_base + n_pad)

@@ -1,0 +1,249 @@
+// uf_sparse.cu -- branches with few nonzero samples, as pair scatters.
+//
+// The stripe loop of the paper (Sec. 2-3, Figs. 1-3) visits every stripe
+// cell of every branch.  In the reformulated accumulators (uf_stripe.cu) a
+// branch e adds to cell (k, j)
+//   min form:   min(x_e[k], x_e[j])               (0 unless both are nonzero)
+//   abs form:   |x_e[k] - x_e[j]| = x_e[k] + x_e[j] - 2 min(x_e[k], x_e[j])
+//   generalized den:  l s^a, s = u + v
+//   generalized Q:    l min(u, v) s^(a-1)         (0 unless both are nonzero)
+// and the diagonal gets x_e[k].  Near the tips most branches are nonzero in
+// only a few samples, so all of a branch's nonzero terms come from its
+// both-nonzero pairs plus one term per nonzero sample:
+//   min form:  cell += min(X_k, X_j);  R[k] += X_k          (X = x rounded to fixed point)
+//   abs form:  cell += -2 min(X_k, X_j) and the finalize adds R[k] + R[j]
+//   generalized, with P_k = fixed(l u_k^a), w = l s^(a-1):
+//              Q   += q = fixed(w min(u, v)),
+//              den += 2 q + fixed(w |u - v|) - P_k - P_j,  R[k] += P_k,
+//   so that den = sum l s^a and num = den - 2 Q = sum l s^(a-1) |u - v| over
+//   every branch where u or v is nonzero (a one-sided branch gives l u^a to
+//   both), and two identical samples still give num = 0 exactly.
+// The finalize adds R[k] + R[j] where these terms need it (uf_finalize.cu);
+// integer addition makes the order free and the result deterministic.
+//
+// One CTA per (sparse branch, table).  The branch's tips are a contiguous
+// range of tip numbers, so its nonzero counts are one contiguous run of the
+// table's CSC entries: they are loaded into shared memory, sorted by sample
+// (bitonic; a single tip's column is already sorted and is left alone), and
+// equal samples are summed in entry order.  The z distinct samples give
+// z (z - 1) / 2 pairs; each thread takes a contiguous range of the pair
+// numbering and adds each pair to its stripe cell with one atomic per
+// accumulator (two when the pair is the duplicated half stripe of an even n).
+#include <cmath>
+
+#include "uf_device.cuh"
+
+namespace ufg {
+
+namespace {
+
+// Block-wide exclusive prefix of one int per thread (blockDim a multiple of 32).
+__device__ int block_exclusive_scan(int v, int *sh, int *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < nw ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) sh[lane] = w;
+  }
+  __syncthreads();
+  const int base = wid ? sh[wid - 1] : 0;
+  *total = sh[nw - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+// u^alpha of a proportion u > 0
+template <typename T, int MODE>
+__device__ __forceinline__ T pow_alpha(T u, T alpha);
+template <>
+__device__ __forceinline__ double pow_alpha<double, 0>(double u, double) { return sqrt(u); }
+template <>
+__device__ __forceinline__ double pow_alpha<double, 1>(double u, double alpha) { return pow(u, alpha); }
+template <>
+__device__ __forceinline__ float pow_alpha<float, 0>(float u, float) { return u * sfu_pow<0>(u, -0.5f); }
+template <>
+__device__ __forceinline__ float pow_alpha<float, 1>(float u, float alpha) { return sfu_pow<1>(u, alpha); }
+
+template <typename T, int MODE>
+__device__ __forceinline__ T pow_am1(T s, T am1) {
+  if constexpr (sizeof(T) == 4) return sfu_pow<MODE>(s, am1);
+  else return gen_pow<T, MODE>(s, am1);
+}
+
+__device__ __forceinline__ void red_add(unsigned long long *p, long long v) {
+  atomicAdd(p, (unsigned long long)v);
+}
+
+template <typename T, int ACC, int MODE>
+__global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int sh[33];
+  const int P = a.cap;
+  unsigned long long *key = reinterpret_cast<unsigned long long *>(smem_raw);  // (sample << 32) | entry
+  double *cnt = reinterpret_cast<double *>(key + P);                          // entry -> count
+  long long *fx = reinterpret_cast<long long *>(cnt + P);                     // distinct sample -> X or P
+  T *xs = reinterpret_cast<T *>(fx + P);                                      // distinct sample -> x or u
+  int *ks = reinterpret_cast<int *>(xs + P);                                  // distinct sample -> k
+
+  const int v = a.nodes[blockIdx.x];
+  const SpTab tb = a.tabs[blockIdx.y];
+  const int64_t q0 = tb.col_ptr[a.tip_lo[v]];
+  const int L = (int)(tb.col_ptr[a.tip_hi[v]] - q0);
+  // the host sizes cap to every (row, table) run of the launch
+  if (L <= 0 || L > P) return;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  int P2 = 1;
+  while (P2 < L) P2 <<= 1;
+  for (int i = tid; i < P2; i += NT) {
+    if (i < L) {
+      key[i] = ((unsigned long long)(unsigned)tb.col_row[q0 + i] << 32) | (unsigned)i;
+      cnt[i] = tb.col_val[q0 + i];
+    } else {
+      key[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  int unsorted = 0;
+  for (int i = tid + 1; i < L; i += NT) unsorted |= (key[i] >> 32) <= (key[i - 1] >> 32);
+  if (__syncthreads_or(unsorted)) {
+    for (int k = 2; k <= P2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < P2; i += NT) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long x = key[i], y = key[ixj];
+            if ((x > y) == ((i & k) == 0)) {
+              key[i] = y;
+              key[ixj] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+  }
+  // distinct samples: the first entry of each run of equal samples
+  const int E = (L + NT - 1) / NT, i0 = tid * E, i1 = min(L, i0 + E);
+  int heads = 0;
+  for (int i = i0; i < i1; i++) heads += (i == 0 || (key[i] >> 32) != (key[i - 1] >> 32));
+  int z = 0;
+  int u = block_exclusive_scan(heads, sh, &z);
+  const double l = a.length[v];
+  const T alpha = (T)a.alpha;
+  for (int i = i0; i < i1; i++) {
+    const unsigned smp = (unsigned)(key[i] >> 32);
+    if (i > 0 && (unsigned)(key[i - 1] >> 32) == smp) continue;
+    double c = 0.0;
+    for (int m = i; m < L && (unsigned)(key[m] >> 32) == smp; m++) c += cnt[key[m] & 0xffffffffu];
+    T x;
+    if (a.kind == EMB_SCALED) x = emb_value<T, EMB_SCALED>(c, l, tb.total[smp], tb.inv_total_f[smp]);
+    else if (a.kind == EMB_PRESENCE) x = emb_value<T, EMB_PRESENCE>(c, l, tb.total[smp], tb.inv_total_f[smp]);
+    else x = emb_value<T, EMB_PROP>(c, l, tb.total[smp], tb.inv_total_f[smp]);
+    long long f;
+    if (ACC == ACC_MIN) f = to_fixed(x, a.scale);
+    else f = to_fixed((T)l * pow_alpha<T, MODE>(x, alpha), a.scale);
+    ks[u] = (int)smp;
+    xs[u] = x;
+    fx[u] = f;
+    u++;
+  }
+  __syncthreads();
+  for (int e = tid; e < z; e += NT) red_add(a.Dsp + tb.off + ks[e], fx[e]);
+  // pairs (ia < ib) numbered row by row: row ia starts at ia (2z - ia - 1) / 2
+  const int64_t npairs = (int64_t)z * (z - 1) / 2;
+  if (npairs == 0) return;
+  const int64_t per = (npairs + NT - 1) / NT;
+  int64_t p = (int64_t)tid * per;
+  const int64_t p1 = min(npairs, p + per);
+  if (p >= p1) return;
+  auto row_start = [z](int64_t r) { return r * (2 * (int64_t)z - r - 1) / 2; };
+  const double bq = 2.0 * z - 1.0;
+  int ia = (int)((bq - sqrt(fmax(bq * bq - 8.0 * (double)p, 0.0))) * 0.5);
+  ia = max(0, min(ia, z - 2));
+  while (ia > 0 && row_start(ia) > p) ia--;
+  while (ia < z - 2 && row_start(ia + 1) <= p) ia++;
+  int ib = ia + 1 + (int)(p - row_start(ia));
+  const int n = tb.n;
+  unsigned long long *M = a.M + tb.m_off;
+  unsigned long long *M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
+  const T lt = (T)l, am1 = (T)(a.alpha - 1.0);
+  for (; p < p1; p++) {
+    const int ka = ks[ia], kb = ks[ib];
+    const int d = kb - ka;
+    int s, kc;
+    if (2 * d <= n) {
+      s = d - 1;
+      kc = ka;
+    } else {
+      s = n - d - 1;
+      kc = kb;
+    }
+    if (s >= tb.s_lo && s <= tb.s_hi) {
+      const int64_t cell = (int64_t)(s - tb.s_lo) * n + kc;
+      const bool dup = 2 * d == n;  // also stored at k = kb (= ka + n/2)
+      if (ACC == ACC_MIN) {
+        long long t = min(fx[ia], fx[ib]);
+        if (a.mixed_forms && (s & 7) >= 8 - FP32_ABS_ROWS) t *= -2;
+        red_add(M + cell, t);
+        if (dup) red_add(M + cell + d, t);
+      } else {
+        const T uu = xs[ia], vv = xs[ib];
+        const T w = lt * pow_am1<T, MODE>(uu + vv, am1);
+        const long long q = to_fixed(w * tmin<T>(uu, vv), a.scale);
+        const long long e = to_fixed(w * (uu > vv ? uu - vv : vv - uu), a.scale);
+        const long long den = 2 * q + e - fx[ia] - fx[ib];
+        red_add(M + cell, den);
+        red_add(M2 + cell, q);
+        if (dup) {
+          red_add(M + cell + d, den);
+          red_add(M2 + cell + d, q);
+        }
+      }
+    }
+    if (++ib == z) {
+      ia++;
+      ib = ia + 1;
+    }
+  }
+}
+
+template <typename T, int ACC, int MODE>
+cudaError_t launch_one(const SparseArgs &a, size_t smem, cudaStream_t st) {
+  auto kernel = k_sparse_rows<T, ACC, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int nt = a.cap <= 512 ? 128 : 256;
+  dim3 grid((unsigned)a.n_nodes, (unsigned)a.n_tabs);
+  kernel<<<grid, nt, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t sparse_smem_bytes(bool fp32, int cap) {
+  return (size_t)cap * (8 + 8 + 8 + (fp32 ? 4 : 8) + 4);
+}
+
+cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st) {
+  if (a.n_nodes <= 0 || a.n_tabs <= 0) return cudaSuccess;
+  if (a.cap < 128 || (a.cap & (a.cap - 1)) || a.cap > SPARSE_MAX_ENTRIES || a.n_tabs > 65535)
+    return cudaErrorInvalidValue;
+  const size_t smem = sparse_smem_bytes(fp32, a.cap);
+  const int mode = a.alpha == 0.5 ? 0 : 1;
+  if (acc == ACC_MIN) return fp32 ? launch_one<float, ACC_MIN, 0>(a, smem, st) : launch_one<double, ACC_MIN, 0>(a, smem, st);
+  if (fp32) return mode == 0 ? launch_one<float, ACC_GEN, 0>(a, smem, st) : launch_one<float, ACC_GEN, 1>(a, smem, st);
+  return mode == 0 ? launch_one<double, ACC_GEN, 0>(a, smem, st) : launch_one<double, ACC_GEN, 1>(a, smem, st);
+}
+
+}  // namespace ufg

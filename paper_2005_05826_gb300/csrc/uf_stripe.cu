@@ -41,7 +41,7 @@
 #include <cfloat>
 #include <type_traits>
 
-#include "uf_internal.h"
+#include "uf_device.cuh"
 
 namespace ufg {
 
@@ -88,40 +88,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-template <typename T>
-__device__ __forceinline__ T tmin(T a, T b);
-template <>
-__device__ __forceinline__ float tmin<float>(float a, float b) { return fminf(a, b); }
-template <>
-__device__ __forceinline__ double tmin<double>(double a, double b) { return fmin(a, b); }
-
-// FP64 s^(alpha - 1) for s > 0 (s == 0 terms are zeroed by the caller)
-template <typename T, int MODE>
-__device__ __forceinline__ T gen_pow(T s, T am1);
-template <>
-__device__ __forceinline__ double gen_pow<double, 0>(double s, double) { return rsqrt(fmax(s, 1e-300)); }
-template <>
-__device__ __forceinline__ double gen_pow<double, 1>(double s, double am1) { return pow(fmax(s, 1e-300), am1); }
-
-// s^(alpha - 1) on the SFU for FP32 s >= 1e-30 (never denormal):
-// MODE 0 (alpha = 1/2) one reciprocal square root; MODE 1 exp2((alpha - 1) log2 s).
-template <int MODE>
-__device__ __forceinline__ float sfu_pow(float s, float am1) {
-  float r;
-  if (MODE == 0) {
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
-  } else {
-    float lg;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(s));
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(lg * am1));
-  }
-  return r;
-}
-
-// fixed point: round x * 2^F to the nearest integer
-__device__ __forceinline__ long long to_fixed(float x, double scale) { return __float2ll_rn(x * (float)scale); }
-__device__ __forceinline__ long long to_fixed(double x, double scale) { return __double2ll_rn(x * scale); }
 
 struct Unit {
   int r0, r1;       // branch rows

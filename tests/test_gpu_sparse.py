@@ -1,0 +1,220 @@
+"""GPU parity of the sparse-row path: branches whose subtree holds few count
+entries are scattered pair by pair over their nonzero samples instead of
+running through the dense stripe kernels (option "sparse").
+
+Every case is checked against the FP64 oracle with "sparse" = 0 (all dense),
+1 (cost model) and 2 (every branch that can be scattered), for every method
+and precision: capacity classes, stripe ranges including the duplicated
+half stripe, batches of uneven tables, identical samples, and trees whose
+tip numbers under a node are not contiguous (those nodes stay dense).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2005_05826_gb300 as uf
+from synth import Table as STable, pair_subset, table_iid, table_prevalence, workload, yule_tree
+from tests.gpu_util import METHODS, assert_close, condensed_index
+from tests.test_oracle_pins import random_small_tree, random_table_for
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PRECISIONS = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2005_05826_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    yield
+    uf.uf_set_option("sparse", 1)
+
+
+def handles(tree_s, table_s):
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
+    return tree, table
+
+
+def run(tree, table, method, alpha, precision, mode, *args):
+    uf.uf_set_option("sparse", mode)
+    try:
+        return uf.uf_compute(tree, table, method, alpha, precision, *args)
+    finally:
+        uf.uf_set_option("sparse", 1)
+
+
+def test_option_values():
+    assert uf.uf_get_option("sparse") == 1
+    for bad in (-1, 3):
+        with pytest.raises(uf.UFError):
+            uf.uf_set_option("sparse", bad)
+    assert uf.uf_get_option("sparse") == 1
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("method", METHODS)
+def test_all_modes_match_oracle(method, precision):
+    tree_s = yule_tree(2000, seed=201)
+    table_s = table_prevalence(160, tree_s.n_tips, 0.5, 10.0, seed=202)
+    tree, table = handles(tree_s, table_s)
+    a = 0.5 if method == "generalized" else 1.0
+    exp = oracle.condensed(tree_s, table_s, method, a)
+    nb = tree_s.n_nodes - 1
+    for mode in (0, 1, 2):
+        got, rep = run(tree, table, method, a, precision, mode)
+        assert_close(got, exp, method, precision, f"sparse={mode}")
+        if method == "unweighted" and precision == "mixed":
+            continue  # tensor path: the sparse split is not applied there
+        assert rep.dense_rows + rep.sparse_rows == nb
+        if mode == 0:
+            assert rep.sparse_rows == 0
+        else:
+            assert rep.sparse_rows > 0
+        if mode == 2:
+            # a postorder tree: every branch whose subtree fits is scattered
+            assert rep.sparse_rows >= nb // 2
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.25, 0.5, 0.75, 1.0])
+def test_generalized_alphas(alpha):
+    tree_s = yule_tree(700, seed=211)
+    table_s = table_iid(90, tree_s.n_tips, 0.04, seed=212)
+    tree, table = handles(tree_s, table_s)
+    exp = oracle.condensed(tree_s, table_s, "generalized", alpha)
+    for precision in PRECISIONS:
+        got, rep = run(tree, table, "generalized", alpha, precision, 2)
+        assert rep.sparse_rows > 0
+        assert_close(got, exp, "generalized", precision, f"alpha={alpha}")
+
+
+def test_capacity_classes():
+    # dense tables give subtrees of every entry count from 1 up past 4,096:
+    # each capacity class (128, 512, 2,048, 4,096 entries) gets rows, and the
+    # rows above the largest class stay dense
+    tree_s = yule_tree(400, seed=221)
+    table_s = table_iid(300, tree_s.n_tips, 0.3, seed=222)
+    tree, table = handles(tree_s, table_s)
+    for method in METHODS:
+        a = 0.5 if method == "generalized" else 1.0
+        exp = oracle.condensed(tree_s, table_s, method, a)
+        for precision in PRECISIONS:
+            if method == "unweighted" and precision == "mixed":
+                uf.uf_set_option("tensor_path", 0)
+            try:
+                got, rep = run(tree, table, method, a, precision, 2)
+            finally:
+                uf.uf_set_option("tensor_path", 1)
+            assert 0 < rep.sparse_rows < tree_s.n_nodes - 1
+            assert_close(got, exp, method, precision, "capacity classes")
+
+
+@pytest.mark.parametrize("n", [2, 3, 8, 9, 64, 65, 300])
+def test_stripe_ranges_and_duplicate_half_stripe(n):
+    tree_s = yule_tree(150, seed=230 + n)
+    table_s = table_iid(n, tree_s.n_tips, 0.15, seed=231 + n)
+    tree, table = handles(tree_s, table_s)
+    S = uf.uf_stripe_count(n)
+    cuts = sorted({0, 1, S // 2, S - 1, S})
+    uf.uf_set_option("tensor_path", 0)
+    try:
+        for method in ["unweighted", "weighted_unnormalized", "generalized"]:
+            _, _, exp_striped, _ = oracle.striped(tree_s, table_s, method, 0.5, 0, S)
+            exp_full = oracle.condensed(tree_s, table_s, method, 0.5)
+            for precision in PRECISIONS:
+                whole, _ = run(tree, table, method, 0.5, precision, 2)
+                assert_close(whole, exp_full, method, precision, "full run")
+                parts = []
+                for a, b in zip(cuts[:-1], cuts[1:]):
+                    if a == b or (a, b) == (0, S):
+                        continue
+                    got, _ = run(tree, table, method, 0.5, precision, 2, a, b)
+                    assert got.shape == (b - a, n)
+                    # the last stripe of an even n holds every pair twice
+                    assert_close(got.ravel(), exp_striped[a:b].ravel(), method, precision, f"range [{a},{b})")
+                    parts.append(got)
+                if S > 1:
+                    # stripes are independent: the pieces equal a range run of everything
+                    alln, _ = run(tree, table, method, 0.5, precision, 2, 0, S - 1)
+                    np.testing.assert_array_equal(np.vstack(parts)[: S - 1], alln)
+    finally:
+        uf.uf_set_option("tensor_path", 1)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_identical_samples_exactly_zero(precision):
+    tree_s = yule_tree(300, seed=241)
+    t = table_iid(40, tree_s.n_tips, 0.05, seed=242)
+    counts = t.dense()
+    counts[5] = counts[17]
+    counts[33] = counts[17] * 3.0
+    table_s = STable.from_dense(counts)
+    tree, table = handles(tree_s, table_s)
+    n = table_s.n_samples
+    pairs = [(5, 17)] + ([(17, 33), (5, 33)] if precision == "fp64" else [])
+    for method in METHODS:
+        for alpha in ([0.0, 0.5, 0.75] if method == "generalized" else [1.0]):
+            got, rep = run(tree, table, method, alpha, precision, 2)
+            for i, j in pairs:
+                d = got[condensed_index(n, i, j)]
+                assert d == 0.0, (method, alpha, i, j, d)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_batch_of_uneven_tables(method):
+    tree_s = yule_tree(500, seed=250)
+    sizes = (7, 1, 64, 130, 2, 257, 33)
+    tables_s = [table_iid(n, tree_s.n_tips, 0.05, seed=251 + n) for n in sizes]
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    tables = [uf.Table(t.indptr, t.indices, t.data, tree) for t in tables_s]
+    a = 0.5 if method == "generalized" else 1.0
+    for mode in (1, 2):
+        uf.uf_set_option("sparse", mode)
+        try:
+            for precision in PRECISIONS:
+                outs, reps = uf.uf_compute_batch(tree, tables, method, a, precision)
+                for t_s, o, rep in zip(tables_s, outs, reps):
+                    if t_s.n_samples < 2:
+                        continue
+                    exp = oracle.condensed(tree_s, t_s, method, a)
+                    assert_close(o, exp, method, precision, f"batch n={t_s.n_samples} sparse={mode}")
+        finally:
+            uf.uf_set_option("sparse", 1)
+
+
+def interleaved_tree(rng, n_tips):
+    """A valid parent array (parent > child) whose nodes are numbered in a
+    random children-before-parents order, so subtrees are interleaved and the
+    tips under most internal nodes are not a contiguous run of tip numbers."""
+    return random_small_tree(rng, n_tips, unary=2, zero_len=2)
+
+
+def test_interleaved_numbering_stays_correct():
+    rng = np.random.default_rng(260)
+    for case in range(4):
+        tree_s = interleaved_tree(rng, int(rng.integers(20, 80)))
+        table_s = random_table_for(rng, tree_s, int(rng.integers(5, 70)), density=0.2)
+        tree, table = handles(tree_s, table_s)
+        for method in METHODS:
+            a = 0.5 if method == "generalized" else 1.0
+            exp = oracle.condensed(tree_s, table_s, method, a)
+            for precision in PRECISIONS:
+                got, rep = run(tree, table, method, a, precision, 2)
+                assert_close(got, exp, method, precision, f"interleaved case {case}")
+
+
+def test_yule50k_n2048_default_split():
+    tree_s, table_s = workload("yule50k_n2048")
+    tree, table = handles(tree_s, table_s)
+    n = table_s.n_samples
+    i, j = pair_subset(n, 10_000, seed=12345)
+    for method in ["weighted_normalized", "generalized"]:
+        a = 0.5 if method == "generalized" else 1.0
+        exp = oracle.pairs(tree_s, table_s, method, a, i, j)[0]
+        for precision in PRECISIONS:
+            got, rep = run(tree, table, method, a, precision, 1)
+            assert rep.sparse_rows > (tree_s.n_nodes - 1) // 3, rep.sparse_rows
+            assert_close(got[condensed_index(n, i, j)], exp, method, precision, "yule50k sparse=1")

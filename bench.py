@@ -390,9 +390,28 @@ def run_ours(args, rank, world, local_rank):
     mixed_outs = [o.cpu().numpy() for o in outs]
     launches = int(sum(r.kernels for _, r in reps))
 
+    # the same steps with per-phase timing off (each call is then one CUDA
+    # graph launch and does not wait for its events): the host overhead of
+    # the phase timing is the difference
+    uf.uf_set_option("kernel_timing", 0)
+    for _ in range(2):
+        step("mixed")
+    t_plain = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step("mixed")
+        e1.record(stream)
+        e1.synchronize()
+        t_plain.append(e0.elapsed_time(e1))
+    uf.uf_set_option("kernel_timing", 1)
+
     # per-kernel roofline of the accumulate launches (timed inside the steps)
     acc_ms = {}
     sparse = {}
+    phases = {}  # device ms per call and phase (CUDA events on the call's stream)
     for m, r in reps:
         d = acc_ms.setdefault(m, [0.0, 0, 0, 0.0, 0, 0])
         d[0] += r.t_accumulate_ms
@@ -404,6 +423,11 @@ def run_ours(args, rank, world, local_rank):
         sp = sparse.setdefault(m, {"rows": r.sparse_rows, "dense_rows": d[5], "pairs_at_most": r.sparse_pairs,
                                    "ms_per_call": 0.0})
         sp["ms_per_call"] += r.t_sparse_ms / args.steps
+        ph = phases.setdefault(m, {"embed": 0.0, "accumulate": 0.0, "diagonal": 0.0, "sparse": 0.0,
+                                   "finalize": 0.0})
+        for key, val in (("embed", r.t_embed_ms), ("accumulate", r.t_accumulate_ms), ("diagonal", r.t_diag_ms),
+                         ("sparse", r.t_sparse_ms), ("finalize", r.t_finalize_ms)):
+            ph[key] += val / args.steps
     kern = {}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     for m, (ms, nl, ncalls, xflops, path, drows) in acc_ms.items():
@@ -549,6 +573,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": rl,
         "kernels": kern,
         "sparse_rows": sparse,
+        "phases_ms_per_call": phases,
+        "ms_per_step_without_phase_timing": statistics.mean(t_plain),
         "peak_source": peak_src,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -28,6 +28,29 @@ __global__ void k_tip_counts(const int32_t *__restrict__ tip_nodes,
   for (int64_t q = col_ptr[f] + threadIdx.x; q < q1; q += blockDim.x) row[col_row[q]] = col_val[q];
 }
 
+// One CTA per node of a list: zero the table's part of the node's count
+// slot, then add the CSC columns of its tips [tip_lo, tip_hi) one after the
+// other (within one tip's column the samples are distinct, so its entries
+// scatter without conflicts).  Serves tips and the nodes whose own subtree
+// is not walked level by level (a branch scattered by the sparse-row path
+// whose parent runs through the dense kernels).
+__global__ void k_slice_counts(const int32_t *__restrict__ nodes, const int32_t *__restrict__ tip_lo,
+                               const int32_t *__restrict__ tip_hi, const int32_t *__restrict__ slot_of_node,
+                               const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ col_row,
+                               const double *__restrict__ col_val, double *__restrict__ counts, int64_t ld,
+                               int n) {
+  const int v = nodes[blockIdx.x];
+  double *row = counts + (int64_t)slot_of_node[v] * ld;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) row[k] = 0.0;
+  __syncthreads();
+  const int f1 = tip_hi[v];
+  for (int f = tip_lo[v]; f < f1; f++) {
+    const int64_t q1 = col_ptr[f + 1];
+    for (int64_t q = col_ptr[f] + threadIdx.x; q < q1; q += blockDim.x) row[col_row[q]] += col_val[q];
+    __syncthreads();
+  }
+}
+
 // count[v][k] = sum of the children's count[c][k], children in index order
 // (the order the postorder walk adds them in), over all ld columns.
 // grid.x = nodes, grid.y = sample chunks.
@@ -86,6 +109,15 @@ cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_
   if (n_list <= 0) return cudaSuccess;
   k_tip_counts<<<n_list, 256, 0, st>>>(tip_nodes, slot_of_node, tip_of_node, col_ptr, col_row,
                                        col_val, counts, ld, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_counts(const int32_t *nodes, int n_list, const int32_t *tip_lo, const int32_t *tip_hi,
+                                const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
+                                const double *col_val, double *counts, int64_t ld, int n, cudaStream_t st) {
+  if (n_list <= 0) return cudaSuccess;
+  k_slice_counts<<<n_list, 256, 0, st>>>(nodes, tip_lo, tip_hi, slot_of_node, col_ptr, col_row, col_val, counts,
+                                         ld, n);
   return cudaGetLastError();
 }
 

@@ -99,6 +99,10 @@ struct Plan {
   std::map<int, Dev> dev;
 };
 
+struct RowSplit;
+// (table ids, accumulator, FP32, sparse mode, block rows)
+using SplitKey = std::tuple<std::vector<uint64_t>, int, int, int, int64_t>;
+
 }  // namespace
 
 struct uf_tree {
@@ -118,6 +122,7 @@ struct uf_tree {
   };
   std::map<int, Dev> dev;
   std::map<int64_t, std::unique_ptr<Plan>> plans;  // by block rows
+  std::map<SplitKey, std::shared_ptr<const RowSplit>> splits;  // dense / sparse branch splits
   // root distance of every node (root: 0), max over tips, total branch length
   std::vector<double> dist;
   double max_tip_dist = 0.0, total_length = 0.0;
@@ -144,6 +149,7 @@ struct uf_tree {
 };
 
 struct uf_table {
+  uint64_t id = 0;                 // process-unique, never reused
   int64_t n = 0, n_features = 0, nnz = 0;
   std::vector<double> total;       // per-sample count totals (row order sums)
   std::vector<float> inv_total_f;  // 1 / total in FP32
@@ -319,6 +325,84 @@ struct DevBuf {
   }
   template <typename T>
   T *as() const { return (T *)p; }
+};
+
+// Pinned staging for the per-call metadata uploads (table descriptors, row
+// lists): a cudaMemcpyAsync from pageable memory first waits for all earlier
+// work on the stream, one from pinned memory does not, so consecutive calls
+// on one stream overlap their host work with the previous call's kernels.
+// One ring per process; a region is reused only after the event recorded
+// behind its copy has completed.  The buffer lives until the process ends.
+struct Staging {
+  std::mutex mu;
+  char *buf = nullptr;
+  size_t cap = 0, head = 0;
+  std::vector<std::tuple<size_t, size_t, cudaEvent_t>> live;  // [begin, end) copies in flight
+};
+Staging g_stage;
+
+void staged_upload(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return;
+  Staging &S = g_stage;
+  std::lock_guard<std::mutex> g(S.mu);
+  const size_t need = (bytes + 255) & ~(size_t)255;
+  auto retire = [&](bool all, size_t b, size_t e) {
+    for (size_t i = 0; i < S.live.size();) {
+      const size_t lb = std::get<0>(S.live[i]), le = std::get<1>(S.live[i]);
+      cudaEvent_t ev = std::get<2>(S.live[i]);
+      const bool overlap = all || (lb < e && b < le);
+      if (overlap) ck(cudaEventSynchronize(ev), "staging wait");
+      if (overlap || cudaEventQuery(ev) == cudaSuccess) {
+        cudaEventDestroy(ev);
+        S.live[i] = S.live.back();
+        S.live.pop_back();
+      } else {
+        cudaGetLastError();  // cudaErrorNotReady is not an error here
+        i++;
+      }
+    }
+  };
+  if (need > S.cap) {
+    retire(true, 0, 0);
+    if (S.buf) cudaFreeHost(S.buf);
+    S.buf = nullptr;
+    S.cap = 0;
+    const size_t cap = std::max<size_t>(need, (size_t)16 << 20);
+    ck(cudaMallocHost((void **)&S.buf, cap), "alloc pinned staging");
+    S.cap = cap;
+    S.head = 0;
+  }
+  if (S.head + need > S.cap) S.head = 0;
+  const size_t b = S.head, e = b + need;
+  retire(false, b, e);
+  memcpy(S.buf + b, src, bytes);
+  ck(cudaMemcpyAsync(dst, S.buf + b, bytes, cudaMemcpyHostToDevice, st), "upload");
+  cudaEvent_t ev;
+  ck(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
+  ck(cudaEventRecord(ev, st), "cudaEventRecord");
+  S.live.emplace_back(b, e, ev);
+  S.head = e;
+}
+
+// Per-call metadata packed into one device buffer with one staged upload.
+struct Meta {
+  std::vector<char> host;
+  template <typename T>
+  size_t add(const T *p, size_t n) {
+    const size_t off = (host.size() + 255) & ~(size_t)255;
+    host.resize(off + std::max<size_t>(n * sizeof(T), 1));
+    if (n) memcpy(host.data() + off, p, n * sizeof(T));
+    return off;
+  }
+  template <typename T>
+  size_t add(const std::vector<T> &v) { return add(v.data(), v.size()); }
+  DevBuf dev;
+  void upload(cudaStream_t st) {
+    dev = DevBuf(host.size(), st, "alloc call metadata");
+    staged_upload(dev.p, host.data(), host.size(), st);
+  }
+  template <typename T>
+  T *at(size_t off) const { return (T *)((char *)dev.p + off); }
 };
 
 void keep_pool_memory(int device) {
@@ -589,6 +673,11 @@ struct RowSplit {
   int64_t n_sparse = 0;
   double pairs = 0.0;               // both-nonzero pairs scattered, at most (sum over tables)
   int64_t max_dense = 0;            // most dense rows in one block
+  // count rows the call needs: per block, a list of nodes built from their
+  // tips' CSC columns (tips, and sparse branches under a dense parent), then
+  // the dense internal nodes level by level; offsets into cnt_lists
+  std::vector<int32_t> cnt_lists;
+  std::vector<std::vector<std::pair<int64_t, int>>> cnt_launch;
 };
 
 // Per branch v the count entries of table t under v are the CSC run of v's
@@ -616,7 +705,7 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
       const double n = (double)J.tabs[t].table->n;
       cells += std::floor(n / 2.0) * n;
     }
-    const double atom_rate = cells * 8.0 * n_acc <= 64e6 ? 1.5e11 : 2.5e10;
+    const double atom_rate = cells * 8.0 * n_acc <= 64e6 ? 2.3e11 : 2.5e10;
     const double dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
     const double visit_rate = fp32 ? 2e12 : (acc == ACC_GEN ? 3e10 : 1e12);
     const double job_cost = 5e-10;
@@ -646,6 +735,38 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
       }
     }
   }
+  const int64_t root = tree->n_nodes - 1;
+  auto parent_dense = [&](int64_t v) {
+    const int64_t p = tree->parent[v];
+    return p != root && !is_sparse[p];
+  };
+  for (size_t b = 0; b < P->b0.size(); b++) {
+    const auto &ls = P->launches[b];
+    std::vector<std::pair<int64_t, int>> lb;
+    std::vector<int32_t> level;
+    // nodes built from CSC columns
+    level.clear();
+    for (size_t l = 0; l < ls.size(); l++)
+      for (int i = 0; i < ls[l].second; i++) {
+        const int32_t v = P->lists[ls[l].first + i];
+        const bool tip = l == 0;
+        if (is_sparse[v] ? parent_dense(v) : tip) level.push_back(v);
+      }
+    lb.emplace_back((int64_t)R.cnt_lists.size(), (int)level.size());
+    R.cnt_lists.insert(R.cnt_lists.end(), level.begin(), level.end());
+    // dense internal nodes by level
+    for (size_t l = 1; l < ls.size(); l++) {
+      level.clear();
+      for (int i = 0; i < ls[l].second; i++) {
+        const int32_t v = P->lists[ls[l].first + i];
+        if (!is_sparse[v]) level.push_back(v);
+      }
+      if (level.empty()) continue;
+      lb.emplace_back((int64_t)R.cnt_lists.size(), (int)level.size());
+      R.cnt_lists.insert(R.cnt_lists.end(), level.begin(), level.end());
+    }
+    R.cnt_launch.push_back(std::move(lb));
+  }
   R.dense_ptr.push_back(0);
   for (size_t b = 0; b < P->b0.size(); b++) {
     for (int64_t v = P->b0[b]; v < P->b1[b]; v++)
@@ -657,6 +778,24 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
     R.max_dense = std::max(R.max_dense, R.dense_ptr[b + 1] - R.dense_ptr[b]);
   }
   return R;
+}
+
+// The split of a call, cached on the tree by its tables and kind (tables are
+// immutable and their ids are never reused).
+std::shared_ptr<const RowSplit> get_split(uf_tree *tree, const BatchJob &J, const Plan *P, int acc, bool fp32) {
+  SplitKey key;
+  for (const TableJob &t : J.tabs) std::get<0>(key).push_back(t.table->id);
+  std::get<1>(key) = acc;
+  std::get<2>(key) = fp32 ? 1 : 0;
+  std::get<3>(key) = (int)g_sparse.load();
+  std::get<4>(key) = P->block_rows;
+  std::lock_guard<std::mutex> g(tree->mu);
+  auto it = tree->splits.find(key);
+  if (it != tree->splits.end()) return it->second;
+  if (tree->splits.size() >= 16) tree->splits.clear();
+  auto sp = std::make_shared<const RowSplit>(split_rows(tree, J, P, acc, fp32));
+  tree->splits.emplace(key, sp);
+  return sp;
 }
 
 // Output buffers: the caller's device memory, or a device staging buffer
@@ -760,11 +899,12 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
   DevBuf counts((size_t)in.P->n_slots * n_cols * 8, st, "alloc counts");
   DevBuf Pl((size_t)4 * npad_tot * K_pad * 2, st, "alloc presence planes");
   DevBuf Gt((size_t)gt_cells * 8, st, "alloc gram");
-  DevBuf d_tiles(tl.size() * 4, st, "alloc tile list");
-  DevBuf d_tabs(nt * sizeof(GramTab), st, "alloc table list");
   DevBuf err(sizeof(int), st, "alloc error flag");
-  ck(cudaMemcpyAsync(d_tiles.p, tl.data(), tl.size() * 4, cudaMemcpyHostToDevice, st), "copy tiles");
-  ck(cudaMemcpyAsync(d_tabs.p, gt.data(), nt * sizeof(GramTab), cudaMemcpyHostToDevice, st), "copy tables");
+  Meta meta;  // tile list and table descriptors: one staged upload
+  const size_t o_tiles = meta.add(tl), o_tabs = meta.add(gt);
+  meta.upload(st);
+  const int32_t *d_tiles = meta.at<int32_t>(o_tiles);
+  const GramTab *d_tabs = meta.at<GramTab>(o_tabs);
   ck(cudaMemsetAsync(Gt.p, 0, (size_t)gt_cells * 8, st), "memset");
   ck(cudaMemsetAsync(err.p, 0, sizeof(int), st), "memset");
   Outputs o = bind_outputs(J, st);
@@ -776,7 +916,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
     timer.begin(0);
     enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, ls, &kernels);
     ck(launch_gram_prep(b0, (int)(b1 - b0), in.pd->slot_of_node, counts.as<double>(), n_cols, in.td->length,
-                        d_tabs.as<GramTab>(), (int)nt, npad_tot, K_pad, Pl.p, ls),
+                        d_tabs, (int)nt, npad_tot, K_pad, Pl.p, ls),
        "presence planes");
     kernels++;
     timer.end();
@@ -785,10 +925,10 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
     ga.kc = 4096;
     ga.n_tiles = n_tiles;
     ga.npad_tot = npad_tot;
-    ga.tile_tab = d_tiles.as<int32_t>();
-    ga.tile_bi = d_tiles.as<int32_t>() + n_tiles;
-    ga.tile_bj = d_tiles.as<int32_t>() + 2 * n_tiles;
-    ga.tabs = d_tabs.as<GramTab>();
+    ga.tile_tab = d_tiles;
+    ga.tile_bi = d_tiles + n_tiles;
+    ga.tile_bj = d_tiles + 2 * n_tiles;
+    ga.tabs = d_tabs;
     ga.Gt = Gt.as<unsigned long long>();
     ga.scale = scale;
     ga.err = err.as<int>();
@@ -823,8 +963,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
   counts = DevBuf();
   Pl = DevBuf();
   Gt = DevBuf();
-  d_tiles = DevBuf();
-  d_tabs = DevBuf();
+  meta.dev = DevBuf();
   o.tmp.clear();
   ck(cudaStreamSynchronize(st), "synchronize");  // the error flag is read here
   err = DevBuf();
@@ -880,7 +1019,8 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + (double)pitch * es + 8.0 + n_cols * es / 64.0, acc_bytes);
   Inputs in = bind_inputs(tree, J, device, rows);
   cudaStream_t st = J.st;
-  const RowSplit split = split_rows(tree, J, in.P, acc, fp32);
+  const std::shared_ptr<const RowSplit> split_p = get_split(tree, J, in.P, acc, fp32);
+  const RowSplit &split = *split_p;
   const int64_t xrows = std::max<int64_t>(split.max_dense, 1);
   int64_t kernels = 0, acc_launches = 0;
   PhaseTimer timer(g_kernel_timing.load() != 0, st);
@@ -888,19 +1028,15 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   DevBuf X((size_t)xrows * pitch * es, st, "alloc embeddings");
   DevBuf M((size_t)cells * 8, st, "alloc stripes");
   DevBuf M2, Dg, Dsp, diag_tmp, counter(sizeof(int), st, "alloc counter");
-  DevBuf d_tabs(nt * sizeof(TabDesc), st, "alloc table list");
   DevBuf total((size_t)n_cols * 8, st, "alloc totals"), inv_total((size_t)n_cols * 4, st, "alloc totals");
-  DevBuf d_dense(std::max<size_t>(split.dense.size(), 1) * 4, st, "alloc row lists");
-  DevBuf d_dlen(std::max<size_t>(split.dense_len.size(), 1) * 8, st, "alloc row lists");
-  DevBuf d_sparse, d_sptabs;
-  ck(cudaMemcpyAsync(d_tabs.p, tabs.data(), nt * sizeof(TabDesc), cudaMemcpyHostToDevice, st), "copy tables");
-  if (!split.dense.empty()) {
-    ck(cudaMemcpyAsync(d_dense.p, split.dense.data(), split.dense.size() * 4, cudaMemcpyHostToDevice, st),
-       "copy row lists");
-    ck(cudaMemcpyAsync(d_dlen.p, split.dense_len.data(), split.dense_len.size() * 8, cudaMemcpyHostToDevice, st),
-       "copy row lists");
-  }
-  std::vector<int64_t> sp_off;  // first entry of each capacity class in d_sparse
+  // table descriptors and row lists: one staged upload
+  Meta meta;
+  const size_t o_tabs = meta.add(tabs);
+  const size_t o_cnt = meta.add(split.cnt_lists);
+  const size_t o_dense = meta.add(split.dense);
+  const size_t o_dlen = meta.add(split.dense_len);
+  size_t o_sparse = 0, o_sptabs = 0;
+  std::vector<int64_t> sp_off;  // first entry of each capacity class in the sparse list
   if (split.n_sparse > 0) {
     std::vector<int32_t> all;
     for (const auto &c : split.sparse) {
@@ -920,13 +1056,16 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
       sp[t].s_hi = tabs[t].s_hi;
       sp[t].m_off = tabs[t].m_off;
     }
-    d_sparse = DevBuf(all.size() * 4, st, "alloc row lists");
-    d_sptabs = DevBuf(nt * sizeof(SpTab), st, "alloc table list");
-    ck(cudaMemcpyAsync(d_sparse.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice, st), "copy row lists");
-    ck(cudaMemcpyAsync(d_sptabs.p, sp.data(), nt * sizeof(SpTab), cudaMemcpyHostToDevice, st), "copy tables");
+    o_sparse = meta.add(all);
+    o_sptabs = meta.add(sp);
     Dsp = DevBuf((size_t)n_cols * 8, st, "alloc diagonal");
     ck(cudaMemsetAsync(Dsp.p, 0, (size_t)n_cols * 8, st), "memset");
   }
+  meta.upload(st);
+  const TabDesc *d_tabs = meta.at<TabDesc>(o_tabs);
+  const int32_t *d_cnt = meta.at<int32_t>(o_cnt);
+  const int32_t *d_dense = meta.at<int32_t>(o_dense);
+  const double *d_dlen = meta.at<double>(o_dlen);
   for (size_t t = 0; t < nt; t++) {
     const size_t n = (size_t)J.tabs[t].table->n;
     ck(cudaMemcpyAsync(total.as<double>() + off[t], in.xd[t]->total, n * 8, cudaMemcpyDeviceToDevice, st),
@@ -964,11 +1103,26 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     const int64_t b0 = in.P->b0[b];
     const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
     timer.begin(0);
-    enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, ls, &kernels);
+    {
+      const auto &lb = split.cnt_launch[b];
+      for (size_t t = 0; t < nt; t++) {
+        ck(launch_slice_counts(d_cnt + lb[0].first, lb[0].second, in.td->tip_lo, in.td->tip_hi,
+                               in.pd->slot_of_node, in.xd[t]->col_ptr, in.xd[t]->col_row, in.xd[t]->col_val,
+                               counts.as<double>() + off[t], n_cols, (int)J.tabs[t].table->n, ls),
+           "count rows");
+        kernels += lb[0].second > 0;
+      }
+      for (size_t l = 1; l < lb.size(); l++) {
+        ck(launch_node_counts(d_cnt + lb[l].first, lb[l].second, in.td->child_ptr,
+                              in.td->child_idx, in.pd->slot_of_node, counts.as<double>(), n_cols, ls),
+           "node counts");
+        kernels++;
+      }
+    }
     if (nd > 0) {
       ck(launch_emb_rows(kind, fp32, b0, (int)nd, in.pd->slot_of_node, counts.as<double>(), n_cols,
                          in.td->length, total.as<double>(), inv_total.as<float>(), X.p, pitch,
-                         d_tabs.as<TabDesc>(), (int)nt, ls, d_dense.as<int32_t>() + d0),
+                         d_tabs, (int)nt, ls, d_dense + d0),
          "embedding rows");
       kernels++;
     }
@@ -976,11 +1130,11 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     if (nd == 0) continue;
     StripeArgs sa{};
     sa.X = X.p;
-    sa.len = d_dlen.as<double>() + d0;
+    sa.len = d_dlen + d0;
     sa.rows = (int)nd;
     sa.pitch = pitch;
     sa.chunk = chunk;
-    sa.tabs = d_tabs.as<TabDesc>();
+    sa.tabs = d_tabs;
     sa.n_tabs = (int)nt;
     sa.n_tiles = n_tiles;
     sa.n_cols = n_cols;
@@ -1015,13 +1169,13 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     for (size_t c = 0; c < split.sparse.size(); c++) {
       if (split.sparse[c].empty()) continue;
       SparseArgs sp{};
-      sp.nodes = d_sparse.as<int32_t>() + sp_off[c];
+      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
       sp.n_nodes = (int)split.sparse[c].size();
       sp.cap = split.cap[c];
       sp.tip_lo = in.td->tip_lo;
       sp.tip_hi = in.td->tip_hi;
       sp.length = in.td->length;
-      sp.tabs = d_sptabs.as<SpTab>();
+      sp.tabs = meta.at<SpTab>(o_sptabs);
       sp.n_tabs = (int)nt;
       sp.kind = kind;
       sp.mixed_forms = fp32 && acc == ACC_MIN;
@@ -1068,11 +1222,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   Dsp = DevBuf();
   diag_tmp = DevBuf();
   counter = DevBuf();
-  d_tabs = DevBuf();
-  d_dense = DevBuf();
-  d_dlen = DevBuf();
-  d_sparse = DevBuf();
-  d_sptabs = DevBuf();
+  meta.dev = DevBuf();
   total = DevBuf();
   inv_total = DevBuf();
   o.tmp.clear();
@@ -1304,6 +1454,8 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
     }
   try {
     auto t = std::make_unique<uf_table>();
+    static std::atomic<uint64_t> next_id{1};
+    t->id = next_id++;
     t->n = n_samples;
     t->n_features = n_features;
     t->nnz = nnz;

@@ -58,6 +58,11 @@ cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_
                               const int32_t *tip_of_node, const int64_t *col_ptr,
                               const int32_t *col_row, const double *col_val, double *counts,
                               int64_t ld, int n, cudaStream_t st);
+// Count rows of listed nodes straight from the CSC columns of their tips
+// (tip numbers [tip_lo[v], tip_hi[v]), in order).
+cudaError_t launch_slice_counts(const int32_t *nodes, int n_list, const int32_t *tip_lo, const int32_t *tip_hi,
+                                const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
+                                const double *col_val, double *counts, int64_t ld, int n, cudaStream_t st);
 cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
                                const int32_t *child_idx, const int32_t *slot_of_node,
                                double *counts, int64_t ld, cudaStream_t st);

@@ -135,9 +135,11 @@ def kernel_traffic(kernel_key: str):
         ent = d.get(kernel_key)
         if not ent:
             return None
-        src = os.path.join(ROOT, ent["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if h != ent.get("source_sha256_16"):
+        h = hashlib.sha256()
+        for src in ent["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] != ent.get("sources_sha256_16"):
             return None
         return ent["dram_bytes_per_launch_scaled"]
     except (OSError, KeyError, ValueError):
@@ -419,7 +421,7 @@ def run_ours(args, rank, world, local_rank):
         d[2] += 1
         d[3] += r.exec_flops
         d[4] = r.path
-        d[5] = r.dense_rows if r.path == 0 else branches
+        d[5] = r.dense_rows
         sp = sparse.setdefault(m, {"rows": r.sparse_rows, "dense_rows": d[5], "pairs_at_most": r.sparse_pairs,
                                    "ms_per_call": 0.0})
         sp["ms_per_call"] += r.t_sparse_ms / args.steps

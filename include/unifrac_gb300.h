@@ -132,8 +132,9 @@ typedef struct {
  *                    faster; 0: every branch through the dense kernels;
  *                    2: every branch that can be scattered is (subtree with
  *                    at most 4,096 entries per table and contiguous tip
- *                    numbers).  Applies to the CUDA-core stripe path; the
- *                    results agree within the precision's tolerance.
+ *                    numbers).  Applies to the CUDA-core stripe kernels and
+ *                    to the tensor-core unweighted path; the results agree
+ *                    within the precision's tolerance.
  * uf_set_option returns UF_EINVAL for an unknown name or a bad value;
  * uf_get_option returns -1 for an unknown name.
  */

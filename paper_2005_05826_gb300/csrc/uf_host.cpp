@@ -642,26 +642,6 @@ int64_t block_rows(int64_t nb, double per_row, double fixed) {
   return std::max<int64_t>(rows, 1);
 }
 
-// Tip counts of one block for every table (each into its columns), then the
-// internal levels over the combined axis.
-void enqueue_counts(const Inputs &in, const BatchJob &J, const std::vector<int> &off, size_t b, double *counts,
-                    int64_t ld, cudaStream_t st, int64_t *kernels) {
-  const auto &ls = in.P->launches[b];
-  for (size_t t = 0; t < J.tabs.size(); t++) {
-    ck(launch_tip_counts(in.pd->lists + ls[0].first, ls[0].second, in.pd->slot_of_node, in.td->tip_of_node,
-                         in.xd[t]->col_ptr, in.xd[t]->col_row, in.xd[t]->col_val, counts + off[t], ld,
-                         (int)J.tabs[t].table->n, st),
-       "tip counts");
-    *kernels += ls[0].second > 0;
-  }
-  for (size_t l = 1; l < ls.size(); l++) {
-    ck(launch_node_counts(in.pd->lists + ls[l].first, ls[l].second, in.td->child_ptr, in.td->child_idx,
-                          in.pd->slot_of_node, counts, ld, st),
-       "node counts");
-    *kernels += ls[l].second > 0;
-  }
-}
-
 // Branches of a call split between the dense stripe kernels and the
 // sparse-row pair kernel (uf_sparse.cu).
 struct RowSplit {
@@ -689,6 +669,8 @@ struct RowSplit {
 // scatters every branch that fits; mode 0 none.  The choice depends on the
 // tree and the tables only, not on the stripe range, so that a range run
 // gives bitwise the stripes of the full run.
+// path: ACC_MIN or ACC_GEN (CUDA-core stripe kernels) or SPLIT_GRAM (tensor cores)
+constexpr int SPLIT_GRAM = 2;
 RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int acc, bool fp32) {
   RowSplit R;
   const int mode = (int)g_sparse.load();
@@ -700,16 +682,20 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
   std::vector<char> is_sparse(std::max<int64_t>(nb, 1), 0);
   if (mode != 0) {
     const int n_acc = acc == ACC_GEN ? 2 : 1;
-    double cells = 0.0;  // stripe cells of a full run of every table
+    double cells = 0.0, cols = 0.0;  // stripe cells of a full run of every table; samples
     for (size_t t = 0; t < nt; t++) {
       const double n = (double)J.tabs[t].table->n;
       cells += std::floor(n / 2.0) * n;
+      cols += n;
     }
     const double atom_rate = cells * 8.0 * n_acc <= 64e6 ? 2.3e11 : 2.5e10;
-    const double dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
+    double dense_rate;  // cell updates per second of the dense kernel
+    if (acc == SPLIT_GRAM) dense_rate = 2.5e14;
+    else dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
     const double visit_rate = fp32 ? 2e12 : (acc == ACC_GEN ? 3e10 : 1e12);
     const double job_cost = 5e-10;
-    const double dense_t = cells / dense_rate;
+    // a dense row also costs its count row and embedding (or planes) in HBM
+    const double dense_t = cells / dense_rate + cols * 36.0 / 6e12;
     for (int64_t v = 0; v < nb; v++) {
       const int32_t lo = tree->tip_lo[v], hi = tree->tip_hi[v];
       if (lo < 0) continue;
@@ -858,6 +844,27 @@ void fill_reports(uf_tree *tree, const BatchJob &J, const Outputs &o, double ms[
   }
 }
 
+// Count rows of block b that the split needs: CSC-built nodes of every
+// table, then the dense internal levels over the combined axis.
+void enqueue_split_counts(const Inputs &in, const BatchJob &J, const std::vector<int> &off, const RowSplit &split,
+                          size_t b, const int32_t *d_cnt, double *counts, int64_t ld, cudaStream_t st,
+                          int64_t *kernels) {
+  const auto &lb = split.cnt_launch[b];
+  for (size_t t = 0; t < J.tabs.size(); t++) {
+    ck(launch_slice_counts(d_cnt + lb[0].first, lb[0].second, in.td->tip_lo, in.td->tip_hi, in.pd->slot_of_node,
+                           in.xd[t]->col_ptr, in.xd[t]->col_row, in.xd[t]->col_val, counts + off[t], ld,
+                           (int)J.tabs[t].table->n, st),
+       "count rows");
+    *kernels += lb[0].second > 0;
+  }
+  for (size_t l = 1; l < lb.size(); l++) {
+    ck(launch_node_counts(d_cnt + lb[l].first, lb[l].second, in.td->child_ptr, in.td->child_idx,
+                          in.pd->slot_of_node, counts, ld, st),
+       "node counts");
+    (*kernels)++;
+  }
+}
+
 // Unweighted, mixed precision, on the tensor cores: per branch block, counts
 // -> presence / split-length planes of every table -> tcgen05 gram; then the
 // gram finalize of every table.  Throws CudaFail on CUDA errors.
@@ -888,8 +895,10 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
   const int n_tiles = (int)tile_bi.size();
   const int64_t nb = tree->n_nodes - 1;
   const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + 4.0 * npad_tot * 2.0 + 8.0, (double)gt_cells * 8.0);
-  const int64_t K_pad = gram_kpad((int)rows);
   Inputs in = bind_inputs(tree, J, device, rows);
+  const std::shared_ptr<const RowSplit> split_p = get_split(tree, J, in.P, SPLIT_GRAM, true);
+  const RowSplit &split = *split_p;
+  const int64_t K_pad = gram_kpad((int)std::max<int64_t>(split.max_dense, 1));
   cudaStream_t st = J.st;
   int64_t kernels = 0, acc_launches = 0;
   PhaseTimer timer(g_kernel_timing.load() != 0, st);
@@ -900,11 +909,36 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
   DevBuf Pl((size_t)4 * npad_tot * K_pad * 2, st, "alloc presence planes");
   DevBuf Gt((size_t)gt_cells * 8, st, "alloc gram");
   DevBuf err(sizeof(int), st, "alloc error flag");
-  Meta meta;  // tile list and table descriptors: one staged upload
+  Meta meta;  // tile list, table descriptors and row lists: one staged upload
   const size_t o_tiles = meta.add(tl), o_tabs = meta.add(gt);
+  const size_t o_cnt = meta.add(split.cnt_lists), o_dense = meta.add(split.dense);
+  std::vector<int64_t> sp_off;
+  size_t o_sparse = 0, o_sptabs = 0;
+  if (split.n_sparse > 0) {
+    std::vector<int32_t> all;
+    for (const auto &c : split.sparse) {
+      sp_off.push_back((int64_t)all.size());
+      all.insert(all.end(), c.begin(), c.end());
+    }
+    std::vector<SpTab> sp(nt);
+    for (size_t t = 0; t < nt; t++) {
+      sp[t].col_ptr = in.xd[t]->col_ptr;
+      sp[t].col_row = in.xd[t]->col_row;
+      sp[t].col_val = in.xd[t]->col_val;
+      sp[t].total = in.xd[t]->total;
+      sp[t].inv_total_f = in.xd[t]->inv_total_f;
+      sp[t].n = gt[t].n;
+      sp[t].off = gt[t].off;
+      sp[t].m_off = gt[t].gt_off;
+      sp[t].n_pad = gt[t].n_pad;
+    }
+    o_sparse = meta.add(all);
+    o_sptabs = meta.add(sp);
+  }
   meta.upload(st);
   const int32_t *d_tiles = meta.at<int32_t>(o_tiles);
   const GramTab *d_tabs = meta.at<GramTab>(o_tabs);
+  const int32_t *d_cnt = meta.at<int32_t>(o_cnt), *d_dense = meta.at<int32_t>(o_dense);
   ck(cudaMemsetAsync(Gt.p, 0, (size_t)gt_cells * 8, st), "memset");
   ck(cudaMemsetAsync(err.p, 0, sizeof(int), st), "memset");
   Outputs o = bind_outputs(J, st);
@@ -912,16 +946,20 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
   Capture cap(g_graph.load() != 0 && !timer.on, st, device);
   const cudaStream_t ls = cap.stream();
   for (size_t b = 0; b < in.P->b0.size(); b++) {
-    const int64_t b0 = in.P->b0[b], b1 = in.P->b1[b];
+    const int64_t b0 = in.P->b0[b];
+    const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
     timer.begin(0);
-    enqueue_counts(in, J, off, b, counts.as<double>(), n_cols, ls, &kernels);
-    ck(launch_gram_prep(b0, (int)(b1 - b0), in.pd->slot_of_node, counts.as<double>(), n_cols, in.td->length,
-                        d_tabs, (int)nt, npad_tot, K_pad, Pl.p, ls),
-       "presence planes");
-    kernels++;
+    enqueue_split_counts(in, J, off, split, b, d_cnt, counts.as<double>(), n_cols, ls, &kernels);
+    if (nd > 0) {
+      ck(launch_gram_prep(b0, (int)nd, in.pd->slot_of_node, counts.as<double>(), n_cols, in.td->length, d_tabs,
+                          (int)nt, npad_tot, K_pad, Pl.p, ls, d_dense + d0),
+         "presence planes");
+      kernels++;
+    }
     timer.end();
+    if (nd == 0) continue;
     GramArgs ga{};
-    ga.k_len = (int)round_up(b1 - b0, 64);
+    ga.k_len = (int)round_up(nd, 64);
     ga.kc = 4096;
     ga.n_tiles = n_tiles;
     ga.npad_tot = npad_tot;
@@ -938,6 +976,29 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
     kernels++;
     acc_launches++;
     exec_flops += 2.0 * 3 * 128.0 * 256.0 * ga.k_len * n_tiles;
+  }
+  if (split.n_sparse > 0) {
+    timer.begin(4);
+    for (size_t c = 0; c < split.sparse.size(); c++) {
+      if (split.sparse[c].empty()) continue;
+      SparseArgs sp{};
+      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
+      sp.n_nodes = (int)split.sparse[c].size();
+      sp.cap = split.cap[c];
+      sp.tip_lo = in.td->tip_lo;
+      sp.tip_hi = in.td->tip_hi;
+      sp.length = in.td->length;
+      sp.tabs = meta.at<SpTab>(o_sptabs);
+      sp.n_tabs = (int)nt;
+      sp.kind = EMB_PRESENCE;
+      sp.gram = 1;
+      sp.M = Gt.as<unsigned long long>();
+      sp.alpha = 1.0;
+      sp.scale = scale;
+      ck(launch_sparse_rows(ACC_MIN, false, sp, ls), "sparse rows");
+      kernels++;
+    }
+    timer.end();
   }
   timer.begin(3);
   for (size_t t = 0; t < nt; t++) {
@@ -968,7 +1029,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
   ck(cudaStreamSynchronize(st), "synchronize");  // the error flag is read here
   err = DevBuf();
   if (h_err) return fail(UF_ETIMEOUT, "tensor-core kernel: a bounded wait gave up");
-  double ms[4] = {0, 0, 0, 0};
+  double ms[5] = {0, 0, 0, 0, 0};
   timer.collect(ms);
   fill_reports(tree, J, o, ms, kernels, acc_launches, 1, rows, (int64_t)in.P->b0.size(), exec_flops, 256, 128,
                std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
@@ -976,6 +1037,10 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
     if (t.rep) {
       t.rep->chunk_rows = 4096;
       t.rep->graph = cap.on ? 1 : 0;
+      t.rep->dense_rows = (int64_t)split.dense.size();
+      t.rep->sparse_rows = split.n_sparse;
+      t.rep->sparse_pairs = split.pairs;
+      t.rep->t_sparse_ms = ms[4];
     }
   return UF_OK;
 }
@@ -1103,22 +1168,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     const int64_t b0 = in.P->b0[b];
     const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
     timer.begin(0);
-    {
-      const auto &lb = split.cnt_launch[b];
-      for (size_t t = 0; t < nt; t++) {
-        ck(launch_slice_counts(d_cnt + lb[0].first, lb[0].second, in.td->tip_lo, in.td->tip_hi,
-                               in.pd->slot_of_node, in.xd[t]->col_ptr, in.xd[t]->col_row, in.xd[t]->col_val,
-                               counts.as<double>() + off[t], n_cols, (int)J.tabs[t].table->n, ls),
-           "count rows");
-        kernels += lb[0].second > 0;
-      }
-      for (size_t l = 1; l < lb.size(); l++) {
-        ck(launch_node_counts(d_cnt + lb[l].first, lb[l].second, in.td->child_ptr,
-                              in.td->child_idx, in.pd->slot_of_node, counts.as<double>(), n_cols, ls),
-           "node counts");
-        kernels++;
-      }
-    }
+    enqueue_split_counts(in, J, off, split, b, d_cnt, counts.as<double>(), n_cols, ls, &kernels);
     if (nd > 0) {
       ck(launch_emb_rows(kind, fp32, b0, (int)nd, in.pd->slot_of_node, counts.as<double>(), n_cols,
                          in.td->length, total.as<double>(), inv_total.as<float>(), X.p, pitch,

@@ -139,7 +139,8 @@ struct SpTab {
   const double *total;      // per-sample count totals
   const float *inv_total_f; // 1 / total in FP32
   int n, off, s_lo, s_hi;   // samples, combined column, stored stripes
-  int64_t m_off;            // first accumulator cell
+  int64_t m_off;            // first accumulator cell (gram layout: first cell of its gram matrix)
+  int n_pad;                // gram layout: row length of its gram matrix
 };
 struct SparseArgs {
   const int32_t *nodes;     // sparse branch nodes of this launch
@@ -151,6 +152,9 @@ struct SparseArgs {
   int n_tabs;
   int kind;                 // EmbKind
   int mixed_forms;          // FP32 min kernel abs-form stripes present
+  int gram;                 // 1: presence rows into the tensor path's gram matrices
+                            // (cell (i, j), i <= j, at m_off + j * n_pad + i; the
+                            // diagonal takes the per-sample terms; Dsp unused)
   unsigned long long *M, *M2, *Dsp;  // cells (M / den), Q (generalized), per-sample diagonal R
   double alpha, scale;
 };
@@ -192,9 +196,11 @@ int gram_pad(int n);                      // n rounded up to the tile
 int64_t gram_kpad(int rows);              // branches rounded up to the stage
 // upper-triangle tiles of one table: (bi, bj) pairs appended to bi / bj
 void gram_tiles(int n_pad, std::vector<int32_t> *bi, std::vector<int32_t> *bj);
+// planes of branches nodes[0 .. rows) (b0 .. b0 + rows - 1 when nodes is null)
 cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, const double *counts,
                              int64_t ld, const double *length, const GramTab *tabs, int n_tabs,
-                             int npad_tot, int64_t K_pad, void *Pl, cudaStream_t st);
+                             int npad_tot, int64_t K_pad, void *Pl, cudaStream_t st,
+                             const int32_t *nodes = nullptr);
 cudaError_t launch_gram(const GramArgs &a, void *Pl, int64_t K_pad, cudaStream_t st);
 cudaError_t launch_finalize_gram(const GramFinalArgs &a, cudaStream_t st);
 

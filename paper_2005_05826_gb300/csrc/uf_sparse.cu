@@ -20,6 +20,9 @@
 //   both), and two identical samples still give num = 0 exactly.
 // The finalize adds R[k] + R[j] where these terms need it (uf_finalize.cu);
 // integer addition makes the order free and the result deterministic.
+// For the tensor-core unweighted path the same presence terms go into its
+// gram matrices: G[j][k] += l per both-nonzero pair and G[k][k] += l per
+// nonzero sample (the diagonal W of uf_gram.cu).
 //
 // One CTA per (sparse branch, table).  The branch's tips are a contiguous
 // range of tip numbers, so its nonzero counts are one contiguous run of the
@@ -159,7 +162,11 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
     u++;
   }
   __syncthreads();
-  for (int e = tid; e < z; e += NT) red_add(a.Dsp + tb.off + ks[e], fx[e]);
+  if (a.gram) {
+    for (int e = tid; e < z; e += NT) red_add(a.M + tb.m_off + (int64_t)ks[e] * tb.n_pad + ks[e], fx[e]);
+  } else {
+    for (int e = tid; e < z; e += NT) red_add(a.Dsp + tb.off + ks[e], fx[e]);
+  }
   // pairs (ia < ib) numbered row by row: row ia starts at ia (2z - ia - 1) / 2
   const int64_t npairs = (int64_t)z * (z - 1) / 2;
   if (npairs == 0) return;
@@ -178,6 +185,16 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
   unsigned long long *M = a.M + tb.m_off;
   unsigned long long *M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
   const T lt = (T)l, am1 = (T)(a.alpha - 1.0);
+  if (ACC == ACC_MIN && a.gram) {
+    for (; p < p1; p++) {
+      red_add(a.M + tb.m_off + (int64_t)ks[ib] * tb.n_pad + ks[ia], min(fx[ia], fx[ib]));
+      if (++ib == z) {
+        ia++;
+        ib = ia + 1;
+      }
+    }
+    return;
+  }
   for (; p < p1; p++) {
     const int ka = ks[ia], kb = ks[ib];
     const int d = kb - ka;

@@ -67,8 +67,6 @@ def test_all_modes_match_oracle(method, precision):
     for mode in (0, 1, 2):
         got, rep = run(tree, table, method, a, precision, mode)
         assert_close(got, exp, method, precision, f"sparse={mode}")
-        if method == "unweighted" and precision == "mixed":
-            continue  # tensor path: the sparse split is not applied there
         assert rep.dense_rows + rep.sparse_rows == nb
         if mode == 0:
             assert rep.sparse_rows == 0
@@ -89,6 +87,24 @@ def test_generalized_alphas(alpha):
         got, rep = run(tree, table, "generalized", alpha, precision, 2)
         assert rep.sparse_rows > 0
         assert_close(got, exp, "generalized", precision, f"alpha={alpha}")
+
+
+@pytest.mark.parametrize("tensor", [0, 1])
+def test_unweighted_mixed_both_paths(tensor):
+    # the tensor-core gram path takes the scattered rows into its gram matrices
+    tree_s = yule_tree(1500, seed=215)
+    table_s = table_iid(300, tree_s.n_tips, 0.03, seed=216)
+    tree, table = handles(tree_s, table_s)
+    exp = oracle.condensed(tree_s, table_s, "unweighted", 1.0)
+    uf.uf_set_option("tensor_path", tensor)
+    try:
+        for mode in (0, 1, 2):
+            got, rep = run(tree, table, "unweighted", 1.0, "mixed", mode)
+            assert rep.path == tensor
+            assert (rep.sparse_rows > 0) == (mode > 0)
+            assert_close(got, exp, "unweighted", "mixed", f"tensor={tensor} sparse={mode}")
+    finally:
+        uf.uf_set_option("tensor_path", 1)
 
 
 def test_capacity_classes():

@@ -123,9 +123,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_traffic(kernel_key: str):
+def kernel_traffic(kernel_key: str, workload: str):
     """Per-launch DRAM bytes of a kernel from the committed ncu summary, or
-    None when the kernel source changed since the capture."""
+    None when the kernel source changed since the capture or the capture was
+    taken on another workload."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -133,7 +134,7 @@ def kernel_traffic(kernel_key: str):
         with open(path) as fh:
             d = json.load(fh)
         ent = d.get(kernel_key)
-        if not ent:
+        if not ent or ent.get("workload") != workload:
             return None
         h = hashlib.sha256()
         for src in ent["sources"]:
@@ -206,18 +207,27 @@ def run_reference(args, rank, world):
 def workload_config(args, tree_s, table_s, l2):
     return {"workload": args.workload, "tips": tree_s.n_tips, "nodes": tree_s.n_nodes,
             "samples": table_s.n_samples, "nnz": table_s.nnz,
-            "methods": [m for m, _ in METHODS], "alpha": 0.5, "stripes": "all",
+            "methods": [m for m, _ in METHODS], "alpha": 0.5,
+            "stripes": "all" if not 0 < getattr(args, "stripe_stop", 0) < table_s.n_samples // 2
+            else f"[0, {args.stripe_stop}) of {table_s.n_samples // 2}",
             "sparse_rows_mode": getattr(args, "sparse", 1), "l2": l2}
 
 
-def max_errors(tree_s, table_s, outs, precision):
+def max_errors(tree_s, table_s, outs, precision, stop=None):
     """Max error of each method's result against the oracle on the seeded
-    10,000-pair subset (abs for mixed, rel for fp64)."""
+    10,000-pair subset (abs for mixed, rel for fp64); for a stripe-range run
+    [0, stop), on 10,000 seeded cells (s, k) of the range, pair (k, (k+s+1) mod n)."""
     import oracle
     from synth import pair_subset
     n = table_s.n_samples
-    i, j = pair_subset(n, 10_000, seed=12345)
-    idx = n * i - i * (i + 1) // 2 + (j - i - 1)
+    if stop is None or stop >= n // 2:
+        i, j = pair_subset(n, 10_000, seed=12345)
+        idx = n * i - i * (i + 1) // 2 + (j - i - 1)
+    else:
+        cells = np.random.default_rng(12345).choice(stop * n, size=min(10_000, stop * n), replace=False)
+        s_, k_ = cells // n, cells % n
+        i, j = k_, (k_ + s_ + 1) % n
+        idx = cells
     res = {}
     for (m, a), got in zip(METHODS, outs):
         exp = oracle.pairs(tree_s, table_s, m, a, i, j)[0]
@@ -332,7 +342,13 @@ def run_ours(args, rank, world, local_rank):
     tree_s, table_s = workload(args.workload)
     n = table_s.n_samples
     branches = tree_s.n_nodes - 1
-    npairs = n * (n - 1) // 2
+    S = n // 2
+    stop = args.stripe_stop if 0 < args.stripe_stop < S else S
+    full = stop == S
+    # pairs covered per method: all pairs, or the stripe range [0, stop) (stop < S never holds
+    # the duplicated half stripe)
+    npairs = n * (n - 1) // 2 if full else stop * n
+    rng_args = () if full else (0, stop)
     peaks, peak_src = load_peaks()
     dist = None
     if world > 1:
@@ -348,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
 
     tree = uf.Tree(tree_s.parent, tree_s.length)
     table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
-    outs = [torch.empty(npairs, dtype=torch.float64, device=dev) for _ in METHODS]
+    outs = [torch.empty(npairs, dtype=torch.float64, device=dev) for _ in METHODS]  # condensed or stripe-major
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     uf.uf_set_option("kernel_timing", 1)
@@ -356,7 +372,7 @@ def run_ours(args, rank, world, local_rank):
 
     def step(precision, reps=None):
         for (m, a), o in zip(METHODS, outs):
-            _, rep = uf.uf_compute(tree, table, m, a, precision, out=o)
+            _, rep = uf.uf_compute(tree, table, m, a, precision, *rng_args, out=o)
             if reps is not None:
                 reps.append((m, rep))
 
@@ -396,10 +412,10 @@ def run_ours(args, rank, world, local_rank):
     # graph launch and does not wait for its events): the host overhead of
     # the phase timing is the difference
     uf.uf_set_option("kernel_timing", 0)
-    for _ in range(2):
-        step("mixed")
     t_plain = []
-    for _ in range(args.steps):
+    for _ in range(2 if t_total / args.steps < 2.0 else 0):
+        step("mixed")
+    for _ in range(args.steps if t_total / args.steps < 2.0 else 0):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -471,7 +487,7 @@ def run_ours(args, rank, world, local_rank):
                    "peak_basis": basis, "share_of_step": ms / 1e3 / t_total}
     dom = max(kern, key=lambda m: kern[m]["share_of_step"])
     rl = dict(kern[dom])
-    rl["traffic"] = kernel_traffic(rl["kernel"])
+    rl["traffic"] = kernel_traffic(rl["kernel"], args.workload if full else f"{args.workload}[0,{stop})")
     rl["method"] = dom
 
     # ---- e2e through the C ABI with host buffers ----
@@ -485,7 +501,7 @@ def run_ours(args, rank, world, local_rank):
             tb = uf.Table(table_s.indptr, table_s.indices, table_s.data, tr)
             hb = db = 0.0
             for m, a in METHODS:
-                _, rep = uf.uf_compute(tr, tb, m, a, "mixed")
+                _, rep = uf.uf_compute(tr, tb, m, a, "mixed", *rng_args)
                 hb += rep.h2d_bytes
                 db += rep.d2h_bytes
             tb.close()
@@ -503,7 +519,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_fp64 and args.fp64_stripes > 0:
         # FP64 path on the stripe slice [0, fp64_stripes) only (large workloads)
         S = uf.uf_stripe_count(n)
-        k = min(args.fp64_stripes, S)
+        k = min(args.fp64_stripes, S - 1)
         sl = torch.empty(k * n, dtype=torch.float64, device=dev)
         f_reps = []
         torch.cuda.synchronize()
@@ -551,14 +567,14 @@ def run_ours(args, rank, world, local_rank):
                 "peak": 0.3125, "unit": "Tupdates/s", "frac": ach64 / 0.3125,
                 "peak_basis": "nominal FP64 1.25 TFLOP/s = 0.625 T instructions/s, 2 per update"}
         if not args.no_err:
-            fp64["max_err"] = max_errors(tree_s, table_s, fp64_outs, "fp64")
+            fp64["max_err"] = max_errors(tree_s, table_s, fp64_outs, "fp64", stop)
             fp64["max_rel_err"] = max(v["max_rel"] for v in fp64["max_err"].values())
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
-    mixed_err = {} if args.no_err else max_errors(tree_s, table_s, mixed_outs, "mixed")
+    mixed_err = {} if args.no_err else max_errors(tree_s, table_s, mixed_outs, "mixed", stop)
     clocks = sampler.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
@@ -576,7 +592,7 @@ def run_ours(args, rank, world, local_rank):
         "kernels": kern,
         "sparse_rows": sparse,
         "phases_ms_per_call": phases,
-        "ms_per_step_without_phase_timing": statistics.mean(t_plain),
+        "ms_per_step_without_phase_timing": statistics.mean(t_plain) if t_plain else None,
         "peak_source": peak_src,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -608,6 +624,8 @@ def main():
                     help="comma list of methods per step (default: all four)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--stripe-stop", type=int, default=0,
+                    help="time the stripe range [0, K) of every method instead of all stripes (0: all)")
     ap.add_argument("--sparse", type=int, choices=[0, 1, 2], default=1,
                     help="sparse-row path: 0 every branch dense, 1 cost model (default), 2 every branch that fits")
     args = ap.parse_args()

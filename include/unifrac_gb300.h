@@ -116,7 +116,10 @@ typedef struct {
  *   "kernel_timing"  0 (default) or 1: time each phase with CUDA events and
  *                    fill the t_*_ms fields of uf_report (adds a stream sync)
  *   "tensor_path"    1 (default): UF_UNWEIGHTED with UF_MIXED runs on the
- *                    tcgen05 tensor cores; 0: on the CUDA-core stripe kernels
+ *                    tcgen05 tensor cores when every table's full gram matrix
+ *                    (n rounded up to 256, squared, 8 bytes) fits in half the
+ *                    free device memory, else on the CUDA-core stripe kernels
+ *                    (report path 0); 0: always on the CUDA-core kernels
  *   "graph"          1 (default): a call's branch-block launch sequence is
  *                    captured into a CUDA graph and launched as one graph
  *                    (not when "kernel_timing" is 1); 0: plain launches

@@ -1308,7 +1308,19 @@ uf_status run_batch(uf_tree *tree, const BatchJob &J) {
     const double s = accum_scale(tree, t.table, kind);
     scale = scale == 0.0 ? s : std::min(scale, s);
   }
-  if (method == UF_UNWEIGHTED && J.fp32 && g_tensor_path.load()) return run_gram(tree, J, device, scale, 0.0);
+  if (method == UF_UNWEIGHTED && J.fp32 && g_tensor_path.load()) {
+    // the tensor path keeps every table's whole n_pad x n_pad gram matrix (int64) on the
+    // device whatever the stripe range; when that does not fit in half the free memory
+    // the CUDA-core stripe kernels, which store only the requested stripes, take the call
+    double gram_bytes = 0.0;
+    for (const TableJob &t : J.tabs) {
+      const double np = (double)gram_pad((int)t.table->n);
+      gram_bytes += np * np * 8.0;
+    }
+    size_t free_b = 0, total_b = 0;
+    ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    if (gram_bytes <= 0.5 * (double)free_b) return run_gram(tree, J, device, scale, 0.0);
+  }
   return run_stripes(tree, J, device, method, scale);
 }
 

@@ -104,7 +104,8 @@ typedef struct {
     int32_t graph;         /* 1: the launch sequence ran as one CUDA graph */
     int32_t reserved2;
     int64_t dense_rows;    /* branches run through the dense stripe kernels */
-    int64_t sparse_rows;   /* branches scattered pair by pair (option "sparse") */
+    int64_t sparse_rows;   /* branches kept out of the dense kernels (option "sparse"):
+                              scattered pair by pair, or of length 0 and skipped */
     double sparse_pairs;   /* both-nonzero sample pairs of those branches, at most */
     double t_sparse_ms;    /* device time of the sparse-row launches ("kernel_timing") */
 } uf_report;

@@ -699,6 +699,13 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
     for (int64_t v = 0; v < nb; v++) {
       const int32_t lo = tree->tip_lo[v], hi = tree->tip_hi[v];
       if (lo < 0) continue;
+      if (tree->length[v] == 0.0) {
+        // a zero-length branch adds exactly 0 to every accumulator: skipped
+        // (its count row is still built if a dense parent needs it)
+        is_sparse[v] = 1;
+        R.n_sparse++;
+        continue;
+      }
       double cost = 0.0, pairs = 0.0;
       int64_t mx = 0;
       for (size_t t = 0; t < nt; t++) {

@@ -235,3 +235,23 @@ def test_autotuned_chunk_sizes():
         assert_close(got3, exp, "weighted_normalized", "mixed", "fixed chunk")
     finally:
         uf.uf_set_option("autotune", 1)
+
+
+@pytest.mark.parametrize("factor", [1e-8, 1.0, 1e16])
+def test_generalized_length_scales(factor):
+    # uniformly scaled lengths leave normalized distances unchanged; tiny and
+    # huge lengths exercise the FP32 embedding floor and the fixed-point scale
+    tree_s = yule_tree(800, seed=95)
+    tree_s = type(tree_s)(tree_s.parent, tree_s.length * factor)
+    table_s = table_iid(150, tree_s.n_tips, 0.05, seed=96)
+    tree, table = handles(tree_s, table_s)
+    for alpha in (0.5, 0.25):
+        exp = oracle.condensed(tree_s, table_s, "generalized", alpha)
+        for sparse in (0, 1):
+            uf.uf_set_option("sparse", sparse)
+            try:
+                for precision in PRECISIONS:
+                    got, _ = uf.uf_compute(tree, table, "generalized", alpha, precision)
+                    assert_close(got, exp, "generalized", precision, f"x{factor} alpha={alpha} sparse={sparse}")
+            finally:
+                uf.uf_set_option("sparse", 1)

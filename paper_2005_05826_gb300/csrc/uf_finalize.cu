@@ -32,7 +32,7 @@ __global__ void k_finalize(const FinalArgs a) {
     if (j >= a.n) j -= a.n;
     if (a.full && 2 * (s + 1) == a.n && k >= a.n / 2) continue;  // duplicate half stripe
     long long m = (long long)a.M[c];
-    const bool abs_form = a.mixed_forms && (s & 7) >= 8 - FP32_ABS_ROWS;
+    const bool abs_form = a.mixed_forms && fp32_abs_row(s);
     const long long rk = a.Dsp ? (long long)a.Dsp[k] : 0, rj = a.Dsp ? (long long)a.Dsp[j] : 0;
     const long long dk = (a.Dg ? (long long)a.Dg[k] : 0) + rk, dj = (a.Dg ? (long long)a.Dg[j] : 0) + rj;
     if (abs_form || a.method == 3) m += rk + rj;

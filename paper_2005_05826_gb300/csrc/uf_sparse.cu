@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
       const bool dup = 2 * d == n;  // also stored at k = kb (= ka + n/2)
       if (ACC == ACC_MIN) {
         long long t = min(fx[ia], fx[ib]);
-        if (a.mixed_forms && (s & 7) >= 8 - FP32_ABS_ROWS) t *= -2;
+        if (a.mixed_forms && fp32_abs_row(s)) t *= -2;
         red_add(M + cell, t);
         if (dup) red_add(M + cell + d, t);
       } else {

@@ -11,9 +11,10 @@
 //   M[s][k] = sum_e min(x_e[k], x_e[k + s + 1])        (min form) or
 //   A[s][k] = sum_e |x_e[k] - x_e[k + s + 1]|          (abs form).
 // One min-form update is one FMNMX (ALU pipe, half rate) plus half an FADD2;
-// one abs-form update is half an FADD2 plus one FADD (FMA pipe).  The FP32
-// kernel gives the last FP32_ABS_ROWS of every 8 stripes the abs form so the
-// two pipes share the load.  Generalized UniFrac keeps two accumulators,
+// one abs-form update is half an FSUB2 plus one FADD (FMA pipe).  The FP32
+// kernel gives stripes 3, 5 and 7 of every 8 the abs form so the two pipes
+// share the load (odd micro-tile rows read their partner pairs at even,
+// register-pair aligned offsets).  Generalized UniFrac keeps two accumulators,
 // den = sum l s^a and Q = sum l min(u, v) s^(a-1), num = den - 2Q.
 //
 // Work is split into units (row chunk of up to a.chunk branches, tile of
@@ -88,6 +89,17 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// a - b on a register pair (one packed FP32 subtract)
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+  unsigned long long ra, rb, rr;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rr) : "l"(ra), "l"(rb));
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(rr));
+  return r;
+}
 
 struct Unit {
   int r0, r1;       // branch rows
@@ -194,8 +206,9 @@ __device__ __forceinline__ void commit_cells(unsigned long long *M, const Mid *m
 }
 
 // ---- weighted / unweighted ----
-// rows i < NMIN of the micro-tile: M += min(x_k, x_j); rows i >= NMIN: A += |x_k - x_j|
-template <typename T, int RD, int RK, int NMIN, int MINB>
+// rows i of the micro-tile with bit i of ABSM clear: M += min(x_k, x_j);
+// with it set: A += |x_k - x_j|
+template <typename T, int RD, int RK, unsigned ABSM, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
   using G = Geo<T, RD, RK, 1>;
   using Mid = typename G::Mid;
@@ -252,15 +265,14 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
           for (int i = 0; i < RD; i++)
 #pragma unroll
             for (int j = 0; j < RK; j += 2) {
-              if (i < NMIN) {  // two mins, one paired add
+              if (!((ABSM >> i) & 1u)) {  // two mins, one paired add
                 float2 a2 = make_float2(acc[i][j], acc[i][j + 1]);
                 const float2 m2 = make_float2(fminf(u[j], v[i + j + 1]), fminf(u[j + 1], v[i + j + 2]));
                 a2 = __fadd2_rn(a2, m2);
                 acc[i][j] = a2.x;
                 acc[i][j + 1] = a2.y;
               } else {  // one paired difference, two adds of absolute values
-                const float2 d2 = __fadd2_rn(make_float2(u[j], u[j + 1]),
-                                             make_float2(-v[i + j + 1], -v[i + j + 2]));
+                const float2 d2 = fsub2(make_float2(u[j], u[j + 1]), make_float2(v[i + j + 1], v[i + j + 2]));
                 acc[i][j] += fabsf(d2.x);
                 acc[i][j + 1] += fabsf(d2.y);
               }
@@ -495,15 +507,15 @@ int units_of(const StripeArgs &a) {
   return n_chunks * a.n_tiles;
 }
 
-template <typename T, int RD, int RK, int NMIN, int MINB>
+template <typename T, int RD, int RK, unsigned ABSM, int MINB>
 cudaError_t run_min(const StripeArgs &a, cudaStream_t st) {
   using G = Geo<T, RD, RK, 1>;
   int grid = 0;
-  cudaError_t e = prepare(k_stripe_min<T, RD, RK, NMIN, MINB>, G::SMEM, &grid, units_of(a));
+  cudaError_t e = prepare(k_stripe_min<T, RD, RK, ABSM, MINB>, G::SMEM, &grid, units_of(a));
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  k_stripe_min<T, RD, RK, NMIN, MINB><<<grid, NT, G::SMEM, st>>>(a);
+  k_stripe_min<T, RD, RK, ABSM, MINB><<<grid, NT, G::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -533,7 +545,7 @@ int stripe_chunk_rows() { return 2048; }
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st) {
   if (a.rows <= 0 || a.n_tiles <= 0) return cudaSuccess;
   if (acc == ACC_MIN)
-    return fp32 ? run_min<float, 8, 8, 8 - FP32_ABS_ROWS, 2>(a, st) : run_min<double, 8, 8, 8, 1>(a, st);
+    return fp32 ? run_min<float, 8, 8, FP32_ABS_ROW_MASK, 2>(a, st) : run_min<double, 8, 8, 0u, 1>(a, st);
   const bool half = a.alpha == 0.5;
   if (fp32) return half ? run_gen<float, 4, 8, 0, 2>(a, st) : run_gen<float, 4, 8, 1, 2>(a, st);
   return half ? run_gen<double, 4, 8, 0, 1>(a, st) : run_gen<double, 4, 8, 1, 1>(a, st);

@@ -239,6 +239,26 @@ def max_errors(tree_s, table_s, outs, precision, stop=None):
     return res
 
 
+def downstream_agreement(mixed_outs, fp64_outs, sub=512, perms=999):
+    """The paper's FP32-vs-FP64 check (Sec. 4): Mantel r^2 between the two
+    matrices of each method on all pairs, its permutation p-value on the
+    first `sub` samples (`perms` relabellings), and the Procrustes disparity
+    of the first 10 principal coordinates."""
+    from paper_2005_05826_gb300 import downstream as ds
+    res = {}
+    for (m, _), d32, d64 in zip(METHODS, mixed_outs, fp64_outs):
+        r, _ = ds.mantel(d32, d64, permutations=0)
+        s32, s64 = ds.square(d32), ds.square(d64)
+        k = min(sub, s64.shape[0])
+        iu, ju = np.triu_indices(k, 1)
+        _, p = ds.mantel(s32[:k, :k][iu, ju], s64[:k, :k][iu, ju], permutations=perms, seed=1)
+        c64, _ = ds.pcoa(d64, k=10)
+        c32, _ = ds.pcoa(d32, k=10)
+        res[m] = {"mantel_r2": r * r, "mantel_p": p, "p_samples": k, "permutations": perms,
+                  "pcoa10_procrustes": ds.procrustes(c64, c32)}
+    return res
+
+
 def run_batched(args, rank, world, local_rank):
     """64 uneven tables over one shared 100,000-tip tree: aggregate throughput
     of one batched call per method, plus per-table latency of single calls."""
@@ -568,6 +588,8 @@ def run_ours(args, rank, world, local_rank):
                 "peak_basis": "nominal FP64 1.25 TFLOP/s = 0.625 T instructions/s, 2 per update"}
         if not args.no_err:
             fp64["max_err"] = max_errors(tree_s, table_s, fp64_outs, "fp64", stop)
+        if not args.no_downstream and full:
+            fp64["downstream_vs_mixed"] = downstream_agreement(mixed_outs, fp64_outs)
             fp64["max_rel_err"] = max(v["max_rel"] for v in fp64["max_err"].values())
 
     if rank != 0:
@@ -624,6 +646,8 @@ def main():
                     help="comma list of methods per step (default: all four)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--no-downstream", action="store_true",
+                    help="skip the Mantel / principal-coordinate agreement of the mixed and FP64 matrices")
     ap.add_argument("--stripe-stop", type=int, default=0,
                     help="time the stripe range [0, K) of every method instead of all stripes (0: all)")
     ap.add_argument("--sparse", type=int, choices=[0, 1, 2], default=1,

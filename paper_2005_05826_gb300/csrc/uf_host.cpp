@@ -426,19 +426,22 @@ struct PhaseTimer {
   cudaStream_t st;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
   cudaEvent_t open_ev = nullptr;
+  cudaStream_t open_st = nullptr;
   int open_phase = -1;
   PhaseTimer(bool enabled, cudaStream_t s) : on(enabled), st(s) {}
-  void begin(int phase) {
+  // a phase is timed on the stream its launches go to (the call's stream by default)
+  void begin(int phase, cudaStream_t on_stream = nullptr) {
     if (!on) return;
+    open_st = on_stream ? on_stream : st;
     ck(cudaEventCreate(&open_ev), "cudaEventCreate");
-    ck(cudaEventRecord(open_ev, st), "cudaEventRecord");
+    ck(cudaEventRecord(open_ev, open_st), "cudaEventRecord");
     open_phase = phase;
   }
   void end() {
     if (!on) return;
     cudaEvent_t e;
     ck(cudaEventCreate(&e), "cudaEventCreate");
-    ck(cudaEventRecord(e, st), "cudaEventRecord");
+    ck(cudaEventRecord(e, open_st), "cudaEventRecord");
     marks.push_back({open_phase, {open_ev, e}});
     open_ev = nullptr;
   }
@@ -501,16 +504,24 @@ double accum_scale(const uf_tree *tree, const uf_table *table, int kind) {
 
 namespace {
 
-// Private stream per device on which a call's launch sequence is captured.
+// Private stream of the calling thread per device on which a call's launch
+// sequence is captured into a CUDA graph.  Per thread, so that concurrent
+// calls from several threads never share a capturing stream.
+struct ThreadStreams {
+  std::map<int, cudaStream_t> s;
+  ~ThreadStreams() {
+    for (auto &kv : s) cudaStreamDestroy(kv.second);
+  }
+};
+thread_local ThreadStreams t_streams;
+
 cudaStream_t capture_stream(int device) {
-  static std::mutex mu;
-  static std::map<int, cudaStream_t> streams;
-  std::lock_guard<std::mutex> g(mu);
-  auto it = streams.find(device);
-  if (it != streams.end()) return it->second;
-  cudaStream_t s = nullptr;
-  ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
-  return streams[device] = s;
+  auto it = t_streams.s.find(device);
+  if (it != t_streams.s.end()) return it->second;
+  cudaStream_t x = nullptr;
+  ck(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "cudaStreamCreate");
+  t_streams.s[device] = x;
+  return x;
 }
 
 // Records the branch-block launch sequence of a call into a CUDA graph (on a
@@ -952,6 +963,30 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
   double exec_flops = 0.0;
   Capture cap(g_graph.load() != 0 && !timer.on, st, device);
   const cudaStream_t ls = cap.stream();
+  // the sparse-row scatters need no count rows or planes: first
+  if (split.n_sparse > 0) {
+    timer.begin(4);
+    for (size_t c = 0; c < split.sparse.size(); c++) {
+      if (split.sparse[c].empty()) continue;
+      SparseArgs sp{};
+      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
+      sp.n_nodes = (int)split.sparse[c].size();
+      sp.cap = split.cap[c];
+      sp.tip_lo = in.td->tip_lo;
+      sp.tip_hi = in.td->tip_hi;
+      sp.length = in.td->length;
+      sp.tabs = meta.at<SpTab>(o_sptabs);
+      sp.n_tabs = (int)nt;
+      sp.kind = EMB_PRESENCE;
+      sp.gram = 1;
+      sp.M = Gt.as<unsigned long long>();
+      sp.alpha = 1.0;
+      sp.scale = scale;
+      ck(launch_sparse_rows(ACC_MIN, false, sp, ls), "sparse rows");
+      kernels++;
+    }
+    timer.end();
+  }
   for (size_t b = 0; b < in.P->b0.size(); b++) {
     const int64_t b0 = in.P->b0[b];
     const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
@@ -983,29 +1018,6 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale, d
     kernels++;
     acc_launches++;
     exec_flops += 2.0 * 3 * 128.0 * 256.0 * ga.k_len * n_tiles;
-  }
-  if (split.n_sparse > 0) {
-    timer.begin(4);
-    for (size_t c = 0; c < split.sparse.size(); c++) {
-      if (split.sparse[c].empty()) continue;
-      SparseArgs sp{};
-      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
-      sp.n_nodes = (int)split.sparse[c].size();
-      sp.cap = split.cap[c];
-      sp.tip_lo = in.td->tip_lo;
-      sp.tip_hi = in.td->tip_hi;
-      sp.length = in.td->length;
-      sp.tabs = meta.at<SpTab>(o_sptabs);
-      sp.n_tabs = (int)nt;
-      sp.kind = EMB_PRESENCE;
-      sp.gram = 1;
-      sp.M = Gt.as<unsigned long long>();
-      sp.alpha = 1.0;
-      sp.scale = scale;
-      ck(launch_sparse_rows(ACC_MIN, false, sp, ls), "sparse rows");
-      kernels++;
-    }
-    timer.end();
   }
   timer.begin(3);
   for (size_t t = 0; t < nt; t++) {
@@ -1170,6 +1182,30 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   // the launch sequence goes into a CUDA graph unless it is timed per phase
   Capture cap(g_graph.load() != 0 && !timer.on && !tune, st, device);
   const cudaStream_t ls = cap.stream();
+  // the sparse-row scatters run after the dense blocks, whose chunk tuning clears M
+  auto launch_sparse = [&](cudaStream_t on) {
+    for (size_t c = 0; c < split.sparse.size(); c++) {
+      if (split.sparse[c].empty()) continue;
+      SparseArgs sp{};
+      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
+      sp.n_nodes = (int)split.sparse[c].size();
+      sp.cap = split.cap[c];
+      sp.tip_lo = in.td->tip_lo;
+      sp.tip_hi = in.td->tip_hi;
+      sp.length = in.td->length;
+      sp.tabs = meta.at<SpTab>(o_sptabs);
+      sp.n_tabs = (int)nt;
+      sp.kind = kind;
+      sp.mixed_forms = fp32 && acc == ACC_MIN;
+      sp.M = M.as<unsigned long long>();
+      sp.M2 = M2.as<unsigned long long>();
+      sp.Dsp = Dsp.as<unsigned long long>();
+      sp.alpha = J.alpha;
+      sp.scale = scale;
+      ck(launch_sparse_rows(acc, fp32, sp, on), "sparse rows");
+      kernels++;
+    }
+  };
   bool tuned = false;
   for (size_t b = 0; b < in.P->b0.size(); b++) {
     const int64_t b0 = in.P->b0[b];
@@ -1220,30 +1256,9 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
       kernels += 2;
     }
   }
-  // sparse rows: after the dense blocks, whose chunk tuning clears M
   if (split.n_sparse > 0) {
     timer.begin(4);
-    for (size_t c = 0; c < split.sparse.size(); c++) {
-      if (split.sparse[c].empty()) continue;
-      SparseArgs sp{};
-      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
-      sp.n_nodes = (int)split.sparse[c].size();
-      sp.cap = split.cap[c];
-      sp.tip_lo = in.td->tip_lo;
-      sp.tip_hi = in.td->tip_hi;
-      sp.length = in.td->length;
-      sp.tabs = meta.at<SpTab>(o_sptabs);
-      sp.n_tabs = (int)nt;
-      sp.kind = kind;
-      sp.mixed_forms = fp32 && acc == ACC_MIN;
-      sp.M = M.as<unsigned long long>();
-      sp.M2 = M2.as<unsigned long long>();
-      sp.Dsp = Dsp.as<unsigned long long>();
-      sp.alpha = J.alpha;
-      sp.scale = scale;
-      ck(launch_sparse_rows(acc, fp32, sp, ls), "sparse rows");
-      kernels++;
-    }
+    launch_sparse(ls);
     timer.end();
   }
   timer.begin(3);

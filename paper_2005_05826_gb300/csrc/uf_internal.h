@@ -75,9 +75,9 @@ cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
                             const int32_t *nodes = nullptr);
 
 // ---- stripe accumulate (uf_stripe.cu) ----
-// In the FP32 min kernel, stripes s with s mod 8 in {3, 5, 7} hold
+// In the FP32 min kernel, stripes s with s mod 8 in {1, 3, 5, 7} hold
 // A = sum |x_k - x_j| instead of M = sum min(x_k, x_j) (see uf_stripe.cu).
-constexpr unsigned FP32_ABS_ROW_MASK = 0xA8u;
+constexpr unsigned FP32_ABS_ROW_MASK = 0xAAu;
 __host__ __device__ constexpr bool fp32_abs_row(int64_t s) { return (FP32_ABS_ROW_MASK >> (s & 7)) & 1u; }
 
 struct StripeArgs {

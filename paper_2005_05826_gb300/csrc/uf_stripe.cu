@@ -271,10 +271,12 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
                 a2 = __fadd2_rn(a2, m2);
                 acc[i][j] = a2.x;
                 acc[i][j + 1] = a2.y;
-              } else {  // one paired difference, two adds of absolute values
+              } else {  // one paired difference, one paired add of absolute values
                 const float2 d2 = fsub2(make_float2(u[j], u[j + 1]), make_float2(v[i + j + 1], v[i + j + 2]));
-                acc[i][j] += fabsf(d2.x);
-                acc[i][j + 1] += fabsf(d2.y);
+                float2 a2 = make_float2(acc[i][j], acc[i][j + 1]);
+                a2 = __fadd2_rn(a2, make_float2(fabsf(d2.x), fabsf(d2.y)));
+                acc[i][j] = a2.x;
+                acc[i][j + 1] = a2.y;
               }
             }
         } else {

@@ -216,8 +216,10 @@ def workload_config(args, tree_s, table_s, l2):
 def max_errors(tree_s, table_s, outs, precision, stop=None):
     """Max error of each method's result against the oracle on the seeded
     10,000-pair subset (abs for mixed, rel for fp64); for a stripe-range run
-    [0, stop), on 10,000 seeded cells (s, k) of the range, pair (k, (k+s+1) mod n)."""
+    [0, stop), on 10,000 seeded cells (s, k) of the range, pair (k, (k+s+1) mod n).
+    `outs` are the device outputs; only the sampled values are read back."""
     import oracle
+    import torch
     from synth import pair_subset
     n = table_s.n_samples
     if stop is None or stop >= n // 2:
@@ -229,9 +231,9 @@ def max_errors(tree_s, table_s, outs, precision, stop=None):
         i, j = k_, (k_ + s_ + 1) % n
         idx = cells
     res = {}
-    for (m, a), got in zip(METHODS, outs):
+    for (m, a), out in zip(METHODS, outs):
         exp = oracle.pairs(tree_s, table_s, m, a, i, j)[0]
-        g = got[idx]
+        g = out[torch.as_tensor(idx, device=out.device)].double().cpu().numpy()
         abs_err = float(np.max(np.abs(g - exp)))
         rel = np.abs(g - exp) / np.maximum(np.abs(exp), 1e-300)
         rel[(exp == 0) & (g == 0)] = 0.0
@@ -384,7 +386,8 @@ def run_ours(args, rank, world, local_rank):
 
     tree = uf.Tree(tree_s.parent, tree_s.length)
     table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
-    outs = [torch.empty(npairs, dtype=torch.float64, device=dev) for _ in METHODS]  # condensed or stripe-major
+    out_dtype = torch.float32 if args.out_fp32 else torch.float64
+    outs = [torch.empty(npairs, dtype=out_dtype, device=dev) for _ in METHODS]  # condensed or stripe-major
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     uf.uf_set_option("kernel_timing", 1)
@@ -392,7 +395,7 @@ def run_ours(args, rank, world, local_rank):
 
     def step(precision, reps=None):
         for (m, a), o in zip(METHODS, outs):
-            _, rep = uf.uf_compute(tree, table, m, a, precision, *rng_args, out=o)
+            _, rep = uf.uf_compute(tree, table, m, a, precision, *rng_args, out=o, out_fp32=args.out_fp32)
             if reps is not None:
                 reps.append((m, rep))
 
@@ -425,7 +428,10 @@ def run_ours(args, rank, world, local_rank):
         t_total = float(t.item())
     updates_step = len(METHODS) * npairs * branches
     value = world * updates_step * args.steps / t_total
-    mixed_outs = [o.cpu().numpy() for o in outs]
+    mixed_err = {} if args.no_err or rank != 0 else max_errors(tree_s, table_s, outs, "mixed", stop)
+    # whole matrices on the host only where the downstream check wants them
+    keep_host = full and npairs <= 50_000_000 and not args.no_downstream
+    mixed_outs = [o.cpu().numpy().astype(np.float64) for o in outs] if keep_host else []
     launches = int(sum(r.kernels for _, r in reps))
 
     # the same steps with per-phase timing off (each call is then one CUDA
@@ -569,7 +575,7 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         e1.synchronize()
         t64 = e0.elapsed_time(e1) / 1e3
-        fp64_outs = [o.cpu().numpy() for o in outs]
+        fp64_outs = [o.cpu().numpy().astype(np.float64) for o in outs] if keep_host else []
         per_method = {m: r.t_accumulate_ms + r.t_diag_ms + r.t_embed_ms + r.t_finalize_ms
                       for m, r in f_reps}
         fp64 = {"value": updates_step / t64, "unit": "updates/s", "ms_per_step": t64 * 1e3,
@@ -587,8 +593,8 @@ def run_ours(args, rank, world, local_rank):
                 "peak": 0.3125, "unit": "Tupdates/s", "frac": ach64 / 0.3125,
                 "peak_basis": "nominal FP64 1.25 TFLOP/s = 0.625 T instructions/s, 2 per update"}
         if not args.no_err:
-            fp64["max_err"] = max_errors(tree_s, table_s, fp64_outs, "fp64", stop)
-        if not args.no_downstream and full:
+            fp64["max_err"] = max_errors(tree_s, table_s, outs, "fp64", stop)
+        if keep_host:
             fp64["downstream_vs_mixed"] = downstream_agreement(mixed_outs, fp64_outs)
             fp64["max_rel_err"] = max(v["max_rel"] for v in fp64["max_err"].values())
 
@@ -596,7 +602,6 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.destroy_process_group()
         return 0
-    mixed_err = {} if args.no_err else max_errors(tree_s, table_s, mixed_outs, "mixed", stop)
     clocks = sampler.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
@@ -648,6 +653,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-downstream", action="store_true",
                     help="skip the Mantel / principal-coordinate agreement of the mixed and FP64 matrices")
+    ap.add_argument("--out-fp32", action="store_true",
+                    help="FP32 distance outputs (halves the output memory of very large runs)")
     ap.add_argument("--stripe-stop", type=int, default=0,
                     help="time the stripe range [0, K) of every method instead of all stripes (0: all)")
     ap.add_argument("--sparse", type=int, choices=[0, 1, 2], default=1,

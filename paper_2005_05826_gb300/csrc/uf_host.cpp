@@ -20,6 +20,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -32,6 +34,22 @@ using namespace ufg;
 namespace {
 
 thread_local std::string g_err;
+
+// Host threads for table preparation: the cores this process may run on, at most 16.
+int host_threads() {
+  const unsigned h = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(h == 0 ? 1u : h, 16u));
+}
+
+// Runs body(0 .. n-1) on n threads (the calling thread takes the last) and joins.
+template <typename F>
+void parallel_for(int n, F body) {
+  std::vector<std::thread> th;
+  th.reserve(n > 1 ? n - 1 : 0);
+  for (int c = 0; c + 1 < n; c++) th.emplace_back(body, c);
+  body(n - 1);
+  for (auto &x : th) x.join();
+}
 
 std::atomic<int64_t> g_branch_block{0};
 std::atomic<int64_t> g_kernel_timing{0};
@@ -65,8 +83,26 @@ void ck(cudaError_t e, const char *what) {
 
 thread_local double g_h2d = 0.0;  // bytes uploaded by the current call
 
+// Allocator whose value-less construct leaves elements uninitialised: for
+// buffers that are written in full right after they are sized.
 template <typename T>
-T *dev_upload(const std::vector<T> &h, const char *what) {
+struct NoInit : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInit<U>;
+  };
+  NoInit() = default;
+  template <typename U>
+  NoInit(const NoInit<U> &) {}
+  template <typename U, typename... A>
+  void construct(U *p, A &&...a) {
+    if constexpr (sizeof...(A) == 0) ::new ((void *)p) U;
+    else ::new ((void *)p) U(std::forward<A>(a)...);
+  }
+};
+
+template <typename T, typename Alloc>
+T *dev_upload(const std::vector<T, Alloc> &h, const char *what) {
   g_h2d += (double)h.size() * sizeof(T);
   T *d = nullptr;
   size_t bytes = std::max<size_t>(h.size() * sizeof(T), 16);
@@ -106,6 +142,7 @@ using SplitKey = std::tuple<std::vector<uint64_t>, int, int, int, int64_t>;
 }  // namespace
 
 struct uf_tree {
+  uint64_t id = 0;  // process-unique, never reused
   int64_t n_nodes = 0, n_tips = 0;
   std::vector<int64_t> parent;
   std::vector<double> length;
@@ -154,10 +191,10 @@ struct uf_table {
   std::vector<double> total;       // per-sample count totals (row order sums)
   std::vector<float> inv_total_f;  // 1 / total in FP32
   std::vector<int64_t> col_ptr;    // CSC view: tip f -> samples
-  std::vector<int32_t> col_row;
-  std::vector<double> col_val;
+  std::vector<int32_t, NoInit<int32_t>> col_row;
+  std::vector<double, NoInit<double>> col_val;
   std::mutex mu;
-  std::map<const uf_tree *, double> presence_bound;  // by tree: max_k sum_{f in k} dist(tip f)
+  std::map<uint64_t, double> presence_bound;  // by tree id: max_k sum_{f in k} dist(tip f)
   struct Dev {
     double *total = nullptr, *col_val = nullptr;
     float *inv_total_f = nullptr;
@@ -470,20 +507,35 @@ double accum_bound(uf_tree *tree, uf_table *table, int kind) {
   double pres;
   {
     std::lock_guard<std::mutex> g(table->mu);
-    auto it = table->presence_bound.find(tree);
+    auto it = table->presence_bound.find(tree->id);
     if (it == table->presence_bound.end()) {
-      std::vector<double> per(table->n, 0.0);
-      const int32_t *tip_node_of = nullptr;
       std::vector<int32_t> tip_node(tree->n_tips);
       for (int64_t v = 0; v < tree->n_nodes; v++)
         if (tree->tip_of_node[v] >= 0) tip_node[tree->tip_of_node[v]] = (int32_t)v;
-      tip_node_of = tip_node.data();
-      for (int64_t f = 0; f < table->n_features; f++)
-        for (int64_t q = table->col_ptr[f]; q < table->col_ptr[f + 1]; q++)
-          per[table->col_row[q]] += tree->dist[tip_node_of[f]];
+      // per-sample sums over feature ranges of about equal entries, one per thread
+      const int T = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), table->nnz / 200000));
+      std::vector<int64_t> f_lo(T + 1, table->n_features);
+      f_lo[0] = 0;
+      for (int c = 1, f = 0; c < T; c++) {
+        const int64_t want = table->nnz * c / T;
+        while (f < table->n_features && table->col_ptr[f] < want) f++;
+        f_lo[c] = f;
+      }
+      std::vector<std::vector<double>> part(T, std::vector<double>(table->n, 0.0));
+      parallel_for(T, [&](int c) {
+        double *per = part[c].data();
+        for (int64_t f = f_lo[c]; f < f_lo[c + 1]; f++) {
+          const double d = tree->dist[tip_node[f]];
+          for (int64_t q = table->col_ptr[f]; q < table->col_ptr[f + 1]; q++) per[table->col_row[q]] += d;
+        }
+      });
       double mx = 0.0;
-      for (double x : per) mx = std::max(mx, x);
-      it = table->presence_bound.emplace(tree, mx).first;
+      for (int64_t k = 0; k < table->n; k++) {
+        double x = 0.0;
+        for (int c = 0; c < T; c++) x += part[c][k];
+        mx = std::max(mx, x);
+      }
+      it = table->presence_bound.emplace(tree->id, mx).first;
     }
     pres = std::min(tree->total_length, it->second);
   }
@@ -1453,6 +1505,8 @@ uf_status uf_tree_create(int64_t n_nodes, const int64_t *parent, const double *l
   }
   try {
     auto t = std::make_unique<uf_tree>();
+    static std::atomic<uint64_t> next_tree_id{1};
+    t->id = next_tree_id++;
     t->n_nodes = n_nodes;
     t->parent.assign(parent, parent + n_nodes);
     t->length.assign(length, length + n_nodes);
@@ -1527,16 +1581,38 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
       return fail(UF_ETABLE, "sample %lld is empty or indptr decreases", (long long)k);
   const int64_t nnz = indptr[n_samples];
   if (nnz > 0 && (!indices || !data)) return fail(UF_EINVAL, "null indices or data");
-  for (int64_t k = 0; k < n_samples; k++)
-    for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
-      if (indices[q] < 0 || indices[q] >= n_features)
-        return fail(UF_ETABLE, "sample %lld: feature index %d out of range", (long long)k, indices[q]);
-      if (q > indptr[k] && indices[q] <= indices[q - 1])
-        return fail(UF_ETABLE, "sample %lld: feature indices not strictly increasing", (long long)k);
-      if (!std::isfinite(data[q]) || data[q] <= 0.0)
-        return fail(UF_ETABLE, "sample %lld: count %g must be finite and > 0", (long long)k, data[q]);
-    }
   try {
+    // sample ranges of about equal nonzeros, one per host thread
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), nnz / 100000));
+    std::vector<int64_t> k_lo(T + 1, n_samples);
+    k_lo[0] = 0;
+    for (int c = 1, k = 0; c < T; c++) {
+      const int64_t want = nnz * c / T;
+      while (k < n_samples && indptr[k] < want) k++;
+      k_lo[c] = k;
+    }
+    // validation (first failing sample wins, as a sequential scan would report)
+    std::vector<int64_t> bad_k(T, -1);
+    std::vector<std::string> bad_msg(T);
+    parallel_for(T, [&](int c) {
+      char buf[160];
+      for (int64_t k = k_lo[c]; k < k_lo[c + 1]; k++)
+        for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
+          if (indices[q] < 0 || indices[q] >= n_features)
+            snprintf(buf, sizeof buf, "sample %lld: feature index %d out of range", (long long)k, indices[q]);
+          else if (q > indptr[k] && indices[q] <= indices[q - 1])
+            snprintf(buf, sizeof buf, "sample %lld: feature indices not strictly increasing", (long long)k);
+          else if (!std::isfinite(data[q]) || data[q] <= 0.0)
+            snprintf(buf, sizeof buf, "sample %lld: count %g must be finite and > 0", (long long)k, data[q]);
+          else
+            continue;
+          bad_k[c] = k;
+          bad_msg[c] = buf;
+          return;
+        }
+    });
+    for (int c = 0; c < T; c++)
+      if (bad_k[c] >= 0) return fail(UF_ETABLE, "%s", bad_msg[c].c_str());
     auto t = std::make_unique<uf_table>();
     static std::atomic<uint64_t> next_id{1};
     t->id = next_id++;
@@ -1545,29 +1621,48 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
     t->nnz = nnz;
     t->total.assign(n_samples, 0.0);
     t->inv_total_f.assign(n_samples, 0.f);
-    for (int64_t k = 0; k < n_samples; k++) {
-      double s = 0.0;
-      for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) s += data[q];
-      t->total[k] = s;
-      t->inv_total_f[k] = (float)(1.0 / s);
-    }
-    t->col_ptr.assign(n_features + 1, 0);
-    for (int64_t q = 0; q < nnz; q++) t->col_ptr[indices[q] + 1]++;
-    for (int64_t f = 0; f < n_features; f++) t->col_ptr[f + 1] += t->col_ptr[f];
-    t->col_row.assign(std::max<int64_t>(nnz, 1), 0);
-    t->col_val.assign(std::max<int64_t>(nnz, 1), 0.0);
-    std::vector<int64_t> fill(n_features, 0);
-    for (int64_t k = 0; k < n_samples; k++)
-      for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
-        const int64_t f = indices[q];
-        const int64_t at = t->col_ptr[f] + fill[f]++;
-        t->col_row[at] = (int32_t)k;
-        t->col_val[at] = data[q];
+    // CSC view by a counting sort: per-thread column counts, then each thread
+    // scatters its samples (in increasing order) behind the earlier threads'
+    std::vector<std::vector<int64_t>> cnt(T, std::vector<int64_t>(n_features, 0));
+    parallel_for(T, [&](int c) {
+      int64_t *cc = cnt[c].data();
+      for (int64_t k = k_lo[c]; k < k_lo[c + 1]; k++) {
+        double s = 0.0;
+        for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
+          s += data[q];
+          cc[indices[q]]++;
+        }
+        t->total[k] = s;
+        t->inv_total_f[k] = (float)(1.0 / s);
       }
+    });
+    t->col_ptr.assign(n_features + 1, 0);
+    for (int64_t f = 0; f < n_features; f++) {
+      int64_t at = t->col_ptr[f];
+      for (int c = 0; c < T; c++) {
+        const int64_t x = cnt[c][f];
+        cnt[c][f] = at;  // this thread's first slot in column f
+        at += x;
+      }
+      t->col_ptr[f + 1] = at;
+    }
+    t->col_row.resize(std::max<int64_t>(nnz, 1));  // every entry written below (nnz >= 1)
+    t->col_val.resize(std::max<int64_t>(nnz, 1));
+    parallel_for(T, [&](int c) {
+      int64_t *slot = cnt[c].data();
+      for (int64_t k = k_lo[c]; k < k_lo[c + 1]; k++)
+        for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
+          const int64_t at = slot[indices[q]]++;
+          t->col_row[at] = (int32_t)k;
+          t->col_val[at] = data[q];
+        }
+    });
     *out = t.release();
     return UF_OK;
   } catch (const std::bad_alloc &) {
     return fail(UF_ENOMEM, "host allocation failed");
+  } catch (const std::system_error &) {
+    return fail(UF_ENOMEM, "could not start host threads");
   }
 }
 

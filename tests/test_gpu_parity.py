@@ -255,3 +255,32 @@ def test_generalized_length_scales(factor):
                     assert_close(got, exp, "generalized", precision, f"x{factor} alpha={alpha} sparse={sparse}")
             finally:
                 uf.uf_set_option("sparse", 1)
+
+
+def test_concurrent_calls_from_threads():
+    # each host thread captures its call on its own private stream; results
+    # equal those of one thread bit for bit
+    import threading
+    tree_s = yule_tree(2000, seed=97)
+    table_s = table_iid(300, tree_s.n_tips, 0.03, seed=98)
+    tree, table = handles(tree_s, table_s)
+    jobs = [(m, 0.5 if m == "generalized" else 1.0, p) for m in METHODS for p in PRECISIONS]
+    ref = {j: uf.uf_compute(tree, table, j[0], j[1], j[2])[0] for j in jobs}
+    got, errors = {}, []
+
+    def work(sub):
+        try:
+            for _ in range(2):
+                for j in sub:
+                    got[j] = uf.uf_compute(tree, table, j[0], j[1], j[2])[0]
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(jobs[k::4],)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for j in jobs:
+        np.testing.assert_array_equal(got[j], ref[j])

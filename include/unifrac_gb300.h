@@ -139,6 +139,12 @@ typedef struct {
  *                    numbers).  Applies to the CUDA-core stripe kernels and
  *                    to the tensor-core unweighted path; the results agree
  *                    within the precision's tolerance.
+ *   "sparse_region_bytes"  48,000,000 (default; 0 restores it): a one-table
+ *                    call whose stripe accumulators exceed this many bytes
+ *                    writes the scattered branches' sample lists once and
+ *                    adds their pairs stripe region by region, each region's
+ *                    accumulators at most this size (so that they stay in L2);
+ *                    at least 4,096
  * uf_set_option returns UF_EINVAL for an unknown name or a bad value;
  * uf_get_option returns -1 for an unknown name.
  */

@@ -732,8 +732,19 @@ struct RowSplit {
 // scatters every branch that fits; mode 0 none.  The choice depends on the
 // tree and the tables only, not on the stripe range, so that a range run
 // gives bitwise the stripes of the full run.
-// path: ACC_MIN or ACC_GEN (CUDA-core stripe kernels) or SPLIT_GRAM (tensor cores)
+// Stripe regions of a call's sparse scatter: one table whose accumulators
+// exceed the L2 budget scatters region by region (launch_sparse_region) so
+// that every region's cells stay in L2; otherwise one region.
+constexpr double SPARSE_REGION_BYTES_DEFAULT = 48e6;
+std::atomic<int64_t> g_region_bytes{(int64_t)SPARSE_REGION_BYTES_DEFAULT};
+// split and region path: ACC_MIN or ACC_GEN (CUDA-core stripe kernels) or SPLIT_GRAM (tensor cores)
 constexpr int SPLIT_GRAM = 2;
+double sparse_regions(size_t n_tables, int acc, double acc_bytes) {
+  const double budget = (double)g_region_bytes.load();
+  if (n_tables != 1 || acc == SPLIT_GRAM || acc_bytes <= budget) return 1.0;
+  return std::ceil(acc_bytes / budget);
+}
+
 RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int acc, bool fp32) {
   RowSplit R;
   const int mode = (int)g_sparse.load();
@@ -751,7 +762,11 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
       cells += std::floor(n / 2.0) * n;
       cols += n;
     }
-    const double atom_rate = cells * 8.0 * n_acc <= 64e6 ? 2.3e11 : 2.5e10;
+    // accumulators beyond L2: one table scatters region by region in L2
+    // (sparse_regions), several tables scatter straight into HBM-resident cells
+    const bool regions = sparse_regions(nt, acc, cells * 8.0 * n_acc) > 1;
+    const double atom_rate = cells * 8.0 * n_acc <= 64e6 || regions ? 2.3e11 : 2.5e10;
+    const double n_regions = regions ? sparse_regions(nt, acc, cells * 8.0 * n_acc) : 1.0;
     double dense_rate;  // cell updates per second of the dense kernel
     if (acc == SPLIT_GRAM) dense_rate = 2.5e14;
     else dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
@@ -779,6 +794,7 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
         const double pr = (double)ub * (double)(ub - 1) / 2.0;
         pairs += pr;
         cost += job_cost + pr * (1.0 / visit_rate + n_acc / atom_rate) + (double)ub * 4.0 / atom_rate;
+        if (regions) cost += n_regions * (job_cost + (double)ub * 4e-11);  // one visit per region
       }
       if (mx > SPARSE_MAX_ENTRIES) continue;
       if (mode == 2 || cost < dense_t) {
@@ -1171,13 +1187,35 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const size_t o_cnt = meta.add(split.cnt_lists);
   const size_t o_dense = meta.add(split.dense);
   const size_t o_dlen = meta.add(split.dense_len);
-  size_t o_sparse = 0, o_sptabs = 0;
+  size_t o_sparse = 0, o_sptabs = 0, o_lofs = 0;
   std::vector<int64_t> sp_off;  // first entry of each capacity class in the sparse list
+  // one table whose accumulators exceed the L2 budget: the sparse rows write
+  // their sample lists, then scatter their pairs stripe region by region
+  const int n_acc = acc == ACC_GEN ? 2 : 1;
+  const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc);
+  const bool region_mode = split.n_sparse > 0 && n_regions > 1;
+  int64_t n_sparse_rows = 0;
+  DevBuf lk, lx, lf, lz;
   if (split.n_sparse > 0) {
     std::vector<int32_t> all;
     for (const auto &c : split.sparse) {
       sp_off.push_back((int64_t)all.size());
       all.insert(all.end(), c.begin(), c.end());
+    }
+    n_sparse_rows = (int64_t)all.size();
+    if (region_mode) {
+      const auto &cp = J.tabs[0].table->col_ptr;
+      std::vector<int64_t> lofs(all.size() + 1, 0);
+      for (size_t r = 0; r < all.size(); r++)
+        lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
+      const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
+      lk = DevBuf(total_e * 4, st, "alloc sparse lists");
+      lx = DevBuf(total_e * es, st, "alloc sparse lists");
+      lf = DevBuf(total_e * 8, st, "alloc sparse lists");
+      lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
+      // rows without entries in the table return before writing their count
+      ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
+      o_lofs = meta.add(lofs);
     }
     std::vector<SpTab> sp(nt);
     for (size_t t = 0; t < nt; t++) {
@@ -1235,26 +1273,50 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   Capture cap(g_graph.load() != 0 && !timer.on && !tune, st, device);
   const cudaStream_t ls = cap.stream();
   // the sparse-row scatters run after the dense blocks, whose chunk tuning clears M
+  auto sparse_args = [&]() {
+    SparseArgs sp{};
+    sp.tip_lo = in.td->tip_lo;
+    sp.tip_hi = in.td->tip_hi;
+    sp.length = in.td->length;
+    sp.tabs = meta.at<SpTab>(o_sptabs);
+    sp.n_tabs = (int)nt;
+    sp.kind = kind;
+    sp.mixed_forms = fp32 && acc == ACC_MIN;
+    sp.M = M.as<unsigned long long>();
+    sp.M2 = M2.as<unsigned long long>();
+    sp.Dsp = Dsp.as<unsigned long long>();
+    sp.alpha = J.alpha;
+    sp.scale = scale;
+    if (region_mode) {
+      sp.lk = lk.as<int32_t>();
+      sp.lx = lx.p;
+      sp.lf = lf.as<long long>();
+      sp.lofs = meta.at<int64_t>(o_lofs);
+      sp.lz = lz.as<int>();
+    }
+    return sp;
+  };
   auto launch_sparse = [&](cudaStream_t on) {
     for (size_t c = 0; c < split.sparse.size(); c++) {
       if (split.sparse[c].empty()) continue;
-      SparseArgs sp{};
+      SparseArgs sp = sparse_args();
+      sp.write_lists = region_mode ? 1 : 0;
+      sp.row_base = (int)sp_off[c];
       sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
       sp.n_nodes = (int)split.sparse[c].size();
       sp.cap = split.cap[c];
-      sp.tip_lo = in.td->tip_lo;
-      sp.tip_hi = in.td->tip_hi;
-      sp.length = in.td->length;
-      sp.tabs = meta.at<SpTab>(o_sptabs);
-      sp.n_tabs = (int)nt;
-      sp.kind = kind;
-      sp.mixed_forms = fp32 && acc == ACC_MIN;
-      sp.M = M.as<unsigned long long>();
-      sp.M2 = M2.as<unsigned long long>();
-      sp.Dsp = Dsp.as<unsigned long long>();
-      sp.alpha = J.alpha;
-      sp.scale = scale;
       ck(launch_sparse_rows(acc, fp32, sp, on), "sparse rows");
+      kernels++;
+    }
+    if (!region_mode) return;
+    const int64_t per = std::max<int64_t>(1, (int64_t)((double)g_region_bytes.load() / (8.0 * n_acc * tabs[0].n)));
+    for (int64_t r0 = tabs[0].s_lo; r0 <= tabs[0].s_hi; r0 += per) {
+      SparseArgs sp = sparse_args();
+      sp.nodes = meta.at<int32_t>(o_sparse);
+      sp.n_nodes = (int)n_sparse_rows;
+      sp.r0 = (int)r0;
+      sp.r1 = (int)std::min<int64_t>(r0 + per, (int64_t)tabs[0].s_hi + 1);
+      ck(launch_sparse_region(acc, fp32, sp, on), "sparse regions");
       kernels++;
     }
   };
@@ -1455,6 +1517,11 @@ uf_status uf_set_option(const char *name, int64_t value) {
     g_sparse = value;
     return UF_OK;
   }
+  if (!strcmp(name, "sparse_region_bytes")) {
+    if (value != 0 && value < 4096) return fail(UF_EINVAL, "sparse_region_bytes must be 0 or >= 4096");
+    g_region_bytes = value ? value : (int64_t)SPARSE_REGION_BYTES_DEFAULT;
+    return UF_OK;
+  }
   return fail(UF_EINVAL, "unknown option '%s'", name);
 }
 
@@ -1466,6 +1533,7 @@ int64_t uf_get_option(const char *name) {
   if (!strcmp(name, "graph")) return g_graph.load();
   if (!strcmp(name, "autotune")) return g_autotune.load();
   if (!strcmp(name, "sparse")) return g_sparse.load();
+  if (!strcmp(name, "sparse_region_bytes")) return g_region_bytes.load();
   return -1;
 }
 

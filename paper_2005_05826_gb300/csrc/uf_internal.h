@@ -158,11 +158,28 @@ struct SparseArgs {
                             // diagonal takes the per-sample terms; Dsp unused)
   unsigned long long *M, *M2, *Dsp;  // cells (M / den), Q (generalized), per-sample diagonal R
   double alpha, scale;
+  // list mode (one table): instead of scattering its pairs, row blockIdx.x
+  // writes its distinct samples, values and fixed-point terms at
+  // lofs[row_base + blockIdx.x] (count in lz) for launch_sparse_region
+  int write_lists, row_base;
+  int32_t *lk;              // distinct samples, ascending
+  void *lx;                 // their x (min form) or u (generalized), float or double
+  long long *lf;            // their fixed-point X or P
+  const int64_t *lofs;      // first entry of each row
+  int *lz;                  // entries of each row
+  // region mode: only pairs whose stripe lies in [r0, r1) (launch_sparse_region)
+  int r0, r1;
 };
 // largest subtree entry count a sparse row may have
 constexpr int SPARSE_MAX_ENTRIES = 4096;
 size_t sparse_smem_bytes(bool fp32, int cap);
 cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
+// Pairs of the listed rows (nodes[0 .. n_nodes), lists from a list-mode
+// launch, table tabs[0]) whose stripe lies in [a.r0, a.r1): one CTA per row,
+// each thread takes samples a and finds the partners b of the two windows
+// of k_b - k_a that map into the region by binary search.  Run region by
+// region so that the accumulator cells a launch touches stay in L2.
+cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 
 // ---- unweighted on tensor cores (uf_gram.cu) ----
 // One table of a batch: its samples occupy rows [row_base, row_base + n_pad)

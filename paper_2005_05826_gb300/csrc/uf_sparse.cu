@@ -167,6 +167,18 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
   } else {
     for (int e = tid; e < z; e += NT) red_add(a.Dsp + tb.off + ks[e], fx[e]);
   }
+  if (a.write_lists) {  // the pairs go out region by region (k_sparse_region)
+    const int row = a.row_base + blockIdx.x;
+    const int64_t off = a.lofs[row];
+    T *lx = reinterpret_cast<T *>(a.lx);
+    for (int e = tid; e < z; e += NT) {
+      a.lk[off + e] = ks[e];
+      lx[off + e] = xs[e];
+      a.lf[off + e] = fx[e];
+    }
+    if (tid == 0) a.lz[row] = z;
+    return;
+  }
   // pairs (ia < ib) numbered row by row: row ia starts at ia (2z - ia - 1) / 2
   const int64_t npairs = (int64_t)z * (z - 1) / 2;
   if (npairs == 0) return;
@@ -235,6 +247,72 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
   }
 }
 
+// first index in [lo, hi) of the ascending ks with ks[i] >= key
+__device__ __forceinline__ int lower_index(const int32_t *ks, int lo, int hi, int key) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (ks[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <typename T, int ACC, int MODE>
+__global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
+  const int row = blockIdx.x;
+  const int v = a.nodes[row];
+  const SpTab tb = a.tabs[0];
+  const int64_t off = a.lofs[row];
+  // never past the row's list capacity
+  const int z = (int)min((int64_t)a.lz[row], a.lofs[row + 1] - off);
+  const int32_t *ks = a.lk + off;
+  const T *xs = reinterpret_cast<const T *>(a.lx) + off;
+  const long long *fx = a.lf + off;
+  const int n = tb.n, half = n / 2;
+  unsigned long long *M = a.M + tb.m_off;
+  unsigned long long *M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
+  const T lt = (T)a.length[v], am1 = (T)(a.alpha - 1.0);
+  for (int ia = threadIdx.x; ia < z - 1; ia += blockDim.x) {
+    const int ka = ks[ia];
+    // window 1: d = k_b - k_a in [r0 + 1, min(r1, n/2)], stripe d - 1, cell column k_a
+    // window 2: d in [max(n - r1, n/2 + 1), n - r0 - 1], stripe n - d - 1, column k_b
+    const int d_lo[2] = {a.r0 + 1, max(n - a.r1, half + 1)};
+    const int d_hi[2] = {min(a.r1, half), n - a.r0 - 1};
+#pragma unroll
+    for (int w = 0; w < 2; w++) {
+      if (d_lo[w] > d_hi[w]) continue;
+      const int b0 = lower_index(ks, ia + 1, z, ka + d_lo[w]);
+      const int b1 = lower_index(ks, b0, z, ka + d_hi[w] + 1);
+      for (int ib = b0; ib < b1; ib++) {
+        const int kb = ks[ib];
+        const int d = kb - ka;
+        const int s = w == 0 ? d - 1 : n - d - 1;
+        const int kc = w == 0 ? ka : kb;
+        const int64_t cell = (int64_t)(s - tb.s_lo) * n + kc;
+        const bool dup = 2 * d == n;  // also stored at k = kb (= ka + n/2)
+        if (ACC == ACC_MIN) {
+          long long t = min(fx[ia], fx[ib]);
+          if (a.mixed_forms && fp32_abs_row(s)) t *= -2;
+          red_add(M + cell, t);
+          if (dup) red_add(M + cell + d, t);
+        } else {
+          const T uu = xs[ia], vv = xs[ib];
+          const T wgt = lt * pow_am1<T, MODE>(uu + vv, am1);
+          const long long q = to_fixed(wgt * tmin<T>(uu, vv), a.scale);
+          const long long e = to_fixed(wgt * (uu > vv ? uu - vv : vv - uu), a.scale);
+          const long long den = 2 * q + e - fx[ia] - fx[ib];
+          red_add(M + cell, den);
+          red_add(M2 + cell, q);
+          if (dup) {
+            red_add(M + cell + d, den);
+            red_add(M2 + cell + d, q);
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename T, int ACC, int MODE>
 cudaError_t launch_one(const SparseArgs &a, size_t smem, cudaStream_t st) {
   auto kernel = k_sparse_rows<T, ACC, MODE>;
@@ -261,6 +339,23 @@ cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStre
   if (acc == ACC_MIN) return fp32 ? launch_one<float, ACC_MIN, 0>(a, smem, st) : launch_one<double, ACC_MIN, 0>(a, smem, st);
   if (fp32) return mode == 0 ? launch_one<float, ACC_GEN, 0>(a, smem, st) : launch_one<float, ACC_GEN, 1>(a, smem, st);
   return mode == 0 ? launch_one<double, ACC_GEN, 0>(a, smem, st) : launch_one<double, ACC_GEN, 1>(a, smem, st);
+}
+
+cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaStream_t st) {
+  if (a.n_nodes <= 0 || a.r0 >= a.r1) return cudaSuccess;
+  const int mode = a.alpha == 0.5 ? 0 : 1;
+  const dim3 grid((unsigned)a.n_nodes);
+  if (acc == ACC_MIN) {
+    if (fp32) k_sparse_region<float, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
+    else k_sparse_region<double, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
+  } else if (fp32) {
+    if (mode == 0) k_sparse_region<float, ACC_GEN, 0><<<grid, 128, 0, st>>>(a);
+    else k_sparse_region<float, ACC_GEN, 1><<<grid, 128, 0, st>>>(a);
+  } else {
+    if (mode == 0) k_sparse_region<double, ACC_GEN, 0><<<grid, 128, 0, st>>>(a);
+    else k_sparse_region<double, ACC_GEN, 1><<<grid, 128, 0, st>>>(a);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace ufg

@@ -234,3 +234,36 @@ def test_yule50k_n2048_default_split():
             got, rep = run(tree, table, method, a, precision, 1)
             assert rep.sparse_rows > (tree_s.n_nodes - 1) // 3, rep.sparse_rows
             assert_close(got[condensed_index(n, i, j)], exp, method, precision, "yule50k sparse=1")
+
+
+@pytest.mark.parametrize("n", [97, 300])
+def test_region_scatter_matches_direct_bitwise(n):
+    # a one-table call whose accumulators exceed the region budget writes the
+    # sample lists and scatters stripe region by region; integer sums are
+    # order-free, so the result equals the direct scatter bit for bit
+    tree_s = yule_tree(900, seed=270 + n)
+    table_s = table_iid(n, tree_s.n_tips, 0.04, seed=271 + n)
+    tree, table = handles(tree_s, table_s)
+    S = uf.uf_stripe_count(n)
+    uf.uf_set_option("tensor_path", 0)
+    try:
+        for method in METHODS:
+            a = 0.5 if method == "generalized" else 1.0
+            exp = oracle.condensed(tree_s, table_s, method, a)
+            for precision in PRECISIONS:
+                direct, rep0 = run(tree, table, method, a, precision, 2)
+                uf.uf_set_option("sparse_region_bytes", 8192)
+                try:
+                    regional, rep1 = run(tree, table, method, a, precision, 2)
+                    part, _ = run(tree, table, method, a, precision, 2, 3, S - 2)
+                finally:
+                    uf.uf_set_option("sparse_region_bytes", 0)
+                assert rep1.sparse_rows == rep0.sparse_rows > 0
+                np.testing.assert_array_equal(regional, direct)
+                assert_close(regional, exp, method, precision, f"regions n={n}")
+                whole, _ = run(tree, table, method, a, precision, 2, 0, S)
+                _, _, exp_striped, _ = oracle.striped(tree_s, table_s, method, a, 0, S)
+                assert_close(part.ravel(), exp_striped[3:S - 2].ravel(), method, precision, "region range")
+    finally:
+        uf.uf_set_option("tensor_path", 1)
+    assert uf.uf_get_option("sparse_region_bytes") == 48_000_000

@@ -210,7 +210,8 @@ def workload_config(args, tree_s, table_s, l2):
             "methods": [m for m, _ in METHODS], "alpha": 0.5,
             "stripes": "all" if not 0 < getattr(args, "stripe_stop", 0) < table_s.n_samples // 2
             else f"[0, {args.stripe_stop}) of {table_s.n_samples // 2}",
-            "sparse_rows_mode": getattr(args, "sparse", 1), "l2": l2}
+            "sparse_rows_mode": getattr(args, "sparse", 1),
+            "sparse_region_bytes": getattr(args, "region_bytes", 0) or "default", "l2": l2}
 
 
 def max_errors(tree_s, table_s, outs, precision, stop=None):
@@ -392,6 +393,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     uf.uf_set_option("kernel_timing", 1)
     uf.uf_set_option("sparse", args.sparse)
+    uf.uf_set_option("sparse_region_bytes", args.region_bytes)
 
     def step(precision, reps=None):
         for (m, a), o in zip(METHODS, outs):
@@ -657,6 +659,8 @@ def main():
                     help="FP32 distance outputs (halves the output memory of very large runs)")
     ap.add_argument("--stripe-stop", type=int, default=0,
                     help="time the stripe range [0, K) of every method instead of all stripes (0: all)")
+    ap.add_argument("--region-bytes", type=int, default=0,
+                    help="option sparse_region_bytes (0: the library default)")
     ap.add_argument("--sparse", type=int, choices=[0, 1, 2], default=1,
                     help="sparse-row path: 0 every branch dense, 1 cost model (default), 2 every branch that fits")
     args = ap.parse_args()

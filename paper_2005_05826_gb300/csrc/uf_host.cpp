@@ -136,8 +136,8 @@ struct Plan {
 };
 
 struct RowSplit;
-// (table ids, accumulator, FP32, sparse mode, block rows)
-using SplitKey = std::tuple<std::vector<uint64_t>, int, int, int, int64_t>;
+// (table ids, accumulator, FP32, sparse mode, block rows, region budget)
+using SplitKey = std::tuple<std::vector<uint64_t>, int, int, int, int64_t, int64_t>;
 
 }  // namespace
 
@@ -713,6 +713,7 @@ struct RowSplit {
   std::vector<double> dense_len;    // their branch lengths
   std::vector<std::vector<int32_t>> sparse;  // sparse branch nodes by capacity class
   std::vector<int> cap;             // shared-memory entries of each class
+  bool lists = false;               // one table beyond L2: sample lists + stripe regions
   int64_t n_sparse = 0;
   double pairs = 0.0;               // both-nonzero pairs scattered, at most (sum over tables)
   int64_t max_dense = 0;            // most dense rows in one block
@@ -750,9 +751,9 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
   const int mode = (int)g_sparse.load();
   const int64_t nb = tree->n_nodes - 1;
   const size_t nt = J.tabs.size();
-  const int classes[4] = {128, 512, 2048, SPARSE_MAX_ENTRIES};
-  R.cap.assign(classes, classes + 4);
-  R.sparse.resize(4);
+  const int classes[5] = {128, 512, 2048, SPARSE_MAX_ENTRIES, SPARSE_LIST_MAX_ENTRIES};
+  R.cap.assign(classes, classes + 5);
+  R.sparse.resize(5);
   std::vector<char> is_sparse(std::max<int64_t>(nb, 1), 0);
   if (mode != 0) {
     const int n_acc = acc == ACC_GEN ? 2 : 1;
@@ -765,6 +766,9 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
     // accumulators beyond L2: one table scatters region by region in L2
     // (sparse_regions), several tables scatter straight into HBM-resident cells
     const bool regions = sparse_regions(nt, acc, cells * 8.0 * n_acc) > 1;
+    R.lists = regions;
+    // list mode keeps only sort keys in shared memory: longer runs fit
+    const int64_t max_entries = regions ? SPARSE_LIST_MAX_ENTRIES : SPARSE_MAX_ENTRIES;
     const double atom_rate = cells * 8.0 * n_acc <= 64e6 || regions ? 2.3e11 : 2.5e10;
     const double n_regions = regions ? sparse_regions(nt, acc, cells * 8.0 * n_acc) : 1.0;
     double dense_rate;  // cell updates per second of the dense kernel
@@ -796,7 +800,7 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
         cost += job_cost + pr * (1.0 / visit_rate + n_acc / atom_rate) + (double)ub * 4.0 / atom_rate;
         if (regions) cost += n_regions * (job_cost + (double)ub * 4e-11);  // one visit per region
       }
-      if (mx > SPARSE_MAX_ENTRIES) continue;
+      if (mx > max_entries) continue;
       if (mode == 2 || cost < dense_t) {
         is_sparse[v] = 1;
         int c = 0;
@@ -861,6 +865,7 @@ std::shared_ptr<const RowSplit> get_split(uf_tree *tree, const BatchJob &J, cons
   std::get<2>(key) = fp32 ? 1 : 0;
   std::get<3>(key) = (int)g_sparse.load();
   std::get<4>(key) = P->block_rows;
+  std::get<5>(key) = g_region_bytes.load();
   std::lock_guard<std::mutex> g(tree->mu);
   auto it = tree->splits.find(key);
   if (it != tree->splits.end()) return it->second;
@@ -1193,7 +1198,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   // their sample lists, then scatter their pairs stripe region by region
   const int n_acc = acc == ACC_GEN ? 2 : 1;
   const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc);
-  const bool region_mode = split.n_sparse > 0 && n_regions > 1;
+  const bool region_mode = split.n_sparse > 0 && (n_regions > 1 || split.lists);
   int64_t n_sparse_rows = 0;
   DevBuf lk, lx, lf, lz;
   if (split.n_sparse > 0) {
@@ -1300,12 +1305,12 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     for (size_t c = 0; c < split.sparse.size(); c++) {
       if (split.sparse[c].empty()) continue;
       SparseArgs sp = sparse_args();
-      sp.write_lists = region_mode ? 1 : 0;
       sp.row_base = (int)sp_off[c];
       sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
       sp.n_nodes = (int)split.sparse[c].size();
       sp.cap = split.cap[c];
-      ck(launch_sparse_rows(acc, fp32, sp, on), "sparse rows");
+      if (region_mode) ck(launch_sparse_lists(acc, fp32, sp, on), "sparse lists");
+      else ck(launch_sparse_rows(acc, fp32, sp, on), "sparse rows");
       kernels++;
     }
     if (!region_mode) return;

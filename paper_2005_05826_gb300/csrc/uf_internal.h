@@ -158,10 +158,10 @@ struct SparseArgs {
                             // diagonal takes the per-sample terms; Dsp unused)
   unsigned long long *M, *M2, *Dsp;  // cells (M / den), Q (generalized), per-sample diagonal R
   double alpha, scale;
-  // list mode (one table): instead of scattering its pairs, row blockIdx.x
-  // writes its distinct samples, values and fixed-point terms at
-  // lofs[row_base + blockIdx.x] (count in lz) for launch_sparse_region
-  int write_lists, row_base;
+  // list mode (one table, launch_sparse_lists): row blockIdx.x writes its
+  // distinct samples, values and fixed-point terms at lofs[row_base +
+  // blockIdx.x] (count in lz) for launch_sparse_region
+  int row_base;
   int32_t *lk;              // distinct samples, ascending
   void *lx;                 // their x (min form) or u (generalized), float or double
   long long *lf;            // their fixed-point X or P
@@ -170,10 +170,13 @@ struct SparseArgs {
   // region mode: only pairs whose stripe lies in [r0, r1) (launch_sparse_region)
   int r0, r1;
 };
-// largest subtree entry count a sparse row may have
+// largest subtree entry count a sparse row may have: scattered directly from
+// shared memory, or written as a list (one table, keys alone in shared memory)
 constexpr int SPARSE_MAX_ENTRIES = 4096;
+constexpr int SPARSE_LIST_MAX_ENTRIES = 16384;
 size_t sparse_smem_bytes(bool fp32, int cap);
 cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
+cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 // Pairs of the listed rows (nodes[0 .. n_nodes), lists from a list-mode
 // launch, table tabs[0]) whose stripe lies in [a.r0, a.r1): one CTA per row,
 // each thread takes samples a and finds the partners b of the two windows

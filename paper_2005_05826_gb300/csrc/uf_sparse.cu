@@ -167,18 +167,7 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
   } else {
     for (int e = tid; e < z; e += NT) red_add(a.Dsp + tb.off + ks[e], fx[e]);
   }
-  if (a.write_lists) {  // the pairs go out region by region (k_sparse_region)
-    const int row = a.row_base + blockIdx.x;
-    const int64_t off = a.lofs[row];
-    T *lx = reinterpret_cast<T *>(a.lx);
-    for (int e = tid; e < z; e += NT) {
-      a.lk[off + e] = ks[e];
-      lx[off + e] = xs[e];
-      a.lf[off + e] = fx[e];
-    }
-    if (tid == 0) a.lz[row] = z;
-    return;
-  }
+
   // pairs (ia < ib) numbered row by row: row ia starts at ia (2z - ia - 1) / 2
   const int64_t npairs = (int64_t)z * (z - 1) / 2;
   if (npairs == 0) return;
@@ -245,6 +234,77 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
       ib = ia + 1;
     }
   }
+}
+
+// List mode: the row's CSC run is sorted in shared memory as 8-byte keys
+// only (so runs of up to SPARSE_LIST_MAX_ENTRIES fit), equal samples are
+// summed in entry order reading the counts from global memory, and each
+// distinct sample's k, x (or u) and fixed-point term go straight to the
+// row's list; the per-sample terms R are added here once.
+template <typename T, int ACC, int MODE>
+__global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int sh[33];
+  unsigned long long *key = reinterpret_cast<unsigned long long *>(smem_raw);  // (sample << 32) | entry
+  const int v = a.nodes[blockIdx.x];
+  const int row = a.row_base + blockIdx.x;
+  const SpTab tb = a.tabs[0];
+  const int64_t q0 = tb.col_ptr[a.tip_lo[v]];
+  const int L = (int)(tb.col_ptr[a.tip_hi[v]] - q0);
+  // the host sizes cap to every run of the launch and lz starts at 0
+  if (L <= 0 || L > a.cap) return;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  int P2 = 1;
+  while (P2 < L) P2 <<= 1;
+  for (int i = tid; i < P2; i += NT)
+    key[i] = i < L ? ((unsigned long long)(unsigned)tb.col_row[q0 + i] << 32) | (unsigned)i : ~0ull;
+  __syncthreads();
+  int unsorted = 0;
+  for (int i = tid + 1; i < L; i += NT) unsorted |= (key[i] >> 32) <= (key[i - 1] >> 32);
+  if (__syncthreads_or(unsorted)) {
+    for (int k = 2; k <= P2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < P2; i += NT) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long x = key[i], y = key[ixj];
+            if ((x > y) == ((i & k) == 0)) {
+              key[i] = y;
+              key[ixj] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+  }
+  const int E = (L + NT - 1) / NT, i0 = tid * E, i1 = min(L, i0 + E);
+  int heads = 0;
+  for (int i = i0; i < i1; i++) heads += (i == 0 || (key[i] >> 32) != (key[i - 1] >> 32));
+  int z = 0;
+  int u = block_exclusive_scan(heads, sh, &z);
+  const double l = a.length[v];
+  const T alpha = (T)a.alpha;
+  const int64_t off = a.lofs[row];
+  T *lx = reinterpret_cast<T *>(a.lx);
+  for (int i = i0; i < i1; i++) {
+    const unsigned smp = (unsigned)(key[i] >> 32);
+    if (i > 0 && (unsigned)(key[i - 1] >> 32) == smp) continue;
+    double c = 0.0;
+    for (int m = i; m < L && (unsigned)(key[m] >> 32) == smp; m++) c += tb.col_val[q0 + (key[m] & 0xffffffffu)];
+    T x;
+    if (a.kind == EMB_SCALED) x = emb_value<T, EMB_SCALED>(c, l, tb.total[smp], tb.inv_total_f[smp]);
+    else if (a.kind == EMB_PRESENCE) x = emb_value<T, EMB_PRESENCE>(c, l, tb.total[smp], tb.inv_total_f[smp]);
+    else x = emb_value<T, EMB_PROP>(c, l, tb.total[smp], tb.inv_total_f[smp]);
+    long long f;
+    if (ACC == ACC_MIN) f = to_fixed(x, a.scale);
+    else f = to_fixed((T)l * pow_alpha<T, MODE>(x, alpha), a.scale);
+    a.lk[off + u] = (int32_t)smp;
+    lx[off + u] = x;
+    a.lf[off + u] = f;
+    red_add(a.Dsp + tb.off + smp, f);
+    u++;
+  }
+  if (tid == 0) a.lz[row] = z;
 }
 
 // first index in [lo, hi) of the ascending ks with ks[i] >= key
@@ -356,6 +416,27 @@ cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaSt
     else k_sparse_region<double, ACC_GEN, 1><<<grid, 128, 0, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+size_t sparse_list_smem_bytes(int cap) { return (size_t)cap * 8; }
+
+cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStream_t st) {
+  if (a.n_nodes <= 0) return cudaSuccess;
+  if (a.cap < 128 || (a.cap & (a.cap - 1)) || a.cap > SPARSE_LIST_MAX_ENTRIES || a.n_tabs != 1)
+    return cudaErrorInvalidValue;
+  const size_t smem = sparse_list_smem_bytes(a.cap);
+  const int mode = a.alpha == 0.5 ? 0 : 1;
+  const int nt = a.cap <= 512 ? 128 : 256;
+  const dim3 grid((unsigned)a.n_nodes);
+  auto go = [&](auto kernel) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, nt, smem, st>>>(a);
+    return cudaGetLastError();
+  };
+  if (acc == ACC_MIN) return fp32 ? go(k_sparse_lists<float, ACC_MIN, 0>) : go(k_sparse_lists<double, ACC_MIN, 0>);
+  if (fp32) return mode == 0 ? go(k_sparse_lists<float, ACC_GEN, 0>) : go(k_sparse_lists<float, ACC_GEN, 1>);
+  return mode == 0 ? go(k_sparse_lists<double, ACC_GEN, 0>) : go(k_sparse_lists<double, ACC_GEN, 1>);
 }
 
 }  // namespace ufg

@@ -107,25 +107,37 @@ def test_unweighted_mixed_both_paths(tensor):
         uf.uf_set_option("tensor_path", 1)
 
 
-def test_capacity_classes():
-    # dense tables give subtrees of every entry count from 1 up past 4,096:
-    # each capacity class (128, 512, 2,048, 4,096 entries) gets rows, and the
-    # rows above the largest class stay dense
+@pytest.mark.parametrize("lists", [False, True])
+def test_capacity_classes(lists):
+    # dense tables give subtrees of every entry count from 1 up past 16,384:
+    # each capacity class (128, 512, 2,048, 4,096 entries; 16,384 when the
+    # rows are written as lists for the stripe-region scatter) gets rows, and
+    # the rows above the largest class stay dense
     tree_s = yule_tree(400, seed=221)
     table_s = table_iid(300, tree_s.n_tips, 0.3, seed=222)
     tree, table = handles(tree_s, table_s)
+    nb = tree_s.n_nodes - 1
+    sparse_rows = {}
     for method in METHODS:
         a = 0.5 if method == "generalized" else 1.0
         exp = oracle.condensed(tree_s, table_s, method, a)
         for precision in PRECISIONS:
-            if method == "unweighted" and precision == "mixed":
-                uf.uf_set_option("tensor_path", 0)
+            uf.uf_set_option("tensor_path", 0 if method == "unweighted" and precision == "mixed" else 1)
+            if lists:
+                uf.uf_set_option("sparse_region_bytes", 8192)
             try:
                 got, rep = run(tree, table, method, a, precision, 2)
             finally:
                 uf.uf_set_option("tensor_path", 1)
-            assert 0 < rep.sparse_rows < tree_s.n_nodes - 1
-            assert_close(got, exp, method, precision, "capacity classes")
+                uf.uf_set_option("sparse_region_bytes", 0)
+            assert 0 < rep.sparse_rows < nb
+            sparse_rows[(method, precision)] = rep.sparse_rows
+            assert_close(got, exp, method, precision, f"capacity classes lists={lists}")
+    if lists:
+        # the list class takes the runs of 4,097 to 16,384 entries too
+        counts = np.diff(table_s.indptr)
+        assert counts.sum() > 16384
+        assert max(sparse_rows.values()) > 0
 
 
 @pytest.mark.parametrize("n", [2, 3, 8, 9, 64, 65, 300])
@@ -236,13 +248,15 @@ def test_yule50k_n2048_default_split():
             assert_close(got[condensed_index(n, i, j)], exp, method, precision, "yule50k sparse=1")
 
 
-@pytest.mark.parametrize("n", [97, 300])
-def test_region_scatter_matches_direct_bitwise(n):
+@pytest.mark.parametrize("n,density", [(97, 0.04), (300, 0.012)])
+def test_region_scatter_matches_direct_bitwise(n, density):
     # a one-table call whose accumulators exceed the region budget writes the
     # sample lists and scatters stripe region by region; integer sums are
-    # order-free, so the result equals the direct scatter bit for bit
+    # order-free, so the result equals the direct scatter bit for bit (the
+    # tables hold at most 4,096 entries, so both modes split the branches alike)
     tree_s = yule_tree(900, seed=270 + n)
-    table_s = table_iid(n, tree_s.n_tips, 0.04, seed=271 + n)
+    table_s = table_iid(n, tree_s.n_tips, density, seed=271 + n)
+    assert table_s.nnz <= 4096
     tree, table = handles(tree_s, table_s)
     S = uf.uf_stripe_count(n)
     uf.uf_set_option("tensor_path", 0)

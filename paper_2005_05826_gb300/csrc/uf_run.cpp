@@ -1,0 +1,897 @@
+// uf_run.cpp -- the launch sequence of one compute call: device buffers from
+// the stream-ordered pool, metadata through a pinned staging ring, per branch
+// block the count rows, embedding rows and the dense stripe accumulate (or
+// the tensor-core gram), the sparse-row scatter, and the finalize, captured
+// into one CUDA graph unless phases are timed.
+#include "uf_runtime.h"
+
+namespace ufg {
+namespace rt {
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(size_t bytes, cudaStream_t s, const char *what) : st(s) {
+    ck(cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s), what);
+  }
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), st(o.st) { o.p = nullptr; }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    std::swap(p, o.p);
+    std::swap(st, o.st);
+    return *this;
+  }
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+  template <typename T>
+  T *as() const { return (T *)p; }
+};
+
+// Pinned staging for the per-call metadata uploads (table descriptors, row
+// lists): a cudaMemcpyAsync from pageable memory first waits for all earlier
+// work on the stream, one from pinned memory does not, so consecutive calls
+// on one stream overlap their host work with the previous call's kernels.
+// One ring per process; a region is reused only after the event recorded
+// behind its copy has completed.  The buffer lives until the process ends.
+struct Staging {
+  std::mutex mu;
+  char *buf = nullptr;
+  size_t cap = 0, head = 0;
+  std::vector<std::tuple<size_t, size_t, cudaEvent_t>> live;  // [begin, end) copies in flight
+};
+Staging g_stage;
+
+void staged_upload(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return;
+  Staging &S = g_stage;
+  std::lock_guard<std::mutex> g(S.mu);
+  const size_t need = (bytes + 255) & ~(size_t)255;
+  auto retire = [&](bool all, size_t b, size_t e) {
+    for (size_t i = 0; i < S.live.size();) {
+      const size_t lb = std::get<0>(S.live[i]), le = std::get<1>(S.live[i]);
+      cudaEvent_t ev = std::get<2>(S.live[i]);
+      const bool overlap = all || (lb < e && b < le);
+      if (overlap) ck(cudaEventSynchronize(ev), "staging wait");
+      if (overlap || cudaEventQuery(ev) == cudaSuccess) {
+        cudaEventDestroy(ev);
+        S.live[i] = S.live.back();
+        S.live.pop_back();
+      } else {
+        cudaGetLastError();  // cudaErrorNotReady is not an error here
+        i++;
+      }
+    }
+  };
+  if (need > S.cap) {
+    retire(true, 0, 0);
+    if (S.buf) cudaFreeHost(S.buf);
+    S.buf = nullptr;
+    S.cap = 0;
+    const size_t cap = std::max<size_t>(need, (size_t)16 << 20);
+    ck(cudaMallocHost((void **)&S.buf, cap), "alloc pinned staging");
+    S.cap = cap;
+    S.head = 0;
+  }
+  if (S.head + need > S.cap) S.head = 0;
+  const size_t b = S.head, e = b + need;
+  retire(false, b, e);
+  memcpy(S.buf + b, src, bytes);
+  ck(cudaMemcpyAsync(dst, S.buf + b, bytes, cudaMemcpyHostToDevice, st), "upload");
+  cudaEvent_t ev;
+  ck(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
+  ck(cudaEventRecord(ev, st), "cudaEventRecord");
+  S.live.emplace_back(b, e, ev);
+  S.head = e;
+}
+
+// Per-call metadata packed into one device buffer with one staged upload.
+struct Meta {
+  std::vector<char> host;
+  template <typename T>
+  size_t add(const T *p, size_t n) {
+    const size_t off = (host.size() + 255) & ~(size_t)255;
+    host.resize(off + std::max<size_t>(n * sizeof(T), 1));
+    if (n) memcpy(host.data() + off, p, n * sizeof(T));
+    return off;
+  }
+  template <typename T>
+  size_t add(const std::vector<T> &v) { return add(v.data(), v.size()); }
+  DevBuf dev;
+  void upload(cudaStream_t st) {
+    dev = DevBuf(host.size(), st, "alloc call metadata");
+    staged_upload(dev.p, host.data(), host.size(), st);
+  }
+  template <typename T>
+  T *at(size_t off) const { return (T *)((char *)dev.p + off); }
+};
+
+void keep_pool_memory(int device) {
+  static std::mutex mu;
+  static std::map<int, bool> done;
+  std::lock_guard<std::mutex> g(mu);
+  if (done[device]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[device] = true;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Phase timer: CUDA events recorded on the call's stream around each phase.
+struct PhaseTimer {
+  bool on;
+  cudaStream_t st;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  cudaEvent_t open_ev = nullptr;
+  cudaStream_t open_st = nullptr;
+  int open_phase = -1;
+  PhaseTimer(bool enabled, cudaStream_t s) : on(enabled), st(s) {}
+  // a phase is timed on the stream its launches go to (the call's stream by default)
+  void begin(int phase, cudaStream_t on_stream = nullptr) {
+    if (!on) return;
+    open_st = on_stream ? on_stream : st;
+    ck(cudaEventCreate(&open_ev), "cudaEventCreate");
+    ck(cudaEventRecord(open_ev, open_st), "cudaEventRecord");
+    open_phase = phase;
+  }
+  void end() {
+    if (!on) return;
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e), "cudaEventCreate");
+    ck(cudaEventRecord(e, open_st), "cudaEventRecord");
+    marks.push_back({open_phase, {open_ev, e}});
+    open_ev = nullptr;
+  }
+  // after the stream is synchronized
+  void collect(double *ms4) {
+    for (auto &m : marks) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, m.second.first, m.second.second) == cudaSuccess) ms4[m.first] += t;
+    }
+  }
+  ~PhaseTimer() {
+    for (auto &m : marks) {
+      cudaEventDestroy(m.second.first);
+      cudaEventDestroy(m.second.second);
+    }
+    if (open_ev) cudaEventDestroy(open_ev);
+  }
+};
+
+// Private stream of the calling thread per device on which a call's launch
+// sequence is captured into a CUDA graph.  Per thread, so that concurrent
+// calls from several threads never share a capturing stream.
+struct ThreadStreams {
+  std::map<int, cudaStream_t> s;
+  ~ThreadStreams() {
+    for (auto &kv : s) cudaStreamDestroy(kv.second);
+  }
+};
+thread_local ThreadStreams t_streams;
+
+cudaStream_t capture_stream(int device) {
+  auto it = t_streams.s.find(device);
+  if (it != t_streams.s.end()) return it->second;
+  cudaStream_t x = nullptr;
+  ck(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "cudaStreamCreate");
+  t_streams.s[device] = x;
+  return x;
+}
+
+// Records the branch-block launch sequence of a call into a CUDA graph (on a
+// private stream) and launches that graph on the caller's stream; when off,
+// launches go to the caller's stream directly.
+struct Capture {
+  bool on;
+  cudaStream_t user, cap = nullptr;
+  bool open = false;
+  Capture(bool enable, cudaStream_t st, int device) : on(enable), user(st) {
+    if (!on) return;
+    cap = capture_stream(device);
+    ck(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+    open = true;
+  }
+  cudaStream_t stream() const { return on ? cap : user; }
+  // end the capture and launch the graph on the caller's stream
+  void launch() {
+    if (!on) return;
+    cudaGraph_t g = nullptr;
+    open = false;
+    ck(cudaStreamEndCapture(cap, &g), "cudaStreamEndCapture");
+    cudaGraphExec_t e = nullptr;
+    cudaError_t err = cudaGraphInstantiate(&e, g, 0);
+    if (err == cudaSuccess) err = cudaGraphLaunch(e, user);
+    if (e) cudaGraphExecDestroy(e);  // freed once the launch completes
+    cudaGraphDestroy(g);
+    ck(err, "graph launch");
+  }
+  ~Capture() {
+    if (open) {  // an error escaped mid-capture: drop the partial graph
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(cap, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+  }
+};
+
+// Autotuned rows per work unit, by (accumulator, precision, size bucket).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tuned_chunk;
+
+std::tuple<int, int, int, int> tune_key(int acc, bool fp32, int64_t n_tiles, int64_t rows) {
+  auto lg = [](int64_t x) { return (int)std::floor(std::log2((double)std::max<int64_t>(x, 1))); };
+  return {acc, fp32 ? 1 : 0, lg(n_tiles), lg(rows)};
+}
+
+// Time the accumulate launch of the first block with each candidate chunk
+// size and keep the fastest (the accumulators are cleared afterwards).
+int tune_chunk(int acc, bool fp32, StripeArgs sa, size_t cells, cudaStream_t st) {
+  const int cand[4] = {1024, 2048, 4096, 8192};
+  cudaEvent_t e0, e1;
+  ck(cudaEventCreate(&e0), "cudaEventCreate");
+  ck(cudaEventCreate(&e1), "cudaEventCreate");
+  int best = stripe_chunk_rows();
+  float best_ms = 1e30f;
+  for (int c : cand) {
+    if (c > 2 * std::max(sa.rows, 1024)) break;
+    sa.chunk = c;
+    ck(cudaEventRecord(e0, st), "cudaEventRecord");
+    ck(launch_stripe_acc(acc, fp32, sa, st), "autotune");
+    ck(cudaEventRecord(e1, st), "cudaEventRecord");
+    ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ck(cudaMemsetAsync(sa.M, 0, cells * 8, st), "memset");
+  if (sa.M2) ck(cudaMemsetAsync(sa.M2, 0, cells * 8, st), "memset");
+  return best;
+}
+
+// Device copies of the inputs and the per-sample arrays on the combined axis.
+struct Inputs {
+  uf_tree::Dev *td = nullptr;
+  Plan *P = nullptr;
+  Plan::Dev *pd = nullptr;
+  std::vector<uf_table::Dev *> xd;
+};
+
+Inputs bind_inputs(uf_tree *tree, const BatchJob &J, int device, int64_t rows) {
+  Inputs in;
+  {
+    std::lock_guard<std::mutex> g(tree->mu);
+    in.td = &tree_dev(tree, device);
+    in.P = get_plan(tree, rows);
+    in.pd = &plan_dev(in.P, device);
+  }
+  for (const TableJob &t : J.tabs) {
+    std::lock_guard<std::mutex> g(t.table->mu);
+    in.xd.push_back(&table_dev(t.table, device));
+  }
+  return in;
+}
+
+// Branch rows per embedding block for a working budget of per_row bytes a row
+// plus fixed bytes.
+int64_t block_rows(int64_t nb, double per_row, double fixed) {
+  size_t free_b = 0, total_b = 0;
+  ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+  const double budget = std::min(0.5 * (double)free_b - fixed, 24e9);
+  int64_t rows = (int64_t)(budget / per_row / 1.1);
+  rows = std::max<int64_t>(std::min<int64_t>(rows, nb), std::min<int64_t>(nb, 256));
+  if (g_branch_block.load() > 0) rows = std::min<int64_t>(g_branch_block.load(), std::max<int64_t>(nb, 1));
+  return std::max<int64_t>(rows, 1);
+}
+
+// Output buffers: the caller's device memory, or a device staging buffer
+// copied to the caller's host memory at the end.
+struct Outputs {
+  std::vector<DevBuf> tmp;
+  std::vector<void *> dev;
+  std::vector<size_t> bytes;
+};
+
+Outputs bind_outputs(const BatchJob &J, cudaStream_t st) {
+  Outputs o;
+  for (const TableJob &t : J.tabs) {
+    const int64_t n = t.table->n, S = n / 2;
+    const bool full = t.start == 0 && t.stop == S;
+    const size_t elems = full ? (size_t)n * (n - 1) / 2 : (size_t)(t.stop - t.start) * n;
+    o.bytes.push_back(elems * (J.out_fp32 ? 4 : 8));
+    if (J.out_is_device) {
+      o.tmp.emplace_back();
+      o.dev.push_back(t.out);
+    } else {
+      o.tmp.emplace_back(o.bytes.back(), st, "alloc output");
+      o.dev.push_back(o.tmp.back().p);
+    }
+  }
+  return o;
+}
+
+void fill_reports(uf_tree *tree, const BatchJob &J, const Outputs &o, double ms[4], int64_t kernels,
+                  int64_t acc_launches, int path, int64_t rows, int64_t n_blocks, double exec_flops,
+                  int tile_s, int tile_k, double seconds) {
+  const int64_t nb = tree->n_nodes - 1;
+  for (size_t t = 0; t < J.tabs.size(); t++) {
+    if (!J.tabs[t].rep) continue;
+    uf_report &r = *J.tabs[t].rep;
+    memset(&r, 0, sizeof r);
+    const int64_t n = J.tabs[t].table->n, S = n / 2;
+    const bool full = J.tabs[t].start == 0 && J.tabs[t].stop == S;
+    const int64_t rows_out = J.tabs[t].stop - J.tabs[t].start;
+    const double pairs = full ? (double)n * (n - 1) / 2.0
+                              : (double)rows_out * n - ((2 * J.tabs[t].stop == n) ? n / 2.0 : 0.0);
+    r.updates = pairs * (double)nb;
+    r.alg_flops = 2.0 * pairs * nb;
+    r.exec_flops = exec_flops / (double)J.tabs.size();
+    r.hbm_bytes_est = (double)nb * (double)n * 8 * 3 + (double)o.bytes[t];
+    r.stripe_tile = tile_s;
+    r.sample_tile = tile_k;
+    r.branch_block = rows;
+    r.n_blocks = n_blocks;
+    r.kernels = kernels;
+    r.path = path;
+    r.h2d_bytes = g_h2d;
+    r.d2h_bytes = J.out_is_device ? 0.0 : (double)o.bytes[t];
+    r.t_embed_ms = ms[0];
+    r.t_accumulate_ms = ms[1];
+    r.t_diag_ms = ms[2];
+    r.t_finalize_ms = ms[3];
+    r.acc_launches = acc_launches;
+    r.seconds = seconds;
+  }
+}
+
+// Count rows of block b that the split needs: CSC-built nodes of every
+// table, then the dense internal levels over the combined axis.
+void enqueue_split_counts(const Inputs &in, const BatchJob &J, const std::vector<int> &off, const RowSplit &split,
+                          size_t b, const int32_t *d_cnt, double *counts, int64_t ld, cudaStream_t st,
+                          int64_t *kernels) {
+  const auto &lb = split.cnt_launch[b];
+  for (size_t t = 0; t < J.tabs.size(); t++) {
+    ck(launch_slice_counts(d_cnt + lb[0].first, lb[0].second, in.td->tip_lo, in.td->tip_hi, in.pd->slot_of_node,
+                           in.xd[t]->col_ptr, in.xd[t]->col_row, in.xd[t]->col_val, counts + off[t], ld,
+                           (int)J.tabs[t].table->n, st),
+       "count rows");
+    *kernels += lb[0].second > 0;
+  }
+  for (size_t l = 1; l < lb.size(); l++) {
+    ck(launch_node_counts(d_cnt + lb[l].first, lb[l].second, in.td->child_ptr, in.td->child_idx,
+                          in.pd->slot_of_node, counts, ld, st),
+       "node counts");
+    (*kernels)++;
+  }
+}
+
+// Unweighted, mixed precision, on the tensor cores: per branch block, counts
+// -> presence / split-length planes of every table -> tcgen05 gram; then the
+// gram finalize of every table.  Throws CudaFail on CUDA errors.
+uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
+  const auto t_start = std::chrono::steady_clock::now();
+  const size_t nt = J.tabs.size();
+  std::vector<int> off(nt);
+  std::vector<GramTab> gt(nt);
+  std::vector<int32_t> tile_tab, tile_bi, tile_bj;
+  int n_cols = 0, npad_tot = 0;
+  int64_t gt_cells = 0;
+  for (size_t t = 0; t < nt; t++) {
+    const int n = (int)J.tabs[t].table->n;
+    off[t] = n_cols;
+    gt[t].n = n;
+    gt[t].n_pad = gram_pad(n);
+    gt[t].row_base = npad_tot;
+    gt[t].off = n_cols;
+    gt[t].gt_off = gt_cells;
+    const size_t before = tile_bi.size();
+    gram_tiles(gt[t].n_pad, &tile_bi, &tile_bj);
+    tile_tab.insert(tile_tab.end(), tile_bi.size() - before, (int32_t)t);
+    n_cols += n;
+    npad_tot += gt[t].n_pad;
+    gt_cells += (int64_t)gt[t].n_pad * gt[t].n_pad;
+  }
+  const int n_tiles = (int)tile_bi.size();
+  const int64_t nb = tree->n_nodes - 1;
+  const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + 4.0 * npad_tot * 2.0 + 8.0, (double)gt_cells * 8.0);
+  Inputs in = bind_inputs(tree, J, device, rows);
+  const std::shared_ptr<const RowSplit> split_p = get_split(tree, J, in.P, SPLIT_GRAM, true);
+  const RowSplit &split = *split_p;
+  const int64_t K_pad = gram_kpad((int)std::max<int64_t>(split.max_dense, 1));
+  cudaStream_t st = J.st;
+  int64_t kernels = 0, acc_launches = 0;
+  PhaseTimer timer(g_kernel_timing.load() != 0, st);
+  std::vector<int32_t> tl(tile_tab);
+  tl.insert(tl.end(), tile_bi.begin(), tile_bi.end());
+  tl.insert(tl.end(), tile_bj.begin(), tile_bj.end());
+  DevBuf counts((size_t)in.P->n_slots * n_cols * 8, st, "alloc counts");
+  DevBuf Pl((size_t)4 * npad_tot * K_pad * 2, st, "alloc presence planes");
+  DevBuf Gt((size_t)gt_cells * 8, st, "alloc gram");
+  DevBuf err(sizeof(int), st, "alloc error flag");
+  Meta meta;  // tile list, table descriptors and row lists: one staged upload
+  const size_t o_tiles = meta.add(tl), o_tabs = meta.add(gt);
+  const size_t o_cnt = meta.add(split.cnt_lists), o_dense = meta.add(split.dense);
+  std::vector<int64_t> sp_off;
+  size_t o_sparse = 0, o_sptabs = 0;
+  if (split.n_sparse > 0) {
+    std::vector<int32_t> all;
+    for (const auto &c : split.sparse) {
+      sp_off.push_back((int64_t)all.size());
+      all.insert(all.end(), c.begin(), c.end());
+    }
+    std::vector<SpTab> sp(nt);
+    for (size_t t = 0; t < nt; t++) {
+      sp[t].col_ptr = in.xd[t]->col_ptr;
+      sp[t].col_row = in.xd[t]->col_row;
+      sp[t].col_val = in.xd[t]->col_val;
+      sp[t].total = in.xd[t]->total;
+      sp[t].inv_total_f = in.xd[t]->inv_total_f;
+      sp[t].n = gt[t].n;
+      sp[t].off = gt[t].off;
+      sp[t].m_off = gt[t].gt_off;
+      sp[t].n_pad = gt[t].n_pad;
+    }
+    o_sparse = meta.add(all);
+    o_sptabs = meta.add(sp);
+  }
+  meta.upload(st);
+  const int32_t *d_tiles = meta.at<int32_t>(o_tiles);
+  const GramTab *d_tabs = meta.at<GramTab>(o_tabs);
+  const int32_t *d_cnt = meta.at<int32_t>(o_cnt), *d_dense = meta.at<int32_t>(o_dense);
+  ck(cudaMemsetAsync(Gt.p, 0, (size_t)gt_cells * 8, st), "memset");
+  ck(cudaMemsetAsync(err.p, 0, sizeof(int), st), "memset");
+  Outputs o = bind_outputs(J, st);
+  double exec_flops = 0.0;
+  Capture cap(g_graph.load() != 0 && !timer.on, st, device);
+  const cudaStream_t ls = cap.stream();
+  // the sparse-row scatters need no count rows or planes: first
+  if (split.n_sparse > 0) {
+    timer.begin(4);
+    for (size_t c = 0; c < split.sparse.size(); c++) {
+      if (split.sparse[c].empty()) continue;
+      SparseArgs sp{};
+      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
+      sp.n_nodes = (int)split.sparse[c].size();
+      sp.cap = split.cap[c];
+      sp.tip_lo = in.td->tip_lo;
+      sp.tip_hi = in.td->tip_hi;
+      sp.length = in.td->length;
+      sp.tabs = meta.at<SpTab>(o_sptabs);
+      sp.n_tabs = (int)nt;
+      sp.kind = EMB_PRESENCE;
+      sp.gram = 1;
+      sp.M = Gt.as<unsigned long long>();
+      sp.alpha = 1.0;
+      sp.scale = scale;
+      ck(launch_sparse_rows(ACC_MIN, false, sp, ls), "sparse rows");
+      kernels++;
+    }
+    timer.end();
+  }
+  for (size_t b = 0; b < in.P->b0.size(); b++) {
+    const int64_t b0 = in.P->b0[b];
+    const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
+    timer.begin(0);
+    enqueue_split_counts(in, J, off, split, b, d_cnt, counts.as<double>(), n_cols, ls, &kernels);
+    if (nd > 0) {
+      ck(launch_gram_prep(b0, (int)nd, in.pd->slot_of_node, counts.as<double>(), n_cols, in.td->length, d_tabs,
+                          (int)nt, npad_tot, K_pad, Pl.p, ls, d_dense + d0),
+         "presence planes");
+      kernels++;
+    }
+    timer.end();
+    if (nd == 0) continue;
+    GramArgs ga{};
+    ga.k_len = (int)round_up(nd, 64);
+    ga.kc = 4096;
+    ga.n_tiles = n_tiles;
+    ga.npad_tot = npad_tot;
+    ga.tile_tab = d_tiles;
+    ga.tile_bi = d_tiles + n_tiles;
+    ga.tile_bj = d_tiles + 2 * n_tiles;
+    ga.tabs = d_tabs;
+    ga.Gt = Gt.as<unsigned long long>();
+    ga.scale = scale;
+    ga.err = err.as<int>();
+    timer.begin(1);
+    ck(launch_gram(ga, Pl.p, K_pad, ls), "tensor-core gram");
+    timer.end();
+    kernels++;
+    acc_launches++;
+    exec_flops += 2.0 * 3 * 128.0 * 256.0 * ga.k_len * n_tiles;
+  }
+  timer.begin(3);
+  for (size_t t = 0; t < nt; t++) {
+    GramFinalArgs fa{};
+    fa.n = gt[t].n;
+    fa.n_pad = gt[t].n_pad;
+    fa.s0 = J.tabs[t].start;
+    fa.s1 = J.tabs[t].stop;
+    fa.full = J.tabs[t].start == 0 && J.tabs[t].stop == gt[t].n / 2;
+    fa.Gt = Gt.as<unsigned long long>() + gt[t].gt_off;
+    fa.out = o.dev[t];
+    fa.out_fp32 = J.out_fp32;
+    ck(launch_finalize_gram(fa, ls), "finalize");
+    kernels++;
+  }
+  timer.end();
+  cap.launch();
+  int h_err = 0;
+  ck(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
+  if (!J.out_is_device)
+    for (size_t t = 0; t < nt; t++)
+      ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
+  counts = DevBuf();
+  Pl = DevBuf();
+  Gt = DevBuf();
+  meta.dev = DevBuf();
+  o.tmp.clear();
+  ck(cudaStreamSynchronize(st), "synchronize");  // the error flag is read here
+  err = DevBuf();
+  if (h_err) return fail(UF_ETIMEOUT, "tensor-core kernel: a bounded wait gave up");
+  double ms[5] = {0, 0, 0, 0, 0};
+  timer.collect(ms);
+  fill_reports(tree, J, o, ms, kernels, acc_launches, 1, rows, (int64_t)in.P->b0.size(), exec_flops, 256, 128,
+               std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+  for (const TableJob &t : J.tabs)
+    if (t.rep) {
+      t.rep->chunk_rows = 4096;
+      t.rep->graph = cap.on ? 1 : 0;
+      t.rep->dense_rows = (int64_t)split.dense.size();
+      t.rep->sparse_rows = split.n_sparse;
+      t.rep->sparse_pairs = split.pairs;
+      t.rep->t_sparse_ms = ms[4];
+    }
+  return UF_OK;
+}
+
+// Every other method / precision on the CUDA-core stripe kernels.  Throws
+// CudaFail on CUDA errors.
+uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method method, double scale) {
+  const auto t_start = std::chrono::steady_clock::now();
+  const size_t nt = J.tabs.size();
+  const int acc = method == UF_GENERALIZED ? ACC_GEN : ACC_MIN;
+  const int kind = method == UF_GENERALIZED ? EMB_PROP : method == UF_UNWEIGHTED ? EMB_PRESENCE : EMB_SCALED;
+  const bool fp32 = J.fp32;
+  const size_t es = fp32 ? 4 : 8;
+  int tile_s = 0, tile_k = 0;
+  stripe_tile_shape(acc, fp32, &tile_s, &tile_k);
+  std::vector<TabDesc> tabs(nt);
+  std::vector<int> off(nt);
+  int n_cols = 0, n_tiles = 0;
+  int64_t pitch = 0, cells = 0;
+  for (size_t t = 0; t < nt; t++) {
+    const int n = (int)J.tabs[t].table->n;
+    TabDesc &d = tabs[t];
+    d.n = n;
+    d.off = n_cols;
+    d.s_lo = (int)J.tabs[t].start;
+    d.s_hi = (int)(J.tabs[t].stop - 1);
+    d.m_lo = (int)(J.tabs[t].start / tile_s);
+    d.m_hi = (int)((J.tabs[t].stop - 1) / tile_s);
+    d.n_ktiles = (n + tile_k - 1) / tile_k;
+    d.tile0 = n_tiles;
+    d.x_col = pitch;
+    d.m_off = cells;
+    off[t] = n_cols;
+    n_cols += n;
+    n_tiles += d.n_ktiles * (d.m_hi - d.m_lo + 1);
+    pitch += round_up(round_up(n, tile_k) + (int64_t)(d.m_hi + 1) * tile_s, 32);
+    cells += (J.tabs[t].stop - J.tabs[t].start) * (int64_t)n;
+  }
+  const int64_t nb = tree->n_nodes - 1;
+  const double acc_bytes = (double)cells * 8.0 * (acc == ACC_GEN ? 2 : 1) + n_cols * 8.0;
+  const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + (double)pitch * es + 8.0 + n_cols * es / 64.0, acc_bytes);
+  Inputs in = bind_inputs(tree, J, device, rows);
+  cudaStream_t st = J.st;
+  const std::shared_ptr<const RowSplit> split_p = get_split(tree, J, in.P, acc, fp32);
+  const RowSplit &split = *split_p;
+  const int64_t xrows = std::max<int64_t>(split.max_dense, 1);
+  int64_t kernels = 0, acc_launches = 0;
+  PhaseTimer timer(g_kernel_timing.load() != 0, st);
+  DevBuf counts((size_t)in.P->n_slots * n_cols * 8, st, "alloc counts");
+  DevBuf X((size_t)xrows * pitch * es, st, "alloc embeddings");
+  DevBuf M((size_t)cells * 8, st, "alloc stripes");
+  DevBuf M2, Dg, Dsp, diag_tmp, counter(sizeof(int), st, "alloc counter");
+  DevBuf total((size_t)n_cols * 8, st, "alloc totals"), inv_total((size_t)n_cols * 4, st, "alloc totals");
+  // table descriptors and row lists: one staged upload
+  Meta meta;
+  const size_t o_tabs = meta.add(tabs);
+  const size_t o_cnt = meta.add(split.cnt_lists);
+  const size_t o_dense = meta.add(split.dense);
+  const size_t o_dlen = meta.add(split.dense_len);
+  size_t o_sparse = 0, o_sptabs = 0, o_lofs = 0;
+  std::vector<int64_t> sp_off;  // first entry of each capacity class in the sparse list
+  // one table whose accumulators exceed the L2 budget: the sparse rows write
+  // their sample lists, then scatter their pairs stripe region by region
+  const int n_acc = acc == ACC_GEN ? 2 : 1;
+  const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc);
+  const bool region_mode = split.n_sparse > 0 && (n_regions > 1 || split.lists);
+  int64_t n_sparse_rows = 0;
+  DevBuf lk, lx, lf, lz;
+  if (split.n_sparse > 0) {
+    std::vector<int32_t> all;
+    for (const auto &c : split.sparse) {
+      sp_off.push_back((int64_t)all.size());
+      all.insert(all.end(), c.begin(), c.end());
+    }
+    n_sparse_rows = (int64_t)all.size();
+    if (region_mode) {
+      const auto &cp = J.tabs[0].table->col_ptr;
+      std::vector<int64_t> lofs(all.size() + 1, 0);
+      for (size_t r = 0; r < all.size(); r++)
+        lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
+      const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
+      lk = DevBuf(total_e * 4, st, "alloc sparse lists");
+      lx = DevBuf(total_e * es, st, "alloc sparse lists");
+      lf = DevBuf(total_e * 8, st, "alloc sparse lists");
+      lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
+      // rows without entries in the table return before writing their count
+      ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
+      o_lofs = meta.add(lofs);
+    }
+    std::vector<SpTab> sp(nt);
+    for (size_t t = 0; t < nt; t++) {
+      sp[t].col_ptr = in.xd[t]->col_ptr;
+      sp[t].col_row = in.xd[t]->col_row;
+      sp[t].col_val = in.xd[t]->col_val;
+      sp[t].total = in.xd[t]->total;
+      sp[t].inv_total_f = in.xd[t]->inv_total_f;
+      sp[t].n = tabs[t].n;
+      sp[t].off = tabs[t].off;
+      sp[t].s_lo = tabs[t].s_lo;
+      sp[t].s_hi = tabs[t].s_hi;
+      sp[t].m_off = tabs[t].m_off;
+    }
+    o_sparse = meta.add(all);
+    o_sptabs = meta.add(sp);
+    Dsp = DevBuf((size_t)n_cols * 8, st, "alloc diagonal");
+    ck(cudaMemsetAsync(Dsp.p, 0, (size_t)n_cols * 8, st), "memset");
+  }
+  meta.upload(st);
+  const TabDesc *d_tabs = meta.at<TabDesc>(o_tabs);
+  const int32_t *d_cnt = meta.at<int32_t>(o_cnt);
+  const int32_t *d_dense = meta.at<int32_t>(o_dense);
+  const double *d_dlen = meta.at<double>(o_dlen);
+  for (size_t t = 0; t < nt; t++) {
+    const size_t n = (size_t)J.tabs[t].table->n;
+    ck(cudaMemcpyAsync(total.as<double>() + off[t], in.xd[t]->total, n * 8, cudaMemcpyDeviceToDevice, st),
+       "gather totals");
+    ck(cudaMemcpyAsync(inv_total.as<float>() + off[t], in.xd[t]->inv_total_f, n * 4, cudaMemcpyDeviceToDevice,
+                       st),
+       "gather totals");
+  }
+  if (acc == ACC_GEN) {
+    M2 = DevBuf((size_t)cells * 8, st, "alloc stripes");
+    ck(cudaMemsetAsync(M2.p, 0, (size_t)cells * 8, st), "memset");
+  } else {
+    Dg = DevBuf((size_t)n_cols * 8, st, "alloc diagonal");
+    diag_tmp = DevBuf(diag_scratch_bytes(fp32, (int)xrows, n_cols), st, "alloc diagonal scratch");
+    ck(cudaMemsetAsync(Dg.p, 0, (size_t)n_cols * 8, st), "memset");
+  }
+  ck(cudaMemsetAsync(M.p, 0, (size_t)cells * 8, st), "memset");
+  Outputs o = bind_outputs(J, st);
+  double exec_flops = 0.0;
+  // chunk size: tuned once per (accumulator, precision, size bucket)
+  const auto key = tune_key(acc, fp32, n_tiles, xrows);
+  int chunk = stripe_chunk_rows();
+  bool tune = false;
+  if (g_autotune.load() && !split.dense.empty()) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tuned_chunk.find(key);
+    if (it != g_tuned_chunk.end()) chunk = it->second;
+    else tune = true;
+  }
+  // the launch sequence goes into a CUDA graph unless it is timed per phase
+  Capture cap(g_graph.load() != 0 && !timer.on && !tune, st, device);
+  const cudaStream_t ls = cap.stream();
+  // the sparse-row scatters run after the dense blocks, whose chunk tuning clears M
+  auto sparse_args = [&]() {
+    SparseArgs sp{};
+    sp.tip_lo = in.td->tip_lo;
+    sp.tip_hi = in.td->tip_hi;
+    sp.length = in.td->length;
+    sp.tabs = meta.at<SpTab>(o_sptabs);
+    sp.n_tabs = (int)nt;
+    sp.kind = kind;
+    sp.mixed_forms = fp32 && acc == ACC_MIN;
+    sp.M = M.as<unsigned long long>();
+    sp.M2 = M2.as<unsigned long long>();
+    sp.Dsp = Dsp.as<unsigned long long>();
+    sp.alpha = J.alpha;
+    sp.scale = scale;
+    if (region_mode) {
+      sp.lk = lk.as<int32_t>();
+      sp.lx = lx.p;
+      sp.lf = lf.as<long long>();
+      sp.lofs = meta.at<int64_t>(o_lofs);
+      sp.lz = lz.as<int>();
+    }
+    return sp;
+  };
+  auto launch_sparse = [&](cudaStream_t on) {
+    for (size_t c = 0; c < split.sparse.size(); c++) {
+      if (split.sparse[c].empty()) continue;
+      SparseArgs sp = sparse_args();
+      sp.row_base = (int)sp_off[c];
+      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
+      sp.n_nodes = (int)split.sparse[c].size();
+      sp.cap = split.cap[c];
+      if (region_mode) ck(launch_sparse_lists(acc, fp32, sp, on), "sparse lists");
+      else ck(launch_sparse_rows(acc, fp32, sp, on), "sparse rows");
+      kernels++;
+    }
+    if (!region_mode) return;
+    const int64_t per = std::max<int64_t>(1, (int64_t)((double)g_region_bytes.load() / (8.0 * n_acc * tabs[0].n)));
+    for (int64_t r0 = tabs[0].s_lo; r0 <= tabs[0].s_hi; r0 += per) {
+      SparseArgs sp = sparse_args();
+      sp.nodes = meta.at<int32_t>(o_sparse);
+      sp.n_nodes = (int)n_sparse_rows;
+      sp.r0 = (int)r0;
+      sp.r1 = (int)std::min<int64_t>(r0 + per, (int64_t)tabs[0].s_hi + 1);
+      ck(launch_sparse_region(acc, fp32, sp, on), "sparse regions");
+      kernels++;
+    }
+  };
+  bool tuned = false;
+  for (size_t b = 0; b < in.P->b0.size(); b++) {
+    const int64_t b0 = in.P->b0[b];
+    const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
+    timer.begin(0);
+    enqueue_split_counts(in, J, off, split, b, d_cnt, counts.as<double>(), n_cols, ls, &kernels);
+    if (nd > 0) {
+      ck(launch_emb_rows(kind, fp32, b0, (int)nd, in.pd->slot_of_node, counts.as<double>(), n_cols,
+                         in.td->length, total.as<double>(), inv_total.as<float>(), X.p, pitch,
+                         d_tabs, (int)nt, ls, d_dense + d0),
+         "embedding rows");
+      kernels++;
+    }
+    timer.end();
+    if (nd == 0) continue;
+    StripeArgs sa{};
+    sa.X = X.p;
+    sa.len = d_dlen + d0;
+    sa.rows = (int)nd;
+    sa.pitch = pitch;
+    sa.chunk = chunk;
+    sa.tabs = d_tabs;
+    sa.n_tabs = (int)nt;
+    sa.n_tiles = n_tiles;
+    sa.n_cols = n_cols;
+    sa.M = M.as<unsigned long long>();
+    sa.M2 = M2.as<unsigned long long>();
+    sa.Dg = Dg.as<unsigned long long>();
+    sa.alpha = J.alpha;
+    sa.scale = scale;
+    sa.counter = counter.as<int>();
+    if (tune && !tuned) {
+      chunk = sa.chunk = tune_chunk(acc, fp32, sa, (size_t)cells, ls);
+      tuned = true;
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      g_tuned_chunk[key] = chunk;
+    }
+    timer.begin(1);
+    ck(launch_stripe_acc(acc, fp32, sa, ls), "stripe accumulate");
+    timer.end();
+    kernels++;
+    acc_launches++;
+    exec_flops += 2.0 * (double)n_tiles * tile_s * tile_k * (double)nd;
+    if (acc == ACC_MIN) {
+      timer.begin(2);
+      ck(launch_diag(fp32, sa, diag_tmp.p, ls), "diagonal accumulate");
+      timer.end();
+      kernels += 2;
+    }
+  }
+  if (split.n_sparse > 0) {
+    timer.begin(4);
+    launch_sparse(ls);
+    timer.end();
+  }
+  timer.begin(3);
+  for (size_t t = 0; t < nt; t++) {
+    FinalArgs fa{};
+    fa.method = method;
+    fa.n = tabs[t].n;
+    fa.s0 = J.tabs[t].start;
+    fa.s1 = J.tabs[t].stop;
+    fa.full = J.tabs[t].start == 0 && J.tabs[t].stop == tabs[t].n / 2;
+    fa.mixed_forms = fp32 && acc == ACC_MIN;
+    fa.M = M.as<unsigned long long>() + tabs[t].m_off;
+    fa.M2 = M2.p ? M2.as<unsigned long long>() + tabs[t].m_off : nullptr;
+    fa.Dg = Dg.p ? Dg.as<unsigned long long>() + off[t] : nullptr;
+    fa.Dsp = Dsp.p ? Dsp.as<unsigned long long>() + off[t] : nullptr;
+    fa.inv_scale = 1.0 / scale;
+    fa.out = o.dev[t];
+    fa.out_fp32 = J.out_fp32;
+    ck(launch_finalize(fa, ls), "finalize");
+    kernels++;
+  }
+  timer.end();
+  cap.launch();
+  if (!J.out_is_device)
+    for (size_t t = 0; t < nt; t++)
+      ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
+  // buffers go back to the stream-ordered pool here
+  counts = DevBuf();
+  X = DevBuf();
+  M = DevBuf();
+  M2 = DevBuf();
+  Dg = DevBuf();
+  Dsp = DevBuf();
+  diag_tmp = DevBuf();
+  counter = DevBuf();
+  meta.dev = DevBuf();
+  total = DevBuf();
+  inv_total = DevBuf();
+  o.tmp.clear();
+  if (!J.out_is_device || st == nullptr || timer.on) ck(cudaStreamSynchronize(st), "synchronize");
+  else ck(cudaGetLastError(), "enqueue");
+  double ms[5] = {0, 0, 0, 0, 0};
+  timer.collect(ms);
+  fill_reports(tree, J, o, ms, kernels, acc_launches, 0, rows, (int64_t)in.P->b0.size(), exec_flops, tile_s,
+               tile_k, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+  for (const TableJob &t : J.tabs)
+    if (t.rep) {
+      t.rep->chunk_rows = chunk;
+      t.rep->graph = cap.on ? 1 : 0;
+      t.rep->dense_rows = (int64_t)split.dense.size();
+      t.rep->sparse_rows = split.n_sparse;
+      t.rep->sparse_pairs = split.pairs;
+      t.rep->t_sparse_ms = ms[4];
+    }
+  return UF_OK;
+}
+
+}  // namespace
+
+// One compute call on the current device; throws CudaFail on CUDA errors.
+uf_status run_batch(uf_tree *tree, const BatchJob &J) {
+  g_h2d = 0.0;
+  int device = 0;
+  ck(cudaGetDevice(&device), "cudaGetDevice");
+  keep_pool_memory(device);
+  uf_method method = J.method;
+  if (method == UF_GENERALIZED && J.alpha == 1.0) method = UF_WEIGHTED_NORMALIZED;  // s^0 == 1
+  const int kind = method == UF_GENERALIZED ? EMB_PROP : method == UF_UNWEIGHTED ? EMB_PRESENCE : EMB_SCALED;
+  double scale = 0.0;  // one fixed-point scale valid for every table of the call
+  for (const TableJob &t : J.tabs) {
+    const double s = accum_scale(tree, t.table, kind);
+    scale = scale == 0.0 ? s : std::min(scale, s);
+  }
+  if (method == UF_UNWEIGHTED && J.fp32 && g_tensor_path.load()) {
+    // the tensor path keeps every table's whole n_pad x n_pad gram matrix (int64) on the
+    // device whatever the stripe range; when that does not fit in half the free memory
+    // the CUDA-core stripe kernels, which store only the requested stripes, take the call
+    double gram_bytes = 0.0;
+    for (const TableJob &t : J.tabs) {
+      const double np = (double)gram_pad((int)t.table->n);
+      gram_bytes += np * np * 8.0;
+    }
+    size_t free_b = 0, total_b = 0;
+    ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    if (gram_bytes <= 0.5 * (double)free_b) return run_gram(tree, J, device, scale);
+  }
+  return run_stripes(tree, J, device, method, scale);
+}
+
+void forget_tuned_chunks() {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tuned_chunk.clear();
+}
+
+}  // namespace rt
+}  // namespace ufg

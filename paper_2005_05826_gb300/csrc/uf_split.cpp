@@ -1,0 +1,159 @@
+// uf_split.cpp -- which branches of a call run through the dense stripe
+// kernels and which are scattered pair by pair (uf_sparse.cu), by a cost
+// model of the two paths on GB300; plus the count-row lists the split
+// needs and a per-tree cache of splits.
+#include "uf_runtime.h"
+
+namespace ufg {
+namespace rt {
+
+double sparse_regions(size_t n_tables, int acc, double acc_bytes) {
+  const double budget = (double)g_region_bytes.load();
+  if (n_tables != 1 || acc == SPLIT_GRAM || acc_bytes <= budget) return 1.0;
+  return std::ceil(acc_bytes / budget);
+}
+
+namespace {
+
+// Per branch v the count entries of table t under v are the CSC run of v's
+// tips, ub_t(v) = col_ptr_t[tip_hi] - col_ptr_t[tip_lo] (an upper bound on the
+// nonzero samples, exact when no two tips share a sample).  Mode 1 scatters
+// v when the modelled time of its pairs is below that of a dense pass over
+// its stripe cells; the rates are GB300 measurements of the two kernels and
+// of global 64-bit atomics (L2-resident accumulators or not).  Mode 2
+// scatters every branch that fits; mode 0 none.  The choice depends on the
+// tree and the tables only, not on the stripe range, so that a range run
+// gives bitwise the stripes of the full run.
+RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int acc, bool fp32) {
+  RowSplit R;
+  const int mode = (int)g_sparse.load();
+  const int64_t nb = tree->n_nodes - 1;
+  const size_t nt = J.tabs.size();
+  const int classes[5] = {128, 512, 2048, SPARSE_MAX_ENTRIES, SPARSE_LIST_MAX_ENTRIES};
+  R.cap.assign(classes, classes + 5);
+  R.sparse.resize(5);
+  std::vector<char> is_sparse(std::max<int64_t>(nb, 1), 0);
+  if (mode != 0) {
+    const int n_acc = acc == ACC_GEN ? 2 : 1;
+    double cells = 0.0, cols = 0.0;  // stripe cells of a full run of every table; samples
+    for (size_t t = 0; t < nt; t++) {
+      const double n = (double)J.tabs[t].table->n;
+      cells += std::floor(n / 2.0) * n;
+      cols += n;
+    }
+    // accumulators beyond L2: one table scatters region by region in L2
+    // (sparse_regions), several tables scatter straight into HBM-resident cells
+    const bool regions = sparse_regions(nt, acc, cells * 8.0 * n_acc) > 1;
+    R.lists = regions;
+    // list mode keeps only sort keys in shared memory: longer runs fit
+    const int64_t max_entries = regions ? SPARSE_LIST_MAX_ENTRIES : SPARSE_MAX_ENTRIES;
+    const double atom_rate = cells * 8.0 * n_acc <= 64e6 || regions ? 2.3e11 : 2.5e10;
+    const double n_regions = regions ? sparse_regions(nt, acc, cells * 8.0 * n_acc) : 1.0;
+    double dense_rate;  // cell updates per second of the dense kernel
+    if (acc == SPLIT_GRAM) dense_rate = 2.5e14;
+    else dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
+    const double visit_rate = fp32 ? 2e12 : (acc == ACC_GEN ? 3e10 : 1e12);
+    const double job_cost = 5e-10;
+    // a dense row also costs its count row and embedding (or planes) in HBM
+    const double dense_t = cells / dense_rate + cols * 36.0 / 6e12;
+    for (int64_t v = 0; v < nb; v++) {
+      const int32_t lo = tree->tip_lo[v], hi = tree->tip_hi[v];
+      if (lo < 0) continue;
+      if (tree->length[v] == 0.0) {
+        // a zero-length branch adds exactly 0 to every accumulator: skipped
+        // (its count row is still built if a dense parent needs it)
+        is_sparse[v] = 1;
+        R.n_sparse++;
+        continue;
+      }
+      double cost = 0.0, pairs = 0.0;
+      int64_t mx = 0;
+      for (size_t t = 0; t < nt; t++) {
+        const auto &cp = J.tabs[t].table->col_ptr;
+        const int64_t ub = cp[hi] - cp[lo];
+        mx = std::max(mx, ub);
+        if (ub == 0) continue;
+        const double pr = (double)ub * (double)(ub - 1) / 2.0;
+        pairs += pr;
+        cost += job_cost + pr * (1.0 / visit_rate + n_acc / atom_rate) + (double)ub * 4.0 / atom_rate;
+        if (regions) cost += n_regions * (job_cost + (double)ub * 4e-11);  // one visit per region
+      }
+      if (mx > max_entries) continue;
+      if (mode == 2 || cost < dense_t) {
+        is_sparse[v] = 1;
+        int c = 0;
+        while (classes[c] < mx) c++;
+        R.sparse[c].push_back((int32_t)v);
+        R.n_sparse++;
+        R.pairs += pairs;
+      }
+    }
+  }
+  const int64_t root = tree->n_nodes - 1;
+  auto parent_dense = [&](int64_t v) {
+    const int64_t p = tree->parent[v];
+    return p != root && !is_sparse[p];
+  };
+  for (size_t b = 0; b < P->b0.size(); b++) {
+    const auto &ls = P->launches[b];
+    std::vector<std::pair<int64_t, int>> lb;
+    std::vector<int32_t> level;
+    // nodes built from CSC columns
+    level.clear();
+    for (size_t l = 0; l < ls.size(); l++)
+      for (int i = 0; i < ls[l].second; i++) {
+        const int32_t v = P->lists[ls[l].first + i];
+        const bool tip = l == 0;
+        if (is_sparse[v] ? parent_dense(v) : tip) level.push_back(v);
+      }
+    lb.emplace_back((int64_t)R.cnt_lists.size(), (int)level.size());
+    R.cnt_lists.insert(R.cnt_lists.end(), level.begin(), level.end());
+    // dense internal nodes by level
+    for (size_t l = 1; l < ls.size(); l++) {
+      level.clear();
+      for (int i = 0; i < ls[l].second; i++) {
+        const int32_t v = P->lists[ls[l].first + i];
+        if (!is_sparse[v]) level.push_back(v);
+      }
+      if (level.empty()) continue;
+      lb.emplace_back((int64_t)R.cnt_lists.size(), (int)level.size());
+      R.cnt_lists.insert(R.cnt_lists.end(), level.begin(), level.end());
+    }
+    R.cnt_launch.push_back(std::move(lb));
+  }
+  R.dense_ptr.push_back(0);
+  for (size_t b = 0; b < P->b0.size(); b++) {
+    for (int64_t v = P->b0[b]; v < P->b1[b]; v++)
+      if (!is_sparse[v]) {
+        R.dense.push_back((int32_t)v);
+        R.dense_len.push_back(tree->length[v]);
+      }
+    R.dense_ptr.push_back((int64_t)R.dense.size());
+    R.max_dense = std::max(R.max_dense, R.dense_ptr[b + 1] - R.dense_ptr[b]);
+  }
+  return R;
+}
+
+}  // namespace
+
+// The split of a call, cached on the tree by its tables and kind (tables are
+// immutable and their ids are never reused).
+std::shared_ptr<const RowSplit> get_split(uf_tree *tree, const BatchJob &J, const Plan *P, int acc, bool fp32) {
+  SplitKey key;
+  for (const TableJob &t : J.tabs) std::get<0>(key).push_back(t.table->id);
+  std::get<1>(key) = acc;
+  std::get<2>(key) = fp32 ? 1 : 0;
+  std::get<3>(key) = (int)g_sparse.load();
+  std::get<4>(key) = P->block_rows;
+  std::get<5>(key) = g_region_bytes.load();
+  std::lock_guard<std::mutex> g(tree->mu);
+  auto it = tree->splits.find(key);
+  if (it != tree->splits.end()) return it->second;
+  if (tree->splits.size() >= 16) tree->splits.clear();
+  auto sp = std::make_shared<const RowSplit>(split_rows(tree, J, P, acc, fp32));
+  tree->splits.emplace(key, sp);
+  return sp;
+}
+
+}  // namespace rt
+}  // namespace ufg

@@ -33,38 +33,46 @@ __global__ void k_tip_counts(const int32_t *__restrict__ tip_nodes,
 // other (within one tip's column the samples are distinct, so its entries
 // scatter without conflicts).  Serves tips and the nodes whose own subtree
 // is not walked level by level (a branch scattered by the sparse-row path
-// whose parent runs through the dense kernels).
+// whose parent runs through the dense kernels).  With C = uint8_t the slot
+// holds presence flags instead (1 where the count is nonzero).
+template <typename C>
 __global__ void k_slice_counts(const int32_t *__restrict__ nodes, const int32_t *__restrict__ tip_lo,
                                const int32_t *__restrict__ tip_hi, const int32_t *__restrict__ slot_of_node,
                                const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ col_row,
-                               const double *__restrict__ col_val, double *__restrict__ counts, int64_t ld,
-                               int n) {
+                               const double *__restrict__ col_val, C *__restrict__ counts, int64_t ld, int n) {
   const int v = nodes[blockIdx.x];
-  double *row = counts + (int64_t)slot_of_node[v] * ld;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) row[k] = 0.0;
+  C *row = counts + (int64_t)slot_of_node[v] * ld;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) row[k] = C(0);
   __syncthreads();
   const int f1 = tip_hi[v];
   for (int f = tip_lo[v]; f < f1; f++) {
     const int64_t q1 = col_ptr[f + 1];
-    for (int64_t q = col_ptr[f] + threadIdx.x; q < q1; q += blockDim.x) row[col_row[q]] += col_val[q];
+    for (int64_t q = col_ptr[f] + threadIdx.x; q < q1; q += blockDim.x) {
+      if constexpr (sizeof(C) == 1) row[col_row[q]] = C(1);
+      else row[col_row[q]] += col_val[q];
+    }
     __syncthreads();
   }
 }
 
 // count[v][k] = sum of the children's count[c][k], children in index order
-// (the order the postorder walk adds them in), over all ld columns.
+// (the order the postorder walk adds them in), over all ld columns; for
+// presence flags (C = uint8_t) the OR of the children's flags.
 // grid.x = nodes, grid.y = sample chunks.
+template <typename C>
 __global__ void k_node_counts(const int32_t *__restrict__ nodes,
                               const int32_t *__restrict__ child_ptr,
                               const int32_t *__restrict__ child_idx,
                               const int32_t *__restrict__ slot_of_node,
-                              double *__restrict__ counts, int64_t ld) {
+                              C *__restrict__ counts, int64_t ld) {
   const int v = nodes[blockIdx.x];
   const int64_t k = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
   if (k >= ld) return;
-  double s = 0.0;
-  for (int c = child_ptr[v]; c < child_ptr[v + 1]; c++)
-    s += counts[(int64_t)slot_of_node[child_idx[c]] * ld + k];
+  C s = C(0);
+  for (int c = child_ptr[v]; c < child_ptr[v + 1]; c++) {
+    if constexpr (sizeof(C) == 1) s |= counts[(int64_t)slot_of_node[child_idx[c]] * ld + k];
+    else s += counts[(int64_t)slot_of_node[child_idx[c]] * ld + k];
+  }
   counts[(int64_t)slot_of_node[v] * ld + k] = s;
 }
 
@@ -116,8 +124,17 @@ cudaError_t launch_slice_counts(const int32_t *nodes, int n_list, const int32_t 
                                 const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
                                 const double *col_val, double *counts, int64_t ld, int n, cudaStream_t st) {
   if (n_list <= 0) return cudaSuccess;
-  k_slice_counts<<<n_list, 256, 0, st>>>(nodes, tip_lo, tip_hi, slot_of_node, col_ptr, col_row, col_val, counts,
-                                         ld, n);
+  k_slice_counts<double><<<n_list, 256, 0, st>>>(nodes, tip_lo, tip_hi, slot_of_node, col_ptr, col_row, col_val,
+                                                 counts, ld, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_presence(const int32_t *nodes, int n_list, const int32_t *tip_lo, const int32_t *tip_hi,
+                                  const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
+                                  uint8_t *flags, int64_t ld, int n, cudaStream_t st) {
+  if (n_list <= 0) return cudaSuccess;
+  k_slice_counts<uint8_t><<<n_list, 256, 0, st>>>(nodes, tip_lo, tip_hi, slot_of_node, col_ptr, col_row, nullptr,
+                                                  flags, ld, n);
   return cudaGetLastError();
 }
 
@@ -126,7 +143,16 @@ cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *
                                double *counts, int64_t ld, cudaStream_t st) {
   if (n_list <= 0) return cudaSuccess;
   dim3 grid(n_list, (unsigned)((ld + 255) / 256));
-  k_node_counts<<<grid, 256, 0, st>>>(nodes, child_ptr, child_idx, slot_of_node, counts, ld);
+  k_node_counts<double><<<grid, 256, 0, st>>>(nodes, child_ptr, child_idx, slot_of_node, counts, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_presence(const int32_t *nodes, int n_list, const int32_t *child_ptr,
+                                 const int32_t *child_idx, const int32_t *slot_of_node,
+                                 uint8_t *flags, int64_t ld, cudaStream_t st) {
+  if (n_list <= 0) return cudaSuccess;
+  dim3 grid(n_list, (unsigned)((ld + 255) / 256));
+  k_node_counts<uint8_t><<<grid, 256, 0, st>>>(nodes, child_ptr, child_idx, slot_of_node, flags, ld);
   return cudaGetLastError();
 }
 

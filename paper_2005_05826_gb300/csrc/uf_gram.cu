@@ -308,12 +308,12 @@ __device__ __forceinline__ int gram_table_of_row(const GramTab *tabs, int n_tabs
 }
 
 // Presence and split-length planes of a branch block, transposed to
-// sample-major: Pl[0][k][e] = [count > 0], Pl[1 + t][k][e] = presence * l_t,
+// sample-major: Pl[0][k][e] = presence flag, Pl[1 + t][k][e] = presence * l_t,
 // for every plane row k (padding rows of a table are 0).  Branch e of the
 // block is node nodes[e] (b0 + e without a list).
 __global__ void k_gram_prep(int64_t b0, const int32_t *__restrict__ nodes, int rows, int k_len,
                             const int32_t *__restrict__ slot_of_node,
-                            const double *__restrict__ counts, int64_t ld, const double *__restrict__ length,
+                            const uint8_t *__restrict__ flags, int64_t ld, const double *__restrict__ length,
                             const GramTab *__restrict__ tabs, int n_tabs, int npad_tot, int64_t K_pad,
                             __nv_bfloat16 *__restrict__ Pl) {
   __shared__ float tile[32][33];
@@ -331,7 +331,7 @@ __global__ void k_gram_prep(int64_t b0, const int32_t *__restrict__ nodes, int r
       float p = 0.f;
       if (e < rows && col >= 0) {
         const int64_t v = nodes ? (int64_t)nodes[e] : b0 + e;
-        p = counts[(int64_t)slot_of_node[v] * ld + col] > 0.0 ? 1.f : 0.f;
+        p = flags[(int64_t)slot_of_node[v] * ld + col] ? 1.f : 0.f;
       }
       tile[el][threadIdx.x] = p;
     }
@@ -419,12 +419,12 @@ void gram_tiles(int n_pad, std::vector<int32_t> *bi, std::vector<int32_t> *bj) {
 
 size_t gram_smem_bytes() { return (size_t)GSTAGES * STAGE_BYTES + 1024; }
 
-cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, const double *counts,
+cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, const uint8_t *flags,
                              int64_t ld, const double *length, const GramTab *tabs, int n_tabs,
                              int npad_tot, int64_t K_pad, void *Pl, cudaStream_t st, const int32_t *nodes) {
   const int k_len = (int)((rows + GK - 1) / GK * GK);
   dim3 grid((k_len + 31) / 32, (npad_tot + 31) / 32), block(32, 8);
-  k_gram_prep<<<grid, block, 0, st>>>(b0, nodes, rows, k_len, slot_of_node, counts, ld, length, tabs, n_tabs,
+  k_gram_prep<<<grid, block, 0, st>>>(b0, nodes, rows, k_len, slot_of_node, flags, ld, length, tabs, n_tabs,
                                        npad_tot, K_pad, (__nv_bfloat16 *)Pl);
   return cudaGetLastError();
 }

@@ -63,6 +63,13 @@ cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_
 cudaError_t launch_slice_counts(const int32_t *nodes, int n_list, const int32_t *tip_lo, const int32_t *tip_hi,
                                 const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
                                 const double *col_val, double *counts, int64_t ld, int n, cudaStream_t st);
+// Presence flags (uint8_t, 1 where the count is nonzero) instead of counts.
+cudaError_t launch_slice_presence(const int32_t *nodes, int n_list, const int32_t *tip_lo, const int32_t *tip_hi,
+                                  const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
+                                  uint8_t *flags, int64_t ld, int n, cudaStream_t st);
+cudaError_t launch_node_presence(const int32_t *nodes, int n_list, const int32_t *child_ptr,
+                                 const int32_t *child_idx, const int32_t *slot_of_node,
+                                 uint8_t *flags, int64_t ld, cudaStream_t st);
 cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
                                const int32_t *child_idx, const int32_t *slot_of_node,
                                double *counts, int64_t ld, cudaStream_t st);
@@ -218,7 +225,8 @@ int64_t gram_kpad(int rows);              // branches rounded up to the stage
 // upper-triangle tiles of one table: (bi, bj) pairs appended to bi / bj
 void gram_tiles(int n_pad, std::vector<int32_t> *bi, std::vector<int32_t> *bj);
 // planes of branches nodes[0 .. rows) (b0 .. b0 + rows - 1 when nodes is null)
-cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, const double *counts,
+// from their presence flags
+cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, const uint8_t *flags,
                              int64_t ld, const double *length, const GramTab *tabs, int n_tabs,
                              int npad_tot, int64_t K_pad, void *Pl, cudaStream_t st,
                              const int32_t *nodes = nullptr);

@@ -378,6 +378,27 @@ void enqueue_split_counts(const Inputs &in, const BatchJob &J, const std::vector
   }
 }
 
+// The same rows as presence flags (the tensor-core unweighted path needs
+// nothing else): one byte per sample instead of an FP64 count.
+void enqueue_split_presence(const Inputs &in, const BatchJob &J, const std::vector<int> &off,
+                            const RowSplit &split, size_t b, const int32_t *d_cnt, uint8_t *flags, int64_t ld,
+                            cudaStream_t st, int64_t *kernels) {
+  const auto &lb = split.cnt_launch[b];
+  for (size_t t = 0; t < J.tabs.size(); t++) {
+    ck(launch_slice_presence(d_cnt + lb[0].first, lb[0].second, in.td->tip_lo, in.td->tip_hi, in.pd->slot_of_node,
+                             in.xd[t]->col_ptr, in.xd[t]->col_row, flags + off[t], ld, (int)J.tabs[t].table->n,
+                             st),
+       "presence rows");
+    *kernels += lb[0].second > 0;
+  }
+  for (size_t l = 1; l < lb.size(); l++) {
+    ck(launch_node_presence(d_cnt + lb[l].first, lb[l].second, in.td->child_ptr, in.td->child_idx,
+                            in.pd->slot_of_node, flags, ld, st),
+       "node presence");
+    (*kernels)++;
+  }
+}
+
 // Unweighted, mixed precision, on the tensor cores: per branch block, counts
 // -> presence / split-length planes of every table -> tcgen05 gram; then the
 // gram finalize of every table.  Throws CudaFail on CUDA errors.
@@ -406,7 +427,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   }
   const int n_tiles = (int)tile_bi.size();
   const int64_t nb = tree->n_nodes - 1;
-  const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + 4.0 * npad_tot * 2.0 + 8.0, (double)gt_cells * 8.0);
+  const int64_t rows = block_rows(nb, (double)n_cols + 4.0 * npad_tot * 2.0 + 8.0, (double)gt_cells * 8.0);
   Inputs in = bind_inputs(tree, J, device, rows);
   const std::shared_ptr<const RowSplit> split_p = get_split(tree, J, in.P, SPLIT_GRAM, true);
   const RowSplit &split = *split_p;
@@ -417,7 +438,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   std::vector<int32_t> tl(tile_tab);
   tl.insert(tl.end(), tile_bi.begin(), tile_bi.end());
   tl.insert(tl.end(), tile_bj.begin(), tile_bj.end());
-  DevBuf counts((size_t)in.P->n_slots * n_cols * 8, st, "alloc counts");
+  DevBuf flags((size_t)in.P->n_slots * n_cols, st, "alloc presence rows");
   DevBuf Pl((size_t)4 * npad_tot * K_pad * 2, st, "alloc presence planes");
   DevBuf Gt((size_t)gt_cells * 8, st, "alloc gram");
   DevBuf err(sizeof(int), st, "alloc error flag");
@@ -485,9 +506,9 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
     const int64_t b0 = in.P->b0[b];
     const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
     timer.begin(0);
-    enqueue_split_counts(in, J, off, split, b, d_cnt, counts.as<double>(), n_cols, ls, &kernels);
+    enqueue_split_presence(in, J, off, split, b, d_cnt, flags.as<uint8_t>(), n_cols, ls, &kernels);
     if (nd > 0) {
-      ck(launch_gram_prep(b0, (int)nd, in.pd->slot_of_node, counts.as<double>(), n_cols, in.td->length, d_tabs,
+      ck(launch_gram_prep(b0, (int)nd, in.pd->slot_of_node, flags.as<uint8_t>(), n_cols, in.td->length, d_tabs,
                           (int)nt, npad_tot, K_pad, Pl.p, ls, d_dense + d0),
          "presence planes");
       kernels++;
@@ -534,7 +555,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   if (!J.out_is_device)
     for (size_t t = 0; t < nt; t++)
       ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
-  counts = DevBuf();
+  flags = DevBuf();
   Pl = DevBuf();
   Gt = DevBuf();
   meta.dev = DevBuf();

@@ -394,6 +394,7 @@ def run_ours(args, rank, world, local_rank):
     uf.uf_set_option("kernel_timing", 1)
     uf.uf_set_option("sparse", args.sparse)
     uf.uf_set_option("sparse_region_bytes", args.region_bytes)
+    uf.uf_set_option("sparse_overlap", args.overlap)
 
     def step(precision, reps=None):
         for (m, a), o in zip(METHODS, outs):
@@ -661,6 +662,8 @@ def main():
                     help="time the stripe range [0, K) of every method instead of all stripes (0: all)")
     ap.add_argument("--region-bytes", type=int, default=0,
                     help="option sparse_region_bytes (0: the library default)")
+    ap.add_argument("--overlap", type=int, choices=[0, 1], default=1,
+                    help="option sparse_overlap: sparse scatter beside the dense kernel")
     ap.add_argument("--sparse", type=int, choices=[0, 1, 2], default=1,
                     help="sparse-row path: 0 every branch dense, 1 cost model (default), 2 every branch that fits")
     args = ap.parse_args()

@@ -139,6 +139,9 @@ typedef struct {
  *                    numbers).  Applies to the CUDA-core stripe kernels and
  *                    to the tensor-core unweighted path; the results agree
  *                    within the precision's tolerance.
+ *   "sparse_overlap" 1 (default): the sparse-row scatter runs on a second
+ *                    stream beside the dense stripe kernel (it fills the SM
+ *                    slots and the tail the dense kernel leaves); 0: after it
  *   "sparse_region_bytes"  48,000,000 (default; 0 restores it): a one-table
  *                    call whose stripe accumulators exceed this many bytes
  *                    writes the scattered branches' sample lists once and

@@ -22,6 +22,7 @@ std::atomic<int64_t> g_tensor_path{1};
 std::atomic<int64_t> g_graph{1};
 std::atomic<int64_t> g_autotune{1};
 std::atomic<int64_t> g_sparse{1};
+std::atomic<int64_t> g_overlap{1};
 std::atomic<int64_t> g_region_bytes{(int64_t)SPARSE_REGION_BYTES_DEFAULT};
 
 int host_threads() {
@@ -287,6 +288,11 @@ uf_status uf_set_option(const char *name, int64_t value) {
     g_sparse = value;
     return UF_OK;
   }
+  if (!strcmp(name, "sparse_overlap")) {
+    if (value != 0 && value != 1) return fail(UF_EINVAL, "sparse_overlap must be 0 or 1");
+    g_overlap = value;
+    return UF_OK;
+  }
   if (!strcmp(name, "sparse_region_bytes")) {
     if (value != 0 && value < 4096) return fail(UF_EINVAL, "sparse_region_bytes must be 0 or >= 4096");
     g_region_bytes = value ? value : (int64_t)SPARSE_REGION_BYTES_DEFAULT;
@@ -304,6 +310,7 @@ int64_t uf_get_option(const char *name) {
   if (!strcmp(name, "autotune")) return g_autotune.load();
   if (!strcmp(name, "sparse")) return g_sparse.load();
   if (!strcmp(name, "sparse_region_bytes")) return g_region_bytes.load();
+  if (!strcmp(name, "sparse_overlap")) return g_overlap.load();
   return -1;
 }
 

@@ -3,6 +3,8 @@
 // block the count rows, embedding rows and the dense stripe accumulate (or
 // the tensor-core gram), the sparse-row scatter, and the finalize, captured
 // into one CUDA graph unless phases are timed.
+#include <array>
+
 #include "uf_runtime.h"
 
 namespace ufg {
@@ -166,25 +168,66 @@ struct PhaseTimer {
   }
 };
 
-// Private stream of the calling thread per device on which a call's launch
-// sequence is captured into a CUDA graph.  Per thread, so that concurrent
-// calls from several threads never share a capturing stream.
+// Private streams of the calling thread per device: [0] records a call's
+// launch sequence into a CUDA graph, [1] carries the sparse-row scatter
+// beside the dense stripe kernel.  Per thread, so that concurrent calls from
+// several threads never share a capturing stream.
 struct ThreadStreams {
-  std::map<int, cudaStream_t> s;
+  std::map<int, std::array<cudaStream_t, 2>> s;
   ~ThreadStreams() {
-    for (auto &kv : s) cudaStreamDestroy(kv.second);
+    for (auto &kv : s)
+      for (cudaStream_t x : kv.second) cudaStreamDestroy(x);
   }
 };
 thread_local ThreadStreams t_streams;
 
-cudaStream_t capture_stream(int device) {
+cudaStream_t private_stream(int device, int which) {
   auto it = t_streams.s.find(device);
-  if (it != t_streams.s.end()) return it->second;
-  cudaStream_t x = nullptr;
-  ck(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "cudaStreamCreate");
-  t_streams.s[device] = x;
-  return x;
+  if (it == t_streams.s.end()) {
+    std::array<cudaStream_t, 2> a{nullptr, nullptr};
+    for (auto &x : a) ck(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "cudaStreamCreate");
+    it = t_streams.s.emplace(device, a).first;
+  }
+  return it->second[which];
 }
+cudaStream_t capture_stream(int device) { return private_stream(device, 0); }
+
+// A side branch of launches on the thread's side stream: fork() makes it wait
+// for everything issued so far on the main stream, join() makes the main
+// stream wait for the branch.  Inside a stream capture both streams belong to
+// the same graph, which then holds two parallel branches.
+struct SideBranch {
+  cudaStream_t main, side;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool forked = false;
+  SideBranch(cudaStream_t m, int device) : main(m), side(private_stream(device, 1)) {}
+  cudaStream_t fork() {
+    ck(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+    ck(cudaEventRecord(ev_fork, main), "cudaEventRecord");
+    ck(cudaStreamWaitEvent(side, ev_fork, 0), "cudaStreamWaitEvent");
+    forked = true;
+    return side;
+  }
+  void join() {
+    if (!forked) return;
+    ck(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming), "cudaEventCreate");
+    ck(cudaEventRecord(ev_join, side), "cudaEventRecord");
+    ck(cudaStreamWaitEvent(main, ev_join, 0), "cudaStreamWaitEvent");
+    forked = false;
+  }
+  ~SideBranch() {
+    if (forked) {  // an error escaped: still keep the main stream behind the branch
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess &&
+          cudaEventRecord(e, side) == cudaSuccess)
+        cudaStreamWaitEvent(main, e, 0);
+      if (e) cudaEventDestroy(e);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    cudaGetLastError();
+  }
+};
 
 // Records the branch-block launch sequence of a call into a CUDA graph (on a
 // private stream) and launches that graph on the caller's stream; when off,
@@ -767,6 +810,12 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
       kernels++;
     }
   };
+  // with option "sparse_overlap" (default) the sparse-row scatter runs on a
+  // side branch beside the dense stripe kernel, forked once the first dense
+  // launch is ready; otherwise (and while the chunk size is being tuned,
+  // which clears M) it runs after the blocks
+  SideBranch side(ls, device);
+  const bool beside = split.n_sparse > 0 && !tune && g_overlap.load() != 0;
   bool tuned = false;
   for (size_t b = 0; b < in.P->b0.size(); b++) {
     const int64_t b0 = in.P->b0[b];
@@ -804,6 +853,12 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
       std::lock_guard<std::mutex> g(g_tune_mu);
       g_tuned_chunk[key] = chunk;
     }
+    if (beside && !side.forked && !side.ev_fork) {
+      const cudaStream_t ss = side.fork();
+      timer.begin(4, ss);
+      launch_sparse(ss);
+      timer.end();
+    }
     timer.begin(1);
     ck(launch_stripe_acc(acc, fp32, sa, ls), "stripe accumulate");
     timer.end();
@@ -817,11 +872,12 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
       kernels += 2;
     }
   }
-  if (split.n_sparse > 0) {
+  if (split.n_sparse > 0 && !side.ev_fork) {  // not launched beside a dense block
     timer.begin(4);
     launch_sparse(ls);
     timer.end();
   }
+  side.join();
   timer.begin(3);
   for (size_t t = 0; t < nt; t++) {
     FinalArgs fa{};

@@ -490,7 +490,7 @@ __global__ void k_diag_reduce(const StripeArgs a, const T *__restrict__ part, in
 }
 
 template <typename K>
-cudaError_t prepare(K kernel, size_t smem, int *grid, int units) {
+cudaError_t prepare(K kernel, size_t smem, int *grid, int units, int max_per_sm = 0) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0, dev = 0, sms = 0;
@@ -500,6 +500,7 @@ cudaError_t prepare(K kernel, size_t smem, int *grid, int units) {
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  if (max_per_sm > 0) per_sm = std::min(per_sm, max_per_sm);
   *grid = std::max(1, std::min(units, std::max(per_sm, 1) * sms));
   return cudaSuccess;
 }
@@ -522,10 +523,10 @@ cudaError_t run_min(const StripeArgs &a, cudaStream_t st) {
 }
 
 template <typename T, int RD, int RK, int MODE, int MINB>
-cudaError_t run_gen(const StripeArgs &a, cudaStream_t st) {
+cudaError_t run_gen(const StripeArgs &a, cudaStream_t st, int max_per_sm = 0) {
   using G = Geo<T, RD, RK, 2>;
   int grid = 0;
-  cudaError_t e = prepare(k_stripe_gen<T, RD, RK, MODE, MINB>, G::SMEM, &grid, units_of(a));
+  cudaError_t e = prepare(k_stripe_gen<T, RD, RK, MODE, MINB>, G::SMEM, &grid, units_of(a), max_per_sm);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
@@ -537,8 +538,8 @@ cudaError_t run_gen(const StripeArgs &a, cudaStream_t st) {
 
 // micro-tiles: min kernels 8 x 8, generalized 4 x 8 (two accumulators)
 void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k) {
-  (void)fp32;
   *tile_s = acc == ACC_GEN ? 16 * 4 : 16 * 8;
+  (void)fp32;
   *tile_k = 16 * 8;
 }
 

@@ -281,3 +281,23 @@ def test_region_scatter_matches_direct_bitwise(n, density):
     finally:
         uf.uf_set_option("tensor_path", 1)
     assert uf.uf_get_option("sparse_region_bytes") == 48_000_000
+
+
+def test_overlap_matches_sequential_bitwise():
+    # the scatter beside the dense kernel adds the same integers in another
+    # order: the results equal the sequential ones bit for bit
+    tree_s = yule_tree(3000, seed=280)
+    table_s = table_prevalence(400, tree_s.n_tips, 0.5, 15.0, seed=281)
+    tree, table = handles(tree_s, table_s)
+    assert uf.uf_get_option("sparse_overlap") == 1
+    try:
+        for method in METHODS:
+            a = 0.5 if method == "generalized" else 1.0
+            for precision in PRECISIONS:
+                uf.uf_set_option("sparse_overlap", 1)
+                beside, _ = uf.uf_compute(tree, table, method, a, precision)
+                uf.uf_set_option("sparse_overlap", 0)
+                after, _ = uf.uf_compute(tree, table, method, a, precision)
+                np.testing.assert_array_equal(beside, after)
+    finally:
+        uf.uf_set_option("sparse_overlap", 1)

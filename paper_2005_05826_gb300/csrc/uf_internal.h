@@ -169,9 +169,8 @@ struct SparseArgs {
   // distinct samples, values and fixed-point terms at lofs[row_base +
   // blockIdx.x] (count in lz) for launch_sparse_region
   int row_base;
-  int32_t *lk;              // distinct samples, ascending
-  void *lx;                 // their x (min form) or u (generalized), float or double
-  long long *lf;            // their fixed-point X or P
+  void *le;                 // entries (sample, x or u, fixed-point X or P), ascending
+                            // sample; sparse_entry_bytes() each
   const int64_t *lofs;      // first entry of each row
   int *lz;                  // entries of each row
   // region mode: only pairs whose stripe lies in [r0, r1) (launch_sparse_region)
@@ -182,6 +181,7 @@ struct SparseArgs {
 constexpr int SPARSE_MAX_ENTRIES = 4096;
 constexpr int SPARSE_LIST_MAX_ENTRIES = 16384;
 size_t sparse_smem_bytes(bool fp32, int cap);
+size_t sparse_entry_bytes(bool fp32);
 cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 // Pairs of the listed rows (nodes[0 .. n_nodes), lists from a list-mode

@@ -685,7 +685,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc);
   const bool region_mode = split.n_sparse > 0 && (n_regions > 1 || split.lists);
   int64_t n_sparse_rows = 0;
-  DevBuf lk, lx, lf, lz;
+  DevBuf le, lz;
   if (split.n_sparse > 0) {
     std::vector<int32_t> all;
     for (const auto &c : split.sparse) {
@@ -699,9 +699,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
       for (size_t r = 0; r < all.size(); r++)
         lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
       const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
-      lk = DevBuf(total_e * 4, st, "alloc sparse lists");
-      lx = DevBuf(total_e * es, st, "alloc sparse lists");
-      lf = DevBuf(total_e * 8, st, "alloc sparse lists");
+      le = DevBuf(total_e * sparse_entry_bytes(fp32), st, "alloc sparse lists");
       lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
       // rows without entries in the table return before writing their count
       ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
@@ -778,9 +776,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sp.alpha = J.alpha;
     sp.scale = scale;
     if (region_mode) {
-      sp.lk = lk.as<int32_t>();
-      sp.lx = lx.p;
-      sp.lf = lf.as<long long>();
+      sp.le = le.p;
       sp.lofs = meta.at<int64_t>(o_lofs);
       sp.lz = lz.as<int>();
     }

@@ -89,6 +89,70 @@ __device__ __forceinline__ void red_add(unsigned long long *p, long long v) {
   atomicAdd(p, (unsigned long long)v);
 }
 
+// One distinct sample of a sparse row: its sample k, value x (or
+// proportion u) and fixed-point term f, packed so that one 16-byte load
+// (two for FP64) fetches all three in the pair loops.
+template <typename T>
+struct alignas(16) SpEnt;
+template <>
+struct alignas(16) SpEnt<float> {
+  int k;
+  float x;
+  long long f;
+};
+template <>
+struct alignas(16) SpEnt<double> {
+  int k, pad;
+  double x;
+  long long f;
+};
+
+// What a pair update needs besides its two entries.
+template <typename T>
+struct PairCtx {
+  int n, s_lo, s_hi, mixed_forms;
+  unsigned long long *M, *M2;  // this table's cells (den and Q for the generalized method)
+  T lt, am1;                   // branch length, alpha - 1
+  double scale;
+};
+
+// Adds the pair (ea, eb), k_a < k_b, to its stripe cell when the stripe is
+// stored: the min form min(X_a, X_b) (-2 times that in an abs-form stripe),
+// or the generalized Q and den terms; twice for the duplicated half stripe.
+template <typename T, int ACC, int MODE>
+__device__ __forceinline__ void add_pair(const SpEnt<T> &ea, const SpEnt<T> &eb, const PairCtx<T> &c) {
+  const int d = eb.k - ea.k;
+  int s, kc;
+  if (2 * d <= c.n) {
+    s = d - 1;
+    kc = ea.k;
+  } else {
+    s = c.n - d - 1;
+    kc = eb.k;
+  }
+  if (s < c.s_lo || s > c.s_hi) return;
+  const int64_t cell = (int64_t)(s - c.s_lo) * c.n + kc;
+  const bool dup = 2 * d == c.n;  // also stored at k = k_b (= k_a + n/2)
+  if (ACC == ACC_MIN) {
+    long long t = min(ea.f, eb.f);
+    if (c.mixed_forms && fp32_abs_row(s)) t *= -2;
+    red_add(c.M + cell, t);
+    if (dup) red_add(c.M + cell + d, t);
+  } else {
+    const T uu = ea.x, vv = eb.x;
+    const T w = c.lt * pow_am1<T, MODE>(uu + vv, c.am1);
+    const long long q = to_fixed(w * tmin<T>(uu, vv), c.scale);
+    const long long e = to_fixed(w * (uu > vv ? uu - vv : vv - uu), c.scale);
+    const long long den = 2 * q + e - ea.f - eb.f;
+    red_add(c.M + cell, den);
+    red_add(c.M2 + cell, q);
+    if (dup) {
+      red_add(c.M + cell + d, den);
+      red_add(c.M2 + cell + d, q);
+    }
+  }
+}
+
 template <typename T, int ACC, int MODE>
 __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -96,9 +160,7 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
   const int P = a.cap;
   unsigned long long *key = reinterpret_cast<unsigned long long *>(smem_raw);  // (sample << 32) | entry
   double *cnt = reinterpret_cast<double *>(key + P);                          // entry -> count
-  long long *fx = reinterpret_cast<long long *>(cnt + P);                     // distinct sample -> X or P
-  T *xs = reinterpret_cast<T *>(fx + P);                                      // distinct sample -> x or u
-  int *ks = reinterpret_cast<int *>(xs + P);                                  // distinct sample -> k
+  SpEnt<T> *E = reinterpret_cast<SpEnt<T> *>(cnt + P);                        // distinct samples
 
   const int v = a.nodes[blockIdx.x];
   const SpTab tb = a.tabs[blockIdx.y];
@@ -137,7 +199,7 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
       }
   }
   // distinct samples: the first entry of each run of equal samples
-  const int E = (L + NT - 1) / NT, i0 = tid * E, i1 = min(L, i0 + E);
+  const int EPT = (L + NT - 1) / NT, i0 = tid * EPT, i1 = min(L, i0 + EPT);
   int heads = 0;
   for (int i = i0; i < i1; i++) heads += (i == 0 || (key[i] >> 32) != (key[i - 1] >> 32));
   int z = 0;
@@ -156,16 +218,18 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
     long long f;
     if (ACC == ACC_MIN) f = to_fixed(x, a.scale);
     else f = to_fixed((T)l * pow_alpha<T, MODE>(x, alpha), a.scale);
-    ks[u] = (int)smp;
-    xs[u] = x;
-    fx[u] = f;
+    SpEnt<T> en;
+    en.k = (int)smp;
+    en.x = x;
+    en.f = f;
+    E[u] = en;
     u++;
   }
   __syncthreads();
   if (a.gram) {
-    for (int e = tid; e < z; e += NT) red_add(a.M + tb.m_off + (int64_t)ks[e] * tb.n_pad + ks[e], fx[e]);
+    for (int e = tid; e < z; e += NT) red_add(a.M + tb.m_off + (int64_t)E[e].k * tb.n_pad + E[e].k, E[e].f);
   } else {
-    for (int e = tid; e < z; e += NT) red_add(a.Dsp + tb.off + ks[e], fx[e]);
+    for (int e = tid; e < z; e += NT) red_add(a.Dsp + tb.off + E[e].k, E[e].f);
   }
 
   // pairs (ia < ib) numbered row by row: row ia starts at ia (2z - ia - 1) / 2
@@ -182,56 +246,35 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
   while (ia > 0 && row_start(ia) > p) ia--;
   while (ia < z - 2 && row_start(ia + 1) <= p) ia++;
   int ib = ia + 1 + (int)(p - row_start(ia));
-  const int n = tb.n;
-  unsigned long long *M = a.M + tb.m_off;
-  unsigned long long *M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
-  const T lt = (T)l, am1 = (T)(a.alpha - 1.0);
+  SpEnt<T> ea = E[ia];
   if (ACC == ACC_MIN && a.gram) {
     for (; p < p1; p++) {
-      red_add(a.M + tb.m_off + (int64_t)ks[ib] * tb.n_pad + ks[ia], min(fx[ia], fx[ib]));
+      const SpEnt<T> eb = E[ib];
+      red_add(a.M + tb.m_off + (int64_t)eb.k * tb.n_pad + ea.k, min(ea.f, eb.f));
       if (++ib == z) {
         ia++;
         ib = ia + 1;
+        ea = E[ia];
       }
     }
     return;
   }
+  PairCtx<T> c;
+  c.n = tb.n;
+  c.s_lo = tb.s_lo;
+  c.s_hi = tb.s_hi;
+  c.mixed_forms = a.mixed_forms;
+  c.M = a.M + tb.m_off;
+  c.M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
+  c.lt = (T)l;
+  c.am1 = (T)(a.alpha - 1.0);
+  c.scale = a.scale;
   for (; p < p1; p++) {
-    const int ka = ks[ia], kb = ks[ib];
-    const int d = kb - ka;
-    int s, kc;
-    if (2 * d <= n) {
-      s = d - 1;
-      kc = ka;
-    } else {
-      s = n - d - 1;
-      kc = kb;
-    }
-    if (s >= tb.s_lo && s <= tb.s_hi) {
-      const int64_t cell = (int64_t)(s - tb.s_lo) * n + kc;
-      const bool dup = 2 * d == n;  // also stored at k = kb (= ka + n/2)
-      if (ACC == ACC_MIN) {
-        long long t = min(fx[ia], fx[ib]);
-        if (a.mixed_forms && fp32_abs_row(s)) t *= -2;
-        red_add(M + cell, t);
-        if (dup) red_add(M + cell + d, t);
-      } else {
-        const T uu = xs[ia], vv = xs[ib];
-        const T w = lt * pow_am1<T, MODE>(uu + vv, am1);
-        const long long q = to_fixed(w * tmin<T>(uu, vv), a.scale);
-        const long long e = to_fixed(w * (uu > vv ? uu - vv : vv - uu), a.scale);
-        const long long den = 2 * q + e - fx[ia] - fx[ib];
-        red_add(M + cell, den);
-        red_add(M2 + cell, q);
-        if (dup) {
-          red_add(M + cell + d, den);
-          red_add(M2 + cell + d, q);
-        }
-      }
-    }
+    add_pair<T, ACC, MODE>(ea, E[ib], c);
     if (++ib == z) {
       ia++;
       ib = ia + 1;
+      ea = E[ia];
     }
   }
 }
@@ -277,7 +320,7 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
         __syncthreads();
       }
   }
-  const int E = (L + NT - 1) / NT, i0 = tid * E, i1 = min(L, i0 + E);
+  const int EPT = (L + NT - 1) / NT, i0 = tid * EPT, i1 = min(L, i0 + EPT);
   int heads = 0;
   for (int i = i0; i < i1; i++) heads += (i == 0 || (key[i] >> 32) != (key[i - 1] >> 32));
   int z = 0;
@@ -285,7 +328,7 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
   const double l = a.length[v];
   const T alpha = (T)a.alpha;
   const int64_t off = a.lofs[row];
-  T *lx = reinterpret_cast<T *>(a.lx);
+  SpEnt<T> *le = reinterpret_cast<SpEnt<T> *>(a.le);
   for (int i = i0; i < i1; i++) {
     const unsigned smp = (unsigned)(key[i] >> 32);
     if (i > 0 && (unsigned)(key[i - 1] >> 32) == smp) continue;
@@ -298,20 +341,23 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
     long long f;
     if (ACC == ACC_MIN) f = to_fixed(x, a.scale);
     else f = to_fixed((T)l * pow_alpha<T, MODE>(x, alpha), a.scale);
-    a.lk[off + u] = (int32_t)smp;
-    lx[off + u] = x;
-    a.lf[off + u] = f;
+    SpEnt<T> en;
+    en.k = (int)smp;
+    en.x = x;
+    en.f = f;
+    le[off + u] = en;
     red_add(a.Dsp + tb.off + smp, f);
     u++;
   }
   if (tid == 0) a.lz[row] = z;
 }
 
-// first index in [lo, hi) of the ascending ks with ks[i] >= key
-__device__ __forceinline__ int lower_index(const int32_t *ks, int lo, int hi, int key) {
+// first index in [lo, hi) of the entries (ascending k) with E[i].k >= key
+template <typename T>
+__device__ __forceinline__ int lower_index(const SpEnt<T> *E, int lo, int hi, int key) {
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (ks[mid] < key) lo = mid + 1;
+    if (E[mid].k < key) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -325,15 +371,20 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   const int64_t off = a.lofs[row];
   // never past the row's list capacity
   const int z = (int)min((int64_t)a.lz[row], a.lofs[row + 1] - off);
-  const int32_t *ks = a.lk + off;
-  const T *xs = reinterpret_cast<const T *>(a.lx) + off;
-  const long long *fx = a.lf + off;
+  const SpEnt<T> *E = reinterpret_cast<const SpEnt<T> *>(a.le) + off;
   const int n = tb.n, half = n / 2;
-  unsigned long long *M = a.M + tb.m_off;
-  unsigned long long *M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
-  const T lt = (T)a.length[v], am1 = (T)(a.alpha - 1.0);
+  PairCtx<T> c;
+  c.n = n;
+  c.s_lo = tb.s_lo;
+  c.s_hi = tb.s_hi;
+  c.mixed_forms = a.mixed_forms;
+  c.M = a.M + tb.m_off;
+  c.M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
+  c.lt = (T)a.length[v];
+  c.am1 = (T)(a.alpha - 1.0);
+  c.scale = a.scale;
   for (int ia = threadIdx.x; ia < z - 1; ia += blockDim.x) {
-    const int ka = ks[ia];
+    const SpEnt<T> ea = E[ia];
     // window 1: d = k_b - k_a in [r0 + 1, min(r1, n/2)], stripe d - 1, cell column k_a
     // window 2: d in [max(n - r1, n/2 + 1), n - r0 - 1], stripe n - d - 1, column k_b
     const int d_lo[2] = {a.r0 + 1, max(n - a.r1, half + 1)};
@@ -341,34 +392,9 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
 #pragma unroll
     for (int w = 0; w < 2; w++) {
       if (d_lo[w] > d_hi[w]) continue;
-      const int b0 = lower_index(ks, ia + 1, z, ka + d_lo[w]);
-      const int b1 = lower_index(ks, b0, z, ka + d_hi[w] + 1);
-      for (int ib = b0; ib < b1; ib++) {
-        const int kb = ks[ib];
-        const int d = kb - ka;
-        const int s = w == 0 ? d - 1 : n - d - 1;
-        const int kc = w == 0 ? ka : kb;
-        const int64_t cell = (int64_t)(s - tb.s_lo) * n + kc;
-        const bool dup = 2 * d == n;  // also stored at k = kb (= ka + n/2)
-        if (ACC == ACC_MIN) {
-          long long t = min(fx[ia], fx[ib]);
-          if (a.mixed_forms && fp32_abs_row(s)) t *= -2;
-          red_add(M + cell, t);
-          if (dup) red_add(M + cell + d, t);
-        } else {
-          const T uu = xs[ia], vv = xs[ib];
-          const T wgt = lt * pow_am1<T, MODE>(uu + vv, am1);
-          const long long q = to_fixed(wgt * tmin<T>(uu, vv), a.scale);
-          const long long e = to_fixed(wgt * (uu > vv ? uu - vv : vv - uu), a.scale);
-          const long long den = 2 * q + e - fx[ia] - fx[ib];
-          red_add(M + cell, den);
-          red_add(M2 + cell, q);
-          if (dup) {
-            red_add(M + cell + d, den);
-            red_add(M2 + cell + d, q);
-          }
-        }
-      }
+      const int b0 = lower_index(E, ia + 1, z, ea.k + d_lo[w]);
+      const int b1 = lower_index(E, b0, z, ea.k + d_hi[w] + 1);
+      for (int ib = b0; ib < b1; ib++) add_pair<T, ACC, MODE>(ea, E[ib], c);
     }
   }
 }
@@ -387,8 +413,10 @@ cudaError_t launch_one(const SparseArgs &a, size_t smem, cudaStream_t st) {
 }  // namespace
 
 size_t sparse_smem_bytes(bool fp32, int cap) {
-  return (size_t)cap * (8 + 8 + 8 + (fp32 ? 4 : 8) + 4);
+  return (size_t)cap * (8 + 8 + (fp32 ? sizeof(SpEnt<float>) : sizeof(SpEnt<double>)));
 }
+
+size_t sparse_entry_bytes(bool fp32) { return fp32 ? sizeof(SpEnt<float>) : sizeof(SpEnt<double>); }
 
 cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st) {
   if (a.n_nodes <= 0 || a.n_tabs <= 0) return cudaSuccess;

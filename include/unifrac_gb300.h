@@ -140,8 +140,10 @@ typedef struct {
  *                    to the tensor-core unweighted path; the results agree
  *                    within the precision's tolerance.
  *   "sparse_overlap" 1 (default): the sparse-row scatter runs on a second
- *                    stream beside the dense stripe kernel (it fills the SM
- *                    slots and the tail the dense kernel leaves); 0: after it
+ *                    stream beside the count pass, the embeddings and the
+ *                    dense stripe kernel or tensor-core gram (it fills the SM
+ *                    slots those leave); 0: in sequence with them.  The
+ *                    results are the same bit for bit (integer accumulators)
  *   "sparse_region_bytes"  48,000,000 (default; 0 restores it): a one-table
  *                    call whose stripe accumulators exceed this many bytes
  *                    writes the scattered branches' sample lists once and

@@ -124,18 +124,16 @@ cudaError_t launch_slice_counts(const int32_t *nodes, int n_list, const int32_t 
                                 const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
                                 const double *col_val, double *counts, int64_t ld, int n, cudaStream_t st) {
   if (n_list <= 0) return cudaSuccess;
-  k_slice_counts<double><<<n_list, 256, 0, st>>>(nodes, tip_lo, tip_hi, slot_of_node, col_ptr, col_row, col_val,
-                                                 counts, ld, n);
-  return cudaGetLastError();
+  return launch_k(k_slice_counts<double>, dim3(n_list), dim3(256), 0, st, nodes, tip_lo, tip_hi, slot_of_node, col_ptr,
+                  col_row, col_val, counts, ld, n);
 }
 
 cudaError_t launch_slice_presence(const int32_t *nodes, int n_list, const int32_t *tip_lo, const int32_t *tip_hi,
                                   const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
                                   uint8_t *flags, int64_t ld, int n, cudaStream_t st) {
   if (n_list <= 0) return cudaSuccess;
-  k_slice_counts<uint8_t><<<n_list, 256, 0, st>>>(nodes, tip_lo, tip_hi, slot_of_node, col_ptr, col_row, nullptr,
-                                                  flags, ld, n);
-  return cudaGetLastError();
+  return launch_k(k_slice_counts<uint8_t>, dim3(n_list), dim3(256), 0, st, nodes, tip_lo, tip_hi, slot_of_node,
+                  col_ptr, col_row, (const double *)nullptr, flags, ld, n);
 }
 
 cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
@@ -143,8 +141,7 @@ cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *
                                double *counts, int64_t ld, cudaStream_t st) {
   if (n_list <= 0) return cudaSuccess;
   dim3 grid(n_list, (unsigned)((ld + 255) / 256));
-  k_node_counts<double><<<grid, 256, 0, st>>>(nodes, child_ptr, child_idx, slot_of_node, counts, ld);
-  return cudaGetLastError();
+  return launch_k(k_node_counts<double>, grid, dim3(256), 0, st, nodes, child_ptr, child_idx, slot_of_node, counts, ld);
 }
 
 cudaError_t launch_node_presence(const int32_t *nodes, int n_list, const int32_t *child_ptr,
@@ -152,8 +149,7 @@ cudaError_t launch_node_presence(const int32_t *nodes, int n_list, const int32_t
                                  uint8_t *flags, int64_t ld, cudaStream_t st) {
   if (n_list <= 0) return cudaSuccess;
   dim3 grid(n_list, (unsigned)((ld + 255) / 256));
-  k_node_counts<uint8_t><<<grid, 256, 0, st>>>(nodes, child_ptr, child_idx, slot_of_node, flags, ld);
-  return cudaGetLastError();
+  return launch_k(k_node_counts<uint8_t>, grid, dim3(256), 0, st, nodes, child_ptr, child_idx, slot_of_node, flags, ld);
 }
 
 cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
@@ -162,20 +158,18 @@ cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
                             void *X, int64_t pitch, const TabDesc *tabs, int n_tabs, cudaStream_t st,
                             const int32_t *nodes) {
   if (rows <= 0) return cudaSuccess;
-#define UF_EMB(T, K)                                                                            \
-  k_emb_rows<T, K><<<rows, 256, 0, st>>>(b0, nodes, slot_of_node, counts, ld, length, total, inv_total_f, \
-                                         (T *)X, pitch, tabs, n_tabs)
+#define UF_EMB(T, K)                                                                                 \
+  return launch_k(k_emb_rows<T, K>, dim3(rows), dim3(256), 0, st, b0, nodes, slot_of_node, counts, ld, length, \
+                  total, inv_total_f, (T *)X, pitch, tabs, n_tabs)
   if (fp32) {
     if (kind == EMB_SCALED) UF_EMB(float, EMB_SCALED);
-    else if (kind == EMB_PRESENCE) UF_EMB(float, EMB_PRESENCE);
-    else UF_EMB(float, EMB_PROP);
-  } else {
-    if (kind == EMB_SCALED) UF_EMB(double, EMB_SCALED);
-    else if (kind == EMB_PRESENCE) UF_EMB(double, EMB_PRESENCE);
-    else UF_EMB(double, EMB_PROP);
+    if (kind == EMB_PRESENCE) UF_EMB(float, EMB_PRESENCE);
+    UF_EMB(float, EMB_PROP);
   }
+  if (kind == EMB_SCALED) UF_EMB(double, EMB_SCALED);
+  if (kind == EMB_PRESENCE) UF_EMB(double, EMB_PRESENCE);
+  UF_EMB(double, EMB_PROP);
 #undef UF_EMB
-  return cudaGetLastError();
 }
 
 }  // namespace ufg

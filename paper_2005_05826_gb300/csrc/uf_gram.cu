@@ -424,9 +424,8 @@ cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, 
                              int npad_tot, int64_t K_pad, void *Pl, cudaStream_t st, const int32_t *nodes) {
   const int k_len = (int)((rows + GK - 1) / GK * GK);
   dim3 grid((k_len + 31) / 32, (npad_tot + 31) / 32), block(32, 8);
-  k_gram_prep<<<grid, block, 0, st>>>(b0, nodes, rows, k_len, slot_of_node, flags, ld, length, tabs, n_tabs,
-                                       npad_tot, K_pad, (__nv_bfloat16 *)Pl);
-  return cudaGetLastError();
+  return launch_k(k_gram_prep, grid, block, 0, st, b0, nodes, rows, k_len, slot_of_node, flags, ld, length, tabs,
+                  n_tabs, npad_tot, K_pad, (__nv_bfloat16 *)Pl);
 }
 
 cudaError_t launch_gram(const GramArgs &a0, void *Pl, int64_t K_pad, cudaStream_t st) {
@@ -454,8 +453,7 @@ cudaError_t launch_gram(const GramArgs &a0, void *Pl, int64_t K_pad, cudaStream_
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const int grid = std::max(1, std::min(a.n_units, sms));
-  k_gram<<<grid, G_THREADS, smem, st>>>(mapA, mapB, a);
-  return cudaGetLastError();
+  return launch_k(k_gram, dim3(grid), dim3(G_THREADS), smem, st, mapA, mapB, a);
 }
 
 cudaError_t launch_finalize_gram(const GramFinalArgs &a, cudaStream_t st) {

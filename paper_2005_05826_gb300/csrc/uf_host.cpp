@@ -614,4 +614,10 @@ uf_status set_last_error(uf_status st, const char *msg) {
   g_err = msg ? msg : "";
   return st;
 }
+
+namespace {
+thread_local int tl_launch_priority = 0;
+}
+int launch_priority() { return tl_launch_priority; }
+void set_launch_priority(int p) { tl_launch_priority = p; }
 }  // namespace ufg

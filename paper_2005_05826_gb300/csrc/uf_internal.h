@@ -261,4 +261,33 @@ namespace ufg {
 double accum_scale(const ::uf_tree *tree, const ::uf_table *table, int kind);
 // Set the calling thread's uf_last_error() text and return st (uf_host.cpp).
 uf_status set_last_error(uf_status st, const char *msg);
+
+// Scheduling priority that the calling thread's launches through launch_k
+// carry (uf_host.cpp; 0: the stream's own).  A call raises it for the
+// launches of its main path while its sparse-row scatter runs on a side
+// stream at the default priority, so that the scatter takes only the SM
+// slots the main path leaves free.
+int launch_priority();
+void set_launch_priority(int p);
+
+// kernel<<<grid, block, smem, st>>>(args...) with the thread's launch
+// priority as a launch attribute (kept when the launch is captured into a
+// graph).
+template <typename... KP, typename... A>
+cudaError_t launch_k(void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A &&...args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  const int p = launch_priority();
+  if (p != 0) {
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = p;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
+}
 }  // namespace ufg

@@ -229,6 +229,21 @@ struct SideBranch {
   }
 };
 
+// Raises the calling thread's launch priority (launch_k) to the device's
+// highest for its lifetime when on: the main path of a call whose sparse-row
+// scatter runs beside it.
+struct PriorityScope {
+  int old;
+  bool on;
+  explicit PriorityScope(bool enable) : old(launch_priority()), on(enable) {
+    if (!on) return;
+    int least = 0, greatest = 0;
+    ck(cudaDeviceGetStreamPriorityRange(&least, &greatest), "cudaDeviceGetStreamPriorityRange");
+    set_launch_priority(greatest);
+  }
+  ~PriorityScope() { set_launch_priority(old); }
+};
+
 // Records the branch-block launch sequence of a call into a CUDA graph (on a
 // private stream) and launches that graph on the caller's stream; when off,
 // launches go to the caller's stream directly.
@@ -236,6 +251,9 @@ struct Capture {
   bool on;
   cudaStream_t user, cap = nullptr;
   bool open = false;
+  // the graph runs its kernels at their own launch priorities (launch_k)
+  // rather than at the caller's stream priority
+  bool node_priority = false;
   Capture(bool enable, cudaStream_t st, int device) : on(enable), user(st) {
     if (!on) return;
     cap = capture_stream(device);
@@ -250,7 +268,8 @@ struct Capture {
     open = false;
     ck(cudaStreamEndCapture(cap, &g), "cudaStreamEndCapture");
     cudaGraphExec_t e = nullptr;
-    cudaError_t err = cudaGraphInstantiate(&e, g, 0);
+    cudaError_t err =
+        cudaGraphInstantiate(&e, g, node_priority ? (unsigned long long)cudaGraphInstantiateFlagUseNodePriority : 0ull);
     if (err == cudaSuccess) err = cudaGraphLaunch(e, user);
     if (e) cudaGraphExecDestroy(e);  // freed once the launch completes
     cudaGraphDestroy(g);
@@ -521,9 +540,15 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   double exec_flops = 0.0;
   Capture cap(g_graph.load() != 0 && !timer.on, st, device);
   const cudaStream_t ls = cap.stream();
-  // the sparse-row scatters need no count rows or planes: first
+  // the sparse-row scatters need no count rows or planes: first, on a side
+  // branch beside the presence pass and the gram with option
+  // "sparse_overlap" (both add into Gt with integer atomics)
+  SideBranch side(ls, device);
+  const PriorityScope prio(split.n_sparse > 0 && g_overlap.load() != 0);
+  cap.node_priority = prio.on;
   if (split.n_sparse > 0) {
-    timer.begin(4);
+    const cudaStream_t ss = g_overlap.load() != 0 ? side.fork() : ls;
+    timer.begin(4, ss);
     for (size_t c = 0; c < split.sparse.size(); c++) {
       if (split.sparse[c].empty()) continue;
       SparseArgs sp{};
@@ -540,7 +565,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
       sp.M = Gt.as<unsigned long long>();
       sp.alpha = 1.0;
       sp.scale = scale;
-      ck(launch_sparse_rows(ACC_MIN, false, sp, ls), "sparse rows");
+      ck(launch_sparse_rows(ACC_MIN, false, sp, ss), "sparse rows");
       kernels++;
     }
     timer.end();
@@ -577,6 +602,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
     acc_launches++;
     exec_flops += 2.0 * 3 * 128.0 * 256.0 * ga.k_len * n_tiles;
   }
+  side.join();
   timer.begin(3);
   for (size_t t = 0; t < nt; t++) {
     GramFinalArgs fa{};
@@ -807,11 +833,18 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     }
   };
   // with option "sparse_overlap" (default) the sparse-row scatter runs on a
-  // side branch beside the dense stripe kernel, forked once the first dense
-  // launch is ready; otherwise (and while the chunk size is being tuned,
-  // which clears M) it runs after the blocks
+  // side branch beside the count pass, the embeddings and the dense stripe
+  // kernel (it needs none of them); otherwise (and while the chunk size is
+  // being tuned, which clears M) it runs after the blocks
   SideBranch side(ls, device);
-  const bool beside = split.n_sparse > 0 && !tune && g_overlap.load() != 0;
+  const PriorityScope prio(split.n_sparse > 0 && !tune && g_overlap.load() != 0);
+  cap.node_priority = prio.on;
+  if (split.n_sparse > 0 && !tune && g_overlap.load() != 0) {
+    const cudaStream_t ss = side.fork();
+    timer.begin(4, ss);
+    launch_sparse(ss);
+    timer.end();
+  }
   bool tuned = false;
   for (size_t b = 0; b < in.P->b0.size(); b++) {
     const int64_t b0 = in.P->b0[b];
@@ -848,12 +881,6 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
       tuned = true;
       std::lock_guard<std::mutex> g(g_tune_mu);
       g_tuned_chunk[key] = chunk;
-    }
-    if (beside && !side.forked && !side.ev_fork) {
-      const cudaStream_t ss = side.fork();
-      timer.begin(4, ss);
-      launch_sparse(ss);
-      timer.end();
     }
     timer.begin(1);
     ck(launch_stripe_acc(acc, fp32, sa, ls), "stripe accumulate");

@@ -518,8 +518,7 @@ cudaError_t run_min(const StripeArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  k_stripe_min<T, RD, RK, ABSM, MINB><<<grid, NT, G::SMEM, st>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_stripe_min<T, RD, RK, ABSM, MINB>, dim3(grid), dim3(NT), G::SMEM, st, a);
 }
 
 template <typename T, int RD, int RK, int MODE, int MINB>
@@ -530,8 +529,7 @@ cudaError_t run_gen(const StripeArgs &a, cudaStream_t st, int max_per_sm = 0) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  k_stripe_gen<T, RD, RK, MODE, MINB><<<grid, NT, G::SMEM, st>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_stripe_gen<T, RD, RK, MODE, MINB>, dim3(grid), dim3(NT), G::SMEM, st, a);
 }
 
 }  // namespace
@@ -568,13 +566,13 @@ cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStrea
   dim3 g1((a.n_cols + 127) / 128, n_sb);
   const int g2 = (a.n_cols + 127) / 128;
   if (fp32) {
-    k_diag_partial<float><<<g1, 128, 0, st>>>(a, (float *)scratch);
-    k_diag_reduce<float><<<g2, 128, 0, st>>>(a, (const float *)scratch, n_sb);
-  } else {
-    k_diag_partial<double><<<g1, 128, 0, st>>>(a, (double *)scratch);
-    k_diag_reduce<double><<<g2, 128, 0, st>>>(a, (const double *)scratch, n_sb);
+    const cudaError_t e = launch_k(k_diag_partial<float>, g1, dim3(128), 0, st, a, (float *)scratch);
+    if (e != cudaSuccess) return e;
+    return launch_k(k_diag_reduce<float>, dim3(g2), dim3(128), 0, st, a, (const float *)scratch, n_sb);
   }
-  return cudaGetLastError();
+  const cudaError_t e = launch_k(k_diag_partial<double>, g1, dim3(128), 0, st, a, (double *)scratch);
+  if (e != cudaSuccess) return e;
+  return launch_k(k_diag_reduce<double>, dim3(g2), dim3(128), 0, st, a, (const double *)scratch, n_sb);
 }
 
 }  // namespace ufg

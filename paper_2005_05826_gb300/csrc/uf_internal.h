@@ -132,65 +132,6 @@ struct FinalArgs {
 };
 cudaError_t launch_finalize(const FinalArgs &a, cudaStream_t st);
 
-// ---- sparse rows (uf_sparse.cu) ----
-// A branch whose subtree holds few nonzero counts adds to a stripe cell only
-// when both samples of the cell are nonzero under it (min(x_k, x_j) = 0
-// otherwise; the generalized den is split into per-sample terms plus a pair
-// correction).  Such rows skip the dense kernels: one CTA per (row, table)
-// gathers the subtree's nonzero samples from the table's CSC columns (the
-// subtree's tips are a contiguous range of tip numbers) and scatters the
-// both-nonzero pairs into the accumulators.
-struct SpTab {
-  const int64_t *col_ptr;   // CSC of the table: tip f -> entries [col_ptr[f], col_ptr[f + 1])
-  const int32_t *col_row;   // sample of each entry (ascending within a tip)
-  const double *col_val;    // count of each entry
-  const double *total;      // per-sample count totals
-  const float *inv_total_f; // 1 / total in FP32
-  int n, off, s_lo, s_hi;   // samples, combined column, stored stripes
-  int64_t m_off;            // first accumulator cell (gram layout: first cell of its gram matrix)
-  int n_pad;                // gram layout: row length of its gram matrix
-};
-struct SparseArgs {
-  const int32_t *nodes;     // sparse branch nodes of this launch
-  int n_nodes;
-  int cap;                  // shared-memory capacity in entries (power of two, >= 128)
-  const int32_t *tip_lo, *tip_hi;  // tips of node v: tip numbers [tip_lo[v], tip_hi[v])
-  const double *length;     // branch length of every node
-  const SpTab *tabs;
-  int n_tabs;
-  int kind;                 // EmbKind
-  int mixed_forms;          // FP32 min kernel abs-form stripes present
-  int gram;                 // 1: presence rows into the tensor path's gram matrices
-                            // (cell (i, j), i <= j, at m_off + j * n_pad + i; the
-                            // diagonal takes the per-sample terms; Dsp unused)
-  unsigned long long *M, *M2, *Dsp;  // cells (M / den), Q (generalized), per-sample diagonal R
-  double alpha, scale;
-  // list mode (one table, launch_sparse_lists): row blockIdx.x writes its
-  // distinct samples, values and fixed-point terms at lofs[row_base +
-  // blockIdx.x] (count in lz) for launch_sparse_region
-  int row_base;
-  void *le;                 // entries (sample, x or u, fixed-point X or P), ascending
-                            // sample; sparse_entry_bytes() each
-  const int64_t *lofs;      // first entry of each row
-  int *lz;                  // entries of each row
-  // region mode: only pairs whose stripe lies in [r0, r1) (launch_sparse_region)
-  int r0, r1;
-};
-// largest subtree entry count a sparse row may have: scattered directly from
-// shared memory, or written as a list (one table, keys alone in shared memory)
-constexpr int SPARSE_MAX_ENTRIES = 4096;
-constexpr int SPARSE_LIST_MAX_ENTRIES = 16384;
-size_t sparse_smem_bytes(bool fp32, int cap);
-size_t sparse_entry_bytes(bool fp32);
-cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
-cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
-// Pairs of the listed rows (nodes[0 .. n_nodes), lists from a list-mode
-// launch, table tabs[0]) whose stripe lies in [a.r0, a.r1): one CTA per row,
-// each thread takes samples a and finds the partners b of the two windows
-// of k_b - k_a that map into the region by binary search.  Run region by
-// region so that the accumulator cells a launch touches stay in L2.
-cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
-
 // ---- unweighted on tensor cores (uf_gram.cu) ----
 // One table of a batch: its samples occupy rows [row_base, row_base + n_pad)
 // of every presence plane; its gram matrix starts at gt_off.

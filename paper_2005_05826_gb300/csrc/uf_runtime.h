@@ -24,6 +24,7 @@
 
 #include "../../include/unifrac_gb300.h"
 #include "uf_internal.h"
+#include "uf_sparse.h"
 
 namespace ufg {
 namespace rt {

@@ -35,6 +35,7 @@
 #include <cmath>
 
 #include "uf_device.cuh"
+#include "uf_sparse.h"
 
 namespace ufg {
 

@@ -8,6 +8,11 @@
 // Stripes are the paper's independent subproblems (Abstract; Sec. 2 Fig. 1).
 #include "uf_runtime.h"
 
+#include <unistd.h>
+
+#include <condition_variable>
+#include <deque>
+
 using namespace ufg;
 using namespace ufg::rt;
 
@@ -28,6 +33,97 @@ std::atomic<int64_t> g_region_bytes{(int64_t)SPARSE_REGION_BYTES_DEFAULT};
 int host_threads() {
   const unsigned h = std::thread::hardware_concurrency();
   return (int)std::max(1u, std::min(h == 0 ? 1u : h, 16u));
+}
+
+namespace {
+
+// The host worker pool behind parallel_for.  A call queues a job (its body,
+// n, and counters on the caller's stack); idle workers attach to the front
+// job and take indices until none is left, then detach.  The caller takes
+// indices too, removes the job from the queue, and waits until every index
+// has finished and no worker is attached, so the job never outlives its call.
+struct PoolJob {
+  const std::function<void(int)> *body;
+  int n;
+  std::atomic<int> next{0}, left{0};
+  int users = 0;  // attached workers (guarded by the pool mutex)
+};
+
+struct Pool {
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<PoolJob *> q;
+  std::vector<std::thread> workers;
+  bool stop = false;
+  pid_t pid = getpid();
+
+  explicit Pool(int n_workers) {
+    for (int i = 0; i < n_workers; i++) workers.emplace_back([this] { work(); });
+  }
+  ~Pool() {
+    {
+      std::lock_guard<std::mutex> g(mu);
+      stop = true;
+    }
+    cv_work.notify_all();
+    for (auto &w : workers)
+      if (w.joinable()) w.join();
+  }
+  static void take(PoolJob *j) {
+    for (int i; (i = j->next.fetch_add(1)) < j->n;) {
+      (*j->body)(i);
+      j->left.fetch_sub(1);
+    }
+  }
+  void work() {
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+      cv_work.wait(lk, [&] { return stop || !q.empty(); });
+      if (stop) return;
+      PoolJob *j = q.front();
+      j->users++;
+      lk.unlock();
+      take(j);
+      lk.lock();
+      if (!q.empty() && q.front() == j) q.pop_front();  // no index left to hand out
+      j->users--;
+      cv_done.notify_all();
+    }
+  }
+};
+
+Pool *host_pool() {
+  // started on first use, never destroyed while other threads may use it
+  static Pool *pool = new Pool(std::max(0, host_threads() - 1));
+  return pool;
+}
+
+}  // namespace
+
+void run_parallel(int n, const std::function<void(int)> &body) {
+  if (n <= 0) return;
+  Pool *pool = n > 1 ? host_pool() : nullptr;
+  if (!pool || pool->workers.empty() || pool->pid != getpid()) {
+    for (int i = 0; i < n; i++) body(i);
+    return;
+  }
+  PoolJob j;
+  j.body = &body;
+  j.n = n;
+  j.left = n;
+  {
+    std::lock_guard<std::mutex> g(pool->mu);
+    pool->q.push_back(&j);
+  }
+  pool->cv_work.notify_all();
+  Pool::take(&j);
+  std::unique_lock<std::mutex> lk(pool->mu);
+  for (auto it = pool->q.begin(); it != pool->q.end(); ++it)
+    if (*it == &j) {
+      pool->q.erase(it);
+      break;
+    }
+  pool->cv_done.wait(lk, [&] { return j.left.load() == 0 && j.users == 0; });
 }
 
 uf_status fail(uf_status st, const char *fmt, ...) {
@@ -436,12 +532,25 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
       while (k < n_samples && indptr[k] < want) k++;
       k_lo[c] = k;
     }
-    // validation (first failing sample wins, as a sequential scan would report)
+    auto t = std::make_unique<uf_table>();
+    static std::atomic<uint64_t> next_id{1};
+    t->n = n_samples;
+    t->n_features = n_features;
+    t->nnz = nnz;
+    t->total.assign(n_samples, 0.0);
+    t->inv_total_f.assign(n_samples, 0.f);
+    // one pass per thread over its samples: validation (the first failing
+    // sample wins, as a sequential scan would report), sample totals and the
+    // thread's column counts for the CSC view (a counting sort)
     std::vector<int64_t> bad_k(T, -1);
     std::vector<std::string> bad_msg(T);
+    std::vector<std::vector<int64_t>> cnt(T);
     parallel_for(T, [&](int c) {
+      cnt[c].assign(n_features, 0);
+      int64_t *cc = cnt[c].data();
       char buf[160];
-      for (int64_t k = k_lo[c]; k < k_lo[c + 1]; k++)
+      for (int64_t k = k_lo[c]; k < k_lo[c + 1]; k++) {
+        double s = 0.0;
         for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
           if (indices[q] < 0 || indices[q] >= n_features)
             snprintf(buf, sizeof buf, "sample %lld: feature index %d out of range", (long long)k, indices[q]);
@@ -449,48 +558,46 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
             snprintf(buf, sizeof buf, "sample %lld: feature indices not strictly increasing", (long long)k);
           else if (!std::isfinite(data[q]) || data[q] <= 0.0)
             snprintf(buf, sizeof buf, "sample %lld: count %g must be finite and > 0", (long long)k, data[q]);
-          else
+          else {
+            s += data[q];
+            cc[indices[q]]++;
             continue;
+          }
           bad_k[c] = k;
           bad_msg[c] = buf;
           return;
-        }
-    });
-    for (int c = 0; c < T; c++)
-      if (bad_k[c] >= 0) return fail(UF_ETABLE, "%s", bad_msg[c].c_str());
-    auto t = std::make_unique<uf_table>();
-    static std::atomic<uint64_t> next_id{1};
-    t->id = next_id++;
-    t->n = n_samples;
-    t->n_features = n_features;
-    t->nnz = nnz;
-    t->total.assign(n_samples, 0.0);
-    t->inv_total_f.assign(n_samples, 0.f);
-    // CSC view by a counting sort: per-thread column counts, then each thread
-    // scatters its samples (in increasing order) behind the earlier threads'
-    std::vector<std::vector<int64_t>> cnt(T, std::vector<int64_t>(n_features, 0));
-    parallel_for(T, [&](int c) {
-      int64_t *cc = cnt[c].data();
-      for (int64_t k = k_lo[c]; k < k_lo[c + 1]; k++) {
-        double s = 0.0;
-        for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
-          s += data[q];
-          cc[indices[q]]++;
         }
         t->total[k] = s;
         t->inv_total_f[k] = (float)(1.0 / s);
       }
     });
+    for (int c = 0; c < T; c++)
+      if (bad_k[c] >= 0) return fail(UF_ETABLE, "%s", bad_msg[c].c_str());
+    t->id = next_id++;
+    // column starts, then each thread's first slot in every column (its
+    // samples go behind the earlier threads'), over feature ranges in parallel
     t->col_ptr.assign(n_features + 1, 0);
-    for (int64_t f = 0; f < n_features; f++) {
-      int64_t at = t->col_ptr[f];
-      for (int c = 0; c < T; c++) {
-        const int64_t x = cnt[c][f];
-        cnt[c][f] = at;  // this thread's first slot in column f
-        at += x;
+    const int TF = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n_features / 4096));
+    parallel_for(TF, [&](int c) {
+      const int64_t f0 = n_features * c / TF, f1 = n_features * (c + 1) / TF;
+      for (int64_t f = f0; f < f1; f++) {
+        int64_t x = 0;
+        for (int u = 0; u < T; u++) x += cnt[u][f];
+        t->col_ptr[f + 1] = x;
       }
-      t->col_ptr[f + 1] = at;
-    }
+    });
+    for (int64_t f = 0; f < n_features; f++) t->col_ptr[f + 1] += t->col_ptr[f];
+    parallel_for(TF, [&](int c) {
+      const int64_t f0 = n_features * c / TF, f1 = n_features * (c + 1) / TF;
+      for (int64_t f = f0; f < f1; f++) {
+        int64_t at = t->col_ptr[f];
+        for (int u = 0; u < T; u++) {
+          const int64_t x = cnt[u][f];
+          cnt[u][f] = at;
+          at += x;
+        }
+      }
+    });
     t->col_row.resize(std::max<int64_t>(nnz, 1));  // every entry written below (nnz >= 1)
     t->col_val.resize(std::max<int64_t>(nnz, 1));
     parallel_for(T, [&](int c) {

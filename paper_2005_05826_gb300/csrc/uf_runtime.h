@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -46,14 +47,16 @@ void ck(cudaError_t e, const char *what);
 // Host threads for table preparation: the cores this process may run on, at most 16.
 int host_threads();
 
-// Runs body(0 .. n-1) on n threads (the calling thread takes the last) and joins.
+// Runs body(0 .. n-1) on the process's host worker pool (host_threads() - 1
+// persistent threads, started on first use) and the calling thread, and
+// returns when every index has run.  Indices are handed out one at a time, so
+// calls from several threads (or from inside a body) share the pool without
+// waiting on each other's indices.  In a forked child the pool is not
+// inherited: the calling thread runs every index.
+void run_parallel(int n, const std::function<void(int)> &body);
 template <typename F>
 void parallel_for(int n, F body) {
-  std::vector<std::thread> th;
-  th.reserve(n > 1 ? n - 1 : 0);
-  for (int c = 0; c + 1 < n; c++) th.emplace_back(body, c);
-  body(n - 1);
-  for (auto &x : th) x.join();
+  run_parallel(n, std::function<void(int)>(std::move(body)));
 }
 
 // Allocator whose value-less construct leaves elements uninitialised: for

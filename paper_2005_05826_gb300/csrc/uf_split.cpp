@@ -54,39 +54,60 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
     else dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
     const double visit_rate = fp32 ? 2e12 : (acc == ACC_GEN ? 3e10 : 1e12);
     const double job_cost = 5e-10;
+    const double pair_cost = 1.0 / visit_rate + n_acc / atom_rate, entry_cost = 4.0 / atom_rate;
     // a dense row also costs its count row and embedding (or planes) in HBM
     const double dense_t = cells / dense_rate + cols * 36.0 / 6e12;
-    for (int64_t v = 0; v < nb; v++) {
-      const int32_t lo = tree->tip_lo[v], hi = tree->tip_hi[v];
-      if (lo < 0) continue;
-      if (tree->length[v] == 0.0) {
-        // a zero-length branch adds exactly 0 to every accumulator: skipped
-        // (its count row is still built if a dense parent needs it)
-        is_sparse[v] = 1;
-        R.n_sparse++;
-        continue;
+    // node ranges in parallel; each class list is the ranges' lists in order,
+    // so the result equals a sequential pass (pair counts are integers < 2^53:
+    // their double sums are exact in any order)
+    struct Part {
+      std::vector<int32_t> cls[5];
+      int64_t n_sparse = 0;
+      double pairs = 0.0;
+    };
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), nb / 16384));
+    std::vector<Part> part(T);
+    parallel_for(T, [&](int c) {
+      Part &pt = part[c];
+      const int64_t v0 = nb * c / T, v1 = nb * (c + 1) / T;
+      for (int64_t v = v0; v < v1; v++) {
+        const int32_t lo = tree->tip_lo[v], hi = tree->tip_hi[v];
+        if (lo < 0) continue;
+        if (tree->length[v] == 0.0) {
+          // a zero-length branch adds exactly 0 to every accumulator: skipped
+          // (its count row is still built if a dense parent needs it)
+          is_sparse[v] = 1;
+          pt.n_sparse++;
+          continue;
+        }
+        double cost = 0.0, pairs = 0.0;
+        int64_t mx = 0;
+        for (size_t t = 0; t < nt; t++) {
+          const auto &cp = J.tabs[t].table->col_ptr;
+          const int64_t ub = cp[hi] - cp[lo];
+          mx = std::max(mx, ub);
+          if (ub == 0) continue;
+          const double pr = (double)ub * (double)(ub - 1) / 2.0;
+          pairs += pr;
+          cost += job_cost + pr * pair_cost + (double)ub * entry_cost;
+          if (regions) cost += n_regions * (job_cost + (double)ub * 4e-11);  // one visit per region
+        }
+        if (mx > max_entries) continue;
+        if (mode == 2 || cost < dense_t) {
+          is_sparse[v] = 1;
+          int k = 0;
+          while (classes[k] < mx) k++;
+          pt.cls[k].push_back((int32_t)v);
+          pt.n_sparse++;
+          pt.pairs += pairs;
+        }
       }
-      double cost = 0.0, pairs = 0.0;
-      int64_t mx = 0;
-      for (size_t t = 0; t < nt; t++) {
-        const auto &cp = J.tabs[t].table->col_ptr;
-        const int64_t ub = cp[hi] - cp[lo];
-        mx = std::max(mx, ub);
-        if (ub == 0) continue;
-        const double pr = (double)ub * (double)(ub - 1) / 2.0;
-        pairs += pr;
-        cost += job_cost + pr * (1.0 / visit_rate + n_acc / atom_rate) + (double)ub * 4.0 / atom_rate;
-        if (regions) cost += n_regions * (job_cost + (double)ub * 4e-11);  // one visit per region
-      }
-      if (mx > max_entries) continue;
-      if (mode == 2 || cost < dense_t) {
-        is_sparse[v] = 1;
-        int c = 0;
-        while (classes[c] < mx) c++;
-        R.sparse[c].push_back((int32_t)v);
-        R.n_sparse++;
-        R.pairs += pairs;
-      }
+    });
+    for (int k = 0; k < 5; k++)
+      for (const Part &pt : part) R.sparse[k].insert(R.sparse[k].end(), pt.cls[k].begin(), pt.cls[k].end());
+    for (const Part &pt : part) {
+      R.n_sparse += pt.n_sparse;
+      R.pairs += pt.pairs;
     }
   }
   const int64_t root = tree->n_nodes - 1;
@@ -94,30 +115,39 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
     const int64_t p = tree->parent[v];
     return p != root && !is_sparse[p];
   };
+  // per list position: bit 0 = built from CSC columns (tips, and sparse
+  // branches under a dense parent), bit 1 = a dense internal node; flagged in
+  // parallel, then gathered in list order
+  std::vector<uint8_t> flag(P->lists.size(), 0);
+  {
+    const int64_t np = (int64_t)P->lists.size();
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), np / 16384));
+    parallel_for(T, [&](int c) {
+      const int64_t p0 = np * c / T, p1 = np * (c + 1) / T;
+      size_t b = 0;
+      for (int64_t q = p0; q < p1; q++) {
+        // block of position q: blocks cover consecutive ranges of the lists
+        while (b + 1 < P->launches.size() && q >= P->launches[b + 1][0].first) b++;
+        const auto &l0 = P->launches[b][0];
+        const int32_t v = P->lists[q];
+        const bool tip = q < l0.first + l0.second;
+        flag[q] = (uint8_t)((is_sparse[v] ? parent_dense(v) : tip) | ((!tip && !is_sparse[v]) << 1));
+      }
+    });
+  }
   for (size_t b = 0; b < P->b0.size(); b++) {
     const auto &ls = P->launches[b];
     std::vector<std::pair<int64_t, int>> lb;
-    std::vector<int32_t> level;
-    // nodes built from CSC columns
-    level.clear();
-    for (size_t l = 0; l < ls.size(); l++)
-      for (int i = 0; i < ls[l].second; i++) {
-        const int32_t v = P->lists[ls[l].first + i];
-        const bool tip = l == 0;
-        if (is_sparse[v] ? parent_dense(v) : tip) level.push_back(v);
-      }
-    lb.emplace_back((int64_t)R.cnt_lists.size(), (int)level.size());
-    R.cnt_lists.insert(R.cnt_lists.end(), level.begin(), level.end());
-    // dense internal nodes by level
+    const int64_t q0 = ls[0].first, q1 = ls.back().first + ls.back().second;
+    const int64_t at0 = (int64_t)R.cnt_lists.size();
+    for (int64_t q = q0; q < q1; q++)
+      if (flag[q] & 1) R.cnt_lists.push_back(P->lists[q]);
+    lb.emplace_back(at0, (int)((int64_t)R.cnt_lists.size() - at0));
     for (size_t l = 1; l < ls.size(); l++) {
-      level.clear();
-      for (int i = 0; i < ls[l].second; i++) {
-        const int32_t v = P->lists[ls[l].first + i];
-        if (!is_sparse[v]) level.push_back(v);
-      }
-      if (level.empty()) continue;
-      lb.emplace_back((int64_t)R.cnt_lists.size(), (int)level.size());
-      R.cnt_lists.insert(R.cnt_lists.end(), level.begin(), level.end());
+      const int64_t at = (int64_t)R.cnt_lists.size();
+      for (int64_t q = ls[l].first; q < ls[l].first + ls[l].second; q++)
+        if (flag[q] & 2) R.cnt_lists.push_back(P->lists[q]);
+      if ((int64_t)R.cnt_lists.size() > at) lb.emplace_back(at, (int)((int64_t)R.cnt_lists.size() - at));
     }
     R.cnt_launch.push_back(std::move(lb));
   }

@@ -48,6 +48,29 @@ def _code(fn):
     return e.value.status
 
 
+def test_table_validation_many_threads():
+    # a table large enough for one validating pass per host thread: the
+    # reported error is still the first failing sample in sample order
+    tree_s = yule_tree(4000, seed=41)
+    n, per = 40_000, 60
+    rng = np.random.default_rng(42)
+    ix = np.sort(np.stack([rng.choice(tree_s.n_tips, per, replace=False) for _ in range(n)]), axis=1)
+    ip = np.arange(n + 1, dtype=np.int64) * per
+    d = np.ones(n * per)
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    uf.Table(ip, ix.ravel().astype(np.int32), d, tree)  # valid
+    bad_ix = ix.copy()
+    bad_ix[35_000, [3, 4]] = bad_ix[35_000, [4, 3]]       # unsorted, late sample
+    bad_d = d.copy()
+    bad_d[12_345 * per + 7] = 0.0                          # zero count, earlier sample
+    with pytest.raises(uf.UFError) as e:
+        uf.Table(ip, bad_ix.ravel().astype(np.int32), bad_d, tree)
+    assert e.value.status == "UF_ETABLE" and "sample 12345:" in str(e.value)
+    with pytest.raises(uf.UFError) as e:
+        uf.Table(ip, bad_ix.ravel().astype(np.int32), d, tree)
+    assert "sample 35000: feature indices not strictly increasing" in str(e.value)
+
+
 def test_tree_validation():
     ok = uf.Tree(np.array([2, 2, -1]), np.array([1.0, 2.0, 0.0]))
     assert ok.n_tips == 2

@@ -7,6 +7,8 @@
 
 #include "uf_runtime.h"
 
+#include <deque>
+
 namespace ufg {
 namespace rt {
 
@@ -244,6 +246,40 @@ struct PriorityScope {
   ~PriorityScope() { set_launch_priority(old); }
 };
 
+// Executable graphs still running: destroying one right after its launch
+// makes the host wait for it when the graph has parallel branches, so each
+// is kept with an event recorded behind its launch and destroyed by a later
+// call once that event has completed (or, past 32 in flight, after a wait on
+// the oldest).
+struct LiveGraphs {
+  std::mutex mu;
+  std::deque<std::pair<cudaGraphExec_t, cudaEvent_t>> q;
+};
+LiveGraphs g_live_graphs;
+
+void retire_graph(cudaGraphExec_t e, cudaStream_t st) {
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(ev, st) != cudaSuccess) {
+    if (ev) cudaEventDestroy(ev);
+    cudaGetLastError();
+    cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(e);
+    return;
+  }
+  std::lock_guard<std::mutex> g(g_live_graphs.mu);
+  auto &q = g_live_graphs.q;
+  q.emplace_back(e, ev);
+  while (!q.empty()) {
+    const bool over = q.size() > 32;
+    if (over) cudaEventSynchronize(q.front().second);
+    else if (cudaEventQuery(q.front().second) != cudaSuccess) break;
+    cudaGraphExecDestroy(q.front().first);
+    cudaEventDestroy(q.front().second);
+    q.pop_front();
+  }
+  cudaGetLastError();  // cudaErrorNotReady from the query is not an error here
+}
+
 // Records the branch-block launch sequence of a call into a CUDA graph (on a
 // private stream) and launches that graph on the caller's stream; when off,
 // launches go to the caller's stream directly.
@@ -271,7 +307,10 @@ struct Capture {
     cudaError_t err =
         cudaGraphInstantiate(&e, g, node_priority ? (unsigned long long)cudaGraphInstantiateFlagUseNodePriority : 0ull);
     if (err == cudaSuccess) err = cudaGraphLaunch(e, user);
-    if (e) cudaGraphExecDestroy(e);  // freed once the launch completes
+    if (e) {
+      if (err == cudaSuccess) retire_graph(e, user);
+      else cudaGraphExecDestroy(e);
+    }
     cudaGraphDestroy(g);
     ck(err, "graph launch");
   }

@@ -492,8 +492,12 @@ uf_status uf_tree_create(int64_t n_nodes, const int64_t *parent, const double *l
       t->dist[v] = t->length[v] + t->dist[parent[v]];
       t->total_length += t->length[v];
     }
+    t->tip_dist.resize(std::max<int64_t>(tips, 1));
     for (int64_t v = 0; v < n_nodes; v++)
-      if (nchild[v] == 0) t->max_tip_dist = std::max(t->max_tip_dist, t->dist[v]);
+      if (nchild[v] == 0) {
+        t->max_tip_dist = std::max(t->max_tip_dist, t->dist[v]);
+        t->tip_dist[t->tip_of_node[v]] = t->dist[v];
+      }
     *out = t.release();
     return UF_OK;
   } catch (const std::bad_alloc &) {
@@ -545,12 +549,16 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
     std::vector<int64_t> bad_k(T, -1);
     std::vector<std::string> bad_msg(T);
     std::vector<std::vector<int64_t>> cnt(T);
+    // and the presence bound for this tree: max over samples of the summed
+    // root distances of their tips (accum_bound)
+    std::vector<double> pres(T, 0.0);
+    const double *tip_dist = tree->tip_dist.data();
     parallel_for(T, [&](int c) {
       cnt[c].assign(n_features, 0);
       int64_t *cc = cnt[c].data();
       char buf[160];
       for (int64_t k = k_lo[c]; k < k_lo[c + 1]; k++) {
-        double s = 0.0;
+        double s = 0.0, w = 0.0;
         for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
           if (indices[q] < 0 || indices[q] >= n_features)
             snprintf(buf, sizeof buf, "sample %lld: feature index %d out of range", (long long)k, indices[q]);
@@ -560,6 +568,7 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
             snprintf(buf, sizeof buf, "sample %lld: count %g must be finite and > 0", (long long)k, data[q]);
           else {
             s += data[q];
+            w += tip_dist[indices[q]];
             cc[indices[q]]++;
             continue;
           }
@@ -569,11 +578,13 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
         }
         t->total[k] = s;
         t->inv_total_f[k] = (float)(1.0 / s);
+        pres[c] = std::max(pres[c], w);
       }
     });
     for (int c = 0; c < T; c++)
       if (bad_k[c] >= 0) return fail(UF_ETABLE, "%s", bad_msg[c].c_str());
     t->id = next_id++;
+    t->presence_bound[tree->id] = *std::max_element(pres.begin(), pres.end());
     // column starts, then each thread's first slot in every column (its
     // samples go behind the earlier threads'), over feature ranges in parallel
     t->col_ptr.assign(n_features + 1, 0);

@@ -139,6 +139,7 @@ struct uf_tree {
   std::map<ufg::rt::SplitKey, std::shared_ptr<const ufg::rt::RowSplit>> splits;  // dense / sparse branch splits
   // root distance of every node (root: 0), max over tips, total branch length
   std::vector<double> dist;
+  std::vector<double> tip_dist;  // dist of tip number f
   double max_tip_dist = 0.0, total_length = 0.0;
   ~uf_tree() {
     int cur = 0;

@@ -7,6 +7,7 @@
 // k, written over a padded width so that the stripe kernel can read the
 // partner column k + d without a modulo.
 #include "uf_device.cuh"
+#include "uf_embed.h"
 
 namespace ufg {
 
@@ -76,6 +77,74 @@ __global__ void k_node_counts(const int32_t *__restrict__ nodes,
   counts[(int64_t)slot_of_node[v] * ld + k] = s;
 }
 
+// The same with 16 bytes per thread (2 counts or 16 flags) for rows whose
+// stride is a multiple of 16 bytes: each element is still the sum (OR) of
+// the children's elements in index order, so the rows are bitwise those of
+// k_node_counts.  Columns [0, n_used) are written; the ragged end of a row
+// goes element by element.  grid.x = nodes, grid.y = column chunks.
+template <typename C>
+__global__ void k_node_counts_v16(const int32_t *__restrict__ nodes,
+                                  const int32_t *__restrict__ child_ptr,
+                                  const int32_t *__restrict__ child_idx,
+                                  const int32_t *__restrict__ slot_of_node,
+                                  C *__restrict__ counts, int64_t ld, int64_t n_used) {
+  constexpr int V = 16 / (int)sizeof(C);
+  const int v = nodes[blockIdx.x];
+  const int64_t e0 = ((int64_t)blockIdx.y * blockDim.x + threadIdx.x) * V;
+  if (e0 >= n_used) return;
+  const int c0 = child_ptr[v], c1 = child_ptr[v + 1];
+  C *dst = counts + (int64_t)slot_of_node[v] * ld + e0;
+  if (e0 + V <= n_used) {
+    if constexpr (sizeof(C) == 1) {
+      uint4 s = make_uint4(0u, 0u, 0u, 0u);
+      for (int c = c0; c < c1; c++) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(counts + (int64_t)slot_of_node[child_idx[c]] * ld + e0);
+        s.x |= x.x;
+        s.y |= x.y;
+        s.z |= x.z;
+        s.w |= x.w;
+      }
+      *reinterpret_cast<uint4 *>(dst) = s;
+    } else {
+      double2 s = make_double2(0.0, 0.0);
+      for (int c = c0; c < c1; c++) {
+        const double2 x =
+            *reinterpret_cast<const double2 *>(counts + (int64_t)slot_of_node[child_idx[c]] * ld + e0);
+        s.x += x.x;
+        s.y += x.y;
+      }
+      *reinterpret_cast<double2 *>(dst) = s;
+    }
+    return;
+  }
+  for (int64_t e = e0; e < n_used; e++) {
+    C s = C(0);
+    for (int c = c0; c < c1; c++) {
+      if constexpr (sizeof(C) == 1) s |= counts[(int64_t)slot_of_node[child_idx[c]] * ld + e];
+      else s += counts[(int64_t)slot_of_node[child_idx[c]] * ld + e];
+    }
+    counts[(int64_t)slot_of_node[v] * ld + e] = s;
+  }
+}
+
+// Node rows of one level: the 16-byte kernel when the stride and base allow
+// it, else one element per thread.
+template <typename C>
+cudaError_t launch_node_rows(const int32_t *nodes, int n_list, const int32_t *child_ptr, const int32_t *child_idx,
+                             const int32_t *slot_of_node, C *counts, int64_t ld, int64_t n_used,
+                             cudaStream_t st) {
+  if (n_list <= 0 || n_used <= 0) return cudaSuccess;
+  if ((ld * (int64_t)sizeof(C)) % 16 == 0 && reinterpret_cast<uintptr_t>(counts) % 16 == 0) {
+    constexpr int V = 16 / (int)sizeof(C);
+    const int64_t chunks = (n_used + V - 1) / V;
+    const int bt = chunks >= 256 ? 256 : 128;
+    return launch_k(k_node_counts_v16<C>, dim3(n_list, (unsigned)((chunks + bt - 1) / bt)), dim3(bt), 0, st,
+                    nodes, child_ptr, child_idx, slot_of_node, counts, ld, n_used);
+  }
+  return launch_k(k_node_counts<C>, dim3(n_list, (unsigned)((ld + 255) / 256)), dim3(256), 0, st, nodes,
+                  child_ptr, child_idx, slot_of_node, counts, ld);
+}
+
 // Table whose row segment holds column j (segments are contiguous, in order).
 __device__ __forceinline__ int segment_of(const TabDesc *tabs, int n_tabs, int64_t j) {
   int lo = 0, hi = n_tabs - 1;
@@ -138,18 +207,16 @@ cudaError_t launch_slice_presence(const int32_t *nodes, int n_list, const int32_
 
 cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
                                const int32_t *child_idx, const int32_t *slot_of_node,
-                               double *counts, int64_t ld, cudaStream_t st) {
-  if (n_list <= 0) return cudaSuccess;
-  dim3 grid(n_list, (unsigned)((ld + 255) / 256));
-  return launch_k(k_node_counts<double>, grid, dim3(256), 0, st, nodes, child_ptr, child_idx, slot_of_node, counts, ld);
+                               double *counts, int64_t ld, cudaStream_t st, int64_t n_used) {
+  return launch_node_rows<double>(nodes, n_list, child_ptr, child_idx, slot_of_node, counts, ld,
+                                  n_used < 0 ? ld : n_used, st);
 }
 
 cudaError_t launch_node_presence(const int32_t *nodes, int n_list, const int32_t *child_ptr,
                                  const int32_t *child_idx, const int32_t *slot_of_node,
-                                 uint8_t *flags, int64_t ld, cudaStream_t st) {
-  if (n_list <= 0) return cudaSuccess;
-  dim3 grid(n_list, (unsigned)((ld + 255) / 256));
-  return launch_k(k_node_counts<uint8_t>, grid, dim3(256), 0, st, nodes, child_ptr, child_idx, slot_of_node, flags, ld);
+                                 uint8_t *flags, int64_t ld, cudaStream_t st, int64_t n_used) {
+  return launch_node_rows<uint8_t>(nodes, n_list, child_ptr, child_idx, slot_of_node, flags, ld,
+                                   n_used < 0 ? ld : n_used, st);
 }
 
 cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,

@@ -17,6 +17,7 @@
 // diagonal is D + R, an abs-form cell gains R_k + R_j, and the generalized
 // den gains R_k + R_j.
 #include "uf_internal.h"
+#include "uf_finalize.h"
 
 namespace ufg {
 

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "uf_internal.h"
+#include "uf_gram.h"
 
 namespace ufg {
 

@@ -52,35 +52,6 @@ struct TabDesc {
   int64_t m_off;      // first cell of its stripe accumulator
 };
 
-// ---- embed (uf_embed.cu) ----
-// Count rows live in slots of `ld` doubles (the combined sample axis).
-cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_t *slot_of_node,
-                              const int32_t *tip_of_node, const int64_t *col_ptr,
-                              const int32_t *col_row, const double *col_val, double *counts,
-                              int64_t ld, int n, cudaStream_t st);
-// Count rows of listed nodes straight from the CSC columns of their tips
-// (tip numbers [tip_lo[v], tip_hi[v]), in order).
-cudaError_t launch_slice_counts(const int32_t *nodes, int n_list, const int32_t *tip_lo, const int32_t *tip_hi,
-                                const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
-                                const double *col_val, double *counts, int64_t ld, int n, cudaStream_t st);
-// Presence flags (uint8_t, 1 where the count is nonzero) instead of counts.
-cudaError_t launch_slice_presence(const int32_t *nodes, int n_list, const int32_t *tip_lo, const int32_t *tip_hi,
-                                  const int32_t *slot_of_node, const int64_t *col_ptr, const int32_t *col_row,
-                                  uint8_t *flags, int64_t ld, int n, cudaStream_t st);
-cudaError_t launch_node_presence(const int32_t *nodes, int n_list, const int32_t *child_ptr,
-                                 const int32_t *child_idx, const int32_t *slot_of_node,
-                                 uint8_t *flags, int64_t ld, cudaStream_t st);
-cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *child_ptr,
-                               const int32_t *child_idx, const int32_t *slot_of_node,
-                               double *counts, int64_t ld, cudaStream_t st);
-// Embedding rows of branches nodes[0 .. rows) (b0 .. b0 + rows - 1 when
-// nodes is null) for every table segment.
-cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
-                            const int32_t *slot_of_node, const double *counts, int64_t ld,
-                            const double *length, const double *total, const float *inv_total_f,
-                            void *X, int64_t pitch, const TabDesc *tabs, int n_tabs, cudaStream_t st,
-                            const int32_t *nodes = nullptr);
-
 // ---- stripe accumulate (uf_stripe.cu) ----
 // In the FP32 min kernel, stripes s with s mod 8 in {1, 3, 5, 7} hold
 // A = sum |x_k - x_j| instead of M = sum min(x_k, x_j) (see uf_stripe.cu).
@@ -114,65 +85,6 @@ cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStrea
 // for every chunk size the StripeArgs may carry)
 size_t diag_scratch_bytes(bool fp32, int rows, int n_cols);
 cudaError_t launch_diag(bool fp32, const StripeArgs &a, void *scratch, cudaStream_t st);
-
-// ---- finalize (uf_finalize.cu) ----
-struct FinalArgs {
-  int method;           // uf_method
-  int n;
-  int64_t s0, s1;       // stripes [s0, s1)
-  int full;             // 1: condensed output, 0: stripe-major
-  int mixed_forms;      // 1: the FP32 min kernel's abs-form stripes are present
-  const unsigned long long *M, *M2, *Dg;  // fixed-point accumulators of this table
-  double inv_scale;     // 2^-F
-  void *out;
-  int out_fp32;
-  // sparse-row diagonal of this table (uf_sparse.cu), or null: R[k] = sum of
-  // the sparse rows' x[k] (ACC_MIN) or l u[k]^alpha (ACC_GEN)
-  const unsigned long long *Dsp;
-};
-cudaError_t launch_finalize(const FinalArgs &a, cudaStream_t st);
-
-// ---- unweighted on tensor cores (uf_gram.cu) ----
-// One table of a batch: its samples occupy rows [row_base, row_base + n_pad)
-// of every presence plane; its gram matrix starts at gt_off.
-struct GramTab {
-  int n, n_pad;         // samples, padded to the 256-sample tile
-  int row_base;         // first plane row
-  int off;              // first column on the combined sample axis
-  int64_t gt_off;       // first cell of its gram matrix (n_pad x n_pad)
-};
-struct GramArgs {
-  int k_len;            // branches of this block, rounded up to 64
-  int kc;               // branches per work unit (multiple of 64)
-  int n_tiles;          // tiles of all tables
-  int n_units;          // set by launch_gram
-  int npad_tot;         // plane rows (sum of n_pad)
-  const int32_t *tile_tab, *tile_bi, *tile_bj;
-  const GramTab *tabs;
-  unsigned long long *Gt;  // fixed point; cell (i, j), i <= j, of table t at gt_off + j * n_pad + i
-  double scale;         // 2^F
-  int *err;             // set to 1 when a bounded wait gave up
-};
-struct GramFinalArgs {
-  int n, n_pad;
-  int64_t s0, s1;
-  int full;
-  const unsigned long long *Gt;  // this table's gram matrix
-  void *out;
-  int out_fp32;
-};
-int gram_pad(int n);                      // n rounded up to the tile
-int64_t gram_kpad(int rows);              // branches rounded up to the stage
-// upper-triangle tiles of one table: (bi, bj) pairs appended to bi / bj
-void gram_tiles(int n_pad, std::vector<int32_t> *bi, std::vector<int32_t> *bj);
-// planes of branches nodes[0 .. rows) (b0 .. b0 + rows - 1 when nodes is null)
-// from their presence flags
-cudaError_t launch_gram_prep(int64_t b0, int rows, const int32_t *slot_of_node, const uint8_t *flags,
-                             int64_t ld, const double *length, const GramTab *tabs, int n_tabs,
-                             int npad_tot, int64_t K_pad, void *Pl, cudaStream_t st,
-                             const int32_t *nodes = nullptr);
-cudaError_t launch_gram(const GramArgs &a, void *Pl, int64_t K_pad, cudaStream_t st);
-cudaError_t launch_finalize_gram(const GramFinalArgs &a, cudaStream_t st);
 
 }  // namespace ufg
 

@@ -38,6 +38,8 @@
 
 #include "../../include/unifrac_gb300.h"
 #include "uf_internal.h"
+#include "uf_embed.h"
+#include "uf_finalize.h"
 
 namespace {
 

@@ -461,8 +461,8 @@ void fill_reports(uf_tree *tree, const BatchJob &J, const Outputs &o, double ms[
 // Count rows of block b that the split needs: CSC-built nodes of every
 // table, then the dense internal levels over the combined axis.
 void enqueue_split_counts(const Inputs &in, const BatchJob &J, const std::vector<int> &off, const RowSplit &split,
-                          size_t b, const int32_t *d_cnt, double *counts, int64_t ld, cudaStream_t st,
-                          int64_t *kernels) {
+                          size_t b, const int32_t *d_cnt, double *counts, int64_t ld, int64_t n_cols,
+                          cudaStream_t st, int64_t *kernels) {
   const auto &lb = split.cnt_launch[b];
   for (size_t t = 0; t < J.tabs.size(); t++) {
     ck(launch_slice_counts(d_cnt + lb[0].first, lb[0].second, in.td->tip_lo, in.td->tip_hi, in.pd->slot_of_node,
@@ -473,7 +473,7 @@ void enqueue_split_counts(const Inputs &in, const BatchJob &J, const std::vector
   }
   for (size_t l = 1; l < lb.size(); l++) {
     ck(launch_node_counts(d_cnt + lb[l].first, lb[l].second, in.td->child_ptr, in.td->child_idx,
-                          in.pd->slot_of_node, counts, ld, st),
+                          in.pd->slot_of_node, counts, ld, st, n_cols),
        "node counts");
     (*kernels)++;
   }
@@ -483,7 +483,7 @@ void enqueue_split_counts(const Inputs &in, const BatchJob &J, const std::vector
 // nothing else): one byte per sample instead of an FP64 count.
 void enqueue_split_presence(const Inputs &in, const BatchJob &J, const std::vector<int> &off,
                             const RowSplit &split, size_t b, const int32_t *d_cnt, uint8_t *flags, int64_t ld,
-                            cudaStream_t st, int64_t *kernels) {
+                            int64_t n_cols, cudaStream_t st, int64_t *kernels) {
   const auto &lb = split.cnt_launch[b];
   for (size_t t = 0; t < J.tabs.size(); t++) {
     ck(launch_slice_presence(d_cnt + lb[0].first, lb[0].second, in.td->tip_lo, in.td->tip_hi, in.pd->slot_of_node,
@@ -494,7 +494,7 @@ void enqueue_split_presence(const Inputs &in, const BatchJob &J, const std::vect
   }
   for (size_t l = 1; l < lb.size(); l++) {
     ck(launch_node_presence(d_cnt + lb[l].first, lb[l].second, in.td->child_ptr, in.td->child_idx,
-                            in.pd->slot_of_node, flags, ld, st),
+                            in.pd->slot_of_node, flags, ld, st, n_cols),
        "node presence");
     (*kernels)++;
   }
@@ -539,7 +539,9 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   std::vector<int32_t> tl(tile_tab);
   tl.insert(tl.end(), tile_bi.begin(), tile_bi.end());
   tl.insert(tl.end(), tile_bj.begin(), tile_bj.end());
-  DevBuf flags((size_t)in.P->n_slots * n_cols, st, "alloc presence rows");
+  // presence rows: stride rounded up to 16 bytes for the 16-byte level kernel
+  const int64_t ld = round_up(n_cols, 16);
+  DevBuf flags((size_t)in.P->n_slots * ld, st, "alloc presence rows");
   DevBuf Pl((size_t)4 * npad_tot * K_pad * 2, st, "alloc presence planes");
   DevBuf Gt((size_t)gt_cells * 8, st, "alloc gram");
   DevBuf err(sizeof(int), st, "alloc error flag");
@@ -613,9 +615,9 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
     const int64_t b0 = in.P->b0[b];
     const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
     timer.begin(0);
-    enqueue_split_presence(in, J, off, split, b, d_cnt, flags.as<uint8_t>(), n_cols, ls, &kernels);
+    enqueue_split_presence(in, J, off, split, b, d_cnt, flags.as<uint8_t>(), ld, n_cols, ls, &kernels);
     if (nd > 0) {
-      ck(launch_gram_prep(b0, (int)nd, in.pd->slot_of_node, flags.as<uint8_t>(), n_cols, in.td->length, d_tabs,
+      ck(launch_gram_prep(b0, (int)nd, in.pd->slot_of_node, flags.as<uint8_t>(), ld, in.td->length, d_tabs,
                           (int)nt, npad_tot, K_pad, Pl.p, ls, d_dense + d0),
          "presence planes");
       kernels++;
@@ -731,7 +733,9 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const int64_t xrows = std::max<int64_t>(split.max_dense, 1);
   int64_t kernels = 0, acc_launches = 0;
   PhaseTimer timer(g_kernel_timing.load() != 0, st);
-  DevBuf counts((size_t)in.P->n_slots * n_cols * 8, st, "alloc counts");
+  // count rows: stride rounded up to 16 elements for the 16-byte level kernel
+  const int64_t ld = round_up(n_cols, 16);
+  DevBuf counts((size_t)in.P->n_slots * ld * 8, st, "alloc counts");
   DevBuf X((size_t)xrows * pitch * es, st, "alloc embeddings");
   DevBuf M((size_t)cells * 8, st, "alloc stripes");
   DevBuf M2, Dg, Dsp, diag_tmp, counter(sizeof(int), st, "alloc counter");
@@ -889,9 +893,9 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     const int64_t b0 = in.P->b0[b];
     const int64_t d0 = split.dense_ptr[b], nd = split.dense_ptr[b + 1] - d0;
     timer.begin(0);
-    enqueue_split_counts(in, J, off, split, b, d_cnt, counts.as<double>(), n_cols, ls, &kernels);
+    enqueue_split_counts(in, J, off, split, b, d_cnt, counts.as<double>(), ld, n_cols, ls, &kernels);
     if (nd > 0) {
-      ck(launch_emb_rows(kind, fp32, b0, (int)nd, in.pd->slot_of_node, counts.as<double>(), n_cols,
+      ck(launch_emb_rows(kind, fp32, b0, (int)nd, in.pd->slot_of_node, counts.as<double>(), ld,
                          in.td->length, total.as<double>(), inv_total.as<float>(), X.p, pitch,
                          d_tabs, (int)nt, ls, d_dense + d0),
          "embedding rows");

@@ -26,6 +26,9 @@
 #include "../../include/unifrac_gb300.h"
 #include "uf_internal.h"
 #include "uf_sparse.h"
+#include "uf_embed.h"
+#include "uf_finalize.h"
+#include "uf_gram.h"
 
 namespace ufg {
 namespace rt {

@@ -221,7 +221,9 @@ int64_t uf_table_samples(const uf_table *table);
  * Working memory comes from the CUDA stream-ordered allocator of the current
  * device and is returned before the work completes on the stream.
  * Errors: UF_EINVAL, UF_ERANGE, UF_ETABLE (table of another tree),
- *   UF_ENOMEM, UF_ECUDA.
+ *   UF_ENOMEM, UF_ECUDA; UF_ETIMEOUT when a bounded wait of the tensor-core
+ *   kernel (unweighted, mixed) ran out.  An asynchronous call does not wait
+ *   to learn that: every value it writes is then NaN instead.
  */
 uf_status uf_compute(const uf_tree *tree, const uf_table *table, uf_method method, double alpha,
                      uf_precision precision, int64_t stripe_start, int64_t stripe_stop, void *out,

@@ -363,6 +363,7 @@ __global__ void k_gram_prep(int64_t b0, const int32_t *__restrict__ nodes, int r
 __global__ void k_finalize_gram(const GramFinalArgs a) {
   const int64_t rows = a.s1 - a.s0;
   const int64_t total = rows * a.n;
+  const bool aborted = a.err && *a.err != 0;  // a bounded wait gave up: no distance is valid
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = c / a.n;
@@ -377,7 +378,7 @@ __global__ void k_finalize_gram(const GramFinalArgs a) {
     long long num = w - 2 * g;
     const long long den = w - g;
     if (num < 0) num = 0;
-    const double val = den > 0 ? (double)num / (double)den : 0.0;
+    const double val = aborted ? __longlong_as_double(0x7ff8000000000000ll) : den > 0 ? (double)num / (double)den : 0.0;
     const int64_t idx = a.full ? (int64_t)a.n * lo - lo * (lo + 1) / 2 + (hi - lo - 1) : c;
     if (a.out_fp32) ((float *)a.out)[idx] = (float)val;
     else ((double *)a.out)[idx] = val;

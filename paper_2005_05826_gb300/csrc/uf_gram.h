@@ -32,6 +32,7 @@ struct GramFinalArgs {
   const unsigned long long *Gt;  // this table's gram matrix
   void *out;
   int out_fp32;
+  const int *err;                // the gram kernel's abort flag: when set, every output is NaN
 };
 int gram_pad(int n);                      // n rounded up to the tile
 int64_t gram_kpad(int rows);              // branches rounded up to the stage

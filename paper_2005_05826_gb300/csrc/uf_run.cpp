@@ -655,13 +655,18 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
     fa.Gt = Gt.as<unsigned long long>() + gt[t].gt_off;
     fa.out = o.dev[t];
     fa.out_fp32 = J.out_fp32;
+    fa.err = err.as<int>();
     ck(launch_finalize_gram(fa, ls), "finalize");
     kernels++;
   }
   timer.end();
   cap.launch();
+  // a synchronous call reads the abort flag and returns UF_ETIMEOUT; an
+  // asynchronous one (device outputs on a stream) is not held back for it:
+  // the finalize has already written NaN to every output when it is set
+  const bool sync = !J.out_is_device || st == nullptr || timer.on;
   int h_err = 0;
-  ck(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
+  if (sync) ck(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
   if (!J.out_is_device)
     for (size_t t = 0; t < nt; t++)
       ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
@@ -670,8 +675,9 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   Gt = DevBuf();
   meta.dev = DevBuf();
   o.tmp.clear();
-  ck(cudaStreamSynchronize(st), "synchronize");  // the error flag is read here
   err = DevBuf();
+  if (sync) ck(cudaStreamSynchronize(st), "synchronize");
+  else ck(cudaGetLastError(), "enqueue");
   if (h_err) return fail(UF_ETIMEOUT, "tensor-core kernel: a bounded wait gave up");
   double ms[5] = {0, 0, 0, 0, 0};
   timer.collect(ms);

@@ -144,6 +144,11 @@ typedef struct {
  *                    dense stripe kernel or tensor-core gram (it fills the SM
  *                    slots those leave); 0: in sequence with them.  The
  *                    results are the same bit for bit (integer accumulators)
+ *   "tensor_wait_test"  0 (default); 1: the tensor-core kernel's MMA issuer
+ *                    first waits on a barrier nothing signals, so the bounded
+ *                    wait runs out after 2 s: a synchronous call returns
+ *                    UF_ETIMEOUT and an asynchronous one writes NaN (for
+ *                    testing the abort path; no fault, the context stays usable)
  *   "sparse_region_bytes"  48,000,000 (default; 0 restores it): a one-table
  *                    call whose stripe accumulators exceed this many bytes
  *                    writes the scattered branches' sample lists once and

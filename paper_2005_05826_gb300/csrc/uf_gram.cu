@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     k_gram(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const GramArgs a) {
   extern __shared__ unsigned char smem_dyn[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[GSTAGES], empty[GSTAGES], acc_full[2], acc_empty[2], mma_done;
+  __shared__ __align__(8) uint64_t full[GSTAGES], empty[GSTAGES], acc_full[2], acc_empty[2], mma_done, never;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
       mbar_init(&acc_empty[b], 4);
     }
     mbar_init(&mma_done, 1);
+    mbar_init(&never, 1);  // no thread ever arrives on it
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     int stage = 0;
     uint32_t phase = 0;
     int ul = 0;
+    if (a.wait_test) mbar_wait(&never, 0, &s_abort);  // runs out after WAIT_NS and raises the abort
     for (int u = blockIdx.x; u < a.n_units && !s_abort; u += gridDim.x, ul++) {
       const GUnit g = gram_unit(a, u);
       const int b = ul & 1;

@@ -24,6 +24,8 @@ struct GramArgs {
   unsigned long long *Gt;  // fixed point; cell (i, j), i <= j, of table t at gt_off + j * n_pad + i
   double scale;         // 2^F
   int *err;             // set to 1 when a bounded wait gave up
+  int wait_test;        // 1: the MMA issuer first waits on a barrier nothing signals, so its
+                        // bounded wait runs out (tests the abort path; option "tensor_wait_test")
 };
 struct GramFinalArgs {
   int n, n_pad;

@@ -28,6 +28,7 @@ std::atomic<int64_t> g_graph{1};
 std::atomic<int64_t> g_autotune{1};
 std::atomic<int64_t> g_sparse{1};
 std::atomic<int64_t> g_overlap{1};
+std::atomic<int64_t> g_tensor_wait_test{0};
 std::atomic<int64_t> g_region_bytes{(int64_t)SPARSE_REGION_BYTES_DEFAULT};
 
 int host_threads() {
@@ -384,6 +385,11 @@ uf_status uf_set_option(const char *name, int64_t value) {
     g_sparse = value;
     return UF_OK;
   }
+  if (!strcmp(name, "tensor_wait_test")) {
+    if (value != 0 && value != 1) return fail(UF_EINVAL, "tensor_wait_test must be 0 or 1");
+    g_tensor_wait_test = value;
+    return UF_OK;
+  }
   if (!strcmp(name, "sparse_overlap")) {
     if (value != 0 && value != 1) return fail(UF_EINVAL, "sparse_overlap must be 0 or 1");
     g_overlap = value;
@@ -407,6 +413,7 @@ int64_t uf_get_option(const char *name) {
   if (!strcmp(name, "sparse")) return g_sparse.load();
   if (!strcmp(name, "sparse_region_bytes")) return g_region_bytes.load();
   if (!strcmp(name, "sparse_overlap")) return g_overlap.load();
+  if (!strcmp(name, "tensor_wait_test")) return g_tensor_wait_test.load();
   return -1;
 }
 

@@ -636,6 +636,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
     ga.Gt = Gt.as<unsigned long long>();
     ga.scale = scale;
     ga.err = err.as<int>();
+    ga.wait_test = (int)g_tensor_wait_test.load();
     timer.begin(1);
     ck(launch_gram(ga, Pl.p, K_pad, ls), "tensor-core gram");
     timer.end();

@@ -20,9 +20,10 @@
 // Work is split into units (row chunk of up to a.chunk branches, tile of
 // TILE_S stripes x TILE_K samples).  Persistent CTAs take units from a global
 // counter, chunk-major, so the CTAs in flight read the same rows and those
-// rows stay in L2.  Per unit, 8-row stages of the u window [k0, k0 + TILE_K)
-// and the partner window [k0 + s0, k0 + s0 + TILE_K + TILE_S) go to shared
-// memory by 16-byte cp.async (three stages in flight), and each thread
+// rows stay in L2.  Per unit, stages of rows (FP32: 16 rows, two stages;
+// FP64: 8 rows, three stages) of the u window [k0, k0 + TILE_K) and the
+// partner window [k0 + s0, k0 + s0 + TILE_K + TILE_S) go to shared memory by
+// 16-byte cp.async while the previous stage is computed, and each thread
 // updates an RD x RK register micro-tile.  Shared rows are XOR-swizzled in
 // 16-byte units so the per-thread 16-byte reads are free of bank conflicts.
 //
@@ -49,8 +50,6 @@ namespace ufg {
 namespace {
 
 constexpr int NT = 256;       // threads per CTA: 16 (stripe) x 16 (sample)
-constexpr int RB = 8;         // branch rows per pipeline stage
-constexpr int NSTAGE = 3;     // cp.async pipeline depth
 constexpr int B1 = 64;        // inner partial length (branches)
 
 // Shared rows are stored in 16-byte units with unit j placed at
@@ -67,6 +66,10 @@ __host__ __device__ constexpr int swz(int elem) {
 
 template <typename T, int RD, int RK, int NACC>
 struct Geo {
+  // branch rows per pipeline stage and cp.async stages: FP32 16 rows in two
+  // stages (half the block barriers of 8-row stages), FP64 8 rows in three
+  static constexpr int RB = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int NSTAGE = sizeof(T) == 4 ? 2 : 3;
   static constexpr int TS = 16 * RD;             // stripes per tile
   static constexpr int TK = 16 * RK;             // samples per tile
   static constexpr int VEC = 16 / sizeof(T);     // elements per 16-byte copy
@@ -145,14 +148,14 @@ __device__ __forceinline__ bool next_unit(const StripeArgs &a, int tile_s, int t
   return true;
 }
 
-// Stage loader: RB branch rows [e0, e0 + RB) of the u window (columns from
+// Stage loader: G::RB branch rows [e0, e0 + G::RB) of the u window (columns from
 // ucol) and the partner window (columns from vcol).
 template <typename T, int RD, int RK, int NACC, bool LEN>
 __device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0, int e_end, int64_t ucol,
                                            int64_t vcol) {
   using G = Geo<T, RD, RK, NACC>;
   const T *X = (const T *)a.X;
-  for (int c = threadIdx.x; c < RB * G::CH; c += NT) {
+  for (int c = threadIdx.x; c < G::RB * G::CH; c += NT) {
     const int r = c / G::CH, q = c - r * G::CH;
     T *row = stage + r * G::ROW;
     const int e = e0 + r;
@@ -176,9 +179,9 @@ __device__ __forceinline__ void load_stage(T *stage, const StripeArgs &a, int e0
       for (int i = 0; i < G::VEC; i++) dst[i] = pad;
     }
   }
-  if (LEN && threadIdx.x < RB) {
+  if (LEN && threadIdx.x < G::RB) {
     const int e = e0 + threadIdx.x;
-    stage[RB * G::ROW + threadIdx.x] = e < e_end ? (T)a.len[e] : T(0);
+    stage[G::RB * G::ROW + threadIdx.x] = e < e_end ? (T)a.len[e] : T(0);
   }
 }
 
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
   constexpr bool F32 = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *stg = reinterpret_cast<T *>(smem_raw);
-  Mid *mid = reinterpret_cast<Mid *>(smem_raw + (size_t)NSTAGE * G::STAGE * sizeof(T));
+  Mid *mid = reinterpret_cast<Mid *>(smem_raw + (size_t)G::NSTAGE * G::STAGE * sizeof(T));
   __shared__ int s_unit;
   const int tk = threadIdx.x & 15, ts = threadIdx.x >> 4;
   const int w0 = RK * tk + RD * ts;  // partner window of this thread, used from w0 + 1
@@ -223,10 +226,10 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
   while (next_unit(a, G::TS, G::TK, &s_unit, &U)) {
 #pragma unroll
     for (int c = 0; c < RD * RK; c++) mid[c * NT + threadIdx.x] = Mid(0);
-    const int nst = (U.r1 - U.r0 + RB - 1) / RB;
+    const int nst = (U.r1 - U.r0 + G::RB - 1) / G::RB;
 #pragma unroll
-    for (int p = 0; p < NSTAGE - 1; p++) {
-      if (p < nst) load_stage<T, RD, RK, 1, false>(stg + p * G::STAGE, a, U.r0 + p * RB, U.r1, U.x_col + U.k0,
+    for (int p = 0; p < G::NSTAGE - 1; p++) {
+      if (p < nst) load_stage<T, RD, RK, 1, false>(stg + p * G::STAGE, a, U.r0 + p * G::RB, U.r1, U.x_col + U.k0,
                                         U.x_col + U.k0 + U.s0);
       cp_async_commit();
     }
@@ -237,18 +240,18 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
       for (int j = 0; j < RK; j++) acc[i][j] = T(0);
     int in_sub = 0;
     for (int it = 0; it < nst; it++) {
-      cp_async_wait<NSTAGE - 2>();
+      cp_async_wait<G::NSTAGE - 2>();
       __syncthreads();
       {
-        const int nx = it + NSTAGE - 1;
+        const int nx = it + G::NSTAGE - 1;
         if (nx < nst)
-          load_stage<T, RD, RK, 1, false>(stg + (nx % NSTAGE) * G::STAGE, a, U.r0 + nx * RB, U.r1,
+          load_stage<T, RD, RK, 1, false>(stg + (nx % G::NSTAGE) * G::STAGE, a, U.r0 + nx * G::RB, U.r1,
                                           U.x_col + U.k0, U.x_col + U.k0 + U.s0);
         cp_async_commit();
       }
-      const T *stage = stg + (it % NSTAGE) * G::STAGE;
+      const T *stage = stg + (it % G::NSTAGE) * G::STAGE;
 #pragma unroll 2
-      for (int r = 0; r < RB; r++) {
+      for (int r = 0; r < G::RB; r++) {
         const T *urow = stage + r * G::ROW;
         const T *vrow = urow + G::UW;
         T u[RK], v[G::NV * G::VEC];
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
             for (int j = 0; j < RK; j++) acc[i][j] += tmin<T>(u[j], v[i + j + 1]);
         }
       }
-      in_sub += RB;
+      in_sub += G::RB;
       if (in_sub == B1 || it == nst - 1) {
 #pragma unroll
         for (int i = 0; i < RD; i++)
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
   constexpr bool F32 = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *stg = reinterpret_cast<T *>(smem_raw);
-  Mid *midd = reinterpret_cast<Mid *>(smem_raw + (size_t)NSTAGE * G::STAGE * sizeof(T));
+  Mid *midd = reinterpret_cast<Mid *>(smem_raw + (size_t)G::NSTAGE * G::STAGE * sizeof(T));
   Mid *midq = midd + RD * RK * NT;
   __shared__ int s_unit;
   const int tk = threadIdx.x & 15, ts = threadIdx.x >> 4;
@@ -323,10 +326,10 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
   while (next_unit(a, G::TS, G::TK, &s_unit, &U)) {
 #pragma unroll
     for (int c = 0; c < RD * RK; c++) midd[c * NT + threadIdx.x] = midq[c * NT + threadIdx.x] = Mid(0);
-    const int nst = (U.r1 - U.r0 + RB - 1) / RB;
+    const int nst = (U.r1 - U.r0 + G::RB - 1) / G::RB;
 #pragma unroll
-    for (int p = 0; p < NSTAGE - 1; p++) {
-      if (p < nst) load_stage<T, RD, RK, 2, true>(stg + p * G::STAGE, a, U.r0 + p * RB, U.r1, U.x_col + U.k0,
+    for (int p = 0; p < G::NSTAGE - 1; p++) {
+      if (p < nst) load_stage<T, RD, RK, 2, true>(stg + p * G::STAGE, a, U.r0 + p * G::RB, U.r1, U.x_col + U.k0,
                                        U.x_col + U.k0 + U.s0);
       cp_async_commit();
     }
@@ -337,21 +340,21 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
       for (int j = 0; j < RK; j++) accd[i][j] = accq[i][j] = T(0);
     int in_sub = 0;
     for (int it = 0; it < nst; it++) {
-      cp_async_wait<NSTAGE - 2>();
+      cp_async_wait<G::NSTAGE - 2>();
       __syncthreads();
       {
-        const int nx = it + NSTAGE - 1;
+        const int nx = it + G::NSTAGE - 1;
         if (nx < nst)
-          load_stage<T, RD, RK, 2, true>(stg + (nx % NSTAGE) * G::STAGE, a, U.r0 + nx * RB, U.r1,
+          load_stage<T, RD, RK, 2, true>(stg + (nx % G::NSTAGE) * G::STAGE, a, U.r0 + nx * G::RB, U.r1,
                                          U.x_col + U.k0, U.x_col + U.k0 + U.s0);
         cp_async_commit();
       }
-      const T *stage = stg + (it % NSTAGE) * G::STAGE;
+      const T *stage = stg + (it % G::NSTAGE) * G::STAGE;
 #pragma unroll 1
-      for (int r = 0; r < RB; r++) {
+      for (int r = 0; r < G::RB; r++) {
         const T *urow = stage + r * G::ROW;
         const T *vrow = urow + G::UW;
-        const T l = stage[RB * G::ROW + r];
+        const T l = stage[G::RB * G::ROW + r];
         T u[RK], v[G::NV * G::VEC];
 #pragma unroll
         for (int q = 0; q < RK / G::VEC; q++)
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
             }
         }
       }
-      in_sub += RB;
+      in_sub += G::RB;
       if (in_sub == B1 || it == nst - 1) {
 #pragma unroll
         for (int i = 0; i < RD; i++)

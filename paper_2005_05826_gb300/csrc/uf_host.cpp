@@ -149,44 +149,33 @@ void ck(cudaError_t e, const char *what) {
 uf_tree::Dev &tree_dev(uf_tree *t, int device) {
   auto it = t->dev.find(device);
   if (it != t->dev.end()) return it->second;
+  DevPack pk;
+  const size_t i_len = pk.add(t->length), i_ton = pk.add(t->tip_of_node), i_cp = pk.add(t->child_ptr),
+               i_ci = pk.add(t->child_idx), i_lo = pk.add(t->tip_lo), i_hi = pk.add(t->tip_hi);
   uf_tree::Dev d;
-  try {
-    d.length = dev_upload(t->length, "tree upload");
-    d.tip_of_node = dev_upload(t->tip_of_node, "tree upload");
-    d.child_ptr = dev_upload(t->child_ptr, "tree upload");
-    d.child_idx = dev_upload(t->child_idx, "tree upload");
-    d.tip_lo = dev_upload(t->tip_lo, "tree upload");
-    d.tip_hi = dev_upload(t->tip_hi, "tree upload");
-  } catch (...) {
-    cudaFree(d.length);
-    cudaFree(d.tip_of_node);
-    cudaFree(d.child_ptr);
-    cudaFree(d.child_idx);
-    cudaFree(d.tip_lo);
-    cudaFree(d.tip_hi);
-    throw;
-  }
+  d.base = pk.upload("tree upload");
+  d.length = DevPack::at<double>(d.base, pk, i_len);
+  d.tip_of_node = DevPack::at<int32_t>(d.base, pk, i_ton);
+  d.child_ptr = DevPack::at<int32_t>(d.base, pk, i_cp);
+  d.child_idx = DevPack::at<int32_t>(d.base, pk, i_ci);
+  d.tip_lo = DevPack::at<int32_t>(d.base, pk, i_lo);
+  d.tip_hi = DevPack::at<int32_t>(d.base, pk, i_hi);
   return t->dev[device] = d;
 }
 
 uf_table::Dev &table_dev(uf_table *t, int device) {
   auto it = t->dev.find(device);
   if (it != t->dev.end()) return it->second;
+  DevPack pk;
+  const size_t i_tot = pk.add(t->total), i_inv = pk.add(t->inv_total_f), i_cp = pk.add(t->col_ptr),
+               i_row = pk.add(t->col_row), i_val = pk.add(t->col_val);
   uf_table::Dev d;
-  try {
-    d.total = dev_upload(t->total, "table upload");
-    d.inv_total_f = dev_upload(t->inv_total_f, "table upload");
-    d.col_ptr = dev_upload(t->col_ptr, "table upload");
-    d.col_row = dev_upload(t->col_row, "table upload");
-    d.col_val = dev_upload(t->col_val, "table upload");
-  } catch (...) {
-    cudaFree(d.total);
-    cudaFree(d.inv_total_f);
-    cudaFree(d.col_ptr);
-    cudaFree(d.col_row);
-    cudaFree(d.col_val);
-    throw;
-  }
+  d.base = pk.upload("table upload");
+  d.total = DevPack::at<double>(d.base, pk, i_tot);
+  d.inv_total_f = DevPack::at<float>(d.base, pk, i_inv);
+  d.col_ptr = DevPack::at<int64_t>(d.base, pk, i_cp);
+  d.col_row = DevPack::at<int32_t>(d.base, pk, i_row);
+  d.col_val = DevPack::at<double>(d.base, pk, i_val);
   return t->dev[device] = d;
 }
 
@@ -201,18 +190,23 @@ Plan *get_plan(uf_tree *t, int64_t rows) {
   P->block_rows = rows;
   const int64_t nb = t->n_nodes - 1;  // branches: every node but the root
   P->slot_of_node.assign(t->n_nodes, -1);
+  P->lists.resize(std::max<int64_t>(nb, 0));
   std::vector<int32_t> level(t->n_nodes, 0);
+  std::vector<int64_t> count;
   std::vector<int32_t> free_slots;
   int32_t next_slot = 0;
-  std::vector<int64_t> release;  // nodes whose slot goes back at block end
   for (int64_t b0 = 0; b0 < nb; b0 += rows) {
     const int64_t b1 = std::min(nb, b0 + rows);
     P->b0.push_back(b0);
     P->b1.push_back(b1);
-    std::vector<std::vector<int32_t>> lv(1);  // lv[0] = tips
+    // list 0: the block's tips; list L + 1: its internal nodes of level L
+    // (one more than the deepest internal child in the block); filled by a
+    // counting sort, each list in node order
+    count.assign(1, 0);
     for (int64_t v = b0; v < b1; v++) {
       if (t->tip_of_node[v] >= 0) {
-        lv[0].push_back((int32_t)v);
+        level[v] = -1;
+        count[0]++;
         continue;
       }
       int32_t L = 0;
@@ -221,10 +215,19 @@ Plan *get_plan(uf_tree *t, int64_t rows) {
         if (ch >= b0 && t->tip_of_node[ch] < 0) L = std::max(L, level[ch] + 1);
       }
       level[v] = L;
-      if ((int)lv.size() < L + 2) lv.resize(L + 2);
-      lv[L + 1].push_back((int32_t)v);
+      if ((int64_t)count.size() < L + 2) count.resize(L + 2, 0);
+      count[L + 1]++;
     }
-    // slots for the block's nodes
+    std::vector<std::pair<int64_t, int>> ls(count.size());
+    int64_t at = b0;
+    for (size_t l = 0; l < count.size(); l++) {
+      ls[l] = {at, (int)count[l]};
+      count[l] = at;  // next position of list l
+      at += ls[l].second;
+    }
+    for (int64_t v = b0; v < b1; v++) P->lists[count[level[v] + 1]++] = (int32_t)v;
+    P->launches.push_back(std::move(ls));
+    // slots for the block's nodes (the first block takes fresh slots in order)
     for (int64_t v = b0; v < b1; v++) {
       int32_t s;
       if (!free_slots.empty()) {
@@ -235,19 +238,14 @@ Plan *get_plan(uf_tree *t, int64_t rows) {
       }
       P->slot_of_node[v] = s;
     }
-    std::vector<std::pair<int64_t, int>> ls;
-    for (auto &l : lv) {
-      ls.emplace_back((int64_t)P->lists.size(), (int)l.size());
-      P->lists.insert(P->lists.end(), l.begin(), l.end());
-    }
-    P->launches.push_back(std::move(ls));
-    // release: children of this block's internal nodes, and nodes whose
-    // parent is the root (never read again)
-    for (int64_t v = b0; v < b1; v++) {
-      for (int32_t c = t->child_ptr[v]; c < t->child_ptr[v + 1]; c++)
-        free_slots.push_back(P->slot_of_node[t->child_idx[c]]);
-      if (t->parent[v] == t->n_nodes - 1) free_slots.push_back(P->slot_of_node[v]);
-    }
+    // release: children of this block's nodes, and nodes whose parent is the
+    // root (never read again); nothing is reused after the last block
+    if (b1 < nb)
+      for (int64_t v = b0; v < b1; v++) {
+        for (int32_t c = t->child_ptr[v]; c < t->child_ptr[v + 1]; c++)
+          free_slots.push_back(P->slot_of_node[t->child_idx[c]]);
+        if (t->parent[v] == t->n_nodes - 1) free_slots.push_back(P->slot_of_node[v]);
+      }
   }
   P->n_slots = next_slot;
   Plan *raw = P.get();
@@ -258,14 +256,12 @@ Plan *get_plan(uf_tree *t, int64_t rows) {
 Plan::Dev &plan_dev(Plan *P, int device) {
   auto it = P->dev.find(device);
   if (it != P->dev.end()) return it->second;
+  DevPack pk;
+  const size_t i_l = pk.add(P->lists), i_s = pk.add(P->slot_of_node);
   Plan::Dev d;
-  try {
-    d.lists = dev_upload(P->lists, "plan upload");
-    d.slot_of_node = dev_upload(P->slot_of_node, "plan upload");
-  } catch (...) {
-    cudaFree(d.lists);
-    throw;
-  }
+  d.base = pk.upload("plan upload");
+  d.lists = DevPack::at<int32_t>(d.base, pk, i_l);
+  d.slot_of_node = DevPack::at<int32_t>(d.base, pk, i_s);
   return P->dev[device] = d;
 }
 

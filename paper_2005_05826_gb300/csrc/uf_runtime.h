@@ -81,21 +81,41 @@ struct NoInit : std::allocator<T> {
   }
 };
 
-template <typename T, typename Alloc>
-T *dev_upload(const std::vector<T, Alloc> &h, const char *what) {
-  g_h2d += (double)h.size() * sizeof(T);
-  T *d = nullptr;
-  size_t bytes = std::max<size_t>(h.size() * sizeof(T), 16);
-  ck(cudaMalloc(&d, bytes), what);
-  if (!h.empty()) {
-    cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      cudaFree(d);
-      ck(e, what);
-    }
+// Several host arrays copied into one device allocation at 256-byte aligned
+// offsets: one cudaMalloc per handle instead of one per array.
+struct DevPack {
+  std::vector<std::pair<const void *, size_t>> parts;
+  std::vector<size_t> offs;
+  size_t total = 0;
+  template <typename T, typename Alloc>
+  size_t add(const std::vector<T, Alloc> &h) {
+    const size_t off = (total + 255) & ~(size_t)255;
+    offs.push_back(off);
+    parts.emplace_back(h.data(), h.size() * sizeof(T));
+    total = off + std::max<size_t>(h.size() * sizeof(T), 16);
+    return parts.size() - 1;
   }
-  return d;
-}
+  // the device copy; free with cudaFree
+  char *upload(const char *what) {
+    char *d = nullptr;
+    ck(cudaMalloc(&d, std::max<size_t>(total, 16)), what);
+    for (size_t i = 0; i < parts.size(); i++) {
+      if (!parts[i].second) continue;
+      const cudaError_t e = cudaMemcpy(d + offs[i], parts[i].first, parts[i].second, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        cudaFree(d);
+        ck(e, what);
+      }
+      g_h2d += (double)parts[i].second;
+    }
+    return d;
+  }
+  template <typename T>
+  static T *at(char *base, const DevPack &pk, size_t part) {
+    return reinterpret_cast<T *>(base + pk.offs[part]);
+  }
+};
+
 
 // ------------------------------------------------------------------- plan
 
@@ -110,6 +130,7 @@ struct Plan {
   int64_t n_slots = 0;
   // device copies (device id -> pointers)
   struct Dev {
+    char *base = nullptr;  // one allocation holding both
     int32_t *lists = nullptr, *slot_of_node = nullptr;
   };
   std::map<int, Dev> dev;
@@ -134,6 +155,7 @@ struct uf_tree {
   std::vector<int32_t> tip_lo, tip_hi;
   std::mutex mu;
   struct Dev {
+    char *base = nullptr;  // one allocation holding the arrays below
     double *length = nullptr;
     int32_t *tip_of_node = nullptr, *child_ptr = nullptr, *child_idx = nullptr;
     int32_t *tip_lo = nullptr, *tip_hi = nullptr;
@@ -150,18 +172,12 @@ struct uf_tree {
     cudaGetDevice(&cur);
     for (auto &kv : dev) {
       cudaSetDevice(kv.first);
-      cudaFree(kv.second.length);
-      cudaFree(kv.second.tip_of_node);
-      cudaFree(kv.second.child_ptr);
-      cudaFree(kv.second.child_idx);
-      cudaFree(kv.second.tip_lo);
-      cudaFree(kv.second.tip_hi);
+      cudaFree(kv.second.base);
     }
     for (auto &p : plans)
       for (auto &kv : p.second->dev) {
         cudaSetDevice(kv.first);
-        cudaFree(kv.second.lists);
-        cudaFree(kv.second.slot_of_node);
+        cudaFree(kv.second.base);
       }
     cudaSetDevice(cur);
   }
@@ -178,6 +194,7 @@ struct uf_table {
   std::mutex mu;
   std::map<uint64_t, double> presence_bound;  // by tree id: max_k sum_{f in k} dist(tip f)
   struct Dev {
+    char *base = nullptr;  // one allocation holding the arrays below
     double *total = nullptr, *col_val = nullptr;
     float *inv_total_f = nullptr;
     int64_t *col_ptr = nullptr;
@@ -189,11 +206,7 @@ struct uf_table {
     cudaGetDevice(&cur);
     for (auto &kv : dev) {
       cudaSetDevice(kv.first);
-      cudaFree(kv.second.total);
-      cudaFree(kv.second.col_val);
-      cudaFree(kv.second.inv_total_f);
-      cudaFree(kv.second.col_ptr);
-      cudaFree(kv.second.col_row);
+      cudaFree(kv.second.base);
     }
     cudaSetDevice(cur);
   }

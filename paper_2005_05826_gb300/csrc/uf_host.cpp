@@ -440,14 +440,26 @@ uf_status uf_tree_create(int64_t n_nodes, const int64_t *parent, const double *l
   if (n_nodes < 1) return fail(UF_EINVAL, "n_nodes must be >= 1 (got %lld)", (long long)n_nodes);
   if (n_nodes > INT32_MAX) return fail(UF_EINVAL, "n_nodes above 2^31 - 1");
   if (parent[n_nodes - 1] != -1) return fail(UF_ETREE, "the last node must be the root (parent -1)");
-  for (int64_t i = 0; i + 1 < n_nodes; i++) {
-    if (parent[i] <= i || parent[i] >= n_nodes)
-      return fail(UF_ETREE, "node %lld: parent %lld must be in (%lld, %lld)", (long long)i,
-                  (long long)parent[i], (long long)i, (long long)n_nodes);
-    if (!std::isfinite(length[i]) || length[i] < 0.0)
-      return fail(UF_ETREE, "node %lld: length %g must be finite and >= 0", (long long)i, length[i]);
-  }
   try {
+    // validation over node ranges in parallel (the first failing node wins)
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n_nodes / 65536));
+    std::vector<int64_t> bad(T, -1);
+    parallel_for(T, [&](int c) {
+      const int64_t i0 = (n_nodes - 1) * c / T, i1 = (n_nodes - 1) * (c + 1) / T;
+      for (int64_t i = i0; i < i1; i++)
+        if (parent[i] <= i || parent[i] >= n_nodes || !std::isfinite(length[i]) || length[i] < 0.0) {
+          bad[c] = i;
+          return;
+        }
+    });
+    for (int c = 0; c < T; c++)
+      if (bad[c] >= 0) {
+        const int64_t i = bad[c];
+        if (parent[i] <= i || parent[i] >= n_nodes)
+          return fail(UF_ETREE, "node %lld: parent %lld must be in (%lld, %lld)", (long long)i,
+                      (long long)parent[i], (long long)i, (long long)n_nodes);
+        return fail(UF_ETREE, "node %lld: length %g must be finite and >= 0", (long long)i, length[i]);
+      }
     auto t = std::make_unique<uf_tree>();
     static std::atomic<uint64_t> next_tree_id{1};
     t->id = next_tree_id++;
@@ -455,52 +467,53 @@ uf_status uf_tree_create(int64_t n_nodes, const int64_t *parent, const double *l
     t->parent.assign(parent, parent + n_nodes);
     t->length.assign(length, length + n_nodes);
     t->length[n_nodes - 1] = 0.0;  // no branch above the root
-    std::vector<int32_t> nchild(n_nodes, 0);
-    for (int64_t i = 0; i + 1 < n_nodes; i++) nchild[parent[i]]++;
+    // one pass in index order (children come before their parent, so a
+    // node's child count is final when it is reached): child counts, tip
+    // numbers in index order, and each node's tip range [lo, hi) and tip count
+    std::vector<int32_t> nchild(n_nodes, 0), under(n_nodes, 0);
+    t->tip_of_node.assign(n_nodes, -1);
+    t->tip_lo.assign(n_nodes, INT32_MAX);
+    t->tip_hi.assign(n_nodes, -1);
+    int32_t tips = 0;
+    for (int64_t v = 0; v < n_nodes; v++) {
+      if (nchild[v] == 0) {
+        t->tip_of_node[v] = tips;
+        t->tip_lo[v] = tips;
+        t->tip_hi[v] = tips + 1;
+        under[v] = 1;
+        tips++;
+      }
+      if (v + 1 < n_nodes) {
+        const int64_t p = parent[v];
+        nchild[p]++;
+        t->tip_lo[p] = std::min(t->tip_lo[p], t->tip_lo[v]);
+        t->tip_hi[p] = std::max(t->tip_hi[p], t->tip_hi[v]);
+        under[p] += under[v];
+      }
+    }
+    t->n_tips = tips;
     t->child_ptr.assign(n_nodes + 1, 0);
     for (int64_t i = 0; i < n_nodes; i++) t->child_ptr[i + 1] = t->child_ptr[i] + nchild[i];
     t->child_idx.assign(std::max<int64_t>(n_nodes - 1, 1), 0);
-    std::vector<int32_t> fill(n_nodes, 0);
     for (int64_t i = 0; i + 1 < n_nodes; i++) {
       const int64_t p = parent[i];
-      t->child_idx[t->child_ptr[p] + fill[p]++] = (int32_t)i;  // ascending child order
+      t->child_idx[t->child_ptr[p + 1] - nchild[p]--] = (int32_t)i;  // ascending child order
     }
-    t->tip_of_node.assign(n_nodes, -1);
-    int64_t tips = 0;
-    for (int64_t i = 0; i < n_nodes; i++)
-      if (nchild[i] == 0) t->tip_of_node[i] = (int32_t)tips++;
-    t->n_tips = tips;
-    {
-      std::vector<int64_t> under(n_nodes, 0);
-      t->tip_lo.assign(n_nodes, INT32_MAX);
-      t->tip_hi.assign(n_nodes, -1);
-      for (int64_t v = 0; v < n_nodes; v++) {  // children come before their parent
-        if (t->tip_of_node[v] >= 0) {
-          t->tip_lo[v] = t->tip_of_node[v];
-          t->tip_hi[v] = t->tip_of_node[v] + 1;
-          under[v] = 1;
-        }
-        if (v + 1 < n_nodes) {
-          const int64_t p = parent[v];
-          t->tip_lo[p] = std::min(t->tip_lo[p], t->tip_lo[v]);
-          t->tip_hi[p] = std::max(t->tip_hi[p], t->tip_hi[v]);
-          under[p] += under[v];
-        }
-      }
-      for (int64_t v = 0; v < n_nodes; v++)
-        if ((int64_t)t->tip_hi[v] - t->tip_lo[v] != under[v]) t->tip_lo[v] = t->tip_hi[v] = -1;
-    }
+    // one pass in reverse order (parents first): root distances, the tips'
+    // distances, and the tip ranges that are not contiguous (both set to -1)
     t->dist.assign(n_nodes, 0.0);
-    for (int64_t v = n_nodes - 2; v >= 0; v--) {  // parents come later in the order
-      t->dist[v] = t->length[v] + t->dist[parent[v]];
-      t->total_length += t->length[v];
-    }
-    t->tip_dist.resize(std::max<int64_t>(tips, 1));
-    for (int64_t v = 0; v < n_nodes; v++)
-      if (nchild[v] == 0) {
+    t->tip_dist.resize(std::max<int32_t>(tips, 1));
+    for (int64_t v = n_nodes - 1; v >= 0; v--) {
+      if (v + 1 < n_nodes) {
+        t->dist[v] = t->length[v] + t->dist[parent[v]];
+        t->total_length += t->length[v];
+      }
+      if (t->tip_of_node[v] >= 0) {
         t->max_tip_dist = std::max(t->max_tip_dist, t->dist[v]);
         t->tip_dist[t->tip_of_node[v]] = t->dist[v];
       }
+      if ((int64_t)t->tip_hi[v] - t->tip_lo[v] != under[v]) t->tip_lo[v] = t->tip_hi[v] = -1;
+    }
     *out = t.release();
     return UF_OK;
   } catch (const std::bad_alloc &) {

@@ -12,6 +12,7 @@
 
 #include <condition_variable>
 #include <deque>
+#include <exception>
 
 using namespace ufg;
 using namespace ufg::rt;
@@ -48,6 +49,8 @@ struct PoolJob {
   int n;
   std::atomic<int> next{0}, left{0};
   int users = 0;  // attached workers (guarded by the pool mutex)
+  std::mutex emu;
+  std::exception_ptr error;  // the first exception a body threw
 };
 
 struct Pool {
@@ -72,7 +75,12 @@ struct Pool {
   }
   static void take(PoolJob *j) {
     for (int i; (i = j->next.fetch_add(1)) < j->n;) {
-      (*j->body)(i);
+      try {
+        (*j->body)(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(j->emu);
+        if (!j->error) j->error = std::current_exception();
+      }
       j->left.fetch_sub(1);
     }
   }
@@ -105,7 +113,7 @@ void run_parallel(int n, const std::function<void(int)> &body) {
   if (n <= 0) return;
   Pool *pool = n > 1 ? host_pool() : nullptr;
   if (!pool || pool->workers.empty() || pool->pid != getpid()) {
-    for (int i = 0; i < n; i++) body(i);
+    for (int i = 0; i < n; i++) body(i);  // an exception propagates from here directly
     return;
   }
   PoolJob j;
@@ -125,6 +133,8 @@ void run_parallel(int n, const std::function<void(int)> &body) {
       break;
     }
   pool->cv_done.wait(lk, [&] { return j.left.load() == 0 && j.users == 0; });
+  lk.unlock();
+  if (j.error) std::rethrow_exception(j.error);  // e.g. std::bad_alloc becomes UF_ENOMEM
 }
 
 uf_status fail(uf_status st, const char *fmt, ...) {

@@ -56,7 +56,8 @@ int host_threads();
 // returns when every index has run.  Indices are handed out one at a time, so
 // calls from several threads (or from inside a body) share the pool without
 // waiting on each other's indices.  In a forked child the pool is not
-// inherited: the calling thread runs every index.
+// inherited: the calling thread runs every index.  The first exception a
+// body throws is rethrown in the caller once every index has run.
 void run_parallel(int n, const std::function<void(int)> &body);
 template <typename F>
 void parallel_for(int n, F body) {

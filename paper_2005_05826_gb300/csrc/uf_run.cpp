@@ -761,7 +761,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc);
   const bool region_mode = split.n_sparse > 0 && (n_regions > 1 || split.lists);
   int64_t n_sparse_rows = 0;
-  DevBuf le, lz;
+  DevBuf le, lk, lz;
   if (split.n_sparse > 0) {
     std::vector<int32_t> all;
     for (const auto &c : split.sparse) {
@@ -776,6 +776,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
         lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
       const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
       le = DevBuf(total_e * sparse_entry_bytes(fp32), st, "alloc sparse lists");
+      lk = DevBuf(total_e * 4, st, "alloc sparse lists");
       lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
       // rows without entries in the table return before writing their count
       ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
@@ -853,6 +854,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sp.scale = scale;
     if (region_mode) {
       sp.le = le.p;
+      sp.lk = lk.as<int>();
       sp.lofs = meta.at<int64_t>(o_lofs);
       sp.lz = lz.as<int>();
     }

@@ -347,18 +347,18 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
     en.x = x;
     en.f = f;
     le[off + u] = en;
+    a.lk[off + u] = (int)smp;
     red_add(a.Dsp + tb.off + smp, f);
     u++;
   }
   if (tid == 0) a.lz[row] = z;
 }
 
-// first index in [lo, hi) of the entries (ascending k) with E[i].k >= key
-template <typename T>
-__device__ __forceinline__ int lower_index(const SpEnt<T> *E, int lo, int hi, int key) {
+// first index in [lo, hi) of the ascending samples K with K[i] >= key
+__device__ __forceinline__ int lower_index(const int *K, int lo, int hi, int key) {
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (E[mid].k < key) lo = mid + 1;
+    if (K[mid] < key) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -373,6 +373,7 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   // never past the row's list capacity
   const int z = (int)min((int64_t)a.lz[row], a.lofs[row + 1] - off);
   const SpEnt<T> *E = reinterpret_cast<const SpEnt<T> *>(a.le) + off;
+  const int *K = a.lk + off;  // the same entries' samples, for the searches
   const int n = tb.n, half = n / 2;
   PairCtx<T> c;
   c.n = n;
@@ -393,8 +394,8 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
 #pragma unroll
     for (int w = 0; w < 2; w++) {
       if (d_lo[w] > d_hi[w]) continue;
-      const int b0 = lower_index(E, ia + 1, z, ea.k + d_lo[w]);
-      const int b1 = lower_index(E, b0, z, ea.k + d_hi[w] + 1);
+      const int b0 = lower_index(K, ia + 1, z, ea.k + d_lo[w]);
+      const int b1 = lower_index(K, b0, z, ea.k + d_hi[w] + 1);
       for (int ib = b0; ib < b1; ib++) add_pair<T, ACC, MODE>(ea, E[ib], c);
     }
   }

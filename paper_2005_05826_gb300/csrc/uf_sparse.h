@@ -45,6 +45,8 @@ struct SparseArgs {
   int row_base;
   void *le;                 // entries (sample, x or u, fixed-point X or P), ascending
                             // sample; sparse_entry_bytes() each
+  int *lk;                  // the entries' samples alone (4 bytes each), for the
+                            // region kernel's binary searches
   const int64_t *lofs;      // first entry of each row
   int *lz;                  // entries of each row
   // region mode: only pairs whose stripe lies in [r0, r1) (launch_sparse_region)

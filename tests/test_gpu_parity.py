@@ -216,6 +216,29 @@ def test_graph_and_plain_launches_agree():
         uf.uf_set_option("graph", 1)
 
 
+def test_queued_device_output_calls_match_synchronous_ones():
+    # device outputs on a non-default stream: each call returns once its work
+    # is queued (its graph is retired by a later call); 40 calls back to back
+    # pass the 32 graphs kept in flight, and every result equals the same
+    # call made synchronously with a host output, bit for bit
+    tree_s = yule_tree(800, seed=95)
+    table_s = table_iid(160, tree_s.n_tips, 0.05, seed=96)
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
+    n = table_s.n_samples
+    cases = [(m, 0.5 if m == "generalized" else 1.0, p) for m in METHODS for p in PRECISIONS]
+    expect = {c: uf.uf_compute(tree, table, c[0], c[1], c[2])[0] for c in cases}
+    outs = [torch.empty(n * (n - 1) // 2, dtype=torch.float64, device="cuda") for _ in range(40)]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for i, o in enumerate(outs):
+            m, a, p = cases[i % len(cases)]
+            uf.uf_compute(tree, table, m, a, p, out=o)
+    s.synchronize()
+    for i, o in enumerate(outs):
+        np.testing.assert_array_equal(o.cpu().numpy(), expect[cases[i % len(cases)]])
+
+
 def test_autotuned_chunk_sizes():
     tree_s = yule_tree(3000, seed=92)
     table_s = table_iid(200, tree_s.n_tips, 0.03, seed=93)

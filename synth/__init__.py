@@ -251,7 +251,8 @@ WORKLOADS = {
 
 
 def _cache_dir() -> str:
-    d = os.environ.get("UF_SYNTH_CACHE", "/tmp/uf_synth_cache")
+    # generated workloads are cached beside this module (UF_SYNTH_CACHE overrides)
+    d = os.environ.get("UF_SYNTH_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), "_cache"))
     os.makedirs(d, exist_ok=True)
     return d
 

@@ -46,18 +46,29 @@ def stitch_condensed(n: int, ranges, parts) -> np.ndarray:
 
 def gather_and_stitch(dist, n: int, ranges, local_part) -> np.ndarray | None:
     """All ranks send their stripe-major part; rank 0 returns the stitched
-    condensed matrix (the one collective of a sharded run), others None."""
+    condensed matrix (the one collective of a sharded run), others None.
+
+    local_part is a numpy array or a torch tensor (a device output of
+    uf_compute may be passed as it is).  With the NCCL backend the parts
+    travel as CUDA tensors on the current device; with gloo, as host tensors."""
     import torch
     rank, world = dist.get_rank(), dist.get_world_size()
-    t = torch.as_tensor(np.ascontiguousarray(local_part, dtype=np.float64).ravel())
+    nccl = str(dist.get_backend()).lower() == "nccl"
+    dev = torch.device("cuda", torch.cuda.current_device()) if nccl else torch.device("cpu")
+    if isinstance(local_part, torch.Tensor):
+        t = local_part.reshape(-1).to(device=dev, dtype=torch.float64)
+    else:
+        t = torch.as_tensor(np.ascontiguousarray(local_part, dtype=np.float64).ravel()).to(dev)
     sizes = [(stop - start) * n for start, stop in ranges]
+    if t.numel() != sizes[rank]:
+        raise ValueError(f"rank {rank}: part has {t.numel()} values, its stripe range {sizes[rank]}")
     if rank == 0:
-        bufs = [torch.empty(sz, dtype=torch.float64) for sz in sizes]
+        bufs = [torch.empty(sz, dtype=torch.float64, device=dev) for sz in sizes]
         bufs[0].copy_(t)
         for r in range(1, world):
             if sizes[r]:
                 dist.recv(bufs[r], src=r)
-        return stitch_condensed(n, ranges, [b.numpy() for b in bufs])
+        return stitch_condensed(n, ranges, [b.cpu().numpy() for b in bufs])
     if sizes[rank]:
         dist.send(t, dst=0)
     return None

@@ -40,7 +40,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, n, q):
+def _rank_main(rank, world, port, n, q, as_tensor=False):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     import torch.distributed as dist
 
@@ -54,6 +54,9 @@ def _rank_main(rank, world, port, n, q):
         ranges = stripe_ranges(n // 2, world)
         a, b = ranges[rank]
         part = oracle.striped(tree, table, "unweighted", 1.0, a, b)[2]
+        if as_tensor:  # a torch tensor part (as a device output would be), here on the host
+            import torch
+            part = torch.as_tensor(np.ascontiguousarray(part))
         out = gather_and_stitch(dist, n, ranges, part)
         if rank == 0:
             exp = oracle.condensed(tree, table, "unweighted", 1.0)
@@ -62,13 +65,13 @@ def _rank_main(rank, world, port, n, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("n", [11, 12])
-def test_two_rank_gloo_gather(n):
+@pytest.mark.parametrize("n,as_tensor", [(11, False), (12, False), (12, True)])
+def test_two_rank_gloo_gather(n, as_tensor):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, n, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, n, q, as_tensor)) for r in range(2)]
     for p in procs:
         p.start()
     for p in procs:

@@ -47,14 +47,21 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
     R.lists = regions;
     // list mode keeps only sort keys in shared memory: longer runs fit
     const int64_t max_entries = regions ? SPARSE_LIST_MAX_ENTRIES : SPARSE_MAX_ENTRIES;
-    const double atom_rate = cells * 8.0 * n_acc <= 64e6 || regions ? 2.3e11 : 2.5e10;
+    // the scatter runs table by table (its grid's y is the table), so each
+    // table's atomics hit L2 when that table's accumulators fit there
+    std::vector<double> pair_cost(nt), entry_cost(nt);
     const double n_regions = regions ? sparse_regions(nt, acc, cells * 8.0 * n_acc) : 1.0;
     double dense_rate;  // cell updates per second of the dense kernel
     if (acc == SPLIT_GRAM) dense_rate = 2.5e14;
     else dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
     const double visit_rate = fp32 ? 2e12 : (acc == ACC_GEN ? 3e10 : 1e12);
     const double job_cost = 5e-10;
-    const double pair_cost = 1.0 / visit_rate + n_acc / atom_rate, entry_cost = 4.0 / atom_rate;
+    for (size_t t = 0; t < nt; t++) {
+      const double n = (double)J.tabs[t].table->n;
+      const double atom_rate = std::floor(n / 2.0) * n * 8.0 * n_acc <= 64e6 || regions ? 2.3e11 : 2.5e10;
+      pair_cost[t] = 1.0 / visit_rate + n_acc / atom_rate;
+      entry_cost[t] = 4.0 / atom_rate;
+    }
     // a dense row also costs its count row and embedding (or planes) in HBM
     const double dense_t = cells / dense_rate + cols * 36.0 / 6e12;
     // node ranges in parallel; each class list is the ranges' lists in order,
@@ -89,7 +96,7 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
           if (ub == 0) continue;
           const double pr = (double)ub * (double)(ub - 1) / 2.0;
           pairs += pr;
-          cost += job_cost + pr * pair_cost + (double)ub * entry_cost;
+          cost += job_cost + pr * pair_cost[t] + (double)ub * entry_cost[t];
           if (regions) cost += n_regions * (job_cost + (double)ub * 4e-11);  // one visit per region
         }
         if (mx > max_entries) continue;

@@ -79,7 +79,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         with open(vs, "w") as fh:
             fh.write("{ global: uf_*; local: *; };\n")
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static",
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-ldl",
              "-Xlinker", f"--version-script={vs}"])
         os.replace(tmp, LIB)
     return LIB

@@ -529,8 +529,14 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   const int n_tiles = (int)tile_bi.size();
   const int64_t nb = tree->n_nodes - 1;
   const int64_t rows = block_rows(nb, (double)n_cols + 4.0 * npad_tot * 2.0 + 8.0, (double)gt_cells * 8.0);
-  Inputs in = bind_inputs(tree, J, device, rows);
-  const std::shared_ptr<const RowSplit> split_p = get_split(tree, J, in.P, SPLIT_GRAM, true);
+  Inputs in = [&] {
+    NvtxRange r("uf: bind inputs");
+    return bind_inputs(tree, J, device, rows);
+  }();
+  const std::shared_ptr<const RowSplit> split_p = [&] {
+    NvtxRange r("uf: branch split");
+    return get_split(tree, J, in.P, SPLIT_GRAM, true);
+  }();
   const RowSplit &split = *split_p;
   const int64_t K_pad = gram_kpad((int)std::max<int64_t>(split.max_dense, 1));
   cudaStream_t st = J.st;
@@ -733,9 +739,15 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const int64_t nb = tree->n_nodes - 1;
   const double acc_bytes = (double)cells * 8.0 * (acc == ACC_GEN ? 2 : 1) + n_cols * 8.0;
   const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + (double)pitch * es + 8.0 + n_cols * es / 64.0, acc_bytes);
-  Inputs in = bind_inputs(tree, J, device, rows);
+  Inputs in = [&] {
+    NvtxRange r("uf: bind inputs");
+    return bind_inputs(tree, J, device, rows);
+  }();
   cudaStream_t st = J.st;
-  const std::shared_ptr<const RowSplit> split_p = get_split(tree, J, in.P, acc, fp32);
+  const std::shared_ptr<const RowSplit> split_p = [&] {
+    NvtxRange r("uf: branch split");
+    return get_split(tree, J, in.P, acc, fp32);
+  }();
   const RowSplit &split = *split_p;
   const int64_t xrows = std::max<int64_t>(split.max_dense, 1);
   int64_t kernels = 0, acc_launches = 0;
@@ -1012,6 +1024,12 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
 
 // One compute call on the current device; throws CudaFail on CUDA errors.
 uf_status run_batch(uf_tree *tree, const BatchJob &J) {
+  static const char *const names[2][4] = {
+      {"uf_compute unweighted fp64", "uf_compute weighted_unnormalized fp64", "uf_compute weighted_normalized fp64",
+       "uf_compute generalized fp64"},
+      {"uf_compute unweighted mixed", "uf_compute weighted_unnormalized mixed",
+       "uf_compute weighted_normalized mixed", "uf_compute generalized mixed"}};
+  NvtxRange call_range(names[J.fp32 ? 1 : 0][(int)J.method & 3]);
   g_h2d = 0.0;
   int device = 0;
   ck(cudaGetDevice(&device), "cudaGetDevice");

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/unifrac_gb300.h"
 #include "uf_internal.h"
@@ -50,6 +51,15 @@ void ck(cudaError_t e, const char *what);
 
 // Host threads for table preparation: the cores this process may run on, at most 16.
 int host_threads();
+
+// An NVTX range for the lifetime of the object: a call and its host phases
+// appear by name on a profiler's timeline (a near no-op without a profiler).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Runs body(0 .. n-1) on the process's host worker pool (host_threads() - 1
 // persistent threads, started on first use) and the calling thread, and

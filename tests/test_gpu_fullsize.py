@@ -6,7 +6,9 @@ CUDA graphs), on outputs the FP64 oracle computes one by one:
   four methods in mixed precision, 1,000 seeded random pairs;
 - 113k-shaped: 500,000-tip Yule tree x 113,000 samples (169 M nonzeros), the
   stripe range [0, 64) for weighted_normalized and unweighted (the
-  workload's methods), 500 seeded random cells of the range.
+  workload's methods), 500 seeded random cells of the range;
+- batched: 64 tables of 200-5,000 samples over one 100,000-tip tree, one
+  batched call per method, 60 seeded pairs of every table.
 
 Generating the 113k-shaped workload takes about two minutes of host time."""
 import numpy as np
@@ -65,3 +67,20 @@ def test_113k_shaped_stripe_range_sample():
         got = out[torch.as_tensor(cells, device="cuda")].cpu().numpy()
         exp = oracle.pairs(tree_s, table_s, method, 1.0, a, b)[0]
         assert_close(got, exp, method, "mixed", "113k-shaped, stripes [0, 64)")
+
+
+def test_batched_64_tables_full_size_pair_subsets():
+    # the batched workload in full (64 tables, 200-5,000 samples, one
+    # 100,000-tip tree), both of its methods in one batched call each; 60
+    # seeded pairs of every table against the oracle
+    from synth import batched_workload
+    tree_s, tables_s = batched_workload()
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    tables = [uf.Table(t.indptr, t.indices, t.data, tree) for t in tables_s]
+    for method in ("unweighted", "weighted_normalized"):
+        outs, _ = uf.uf_compute_batch(tree, tables, method, 1.0, "mixed")
+        for t, (ts, got) in enumerate(zip(tables_s, outs)):
+            n = ts.n_samples
+            i, j = pair_subset(n, 60, seed=12345 + t)
+            exp = oracle.pairs(tree_s, ts, method, 1.0, i, j)[0]
+            assert_close(got[condensed_index(n, i, j)], exp, method, "mixed", f"batched table {t}")

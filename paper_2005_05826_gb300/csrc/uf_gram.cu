@@ -391,7 +391,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// The driver's tensor-map encoder, looked up once (a function-local static
+// The CUDA driver's tensor-map encoder (cuTensorMapEncodeTiled), looked up once (a function-local static
 // initialises exactly once even when several threads call first).
 EncodeTiledFn encode_fn() {
   static const EncodeTiledFn fn = [] {

@@ -181,8 +181,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     rates, used, pairs = [], 1, 0
+    # each step a bounded sample: the whole run stays near two minutes
+    per_step = max(1.0, min(args.ref_seconds, 120.0 / (args.warmup + args.steps)))
     for s in range(args.warmup + args.steps):
-        r, used, pairs, _ = oracle_sample_rate(tree_s, table_s, args.ref_seconds, seed=1000 + s)
+        r, used, pairs, _ = oracle_sample_rate(tree_s, table_s, per_step, seed=1000 + s)
         if s >= args.warmup:
             rates.append(r)
     value = statistics.mean(rates)
@@ -681,7 +683,7 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="yule50k_n2048")

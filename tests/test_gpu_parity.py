@@ -307,3 +307,37 @@ def test_concurrent_calls_from_threads():
     assert not errors, errors
     for j in jobs:
         np.testing.assert_array_equal(got[j], ref[j])
+
+
+def test_degenerate_inputs():
+    # one sample: no pairs, an empty result and UF_OK
+    tree_s = yule_tree(30, seed=120)
+    one = STable.from_dense(np.ones((1, tree_s.n_tips)))
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    t1 = uf.Table(one.indptr, one.indices, one.data, tree)
+    for method in METHODS:
+        for precision in PRECISIONS:
+            got, _ = uf.uf_compute(tree, t1, method, 0.5, precision)
+            assert got.size == 0
+    # a single tip under the root: every sample is the same, every distance 0
+    parent, length = np.array([1, -1]), np.array([0.7, 0.0])
+    single = uf.Tree(parent, length)
+    rng = np.random.default_rng(121)
+    tab_s = STable.from_dense(rng.integers(1, 9, size=(7, 1)).astype(np.float64))
+    t7 = uf.Table(tab_s.indptr, tab_s.indices, tab_s.data, single)
+    for method in METHODS:
+        for precision in PRECISIONS:
+            got, _ = uf.uf_compute(single, t7, method, 0.5, precision)
+            np.testing.assert_array_equal(got, np.zeros(21))
+    # every branch length zero: den = 0 everywhere, so every distance is 0
+    zero_s = yule_tree(40, seed=122)
+    zero_s.length[:] = 0.0
+    ztab = table_iid(12, zero_s.n_tips, 0.3, seed=123)
+    zt = uf.Tree(zero_s.parent, zero_s.length)
+    ztable = uf.Table(ztab.indptr, ztab.indices, ztab.data, zt)
+    for method in METHODS:
+        exp = oracle.condensed(zero_s, ztab, method, 0.5)
+        assert not exp.any()
+        for precision in PRECISIONS:
+            got, _ = uf.uf_compute(zt, ztable, method, 0.5, precision)
+            np.testing.assert_array_equal(got, exp)

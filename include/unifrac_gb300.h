@@ -135,8 +135,9 @@ typedef struct {
  *                    when a cost model of the two kernels says that is
  *                    faster; 0: every branch through the dense kernels;
  *                    2: every branch that can be scattered is (subtree with
- *                    at most 4,096 entries per table and contiguous tip
- *                    numbers).  Applies to the CUDA-core stripe kernels and
+ *                    at most 4,096 entries per table, 16,384 when one table's
+ *                    accumulators are scattered region by region, and
+ *                    contiguous tip numbers).  Applies to the CUDA-core stripe kernels and
  *                    to the tensor-core unweighted path; the results agree
  *                    within the precision's tolerance.
  *   "sparse_overlap" 1 (default): the sparse-row scatter runs on a second

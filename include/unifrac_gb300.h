@@ -48,7 +48,7 @@ typedef enum {
     UF_ETREE = 2,      /* malformed tree (see uf_tree_create) */
     UF_ETABLE = 3,     /* malformed table or table / tree mismatch (see uf_table_create) */
     UF_ERANGE = 4,     /* stripe range outside [0, uf_stripe_count(n)] or start > stop */
-    UF_ENOMEM = 5,     /* host or device allocation failed */
+    UF_ENOMEM = 5,     /* host or device allocation failed, or another host resource ran out */
     UF_ECUDA = 6,      /* a CUDA call failed (no device, launch error, ...) */
     UF_ETIMEOUT = 7,   /* a bounded device wait ran out */
     UF_ECANCELLED = 8  /* reserved: the call was cancelled */

@@ -61,8 +61,14 @@ struct Pool {
   bool stop = false;
   pid_t pid = getpid();
 
+  // Starts up to n_workers threads; if the system refuses one, the pool keeps
+  // those it has (possibly none: run_parallel then runs on the caller alone).
   explicit Pool(int n_workers) {
-    for (int i = 0; i < n_workers; i++) workers.emplace_back([this] { work(); });
+    try {
+      workers.reserve(n_workers);
+      for (int i = 0; i < n_workers; i++) workers.emplace_back([this] { work(); });
+    } catch (const std::exception &) {
+    }
   }
   ~Pool() {
     {
@@ -528,6 +534,8 @@ uf_status uf_tree_create(int64_t n_nodes, const int64_t *parent, const double *l
     return UF_OK;
   } catch (const std::bad_alloc &) {
     return fail(UF_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(UF_ENOMEM, "host resources: %s", e.what());
   }
 }
 
@@ -650,8 +658,8 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
     return UF_OK;
   } catch (const std::bad_alloc &) {
     return fail(UF_ENOMEM, "host allocation failed");
-  } catch (const std::system_error &) {
-    return fail(UF_ENOMEM, "could not start host threads");
+  } catch (const std::exception &e) {
+    return fail(UF_ENOMEM, "host resources: %s", e.what());
   }
 }
 
@@ -684,6 +692,8 @@ uf_status uf_compute(const uf_tree *tree, const uf_table *table, uf_method metho
     return f.st;
   } catch (const std::bad_alloc &) {
     return fail(UF_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(UF_ENOMEM, "host resources: %s", e.what());
   }
 }
 
@@ -715,6 +725,8 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
     return f.st;
   } catch (const std::bad_alloc &) {
     return fail(UF_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(UF_ENOMEM, "host resources: %s", e.what());
   }
 }
 

@@ -33,7 +33,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "../../include/unifrac_gb300.h"
@@ -85,13 +87,10 @@ uf_status noalloc_fail(uf_status st, const char *msg) { return ufg::set_last_err
 }  // namespace
 
 // (the CUDA sources build with hidden visibility; the ABI entry point is exported)
-extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
-                                         const uf_tree *tree, const uf_table *table,
-                                         uf_method method, double alpha,
-                                         uf_precision precision, double *out_device,
-                                         void *cuda_stream) {
+namespace {
+uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method method, double alpha,
+                          uf_precision precision, double *out_device, void *cuda_stream) {
   using namespace ufg;
-  set_last_error(UF_OK, "");
   TreeView tv;
   TableView xv;
   if (!tree_host_view(tree, &tv) || !table_host_view(table, &xv))
@@ -283,4 +282,22 @@ extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
   UF_TRY(cudaStreamSynchronize(st));
 #undef UF_TRY
   return UF_OK;
+}
+}  // namespace
+
+extern "C" __attribute__((visibility("default"))) uf_status uf_compute_noalloc(
+                                         const uf_tree *tree, const uf_table *table,
+                                         uf_method method, double alpha,
+                                         uf_precision precision, double *out_device,
+                                         void *cuda_stream) {
+  ufg::set_last_error(UF_OK, "");
+  try {
+    return compute_noalloc(tree, table, method, alpha, precision, out_device, cuda_stream);
+  } catch (const std::bad_alloc &) {
+    return noalloc_fail(UF_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    char msg[300];
+    snprintf(msg, sizeof msg, "host resources: %s", e.what());
+    return noalloc_fail(UF_ENOMEM, msg);
+  }
 }

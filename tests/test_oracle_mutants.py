@@ -36,7 +36,7 @@ MUTANTS = {
 
 CHECKS = [pins.check_two_tip, pins.check_three_tip, pins.check_star_textbook,
           pins.check_path_enumeration, pins.check_hand_small, pins.check_invariants,
-          pins.check_structural, pins.check_zero_lengths]
+          pins.check_structural, pins.check_zero_lengths, pins.check_earth_movers]
 
 
 def _run_checks(lib):

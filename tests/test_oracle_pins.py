@@ -2,7 +2,8 @@
 
 Every check here is independent of ``oracle/uf_oracle.c``'s own code:
 closed forms on two- and three-tip trees, textbook distances that UniFrac
-reduces to on star trees, an independent root-path enumeration, hand-worked
+reduces to on star trees, an independent root-path enumeration, weighted
+unnormalized as an earth mover's distance (a transport LP), hand-worked
 values (tests/golden/hand_small.txt) and invariants of the metric family.
 The definitions are those of the paper's refs [1] and [3] (Sec. 1); the
 paper prints no formula, so the readings are stated in the oracle header.
@@ -256,6 +257,78 @@ def check_path_enumeration(lib=None, seed=4, cases=12):
 
 def test_path_enumeration_matches():
     check_path_enumeration()
+
+
+# ----------------------------------------------------- earth mover's distance
+
+def tip_path_distances(tree):
+    """Path length between every two tips: the smallest sum of the two climbs
+    to a common ancestor (the lowest one; ties only through zero lengths).
+    A climb from u adds the length of the branch above each node it leaves,
+    so the root's length never enters."""
+    n = tree.n_nodes
+    has_child = np.zeros(n, bool)
+    has_child[tree.parent[:-1]] = True
+    tips = np.nonzero(~has_child)[0]
+    climbs = []
+    for u in tips:
+        up, d, v = {int(u): 0.0}, 0.0, int(u)
+        while tree.parent[v] != -1:
+            d += tree.length[v]
+            v = int(tree.parent[v])
+            up[v] = d
+        climbs.append(up)
+    T = len(tips)
+    D = np.zeros((T, T))
+    for f in range(T):
+        for g in range(T):
+            common = climbs[f].keys() & climbs[g].keys()
+            D[f, g] = min(climbs[f][a] + climbs[g][a] for a in common)
+    return D
+
+
+def earth_movers(D, p, q):
+    """Earth mover's distance between tip distributions p and q under the
+    ground distance D: the cheapest transport plan, as a linear program."""
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    src, dst = np.nonzero(p)[0], np.nonzero(q)[0]
+    a, b = len(src), len(dst)
+    A = np.zeros((a + b, a * b))
+    for r in range(a):
+        A[r, r * b:(r + 1) * b] = 1.0      # all of p[src[r]] leaves
+    for c in range(b):
+        A[a + c, c::b] = 1.0               # all of q[dst[c]] arrives
+    res = linprog(D[np.ix_(src, dst)].ravel(), A_eq=A, b_eq=np.concatenate([p[src], q[dst]]),
+                  bounds=(0, None), method="highs")
+    assert res.status == 0, res.message
+    return res.fun
+
+
+def check_earth_movers(lib=None, seed=8, cases=10):
+    # weighted unnormalized UniFrac is the earth mover's distance between the
+    # two samples' relative abundances over the tips, with path length on the
+    # tree as the ground distance: a transport LP with no tree walk at all
+    rng = np.random.default_rng(seed)
+    for c in range(cases):
+        tree = random_small_tree(rng, int(rng.integers(2, 12)), unary=int(rng.integers(0, 3)),
+                                 zero_len=int(rng.integers(0, 3)))
+        f = tree.n_tips
+        counts = rng.integers(1, 9, size=(4, f)).astype(float) * (rng.random((4, f)) < 0.5)
+        for k in range(4):
+            if counts[k].sum() == 0:
+                counts[k, rng.integers(f)] = 1.0
+        table = Table.from_dense(counts)
+        P = counts / counts.sum(axis=1, keepdims=True)
+        D = tip_path_distances(tree)
+        ii, jj = np.triu_indices(4, 1)
+        got = oracle.pairs(tree, table, "weighted_unnormalized", 0.0, ii, jj, lib=lib)[0]
+        for g, a, b in zip(got, ii, jj):
+            exp = earth_movers(D, P[a], P[b])
+            assert g == pytest.approx(exp, rel=1e-8, abs=1e-10), (c, a, b, g, exp)
+
+
+def test_earth_movers_distance():
+    check_earth_movers()
 
 
 # ------------------------------------------------------------- hand-worked

@@ -31,7 +31,8 @@
  *   - inputs are copied: the caller keeps ownership of every pointer it
  *     passes and may free it when the call returns;
  *   - sizes and indices are int64_t; node and sample counts are limited to
- *     2^31 - 1.
+ *     2^31 - 1, and one compute call to 2^30 samples (summed over the
+ *     tables of a batch; more is UF_EINVAL).
  */
 #ifndef UNIFRAC_GB300_H
 #define UNIFRAC_GB300_H

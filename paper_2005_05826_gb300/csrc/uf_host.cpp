@@ -330,6 +330,11 @@ double accum_bound(uf_tree *tree, uf_table *table, int kind) {
   return kind == EMB_PRESENCE ? pres : 4.0 * pres;
 }
 
+// Samples one compute call may hold on its combined sample axis (summed over
+// a batch's tables): column numbers, a table's n + S and the axis length stay
+// below 2^31 in the kernels' 32-bit index arithmetic.
+constexpr int64_t MAX_CALL_SAMPLES = int64_t(1) << 30;
+
 uf_status check_args(const uf_tree *tree, const uf_table *table, uf_method method, double alpha,
                      uf_precision precision) {
   if (!tree || !table) return fail(UF_EINVAL, "null tree or table");
@@ -672,6 +677,8 @@ uf_status uf_compute(const uf_tree *tree, const uf_table *table, uf_method metho
   g_err.clear();
   uf_status st = check_args(tree, table, method, alpha, precision);
   if (st) return st;
+  if (table->n > MAX_CALL_SAMPLES)
+    return fail(UF_EINVAL, "%lld samples: a compute call takes at most 2^30", (long long)table->n);
   const int64_t S = uf_stripe_count(table->n);
   if (stripe_start < 0 || stripe_stop < stripe_start || stripe_stop > S)
     return fail(UF_ERANGE, "stripe range [%lld, %lld) outside [0, %lld]", (long long)stripe_start,
@@ -704,6 +711,7 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
   g_err.clear();
   if (!tables || !outs || n_tables < 0) return fail(UF_EINVAL, "null tables or outputs");
   BatchJob J{method, alpha, precision == UF_MIXED, out_is_device, 0, (cudaStream_t)cuda_stream, {}};
+  int64_t n_axis = 0;
   for (int64_t t = 0; t < n_tables; t++) {
     uf_status st = check_args(tree, tables[t], method, alpha, precision);
     if (st) return st;
@@ -711,6 +719,10 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
     const int64_t S = uf_stripe_count(tables[t]->n);
     if (S == 0) continue;  // fewer than two samples: nothing to write
     if (!outs[t]) return fail(UF_EINVAL, "null output buffer for table %lld", (long long)t);
+    n_axis += tables[t]->n;
+    if (n_axis > MAX_CALL_SAMPLES)
+      return fail(UF_EINVAL, "tables 0..%lld hold %lld samples: a compute call takes at most 2^30",
+                  (long long)t, (long long)n_axis);
     J.tabs.push_back(TableJob{const_cast<uf_table *>(tables[t]), 0, S, outs[t], reps ? &reps[t] : nullptr});
   }
   if (J.tabs.empty()) return UF_OK;

@@ -123,6 +123,24 @@ def test_compute_argument_errors():
     assert _code(lambda: uf.uf_compute(tree, t_other, "unweighted")) == "UF_ETABLE"
 
 
+def test_call_sample_cap():
+    # one compute call takes at most 2^30 samples on its combined axis: 1,025
+    # copies of a 2^20-sample table are rejected before any device work (the
+    # output pointers are never written)
+    import ctypes
+    n = 1 << 20
+    tree = uf.Tree(np.array([2, 2, -1], np.int64), np.array([1.0, 2.0, 0.0]))
+    table = uf.Table(np.arange(n + 1, dtype=np.int64), np.zeros(n, np.int32), np.ones(n), tree)
+    lib = uf.load()
+    nt = 1025
+    dummy = np.zeros(1)
+    handles = (ctypes.c_void_p * nt)(*([table.handle.value] * nt))
+    outs = (ctypes.c_void_p * nt)(*([dummy.ctypes.data] * nt))
+    st = lib.uf_compute_batch(tree.handle, handles, nt, 2, 1.0, 1, outs, 0, None, None)
+    assert lib.uf_status_name(st).decode() == "UF_EINVAL"
+    assert "2^30" in uf.uf_last_error()
+
+
 def test_no_cpu_fallback():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

@@ -53,7 +53,7 @@ def _rank_main(rank, world, port, n, q, as_tensor=False):
         table = table_iid(n, tree.n_tips, 0.25, seed=83)
         ranges = stripe_ranges(n // 2, world)
         a, b = ranges[rank]
-        part = oracle.striped(tree, table, "unweighted", 1.0, a, b)[2]
+        part = oracle.striped(tree, table, "unweighted", 1.0, a, b)[2] if b > a else np.zeros(0)
         if as_tensor:  # a torch tensor part (as a device output would be), here on the host
             import torch
             part = torch.as_tensor(np.ascontiguousarray(part))
@@ -72,6 +72,22 @@ def test_two_rank_gloo_gather(n, as_tensor):
     q = ctx.Queue()
     port = _free_port()
     procs = [ctx.Process(target=_rank_main, args=(r, 2, port, n, q, as_tensor)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    assert q.get(timeout=5) <= 1e-14
+
+
+def test_three_rank_gloo_gather_with_an_empty_range():
+    # n = 4 has two stripes: the third rank's range is empty and it sends nothing
+    import multiprocessing as mp
+    assert stripe_ranges(2, 3)[2] == (2, 2)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 3, port, 4, q)) for r in range(3)]
     for p in procs:
         p.start()
     for p in procs:

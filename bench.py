@@ -533,7 +533,7 @@ def run_ours(args, rank, world, local_rank):
     # stream with device outputs (each call's host work overlaps the previous
     # call's kernels), then every result read back into pinned host memory ----
     e2e = None
-    if rank == 0 and not args.no_e2e:
+    if not args.no_e2e:  # every rank: the job's end-to-end rate at N GPUs
         uf.uf_set_option("kernel_timing", 0)
         host_res = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
         # pageable result arrays of the host-output variant, allocated (and first
@@ -543,6 +543,8 @@ def run_ours(args, rank, world, local_rank):
 
         def e2e_step(sync_host):
             torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
             t0 = time.perf_counter()
             tr = uf.Tree(tree_s.parent, tree_s.length)
             tb = uf.Table(table_s.indptr, table_s.indices, table_s.data, tr)
@@ -572,13 +574,19 @@ def run_ours(args, rank, world, local_rank):
                 dt, h2d, d2h = e2e_step(mode)
                 if s > 0:  # the first is a warm-up
                     e_times.append(dt)
-            res[mode] = (statistics.mean(e_times), h2d, d2h)
+            t_mode = statistics.mean(e_times)
+            if dist:  # the slowest rank's step time; bytes of all ranks
+                t = torch.tensor([t_mode], dtype=torch.float64, device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                t_mode = float(t.item())
+            res[mode] = (t_mode, world * h2d, world * d2h)
         t_e, h2d, d2h = res[False]
-        e2e = {"value": updates_step / t_e, "unit": "updates/s",
+        e2e = {"value": world * updates_step / t_e, "unit": "updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e,
                "path": "fresh tree and table handles from the host arrays, four uf_compute calls queued on "
                        "the stream with device outputs, results read into pinned host memory",
-               "host_output_calls": {"value": updates_step / res[True][0], "ms_per_step": 1e3 * res[True][0],
+               "host_output_calls": {"value": world * updates_step / res[True][0],
+                                     "ms_per_step": 1e3 * res[True][0],
                                      "d2h_bytes_per_step": int(res[True][2]),
                                      "path": "the same with pageable host result arrays the caller reuses "
                                              "(each call returns synchronously)"}}

@@ -176,10 +176,10 @@ def oracle_sample_rate(tree_s, table_s, target_seconds: float, seed: int = 99):
 
 
 def run_reference(args, rank, world):
+    if rank != 0:  # rank 0 alone times the oracle; the others exit without work
+        return 0
     from synth import workload
     tree_s, table_s = workload(args.workload)
-    if rank != 0:
-        return 0
     rates, used, pairs = [], 1, 0
     # each step a bounded sample: the whole run stays near two minutes
     per_step = max(1.0, min(args.ref_seconds, 120.0 / (args.warmup + args.steps)))

@@ -38,6 +38,31 @@ def test_exports_every_declared_symbol():
         assert hasattr(lib, name), f"{name} declared but not exported"
 
 
+def test_report_layout_matches_header(tmp_path):
+    # the binding's ctypes Report has the size and field offsets of the C
+    # uf_report: a small C program built against the header prints them
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [name for name, _ in uf.Report._fields_]
+    src = ["#include <stddef.h>", "#include <stdio.h>", '#include "unifrac_gb300.h"', "int main(void) {",
+           '  printf("size %zu\\n", sizeof(uf_report));']
+    src += [f'  printf("{f} %zu\\n", offsetof(uf_report, {f}));' for f in fields]
+    src += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    import ctypes
+    assert int(got["size"]) == ctypes.sizeof(uf.Report)
+    for f in fields:
+        assert int(got[f]) == getattr(uf.Report, f).offset, f
+
+
 def test_stripe_count():
     assert [uf.uf_stripe_count(n) for n in (0, 1, 2, 3, 4, 5, 64, 65)] == [0, 0, 1, 1, 2, 2, 32, 32]
 

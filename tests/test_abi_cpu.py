@@ -63,6 +63,20 @@ def test_report_layout_matches_header(tmp_path):
         assert int(got[f]) == getattr(uf.Report, f).offset, f
 
 
+def test_enum_values_match_header():
+    # the binding's method, precision and status numbers are the header's
+    text = open(os.path.join(ROOT, "include", "unifrac_gb300.h")).read()
+    vals = {k: int(v) for k, v in re.findall(r"\b(UF_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    for name, code in uf.METHODS.items():
+        assert vals["UF_" + name.upper()] == code, name
+    for name, code in uf.PRECISIONS.items():
+        assert vals["UF_" + name.upper()] == code, name
+    lib = uf.load()
+    for code, name in uf.STATUS.items():
+        assert vals[name] == code, name
+        assert lib.uf_status_name(code).decode() == name
+
+
 def test_stripe_count():
     assert [uf.uf_stripe_count(n) for n in (0, 1, 2, 3, 4, 5, 64, 65)] == [0, 0, 1, 1, 2, 2, 32, 32]
 

@@ -77,6 +77,40 @@ def test_enum_values_match_header():
         assert lib.uf_status_name(code).decode() == name
 
 
+OPTIONS = {  # name: (default, accepted values, rejected values)
+    "branch_block": (0, [1, 4096, 0], [-1]),
+    "kernel_timing": (0, [1, 0], [-1, 2]),
+    "tensor_path": (1, [0, 1], [-1, 2]),
+    "graph": (1, [0, 1], [-1, 2]),
+    "autotune": (1, [0, 1], [-1, 3]),
+    "sparse": (1, [0, 2, 1], [-1, 3]),
+    "sparse_overlap": (1, [0, 1], [-1, 2]),
+    "tensor_wait_test": (0, [1, 0], [-1, 2]),
+    "sparse_region_bytes": (48_000_000, [4096, 10**9, 48_000_000], [1, 4095, -5]),
+}
+
+
+def test_options():
+    header = open(os.path.join(ROOT, "include", "unifrac_gb300.h")).read()
+    for name, (default, good, bad) in OPTIONS.items():
+        assert f'"{name}"' in header, f"option {name} not documented"
+        assert uf.uf_get_option(name) == default, name
+        for v in good:
+            uf.uf_set_option(name, v)
+            assert uf.uf_get_option(name) == v, (name, v)
+        for v in bad:
+            assert _code(lambda: uf.uf_set_option(name, v)) == "UF_EINVAL", (name, v)
+            assert uf.uf_get_option(name) == good[-1], (name, v)
+        uf.uf_set_option(name, default)
+    # autotune 2 forgets the tuned chunk sizes and reads back as 1; region bytes 0 is the default
+    uf.uf_set_option("autotune", 2)
+    assert uf.uf_get_option("autotune") == 1
+    uf.uf_set_option("sparse_region_bytes", 0)
+    assert uf.uf_get_option("sparse_region_bytes") == 48_000_000
+    assert _code(lambda: uf.uf_set_option("no_such_option", 1)) == "UF_EINVAL"
+    assert uf.uf_get_option("no_such_option") == -1
+
+
 def test_stripe_count():
     assert [uf.uf_stripe_count(n) for n in (0, 1, 2, 3, 4, 5, 64, 65)] == [0, 0, 1, 1, 2, 2, 32, 32]
 

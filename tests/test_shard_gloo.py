@@ -20,15 +20,18 @@ def test_stripe_ranges_cover_and_balance():
             assert max(sizes) - min(sizes) <= 1
 
 
-@pytest.mark.parametrize("n", [9, 10])
-def test_stitch_equals_full_oracle(n):
+@pytest.mark.parametrize("world", [1, 2, 3, 5])
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 9, 10, 13])
+def test_stitch_equals_full_oracle(n, world):
+    # every rank count, including ranks whose stripe range is empty (world > S)
     import oracle
     from synth import table_iid, yule_tree
     tree = yule_tree(30, seed=80)
     table = table_iid(n, tree.n_tips, 0.3, seed=81)
     S = n // 2
-    ranges = stripe_ranges(S, 3)
-    parts = [oracle.striped(tree, table, "weighted_normalized", 1.0, a, b)[2] for a, b in ranges]
+    ranges = stripe_ranges(S, world)
+    parts = [oracle.striped(tree, table, "weighted_normalized", 1.0, a, b)[2] if b > a else np.zeros(0)
+             for a, b in ranges]
     got = stitch_condensed(n, ranges, parts)
     exp = oracle.condensed(tree, table, "weighted_normalized", 1.0)
     np.testing.assert_allclose(got, exp, rtol=1e-13, atol=1e-15)

@@ -9,8 +9,10 @@ accumulate, diagonal, finalize) for each of the four methods (unweighted,
 weighted_unnormalized, weighted_normalized, generalized alpha = 0.5) over
 all stripes.  ``value`` is pair x branch updates per second of the mixed
 path with inputs resident on the GPU; the FP64 path is measured beside it,
-and both report their max error against the FP64 oracle on a seeded
-10,000-pair subset.
+and the mixed result's largest difference from the FP64 result is reported
+over every value (parity of both paths with the FP64 oracle is the tests'
+job).  The oracle runs here only as the CPU baseline and as the reference
+arm.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -216,31 +218,17 @@ def workload_config(args, tree_s, table_s, l2):
             "sparse_region_bytes": getattr(args, "region_bytes", 0) or "default", "l2": l2}
 
 
-def max_errors(tree_s, table_s, outs, precision, stop=None):
-    """Max error of each method's result against the oracle on the seeded
-    10,000-pair subset (abs for mixed, rel for fp64); for a stripe-range run
-    [0, stop), on 10,000 seeded cells (s, k) of the range, pair (k, (k+s+1) mod n).
-    `outs` are the device outputs; only the sampled values are read back."""
-    import oracle
-    import torch
-    from synth import pair_subset
-    n = table_s.n_samples
-    if stop is None or stop >= n // 2:
-        i, j = pair_subset(n, 10_000, seed=12345)
-        idx = n * i - i * (i + 1) // 2 + (j - i - 1)
-    else:
-        cells = np.random.default_rng(12345).choice(stop * n, size=min(10_000, stop * n), replace=False)
-        s_, k_ = cells // n, cells % n
-        i, j = k_, (k_ + s_ + 1) % n
-        idx = cells
+def max_err_vs_fp64(mixed_outs, fp64_outs):
+    """Largest difference of each method's mixed-precision result from the
+    FP64 GPU path, over every value of the matrix: absolute, and scaled by
+    max(1, |d|) as the unbounded unnormalized method's tolerance is.  (Parity
+    of both paths with the FP64 oracle is checked by the tests.)"""
     res = {}
-    for (m, a), out in zip(METHODS, outs):
-        exp = oracle.pairs(tree_s, table_s, m, a, i, j)[0]
-        g = out[torch.as_tensor(idx, device=out.device)].double().cpu().numpy()
-        abs_err = float(np.max(np.abs(g - exp)))
-        rel = np.abs(g - exp) / np.maximum(np.abs(exp), 1e-300)
-        rel[(exp == 0) & (g == 0)] = 0.0
-        res[m] = {"max_abs": abs_err, "max_rel": float(np.max(rel))}
+    for (m, _), d32, d64 in zip(METHODS, mixed_outs, fp64_outs):
+        diff = np.abs(d32 - d64)
+        res[m] = {"max_abs": float(diff.max()) if diff.size else 0.0,
+                  "max_scaled": float((diff / np.maximum(1.0, np.abs(d64))).max()) if diff.size else 0.0,
+                  "values": int(diff.size)}
     return res
 
 
@@ -458,9 +446,9 @@ def run_ours(args, rank, world, local_rank):
         t_total = float(t.item())
     updates_step = len(METHODS) * npairs * branches
     value = world * updates_step * args.steps / t_total
-    mixed_err = {} if args.no_err or rank != 0 else max_errors(tree_s, table_s, outs, "mixed", stop)
+    mixed_err = {}  # filled beside the FP64 path when both whole matrices are on the host
     # whole matrices on the host only where the downstream check wants them
-    keep_host = full and npairs <= 50_000_000 and not args.no_downstream
+    keep_host = full and npairs <= 50_000_000 and not (args.no_downstream and args.no_err)
     mixed_outs = [o.cpu().numpy().astype(np.float64) for o in outs] if keep_host else []
     launches = int(sum(r.kernels for _, r in reps))
 
@@ -644,11 +632,10 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "k_stripe_min<double,8,8>", "bound": "alu", "achieved": ach64,
                 "peak": 0.3125, "unit": "Tupdates/s", "frac": ach64 / 0.3125,
                 "peak_basis": "nominal FP64 1.25 TFLOP/s = 0.625 T instructions/s, 2 per update"}
-        if not args.no_err:
-            fp64["max_err"] = max_errors(tree_s, table_s, outs, "fp64", stop)
-        if keep_host:
+        if keep_host and not args.no_err:
+            mixed_err = max_err_vs_fp64(mixed_outs, fp64_outs)
+        if keep_host and not args.no_downstream:
             fp64["downstream_vs_mixed"] = downstream_agreement(mixed_outs, fp64_outs)
-            fp64["max_rel_err"] = max(v["max_rel"] for v in fp64["max_err"].values())
 
     if rank != 0:
         if dist:
@@ -663,8 +650,8 @@ def run_ours(args, rank, world, local_rank):
         "config": workload_config(args, tree_s, table_s, l2="flushed between steps (256 MB write)"),
         "precision": "mixed: FP32 updates (unweighted: exact 0/1 x split-BF16 lengths on tcgen05, "
                      "FP32 accumulation), int64 fixed-point accumulators, FP64 division",
-        "max_abs_err_vs_oracle": max((v["max_abs"] for v in mixed_err.values()), default=None),
-        "max_err": mixed_err,
+        "max_abs_err_vs_fp64": max((v["max_abs"] for v in mixed_err.values()), default=None),
+        "max_err_vs_fp64": mixed_err or None,
         "updates_basis": "dense-equivalent: every sample pair x every non-root branch per method, "
                          "including the zero terms that the sparse-row path skips",
         "roofline": rl,
@@ -700,7 +687,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--fp64-stripes", type=int, default=0,
                     help="run the FP64 comparison on stripes [0, K) only (large workloads)")
-    ap.add_argument("--no-err", action="store_true", help="skip the max-error check vs the oracle")
+    ap.add_argument("--no-err", action="store_true", help="skip the comparison of the mixed and FP64 results")
     ap.add_argument("--methods", default="all",
                     help="comma list of methods per step (default: all four)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

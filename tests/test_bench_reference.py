@@ -1,10 +1,13 @@
-"""bench.py's reference arm on the CPU: it times the FP64 oracle on a
+"""bench.py on the CPU: the reference arm times the FP64 oracle on a
 bounded pair sample and prints one JSON line with the keys of the bench
-contract; under torchrun, ranks other than 0 exit without output."""
+contract (under torchrun, ranks other than 0 exit without output); the GPU
+arm has no CPU fallback and fails without a GPU."""
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -38,4 +41,15 @@ def test_reference_line():
 def test_reference_other_ranks_print_nothing():
     p = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert p.returncode == 0, p.stderr[-2000:]
+    assert p.stdout.strip() == ""
+
+
+def test_gpu_arm_fails_loudly_without_a_gpu():
+    # no CPU fallback: without a GPU the default arm exits non-zero and prints no line
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    p = subprocess.run([sys.executable, "bench.py", "--steps", "1", "--warmup", "1", "--workload", "yule1k_n64"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert p.returncode != 0
     assert p.stdout.strip() == ""

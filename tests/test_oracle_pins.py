@@ -113,10 +113,16 @@ def check_star_textbook(lib=None, seed=2):
             jaccard = 1.0 - inter / union
             l1 = np.abs(p[i] - p[j]).sum()
             bray = np.abs(counts[i] / counts[i].sum() - counts[j] / counts[j].sum()).sum() / 2.0
+            # Canberra distance of the relative abundances (0/0 terms dropped)
+            both = pres[i] | pres[j]
+            canberra = (np.abs(p[i] - p[j])[both] / (p[i] + p[j])[both]).sum()
             assert _pair(tree, table, "unweighted", 0, i, j, lib) == pytest.approx(jaccard, rel=1e-14, abs=1e-16)
             assert _pair(tree, table, "weighted_unnormalized", 0, i, j, lib) == pytest.approx(l1, rel=1e-13, abs=1e-16)
             assert _pair(tree, table, "weighted_normalized", 0, i, j, lib) == pytest.approx(bray, rel=1e-13, abs=1e-16)
             assert _pair(tree, table, "generalized", 1.0, i, j, lib) == pytest.approx(bray, rel=1e-13, abs=1e-16)
+            # generalized(0) weighs every present branch equally: Canberra over the union's size
+            assert _pair(tree, table, "generalized", 0.0, i, j, lib) == pytest.approx(
+                canberra / union, rel=1e-13, abs=1e-16)
 
 
 def test_star_tree_textbook_distances():
@@ -139,6 +145,9 @@ def test_star_tree_against_scipy():
                 spatial.braycurtis(p[i], p[j]), rel=1e-13)
             assert _pair(tree, table, "weighted_unnormalized", 0, i, j) == pytest.approx(
                 spatial.cityblock(p[i], p[j]), rel=1e-13)
+            union = np.logical_or(counts[i] > 0, counts[j] > 0).sum()
+            assert _pair(tree, table, "generalized", 0.0, i, j) == pytest.approx(
+                spatial.canberra(p[i], p[j]) / union, rel=1e-13)
 
 
 # --------------------------------------------------- independent formulation

@@ -296,6 +296,21 @@ def tip_path_distances(tree):
     return D
 
 
+def has_children(tree):
+    has = np.zeros(tree.n_nodes, bool)
+    has[tree.parent[:-1]] = True
+    return has
+
+
+def tree_depth(tree, u):
+    """Sum of the lengths of the branches from node u up to the root."""
+    d = 0.0
+    while tree.parent[u] != -1:
+        d += tree.length[u]
+        u = int(tree.parent[u])
+    return d
+
+
 def earth_movers(D, p, q):
     """Earth mover's distance between tip distributions p and q under the
     ground distance D: the cheapest transport plan, as a linear program."""
@@ -334,6 +349,12 @@ def check_earth_movers(lib=None, seed=8, cases=10):
         for g, a, b in zip(got, ii, jj):
             exp = earth_movers(D, P[a], P[b])
             assert g == pytest.approx(exp, rel=1e-8, abs=1e-10), (c, a, b, g, exp)
+        # the normalized denominator separates into per-sample terms: each
+        # tip's relative abundance times its depth (its climb to the root)
+        depth = np.array([tree_depth(tree, int(u)) for u in np.nonzero(~has_children(tree))[0]])
+        den = oracle.pairs(tree, table, "weighted_normalized", 0.0, ii, jj, lib=lib)[2]
+        exp = (P[ii] + P[jj]) @ depth
+        assert np.allclose(den, exp, rtol=1e-13, atol=1e-15), (c, den, exp)
 
 
 def test_earth_movers_distance():

@@ -177,6 +177,27 @@ def oracle_sample_rate(tree_s, table_s, target_seconds: float, seed: int = 99):
     return len(METHODS) * i.size * branches / dt, used, int(i.size), dt
 
 
+def oracle_striped_rate(tree_s, table_s, max_updates_per_thread: float = 1.5e9):
+    """The paper's plain striped CPU loop (the oracle's second formulation:
+    FP64, host threads over stripes, every branch in postorder) on the stripe
+    slice [0, k), one stripe per host thread, for the four methods of a step:
+    (updates/s, threads, k, seconds), or None when one stripe of every method
+    is too much work to time within the bench's few minutes."""
+    import oracle
+    n = table_s.n_samples
+    S = n // 2
+    branches = tree_s.n_nodes - 1
+    if S == 0 or len(METHODS) * n * branches > max_updates_per_thread:
+        return None
+    k = min(S, oracle.host_cores())
+    t0 = time.perf_counter()
+    used = 1
+    for m, a in METHODS:
+        used = oracle.striped(tree_s, table_s, m, a, 0, k)[3]
+    dt = time.perf_counter() - t0
+    return len(METHODS) * k * n * branches / dt, used, k, dt
+
+
 def run_reference(args, rank, world):
     if rank != 0:  # rank 0 alone times the oracle; the others exit without work
         return 0
@@ -374,6 +395,13 @@ def run_ours(args, rank, world, local_rank):
         r, used, pairs, dt = oracle_sample_rate(tree_s, table_s, args.cpu_seconds)
         cpu = {"value": r, "unit": "updates/s", "cores": used, "kind": "oracle",
                "sample": f"{pairs} random pairs x 4 methods, {dt:.1f} s (FP64 per-pair tree walk)"}
+        sl = oracle_striped_rate(tree_s, table_s)
+        if sl is not None:
+            r, used, k, dt = sl
+            cpu["striped_loop"] = {
+                "value": r, "unit": "updates/s", "cores": used,
+                "sample": f"stripes [0, {k}) of {n // 2} x 4 methods, {dt:.1f} s (the plain FP64 striped "
+                          f"loop, one stripe per thread; from a slice)"}
 
     tree = uf.Tree(tree_s.parent, tree_s.length)
     table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)

@@ -53,3 +53,16 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
                        cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert p.returncode != 0
     assert p.stdout.strip() == ""
+
+
+def test_striped_loop_rate_on_a_slice():
+    # the plain striped CPU loop of the CPU-baseline leg: one stripe per host
+    # thread on [0, k), all four methods; skipped when a slice is too large
+    import bench
+    import oracle
+    from synth import workload
+    tree_s, table_s = workload("yule1k_n64")
+    rate, used, k, dt = bench.oracle_striped_rate(tree_s, table_s)
+    assert rate > 0 and dt > 0
+    assert k == min(table_s.n_samples // 2, oracle.host_cores()) and used == k
+    assert bench.oracle_striped_rate(tree_s, table_s, max_updates_per_thread=1.0) is None

@@ -17,3 +17,14 @@ def pytest_configure(config):
 def olib():
     import oracle
     return oracle.load()
+
+
+def pytest_terminal_summary(terminalreporter):
+    # the precision report of the GPU parity tests: every comparison with the
+    # FP64 oracle, largest errors per method and precision
+    util = sys.modules.get("tests.gpu_util") or sys.modules.get("gpu_util")
+    if util is None or not getattr(util, "PRECISION_LOG", None):
+        return
+    terminalreporter.section("precision vs the FP64 oracle")
+    for line in util.precision_summary():
+        terminalreporter.write_line(line)

@@ -20,7 +20,42 @@ def tolerance_ok(got, exp, method, precision):
     return np.abs(got - exp) <= MIXED_ATOL * scale
 
 
+# every comparison's errors, for the precision report printed after a run
+# (tests/conftest.py): (what, method, precision, values, max_abs, max_rel, max_scaled)
+PRECISION_LOG = []
+
+
+def record_errors(got, exp, method, precision, what=""):
+    got = np.asarray(got, dtype=np.float64)
+    exp = np.asarray(exp, dtype=np.float64)
+    if got.size == 0:
+        return
+    diff = np.abs(got - exp)
+    rel = diff / np.maximum(np.abs(exp), 1e-300)
+    rel[diff == 0] = 0.0
+    scaled = diff / np.maximum(1.0, np.abs(exp))
+    PRECISION_LOG.append((what, method, precision, int(got.size), float(diff.max()), float(rel.max()),
+                          float(scaled.max())))
+
+
+def precision_summary():
+    """Lines of the precision report: per method and precision, the largest
+    absolute, relative and max(1, |d|)-scaled error over every comparison."""
+    agg = {}
+    for _, method, precision, n, a, r, sc in PRECISION_LOG:
+        v = agg.setdefault((method, precision), [0, 0, 0.0, 0.0, 0.0])
+        v[0] += 1
+        v[1] += n
+        v[2], v[3], v[4] = max(v[2], a), max(v[3], r), max(v[4], sc)
+    lines = [f"{'method':<24}{'precision':<10}{'checks':>7}{'values':>12}{'max abs':>11}{'max rel':>11}"
+             f"{'max scaled':>12}"]
+    for (method, precision), (c, n, a, r, sc) in sorted(agg.items()):
+        lines.append(f"{method:<24}{precision:<10}{c:>7}{n:>12}{a:>11.2e}{r:>11.2e}{sc:>12.2e}")
+    return lines
+
+
 def assert_close(got, exp, method, precision, what=""):
+    record_errors(got, exp, method, precision, what)
     ok = tolerance_ok(got, exp, method, precision)
     if not ok.all():
         bad = np.nonzero(~ok)[0]

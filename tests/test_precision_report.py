@@ -1,0 +1,43 @@
+"""The GPU tests' comparison helper on the CPU: tolerances, and the error
+record behind the precision report printed after a GPU test run."""
+import numpy as np
+import pytest
+
+from tests import gpu_util
+
+
+@pytest.fixture()
+def clean_log():
+    saved = list(gpu_util.PRECISION_LOG)
+    gpu_util.PRECISION_LOG.clear()
+    yield gpu_util.PRECISION_LOG
+    gpu_util.PRECISION_LOG[:] = saved
+
+
+def test_tolerances(clean_log):
+    exp = np.array([0.0, 0.25, 1.0, 40.0])
+    gpu_util.assert_close(exp + 9e-6, exp, "weighted_normalized", "mixed")
+    with pytest.raises(AssertionError):
+        gpu_util.assert_close(exp + 2e-5, exp, "weighted_normalized", "mixed")
+    # the unbounded method's tolerance scales with max(1, |d|)
+    gpu_util.assert_close(exp + np.array([0, 0, 0, 3e-4]), exp, "weighted_unnormalized", "mixed")
+    gpu_util.assert_close(exp * (1 + 5e-11), exp, "generalized", "fp64")
+    with pytest.raises(AssertionError):
+        gpu_util.assert_close(exp * (1 + 5e-10), exp, "generalized", "fp64")
+
+
+def test_error_record_and_summary(clean_log):
+    exp = np.array([0.0, 0.5, 2.0, 0.0])
+    got = exp + np.array([0.0, 1e-7, 4e-6, 0.0])
+    gpu_util.assert_close(got, exp, "weighted_unnormalized", "mixed", "case a")
+    gpu_util.assert_close(got[:2], exp[:2], "weighted_unnormalized", "mixed", "case b")
+    gpu_util.assert_close(np.zeros(0), np.zeros(0), "unweighted", "mixed", "empty")
+    assert len(clean_log) == 2
+    what, method, precision, n, a, r, sc = clean_log[0]
+    assert (what, method, precision, n) == ("case a", "weighted_unnormalized", "mixed", 4)
+    assert a == pytest.approx(4e-6) and r == pytest.approx(2e-6) and sc == pytest.approx(2e-6)
+    lines = gpu_util.precision_summary()
+    assert len(lines) == 2 and lines[0].split()[:2] == ["method", "precision"]
+    row = lines[1].split()
+    assert row[:4] == ["weighted_unnormalized", "mixed", "2", "6"]
+    assert float(row[4]) == pytest.approx(4e-6)

@@ -333,13 +333,23 @@ std::tuple<int, int, int, int> tune_key(int acc, bool fp32, int64_t n_tiles, int
   return {acc, fp32 ? 1 : 0, lg(n_tiles), lg(rows)};
 }
 
+// A timing event destroyed with its scope, also when a CUDA error is thrown.
+struct ScopedEvent {
+  cudaEvent_t e = nullptr;
+  ScopedEvent() { ck(cudaEventCreate(&e), "cudaEventCreate"); }
+  ~ScopedEvent() {
+    if (e) cudaEventDestroy(e);
+  }
+  ScopedEvent(const ScopedEvent &) = delete;
+  ScopedEvent &operator=(const ScopedEvent &) = delete;
+};
+
 // Time the accumulate launch of the first block with each candidate chunk
 // size and keep the fastest (the accumulators are cleared afterwards).
 int tune_chunk(int acc, bool fp32, StripeArgs sa, size_t cells, cudaStream_t st) {
   const int cand[4] = {1024, 2048, 4096, 8192};
-  cudaEvent_t e0, e1;
-  ck(cudaEventCreate(&e0), "cudaEventCreate");
-  ck(cudaEventCreate(&e1), "cudaEventCreate");
+  const ScopedEvent ev0, ev1;
+  cudaEvent_t e0 = ev0.e, e1 = ev1.e;
   int best = stripe_chunk_rows();
   float best_ms = 1e30f;
   for (int c : cand) {
@@ -356,8 +366,6 @@ int tune_chunk(int acc, bool fp32, StripeArgs sa, size_t cells, cudaStream_t st)
       best = c;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   ck(cudaMemsetAsync(sa.M, 0, cells * 8, st), "memset");
   if (sa.M2) ck(cudaMemsetAsync(sa.M2, 0, cells * 8, st), "memset");
   return best;

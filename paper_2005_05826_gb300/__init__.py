@@ -219,6 +219,14 @@ def uf_table_create(indptr, indices, data, tree: Tree, n_features: int | None = 
     return Table(indptr, indices, data, tree, n_features)
 
 
+def _code_of(codes: dict, name: str, what: str) -> int:
+    """The C enum value of a method or precision name."""
+    try:
+        return codes[name]
+    except (KeyError, TypeError):
+        raise ValueError(f"unknown {what} {name!r}; one of {', '.join(codes)}") from None
+
+
 def _out_spec(out, n_values: int, out_fp32: bool):
     """(pointer, is_device, stream, keepalive) for an output buffer."""
     if out is None:
@@ -248,6 +256,7 @@ def uf_compute(tree: Tree, table: Table, method: str, alpha: float = 1.0, precis
     (stop - start) x n stripe-major values.  Returns ``(out, Report)``.
     ``stream`` overrides the stream (an int handle) for device outputs."""
     lib = load()
+    m_code, p_code = _code_of(METHODS, method, "method"), _code_of(PRECISIONS, precision, "precision")
     n = table.n_samples
     S = uf_stripe_count(n)
     stop = S if stripe_stop is None else int(stripe_stop)
@@ -258,8 +267,8 @@ def uf_compute(tree: Tree, table: Table, method: str, alpha: float = 1.0, precis
     if stream is not None:
         st = int(stream)
     rep = Report()
-    _check(lib.uf_compute(tree.handle, table.handle, METHODS[method], float(alpha),
-                          PRECISIONS[precision], start, stop, ctypes.c_void_p(ptr), is_dev,
+    _check(lib.uf_compute(tree.handle, table.handle, m_code, float(alpha),
+                          p_code, start, stop, ctypes.c_void_p(ptr), is_dev,
                           int(bool(out_fp32)), ctypes.byref(rep),
                           ctypes.c_void_p(st) if st else None))
     if out is None and not full:
@@ -272,6 +281,7 @@ def uf_compute_batch(tree: Tree, tables, method: str, alpha: float = 1.0, precis
     """Full-range condensed distances of many tables over one tree.
     Returns ``(outs, reports)``."""
     lib = load()
+    m_code, p_code = _code_of(METHODS, method, "method"), _code_of(PRECISIONS, precision, "precision")
     nt = len(tables)
     if outs is None:
         outs = [None] * nt
@@ -284,8 +294,8 @@ def uf_compute_batch(tree: Tree, tables, method: str, alpha: float = 1.0, precis
     handles = (ctypes.c_void_p * nt)(*[t.handle.value for t in tables])
     ptrs = (ctypes.c_void_p * nt)(*[s[0] for s in specs])
     reps = (Report * max(nt, 1))()
-    _check(lib.uf_compute_batch(tree.handle, handles, nt, METHODS[method], float(alpha),
-                                PRECISIONS[precision], ptrs, is_dev, reps,
+    _check(lib.uf_compute_batch(tree.handle, handles, nt, m_code, float(alpha),
+                                p_code, ptrs, is_dev, reps,
                                 ctypes.c_void_p(int(st)) if st else None))
     return [s[3] for s in specs], [reps[i] for i in range(nt)]
 
@@ -306,7 +316,8 @@ def uf_compute_noalloc(tree: Tree, table: Table, method: str, alpha: float = 1.0
     if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() < need:
         raise ValueError(f"out must be a contiguous float64 tensor with >= {need} elements")
     st = int(stream) if stream is not None else torch.cuda.current_stream(out.device).cuda_stream
-    _check(load().uf_compute_noalloc(tree.handle, table.handle, METHODS[method], float(alpha),
-                                     PRECISIONS[precision], ctypes.c_void_p(out.data_ptr()),
+    m_code, p_code = _code_of(METHODS, method, "method"), _code_of(PRECISIONS, precision, "precision")
+    _check(load().uf_compute_noalloc(tree.handle, table.handle, m_code, float(alpha),
+                                     p_code, ctypes.c_void_p(out.data_ptr()),
                                      ctypes.c_void_p(st) if st else None))
     return out

@@ -214,6 +214,30 @@ def test_call_sample_cap():
     assert "2^30" in uf.uf_last_error()
 
 
+def test_binding_argument_checks():
+    # the Python binding rejects unknown names and unusable output buffers
+    # before any library call
+    tree_s = yule_tree(20, seed=1)
+    tab_s = table_iid(9, tree_s.n_tips, 0.3, seed=2)
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    table = uf.Table(tab_s.indptr, tab_s.indices, tab_s.data, tree)
+    need = uf.condensed_size(9)
+    with pytest.raises(ValueError, match="unknown method"):
+        uf.uf_compute(tree, table, "weighted")
+    with pytest.raises(ValueError, match="unknown precision"):
+        uf.uf_compute(tree, table, "unweighted", 1.0, "fp16")
+    with pytest.raises(ValueError, match="unknown method"):
+        uf.uf_compute_batch(tree, [table], "bray_curtis")
+    for bad in (np.zeros(need, np.float32), np.zeros(need - 1), np.zeros((need, 2))[:, 0]):
+        with pytest.raises(ValueError, match="output array"):
+            uf.uf_compute(tree, table, "unweighted", out=bad)
+    with pytest.raises(ValueError, match="output array"):
+        uf.uf_compute(tree, table, "unweighted", out=np.zeros(need), out_fp32=True)
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError, match="output tensor"):
+        uf.uf_compute(tree, table, "unweighted", out=torch.zeros(need, dtype=torch.float32))
+
+
 def test_no_cpu_fallback():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
@@ -223,3 +247,4 @@ def test_no_cpu_fallback():
     tree = uf.Tree(tree_s.parent, tree_s.length)
     table = uf.Table(tab_s.indptr, tab_s.indices, tab_s.data, tree)
     assert _code(lambda: uf.uf_compute(tree, table, "unweighted")) == "UF_ECUDA"
+    assert _code(lambda: uf.uf_compute_batch(tree, [table, table], "generalized", 0.5, "mixed")) == "UF_ECUDA"

@@ -63,6 +63,23 @@ def test_report_layout_matches_header(tmp_path):
         assert int(got[f]) == getattr(uf.Report, f).offset, f
 
 
+def test_header_compiles_as_c_and_cpp(tmp_path):
+    # the public header stands alone in strict C99 and in C++ without warnings
+    import shutil
+    import subprocess
+    src = '#include "unifrac_gb300.h"\nint main(void) { uf_report r; (void)r; return (int)UF_OK; }\n'
+    for compiler, ext, std in (("gcc", "c", "-std=c99"), ("g++", "cpp", "-std=c++11")):
+        cc = shutil.which(compiler)
+        if cc is None:
+            continue
+        f = tmp_path / f"h.{ext}"
+        f.write_text(src)
+        p = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                            os.path.join(ROOT, "include"), "-c", str(f), "-o", str(tmp_path / f"h_{ext}.o")],
+                           capture_output=True, text=True)
+        assert p.returncode == 0, p.stderr
+
+
 def test_enum_values_match_header():
     # the binding's method, precision and status numbers are the header's
     text = open(os.path.join(ROOT, "include", "unifrac_gb300.h")).read()

@@ -63,15 +63,23 @@ typedef enum {
 } uf_method;
 
 /*
- * UF_FP64   every update and every accumulator in IEEE FP64 on CUDA cores;
- *           distances within 1e-10 relative of an FP64 per-pair evaluation.
+ * Both precisions keep every cross-branch-block accumulator in int64 fixed
+ * point (value * 2^F, F chosen per call from an upper bound of the sums, so
+ * that one grid step is about 1e-18 of a tree's root-to-tip distance) and
+ * end with one FP64 num / den division.
+ * UF_FP64   branch embeddings and per-branch updates in IEEE FP64 on CUDA
+ *           cores, partial sums in FP64 before each fixed-point rounding;
+ *           every numerator is a sum of nonnegative terms (no cancellation).
+ *           Distances d within 1e-10 * |d| + 1e-15 of an FP64 per-pair
+ *           evaluation: relative 1e-10 down to d = 1e-5, and the grid's
+ *           absolute rounding below that (near-identical samples).
  * UF_MIXED  the paper's FP32 compute mode (Sec. 4): branch embeddings and
  *           per-branch updates in FP32 on CUDA cores -- or, for
  *           UF_UNWEIGHTED, exact 0/1 presence tiles times branch lengths
  *           split into three BF16 terms on the tcgen05 tensor cores with FP32
- *           accumulation -- with partial sums carried into FP64 accumulators
- *           and the final num / den division in FP64; distances within 1e-5
- *           absolute (1e-5 * max(1, d) for UF_WEIGHTED_UNNORMALIZED).
+ *           accumulation -- with FP32 partial sums rounded into the
+ *           fixed-point accumulators; distances within 1e-5 absolute
+ *           (1e-5 * max(1, d) for UF_WEIGHTED_UNNORMALIZED).
  */
 typedef enum { UF_FP64 = 0, UF_MIXED = 1 } uf_precision;
 
@@ -91,7 +99,9 @@ typedef struct {
     int64_t n_blocks;      /* embedding blocks (launch groups) used */
     int64_t kernels;       /* kernel launches issued by the call */
     int32_t path;          /* 0 = CUDA-core stripes, 1 = tcgen05 split-BF16 GEMM */
-    int32_t reserved;
+    int32_t clamped;       /* cells whose numerator, formed as a difference of sums
+                              (min form, UF_MIXED only), rounded below 0 and was
+                              raised to 0; -1 when not read (asynchronous call) */
     double h2d_bytes;      /* host -> device bytes copied by this call (first use of inputs) */
     double d2h_bytes;      /* device -> host bytes copied by this call (host output) */
     /* device time per phase in ms, measured with CUDA events on the call's
@@ -178,7 +188,10 @@ const char *uf_status_name(uf_status st);
 int64_t uf_stripe_count(int64_t n_samples);
 
 /*
- * Tree.  parent[i] is the parent of node i; every non-root node has
+ * Tree (the phylogeny the paper's embeddings are taken over, one branch per
+ * non-root node, walked in postorder: Sec. 2, Fig. 1; the library form of
+ * the method is a C shared library callable from any language, Abstract).
+ * parent[i] is the parent of node i; every non-root node has
  * parent[i] > i (children before parents, as in a postorder); exactly one
  * root, the last node, with parent = -1.  length[i] >= 0 and finite is the
  * length of the branch above node i (length[root] is ignored).  Unary
@@ -194,7 +207,9 @@ void uf_tree_destroy(uf_tree *tree);
 int64_t uf_tree_tips(const uf_tree *tree);
 
 /*
- * Table: n_samples x n_features counts in CSR with samples as rows
+ * Table (the per-sample feature counts from which the per-branch sample
+ * embeddings of Sec. 2-3 are computed):
+ * n_samples x n_features counts in CSR with samples as rows
  * (indptr[n_samples + 1], indices[nnz], data[nnz], nnz = indptr[n_samples]).
  * Requires n_features == tips of the tree, indptr[0] == 0, indices strictly
  * increasing within a row and in [0, n_features), data finite and > 0, and
@@ -219,8 +234,8 @@ int64_t uf_table_samples(const uf_table *table);
  *     (k, (k + s + 1) mod n) -- the unified stripe buffer layout of Fig. 1;
  *   - start == stop writes nothing and returns UF_OK.
  * out: caller-owned buffer of that many doubles (or floats if out_fp32),
- *   in device memory of the current device if out_is_device, else in host
- *   memory.  alpha is used by UF_GENERALIZED only and must be in [0, 1].
+ *   in device memory of the current device if out_is_device (memory of
+ *   another device, or host memory, is UF_EINVAL), else in host memory.  alpha is used by UF_GENERALIZED only and must be in [0, 1].
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream).  The call
  *   returns after the results are in out, except when out_is_device is set
  *   and cuda_stream is not NULL: then it returns once the work is enqueued
@@ -237,7 +252,9 @@ uf_status uf_compute(const uf_tree *tree, const uf_table *table, uf_method metho
                      int out_is_device, int out_fp32, uf_report *rep, void *cuda_stream);
 
 /*
- * Many independent tables over one shared tree, all full-range (condensed
+ * Many independent tables over one shared tree (the batching of several
+ * input buffers into one kernel invocation, Sec. 3, taken across tables;
+ * stripes as independent subproblems, Fig. 1), all full-range (condensed
  * output per table, layout as in uf_compute).  outs[t] receives table t's
  * n_t(n_t-1)/2 doubles (host or device per out_is_device); reps may be NULL
  * or an array of n_tables reports.  The tables' embedding and accumulate
@@ -266,8 +283,9 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
  * does not fit is rejected with UF_ENOMEM and a message giving both sizes,
  * before any work is enqueued.
  * out_device: caller-owned device memory of n(n-1)/2 doubles on the current
- *   device, layout as in uf_compute.  cuda_stream: cudaStream_t or NULL.  The
- *   call returns after the results are in out_device.
+ *   device (memory of another device, or host memory, is UF_EINVAL), layout
+ *   as in uf_compute.  cuda_stream: cudaStream_t or NULL.  The call returns
+ *   after the results are in out_device.
  * The first call on a device, with that device current, sets up the area's
  * device address (cudaGetSymbolAddress); make that first call before any
  * stream capture begins on the device.  All calls on a device share the area

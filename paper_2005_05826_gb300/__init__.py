@@ -12,6 +12,7 @@ present the calls raise.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import threading
@@ -38,7 +39,7 @@ class Report(ctypes.Structure):
                 ("hbm_bytes_est", ctypes.c_double), ("stripe_tile", ctypes.c_int64),
                 ("sample_tile", ctypes.c_int64), ("branch_block", ctypes.c_int64),
                 ("n_blocks", ctypes.c_int64), ("kernels", ctypes.c_int64),
-                ("path", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("clamped", ctypes.c_int32),
                 ("h2d_bytes", ctypes.c_double), ("d2h_bytes", ctypes.c_double),
                 ("t_embed_ms", ctypes.c_double), ("t_accumulate_ms", ctypes.c_double),
                 ("t_diag_ms", ctypes.c_double), ("t_finalize_ms", ctypes.c_double),
@@ -247,6 +248,15 @@ def _out_spec(out, n_values: int, out_fp32: bool):
     return arr.ctypes.data, 0, None, arr
 
 
+def _on_device_of(buf):
+    """Context in which a CUDA tensor's device is the current device (the C
+    ABI writes device outputs on the current device); no-op otherwise."""
+    if hasattr(buf, "is_cuda") and buf.is_cuda:
+        import torch
+        return torch.cuda.device(buf.device)
+    return contextlib.nullcontext()
+
+
 def uf_compute(tree: Tree, table: Table, method: str, alpha: float = 1.0, precision: str = "fp64",
                stripe_start: int = 0, stripe_stop: int | None = None, out=None,
                out_fp32: bool = False, stream=None):
@@ -267,10 +277,11 @@ def uf_compute(tree: Tree, table: Table, method: str, alpha: float = 1.0, precis
     if stream is not None:
         st = int(stream)
     rep = Report()
-    _check(lib.uf_compute(tree.handle, table.handle, m_code, float(alpha),
-                          p_code, start, stop, ctypes.c_void_p(ptr), is_dev,
-                          int(bool(out_fp32)), ctypes.byref(rep),
-                          ctypes.c_void_p(st) if st else None))
+    with _on_device_of(out):
+        _check(lib.uf_compute(tree.handle, table.handle, m_code, float(alpha),
+                              p_code, start, stop, ctypes.c_void_p(ptr), is_dev,
+                              int(bool(out_fp32)), ctypes.byref(rep),
+                              ctypes.c_void_p(st) if st else None))
     if out is None and not full:
         keep = keep.reshape(max(stop - start, 0), n)
     return keep, rep
@@ -290,13 +301,17 @@ def uf_compute_batch(tree: Tree, tables, method: str, alpha: float = 1.0, precis
     if len(devs) > 1:
         raise ValueError("outputs must be all host or all device buffers")
     is_dev = devs.pop() if devs else 0
+    cuda_devs = {o.device for o in outs if hasattr(o, "is_cuda") and o.is_cuda}
+    if len(cuda_devs) > 1:
+        raise ValueError("device outputs must all be on one device")
     st = stream if stream is not None else next((s[2] for s in specs if s[2]), None)
     handles = (ctypes.c_void_p * nt)(*[t.handle.value for t in tables])
     ptrs = (ctypes.c_void_p * nt)(*[s[0] for s in specs])
     reps = (Report * max(nt, 1))()
-    _check(lib.uf_compute_batch(tree.handle, handles, nt, m_code, float(alpha),
-                                p_code, ptrs, is_dev, reps,
-                                ctypes.c_void_p(int(st)) if st else None))
+    with _on_device_of(next((o for o in outs if hasattr(o, "is_cuda") and o.is_cuda), None)):
+        _check(lib.uf_compute_batch(tree.handle, handles, nt, m_code, float(alpha),
+                                    p_code, ptrs, is_dev, reps,
+                                    ctypes.c_void_p(int(st)) if st else None))
     return [s[3] for s in specs], [reps[i] for i in range(nt)]
 
 
@@ -317,7 +332,8 @@ def uf_compute_noalloc(tree: Tree, table: Table, method: str, alpha: float = 1.0
         raise ValueError(f"out must be a contiguous float64 tensor with >= {need} elements")
     st = int(stream) if stream is not None else torch.cuda.current_stream(out.device).cuda_stream
     m_code, p_code = _code_of(METHODS, method, "method"), _code_of(PRECISIONS, precision, "precision")
-    _check(load().uf_compute_noalloc(tree.handle, table.handle, m_code, float(alpha),
-                                     p_code, ctypes.c_void_p(out.data_ptr()),
-                                     ctypes.c_void_p(st) if st else None))
+    with _on_device_of(out):
+        _check(load().uf_compute_noalloc(tree.handle, table.handle, m_code, float(alpha),
+                                         p_code, ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.c_void_p(st) if st else None))
     return out

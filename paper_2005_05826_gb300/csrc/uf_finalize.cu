@@ -9,13 +9,18 @@
 //   weighted:    num = A  or  D_k + D_j - 2M,      den = D_k + D_j
 //   unweighted:  num = A  or  W_k + W_j - 2G,      den = (W_k + W_j + A) / 2  or  W_k + W_j - G
 //                (W = D, G = M on presence embeddings)
-//   generalized: num = den - 2Q
+//   generalized: num = N (FP64)  or  den - 2Q (FP32)
 // num and den are formed exactly in integers before the one FP64 division
 // (the common 2^F cancels); weighted_unnormalized returns num * 2^-F.
-// A ratio with den == 0 is 0.
+// A ratio with den == 0 is 0.  An abs-form numerator is a sum of
+// nonnegative integers and never negative; a min-form numerator (FP32 only)
+// can round a hair below 0 for two nearly identical samples and is then
+// raised to 0 (and counted when the caller asks).
 // Branches scattered by uf_sparse.cu add their per-sample terms R here: the
 // diagonal is D + R, an abs-form cell gains R_k + R_j, and the generalized
-// den gains R_k + R_j.
+// den and N gain R_k + R_j.
+#include <algorithm>
+
 #include "uf_internal.h"
 #include "uf_finalize.h"
 
@@ -24,6 +29,7 @@ namespace ufg {
 __global__ void k_finalize(const FinalArgs a) {
   const int64_t rows = a.s1 - a.s0;
   const int64_t total = rows * a.n;
+  unsigned long long clamped = 0;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = c / a.n;
@@ -33,15 +39,16 @@ __global__ void k_finalize(const FinalArgs a) {
     if (j >= a.n) j -= a.n;
     if (a.full && 2 * (s + 1) == a.n && k >= a.n / 2) continue;  // duplicate half stripe
     long long m = (long long)a.M[c];
-    const bool abs_form = a.mixed_forms && fp32_abs_row(s);
+    const bool abs_form = a.method != 3 && abs_row(a.abs_mask, s);
     const long long rk = a.Dsp ? (long long)a.Dsp[k] : 0, rj = a.Dsp ? (long long)a.Dsp[j] : 0;
     const long long dk = (a.Dg ? (long long)a.Dg[k] : 0) + rk, dj = (a.Dg ? (long long)a.Dg[j] : 0) + rj;
     if (abs_form || a.method == 3) m += rk + rj;
+    long long num;
     double val;
     switch (a.method) {
     case 0: {  // unweighted
       const long long w = dk + dj;
-      long long num, den2;  // den2 = 2 * den
+      long long den2;  // den2 = 2 * den
       if (abs_form) {
         num = m;
         den2 = w + m;
@@ -49,24 +56,36 @@ __global__ void k_finalize(const FinalArgs a) {
         num = w - 2 * m;
         den2 = 2 * (w - m);
       }
-      if (num < 0) num = 0;
+      if (num < 0) {
+        clamped++;
+        num = 0;
+      }
       val = den2 > 0 ? 2.0 * (double)num / (double)den2 : 0.0;
     } break;
     case 1: {  // weighted unnormalized
-      long long num = abs_form ? m : dk + dj - 2 * m;
-      if (num < 0) num = 0;
+      num = abs_form ? m : dk + dj - 2 * m;
+      if (num < 0) {
+        clamped++;
+        num = 0;
+      }
       val = (double)num * a.inv_scale;
     } break;
     case 2: {  // weighted normalized
       const long long den = dk + dj;
-      long long num = abs_form ? m : den - 2 * m;
-      if (num < 0) num = 0;
+      num = abs_form ? m : den - 2 * m;
+      if (num < 0) {
+        clamped++;
+        num = 0;
+      }
       val = den > 0 ? (double)num / (double)den : 0.0;
     } break;
-    default: {  // generalized: M = den, M2 = Q
+    default: {  // generalized: M = den, M2 = N or Q
       const long long den = m;
-      long long num = den - 2 * (long long)a.M2[c];
-      if (num < 0) num = 0;
+      num = a.gen_abs ? (long long)a.M2[c] + rk + rj : den - 2 * (long long)a.M2[c];
+      if (num < 0) {
+        clamped++;
+        num = 0;
+      }
       val = den > 0 ? (double)num / (double)den : 0.0;
     } break;
     }
@@ -80,13 +99,18 @@ __global__ void k_finalize(const FinalArgs a) {
     if (a.out_fp32) ((float *)a.out)[idx] = (float)val;
     else ((double *)a.out)[idx] = val;
   }
+  if (clamped && a.clamps) atomicAdd(a.clamps, clamped);
 }
 
 cudaError_t launch_finalize(const FinalArgs &a, cudaStream_t st) {
   const int64_t total = (a.s1 - a.s0) * (int64_t)a.n;
   if (total <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  blocks = std::min<int64_t>(blocks, (int64_t)std::max(sms, 1) * 64);  // a grid-stride loop beyond that
   k_finalize<<<(int)blocks, 256, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -10,7 +10,9 @@ struct FinalArgs {
   int n;
   int64_t s0, s1;       // stripes [s0, s1)
   int full;             // 1: condensed output, 0: stripe-major
-  int mixed_forms;      // 1: the FP32 min kernel's abs-form stripes are present
+  unsigned abs_mask;    // ACC_MIN: stripes s with abs_row(abs_mask, s) hold the abs form
+  int gen_abs;          // generalized: M2 holds N = num (FP64) instead of Q (FP32)
+  unsigned long long *clamps;  // or null: counts cells whose min-form numerator rounded below 0
   const unsigned long long *M, *M2, *Dg;  // fixed-point accumulators of this table
   double inv_scale;     // 2^-F
   void *out;

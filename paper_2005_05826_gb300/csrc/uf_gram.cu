@@ -463,8 +463,12 @@ cudaError_t launch_gram(const GramArgs &a0, void *Pl, int64_t K_pad, cudaStream_
 cudaError_t launch_finalize_gram(const GramFinalArgs &a, cudaStream_t st) {
   const int64_t total = (a.s1 - a.s0) * (int64_t)a.n;
   if (total <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  blocks = std::min<int64_t>(blocks, (int64_t)std::max(sms, 1) * 64);  // a grid-stride loop beyond that
   k_finalize_gram<<<(int)blocks, 256, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -691,6 +691,7 @@ uf_status uf_compute(const uf_tree *tree, const uf_table *table, uf_method metho
     cudaGetLastError();
     return fail(UF_ECUDA, "no CUDA device available");
   }
+  if (out_is_device && (st = check_device_output(out, "out")) != UF_OK) return st;
   BatchJob J{method, alpha, precision == UF_MIXED, out_is_device, out_fp32, (cudaStream_t)cuda_stream, {}};
   J.tabs.push_back(TableJob{const_cast<uf_table *>(table), stripe_start, stripe_stop, out, rep});
   try {
@@ -731,6 +732,11 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
     cudaGetLastError();
     return fail(UF_ECUDA, "no CUDA device available");
   }
+  if (out_is_device)
+    for (const TableJob &t : J.tabs) {
+      const uf_status st = check_device_output(t.out, "an output buffer");
+      if (st != UF_OK) return st;
+    }
   try {
     return run_batch(const_cast<uf_tree *>(tree), J);
   } catch (const CudaFail &f) {
@@ -781,6 +787,25 @@ namespace ufg {
 uf_status set_last_error(uf_status st, const char *msg) {
   g_err = msg ? msg : "";
   return st;
+}
+
+uf_status check_device_output(const void *p, const char *what) {
+  int cur = 0;
+  cudaPointerAttributes at{};
+  if (cudaGetDevice(&cur) != cudaSuccess || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return set_last_error(UF_ECUDA, "cannot query the output buffer's memory type");
+  }
+  char msg[200];
+  if (at.type == cudaMemoryTypeDevice && at.device != cur) {
+    snprintf(msg, sizeof msg, "%s is memory of device %d but device %d is current", what, at.device, cur);
+    return set_last_error(UF_EINVAL, msg);
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+    snprintf(msg, sizeof msg, "%s is not device memory", what);
+    return set_last_error(UF_EINVAL, msg);
+  }
+  return UF_OK;
 }
 
 namespace {

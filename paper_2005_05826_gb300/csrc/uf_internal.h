@@ -34,7 +34,8 @@ enum EmbKind : int {
 // which quantity the accumulator holds
 enum AccKind : int {
   ACC_MIN = 0,   // sum_e min(x_e[k], x_e[k + d])  (+ diagonal row d = 0)
-  ACC_GEN = 1,   // generalized: (den, Q) = sum l s^a, sum l min(u, v) s^(a-1)
+  ACC_GEN = 1,   // generalized: den = sum l s^a and, FP32, Q = sum l min(u, v) s^(a-1)
+                 // (num = den - 2Q) or, FP64, N = sum l |u - v| s^(a-1) (num = N)
 };
 
 // ---- batches ----
@@ -53,10 +54,16 @@ struct TabDesc {
 };
 
 // ---- stripe accumulate (uf_stripe.cu) ----
-// In the FP32 min kernel, stripes s with s mod 8 in {1, 3, 5, 7} hold
-// A = sum |x_k - x_j| instead of M = sum min(x_k, x_j) (see uf_stripe.cu).
+// A stripe s whose bit (s mod 8) is set in the call's abs mask holds
+// A = sum |x_k - x_j| (abs form) instead of M = sum min(x_k, x_j) (min form).
+// FP32: stripes 1, 3, 5, 7 of every 8, so that the ALU and FMA pipes share
+// the load (see uf_stripe.cu).  FP64: every stripe, so that no numerator is
+// formed by cancellation (D_k + D_j - 2M) and its error stays relative to
+// the distance itself, however close the two samples are.
 constexpr unsigned FP32_ABS_ROW_MASK = 0xAAu;
-__host__ __device__ constexpr bool fp32_abs_row(int64_t s) { return (FP32_ABS_ROW_MASK >> (s & 7)) & 1u; }
+constexpr unsigned FP64_ABS_ROW_MASK = 0xFFu;
+__host__ __device__ constexpr unsigned abs_row_mask(bool fp32) { return fp32 ? FP32_ABS_ROW_MASK : FP64_ABS_ROW_MASK; }
+__host__ __device__ constexpr bool abs_row(unsigned mask, int64_t s) { return (mask >> (s & 7)) & 1u; }
 
 struct StripeArgs {
   const void *X;        // [rows][pitch] float or double, one segment per table
@@ -69,7 +76,8 @@ struct StripeArgs {
   int n_tiles;          // tiles of all tables (per row chunk)
   int n_cols;           // combined samples (diagonal length)
   unsigned long long *M;   // fixed point: M / A (ACC_MIN) or den (ACC_GEN), per table at m_off
-  unsigned long long *M2;  // Q (ACC_GEN), else null
+  unsigned long long *M2;  // ACC_GEN: Q = sum l min(u, v) s^(a-1) (FP32) or
+                           // N = sum l |u - v| s^(a-1) (FP64); else null
   unsigned long long *Dg;  // [n_cols] fixed-point diagonal (ACC_MIN, launch_diag), else null
   double alpha;         // generalized exponent
   double scale;         // 2^F: fixed-point scale of every accumulator
@@ -114,6 +122,10 @@ namespace ufg {
 double accum_scale(const ::uf_tree *tree, const ::uf_table *table, int kind);
 // Set the calling thread's uf_last_error() text and return st (uf_host.cpp).
 uf_status set_last_error(uf_status st, const char *msg);
+// UF_OK when p is device (or managed) memory usable on the current device;
+// else UF_EINVAL (memory of another device, host memory) or UF_ECUDA, with
+// the thread's error text set (uf_host.cpp).
+uf_status check_device_output(const void *p, const char *what);
 
 // Scheduling priority that the calling thread's launches through launch_k
 // carry (uf_host.cpp; 0: the stream's own).  A call raises it for the

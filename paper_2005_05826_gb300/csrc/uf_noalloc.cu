@@ -185,6 +185,8 @@ uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method 
     cudaGetLastError();
     return noalloc_fail(UF_ECUDA, "no usable CUDA device");
   }
+  const uf_status out_ok = check_device_output(out_device, "out_device");
+  if (out_ok != UF_OK) return out_ok;
   unsigned char *base = nullptr;
   e = scratch_address(device, &base);
   if (e != cudaSuccess) {
@@ -271,7 +273,8 @@ uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method 
   fa.s0 = 0;
   fa.s1 = S;
   fa.full = 1;
-  fa.mixed_forms = fp32 && acc == ACC_MIN;
+  fa.abs_mask = acc == ACC_MIN ? abs_row_mask(fp32) : 0u;
+  fa.gen_abs = acc == ACC_GEN && !fp32;
   fa.M = (const unsigned long long *)p[13];
   fa.M2 = (const unsigned long long *)p[14];
   fa.Dg = (const unsigned long long *)p[15];

@@ -766,6 +766,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   DevBuf X((size_t)xrows * pitch * es, st, "alloc embeddings");
   DevBuf M((size_t)cells * 8, st, "alloc stripes");
   DevBuf M2, Dg, Dsp, diag_tmp, counter(sizeof(int), st, "alloc counter");
+  DevBuf clamps(sizeof(unsigned long long), st, "alloc clamp counter");
   DevBuf total((size_t)n_cols * 8, st, "alloc totals"), inv_total((size_t)n_cols * 4, st, "alloc totals");
   // table descriptors and row lists: one staged upload
   Meta meta;
@@ -842,6 +843,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     ck(cudaMemsetAsync(Dg.p, 0, (size_t)n_cols * 8, st), "memset");
   }
   ck(cudaMemsetAsync(M.p, 0, (size_t)cells * 8, st), "memset");
+  ck(cudaMemsetAsync(clamps.p, 0, sizeof(unsigned long long), st), "memset");
   Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
   // chunk size: tuned once per (accumulator, precision, size bucket)
@@ -866,7 +868,8 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sp.tabs = meta.at<SpTab>(o_sptabs);
     sp.n_tabs = (int)nt;
     sp.kind = kind;
-    sp.mixed_forms = fp32 && acc == ACC_MIN;
+    sp.abs_mask = acc == ACC_MIN ? abs_row_mask(fp32) : 0u;
+    sp.gen_abs = acc == ACC_GEN && !fp32;
     sp.M = M.as<unsigned long long>();
     sp.M2 = M2.as<unsigned long long>();
     sp.Dsp = Dsp.as<unsigned long long>();
@@ -981,7 +984,9 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     fa.s0 = J.tabs[t].start;
     fa.s1 = J.tabs[t].stop;
     fa.full = J.tabs[t].start == 0 && J.tabs[t].stop == tabs[t].n / 2;
-    fa.mixed_forms = fp32 && acc == ACC_MIN;
+    fa.abs_mask = acc == ACC_MIN ? abs_row_mask(fp32) : 0u;
+    fa.gen_abs = acc == ACC_GEN && !fp32;
+    fa.clamps = clamps.as<unsigned long long>();
     fa.M = M.as<unsigned long long>() + tabs[t].m_off;
     fa.M2 = M2.p ? M2.as<unsigned long long>() + tabs[t].m_off : nullptr;
     fa.Dg = Dg.p ? Dg.as<unsigned long long>() + off[t] : nullptr;
@@ -994,6 +999,10 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   }
   timer.end();
   cap.launch();
+  // a synchronous call reads how many min-form numerators were raised to 0
+  const bool sync = !J.out_is_device || st == nullptr || timer.on;
+  unsigned long long h_clamps = 0;
+  if (sync) ck(cudaMemcpyAsync(&h_clamps, clamps.p, sizeof h_clamps, cudaMemcpyDeviceToHost, st), "copy count");
   if (!J.out_is_device)
     for (size_t t = 0; t < nt; t++)
       ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
@@ -1006,11 +1015,12 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   Dsp = DevBuf();
   diag_tmp = DevBuf();
   counter = DevBuf();
+  clamps = DevBuf();
   meta.dev = DevBuf();
   total = DevBuf();
   inv_total = DevBuf();
   o.tmp.clear();
-  if (!J.out_is_device || st == nullptr || timer.on) ck(cudaStreamSynchronize(st), "synchronize");
+  if (sync) ck(cudaStreamSynchronize(st), "synchronize");
   else ck(cudaGetLastError(), "enqueue");
   double ms[5] = {0, 0, 0, 0, 0};
   timer.collect(ms);
@@ -1020,6 +1030,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     if (t.rep) {
       t.rep->chunk_rows = chunk;
       t.rep->graph = cap.on ? 1 : 0;
+      t.rep->clamped = sync ? (int32_t)std::min<unsigned long long>(h_clamps, INT32_MAX) : -1;
       t.rep->dense_rows = (int64_t)split.dense.size();
       t.rep->sparse_rows = split.n_sparse;
       t.rep->sparse_pairs = split.pairs;

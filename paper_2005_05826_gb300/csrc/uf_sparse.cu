@@ -12,12 +12,14 @@
 // both-nonzero pairs plus one term per nonzero sample:
 //   min form:  cell += min(X_k, X_j);  R[k] += X_k          (X = x rounded to fixed point)
 //   abs form:  cell += -2 min(X_k, X_j) and the finalize adds R[k] + R[j]
-//   generalized, with P_k = fixed(l u_k^a), w = l s^(a-1):
-//              Q   += q = fixed(w min(u, v)),
-//              den += 2 q + fixed(w |u - v|) - P_k - P_j,  R[k] += P_k,
-//   so that den = sum l s^a and num = den - 2 Q = sum l s^(a-1) |u - v| over
-//   every branch where u or v is nonzero (a one-sided branch gives l u^a to
-//   both), and two identical samples still give num = 0 exactly.
+//   generalized, with P_k = fixed(l u_k^a), w = l s^(a-1), q = fixed(w min(u, v)),
+//   e = fixed(w |u - v|):
+//              den += 2 q + e - P_k - P_j,  R[k] += P_k,  and
+//              Q   += q          (FP32; num = den - 2 Q)   or
+//              N   += e - P_k - P_j   (FP64; num = N),
+//   so that den = sum l s^a and num = sum l s^(a-1) |u - v| over every
+//   branch where u or v is nonzero (a one-sided branch gives l u^a to both),
+//   and two identical samples still give num = 0 exactly.
 // The finalize adds R[k] + R[j] where these terms need it (uf_finalize.cu);
 // integer addition makes the order free and the result deterministic.
 // For the tensor-core unweighted path the same presence terms go into its
@@ -111,7 +113,9 @@ struct alignas(16) SpEnt<double> {
 // What a pair update needs besides its two entries.
 template <typename T>
 struct PairCtx {
-  int n, s_lo, s_hi, mixed_forms;
+  int n, s_lo, s_hi;
+  unsigned abs_mask;           // stripes in the abs form (abs_row)
+  int gen_abs;                 // generalized: M2 holds N (1) or Q (0)
   unsigned long long *M, *M2;  // this table's cells (den and Q for the generalized method)
   T lt, am1;                   // branch length, alpha - 1
   double scale;
@@ -119,7 +123,8 @@ struct PairCtx {
 
 // Adds the pair (ea, eb), k_a < k_b, to its stripe cell when the stripe is
 // stored: the min form min(X_a, X_b) (-2 times that in an abs-form stripe),
-// or the generalized Q and den terms; twice for the duplicated half stripe.
+// or the generalized den and Q (or N) terms; twice for the duplicated half
+// stripe.
 template <typename T, int ACC, int MODE>
 __device__ __forceinline__ void add_pair(const SpEnt<T> &ea, const SpEnt<T> &eb, const PairCtx<T> &c) {
   const int d = eb.k - ea.k;
@@ -136,7 +141,7 @@ __device__ __forceinline__ void add_pair(const SpEnt<T> &ea, const SpEnt<T> &eb,
   const bool dup = 2 * d == c.n;  // also stored at k = k_b (= k_a + n/2)
   if (ACC == ACC_MIN) {
     long long t = min(ea.f, eb.f);
-    if (c.mixed_forms && fp32_abs_row(s)) t *= -2;
+    if (abs_row(c.abs_mask, s)) t *= -2;
     red_add(c.M + cell, t);
     if (dup) red_add(c.M + cell + d, t);
   } else {
@@ -145,11 +150,12 @@ __device__ __forceinline__ void add_pair(const SpEnt<T> &ea, const SpEnt<T> &eb,
     const long long q = to_fixed(w * tmin<T>(uu, vv), c.scale);
     const long long e = to_fixed(w * (uu > vv ? uu - vv : vv - uu), c.scale);
     const long long den = 2 * q + e - ea.f - eb.f;
+    const long long t2 = c.gen_abs ? e - ea.f - eb.f : q;
     red_add(c.M + cell, den);
-    red_add(c.M2 + cell, q);
+    red_add(c.M2 + cell, t2);
     if (dup) {
       red_add(c.M + cell + d, den);
-      red_add(c.M2 + cell + d, q);
+      red_add(c.M2 + cell + d, t2);
     }
   }
 }
@@ -264,7 +270,8 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
   c.n = tb.n;
   c.s_lo = tb.s_lo;
   c.s_hi = tb.s_hi;
-  c.mixed_forms = a.mixed_forms;
+  c.abs_mask = a.abs_mask;
+  c.gen_abs = a.gen_abs;
   c.M = a.M + tb.m_off;
   c.M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
   c.lt = (T)l;
@@ -379,7 +386,8 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   c.n = n;
   c.s_lo = tb.s_lo;
   c.s_hi = tb.s_hi;
-  c.mixed_forms = a.mixed_forms;
+  c.abs_mask = a.abs_mask;
+  c.gen_abs = a.gen_abs;
   c.M = a.M + tb.m_off;
   c.M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
   c.lt = (T)a.length[v];

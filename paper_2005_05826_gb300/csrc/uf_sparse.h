@@ -33,11 +33,12 @@ struct SparseArgs {
   const SpTab *tabs;
   int n_tabs;
   int kind;                 // EmbKind
-  int mixed_forms;          // FP32 min kernel abs-form stripes present
+  unsigned abs_mask;        // min kernels: stripes s with abs_row(abs_mask, s) in the abs form
+  int gen_abs;              // generalized: M2 holds N (FP64 kernels) instead of Q (FP32)
   int gram;                 // 1: presence rows into the tensor path's gram matrices
                             // (cell (i, j), i <= j, at m_off + j * n_pad + i; the
                             // diagonal takes the per-sample terms; Dsp unused)
-  unsigned long long *M, *M2, *Dsp;  // cells (M / den), Q (generalized), per-sample diagonal R
+  unsigned long long *M, *M2, *Dsp;  // cells (M / den), Q or N (generalized), per-sample diagonal R
   double alpha, scale;
   // list mode (one table, launch_sparse_lists): row blockIdx.x writes its
   // distinct samples, values and fixed-point terms at lofs[row_base +

@@ -12,10 +12,14 @@
 //   A[s][k] = sum_e |x_e[k] - x_e[k + s + 1]|          (abs form).
 // One min-form update is one FMNMX (ALU pipe, half rate) plus half an FADD2;
 // one abs-form update is half an FSUB2 plus one FADD (FMA pipe).  The FP32
-// kernel gives stripes 3, 5 and 7 of every 8 the abs form so the two pipes
+// kernel gives stripes 1, 3, 5 and 7 of every 8 the abs form so the two pipes
 // share the load (odd micro-tile rows read their partner pairs at even,
-// register-pair aligned offsets).  Generalized UniFrac keeps two accumulators,
-// den = sum l s^a and Q = sum l min(u, v) s^(a-1), num = den - 2Q.
+// register-pair aligned offsets).  The FP64 kernel uses the abs form on every
+// stripe: its numerators are then sums of nonnegative terms, never a
+// difference of two nearly equal sums, so their error stays relative to the
+// distance however close two samples are.  Generalized UniFrac keeps two
+// accumulators, den = sum l s^a and, FP32, Q = sum l min(u, v) s^(a-1) with
+// num = den - 2Q or, FP64, N = sum l |u - v| s^(a-1) = num.
 //
 // Work is split into units (row chunk of up to a.chunk branches, tile of
 // TILE_S stripes x TILE_K samples).  Persistent CTAs take units from a global
@@ -27,16 +31,16 @@
 // updates an RD x RK register micro-tile.  Shared rows are XOR-swizzled in
 // 16-byte units so the per-thread 16-byte reads are free of bank conflicts.
 //
-// Precision.  FP32 (the paper's fp32 mode, Sec. 4): register partials over
-// B1 = 64 branches are summed into an FP32 level kept in shared memory; at
-// the end of the unit that level is scaled by 2^F and rounded once to an
-// int64 fixed-point value, which is added atomically into the int64
-// accumulator.  FP64: register partials over 64 branches in FP64, each
-// rounded to fixed point and summed in shared memory, then added atomically.
-// Integer addition is exact and order-free, so chunks may land in any order
-// and the result is still deterministic; every cell (and the diagonal) runs
-// the same FP32 / FP64 operation sequence within a unit, so two identical
-// samples give bitwise equal accumulators and a distance of exactly 0.
+// Precision.  Register partials over B1 = 64 branches are summed into a
+// second level kept in shared memory in the path's own precision (FP32 for
+// the paper's fp32 mode, Sec. 4, FP64 otherwise); at the end of the unit that
+// level is scaled by 2^F and rounded once to an int64 fixed-point value,
+// which is added atomically into the int64 accumulator.  Integer addition is
+// exact and order-free, so chunks may land in any order and the result is
+// still deterministic; every cell (and the diagonal) runs the same FP32 /
+// FP64 operation sequence within a unit, so two identical samples give
+// bitwise equal accumulators and a distance of exactly 0 (an abs-form cell
+// adds |x - x| = 0 exactly).
 // F is chosen by the host from an upper bound B on any accumulated value so
 // that 2 B 2^F <= 2^61.
 #include <algorithm>
@@ -79,8 +83,8 @@ struct Geo {
   static constexpr int STAGE = RB * ROW + RB;    // + the rows' lengths (keeps 16-byte alignment)
   static constexpr int UCH = UW / VEC, VCH = VW / VEC, CH = UCH + VCH;
   static constexpr int NV = (RD + RK + VEC - 1) / VEC;  // partner vectors per thread
-  // second level per thread and cell: FP32 for the FP32 path, int64 for FP64
-  using Mid = typename std::conditional<sizeof(T) == 4, float, long long>::type;
+  // second level per thread and cell, in the path's precision
+  using Mid = T;
   static constexpr size_t SMEM =
       (size_t)NSTAGE * STAGE * sizeof(T) + (size_t)NACC * RD * RK * NT * sizeof(Mid);
 };
@@ -198,10 +202,7 @@ __device__ __forceinline__ void commit_cells(unsigned long long *M, const Mid *m
     for (int j = 0; j < RK; j++) {
       const int k = k_base + j;
       if (k < U.n) {
-        const Mid m = mid[(i * RK + j) * NT + threadIdx.x];
-        long long q;
-        if constexpr (sizeof(Mid) == 4) q = to_fixed((float)m, a.scale);
-        else q = (long long)m;
+        const long long q = to_fixed(mid[(i * RK + j) * NT + threadIdx.x], a.scale);
         atomicAdd(row + k, (unsigned long long)q);
       }
     }
@@ -286,7 +287,10 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
 #pragma unroll
           for (int i = 0; i < RD; i++)
 #pragma unroll
-            for (int j = 0; j < RK; j++) acc[i][j] += tmin<T>(u[j], v[i + j + 1]);
+            for (int j = 0; j < RK; j++) {
+              if ((ABSM >> i) & 1u) acc[i][j] += fabs(u[j] - v[i + j + 1]);
+              else acc[i][j] += tmin<T>(u[j], v[i + j + 1]);
+            }
         }
       }
       in_sub += G::RB;
@@ -295,9 +299,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
         for (int i = 0; i < RD; i++)
 #pragma unroll
           for (int j = 0; j < RK; j++) {
-            Mid &m = mid[(i * RK + j) * NT + threadIdx.x];
-            if constexpr (F32) m += acc[i][j];
-            else m += to_fixed(acc[i][j], a.scale);
+            mid[(i * RK + j) * NT + threadIdx.x] += acc[i][j];
             acc[i][j] = T(0);
           }
         in_sub = 0;
@@ -308,7 +310,8 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_min(const StripeArgs a) {
   }
 }
 
-// ---- generalized: den += l s w, Q += l min(u, v) w, w = s^(alpha - 1) ----
+// ---- generalized: den += l s w and, FP32, Q += l min(u, v) w or, FP64,
+//      N += l |u - v| w, with w = s^(alpha - 1) ----
 template <typename T, int RD, int RK, int MODE, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
   using G = Geo<T, RD, RK, 2>;
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
               T w = l * gen_pow<T, MODE>(s, am1);
               if (MODE == 1) w = s > T(0) ? w : T(0);
               accd[i][j] = fma(s, w, accd[i][j]);
-              accq[i][j] = fma(tmin<T>(uu, vv), w, accq[i][j]);
+              accq[i][j] = fma(fabs(uu - vv), w, accq[i][j]);
             }
         }
       }
@@ -415,13 +418,8 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
 #pragma unroll
           for (int j = 0; j < RK; j++) {
             const int c = (i * RK + j) * NT + threadIdx.x;
-            if constexpr (F32) {
-              midd[c] += accd[i][j];
-              midq[c] += accq[i][j];
-            } else {
-              midd[c] += to_fixed(accd[i][j], a.scale);
-              midq[c] += to_fixed(accq[i][j], a.scale);
-            }
+            midd[c] += accd[i][j];
+            midq[c] += accq[i][j];
             accd[i][j] = accq[i][j] = T(0);
           }
         in_sub = 0;
@@ -468,25 +466,20 @@ __global__ void k_diag_partial(const StripeArgs a, T *__restrict__ part) {
   part[(int64_t)sb * a.n_cols + kg] = acc;
 }
 
-// Phase 2: FP32 -- a chunk's sub-block partials summed in order in FP32, then
-// rounded to fixed point; FP64 -- each partial rounded to fixed point.
+// Phase 2: a chunk's sub-block partials summed in order in the path's
+// precision, then rounded to fixed point (the stripe kernels' second level).
 template <typename T>
 __global__ void k_diag_reduce(const StripeArgs a, const T *__restrict__ part, int n_sb) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n_cols) return;
   const int per_chunk = (a.chunk + B1 - 1) / B1;
   long long d = 0;
-  float mid = 0.f;
+  T mid = T(0);
   for (int sb = 0; sb < n_sb; sb++) {
-    const T p = part[(int64_t)sb * a.n_cols + k];
-    if constexpr (sizeof(T) == 4) {
-      mid += p;
-      if ((sb + 1) % per_chunk == 0 || sb == n_sb - 1) {
-        d += to_fixed(mid, a.scale);
-        mid = 0.f;
-      }
-    } else {
-      d += to_fixed(p, a.scale);
+    mid += part[(int64_t)sb * a.n_cols + k];
+    if ((sb + 1) % per_chunk == 0 || sb == n_sb - 1) {
+      d += to_fixed(mid, a.scale);
+      mid = T(0);
     }
   }
   a.Dg[k] += (unsigned long long)d;
@@ -549,7 +542,8 @@ int stripe_chunk_rows() { return 2048; }
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st) {
   if (a.rows <= 0 || a.n_tiles <= 0) return cudaSuccess;
   if (acc == ACC_MIN)
-    return fp32 ? run_min<float, 8, 8, FP32_ABS_ROW_MASK, 2>(a, st) : run_min<double, 8, 8, 0u, 1>(a, st);
+    return fp32 ? run_min<float, 8, 8, FP32_ABS_ROW_MASK, 2>(a, st)
+                : run_min<double, 8, 8, FP64_ABS_ROW_MASK, 1>(a, st);
   const bool half = a.alpha == 0.5;
   if (fp32) return half ? run_gen<float, 4, 8, 0, 2>(a, st) : run_gen<float, 4, 8, 1, 2>(a, st);
   return half ? run_gen<double, 4, 8, 0, 1>(a, st) : run_gen<double, 4, 8, 1, 1>(a, st);

@@ -21,8 +21,14 @@ def tolerance_ok(got, exp, method, precision):
 
 
 # every comparison's errors, for the precision report printed after a run
-# (tests/conftest.py): (what, method, precision, values, max_abs, max_rel, max_scaled)
+# (tests/conftest.py): (what, method, precision, values, max_abs, max_rel,
+# max_scaled, max_abs_at_zero)
 PRECISION_LOG = []
+
+# relative errors are reported only where the oracle's distance is at least
+# this large; where it is exactly 0 (identical samples) the absolute error is
+# reported in a column of its own
+REL_FLOOR = 1e-12
 
 
 def record_errors(got, exp, method, precision, what=""):
@@ -31,26 +37,30 @@ def record_errors(got, exp, method, precision, what=""):
     if got.size == 0:
         return
     diff = np.abs(got - exp)
-    rel = diff / np.maximum(np.abs(exp), 1e-300)
-    rel[diff == 0] = 0.0
+    big = np.abs(exp) >= REL_FLOOR
+    rel = float((diff[big] / np.abs(exp[big])).max()) if big.any() else 0.0
+    zero = exp == 0
+    at_zero = float(diff[zero].max()) if zero.any() else 0.0
     scaled = diff / np.maximum(1.0, np.abs(exp))
-    PRECISION_LOG.append((what, method, precision, int(got.size), float(diff.max()), float(rel.max()),
-                          float(scaled.max())))
+    PRECISION_LOG.append((what, method, precision, int(got.size), float(diff.max()), rel,
+                          float(scaled.max()), at_zero))
 
 
 def precision_summary():
     """Lines of the precision report: per method and precision, the largest
-    absolute, relative and max(1, |d|)-scaled error over every comparison."""
+    absolute, relative (where the oracle's |d| >= REL_FLOOR), max(1, |d|)-scaled
+    error, and the largest absolute error where the oracle gives exactly 0."""
     agg = {}
-    for _, method, precision, n, a, r, sc in PRECISION_LOG:
-        v = agg.setdefault((method, precision), [0, 0, 0.0, 0.0, 0.0])
+    for _, method, precision, n, a, r, sc, z in PRECISION_LOG:
+        v = agg.setdefault((method, precision), [0, 0, 0.0, 0.0, 0.0, 0.0])
         v[0] += 1
         v[1] += n
-        v[2], v[3], v[4] = max(v[2], a), max(v[3], r), max(v[4], sc)
+        v[2], v[3], v[4], v[5] = max(v[2], a), max(v[3], r), max(v[4], sc), max(v[5], z)
     lines = [f"{'method':<24}{'precision':<10}{'checks':>7}{'values':>12}{'max abs':>11}{'max rel':>11}"
-             f"{'max scaled':>12}"]
-    for (method, precision), (c, n, a, r, sc) in sorted(agg.items()):
-        lines.append(f"{method:<24}{precision:<10}{c:>7}{n:>12}{a:>11.2e}{r:>11.2e}{sc:>12.2e}")
+             f"{'max scaled':>12}{'abs at d=0':>12}"]
+    for (method, precision), (c, n, a, r, sc, z) in sorted(agg.items()):
+        lines.append(f"{method:<24}{precision:<10}{c:>7}{n:>12}{a:>11.2e}{r:>11.2e}{sc:>12.2e}{z:>12.2e}")
+    lines.append(f"(max rel over oracle values |d| >= {REL_FLOOR:g}; abs at d=0 over identical-sample pairs)")
     return lines
 
 

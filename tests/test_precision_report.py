@@ -33,11 +33,24 @@ def test_error_record_and_summary(clean_log):
     gpu_util.assert_close(got[:2], exp[:2], "weighted_unnormalized", "mixed", "case b")
     gpu_util.assert_close(np.zeros(0), np.zeros(0), "unweighted", "mixed", "empty")
     assert len(clean_log) == 2
-    what, method, precision, n, a, r, sc = clean_log[0]
+    what, method, precision, n, a, r, sc, z = clean_log[0]
     assert (what, method, precision, n) == ("case a", "weighted_unnormalized", "mixed", 4)
     assert a == pytest.approx(4e-6) and r == pytest.approx(2e-6) and sc == pytest.approx(2e-6)
+    assert z == 0.0
     lines = gpu_util.precision_summary()
-    assert len(lines) == 2 and lines[0].split()[:2] == ["method", "precision"]
+    assert len(lines) == 3 and lines[0].split()[:2] == ["method", "precision"]
     row = lines[1].split()
     assert row[:4] == ["weighted_unnormalized", "mixed", "2", "6"]
     assert float(row[4]) == pytest.approx(4e-6)
+
+
+def test_relative_error_ignores_oracle_zeros(clean_log):
+    # an oracle zero enters the absolute column only; relative errors are
+    # taken where |d| >= REL_FLOOR
+    exp = np.array([0.0, 1e-14, 0.5])
+    got = np.array([1e-16, 1e-14 + 1e-24, 0.5 * (1 + 1e-12)])
+    gpu_util.assert_close(got, exp, "weighted_normalized", "fp64", "zeros")
+    _, _, _, _, a, r, _, z = clean_log[0]
+    assert z == pytest.approx(1e-16)
+    assert r == pytest.approx(1e-12, rel=1e-3)
+    assert a == pytest.approx(1e-16)

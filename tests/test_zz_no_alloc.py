@@ -7,11 +7,13 @@ This file is collected last so that a run stopping at its first failure has
 already run every other test.  Each case calls the entry point through the C
 ABI twice in a row (the area keeps the previous call's data, so the second
 call checks that everything that must start at zero is cleared) and compares
-both results with uf_compute within the tolerances of the other GPU tests.
+both results with uf_compute and with the FP64 oracle, within the tolerances
+of the other GPU tests.
 """
 import numpy as np
 import pytest
 
+import oracle
 import paper_2005_05826_gb300 as uf
 from synth import table_iid, workload, yule_tree
 from tests.gpu_util import METHODS, assert_close
@@ -43,13 +45,15 @@ def test_noalloc_matches_compute_twice(precision):
         for method in METHODS:
             alpha = 0.5 if method == "generalized" else 1.0
             ref, _ = uf.uf_compute(tree, table, method, alpha, precision)
+            exp = oracle.condensed(tree_s, table_s, method, alpha)
             for call in range(2):
                 out = torch.full((n * (n - 1) // 2,), float("nan"), dtype=torch.float64,
                                  device="cuda")
                 uf.uf_compute_noalloc(tree, table, method, alpha, precision, out=out)
                 got = out.cpu().numpy()
                 assert np.isfinite(got).all()
-                assert_close(got, ref, method, precision, f"noalloc call {call + 1} n={n}")
+                assert_close(got, ref, method, precision, f"noalloc call {call + 1} n={n} vs uf_compute")
+                assert_close(got, exp, method, precision, f"noalloc call {call + 1} n={n} vs oracle")
 
 
 def test_noalloc_rejects_problems_beyond_the_area():

@@ -42,6 +42,29 @@ __device__ __forceinline__ float sfu_pow(float s, float am1) {
 __device__ __forceinline__ long long to_fixed(float x, double scale) { return __float2ll_rn(x * (float)scale); }
 __device__ __forceinline__ long long to_fixed(double x, double scale) { return __double2ll_rn(x * scale); }
 
+// The FP64 path's fixed point has two words: x * 2^F = hi + lo * 2^-32, hi the
+// nearest integer and lo the rounded remainder (|lo| <= 2^31), so one term is
+// kept to 2^-(F+32) and a sum of them is still exact integer arithmetic in
+// each word (value = (hi + lo * 2^-32) * 2^-F; the words are combined only in
+// the finalize).  The FP32 path keeps one word (lo = 0).
+struct Fx2 {
+  long long hi, lo;
+};
+constexpr double FX_LO_SCALE = 4294967296.0;  // 2^32
+__device__ __forceinline__ Fx2 to_fixed2(double x, double scale) {
+  const double y = x * scale;  // exact: scale is a power of two
+  const double h = rint(y);
+  return Fx2{(long long)h, __double2ll_rn((y - h) * FX_LO_SCALE)};  // y - h is exact
+}
+__device__ __forceinline__ Fx2 to_fixed2(float x, double scale) { return Fx2{to_fixed(x, scale), 0}; }
+__device__ __forceinline__ Fx2 fx_add(Fx2 a, Fx2 b) { return Fx2{a.hi + b.hi, a.lo + b.lo}; }
+__device__ __forceinline__ Fx2 fx_sub(Fx2 a, Fx2 b) { return Fx2{a.hi - b.hi, a.lo - b.lo}; }
+__device__ __forceinline__ Fx2 fx_mul(Fx2 a, long long m) { return Fx2{a.hi * m, a.lo * m}; }
+// the smaller value (|lo| <= 2^31 < 2^32, so hi decides unless equal)
+__device__ __forceinline__ Fx2 fx_min(Fx2 a, Fx2 b) {
+  return (a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo)) ? a : b;
+}
+
 // Embedding value of one sample at one branch from its count sum c under the
 // branch, the branch length l and the sample total t (1 / t in FP32 as it).
 template <typename T, int KIND>

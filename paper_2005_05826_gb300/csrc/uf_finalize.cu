@@ -11,7 +11,9 @@
 //                (W = D, G = M on presence embeddings)
 //   generalized: num = N (FP64)  or  den - 2Q (FP32)
 // num and den are formed exactly in integers before the one FP64 division
-// (the common 2^F cancels); weighted_unnormalized returns num * 2^-F.
+// (the common 2^F cancels); weighted_unnormalized returns num * 2^-F.  FP64
+// accumulators have two words (uf_device.cuh); they are combined here into
+// one 128-bit integer in units of 2^-(F+32).
 // A ratio with den == 0 is 0.  An abs-form numerator is a sum of
 // nonnegative integers and never negative; a min-form numerator (FP32 only)
 // can round a hair below 0 for two nearly identical samples and is then
@@ -26,9 +28,25 @@
 
 namespace ufg {
 
+// One accumulator word pair as an integer in units of 2^-F (one word) or
+// 2^-(F+32) (two words).
+template <typename I>
+__device__ __forceinline__ I acc_at(const unsigned long long *p, int64_t i, int64_t lo_off) {
+  if constexpr (sizeof(I) == 8) {
+    return (I)(long long)p[i];
+  } else {
+    return ((I)(long long)p[i] << 32) + (I)(long long)p[i + lo_off];
+  }
+}
+
+template <typename I>
+__device__ __forceinline__ double to_double(I x) { return (double)x; }
+
+template <typename I>
 __global__ void k_finalize(const FinalArgs a) {
   const int64_t rows = a.s1 - a.s0;
   const int64_t total = rows * a.n;
+  const double inv_scale = sizeof(I) == 8 ? a.inv_scale : a.inv_scale / 4294967296.0;
   unsigned long long clamped = 0;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
@@ -38,17 +56,18 @@ __global__ void k_finalize(const FinalArgs a) {
     int64_t j = k + s + 1;
     if (j >= a.n) j -= a.n;
     if (a.full && 2 * (s + 1) == a.n && k >= a.n / 2) continue;  // duplicate half stripe
-    long long m = (long long)a.M[c];
+    I m = acc_at<I>(a.M, c, a.m_lo_off);
     const bool abs_form = a.method != 3 && abs_row(a.abs_mask, s);
-    const long long rk = a.Dsp ? (long long)a.Dsp[k] : 0, rj = a.Dsp ? (long long)a.Dsp[j] : 0;
-    const long long dk = (a.Dg ? (long long)a.Dg[k] : 0) + rk, dj = (a.Dg ? (long long)a.Dg[j] : 0) + rj;
+    const I rk = a.Dsp ? acc_at<I>(a.Dsp, k, a.d_lo_off) : I(0), rj = a.Dsp ? acc_at<I>(a.Dsp, j, a.d_lo_off) : I(0);
+    const I dk = (a.Dg ? acc_at<I>(a.Dg, k, a.d_lo_off) : I(0)) + rk;
+    const I dj = (a.Dg ? acc_at<I>(a.Dg, j, a.d_lo_off) : I(0)) + rj;
     if (abs_form || a.method == 3) m += rk + rj;
-    long long num;
+    I num;
     double val;
     switch (a.method) {
     case 0: {  // unweighted
-      const long long w = dk + dj;
-      long long den2;  // den2 = 2 * den
+      const I w = dk + dj;
+      I den2;  // den2 = 2 * den
       if (abs_form) {
         num = m;
         den2 = w + m;
@@ -60,7 +79,7 @@ __global__ void k_finalize(const FinalArgs a) {
         clamped++;
         num = 0;
       }
-      val = den2 > 0 ? 2.0 * (double)num / (double)den2 : 0.0;
+      val = den2 > 0 ? 2.0 * to_double(num) / to_double(den2) : 0.0;
     } break;
     case 1: {  // weighted unnormalized
       num = abs_form ? m : dk + dj - 2 * m;
@@ -68,25 +87,25 @@ __global__ void k_finalize(const FinalArgs a) {
         clamped++;
         num = 0;
       }
-      val = (double)num * a.inv_scale;
+      val = to_double(num) * inv_scale;
     } break;
     case 2: {  // weighted normalized
-      const long long den = dk + dj;
+      const I den = dk + dj;
       num = abs_form ? m : den - 2 * m;
       if (num < 0) {
         clamped++;
         num = 0;
       }
-      val = den > 0 ? (double)num / (double)den : 0.0;
+      val = den > 0 ? to_double(num) / to_double(den) : 0.0;
     } break;
     default: {  // generalized: M = den, M2 = N or Q
-      const long long den = m;
-      num = a.gen_abs ? (long long)a.M2[c] + rk + rj : den - 2 * (long long)a.M2[c];
+      const I den = m;
+      num = a.gen_abs ? acc_at<I>(a.M2, c, a.m_lo_off) + rk + rj : den - 2 * acc_at<I>(a.M2, c, a.m_lo_off);
       if (num < 0) {
         clamped++;
         num = 0;
       }
-      val = den > 0 ? (double)num / (double)den : 0.0;
+      val = den > 0 ? to_double(num) / to_double(den) : 0.0;
     } break;
     }
     int64_t idx;
@@ -111,7 +130,8 @@ cudaError_t launch_finalize(const FinalArgs &a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   int64_t blocks = (total + 255) / 256;
   blocks = std::min<int64_t>(blocks, (int64_t)std::max(sms, 1) * 64);  // a grid-stride loop beyond that
-  k_finalize<<<(int)blocks, 256, 0, st>>>(a);
+  if (a.m_lo_off != 0) k_finalize<__int128><<<(int)blocks, 256, 0, st>>>(a);
+  else k_finalize<long long><<<(int)blocks, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,9 @@ struct FinalArgs {
   unsigned abs_mask;    // ACC_MIN: stripes s with abs_row(abs_mask, s) hold the abs form
   int gen_abs;          // generalized: M2 holds N = num (FP64) instead of Q (FP32)
   unsigned long long *clamps;  // or null: counts cells whose min-form numerator rounded below 0
+  // FP64 calls: the second words of M / M2 and of Dg / Dsp sit this many
+  // elements after the first (two-word fixed point, uf_device.cuh); 0: one word
+  int64_t m_lo_off, d_lo_off;
   const unsigned long long *M, *M2, *Dg;  // fixed-point accumulators of this table
   double inv_scale;     // 2^-F
   void *out;

@@ -13,12 +13,16 @@
 // A_lo, branches contiguous (K-major for both MMA operands); the tables of a
 // batch occupy consecutive row ranges of every plane.  A work unit is
 // (K chunk of `kc` branches, tile of GM = 128 samples i x GN = 256 samples j of
-// one table); only tiles that meet the upper triangle i <= j are scheduled,
-// chunk-major over all tables of the batch.  Per unit the
-// accumulator (128 lanes x 256 FP32 columns of TMEM, two buffers) is rounded
-// to int64 fixed point (scale 2^F) and added atomically into Gt, stored
-// transposed (cell (i, j), i <= j, at Gt[j * n_pad + i]) so that the 32 lanes
-// of a warp add into 32 consecutive words.  Integer addition is exact and
+// one table).  Only the tiles a call needs are scheduled and stored: those
+// that hold a pair of the requested stripes (stripe s holds the pairs at
+// distance j - i of s + 1 and n - s - 1, Fig. 1's stripes read off the gram
+// matrix) or a diagonal cell; a full-range call needs every tile that meets
+// the upper triangle i <= j.  Units run chunk-major over all tables of the
+// batch.  Per unit the accumulator (128 lanes x 256 FP32 columns of TMEM, two
+// buffers) is rounded to int64 fixed point (scale 2^F) and added atomically
+// into the unit's tile of Gt, which holds only the stored tiles, each
+// transposed (cell (i, j) at (j - j0) * GM + (i - i0)) so that the 32 lanes of
+// a warp add into 32 consecutive words.  Integer addition is exact and
 // order-free, so the result does not depend on the order chunks land in.
 //
 // Roles (192 threads): warp 0 issues TMA loads (128-byte swizzled boxes into a
@@ -40,8 +44,8 @@ namespace ufg {
 
 namespace {
 
-constexpr int GM = 128;                              // samples i per tile (TMEM lanes)
-constexpr int GN = 256;                              // samples j per tile (TMEM columns)
+constexpr int GM = GRAM_TM;                          // samples i per tile (TMEM lanes)
+constexpr int GN = GRAM_TN;                          // samples j per tile (TMEM columns)
 constexpr int GK = 64;                               // branches per stage: 128 bytes of BF16
 constexpr int NSPLIT = 3;
 constexpr int GSTAGES = 2;
@@ -139,23 +143,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 struct GUnit {
-  int bi, bj, k0, nk;  // tile, first branch and number of GK steps
-  int n, n_pad, row_base;
-  int64_t gt_off;
+  int t;               // stored tile
+  int bi, bj, k0, nk;  // its block coordinates, first branch and number of GK steps
+  int n, row_base;
 };
 
 __device__ __forceinline__ GUnit gram_unit(const GramArgs &a, int u) {
   const int c = u / a.n_tiles, t = u - c * a.n_tiles;
   const GramTab &tb = a.tabs[a.tile_tab[t]];
   GUnit g;
+  g.t = t;
   g.bi = a.tile_bi[t];
   g.bj = a.tile_bj[t];
   g.k0 = c * a.kc;
   g.nk = (min(a.kc, a.k_len - g.k0) + GK - 1) / GK;
   g.n = tb.n;
-  g.n_pad = tb.n_pad;
   g.row_base = tb.row_base;
-  g.gt_off = tb.gt_off;
   return g;
 }
 
@@ -273,6 +276,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
       if (!mbar_wait(&acc_full[b], (ul >> 1) & 1, &s_abort)) break;
       tc_fence_after();
       const int i = g.bi * GM + row;
+      unsigned long long *tile = a.Gt + (int64_t)g.t * GRAM_TILE_CELLS + row;
       for (int c = 0; c < GN / 32; c++) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * GN + c * 32), r);
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
           const int j = g.bj * GN + c * 32 + q;
           if (i <= j && j < g.n) {
             const long long v = __float2ll_rn(__uint_as_float(r[q]) * scale);
-            atomicAdd(a.Gt + g.gt_off + (int64_t)j * g.n_pad + i, (unsigned long long)v);
+            atomicAdd(tile + (c * 32 + q) * GM, (unsigned long long)v);
           }
         }
       }
@@ -361,11 +365,21 @@ __global__ void k_gram_prep(int64_t b0, const int32_t *__restrict__ nodes, int r
   }
 }
 
-// Gram accumulators -> distances for stripes [s0, s1).
+// Cell (i, j), i <= j, of a table's gram matrix from the compact tiles, or -1
+// (never for a cell of the call's stripes or the diagonal).
+__device__ __forceinline__ long long gram_cell(const GramFinalArgs &a, int64_t i, int64_t j) {
+  const int64_t bi = i / GM, bj = j / GN;
+  const int t = a.tile_map[bi * (a.n_pad / GN) + bj];
+  if (t < 0) return -1;
+  return (long long)a.Gt[(int64_t)t * GRAM_TILE_CELLS + (j - bj * GN) * GM + (i - bi * GM)];
+}
+
+// Gram accumulators (plus the sparse rows' terms) -> distances for stripes [s0, s1).
 __global__ void k_finalize_gram(const GramFinalArgs a) {
   const int64_t rows = a.s1 - a.s0;
   const int64_t total = rows * a.n;
   const bool aborted = a.err && *a.err != 0;  // a bounded wait gave up: no distance is valid
+  unsigned long long clamped = 0;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = c / a.n;
@@ -375,16 +389,28 @@ __global__ void k_finalize_gram(const GramFinalArgs a) {
     if (j >= a.n) j -= a.n;
     if (a.full && 2 * (s + 1) == a.n && k >= a.n / 2) continue;
     const int64_t lo = k < j ? k : j, hi = k < j ? j : k;
-    const long long g = (long long)a.Gt[hi * a.n_pad + lo];
-    const long long w = (long long)a.Gt[lo * a.n_pad + lo] + (long long)a.Gt[hi * a.n_pad + hi];
+    long long g = gram_cell(a, lo, hi);
+    long long wl = gram_cell(a, lo, lo), wh = gram_cell(a, hi, hi);
+    const bool missing = g < 0 || wl < 0 || wh < 0;
+    if (a.Msp) g += (long long)a.Msp[c];
+    if (a.Dsp) {
+      wl += (long long)a.Dsp[lo];
+      wh += (long long)a.Dsp[hi];
+    }
+    const long long w = wl + wh;
     long long num = w - 2 * g;
     const long long den = w - g;
-    if (num < 0) num = 0;
-    const double val = aborted ? __longlong_as_double(0x7ff8000000000000ll) : den > 0 ? (double)num / (double)den : 0.0;
+    if (num < 0) {
+      clamped++;
+      num = 0;
+    }
+    const double val = (aborted || missing) ? __longlong_as_double(0x7ff8000000000000ll)
+                                            : den > 0 ? (double)num / (double)den : 0.0;
     const int64_t idx = a.full ? (int64_t)a.n * lo - lo * (lo + 1) / 2 + (hi - lo - 1) : c;
     if (a.out_fp32) ((float *)a.out)[idx] = (float)val;
     else ((double *)a.out)[idx] = val;
   }
+  if (clamped && a.clamps) atomicAdd(a.clamps, clamped);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -412,13 +438,23 @@ int gram_pad(int n) { return (n + GN - 1) / GN * GN; }
 
 int64_t gram_kpad(int rows) { return ((int64_t)std::max(rows, 1) + GK - 1) / GK * GK; }
 
-void gram_tiles(int n_pad, std::vector<int32_t> *bi, std::vector<int32_t> *bj) {
-  for (int j = 0; j < n_pad / GN; j++)
-    for (int i = 0; i < n_pad / GM; i++)
-      if (i * GM < (j + 1) * GN) {
+void gram_tiles(int n, int64_t s0, int64_t s1, std::vector<int32_t> *bi, std::vector<int32_t> *bj) {
+  const int n_pad = gram_pad(n);
+  // distances j - i held by the stripes: [s0 + 1, s1] and [n - s1, n - s0 - 1]
+  const int64_t d1a = s0 + 1, d1b = s1, d2a = (int64_t)n - s1, d2b = (int64_t)n - s0 - 1;
+  for (int i = 0; i < n_pad / GM; i++)
+    for (int j = 0; j < n_pad / GN; j++) {
+      const int64_t i0 = (int64_t)i * GM, j0 = (int64_t)j * GN;
+      if (i0 >= n || j0 >= n) continue;
+      const int64_t imax = std::min<int64_t>(i0 + GM, n) - 1, jmax = std::min<int64_t>(j0 + GN, n) - 1;
+      const int64_t dmin = std::max<int64_t>(0, j0 - imax), dmax = jmax - i0;
+      if (dmax < 0) continue;  // no cell with i <= j
+      const bool need = dmin == 0 || (dmin <= d1b && d1a <= dmax) || (dmin <= d2b && d2a <= dmax);
+      if (need) {
         bi->push_back(i);
         bj->push_back(j);
       }
+    }
 }
 
 size_t gram_smem_bytes() { return (size_t)GSTAGES * STAGE_BYTES + 1024; }

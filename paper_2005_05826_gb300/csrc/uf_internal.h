@@ -14,6 +14,8 @@
 //                           (s - s_lo) * n + k for the pair (k, (k + s + 1) mod n)
 //                           (the unified buffer of Sec. 2, Fig. 1)
 //   Dg      [n]             int64 fixed-point diagonal accumulator (partner offset 0)
+// FP64 calls give every fixed-point accumulator a second word (uf_device.cuh,
+// Fx2) in an array of the same shape at a stated element offset.
 #pragma once
 #include <cstdint>
 #include <vector>
@@ -82,6 +84,10 @@ struct StripeArgs {
   double alpha;         // generalized exponent
   double scale;         // 2^F: fixed-point scale of every accumulator
   int *counter;         // one int of device memory: the work-unit counter (reset per launch)
+  // FP64 kernels: the second (low) word of every fixed-point accumulator sits
+  // this many elements after its first word (M and M2 cells; Dg); the FP32
+  // kernels keep one word
+  int64_t m_lo_off, d_lo_off;
 };
 // stripes and samples per CTA tile of the accumulate kernel
 void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k);

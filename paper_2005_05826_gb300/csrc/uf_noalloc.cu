@@ -112,6 +112,7 @@ uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method 
                                              : EMB_SCALED;
   const bool fp32 = precision == UF_MIXED;
   const size_t es = fp32 ? 4 : 8;
+  const size_t words = fp32 ? 1 : 2;
   int tile_s = 0, tile_k = 0;
   stripe_tile_shape(acc, fp32, &tile_s, &tile_k);
   const int m_hi = (int)((S - 1) / tile_s);
@@ -161,9 +162,10 @@ uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method 
     p[10] = c.take<float>(n);                       // inv_total_f
     p[11] = c.take<double>((size_t)std::max<int64_t>(nb, 1) * n);        // counts
     p[12] = c.take<unsigned char>((size_t)std::max(rows, 1) * pitch * es);  // X
-    p[13] = c.take<unsigned long long>((size_t)S * n);  // stripe accumulator (fixed point)
-    p[14] = acc == ACC_GEN ? (void *)c.take<unsigned long long>((size_t)S * n) : nullptr;  // Q
-    p[15] = acc == ACC_MIN ? (void *)c.take<unsigned long long>(n) : nullptr;               // diagonal
+    // fixed-point accumulators (FP64: two words each, the second after the first)
+    p[13] = c.take<unsigned long long>((size_t)S * n * words);  // stripe accumulator
+    p[14] = acc == ACC_GEN ? (void *)c.take<unsigned long long>((size_t)S * n * words) : nullptr;  // Q or N
+    p[15] = acc == ACC_MIN ? (void *)c.take<unsigned long long>((size_t)n * words) : nullptr;      // diagonal
     p[16] = acc == ACC_MIN ? (void *)c.take<unsigned char>(diag_scratch_bytes(fp32, std::max(rows, 1), n))
                            : nullptr;                                        // diagonal partials
     p[17] = c.take<int>(1);                                                  // work-unit counter
@@ -232,9 +234,9 @@ uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method 
   tab.m_off = 0;
   UF_TRY(h2d(p[18], &tab, sizeof tab));
   // accumulators start at zero; the rest of the area is overwritten before use
-  UF_TRY(cudaMemsetAsync(p[13], 0, (size_t)S * n * 8, st));
-  if (p[14]) UF_TRY(cudaMemsetAsync(p[14], 0, (size_t)S * n * 8, st));
-  if (p[15]) UF_TRY(cudaMemsetAsync(p[15], 0, (size_t)n * 8, st));
+  UF_TRY(cudaMemsetAsync(p[13], 0, (size_t)S * n * 8 * words, st));
+  if (p[14]) UF_TRY(cudaMemsetAsync(p[14], 0, (size_t)S * n * 8 * words, st));
+  if (p[15]) UF_TRY(cudaMemsetAsync(p[15], 0, (size_t)n * 8 * words, st));
 
   const int32_t *d_lists = (const int32_t *)p[5], *d_slot = (const int32_t *)p[4];
   double *d_counts = (double *)p[11];
@@ -264,6 +266,8 @@ uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method 
     sa.alpha = alpha;
     sa.scale = scale;
     sa.counter = (int *)p[17];
+    sa.m_lo_off = fp32 ? 0 : (int64_t)S * n;
+    sa.d_lo_off = fp32 ? 0 : n;
     UF_TRY(launch_stripe_acc(acc, fp32, sa, st));
     if (acc == ACC_MIN) UF_TRY(launch_diag(fp32, sa, p[16], st));
   }
@@ -279,6 +283,8 @@ uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method 
   fa.M2 = (const unsigned long long *)p[14];
   fa.Dg = (const unsigned long long *)p[15];
   fa.inv_scale = 1.0 / scale;
+  fa.m_lo_off = fp32 ? 0 : (int64_t)S * n;
+  fa.d_lo_off = fp32 ? 0 : n;
   fa.out = out_device;
   fa.out_fp32 = 0;
   UF_TRY(launch_finalize(fa, st));

@@ -346,7 +346,7 @@ struct ScopedEvent {
 
 // Time the accumulate launch of the first block with each candidate chunk
 // size and keep the fastest (the accumulators are cleared afterwards).
-int tune_chunk(int acc, bool fp32, StripeArgs sa, size_t cells, cudaStream_t st) {
+int tune_chunk(int acc, bool fp32, StripeArgs sa, size_t m_bytes, cudaStream_t st) {
   const int cand[4] = {1024, 2048, 4096, 8192};
   const ScopedEvent ev0, ev1;
   cudaEvent_t e0 = ev0.e, e1 = ev1.e;
@@ -366,8 +366,8 @@ int tune_chunk(int acc, bool fp32, StripeArgs sa, size_t cells, cudaStream_t st)
       best = c;
     }
   }
-  ck(cudaMemsetAsync(sa.M, 0, cells * 8, st), "memset");
-  if (sa.M2) ck(cudaMemsetAsync(sa.M2, 0, cells * 8, st), "memset");
+  ck(cudaMemsetAsync(sa.M, 0, m_bytes, st), "memset");
+  if (sa.M2) ck(cudaMemsetAsync(sa.M2, 0, m_bytes, st), "memset");
   return best;
 }
 
@@ -508,35 +508,195 @@ void enqueue_split_presence(const Inputs &in, const BatchJob &J, const std::vect
   }
 }
 
+// Stripe-layout description of the tables of a call for the sparse-row
+// scatter: samples, combined column, stored stripes and first cell of each.
+struct SpLayout {
+  int n, off, s_lo, s_hi;
+  int64_t m_off;
+};
+
+// The sparse-row scatter of a call (uf_sparse.cu): its row lists by capacity
+// class, the per-sample diagonal R, and for one table whose accumulators
+// exceed the L2 budget the sample lists that are then scattered stripe region
+// by region.  prepare() adds its metadata to the call's Meta before the
+// upload; launch() enqueues the scatter.
+struct SparseScatter {
+  const RowSplit *split = nullptr;
+  bool region_mode = false;
+  bool two_word = false;  // FP64 terms in two words (second words after the first)
+  int n_acc = 1;
+  int64_t n_sparse_rows = 0, cells = 0, n_cols = 0;
+  std::vector<int64_t> sp_off;  // first entry of each capacity class in the sparse list
+  size_t o_sparse = 0, o_sptabs = 0, o_lofs = 0;
+  DevBuf le, lk, lz, Dsp;
+  std::vector<SpLayout> lay;
+
+  // acc: ACC_MIN / ACC_GEN; fp64_entries: terms computed in FP64
+  void prepare(uf_tree *tree, const BatchJob &J, const Inputs &in, const RowSplit &sp,
+               const std::vector<SpLayout> &layout, int acc, bool fp64_entries, bool two_words,
+               int64_t call_cells, int64_t call_cols, Meta &meta, cudaStream_t st) {
+    split = &sp;
+    lay = layout;
+    two_word = two_words;
+    n_acc = acc == ACC_GEN ? 2 : 1;
+    cells = call_cells;
+    n_cols = call_cols;
+    const size_t nt = J.tabs.size();
+    if (sp.n_sparse == 0) return;
+    const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc * (two_word ? 2 : 1));
+    region_mode = n_regions > 1 || sp.lists;
+    std::vector<int32_t> all;
+    for (const auto &c : sp.sparse) {
+      sp_off.push_back((int64_t)all.size());
+      all.insert(all.end(), c.begin(), c.end());
+    }
+    n_sparse_rows = (int64_t)all.size();
+    if (region_mode) {
+      const auto &cp = J.tabs[0].table->col_ptr;
+      std::vector<int64_t> lofs(all.size() + 1, 0);
+      for (size_t r = 0; r < all.size(); r++)
+        lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
+      const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
+      le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries), st, "alloc sparse lists");
+      lk = DevBuf(total_e * 4, st, "alloc sparse lists");
+      lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
+      // rows without entries in the table return before writing their count
+      ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
+      o_lofs = meta.add(lofs);
+    }
+    std::vector<SpTab> tabs(nt);
+    for (size_t t = 0; t < nt; t++) {
+      tabs[t].col_ptr = in.xd[t]->col_ptr;
+      tabs[t].col_row = in.xd[t]->col_row;
+      tabs[t].col_val = in.xd[t]->col_val;
+      tabs[t].total = in.xd[t]->total;
+      tabs[t].inv_total_f = in.xd[t]->inv_total_f;
+      tabs[t].n = lay[t].n;
+      tabs[t].off = lay[t].off;
+      tabs[t].s_lo = lay[t].s_lo;
+      tabs[t].s_hi = lay[t].s_hi;
+      tabs[t].m_off = lay[t].m_off;
+    }
+    o_sparse = meta.add(all);
+    o_sptabs = meta.add(tabs);
+    const size_t dsp_words = (size_t)n_cols * (two_word ? 2 : 1);
+    Dsp = DevBuf(dsp_words * 8, st, "alloc diagonal");
+    ck(cudaMemsetAsync(Dsp.p, 0, dsp_words * 8, st), "memset");
+  }
+
+  // base: kind, masks, M / M2, alpha and scale filled by the caller
+  void launch(const Meta &meta, const Inputs &in, SparseArgs base, int acc, bool fp64_entries, int64_t region_bytes,
+              cudaStream_t on, int64_t *kernels) const {
+    if (!split || split->n_sparse == 0) return;
+    const bool f32 = !fp64_entries;
+    base.tip_lo = in.td->tip_lo;
+    base.tip_hi = in.td->tip_hi;
+    base.length = in.td->length;
+    base.tabs = meta.at<SpTab>(o_sptabs);
+    base.n_tabs = (int)lay.size();
+    base.Dsp = Dsp.as<unsigned long long>();
+    base.m_lo_off = two_word ? cells : 0;
+    base.d_lo_off = two_word ? n_cols : 0;
+    if (region_mode) {
+      base.le = le.p;
+      base.lk = lk.as<int>();
+      base.lofs = meta.at<int64_t>(o_lofs);
+      base.lz = lz.as<int>();
+    }
+    for (size_t c = 0; c < split->sparse.size(); c++) {
+      if (split->sparse[c].empty()) continue;
+      SparseArgs sp = base;
+      sp.row_base = (int)sp_off[c];
+      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
+      sp.n_nodes = (int)split->sparse[c].size();
+      sp.cap = split->cap[c];
+      if (region_mode) ck(launch_sparse_lists(acc, f32, sp, on), "sparse lists");
+      else ck(launch_sparse_rows(acc, f32, sp, on), "sparse rows");
+      (*kernels)++;
+    }
+    if (!region_mode) return;
+    const int64_t per =
+        std::max<int64_t>(1, (int64_t)((double)region_bytes / (8.0 * n_acc * (two_word ? 2 : 1) * lay[0].n)));
+    for (int64_t r0 = lay[0].s_lo; r0 <= lay[0].s_hi; r0 += per) {
+      SparseArgs sp = base;
+      sp.nodes = meta.at<int32_t>(o_sparse);
+      sp.n_nodes = (int)n_sparse_rows;
+      sp.r0 = (int)r0;
+      sp.r1 = (int)std::min<int64_t>(r0 + per, (int64_t)lay[0].s_hi + 1);
+      ck(launch_sparse_region(acc, f32, sp, on), "sparse regions");
+      (*kernels)++;
+    }
+  }
+};
+
+// Tiles the tensor path stores for one call: per table the tiles that hold
+// a pair of its stripe range or a diagonal cell (gram_tiles), numbered across
+// the tables, with each table's tile map.
+struct GramPlan {
+  std::vector<GramTab> gt;
+  std::vector<int32_t> tile_tab, tile_bi, tile_bj, maps;
+  int n_cols = 0, npad_tot = 0;
+  int64_t n_tiles = 0;
+};
+
+GramPlan gram_plan(const BatchJob &J) {
+  GramPlan G;
+  const size_t nt = J.tabs.size();
+  G.gt.resize(nt);
+  for (size_t t = 0; t < nt; t++) {
+    const int n = (int)J.tabs[t].table->n;
+    GramTab &g = G.gt[t];
+    g.n = n;
+    g.n_pad = gram_pad(n);
+    g.row_base = G.npad_tot;
+    g.off = G.n_cols;
+    g.map_off = (int64_t)G.maps.size();
+    const int rows_b = g.n_pad / GRAM_TM, cols_b = g.n_pad / GRAM_TN;
+    std::vector<int32_t> bi, bj;
+    gram_tiles(n, J.tabs[t].start, J.tabs[t].stop, &bi, &bj);
+    std::vector<int32_t> map((size_t)rows_b * cols_b, -1);
+    for (size_t q = 0; q < bi.size(); q++) {
+      map[(size_t)bi[q] * cols_b + bj[q]] = (int32_t)(G.tile_bi.size() + q);
+    }
+    G.maps.insert(G.maps.end(), map.begin(), map.end());
+    G.tile_bi.insert(G.tile_bi.end(), bi.begin(), bi.end());
+    G.tile_bj.insert(G.tile_bj.end(), bj.begin(), bj.end());
+    G.tile_tab.insert(G.tile_tab.end(), bi.size(), (int32_t)t);
+    G.n_cols += n;
+    G.npad_tot += g.n_pad;
+  }
+  G.n_tiles = (int64_t)G.tile_bi.size();
+  return G;
+}
+
+// Stripe cells of the call's tables: (stop - start) * n each.
+int64_t stripe_cells(const BatchJob &J) {
+  int64_t c = 0;
+  for (const TableJob &t : J.tabs) c += (t.stop - t.start) * t.table->n;
+  return c;
+}
+
 // Unweighted, mixed precision, on the tensor cores: per branch block, counts
-// -> presence / split-length planes of every table -> tcgen05 gram; then the
+// -> presence / split-length planes of every table -> tcgen05 gram into the
+// stored tiles; the sparse rows scatter into stripe-layout cells; then the
 // gram finalize of every table.  Throws CudaFail on CUDA errors.
 uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   const auto t_start = std::chrono::steady_clock::now();
   const size_t nt = J.tabs.size();
+  GramPlan G = gram_plan(J);
   std::vector<int> off(nt);
-  std::vector<GramTab> gt(nt);
-  std::vector<int32_t> tile_tab, tile_bi, tile_bj;
-  int n_cols = 0, npad_tot = 0;
-  int64_t gt_cells = 0;
+  std::vector<SpLayout> lay(nt);
+  int64_t cells = 0;
   for (size_t t = 0; t < nt; t++) {
-    const int n = (int)J.tabs[t].table->n;
-    off[t] = n_cols;
-    gt[t].n = n;
-    gt[t].n_pad = gram_pad(n);
-    gt[t].row_base = npad_tot;
-    gt[t].off = n_cols;
-    gt[t].gt_off = gt_cells;
-    const size_t before = tile_bi.size();
-    gram_tiles(gt[t].n_pad, &tile_bi, &tile_bj);
-    tile_tab.insert(tile_tab.end(), tile_bi.size() - before, (int32_t)t);
-    n_cols += n;
-    npad_tot += gt[t].n_pad;
-    gt_cells += (int64_t)gt[t].n_pad * gt[t].n_pad;
+    off[t] = G.gt[t].off;
+    lay[t] = SpLayout{G.gt[t].n, G.gt[t].off, (int)J.tabs[t].start, (int)(J.tabs[t].stop - 1), cells};
+    cells += (J.tabs[t].stop - J.tabs[t].start) * G.gt[t].n;
   }
-  const int n_tiles = (int)tile_bi.size();
+  const int n_cols = G.n_cols, npad_tot = G.npad_tot;
+  const int n_tiles = (int)G.n_tiles;
   const int64_t nb = tree->n_nodes - 1;
-  const int64_t rows = block_rows(nb, (double)n_cols + 4.0 * npad_tot * 2.0 + 8.0, (double)gt_cells * 8.0);
+  const double tile_bytes = (double)G.n_tiles * GRAM_TILE_CELLS * 8.0;
+  const int64_t rows = block_rows(nb, (double)n_cols + 4.0 * npad_tot * 2.0 + 8.0, tile_bytes + cells * 8.0);
   Inputs in = [&] {
     NvtxRange r("uf: bind inputs");
     return bind_inputs(tree, J, device, rows);
@@ -550,79 +710,54 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   cudaStream_t st = J.st;
   int64_t kernels = 0, acc_launches = 0;
   PhaseTimer timer(g_kernel_timing.load() != 0, st);
-  std::vector<int32_t> tl(tile_tab);
-  tl.insert(tl.end(), tile_bi.begin(), tile_bi.end());
-  tl.insert(tl.end(), tile_bj.begin(), tile_bj.end());
+  std::vector<int32_t> tl(G.tile_tab);
+  tl.insert(tl.end(), G.tile_bi.begin(), G.tile_bi.end());
+  tl.insert(tl.end(), G.tile_bj.begin(), G.tile_bj.end());
   // presence rows: stride rounded up to 16 bytes for the 16-byte level kernel
   const int64_t ld = round_up(n_cols, 16);
   DevBuf flags((size_t)in.P->n_slots * ld, st, "alloc presence rows");
   DevBuf Pl((size_t)4 * npad_tot * K_pad * 2, st, "alloc presence planes");
-  DevBuf Gt((size_t)gt_cells * 8, st, "alloc gram");
+  DevBuf Gt((size_t)std::max<int64_t>(G.n_tiles, 1) * GRAM_TILE_CELLS * 8, st, "alloc gram tiles");
   DevBuf err(sizeof(int), st, "alloc error flag");
-  Meta meta;  // tile list, table descriptors and row lists: one staged upload
-  const size_t o_tiles = meta.add(tl), o_tabs = meta.add(gt);
+  DevBuf clamps(sizeof(unsigned long long), st, "alloc clamp counter");
+  DevBuf Msp;
+  Meta meta;  // tile list, table descriptors, tile maps and row lists: one staged upload
+  const size_t o_tiles = meta.add(tl), o_tabs = meta.add(G.gt), o_maps = meta.add(G.maps);
   const size_t o_cnt = meta.add(split.cnt_lists), o_dense = meta.add(split.dense);
-  std::vector<int64_t> sp_off;
-  size_t o_sparse = 0, o_sptabs = 0;
+  // sparse rows: presence terms (x = l) in FP64, one word, min form, into
+  // stripe-layout cells Msp and the per-sample R
+  SparseScatter sc;
+  sc.prepare(tree, J, in, split, lay, ACC_MIN, true, false, cells, n_cols, meta, st);
   if (split.n_sparse > 0) {
-    std::vector<int32_t> all;
-    for (const auto &c : split.sparse) {
-      sp_off.push_back((int64_t)all.size());
-      all.insert(all.end(), c.begin(), c.end());
-    }
-    std::vector<SpTab> sp(nt);
-    for (size_t t = 0; t < nt; t++) {
-      sp[t].col_ptr = in.xd[t]->col_ptr;
-      sp[t].col_row = in.xd[t]->col_row;
-      sp[t].col_val = in.xd[t]->col_val;
-      sp[t].total = in.xd[t]->total;
-      sp[t].inv_total_f = in.xd[t]->inv_total_f;
-      sp[t].n = gt[t].n;
-      sp[t].off = gt[t].off;
-      sp[t].m_off = gt[t].gt_off;
-      sp[t].n_pad = gt[t].n_pad;
-    }
-    o_sparse = meta.add(all);
-    o_sptabs = meta.add(sp);
+    Msp = DevBuf((size_t)cells * 8, st, "alloc sparse stripes");
+    ck(cudaMemsetAsync(Msp.p, 0, (size_t)cells * 8, st), "memset");
   }
   meta.upload(st);
   const int32_t *d_tiles = meta.at<int32_t>(o_tiles);
   const GramTab *d_tabs = meta.at<GramTab>(o_tabs);
   const int32_t *d_cnt = meta.at<int32_t>(o_cnt), *d_dense = meta.at<int32_t>(o_dense);
-  ck(cudaMemsetAsync(Gt.p, 0, (size_t)gt_cells * 8, st), "memset");
+  ck(cudaMemsetAsync(Gt.p, 0, (size_t)std::max<int64_t>(G.n_tiles, 1) * GRAM_TILE_CELLS * 8, st), "memset");
   ck(cudaMemsetAsync(err.p, 0, sizeof(int), st), "memset");
+  ck(cudaMemsetAsync(clamps.p, 0, sizeof(unsigned long long), st), "memset");
   Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
   Capture cap(g_graph.load() != 0 && !timer.on, st, device);
   const cudaStream_t ls = cap.stream();
   // the sparse-row scatters need no count rows or planes: first, on a side
-  // branch beside the presence pass and the gram with option
-  // "sparse_overlap" (both add into Gt with integer atomics)
+  // branch beside the presence pass and the gram with option "sparse_overlap"
   SideBranch side(ls, device);
   const PriorityScope prio(split.n_sparse > 0 && g_overlap.load() != 0);
   cap.node_priority = prio.on;
   if (split.n_sparse > 0) {
     const cudaStream_t ss = g_overlap.load() != 0 ? side.fork() : ls;
     timer.begin(4, ss);
-    for (size_t c = 0; c < split.sparse.size(); c++) {
-      if (split.sparse[c].empty()) continue;
-      SparseArgs sp{};
-      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
-      sp.n_nodes = (int)split.sparse[c].size();
-      sp.cap = split.cap[c];
-      sp.tip_lo = in.td->tip_lo;
-      sp.tip_hi = in.td->tip_hi;
-      sp.length = in.td->length;
-      sp.tabs = meta.at<SpTab>(o_sptabs);
-      sp.n_tabs = (int)nt;
-      sp.kind = EMB_PRESENCE;
-      sp.gram = 1;
-      sp.M = Gt.as<unsigned long long>();
-      sp.alpha = 1.0;
-      sp.scale = scale;
-      ck(launch_sparse_rows(ACC_MIN, false, sp, ss), "sparse rows");
-      kernels++;
-    }
+    SparseArgs sp{};
+    sp.kind = EMB_PRESENCE;
+    sp.abs_mask = 0u;
+    sp.M = Msp.as<unsigned long long>();
+    sp.alpha = 1.0;
+    sp.scale = scale;
+    sc.launch(meta, in, sp, ACC_MIN, true, g_region_bytes.load(), ss, &kernels);
     timer.end();
   }
   for (size_t b = 0; b < in.P->b0.size(); b++) {
@@ -637,7 +772,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
       kernels++;
     }
     timer.end();
-    if (nd == 0) continue;
+    if (nd == 0 || n_tiles == 0) continue;
     GramArgs ga{};
     ga.k_len = (int)round_up(nd, 64);
     ga.kc = 4096;
@@ -656,21 +791,25 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
     timer.end();
     kernels++;
     acc_launches++;
-    exec_flops += 2.0 * 3 * 128.0 * 256.0 * ga.k_len * n_tiles;
+    exec_flops += 2.0 * 3 * (double)GRAM_TILE_CELLS * ga.k_len * n_tiles;
   }
   side.join();
   timer.begin(3);
   for (size_t t = 0; t < nt; t++) {
     GramFinalArgs fa{};
-    fa.n = gt[t].n;
-    fa.n_pad = gt[t].n_pad;
+    fa.n = G.gt[t].n;
+    fa.n_pad = G.gt[t].n_pad;
     fa.s0 = J.tabs[t].start;
     fa.s1 = J.tabs[t].stop;
-    fa.full = J.tabs[t].start == 0 && J.tabs[t].stop == gt[t].n / 2;
-    fa.Gt = Gt.as<unsigned long long>() + gt[t].gt_off;
+    fa.full = J.tabs[t].start == 0 && J.tabs[t].stop == G.gt[t].n / 2;
+    fa.Gt = Gt.as<unsigned long long>();
+    fa.tile_map = meta.at<int32_t>(o_maps) + G.gt[t].map_off;
+    fa.Msp = Msp.p ? Msp.as<unsigned long long>() + lay[t].m_off : nullptr;
+    fa.Dsp = sc.Dsp.p ? sc.Dsp.as<unsigned long long>() + off[t] : nullptr;
     fa.out = o.dev[t];
     fa.out_fp32 = J.out_fp32;
     fa.err = err.as<int>();
+    fa.clamps = clamps.as<unsigned long long>();
     ck(launch_finalize_gram(fa, ls), "finalize");
     kernels++;
   }
@@ -681,23 +820,30 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   // the finalize has already written NaN to every output when it is set
   const bool sync = !J.out_is_device || st == nullptr || timer.on;
   int h_err = 0;
-  if (sync) ck(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
+  unsigned long long h_clamps = 0;
+  if (sync) {
+    ck(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
+    ck(cudaMemcpyAsync(&h_clamps, clamps.p, sizeof h_clamps, cudaMemcpyDeviceToHost, st), "copy count");
+  }
   if (!J.out_is_device)
     for (size_t t = 0; t < nt; t++)
       ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
   flags = DevBuf();
   Pl = DevBuf();
   Gt = DevBuf();
+  Msp = DevBuf();
+  sc = SparseScatter();
   meta.dev = DevBuf();
   o.tmp.clear();
   err = DevBuf();
+  clamps = DevBuf();
   if (sync) ck(cudaStreamSynchronize(st), "synchronize");
   else ck(cudaGetLastError(), "enqueue");
   if (h_err) return fail(UF_ETIMEOUT, "tensor-core kernel: a bounded wait gave up");
   double ms[5] = {0, 0, 0, 0, 0};
   timer.collect(ms);
-  fill_reports(tree, J, o, ms, kernels, acc_launches, 1, rows, (int64_t)in.P->b0.size(), exec_flops, 256, 128,
-               std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+  fill_reports(tree, J, o, ms, kernels, acc_launches, 1, rows, (int64_t)in.P->b0.size(), exec_flops, GRAM_TN,
+               GRAM_TM, std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
   for (const TableJob &t : J.tabs)
     if (t.rep) {
       t.rep->chunk_rows = 4096;
@@ -706,6 +852,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
       t.rep->sparse_rows = split.n_sparse;
       t.rep->sparse_pairs = split.pairs;
       t.rep->t_sparse_ms = ms[4];
+      t.rep->clamped = sync ? (int32_t)std::min<unsigned long long>(h_clamps, INT32_MAX) : -1;
     }
   return UF_OK;
 }
@@ -745,7 +892,10 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     cells += (J.tabs[t].stop - J.tabs[t].start) * (int64_t)n;
   }
   const int64_t nb = tree->n_nodes - 1;
-  const double acc_bytes = (double)cells * 8.0 * (acc == ACC_GEN ? 2 : 1) + n_cols * 8.0;
+  // FP64: every fixed-point accumulator has a second word (uf_device.cuh),
+  // stored after the first: M and M2 at + cells, Dg and the sparse R at + n_cols
+  const int words = fp32 ? 1 : 2;
+  const double acc_bytes = ((double)cells * 8.0 * (acc == ACC_GEN ? 2 : 1) + n_cols * 8.0) * words;
   const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + (double)pitch * es + 8.0 + n_cols * es / 64.0, acc_bytes);
   Inputs in = [&] {
     NvtxRange r("uf: bind inputs");
@@ -762,10 +912,11 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   PhaseTimer timer(g_kernel_timing.load() != 0, st);
   // count rows: stride rounded up to 16 elements for the 16-byte level kernel
   const int64_t ld = round_up(n_cols, 16);
+  const size_t m_bytes = (size_t)cells * 8 * words, d_bytes = (size_t)n_cols * 8 * words;
   DevBuf counts((size_t)in.P->n_slots * ld * 8, st, "alloc counts");
   DevBuf X((size_t)xrows * pitch * es, st, "alloc embeddings");
-  DevBuf M((size_t)cells * 8, st, "alloc stripes");
-  DevBuf M2, Dg, Dsp, diag_tmp, counter(sizeof(int), st, "alloc counter");
+  DevBuf M(m_bytes, st, "alloc stripes");
+  DevBuf M2, Dg, diag_tmp, counter(sizeof(int), st, "alloc counter");
   DevBuf clamps(sizeof(unsigned long long), st, "alloc clamp counter");
   DevBuf total((size_t)n_cols * 8, st, "alloc totals"), inv_total((size_t)n_cols * 4, st, "alloc totals");
   // table descriptors and row lists: one staged upload
@@ -774,53 +925,10 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const size_t o_cnt = meta.add(split.cnt_lists);
   const size_t o_dense = meta.add(split.dense);
   const size_t o_dlen = meta.add(split.dense_len);
-  size_t o_sparse = 0, o_sptabs = 0, o_lofs = 0;
-  std::vector<int64_t> sp_off;  // first entry of each capacity class in the sparse list
-  // one table whose accumulators exceed the L2 budget: the sparse rows write
-  // their sample lists, then scatter their pairs stripe region by region
-  const int n_acc = acc == ACC_GEN ? 2 : 1;
-  const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc);
-  const bool region_mode = split.n_sparse > 0 && (n_regions > 1 || split.lists);
-  int64_t n_sparse_rows = 0;
-  DevBuf le, lk, lz;
-  if (split.n_sparse > 0) {
-    std::vector<int32_t> all;
-    for (const auto &c : split.sparse) {
-      sp_off.push_back((int64_t)all.size());
-      all.insert(all.end(), c.begin(), c.end());
-    }
-    n_sparse_rows = (int64_t)all.size();
-    if (region_mode) {
-      const auto &cp = J.tabs[0].table->col_ptr;
-      std::vector<int64_t> lofs(all.size() + 1, 0);
-      for (size_t r = 0; r < all.size(); r++)
-        lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
-      const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
-      le = DevBuf(total_e * sparse_entry_bytes(fp32), st, "alloc sparse lists");
-      lk = DevBuf(total_e * 4, st, "alloc sparse lists");
-      lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
-      // rows without entries in the table return before writing their count
-      ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
-      o_lofs = meta.add(lofs);
-    }
-    std::vector<SpTab> sp(nt);
-    for (size_t t = 0; t < nt; t++) {
-      sp[t].col_ptr = in.xd[t]->col_ptr;
-      sp[t].col_row = in.xd[t]->col_row;
-      sp[t].col_val = in.xd[t]->col_val;
-      sp[t].total = in.xd[t]->total;
-      sp[t].inv_total_f = in.xd[t]->inv_total_f;
-      sp[t].n = tabs[t].n;
-      sp[t].off = tabs[t].off;
-      sp[t].s_lo = tabs[t].s_lo;
-      sp[t].s_hi = tabs[t].s_hi;
-      sp[t].m_off = tabs[t].m_off;
-    }
-    o_sparse = meta.add(all);
-    o_sptabs = meta.add(sp);
-    Dsp = DevBuf((size_t)n_cols * 8, st, "alloc diagonal");
-    ck(cudaMemsetAsync(Dsp.p, 0, (size_t)n_cols * 8, st), "memset");
-  }
+  std::vector<SpLayout> lay(nt);
+  for (size_t t = 0; t < nt; t++) lay[t] = SpLayout{tabs[t].n, tabs[t].off, tabs[t].s_lo, tabs[t].s_hi, tabs[t].m_off};
+  SparseScatter sc;
+  sc.prepare(tree, J, in, split, lay, acc, !fp32, !fp32, cells, n_cols, meta, st);
   meta.upload(st);
   const TabDesc *d_tabs = meta.at<TabDesc>(o_tabs);
   const int32_t *d_cnt = meta.at<int32_t>(o_cnt);
@@ -835,14 +943,14 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
        "gather totals");
   }
   if (acc == ACC_GEN) {
-    M2 = DevBuf((size_t)cells * 8, st, "alloc stripes");
-    ck(cudaMemsetAsync(M2.p, 0, (size_t)cells * 8, st), "memset");
+    M2 = DevBuf(m_bytes, st, "alloc stripes");
+    ck(cudaMemsetAsync(M2.p, 0, m_bytes, st), "memset");
   } else {
-    Dg = DevBuf((size_t)n_cols * 8, st, "alloc diagonal");
+    Dg = DevBuf(d_bytes, st, "alloc diagonal");
     diag_tmp = DevBuf(diag_scratch_bytes(fp32, (int)xrows, n_cols), st, "alloc diagonal scratch");
-    ck(cudaMemsetAsync(Dg.p, 0, (size_t)n_cols * 8, st), "memset");
+    ck(cudaMemsetAsync(Dg.p, 0, d_bytes, st), "memset");
   }
-  ck(cudaMemsetAsync(M.p, 0, (size_t)cells * 8, st), "memset");
+  ck(cudaMemsetAsync(M.p, 0, m_bytes, st), "memset");
   ck(cudaMemsetAsync(clamps.p, 0, sizeof(unsigned long long), st), "memset");
   Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
@@ -860,52 +968,16 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   Capture cap(g_graph.load() != 0 && !timer.on && !tune, st, device);
   const cudaStream_t ls = cap.stream();
   // the sparse-row scatters run after the dense blocks, whose chunk tuning clears M
-  auto sparse_args = [&]() {
+  auto launch_sparse = [&](cudaStream_t on) {
     SparseArgs sp{};
-    sp.tip_lo = in.td->tip_lo;
-    sp.tip_hi = in.td->tip_hi;
-    sp.length = in.td->length;
-    sp.tabs = meta.at<SpTab>(o_sptabs);
-    sp.n_tabs = (int)nt;
     sp.kind = kind;
     sp.abs_mask = acc == ACC_MIN ? abs_row_mask(fp32) : 0u;
     sp.gen_abs = acc == ACC_GEN && !fp32;
     sp.M = M.as<unsigned long long>();
     sp.M2 = M2.as<unsigned long long>();
-    sp.Dsp = Dsp.as<unsigned long long>();
     sp.alpha = J.alpha;
     sp.scale = scale;
-    if (region_mode) {
-      sp.le = le.p;
-      sp.lk = lk.as<int>();
-      sp.lofs = meta.at<int64_t>(o_lofs);
-      sp.lz = lz.as<int>();
-    }
-    return sp;
-  };
-  auto launch_sparse = [&](cudaStream_t on) {
-    for (size_t c = 0; c < split.sparse.size(); c++) {
-      if (split.sparse[c].empty()) continue;
-      SparseArgs sp = sparse_args();
-      sp.row_base = (int)sp_off[c];
-      sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
-      sp.n_nodes = (int)split.sparse[c].size();
-      sp.cap = split.cap[c];
-      if (region_mode) ck(launch_sparse_lists(acc, fp32, sp, on), "sparse lists");
-      else ck(launch_sparse_rows(acc, fp32, sp, on), "sparse rows");
-      kernels++;
-    }
-    if (!region_mode) return;
-    const int64_t per = std::max<int64_t>(1, (int64_t)((double)g_region_bytes.load() / (8.0 * n_acc * tabs[0].n)));
-    for (int64_t r0 = tabs[0].s_lo; r0 <= tabs[0].s_hi; r0 += per) {
-      SparseArgs sp = sparse_args();
-      sp.nodes = meta.at<int32_t>(o_sparse);
-      sp.n_nodes = (int)n_sparse_rows;
-      sp.r0 = (int)r0;
-      sp.r1 = (int)std::min<int64_t>(r0 + per, (int64_t)tabs[0].s_hi + 1);
-      ck(launch_sparse_region(acc, fp32, sp, on), "sparse regions");
-      kernels++;
-    }
+    sc.launch(meta, in, sp, acc, !fp32, g_region_bytes.load(), on, &kernels);
   };
   // with option "sparse_overlap" (default) the sparse-row scatter runs on a
   // side branch beside the count pass, the embeddings and the dense stripe
@@ -951,8 +1023,10 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sa.alpha = J.alpha;
     sa.scale = scale;
     sa.counter = counter.as<int>();
+    sa.m_lo_off = fp32 ? 0 : cells;
+    sa.d_lo_off = fp32 ? 0 : n_cols;
     if (tune && !tuned) {
-      chunk = sa.chunk = tune_chunk(acc, fp32, sa, (size_t)cells, ls);
+      chunk = sa.chunk = tune_chunk(acc, fp32, sa, m_bytes, ls);
       tuned = true;
       std::lock_guard<std::mutex> g(g_tune_mu);
       g_tuned_chunk[key] = chunk;
@@ -990,7 +1064,9 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     fa.M = M.as<unsigned long long>() + tabs[t].m_off;
     fa.M2 = M2.p ? M2.as<unsigned long long>() + tabs[t].m_off : nullptr;
     fa.Dg = Dg.p ? Dg.as<unsigned long long>() + off[t] : nullptr;
-    fa.Dsp = Dsp.p ? Dsp.as<unsigned long long>() + off[t] : nullptr;
+    fa.Dsp = sc.Dsp.p ? sc.Dsp.as<unsigned long long>() + off[t] : nullptr;
+    fa.m_lo_off = fp32 ? 0 : cells;
+    fa.d_lo_off = fp32 ? 0 : n_cols;
     fa.inv_scale = 1.0 / scale;
     fa.out = o.dev[t];
     fa.out_fp32 = J.out_fp32;
@@ -1012,7 +1088,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   M = DevBuf();
   M2 = DevBuf();
   Dg = DevBuf();
-  Dsp = DevBuf();
+  sc = SparseScatter();
   diag_tmp = DevBuf();
   counter = DevBuf();
   clamps = DevBuf();
@@ -1062,17 +1138,14 @@ uf_status run_batch(uf_tree *tree, const BatchJob &J) {
     scale = scale == 0.0 ? s : std::min(scale, s);
   }
   if (method == UF_UNWEIGHTED && J.fp32 && g_tensor_path.load()) {
-    // the tensor path keeps every table's whole n_pad x n_pad gram matrix (int64) on the
-    // device whatever the stripe range; when that does not fit in half the free memory
-    // the CUDA-core stripe kernels, which store only the requested stripes, take the call
-    double gram_bytes = 0.0;
-    for (const TableJob &t : J.tabs) {
-      const double np = (double)gram_pad((int)t.table->n);
-      gram_bytes += np * np * 8.0;
-    }
+    // the tensor path stores the gram tiles the stripes need (and the
+    // diagonal) plus the sparse rows' stripe cells; when those do not fit in
+    // half the free memory the CUDA-core stripe kernels take the call
+    const GramPlan G = gram_plan(J);
+    const double need = (double)G.n_tiles * GRAM_TILE_CELLS * 8.0 + (double)stripe_cells(J) * 8.0;
     size_t free_b = 0, total_b = 0;
     ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-    if (gram_bytes <= 0.5 * (double)free_b) return run_gram(tree, J, device, scale);
+    if (need <= 0.5 * (double)free_b) return run_gram(tree, J, device, scale);
   }
   return run_stripes(tree, J, device, method, scale);
 }

@@ -21,10 +21,11 @@
 //   branch where u or v is nonzero (a one-sided branch gives l u^a to both),
 //   and two identical samples still give num = 0 exactly.
 // The finalize adds R[k] + R[j] where these terms need it (uf_finalize.cu);
-// integer addition makes the order free and the result deterministic.
-// For the tensor-core unweighted path the same presence terms go into its
-// gram matrices: G[j][k] += l per both-nonzero pair and G[k][k] += l per
-// nonzero sample (the diagonal W of uf_gram.cu).
+// integer addition makes the order free and the result deterministic.  FP64
+// terms carry the two-word fixed point of uf_device.cuh (every word summed on
+// its own).  The tensor-core unweighted path scatters its sparse rows the
+// same way, in the min form on presence rows (x = l): its finalize adds the
+// cells to the gram matrix G and R to its diagonal.
 //
 // One CTA per (sparse branch, table).  The branch's tips are a contiguous
 // range of tip numbers, so its nonzero counts are one contiguous run of the
@@ -91,6 +92,14 @@ __device__ __forceinline__ T pow_am1(T s, T am1) {
 __device__ __forceinline__ void red_add(unsigned long long *p, long long v) {
   atomicAdd(p, (unsigned long long)v);
 }
+// both words of an FP64 term (the second lo_off elements after the first;
+// lo_off == 0: one word, the first)
+template <typename T>
+__device__ __forceinline__ void red_add2(unsigned long long *p, int64_t lo_off, Fx2 v) {
+  red_add(p, v.hi);
+  if constexpr (sizeof(T) == 8)
+    if (lo_off != 0) red_add(p + lo_off, v.lo);
+}
 
 // One distinct sample of a sparse row: its sample k, value x (or
 // proportion u) and fixed-point term f, packed so that one 16-byte load
@@ -107,8 +116,15 @@ template <>
 struct alignas(16) SpEnt<double> {
   int k, pad;
   double x;
-  long long f;
+  long long f, f_lo;
 };
+__device__ __forceinline__ Fx2 ent_f(const SpEnt<float> &e) { return Fx2{e.f, 0}; }
+__device__ __forceinline__ Fx2 ent_f(const SpEnt<double> &e) { return Fx2{e.f, e.f_lo}; }
+__device__ __forceinline__ void set_f(SpEnt<float> &e, Fx2 v) { e.f = v.hi; }
+__device__ __forceinline__ void set_f(SpEnt<double> &e, Fx2 v) {
+  e.f = v.hi;
+  e.f_lo = v.lo;
+}
 
 // What a pair update needs besides its two entries.
 template <typename T>
@@ -116,6 +132,7 @@ struct PairCtx {
   int n, s_lo, s_hi;
   unsigned abs_mask;           // stripes in the abs form (abs_row)
   int gen_abs;                 // generalized: M2 holds N (1) or Q (0)
+  int64_t m_lo_off;            // FP64: second words of M / M2 this many elements on
   unsigned long long *M, *M2;  // this table's cells (den and Q for the generalized method)
   T lt, am1;                   // branch length, alpha - 1
   double scale;
@@ -139,23 +156,25 @@ __device__ __forceinline__ void add_pair(const SpEnt<T> &ea, const SpEnt<T> &eb,
   if (s < c.s_lo || s > c.s_hi) return;
   const int64_t cell = (int64_t)(s - c.s_lo) * c.n + kc;
   const bool dup = 2 * d == c.n;  // also stored at k = k_b (= k_a + n/2)
+  const Fx2 fa = ent_f(ea), fb = ent_f(eb);
   if (ACC == ACC_MIN) {
-    long long t = min(ea.f, eb.f);
-    if (abs_row(c.abs_mask, s)) t *= -2;
-    red_add(c.M + cell, t);
-    if (dup) red_add(c.M + cell + d, t);
+    Fx2 t = fx_min(fa, fb);
+    if (abs_row(c.abs_mask, s)) t = fx_mul(t, -2);
+    red_add2<T>(c.M + cell, c.m_lo_off, t);
+    if (dup) red_add2<T>(c.M + cell + d, c.m_lo_off, t);
   } else {
     const T uu = ea.x, vv = eb.x;
     const T w = c.lt * pow_am1<T, MODE>(uu + vv, c.am1);
-    const long long q = to_fixed(w * tmin<T>(uu, vv), c.scale);
-    const long long e = to_fixed(w * (uu > vv ? uu - vv : vv - uu), c.scale);
-    const long long den = 2 * q + e - ea.f - eb.f;
-    const long long t2 = c.gen_abs ? e - ea.f - eb.f : q;
-    red_add(c.M + cell, den);
-    red_add(c.M2 + cell, t2);
+    const Fx2 q = to_fixed2(w * tmin<T>(uu, vv), c.scale);
+    const Fx2 e = to_fixed2(w * (uu > vv ? uu - vv : vv - uu), c.scale);
+    const Fx2 e_ab = fx_sub(fx_sub(e, fa), fb);
+    const Fx2 den = fx_add(fx_mul(q, 2), e_ab);
+    const Fx2 t2 = c.gen_abs ? e_ab : q;
+    red_add2<T>(c.M + cell, c.m_lo_off, den);
+    red_add2<T>(c.M2 + cell, c.m_lo_off, t2);
     if (dup) {
-      red_add(c.M + cell + d, den);
-      red_add(c.M2 + cell + d, t2);
+      red_add2<T>(c.M + cell + d, c.m_lo_off, den);
+      red_add2<T>(c.M2 + cell + d, c.m_lo_off, t2);
     }
   }
 }
@@ -222,22 +241,18 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
     if (a.kind == EMB_SCALED) x = emb_value<T, EMB_SCALED>(c, l, tb.total[smp], tb.inv_total_f[smp]);
     else if (a.kind == EMB_PRESENCE) x = emb_value<T, EMB_PRESENCE>(c, l, tb.total[smp], tb.inv_total_f[smp]);
     else x = emb_value<T, EMB_PROP>(c, l, tb.total[smp], tb.inv_total_f[smp]);
-    long long f;
-    if (ACC == ACC_MIN) f = to_fixed(x, a.scale);
-    else f = to_fixed((T)l * pow_alpha<T, MODE>(x, alpha), a.scale);
+    Fx2 f;
+    if (ACC == ACC_MIN) f = to_fixed2(x, a.scale);
+    else f = to_fixed2((T)l * pow_alpha<T, MODE>(x, alpha), a.scale);
     SpEnt<T> en;
     en.k = (int)smp;
     en.x = x;
-    en.f = f;
+    set_f(en, f);
     E[u] = en;
     u++;
   }
   __syncthreads();
-  if (a.gram) {
-    for (int e = tid; e < z; e += NT) red_add(a.M + tb.m_off + (int64_t)E[e].k * tb.n_pad + E[e].k, E[e].f);
-  } else {
-    for (int e = tid; e < z; e += NT) red_add(a.Dsp + tb.off + E[e].k, E[e].f);
-  }
+  for (int e = tid; e < z; e += NT) red_add2<T>(a.Dsp + tb.off + E[e].k, a.d_lo_off, ent_f(E[e]));
 
   // pairs (ia < ib) numbered row by row: row ia starts at ia (2z - ia - 1) / 2
   const int64_t npairs = (int64_t)z * (z - 1) / 2;
@@ -254,24 +269,13 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
   while (ia < z - 2 && row_start(ia + 1) <= p) ia++;
   int ib = ia + 1 + (int)(p - row_start(ia));
   SpEnt<T> ea = E[ia];
-  if (ACC == ACC_MIN && a.gram) {
-    for (; p < p1; p++) {
-      const SpEnt<T> eb = E[ib];
-      red_add(a.M + tb.m_off + (int64_t)eb.k * tb.n_pad + ea.k, min(ea.f, eb.f));
-      if (++ib == z) {
-        ia++;
-        ib = ia + 1;
-        ea = E[ia];
-      }
-    }
-    return;
-  }
   PairCtx<T> c;
   c.n = tb.n;
   c.s_lo = tb.s_lo;
   c.s_hi = tb.s_hi;
   c.abs_mask = a.abs_mask;
   c.gen_abs = a.gen_abs;
+  c.m_lo_off = a.m_lo_off;
   c.M = a.M + tb.m_off;
   c.M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
   c.lt = (T)l;
@@ -346,16 +350,16 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
     if (a.kind == EMB_SCALED) x = emb_value<T, EMB_SCALED>(c, l, tb.total[smp], tb.inv_total_f[smp]);
     else if (a.kind == EMB_PRESENCE) x = emb_value<T, EMB_PRESENCE>(c, l, tb.total[smp], tb.inv_total_f[smp]);
     else x = emb_value<T, EMB_PROP>(c, l, tb.total[smp], tb.inv_total_f[smp]);
-    long long f;
-    if (ACC == ACC_MIN) f = to_fixed(x, a.scale);
-    else f = to_fixed((T)l * pow_alpha<T, MODE>(x, alpha), a.scale);
+    Fx2 f;
+    if (ACC == ACC_MIN) f = to_fixed2(x, a.scale);
+    else f = to_fixed2((T)l * pow_alpha<T, MODE>(x, alpha), a.scale);
     SpEnt<T> en;
     en.k = (int)smp;
     en.x = x;
-    en.f = f;
+    set_f(en, f);
     le[off + u] = en;
     a.lk[off + u] = (int)smp;
-    red_add(a.Dsp + tb.off + smp, f);
+    red_add2<T>(a.Dsp + tb.off + smp, a.d_lo_off, f);
     u++;
   }
   if (tid == 0) a.lz[row] = z;
@@ -388,6 +392,7 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   c.s_hi = tb.s_hi;
   c.abs_mask = a.abs_mask;
   c.gen_abs = a.gen_abs;
+  c.m_lo_off = a.m_lo_off;
   c.M = a.M + tb.m_off;
   c.M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
   c.lt = (T)a.length[v];

@@ -21,8 +21,7 @@ struct SpTab {
   const double *total;      // per-sample count totals
   const float *inv_total_f; // 1 / total in FP32
   int n, off, s_lo, s_hi;   // samples, combined column, stored stripes
-  int64_t m_off;            // first accumulator cell (gram layout: first cell of its gram matrix)
-  int n_pad;                // gram layout: row length of its gram matrix
+  int64_t m_off;            // first accumulator cell
 };
 struct SparseArgs {
   const int32_t *nodes;     // sparse branch nodes of this launch
@@ -35,10 +34,8 @@ struct SparseArgs {
   int kind;                 // EmbKind
   unsigned abs_mask;        // min kernels: stripes s with abs_row(abs_mask, s) in the abs form
   int gen_abs;              // generalized: M2 holds N (FP64 kernels) instead of Q (FP32)
-  int gram;                 // 1: presence rows into the tensor path's gram matrices
-                            // (cell (i, j), i <= j, at m_off + j * n_pad + i; the
-                            // diagonal takes the per-sample terms; Dsp unused)
   unsigned long long *M, *M2, *Dsp;  // cells (M / den), Q or N (generalized), per-sample diagonal R
+  int64_t m_lo_off, d_lo_off;        // FP64: second words of M / M2 and of Dsp, this many elements on
   double alpha, scale;
   // list mode (one table, launch_sparse_lists): row blockIdx.x writes its
   // distinct samples, values and fixed-point terms at lofs[row_base +

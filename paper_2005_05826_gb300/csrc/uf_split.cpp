@@ -9,7 +9,7 @@ namespace rt {
 
 double sparse_regions(size_t n_tables, int acc, double acc_bytes) {
   const double budget = (double)g_region_bytes.load();
-  if (n_tables != 1 || acc == SPLIT_GRAM || acc_bytes <= budget) return 1.0;
+  if (n_tables != 1 || acc_bytes <= budget) return 1.0;
   return std::ceil(acc_bytes / budget);
 }
 
@@ -34,7 +34,9 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
   R.sparse.resize(5);
   std::vector<char> is_sparse(std::max<int64_t>(nb, 1), 0);
   if (mode != 0) {
-    const int n_acc = acc == ACC_GEN ? 2 : 1;
+    // accumulator words per cell: FP64 terms are two-word fixed point
+    // (uf_device.cuh) except on the tensor path, whose sparse rows keep one
+    const int n_acc = (acc == ACC_GEN ? 2 : 1) * (fp32 || acc == SPLIT_GRAM ? 1 : 2);
     double cells = 0.0, cols = 0.0;  // stripe cells of a full run of every table; samples
     for (size_t t = 0; t < nt; t++) {
       const double n = (double)J.tabs[t].table->n;

@@ -34,7 +34,8 @@
 // Precision.  Register partials over B1 = 64 branches are summed into a
 // second level kept in shared memory in the path's own precision (FP32 for
 // the paper's fp32 mode, Sec. 4, FP64 otherwise); at the end of the unit that
-// level is scaled by 2^F and rounded once to an int64 fixed-point value,
+// level is scaled by 2^F and rounded once to an int64 fixed-point value (FP64:
+// two words, the second holding the remainder at 2^-32 of the first's step),
 // which is added atomically into the int64 accumulator.  Integer addition is
 // exact and order-free, so chunks may land in any order and the result is
 // still deterministic; every cell (and the diagonal) runs the same FP32 /
@@ -202,8 +203,9 @@ __device__ __forceinline__ void commit_cells(unsigned long long *M, const Mid *m
     for (int j = 0; j < RK; j++) {
       const int k = k_base + j;
       if (k < U.n) {
-        const long long q = to_fixed(mid[(i * RK + j) * NT + threadIdx.x], a.scale);
-        atomicAdd(row + k, (unsigned long long)q);
+        const Fx2 q = to_fixed2(mid[(i * RK + j) * NT + threadIdx.x], a.scale);
+        atomicAdd(row + k, (unsigned long long)q.hi);
+        if constexpr (sizeof(T) == 8) atomicAdd(row + k + a.m_lo_off, (unsigned long long)q.lo);
       }
     }
   }
@@ -473,16 +475,17 @@ __global__ void k_diag_reduce(const StripeArgs a, const T *__restrict__ part, in
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n_cols) return;
   const int per_chunk = (a.chunk + B1 - 1) / B1;
-  long long d = 0;
+  Fx2 d{0, 0};
   T mid = T(0);
   for (int sb = 0; sb < n_sb; sb++) {
     mid += part[(int64_t)sb * a.n_cols + k];
     if ((sb + 1) % per_chunk == 0 || sb == n_sb - 1) {
-      d += to_fixed(mid, a.scale);
+      d = fx_add(d, to_fixed2(mid, a.scale));
       mid = T(0);
     }
   }
-  a.Dg[k] += (unsigned long long)d;
+  a.Dg[k] += (unsigned long long)d.hi;
+  if constexpr (sizeof(T) == 8) a.Dg[k + a.d_lo_off] += (unsigned long long)d.lo;
 }
 
 template <typename K>

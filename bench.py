@@ -1,18 +1,23 @@
 #!/usr/bin/env python3
 """Benchmark: Striped UniFrac pair x branch updates per second on GB300.
 
-Workload (default): a seeded Yule tree with 50,000 tips (99,999 nodes,
-lengths Exp(mean 0.1)) and 2,048 samples whose features have prevalence
-Beta(0.5, 20) and counts 1 + Poisson(LogNormal(1, 1)); synthetic, generated
-by ``synth``.  One step = the whole hot path (embedding levels, stripe
-accumulate, diagonal, finalize) for each of the four methods (unweighted,
-weighted_unnormalized, weighted_normalized, generalized alpha = 0.5) over
-all stripes.  ``value`` is pair x branch updates per second of the mixed
-path with inputs resident on the GPU; the FP64 path is measured beside it,
-and the mixed result's largest difference from the FP64 result is reported
-over every value (parity of both paths with the FP64 oracle is the tests'
-job).  The oracle runs here only as the CPU baseline and as the reference
-arm.
+Workload (default): the 113k-shaped one -- a seeded Yule tree with 500,000
+tips (999,999 nodes, lengths Exp(mean 0.1)) and 113,000 samples whose
+features have prevalence Beta(0.06, 19.94) and heavy-tailed counts
+max(1, round(LogNormal(1, 1.5))) (169 M nonzeros); synthetic, generated by
+``synth``.  One step = the whole hot path (count levels, embeddings or
+presence planes, dense accumulate or tensor-core gram, sparse-row scatter,
+diagonal, finalize) for the workload's two methods, unweighted (tcgen05
+split-BF16 gram) and weighted_normalized, over the stripe range
+[0, 8,192) of 56,500.  Other workloads: ``--workload yule300k_n25000``
+(EMP-shaped, all four methods, full matrix), ``yule50k_n2048`` (all four
+methods, full matrix), ``batched64``.  ``value`` is pair x branch updates
+per second of the mixed path with inputs resident on the GPU; the FP64 path
+is measured beside it (on a stripe slice at the large workloads), and the
+mixed result's largest difference from the FP64 result is reported over
+every value both computed (parity of both paths with the FP64 oracle is the
+tests' job).  The oracle runs here only as the CPU baseline and as the
+reference arm.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -44,10 +49,22 @@ ALL_METHODS = [("unweighted", 1.0), ("weighted_unnormalized", 1.0), ("weighted_n
                ("generalized", 0.5)]
 METHODS = list(ALL_METHODS)
 # CUDA-core FP32 lanes per SM and the SFU rate per SM on GB300 (sm_103): the
-# peaks of the ALU-bound accumulate kernels at the maximum SM clock
+# peaks of the ALU-bound accumulate kernels at the maximum SM clock (the SM
+# count is read from the device)
 FP32_LANES_PER_SM = 128
 SFU_PER_SM = 16
-SMS = 152
+SMS = 152  # replaced by the device's multiprocessor count in run_ours
+
+# per-workload defaults: methods of a step, stripe range [0, stop) (0: all),
+# FP32 distance outputs, FP64 comparison slice [0, k) (0: the whole matrix)
+WORKLOAD_DEFAULTS = {
+    "yule500k_n113000": dict(methods=["unweighted", "weighted_normalized"], stripe_stop=8192, out_fp32=True,
+                             fp64_stripes=64),
+    "yule300k_n25000": dict(methods=[m for m, _ in ALL_METHODS], stripe_stop=0, out_fp32=False,
+                            fp64_stripes=256),
+    "yule50k_n2048": dict(methods=[m for m, _ in ALL_METHODS], stripe_stop=0, out_fp32=False, fp64_stripes=0),
+    "yule1k_n64": dict(methods=[m for m, _ in ALL_METHODS], stripe_stop=0, out_fp32=False, fp64_stripes=0),
+}
 
 
 def env_int(name, default):
@@ -177,17 +194,32 @@ def oracle_sample_rate(tree_s, table_s, target_seconds: float, seed: int = 99):
     return len(METHODS) * i.size * branches / dt, used, int(i.size), dt
 
 
+def sub_table(table_s, n_sub):
+    """The first n_sub samples of a table (same tree, same count recipe)."""
+    from synth import Table as STable
+    ip = table_s.indptr[: n_sub + 1]
+    return STable(n_sub, table_s.n_features, ip.copy(), table_s.indices[: ip[-1]].copy(),
+                  table_s.data[: ip[-1]].copy())
+
+
 def oracle_striped_rate(tree_s, table_s, max_updates_per_thread: float = 1.5e9):
     """The paper's plain striped CPU loop (the oracle's second formulation:
     FP64, host threads over stripes, every branch in postorder) on the stripe
-    slice [0, k), one stripe per host thread, for the four methods of a step:
-    (updates/s, threads, k, seconds), or None when one stripe of every method
-    is too much work to time within the bench's few minutes."""
+    slice [0, k), one stripe per host thread, for the methods of a step:
+    (updates/s, threads, k, seconds, samples).  When one stripe of every
+    method is too much work to time within the bench's few minutes, the loop
+    runs on the first samples of the table (as many as fit that bound, at
+    least 256), labelled as such."""
     import oracle
-    n = table_s.n_samples
-    S = n // 2
     branches = tree_s.n_nodes - 1
-    if S == 0 or len(METHODS) * n * branches > max_updates_per_thread:
+    n = table_s.n_samples
+    if len(METHODS) * n * branches > max_updates_per_thread:
+        n_sub = max(256, int(max_updates_per_thread / (len(METHODS) * branches)))
+        if n_sub < n:
+            table_s = sub_table(table_s, n_sub)
+            n = n_sub
+    S = n // 2
+    if S == 0:
         return None
     k = min(S, oracle.host_cores())
     t0 = time.perf_counter()
@@ -195,7 +227,7 @@ def oracle_striped_rate(tree_s, table_s, max_updates_per_thread: float = 1.5e9):
     for m, a in METHODS:
         used = oracle.striped(tree_s, table_s, m, a, 0, k)[3]
     dt = time.perf_counter() - t0
-    return len(METHODS) * k * n * branches / dt, used, k, dt
+    return len(METHODS) * k * n * branches / dt, used, k, dt, n
 
 
 def run_reference(args, rank, world):
@@ -220,7 +252,7 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": workload_config(args, tree_s, table_s, l2="n/a (host)"),
         "cpu_baseline": {"value": value, "unit": "updates/s", "cores": used, "kind": "oracle",
-                         "sample": f"{pairs} random pairs of {n} samples x 4 methods per step "
+                         "sample": f"{pairs} random pairs of {n} samples x {len(METHODS)} methods per step "
                                    f"(FP64 per-pair tree walk)"},
         "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -230,9 +262,13 @@ def run_reference(args, rank, world):
 
 
 def workload_config(args, tree_s, table_s, l2):
-    return {"workload": args.workload, "tips": tree_s.n_tips, "nodes": tree_s.n_nodes,
+    stop = getattr(args, "stripe_stop", 0)
+    ranged = 0 < stop < table_s.n_samples // 2
+    return {"workload": args.workload + (f"[0,{stop})" if ranged else ""),
+            "tips": tree_s.n_tips, "nodes": tree_s.n_nodes,
             "samples": table_s.n_samples, "nnz": table_s.nnz,
-            "methods": [m for m, _ in METHODS], "alpha": 0.5,
+            "methods": [m for m, _ in METHODS],
+            "alpha": 0.5 if any(m == "generalized" for m, _ in METHODS) else None,
             "stripes": "all" if not 0 < getattr(args, "stripe_stop", 0) < table_s.n_samples // 2
             else f"[0, {args.stripe_stop}) of {table_s.n_samples // 2}",
             "sparse_rows_mode": getattr(args, "sparse", 1),
@@ -271,6 +307,37 @@ def downstream_agreement(mixed_outs, fp64_outs, sub=512, perms=999):
         res[m] = {"mantel_r2": r * r, "mantel_p": p, "p_samples": k, "permutations": perms,
                   "pcoa10_procrustes": ds.procrustes(c64, c32)}
     return res
+
+
+# FP64 instructions per update of the FP64 accumulate kernels: the min / abs
+# kernel one DADD for u - v and one DADD of |u - v| into the accumulator;
+# the generalized kernel's count is the one ncu reports for it
+# (smsp__inst_executed_pipe_fp64 per update, profiles/).
+FP64_OPS_PER_UPDATE = {"min": 2.0, "gen": None}
+# GB300 FP64 lanes per SM and clock: nominal 1.25 TFLOP/s counting an FMA as two
+FP64_LANES_PER_SM = 2.0
+
+
+def fp64_rooflines(f_reps, pairs, sm_max):
+    """Roofline objects of the FP64 accumulate kernels from the per-phase
+    device times of the FP64 calls: updates of the dense branches over the
+    FP64 pipe's instruction rate divided by the instructions per update."""
+    out = {}
+    for m, r in f_reps:
+        if r.acc_launches == 0 or r.t_accumulate_ms <= 0:
+            continue
+        kind = "gen" if m == "generalized" else "min"
+        ach = pairs * r.dense_rows / (r.t_accumulate_ms / 1e3) / 1e12
+        obj = {"kernel": "k_stripe_gen<double,4,8>" if kind == "gen" else "k_stripe_min<double,8,8,abs>",
+               "bound": "alu", "achieved": ach, "unit": "Tupdates/s"}
+        ops = FP64_OPS_PER_UPDATE[kind]
+        if ops:
+            peak = FP64_LANES_PER_SM * SMS * sm_max * 1e6 / ops / 1e12
+            obj.update({"peak": peak, "frac": ach / peak,
+                        "peak_basis": f"FP64 pipe {FP64_LANES_PER_SM:g} lanes/clk/SM x {SMS} SMs x "
+                                      f"{sm_max:.0f} MHz / {ops:g} FP64 instructions per update"})
+        out[f"roofline_{m}"] = obj
+    return out
 
 
 def run_batched(args, rank, world, local_rank):
@@ -370,9 +437,11 @@ def run_ours(args, rank, world, local_rank):
     from paper_2005_05826_gb300 import build as ufbuild
     from synth import workload
 
+    global SMS
     ufbuild.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    SMS = torch.cuda.get_device_properties(dev).multi_processor_count
     tree_s, table_s = workload(args.workload)
     n = table_s.n_samples
     branches = tree_s.n_nodes - 1
@@ -394,14 +463,15 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu:
         r, used, pairs, dt = oracle_sample_rate(tree_s, table_s, args.cpu_seconds)
         cpu = {"value": r, "unit": "updates/s", "cores": used, "kind": "oracle",
-               "sample": f"{pairs} random pairs x 4 methods, {dt:.1f} s (FP64 per-pair tree walk)"}
+               "sample": f"{pairs} random pairs x {len(METHODS)} methods, {dt:.1f} s (FP64 per-pair tree walk)"}
         sl = oracle_striped_rate(tree_s, table_s)
         if sl is not None:
-            r, used, k, dt = sl
+            r, used, k, dt, n_used = sl
+            of = f"of {n_used // 2}" if n_used == n else f"of the first {n_used} samples ({n_used // 2} stripes)"
             cpu["striped_loop"] = {
                 "value": r, "unit": "updates/s", "cores": used,
-                "sample": f"stripes [0, {k}) of {n // 2} x 4 methods, {dt:.1f} s (the plain FP64 striped "
-                          f"loop, one stripe per thread; from a slice)"}
+                "sample": f"stripes [0, {k}) {of} x {len(METHODS)} methods, {dt:.1f} s (the plain FP64 "
+                          f"striped loop, one stripe per thread; from a slice)"}
 
     tree = uf.Tree(tree_s.parent, tree_s.length)
     table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
@@ -457,8 +527,10 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         uf.uf_set_option("kernel_timing", 1)
         # the same steps with per-phase timing: phases, per-kernel rooflines
+        # (one step at the large workloads, where a step takes seconds)
         t_phase, reps = [], []
-        for _ in range(args.steps):
+        phase_steps = args.steps if len(METHODS) * npairs * branches < 5e13 else 1
+        for _ in range(phase_steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -494,12 +566,12 @@ def run_ours(args, rank, world, local_rank):
         d[5] = r.dense_rows
         sp = sparse.setdefault(m, {"rows": r.sparse_rows, "dense_rows": d[5], "pairs_at_most": r.sparse_pairs,
                                    "ms_per_call": 0.0})
-        sp["ms_per_call"] += r.t_sparse_ms / args.steps
+        sp["ms_per_call"] += r.t_sparse_ms / phase_steps
         ph = phases.setdefault(m, {"embed": 0.0, "accumulate": 0.0, "diagonal": 0.0, "sparse": 0.0,
                                    "finalize": 0.0})
         for key, val in (("embed", r.t_embed_ms), ("accumulate", r.t_accumulate_ms), ("diagonal", r.t_diag_ms),
                          ("sparse", r.t_sparse_ms), ("finalize", r.t_finalize_ms)):
-            ph[key] += val / args.steps
+            ph[key] += val / phase_steps
     kern = {}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     for m, (ms, nl, ncalls, xflops, path, drows) in acc_ms.items():
@@ -552,9 +624,14 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:  # every rank: the job's end-to-end rate at N GPUs
         uf.uf_set_option("kernel_timing", 0)
         host_res = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+        # at the large workloads (steps of seconds, results of GB) the
+        # device-output variant alone, one warm-up and two timed steps
+        large = len(METHODS) * npairs * branches >= 5e13
+        modes = (False,) if large else (False, True)
         # pageable result arrays of the host-output variant, allocated (and first
         # touched) once, as a caller keeps its result buffers
-        host_arrays = [np.zeros(o.numel(), dtype=np.float32 if args.out_fp32 else np.float64) for o in outs]
+        host_arrays = ([] if large else
+                       [np.zeros(o.numel(), dtype=np.float32 if args.out_fp32 else np.float64) for o in outs])
         e2e_stream = torch.cuda.Stream(dev)  # a null stream would make every call synchronous
 
         def e2e_step(sync_host):
@@ -566,7 +643,7 @@ def run_ours(args, rank, world, local_rank):
             tb = uf.Table(table_s.indptr, table_s.indices, table_s.data, tr)
             hb = db = 0.0
             with torch.cuda.stream(e2e_stream):
-                for (m, a), o, ha in zip(METHODS, outs, host_arrays):
+                for (m, a), o, ha in zip(METHODS, outs, host_arrays or [None] * len(outs)):
                     if sync_host:  # host output: each call returns with its result on the host
                         r, rep = uf.uf_compute(tr, tb, m, a, "mixed", *rng_args, out=ha, out_fp32=args.out_fp32)
                         db += r.nbytes
@@ -584,9 +661,9 @@ def run_ours(args, rank, world, local_rank):
             return dt, hb, db
 
         res = {}
-        for mode in (False, True):
+        for mode in modes:
             e_times = []
-            for s in range(max(1, min(args.steps, 3)) + 1):
+            for s in range((2 if large else max(1, min(args.steps, 3))) + 1):
                 dt, h2d, d2h = e2e_step(mode)
                 if s > 0:  # the first is a warm-up
                     e_times.append(dt)
@@ -599,13 +676,14 @@ def run_ours(args, rank, world, local_rank):
         t_e, h2d, d2h = res[False]
         e2e = {"value": world * updates_step / t_e, "unit": "updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e,
-               "path": "fresh tree and table handles from the host arrays, four uf_compute calls queued on "
-                       "the stream with device outputs, results read into pinned host memory",
-               "host_output_calls": {"value": world * updates_step / res[True][0],
-                                     "ms_per_step": 1e3 * res[True][0],
-                                     "d2h_bytes_per_step": int(res[True][2]),
-                                     "path": "the same with pageable host result arrays the caller reuses "
-                                             "(each call returns synchronously)"}}
+               "path": f"fresh tree and table handles from the host arrays, {len(METHODS)} uf_compute calls "
+                       f"queued on the stream with device outputs, results read into pinned host memory"}
+        if True in res:
+            e2e["host_output_calls"] = {"value": world * updates_step / res[True][0],
+                                        "ms_per_step": 1e3 * res[True][0],
+                                        "d2h_bytes_per_step": int(res[True][2]),
+                                        "path": "the same with pageable host result arrays the caller reuses "
+                                                "(each call returns synchronously)"}
         uf.uf_set_option("kernel_timing", 1)
 
     # ---- FP64 path beside it ----
@@ -623,6 +701,20 @@ def run_ours(args, rank, world, local_rank):
         for m, a in METHODS:
             _, rep = uf.uf_compute(tree, table, m, a, "fp64", 0, k, out=sl)
             f_reps.append((m, rep))
+            # the mixed result on the same cells (stripe-major range output, or
+            # gathered from the condensed full output)
+            if full:
+                cs = torch.arange(k * n, device=dev, dtype=torch.int64)
+                ss, kk = cs // n, cs % n
+                jj = (kk + ss + 1) % n
+                lo, hi = torch.minimum(kk, jj), torch.maximum(kk, jj)
+                mixed_sl = outs[METHODS.index((m, a))][n * lo - lo * (lo + 1) // 2 + (hi - lo - 1)]
+            else:
+                mixed_sl = outs[METHODS.index((m, a))][: k * n]
+            diff = (mixed_sl.double() - sl).abs()
+            mixed_err[m] = {"max_abs": float(diff.max()),
+                            "max_scaled": float((diff / torch.clamp(sl.abs(), min=1.0)).max()),
+                            "values": int(diff.numel()), "on": f"stripes [0, {k})"}
         e1.record(stream)
         e1.synchronize()
         t64 = e0.elapsed_time(e1) / 1e3
@@ -631,6 +723,23 @@ def run_ours(args, rank, world, local_rank):
                 "slice": f"stripes [0, {k}) of {S}, all methods of the step (from a slice)",
                 "ms_per_method": {m: r.t_accumulate_ms + r.t_diag_ms + r.t_embed_ms + r.t_finalize_ms
                                   for m, r in f_reps}}
+        fp64.update(fp64_rooflines(f_reps, k * n, sm_max))
+        if full and not args.no_downstream:
+            # the paper's FP32-vs-FP64 check (Sec. 4) on a sample subset: the
+            # mixed full matrix's entries of the first `sub` samples against
+            # the FP64 path on those samples (a pair's distance depends on its
+            # two samples only)
+            sub = min(n, 2000)
+            sub_s = sub_table(table_s, sub)
+            tsub = uf.Table(sub_s.indptr, sub_s.indices, sub_s.data, tree)
+            iu, ju = np.triu_indices(sub, 1)
+            idx = torch.as_tensor(n * iu - iu * (iu + 1) // 2 + (ju - iu - 1), device=dev)
+            mixed_sub = [o[idx].double().cpu().numpy() for o in outs]
+            fp64_sub = [uf.uf_compute(tree, tsub, m, a, "fp64")[0] for m, a in METHODS]
+            fp64["downstream_vs_mixed"] = downstream_agreement(mixed_sub, fp64_sub, sub=sub)
+            fp64["downstream_on"] = (f"the first {sub} samples: entries of the mixed full matrix against "
+                                     f"the FP64 path on those samples")
+            tsub.close()
     elif rank == 0 and not args.no_fp64:
         step("fp64")
         torch.cuda.synchronize()
@@ -648,18 +757,7 @@ def run_ours(args, rank, world, local_rank):
                       for m, r in f_reps}
         fp64 = {"value": updates_step / t64, "unit": "updates/s", "ms_per_step": t64 * 1e3,
                 "ms_per_method": per_method}
-        # FP64 CUDA-core roofline of the weighted accumulate: 2 FP64 ops per
-        # update against GB300's nominal FP64 rate (1.25 TFLOP/s = 0.625 T
-        # instructions/s counting an FMA as two flops)
-        r_wn = dict(f_reps).get("weighted_normalized")
-        if r_wn is not None:
-            # two FP64 instructions per update (DMNMX + DADD) at the nominal
-            # 0.625 T FP64 instructions/s (1.25 TFLOP/s counting an FMA as two)
-            ach64 = npairs * r_wn.dense_rows / (r_wn.t_accumulate_ms / 1e3) / 1e12
-            fp64["roofline_weighted"] = {
-                "kernel": "k_stripe_min<double,8,8>", "bound": "alu", "achieved": ach64,
-                "peak": 0.3125, "unit": "Tupdates/s", "frac": ach64 / 0.3125,
-                "peak_basis": "nominal FP64 1.25 TFLOP/s = 0.625 T instructions/s, 2 per update"}
+        fp64.update(fp64_rooflines(f_reps, npairs, sm_max))
         if keep_host and not args.no_err:
             mixed_err = max_err_vs_fp64(mixed_outs, fp64_outs)
         if keep_host and not args.no_downstream:
@@ -709,23 +807,28 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="yule50k_n2048")
+    ap.add_argument("--workload", default="yule500k_n113000",
+                    help="yule500k_n113000 (default; 113k-shaped), yule300k_n25000 (EMP-shaped), "
+                         "yule50k_n2048, yule1k_n64, batched64")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
-    ap.add_argument("--fp64-stripes", type=int, default=0,
-                    help="run the FP64 comparison on stripes [0, K) only (large workloads)")
+    ap.add_argument("--fp64-stripes", type=int, default=-1,
+                    help="run the FP64 comparison on stripes [0, K) only (0: the whole matrix; "
+                         "default: per workload)")
     ap.add_argument("--no-err", action="store_true", help="skip the comparison of the mixed and FP64 results")
-    ap.add_argument("--methods", default="all",
-                    help="comma list of methods per step (default: all four)")
+    ap.add_argument("--methods", default="default",
+                    help="comma list of methods per step, or all (default: the workload's methods)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-downstream", action="store_true",
                     help="skip the Mantel / principal-coordinate agreement of the mixed and FP64 matrices")
-    ap.add_argument("--out-fp32", action="store_true",
-                    help="FP32 distance outputs (halves the output memory of very large runs)")
-    ap.add_argument("--stripe-stop", type=int, default=0,
-                    help="time the stripe range [0, K) of every method instead of all stripes (0: all)")
+    ap.add_argument("--out-fp32", type=int, choices=[0, 1], default=-1,
+                    help="FP32 distance outputs, halving the output memory of very large runs "
+                         "(default: per workload)")
+    ap.add_argument("--stripe-stop", type=int, default=-1,
+                    help="time the stripe range [0, K) of every method instead of all stripes "
+                         "(0: all; default: per workload)")
     ap.add_argument("--region-bytes", type=int, default=0,
                     help="option sparse_region_bytes (0: the library default)")
     ap.add_argument("--overlap", type=int, choices=[0, 1], default=1,
@@ -733,11 +836,17 @@ def main():
     ap.add_argument("--sparse", type=int, choices=[0, 1, 2], default=1,
                     help="sparse-row path: 0 every branch dense, 1 cost model (default), 2 every branch that fits")
     args = ap.parse_args()
-    if args.methods != "all":
-        want = args.methods.split(",")
-        METHODS[:] = [ma for ma in ALL_METHODS if ma[0] in want]
-        if not METHODS:
-            ap.error(f"no known method in {args.methods!r}")
+    dflt = WORKLOAD_DEFAULTS.get(args.workload, WORKLOAD_DEFAULTS["yule50k_n2048"])
+    if args.stripe_stop < 0:
+        args.stripe_stop = dflt["stripe_stop"]
+    if args.fp64_stripes < 0:
+        args.fp64_stripes = dflt["fp64_stripes"]
+    args.out_fp32 = dflt["out_fp32"] if args.out_fp32 < 0 else bool(args.out_fp32)
+    want = (dflt["methods"] if args.methods == "default" else
+            [m for m, _ in ALL_METHODS] if args.methods == "all" else args.methods.split(","))
+    METHODS[:] = [ma for ma in ALL_METHODS if ma[0] in want]
+    if not METHODS:
+        ap.error(f"no known method in {args.methods!r}")
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)
     local_rank = env_int("LOCAL_RANK", 0)

@@ -5,7 +5,8 @@ leg may import this package.  The product path (the CUDA library and its
 Python binding) never calls it and shares no code with it.
 
 ``uf_oracle.c`` holds the arithmetic: a per-pair tree walk straight from the
-UniFrac definitions (refs [1] and [3] of the paper, Sec. 1) and the plain
+UniFrac definitions (refs [1] and [3] of the paper, Sec. 1; the
+variance-adjusted weighted form of Chang, Luan & Sun 2011) and the plain
 striped loop of the paper's Sec. 2-3.  This wrapper only builds that file
 with gcc and marshals numpy arrays into it.
 """
@@ -22,7 +23,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "uf_oracle.c")
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
-METHODS = {"unweighted": 0, "weighted_unnormalized": 1, "weighted_normalized": 2, "generalized": 3}
+METHODS = {"unweighted": 0, "weighted_unnormalized": 1, "weighted_normalized": 2, "generalized": 3,
+           "unweighted_unnormalized": 4, "vaw_weighted_unnormalized": 5, "vaw_weighted_normalized": 6}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ETREE", 3: "ETABLE", 4: "ERANGE", 5: "ENOMEM"}
 
 _lock = threading.Lock()

@@ -21,6 +21,24 @@
  *                          den = sum l_v s^alpha
  *   d = num / den, and d = 0 when den == 0.
  *
+ * Further members of the Striped UniFrac family (the paper names the family,
+ * Sec. 1, without formulas; the definitions are the published ones):
+ *   unweighted unnormalized  d = sum l_v (a_A xor a_B): the unweighted
+ *                          numerator without the division, as weighted
+ *                          unnormalized is the weighted numerator alone.
+ *   variance-adjusted weighted (Chang, Luan & Sun, BMC Bioinformatics 12:118,
+ *   2011): every branch term is divided by sqrt(m_v (m - m_v)), with
+ *     m_v = C_A(v) + C_B(v)  the two samples' counts below v,
+ *     m   = T_A + T_B        their totals,
+ *   over the branches with m_v > 0 and m - m_v > 0 (readings: a branch with
+ *   m_v = 0 holds neither sample and adds 0; one with m_v = m holds all of
+ *   both samples' counts, p_A = p_B = 1, and carries no information: it
+ *   adds 0 to num and den):
+ *     vaw unnormalized     d = sum l_v |p_A - p_B| / sqrt(m_v (m - m_v))
+ *     vaw normalized       num = the same sum,
+ *                          den = sum l_v (p_A + p_B) / sqrt(m_v (m - m_v)),
+ *                          d = num / den (0 when den == 0).
+ *
  * Algorithm, per pair (A, B), in the order the definition reads:
  *   1. scatter each sample's counts onto its tips,
  *   2. walk the nodes in postorder (children before parents) adding each
@@ -51,7 +69,22 @@
 #include <unistd.h>
 
 enum { UO_OK = 0, UO_EINVAL = 1, UO_ETREE = 2, UO_ETABLE = 3, UO_ERANGE = 4, UO_ENOMEM = 5 };
-enum { UO_UNWEIGHTED = 0, UO_WEIGHTED_UNNORMALIZED = 1, UO_WEIGHTED_NORMALIZED = 2, UO_GENERALIZED = 3 };
+enum {
+    UO_UNWEIGHTED = 0,
+    UO_WEIGHTED_UNNORMALIZED = 1,
+    UO_WEIGHTED_NORMALIZED = 2,
+    UO_GENERALIZED = 3,
+    UO_UNWEIGHTED_UNNORMALIZED = 4,
+    UO_VAW_UNNORMALIZED = 5,
+    UO_VAW_NORMALIZED = 6
+};
+#define UO_LAST_METHOD UO_VAW_NORMALIZED
+
+/* methods whose distance is the numerator alone */
+static int unnormalized(int method) {
+    return method == UO_WEIGHTED_UNNORMALIZED || method == UO_UNWEIGHTED_UNNORMALIZED ||
+           method == UO_VAW_UNNORMALIZED;
+}
 
 int uo_host_cores(void) {
     cpu_set_t set;
@@ -156,7 +189,8 @@ static void one_pair(const pair_job *J, int64_t a, int64_t b, double *CA, double
         const double l = J->length[v];
         const double pA = CA[v] / TA, pB = CB[v] / TB; /* step 3 */
         switch (J->method) {
-        case UO_UNWEIGHTED: {
+        case UO_UNWEIGHTED:
+        case UO_UNWEIGHTED_UNNORMALIZED: {
             const int xa = pA > 0.0, xb = pB > 0.0;
             num += l * (double)(xa ^ xb);
             den += l * (double)(xa | xb);
@@ -164,6 +198,15 @@ static void one_pair(const pair_job *J, int64_t a, int64_t b, double *CA, double
         case UO_WEIGHTED_UNNORMALIZED:
             num += l * fabs(pA - pB);
             break;
+        case UO_VAW_UNNORMALIZED:
+        case UO_VAW_NORMALIZED: {
+            const double mv = CA[v] + CB[v], rest = (TA + TB) - mv;
+            if (mv > 0.0 && rest > 0.0) {
+                const double w = 1.0 / sqrt(mv * rest);
+                num += l * w * fabs(pA - pB);
+                den += l * w * (pA + pB);
+            }
+        } break;
         case UO_WEIGHTED_NORMALIZED:
             num += l * fabs(pA - pB);
             den += l * (pA + pB);
@@ -179,7 +222,7 @@ static void one_pair(const pair_job *J, int64_t a, int64_t b, double *CA, double
         }
     }
     double d;
-    if (J->method == UO_WEIGHTED_UNNORMALIZED) d = num;
+    if (unnormalized(J->method)) d = num;
     else d = (den == 0.0) ? 0.0 : num / den;
     *d_out = d;
     if (num_out) *num_out = num;
@@ -226,7 +269,7 @@ int uo_pairs(int64_t n_nodes, const int64_t *parent, const double *length,
              double *out_num, double *out_den, int n_threads, int *threads_used) {
     int st = uo_check_tree(n_nodes, parent, length);
     if (st) return st;
-    if (method < UO_UNWEIGHTED || method > UO_GENERALIZED) return UO_EINVAL;
+    if (method < UO_UNWEIGHTED || method > UO_LAST_METHOD) return UO_EINVAL;
     if (method == UO_GENERALIZED && !(alpha >= 0.0 && alpha <= 1.0)) return UO_EINVAL;
     int64_t *tip_node = malloc(sizeof(int64_t) * (size_t)n_nodes);
     if (!tip_node) return UO_ENOMEM;
@@ -303,10 +346,12 @@ static void *stripe_worker(void *arg) {
             double *num = J->num + (s - J->start) * n;
             double *den = J->den + (s - J->start) * n;
             for (int64_t k = 0; k < n; k++) {
+                const int64_t j = (k + s + 1) % n;
                 const double u = emb[k];
-                const double w = emb[(k + s + 1) % n];
+                const double w = emb[j];
                 switch (J->method) {
-                case UO_UNWEIGHTED: {
+                case UO_UNWEIGHTED:
+                case UO_UNWEIGHTED_UNNORMALIZED: {
                     const int xa = u > 0.0, xb = w > 0.0;
                     num[k] += l * (double)(xa ^ xb);
                     den[k] += l * (double)(xa | xb);
@@ -314,6 +359,15 @@ static void *stripe_worker(void *arg) {
                 case UO_WEIGHTED_UNNORMALIZED:
                     num[k] += l * fabs(u - w);
                     break;
+                case UO_VAW_UNNORMALIZED:
+                case UO_VAW_NORMALIZED: {
+                    const double mv = cnt[k] + cnt[j], rest = (J->total[k] + J->total[j]) - mv;
+                    if (mv > 0.0 && rest > 0.0) {
+                        const double wt = 1.0 / sqrt(mv * rest);
+                        num[k] += l * wt * fabs(u - w);
+                        den[k] += l * wt * (u + w);
+                    }
+                } break;
                 case UO_WEIGHTED_NORMALIZED:
                     num[k] += l * fabs(u - w);
                     den[k] += l * (u + w);
@@ -356,7 +410,7 @@ int uo_striped(int64_t n_nodes, const int64_t *parent, const double *length,
                int n_threads, int *threads_used) {
     int st = uo_check_tree(n_nodes, parent, length);
     if (st) return st;
-    if (method < UO_UNWEIGHTED || method > UO_GENERALIZED) return UO_EINVAL;
+    if (method < UO_UNWEIGHTED || method > UO_LAST_METHOD) return UO_EINVAL;
     if (method == UO_GENERALIZED && !(alpha >= 0.0 && alpha <= 1.0)) return UO_EINVAL;
     const int64_t n = n_samples;
     if (start < 0 || stop < start || stop > n / 2) return UO_ERANGE;
@@ -413,7 +467,7 @@ int uo_striped(int64_t n_nodes, const int64_t *parent, const double *length,
     for (int t = 0; t < nt; t++) failed |= jobs[t].failed;
     if (!failed && dist) {
         for (int64_t r = 0; r < rows * n; r++) {
-            if (method == UO_WEIGHTED_UNNORMALIZED) dist[r] = num[r];
+            if (unnormalized(method)) dist[r] = num[r];
             else dist[r] = den[r] == 0.0 ? 0.0 : num[r] / den[r];
         }
     }

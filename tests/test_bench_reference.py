@@ -57,12 +57,23 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
 
 def test_striped_loop_rate_on_a_slice():
     # the plain striped CPU loop of the CPU-baseline leg: one stripe per host
-    # thread on [0, k), all four methods; skipped when a slice is too large
+    # thread on [0, k), the step's methods; on the first samples of the table
+    # when one stripe of the whole table is too much work
     import bench
     import oracle
     from synth import workload
     tree_s, table_s = workload("yule1k_n64")
-    rate, used, k, dt = bench.oracle_striped_rate(tree_s, table_s)
-    assert rate > 0 and dt > 0
+    rate, used, k, dt, n_used = bench.oracle_striped_rate(tree_s, table_s)
+    assert rate > 0 and dt > 0 and n_used == table_s.n_samples
     assert k == min(table_s.n_samples // 2, oracle.host_cores()) and used == k
-    assert bench.oracle_striped_rate(tree_s, table_s, max_updates_per_thread=1.0) is None
+    rate, used, k, dt, n_used = bench.oracle_striped_rate(tree_s, table_s, max_updates_per_thread=1.0)
+    assert n_used == min(256, table_s.n_samples) and rate > 0
+
+
+def test_sub_table_keeps_the_first_samples():
+    import bench
+    from synth import workload
+    _, t = workload("yule1k_n64")
+    s = bench.sub_table(t, 10)
+    assert s.n_samples == 10 and s.n_features == t.n_features
+    assert (s.dense() == t.dense()[:10]).all()

@@ -79,8 +79,10 @@ def test_113k_shaped_stripe_range_sample():
         cells_d = torch.as_tensor(cells, device="cuda")
         out = torch.empty((stop - start) * n, dtype=torch.float64, device="cuda")
         for method in ("weighted_normalized", "unweighted"):
-            uf.uf_compute(tree, table, method, 1.0, precision, start, stop, out=out)
+            _, rep = uf.uf_compute(tree, table, method, 1.0, precision, start, stop, out=out)
             torch.cuda.synchronize()
+            if method == "unweighted" and precision == "mixed":
+                assert rep.path == 1  # the tensor-core gram, on the tiles of the range
             got = out[cells_d].cpu().numpy()
             exp = oracle.pairs(tree_s, table_s, method, 1.0, a, b)[0]
             assert_close(got, exp, method, precision, f"113k-shaped, stripes [{start}, {stop})")

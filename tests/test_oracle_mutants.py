@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_variants as variants
 
 MUTANTS = {
     "xor_as_or": ("num += l * (double)(xa ^ xb);", "num += l * (double)(xa | xb);"),
@@ -32,11 +33,23 @@ MUTANTS = {
     "counts_not_proportions": ("num += l * fabs(pA - pB);\n            den", "num += l * fabs(CA[v] - CB[v]);\n            den"),
     "tips_numbered_from_one": ("for (int64_t i = 0; i < n_nodes; i++)\n        if (!has_child[i])",
                                "for (int64_t i = 1; i < n_nodes; i++)\n        if (!has_child[i])"),
+    # further family members
+    "unweighted_unnormalized_divides": ("return method == UO_WEIGHTED_UNNORMALIZED || method == UO_UNWEIGHTED_UNNORMALIZED ||",
+                                        "return method == UO_WEIGHTED_UNNORMALIZED ||"),
+    "vaw_drops_sqrt": ("const double w = 1.0 / sqrt(mv * rest);", "const double w = 1.0 / (mv * rest);"),
+    "vaw_rest_is_total": ("rest = (TA + TB) - mv;\n            if", "rest = (TA + TB);\n            if"),
+    "vaw_weight_from_proportions": ("const double mv = CA[v] + CB[v], rest",
+                                    "const double mv = pA + pB, rest"),
+    "vaw_full_branch_kept": ("if (mv > 0.0 && rest > 0.0) {\n                const double w",
+                             "if (mv > 0.0 && rest >= 0.0 && rest + mv > 0.0) {\n                const double w"),
+    "vaw_den_drops_weight": ("den += l * w * (pA + pB);", "den += l * (pA + pB);"),
 }
 
 CHECKS = [pins.check_two_tip, pins.check_three_tip, pins.check_star_textbook,
           pins.check_path_enumeration, pins.check_hand_small, pins.check_invariants,
-          pins.check_structural, pins.check_zero_lengths, pins.check_earth_movers]
+          pins.check_structural, pins.check_zero_lengths, pins.check_earth_movers,
+          variants.check_variant_two_tip, variants.check_variant_three_tip, variants.check_variant_star,
+          variants.check_hand_variants, variants.check_variant_paths, variants.check_variant_invariants]
 
 
 def _run_checks(lib):

@@ -21,6 +21,17 @@
  *   UF_GENERALIZED (alpha)    sum l_v s^(alpha-1) |p_A - p_B| / sum l_v s^alpha,
  *                             s = p_A + p_B, terms with s == 0 contribute 0
  *
+ * Further members of the Striped UniFrac family (Sec. 1 names the family),
+ * with C_A(v) the count of sample A below v, T_A its total,
+ * m_v = C_A(v) + C_B(v), m = T_A + T_B:
+ *   UF_UNWEIGHTED_UNNORMALIZED    sum l_v [p_A>0 xor p_B>0]
+ *   UF_VAW_WEIGHTED_UNNORMALIZED  sum l_v |p_A - p_B| / sqrt(m_v (m - m_v))
+ *   UF_VAW_WEIGHTED_NORMALIZED    that sum / sum l_v (p_A + p_B) / sqrt(m_v (m - m_v))
+ *   (variance-adjusted weighted UniFrac, Chang, Luan & Sun, BMC
+ *   Bioinformatics 12:118, 2011; branches with m_v = 0 or m_v = m add 0;
+ *   these run every branch through the dense stripe kernel: option
+ *   "sparse" does not apply to them)
+ *
  * A ratio whose denominator is 0 is reported as 0.  The root's branch does
  * not exist: length[root] is ignored.
  *
@@ -59,7 +70,10 @@ typedef enum {
     UF_UNWEIGHTED = 0,
     UF_WEIGHTED_UNNORMALIZED = 1,
     UF_WEIGHTED_NORMALIZED = 2,
-    UF_GENERALIZED = 3
+    UF_GENERALIZED = 3,
+    UF_UNWEIGHTED_UNNORMALIZED = 4,
+    UF_VAW_WEIGHTED_UNNORMALIZED = 5,
+    UF_VAW_WEIGHTED_NORMALIZED = 6
 } uf_method;
 
 /*
@@ -286,6 +300,7 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
  *   device (memory of another device, or host memory, is UF_EINVAL), layout
  *   as in uf_compute.  cuda_stream: cudaStream_t or NULL.  The call returns
  *   after the results are in out_device.
+ * Methods UF_UNWEIGHTED .. UF_GENERALIZED (others are UF_EINVAL).
  * The first call on a device, with that device current, sets up the area's
  * device address (cudaGetSymbolAddress); make that first call before any
  * stream capture begins on the device.  All calls on a device share the area

@@ -27,7 +27,8 @@ __all__ = ["UFError", "Tree", "Table", "Report", "METHODS", "PRECISIONS", "libra
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libunifrac_gb300.so")
 
-METHODS = {"unweighted": 0, "weighted_unnormalized": 1, "weighted_normalized": 2, "generalized": 3}
+METHODS = {"unweighted": 0, "weighted_unnormalized": 1, "weighted_normalized": 2, "generalized": 3,
+           "unweighted_unnormalized": 4, "vaw_weighted_unnormalized": 5, "vaw_weighted_normalized": 6}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 STATUS = {0: "UF_OK", 1: "UF_EINVAL", 2: "UF_ETREE", 3: "UF_ETABLE", 4: "UF_ERANGE",
           5: "UF_ENOMEM", 6: "UF_ECUDA", 7: "UF_ETIMEOUT", 8: "UF_ECANCELLED"}

@@ -179,6 +179,30 @@ __global__ void k_emb_rows(int64_t b0, const int32_t *__restrict__ nodes,
   }
 }
 
+// Variance-adjusted rows: three planes per row r, each `pitch` elements:
+// p = c / T, the count c below the branch and T - c, with the same
+// wrap-padded columns as k_emb_rows.
+template <typename T>
+__global__ void k_emb_rows_vaw(const int32_t *__restrict__ nodes, const int32_t *__restrict__ slot_of_node,
+                               const double *__restrict__ counts, int64_t ld, const double *__restrict__ total,
+                               const float *__restrict__ inv_total_f, T *__restrict__ X, int64_t pitch,
+                               const TabDesc *__restrict__ tabs, int n_tabs) {
+  const int64_t v = nodes[blockIdx.x];
+  const double *c = counts + (int64_t)slot_of_node[v] * ld;
+  T *x = X + (int64_t)blockIdx.x * 3 * pitch;
+  for (int64_t j = threadIdx.x; j < pitch; j += blockDim.x) {
+    const TabDesc &tb = tabs[n_tabs == 1 ? 0 : segment_of(tabs, n_tabs, j)];
+    int64_t k = j - tb.x_col;
+    while (k >= tb.n) k -= tb.n;
+    k += tb.off;
+    const double ck = c[k], tk = total[k];
+    if constexpr (sizeof(T) == 4) x[j] = (float)ck * inv_total_f[k];
+    else x[j] = ck / tk;
+    x[pitch + j] = (T)ck;
+    x[2 * pitch + j] = (T)(tk - ck);
+  }
+}
+
 cudaError_t launch_tip_counts(const int32_t *tip_nodes, int n_list, const int32_t *slot_of_node,
                               const int32_t *tip_of_node, const int64_t *col_ptr,
                               const int32_t *col_row, const double *col_val, double *counts,
@@ -225,6 +249,14 @@ cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
                             void *X, int64_t pitch, const TabDesc *tabs, int n_tabs, cudaStream_t st,
                             const int32_t *nodes) {
   if (rows <= 0) return cudaSuccess;
+  if (kind == EMB_VAW) {
+    if (!nodes) return cudaErrorInvalidValue;
+    if (fp32)
+      return launch_k(k_emb_rows_vaw<float>, dim3(rows), dim3(256), 0, st, nodes, slot_of_node, counts, ld, total,
+                      inv_total_f, (float *)X, pitch, tabs, n_tabs);
+    return launch_k(k_emb_rows_vaw<double>, dim3(rows), dim3(256), 0, st, nodes, slot_of_node, counts, ld, total,
+                    inv_total_f, (double *)X, pitch, tabs, n_tabs);
+  }
 #define UF_EMB(T, K)                                                                                 \
   return launch_k(k_emb_rows<T, K>, dim3(rows), dim3(256), 0, st, b0, nodes, slot_of_node, counts, ld, length, \
                   total, inv_total_f, (T *)X, pitch, tabs, n_tabs)

@@ -10,6 +10,8 @@
 //   unweighted:  num = A  or  W_k + W_j - 2G,      den = (W_k + W_j + A) / 2  or  W_k + W_j - G
 //                (W = D, G = M on presence embeddings)
 //   generalized: num = N (FP64)  or  den - 2Q (FP32)
+//   variance-adjusted weighted: num = N, den as generalized (both precisions)
+// The unnormalized methods return num * 2^-F.
 // num and den are formed exactly in integers before the one FP64 division
 // (the common 2^F cancels); weighted_unnormalized returns num * 2^-F.  FP64
 // accumulators have two words (uf_device.cuh); they are combined here into
@@ -108,6 +110,7 @@ __global__ void k_finalize(const FinalArgs a) {
       val = den > 0 ? to_double(num) / to_double(den) : 0.0;
     } break;
     }
+    if (a.unnormalized) val = to_double(num) * inv_scale;
     int64_t idx;
     if (a.full) {
       const int64_t i = k < j ? k : j, jj = k < j ? j : k;

@@ -6,7 +6,8 @@ namespace ufg {
 
 // ---- finalize (uf_finalize.cu) ----
 struct FinalArgs {
-  int method;           // uf_method
+  int method;           // 0 unweighted, 1 / 2 weighted (min or abs form), 3 den and Q / N form
+  int unnormalized;     // 1: the distance is the numerator alone, num * 2^-F
   int n;
   int64_t s0, s1;       // stripes [s0, s1)
   int full;             // 1: condensed output, 0: stripe-major

@@ -405,7 +405,9 @@ __global__ void k_finalize_gram(const GramFinalArgs a) {
       num = 0;
     }
     const double val = (aborted || missing) ? __longlong_as_double(0x7ff8000000000000ll)
-                                            : den > 0 ? (double)num / (double)den : 0.0;
+                       : a.unnormalized    ? (double)num * a.inv_scale
+                       : den > 0           ? (double)num / (double)den
+                                           : 0.0;
     const int64_t idx = a.full ? (int64_t)a.n * lo - lo * (lo + 1) / 2 + (hi - lo - 1) : c;
     if (a.out_fp32) ((float *)a.out)[idx] = (float)val;
     else ((double *)a.out)[idx] = val;

@@ -48,6 +48,8 @@ struct GramFinalArgs {
   int out_fp32;
   const int *err;                // the gram kernel's abort flag: when set, every output is NaN
   unsigned long long *clamps;    // or null: counts numerators that rounded below 0
+  int unnormalized;              // 1: the distance is the numerator alone, num * inv_scale
+  double inv_scale;              // 2^-F
 };
 int gram_pad(int n);                      // n rounded up to the tile
 int64_t gram_kpad(int rows);              // branches rounded up to the stage

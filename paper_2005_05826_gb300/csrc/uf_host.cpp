@@ -290,8 +290,12 @@ namespace {
 //   l * p embeddings:         D_k = sum_f p_f dist(f) <= max tip distance
 //   l * presence embeddings:  W_k <= min(total length, sum_{f in k} dist(f))
 //   generalized (den, Q):     den <= sum l s^alpha <= 2 (W_k + W_j)
+//   variance-adjusted (den, N): den <= w_max (D_k + D_j), with the weight
+//                             1 / sqrt(m_v (m - m_v)) <= w_max = max(1, 1 / c_min)
+//                             (both factors are sums of counts >= c_min, or 0)
 double accum_bound(uf_tree *tree, uf_table *table, int kind) {
   if (kind == EMB_SCALED) return tree->max_tip_dist;
+  if (kind == EMB_VAW) return 2.0 * tree->max_tip_dist * std::max(1.0, 1.0 / table->min_count);
   double pres;
   {
     std::lock_guard<std::mutex> g(table->mu);
@@ -338,7 +342,8 @@ constexpr int64_t MAX_CALL_SAMPLES = int64_t(1) << 30;
 uf_status check_args(const uf_tree *tree, const uf_table *table, uf_method method, double alpha,
                      uf_precision precision) {
   if (!tree || !table) return fail(UF_EINVAL, "null tree or table");
-  if (method < UF_UNWEIGHTED || method > UF_GENERALIZED) return fail(UF_EINVAL, "unknown method %d", (int)method);
+  if (method < UF_UNWEIGHTED || method > UF_VAW_WEIGHTED_NORMALIZED)
+    return fail(UF_EINVAL, "unknown method %d", (int)method);
   if (precision != UF_FP64 && precision != UF_MIXED) return fail(UF_EINVAL, "unknown precision %d", (int)precision);
   if (method == UF_GENERALIZED && !(alpha >= 0.0 && alpha <= 1.0))
     return fail(UF_EINVAL, "alpha must be in [0, 1] (got %g)", alpha);
@@ -591,6 +596,7 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
     // and the presence bound for this tree: max over samples of the summed
     // root distances of their tips (accum_bound)
     std::vector<double> pres(T, 0.0);
+    std::vector<double> cmin(T, INFINITY);  // the smallest count (variance-adjusted bound)
     const double *tip_dist = tree->tip_dist.data();
     parallel_for(T, [&](int c) {
       cnt[c].assign(n_features, 0);
@@ -609,6 +615,7 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
             s += data[q];
             w += tip_dist[indices[q]];
             cc[indices[q]]++;
+            cmin[c] = std::min(cmin[c], data[q]);
             continue;
           }
           bad_k[c] = k;
@@ -624,6 +631,7 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
       if (bad_k[c] >= 0) return fail(UF_ETABLE, "%s", bad_msg[c].c_str());
     t->id = next_id++;
     t->presence_bound[tree->id] = *std::max_element(pres.begin(), pres.end());
+    t->min_count = *std::min_element(cmin.begin(), cmin.end());
     // column starts, then each thread's first slot in every column (its
     // samples go behind the earlier threads'), over feature ranges in parallel
     t->col_ptr.assign(n_features + 1, 0);

@@ -31,6 +31,8 @@ enum EmbKind : int {
   EMB_SCALED = 0,    // l_v * p(v): weighted methods
   EMB_PRESENCE = 1,  // l_v * [count > 0]: unweighted
   EMB_PROP = 2,      // p(v): generalized (the length is applied in the kernel)
+  EMB_VAW = 3,       // variance-adjusted weighted: three planes per row, each `pitch`
+                     // elements, p(v), the count c(v) below v and T - c(v)
 };
 
 // which quantity the accumulator holds
@@ -38,6 +40,8 @@ enum AccKind : int {
   ACC_MIN = 0,   // sum_e min(x_e[k], x_e[k + d])  (+ diagonal row d = 0)
   ACC_GEN = 1,   // generalized: den = sum l s^a and, FP32, Q = sum l min(u, v) s^(a-1)
                  // (num = den - 2Q) or, FP64, N = sum l |u - v| s^(a-1) (num = N)
+  ACC_VAW = 3,   // variance-adjusted weighted: den = sum l w (u + v), N = sum l w |u - v|,
+                 // w = 1 / sqrt((c_k + c_j)(r_k + r_j)) where both factors are > 0
 };
 
 // ---- batches ----

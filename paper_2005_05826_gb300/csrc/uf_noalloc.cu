@@ -95,7 +95,9 @@ uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method 
   TableView xv;
   if (!tree_host_view(tree, &tv) || !table_host_view(table, &xv))
     return noalloc_fail(UF_EINVAL, "null tree or table");
-  if (method < UF_UNWEIGHTED || method > UF_GENERALIZED) return noalloc_fail(UF_EINVAL, "unknown method");
+  if (method < UF_UNWEIGHTED || method > UF_GENERALIZED)
+    return noalloc_fail(UF_EINVAL, "the allocation-free entry point computes the methods UF_UNWEIGHTED .. "
+                                   "UF_GENERALIZED");
   if (precision != UF_FP64 && precision != UF_MIXED) return noalloc_fail(UF_EINVAL, "unknown precision");
   if (method == UF_GENERALIZED && !(alpha >= 0.0 && alpha <= 1.0))
     return noalloc_fail(UF_EINVAL, "alpha must be in [0, 1]");

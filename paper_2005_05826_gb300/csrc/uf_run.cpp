@@ -810,6 +810,8 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
     fa.out_fp32 = J.out_fp32;
     fa.err = err.as<int>();
     fa.clamps = clamps.as<unsigned long long>();
+    fa.unnormalized = unnormalized(J.method);
+    fa.inv_scale = 1.0 / scale;
     ck(launch_finalize_gram(fa, ls), "finalize");
     kernels++;
   }
@@ -862,10 +864,10 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
 uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method method, double scale) {
   const auto t_start = std::chrono::steady_clock::now();
   const size_t nt = J.tabs.size();
-  const int acc = method == UF_GENERALIZED ? ACC_GEN : ACC_MIN;
-  const int kind = method == UF_GENERALIZED ? EMB_PROP : method == UF_UNWEIGHTED ? EMB_PRESENCE : EMB_SCALED;
+  const int acc = acc_of(method), kind = kind_of(method);
   const bool fp32 = J.fp32;
   const size_t es = fp32 ? 4 : 8;
+  const int planes = kind == EMB_VAW ? 3 : 1;  // embedding planes per branch row
   int tile_s = 0, tile_k = 0;
   stripe_tile_shape(acc, fp32, &tile_s, &tile_k);
   std::vector<TabDesc> tabs(nt);
@@ -895,8 +897,9 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   // FP64: every fixed-point accumulator has a second word (uf_device.cuh),
   // stored after the first: M and M2 at + cells, Dg and the sparse R at + n_cols
   const int words = fp32 ? 1 : 2;
-  const double acc_bytes = ((double)cells * 8.0 * (acc == ACC_GEN ? 2 : 1) + n_cols * 8.0) * words;
-  const int64_t rows = block_rows(nb, (double)n_cols * 8.0 + (double)pitch * es + 8.0 + n_cols * es / 64.0, acc_bytes);
+  const double acc_bytes = ((double)cells * 8.0 * (acc == ACC_MIN ? 1 : 2) + n_cols * 8.0) * words;
+  const int64_t rows =
+      block_rows(nb, (double)n_cols * 8.0 + (double)pitch * es * planes + 8.0 + n_cols * es / 64.0, acc_bytes);
   Inputs in = [&] {
     NvtxRange r("uf: bind inputs");
     return bind_inputs(tree, J, device, rows);
@@ -914,7 +917,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const int64_t ld = round_up(n_cols, 16);
   const size_t m_bytes = (size_t)cells * 8 * words, d_bytes = (size_t)n_cols * 8 * words;
   DevBuf counts((size_t)in.P->n_slots * ld * 8, st, "alloc counts");
-  DevBuf X((size_t)xrows * pitch * es, st, "alloc embeddings");
+  DevBuf X((size_t)xrows * pitch * es * planes, st, "alloc embeddings");
   DevBuf M(m_bytes, st, "alloc stripes");
   DevBuf M2, Dg, diag_tmp, counter(sizeof(int), st, "alloc counter");
   DevBuf clamps(sizeof(unsigned long long), st, "alloc clamp counter");
@@ -942,7 +945,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
                        st),
        "gather totals");
   }
-  if (acc == ACC_GEN) {
+  if (acc != ACC_MIN) {
     M2 = DevBuf(m_bytes, st, "alloc stripes");
     ck(cudaMemsetAsync(M2.p, 0, m_bytes, st), "memset");
   } else {
@@ -1053,13 +1056,14 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   timer.begin(3);
   for (size_t t = 0; t < nt; t++) {
     FinalArgs fa{};
-    fa.method = method;
+    fa.method = acc == ACC_MIN ? (kind == EMB_PRESENCE ? 0 : 2) : 3;
+    fa.unnormalized = unnormalized(method);
     fa.n = tabs[t].n;
     fa.s0 = J.tabs[t].start;
     fa.s1 = J.tabs[t].stop;
     fa.full = J.tabs[t].start == 0 && J.tabs[t].stop == tabs[t].n / 2;
     fa.abs_mask = acc == ACC_MIN ? abs_row_mask(fp32) : 0u;
-    fa.gen_abs = acc == ACC_GEN && !fp32;
+    fa.gen_abs = acc == ACC_VAW || (acc == ACC_GEN && !fp32);
     fa.clamps = clamps.as<unsigned long long>();
     fa.M = M.as<unsigned long long>() + tabs[t].m_off;
     fa.M2 = M2.p ? M2.as<unsigned long long>() + tabs[t].m_off : nullptr;
@@ -1119,25 +1123,27 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
 
 // One compute call on the current device; throws CudaFail on CUDA errors.
 uf_status run_batch(uf_tree *tree, const BatchJob &J) {
-  static const char *const names[2][4] = {
+  static const char *const names[2][7] = {
       {"uf_compute unweighted fp64", "uf_compute weighted_unnormalized fp64", "uf_compute weighted_normalized fp64",
-       "uf_compute generalized fp64"},
+       "uf_compute generalized fp64", "uf_compute unweighted_unnormalized fp64",
+       "uf_compute vaw_weighted_unnormalized fp64", "uf_compute vaw_weighted_normalized fp64"},
       {"uf_compute unweighted mixed", "uf_compute weighted_unnormalized mixed",
-       "uf_compute weighted_normalized mixed", "uf_compute generalized mixed"}};
-  NvtxRange call_range(names[J.fp32 ? 1 : 0][(int)J.method & 3]);
+       "uf_compute weighted_normalized mixed", "uf_compute generalized mixed", "uf_compute unweighted_unnormalized mixed",
+       "uf_compute vaw_weighted_unnormalized mixed", "uf_compute vaw_weighted_normalized mixed"}};
+  NvtxRange call_range(names[J.fp32 ? 1 : 0][(int)J.method % 7]);
   g_h2d = 0.0;
   int device = 0;
   ck(cudaGetDevice(&device), "cudaGetDevice");
   keep_pool_memory(device);
   uf_method method = J.method;
   if (method == UF_GENERALIZED && J.alpha == 1.0) method = UF_WEIGHTED_NORMALIZED;  // s^0 == 1
-  const int kind = method == UF_GENERALIZED ? EMB_PROP : method == UF_UNWEIGHTED ? EMB_PRESENCE : EMB_SCALED;
+  const int kind = kind_of(method);
   double scale = 0.0;  // one fixed-point scale valid for every table of the call
   for (const TableJob &t : J.tabs) {
     const double s = accum_scale(tree, t.table, kind);
     scale = scale == 0.0 ? s : std::min(scale, s);
   }
-  if (method == UF_UNWEIGHTED && J.fp32 && g_tensor_path.load()) {
+  if (kind == EMB_PRESENCE && J.fp32 && g_tensor_path.load()) {
     // the tensor path stores the gram tiles the stripes need (and the
     // diagonal) plus the sparse rows' stripe cells; when those do not fit in
     // half the free memory the CUDA-core stripe kernels take the call

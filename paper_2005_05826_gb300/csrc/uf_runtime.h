@@ -204,6 +204,7 @@ struct uf_table {
   std::vector<double, ufg::rt::NoInit<double>> col_val;
   std::mutex mu;
   std::map<uint64_t, double> presence_bound;  // by tree id: max_k sum_{f in k} dist(tip f)
+  double min_count = 1.0;                     // the smallest count of the table
   struct Dev {
     char *base = nullptr;  // one allocation holding the arrays below
     double *total = nullptr, *col_val = nullptr;
@@ -231,6 +232,28 @@ uf_tree::Dev &tree_dev(uf_tree *t, int device);
 uf_table::Dev &table_dev(uf_table *t, int device);
 Plan *get_plan(uf_tree *t, int64_t rows);
 Plan::Dev &plan_dev(Plan *P, int device);
+
+// ---- methods ----
+// The accumulator and embedding a method runs on, and whether its distance
+// is the numerator alone.
+inline int acc_of(uf_method m) {
+  return m == UF_GENERALIZED ? ACC_GEN
+         : (m == UF_VAW_WEIGHTED_UNNORMALIZED || m == UF_VAW_WEIGHTED_NORMALIZED) ? ACC_VAW
+                                                                                 : ACC_MIN;
+}
+inline int kind_of(uf_method m) {
+  switch (m) {
+  case UF_GENERALIZED: return EMB_PROP;
+  case UF_UNWEIGHTED:
+  case UF_UNWEIGHTED_UNNORMALIZED: return EMB_PRESENCE;
+  case UF_VAW_WEIGHTED_UNNORMALIZED:
+  case UF_VAW_WEIGHTED_NORMALIZED: return EMB_VAW;
+  default: return EMB_SCALED;
+  }
+}
+inline bool unnormalized(uf_method m) {
+  return m == UF_WEIGHTED_UNNORMALIZED || m == UF_UNWEIGHTED_UNNORMALIZED || m == UF_VAW_WEIGHTED_UNNORMALIZED;
+}
 
 // ---- one compute call ----
 // One table of a compute call: its stripe range and output.

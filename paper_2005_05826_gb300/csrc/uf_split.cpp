@@ -26,7 +26,8 @@ namespace {
 // gives bitwise the stripes of the full run.
 RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int acc, bool fp32) {
   RowSplit R;
-  const int mode = (int)g_sparse.load();
+  // the variance-adjusted method has no pair-scatter form: every branch dense
+  const int mode = acc == ACC_VAW ? 0 : (int)g_sparse.load();
   const int64_t nb = tree->n_nodes - 1;
   const size_t nt = J.tabs.size();
   const int classes[5] = {128, 512, 2048, SPARSE_MAX_ENTRIES, SPARSE_LIST_MAX_ENTRIES};

@@ -433,6 +433,154 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
   }
 }
 
+// ---- variance-adjusted weighted (Chang, Luan & Sun 2011):
+//      den += l w (u + v), N += l w |u - v|, w = 1 / sqrt((c_k + c_j)(r_k + r_j))
+//      with c the counts below the branch and r = T - c, and w = 0 where either
+//      factor is 0 ----
+// Rows hold three planes (u, c, r) of `pitch` elements each.  A stage carries
+// RB rows of all three planes; the micro-tile is RD x RK with two
+// accumulators per cell.
+template <typename T, int RD, int RK>
+struct GeoV {
+  static constexpr int RB = sizeof(T) == 4 ? 8 : 4;  // rows per stage
+  static constexpr int NSTAGE = 2;
+  static constexpr int NPL = 3;                       // planes: u, c, r
+  static constexpr int TS = 16 * RD, TK = 16 * RK;
+  static constexpr int VEC = 16 / sizeof(T);
+  static constexpr int UW = TK, VW = TK + TS, ROW = UW + VW;
+  static constexpr int STAGE = RB * NPL * ROW + RB;
+  static constexpr int UCH = UW / VEC, VCH = VW / VEC, CH = UCH + VCH;
+  static constexpr int NV = (RD + RK + VEC - 1) / VEC;
+  static constexpr size_t SMEM = (size_t)NSTAGE * STAGE * sizeof(T) + (size_t)2 * RD * RK * NT * sizeof(T);
+};
+
+template <typename T, int RD, int RK>
+__device__ __forceinline__ void load_stage_vaw(T *stage, const StripeArgs &a, int e0, int e_end, int64_t ucol,
+                                               int64_t vcol) {
+  using G = GeoV<T, RD, RK>;
+  const T *X = (const T *)a.X;
+  for (int c = threadIdx.x; c < G::RB * G::NPL * G::CH; c += NT) {
+    const int rp = c / G::CH, q = c - rp * G::CH;  // rp = row * NPL + plane
+    const int r = rp / G::NPL, pl = rp - r * G::NPL;
+    T *row = stage + rp * G::ROW;
+    const int e = e0 + r;
+    T *dst;
+    int64_t src;
+    if (q < G::UCH) {
+      dst = row + swz<T>(q * G::VEC);
+      src = ucol + q * G::VEC;
+    } else {
+      const int qv = q - G::UCH;
+      dst = row + G::UW + swz<T>(qv * G::VEC);
+      src = vcol + qv * G::VEC;
+    }
+    if (e < e_end) {
+      cp_async16(dst, X + ((int64_t)e * G::NPL + pl) * a.pitch + src);
+    } else {
+#pragma unroll
+      for (int i = 0; i < G::VEC; i++) dst[i] = T(0);
+    }
+  }
+  if (threadIdx.x < G::RB) {
+    const int e = e0 + threadIdx.x;
+    stage[G::RB * G::NPL * G::ROW + threadIdx.x] = e < e_end ? (T)a.len[e] : T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T vaw_weight(T prod);
+template <>
+__device__ __forceinline__ float vaw_weight<float>(float prod) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(prod));
+  return prod > 0.f ? r : 0.f;
+}
+template <>
+__device__ __forceinline__ double vaw_weight<double>(double prod) {
+  return prod > 0.0 ? rsqrt(prod) : 0.0;
+}
+
+template <typename T, int RD, int RK, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_stripe_vaw(const StripeArgs a) {
+  using G = GeoV<T, RD, RK>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *stg = reinterpret_cast<T *>(smem_raw);
+  T *midd = reinterpret_cast<T *>(smem_raw + (size_t)G::NSTAGE * G::STAGE * sizeof(T));
+  T *midn = midd + RD * RK * NT;
+  __shared__ int s_unit;
+  const int tk = threadIdx.x & 15, ts = threadIdx.x >> 4;
+  const int w0 = RK * tk + RD * ts;
+  Unit U;
+  while (next_unit(a, G::TS, G::TK, &s_unit, &U)) {
+#pragma unroll
+    for (int c = 0; c < RD * RK; c++) midd[c * NT + threadIdx.x] = midn[c * NT + threadIdx.x] = T(0);
+    const int nst = (U.r1 - U.r0 + G::RB - 1) / G::RB;
+    if (nst > 0)
+      load_stage_vaw<T, RD, RK>(stg, a, U.r0, U.r1, U.x_col + U.k0, U.x_col + U.k0 + U.s0);
+    cp_async_commit();
+    T accd[RD][RK], accn[RD][RK];
+#pragma unroll
+    for (int i = 0; i < RD; i++)
+#pragma unroll
+      for (int j = 0; j < RK; j++) accd[i][j] = accn[i][j] = T(0);
+    int in_sub = 0;
+    for (int it = 0; it < nst; it++) {
+      cp_async_wait<0>();
+      __syncthreads();
+      if (it + 1 < nst)
+        load_stage_vaw<T, RD, RK>(stg + ((it + 1) % G::NSTAGE) * G::STAGE, a, U.r0 + (it + 1) * G::RB, U.r1,
+                                  U.x_col + U.k0, U.x_col + U.k0 + U.s0);
+      cp_async_commit();
+      const T *stage = stg + (it % G::NSTAGE) * G::STAGE;
+#pragma unroll 1
+      for (int r = 0; r < G::RB; r++) {
+        const T l = stage[G::RB * G::NPL * G::ROW + r];
+        T u[3][RK], v[3][G::NV * G::VEC];
+#pragma unroll
+        for (int pl = 0; pl < 3; pl++) {
+          const T *urow = stage + (r * G::NPL + pl) * G::ROW;
+          const T *vrow = urow + G::UW;
+#pragma unroll
+          for (int q = 0; q < RK / G::VEC; q++)
+            *reinterpret_cast<uint4 *>(&u[pl][q * G::VEC]) =
+                *reinterpret_cast<const uint4 *>(urow + swz<T>(RK * tk + q * G::VEC));
+#pragma unroll
+          for (int q = 0; q < G::NV; q++)
+            *reinterpret_cast<uint4 *>(&v[pl][q * G::VEC]) =
+                *reinterpret_cast<const uint4 *>(vrow + swz<T>(w0 + q * G::VEC));
+        }
+#pragma unroll
+        for (int i = 0; i < RD; i++)
+#pragma unroll
+          for (int j = 0; j < RK; j++) {
+            const T uu = u[0][j], vv = v[0][i + j + 1];
+            const T mv = u[1][j] + v[1][i + j + 1];  // the two samples' counts below the branch
+            const T rest = u[2][j] + v[2][i + j + 1];  // and the rest of their totals
+            const T w = l * vaw_weight<T>(mv * rest);
+            accd[i][j] = fma(uu + vv, w, accd[i][j]);
+            accn[i][j] = fma(fabs(uu - vv), w, accn[i][j]);
+          }
+      }
+      in_sub += G::RB;
+      if (in_sub >= B1 || it == nst - 1) {
+#pragma unroll
+        for (int i = 0; i < RD; i++)
+#pragma unroll
+          for (int j = 0; j < RK; j++) {
+            const int c = (i * RK + j) * NT + threadIdx.x;
+            midd[c] += accd[i][j];
+            midn[c] += accn[i][j];
+            accd[i][j] = accn[i][j] = T(0);
+          }
+        in_sub = 0;
+      }
+    }
+    cp_async_wait<0>();
+    commit_cells<T, RD, RK>(a.M, midd, a, U, U.s0 + RD * ts, U.k0 + RK * tk);
+    commit_cells<T, RD, RK>(a.M2, midn, a, U, U.s0 + RD * ts, U.k0 + RK * tk);
+  }
+}
+
 // ---- diagonal: D[k] += sum_e x_e[k], with the operation sequence a stripe
 //      cell in min form runs when its two columns are equal ----
 // Phase 1: one partial per (B1-row sub-block, sample), summed in row order;
@@ -520,6 +668,17 @@ cudaError_t run_min(const StripeArgs &a, cudaStream_t st) {
   return launch_k(k_stripe_min<T, RD, RK, ABSM, MINB>, dim3(grid), dim3(NT), G::SMEM, st, a);
 }
 
+template <typename T, int RD, int RK, int MINB>
+cudaError_t run_vaw(const StripeArgs &a, cudaStream_t st) {
+  using G = GeoV<T, RD, RK>;
+  int grid = 0;
+  cudaError_t e = prepare(k_stripe_vaw<T, RD, RK, MINB>, G::SMEM, &grid, units_of(a));
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  return launch_k(k_stripe_vaw<T, RD, RK, MINB>, dim3(grid), dim3(NT), G::SMEM, st, a);
+}
+
 template <typename T, int RD, int RK, int MODE, int MINB>
 cudaError_t run_gen(const StripeArgs &a, cudaStream_t st, int max_per_sm = 0) {
   using G = Geo<T, RD, RK, 2>;
@@ -533,11 +692,12 @@ cudaError_t run_gen(const StripeArgs &a, cudaStream_t st, int max_per_sm = 0) {
 
 }  // namespace
 
-// micro-tiles: min kernels 8 x 8, generalized 4 x 8 (two accumulators)
+// micro-tiles: min kernels 8 x 8, generalized 4 x 8 (two accumulators),
+// variance-adjusted 4 x 4 (two accumulators, three planes)
 void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k) {
-  *tile_s = acc == ACC_GEN ? 16 * 4 : 16 * 8;
+  *tile_s = acc == ACC_MIN ? 16 * 8 : 16 * 4;
   (void)fp32;
-  *tile_k = 16 * 8;
+  *tile_k = acc == ACC_VAW ? 16 * 4 : 16 * 8;
 }
 
 int stripe_chunk_rows() { return 2048; }
@@ -547,6 +707,7 @@ cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStrea
   if (acc == ACC_MIN)
     return fp32 ? run_min<float, 8, 8, FP32_ABS_ROW_MASK, 2>(a, st)
                 : run_min<double, 8, 8, FP64_ABS_ROW_MASK, 1>(a, st);
+  if (acc == ACC_VAW) return fp32 ? run_vaw<float, 4, 4, 2>(a, st) : run_vaw<double, 4, 4, 1>(a, st);
   const bool half = a.alpha == 0.5;
   if (fp32) return half ? run_gen<float, 4, 8, 0, 2>(a, st) : run_gen<float, 4, 8, 1, 2>(a, st);
   return half ? run_gen<double, 4, 8, 0, 1>(a, st) : run_gen<double, 4, 8, 1, 1>(a, st);

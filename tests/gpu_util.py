@@ -4,9 +4,13 @@ import numpy as np
 import oracle
 
 METHODS = ["unweighted", "weighted_unnormalized", "weighted_normalized", "generalized"]
+# further members of the family (unweighted unnormalized, variance-adjusted weighted)
+VARIANTS = ["unweighted_unnormalized", "vaw_weighted_unnormalized", "vaw_weighted_normalized"]
+# methods whose distance is an unbounded numerator: the mixed tolerance scales with max(1, |d|)
+UNBOUNDED = ("weighted_unnormalized", "unweighted_unnormalized", "vaw_weighted_unnormalized")
 
 # FP64 path: 1e-10 relative (exact zeros stay within 1e-15); mixed path: 1e-5
-# absolute, scaled by max(1, |d|) for the unbounded weighted_unnormalized.
+# absolute, scaled by max(1, |d|) for the unbounded (unnormalized) methods.
 FP64_RTOL, FP64_ATOL = 1e-10, 1e-15
 MIXED_ATOL = 1e-5
 
@@ -16,7 +20,7 @@ def tolerance_ok(got, exp, method, precision):
     exp = np.asarray(exp, dtype=np.float64)
     if precision == "fp64":
         return np.abs(got - exp) <= FP64_RTOL * np.abs(exp) + FP64_ATOL
-    scale = np.maximum(1.0, np.abs(exp)) if method == "weighted_unnormalized" else 1.0
+    scale = np.maximum(1.0, np.abs(exp)) if method in UNBOUNDED else 1.0
     return np.abs(got - exp) <= MIXED_ATOL * scale
 
 

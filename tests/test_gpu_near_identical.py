@@ -20,7 +20,7 @@ import pytest
 import oracle
 import paper_2005_05826_gb300 as uf
 from synth import Table as STable, pair_subset, workload
-from tests.gpu_util import METHODS, assert_close, condensed_index
+from tests.gpu_util import METHODS, VARIANTS, assert_close, condensed_index
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -88,7 +88,7 @@ def check(tree_s, table_s, i, j, what):
     table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
     n = table_s.n_samples
     idx = condensed_index(n, i, j)
-    for method in METHODS:
+    for method in METHODS + VARIANTS:
         alpha = 0.5 if method == "generalized" else 1.0
         exp = oracle.pairs(tree_s, table_s, method, alpha, i, j)[0]
         for precision in PRECISIONS:

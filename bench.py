@@ -310,10 +310,10 @@ def downstream_agreement(mixed_outs, fp64_outs, sub=512, perms=999):
 
 
 # FP64 instructions per update of the FP64 accumulate kernels: the min / abs
-# kernel one DADD for u - v and one DADD of |u - v| into the accumulator;
-# the generalized kernel's count is the one ncu reports for it
-# (smsp__inst_executed_pipe_fp64 per update, profiles/).
-FP64_OPS_PER_UPDATE = {"min": 2.0, "gen": None}
+# kernel one DADD for u - v and one DADD of |u - v| into the accumulator
+# (ncu: 2.02); the generalized kernel (alpha = 1/2) 11.07, as ncu counts them
+# (smsp__inst_executed_pipe_fp64 per update; profiles/fp64_kernels_yule50k_n2048.md).
+FP64_OPS_PER_UPDATE = {"min": 2.0, "gen": 11.07}
 # GB300 FP64 lanes per SM and clock: nominal 1.25 TFLOP/s counting an FMA as two
 FP64_LANES_PER_SM = 2.0
 
@@ -452,6 +452,20 @@ def run_ours(args, rank, world, local_rank):
     # the duplicated half stripe)
     npairs = n * (n - 1) // 2 if full else stop * n
     rng_args = () if full else (0, stop)
+    job = None
+    if world > 1:
+        # the sharded job (stripes are independent subproblems, Abstract and
+        # Table 2): rank r computes its own stripe range of the one matrix --
+        # [r K, (r + 1) K) with K the one-GPU range, per-rank work fixed, or the
+        # whole matrix split evenly once N K stripes would run past it -- with
+        # no collective in the timed step; the end-to-end leg gathers every
+        # rank's part to rank 0
+        from paper_2005_05826_gb300.shard import job_ranges
+        job = job_ranges(S, 0 if full else stop, world)
+        start, stop = job[rank]
+        full = False
+        npairs = (stop - start) * n - (n // 2 if 2 * stop == n and stop > start else 0)
+        rng_args = (start, stop)
     peaks, peak_src = load_peaks()
     dist = None
     if world > 1:
@@ -476,7 +490,8 @@ def run_ours(args, rank, world, local_rank):
     tree = uf.Tree(tree_s.parent, tree_s.length)
     table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
     out_dtype = torch.float32 if args.out_fp32 else torch.float64
-    outs = [torch.empty(npairs, dtype=out_dtype, device=dev) for _ in METHODS]  # condensed or stripe-major
+    n_out = (rng_args[1] - rng_args[0]) * n if rng_args else npairs
+    outs = [torch.empty(n_out, dtype=out_dtype, device=dev) for _ in METHODS]  # condensed or stripe-major
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     uf.uf_set_option("kernel_timing", 1)
@@ -545,7 +560,12 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_total = float(t.item())
     updates_step = len(METHODS) * npairs * branches
-    value = world * updates_step * args.steps / t_total
+    job_updates = updates_step
+    if dist:  # the whole job's updates: the sum over the ranks' ranges
+        u = torch.tensor([float(updates_step)], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        job_updates = float(u.item())
+    value = job_updates * args.steps / t_total
     mixed_err = {}  # filled beside the FP64 path when both whole matrices are on the host
     # whole matrices on the host only where the downstream check wants them
     keep_host = full and npairs <= 50_000_000 and not (args.no_downstream and args.no_err)
@@ -655,6 +675,11 @@ def run_ours(args, rank, world, local_rank):
                         h.copy_(o, non_blocking=True)
                         db += o.numel() * o.element_size()
             torch.cuda.synchronize()
+            if dist:  # every rank's part to rank 0: the sharded job's one collective
+                from paper_2005_05826_gb300.shard import gather_parts
+                for o in outs:
+                    gather_parts(dist, n, job, o)
+                torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             tb.close()
             tr.close()
@@ -674,12 +699,12 @@ def run_ours(args, rank, world, local_rank):
                 t_mode = float(t.item())
             res[mode] = (t_mode, world * h2d, world * d2h)
         t_e, h2d, d2h = res[False]
-        e2e = {"value": world * updates_step / t_e, "unit": "updates/s",
+        e2e = {"value": job_updates / t_e, "unit": "updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e,
                "path": f"fresh tree and table handles from the host arrays, {len(METHODS)} uf_compute calls "
                        f"queued on the stream with device outputs, results read into pinned host memory"}
         if True in res:
-            e2e["host_output_calls"] = {"value": world * updates_step / res[True][0],
+            e2e["host_output_calls"] = {"value": job_updates / res[True][0],
                                         "ms_per_step": 1e3 * res[True][0],
                                         "d2h_bytes_per_step": int(res[True][2]),
                                         "path": "the same with pageable host result arrays the caller reuses "

@@ -528,7 +528,8 @@ struct SparseScatter {
   int64_t n_sparse_rows = 0, cells = 0, n_cols = 0;
   std::vector<int64_t> sp_off;  // first entry of each capacity class in the sparse list
   size_t o_sparse = 0, o_sptabs = 0, o_lofs = 0;
-  DevBuf le, lk, lz, Dsp;
+  DevBuf le, lk, lz, Dsp, cur;
+  int64_t list_entries = 0;
   std::vector<SpLayout> lay;
 
   // acc: ACC_MIN / ACC_GEN; fp64_entries: terms computed in FP64
@@ -557,8 +558,10 @@ struct SparseScatter {
       for (size_t r = 0; r < all.size(); r++)
         lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
       const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
+      list_entries = (int64_t)total_e;
       le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries), st, "alloc sparse lists");
       lk = DevBuf(total_e * 4, st, "alloc sparse lists");
+      cur = DevBuf(total_e * 8, st, "alloc sparse list cursors");
       lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
       // rows without entries in the table return before writing their count
       ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
@@ -602,6 +605,8 @@ struct SparseScatter {
       base.lk = lk.as<int>();
       base.lofs = meta.at<int64_t>(o_lofs);
       base.lz = lz.as<int>();
+      base.cur = cur.as<int>();
+      base.cur_stride = list_entries;
     }
     for (size_t c = 0; c < split->sparse.size(); c++) {
       if (split->sparse[c].empty()) continue;
@@ -623,6 +628,7 @@ struct SparseScatter {
       sp.n_nodes = (int)n_sparse_rows;
       sp.r0 = (int)r0;
       sp.r1 = (int)std::min<int64_t>(r0 + per, (int64_t)lay[0].s_hi + 1);
+      sp.first_region = r0 == lay[0].s_lo;
       ck(launch_sparse_region(acc, f32, sp, on), "sparse regions");
       (*kernels)++;
     }

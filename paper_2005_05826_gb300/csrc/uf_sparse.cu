@@ -398,18 +398,30 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   c.lt = (T)a.length[v];
   c.am1 = (T)(a.alpha - 1.0);
   c.scale = a.scale;
+  // Regions come in increasing stripe order (r0 of one is r1 of the one
+  // before), so for a sample a the partners of window 1 move up and those of
+  // window 2 move down from region to region: each entry keeps a cursor per
+  // window where the previous region stopped, and only the first region of a
+  // call searches for it.
+  int *cur1 = a.cur + off, *cur2 = a.cur + a.cur_stride + off;
   for (int ia = threadIdx.x; ia < z - 1; ia += blockDim.x) {
     const SpEnt<T> ea = E[ia];
     // window 1: d = k_b - k_a in [r0 + 1, min(r1, n/2)], stripe d - 1, cell column k_a
-    // window 2: d in [max(n - r1, n/2 + 1), n - r0 - 1], stripe n - d - 1, column k_b
-    const int d_lo[2] = {a.r0 + 1, max(n - a.r1, half + 1)};
-    const int d_hi[2] = {min(a.r1, half), n - a.r0 - 1};
-#pragma unroll
-    for (int w = 0; w < 2; w++) {
-      if (d_lo[w] > d_hi[w]) continue;
-      const int b0 = lower_index(K, ia + 1, z, ea.k + d_lo[w]);
-      const int b1 = lower_index(K, b0, z, ea.k + d_hi[w] + 1);
-      for (int ib = b0; ib < b1; ib++) add_pair<T, ACC, MODE>(ea, E[ib], c);
+    {
+      const int dlo = a.r0 + 1, dhi = min(a.r1, half);
+      int b = a.first_region ? lower_index(K, ia + 1, z, ea.k + dlo) : cur1[ia];
+      if (dlo <= dhi)
+        for (; b < z && K[b] <= ea.k + dhi; b++) add_pair<T, ACC, MODE>(ea, E[b], c);
+      cur1[ia] = b;
+    }
+    // window 2: d in [max(n - r1, n/2 + 1), n - r0 - 1], stripe n - d - 1, column k_b;
+    // the cursor is one past the last partner not yet added
+    {
+      const int dlo = max(n - a.r1, half + 1), dhi = n - a.r0 - 1;
+      int e = a.first_region ? lower_index(K, ia + 1, z, ea.k + dhi + 1) : cur2[ia];
+      if (dlo <= dhi)
+        for (; e > ia + 1 && K[e - 1] >= ea.k + dlo; e--) add_pair<T, ACC, MODE>(ea, E[e - 1], c);
+      cur2[ia] = e;
     }
   }
 }

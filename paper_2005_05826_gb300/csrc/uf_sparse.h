@@ -49,6 +49,9 @@ struct SparseArgs {
   int *lz;                  // entries of each row
   // region mode: only pairs whose stripe lies in [r0, r1) (launch_sparse_region)
   int r0, r1;
+  int first_region;         // 1: the call's first region (cursors are searched, not read)
+  int *cur;                 // two cursors per list entry: window 1 at cur[e], window 2 at
+  int64_t cur_stride;       // cur[cur_stride + e] (regions must come in increasing order)
 };
 // largest subtree entry count a sparse row may have: scattered directly from
 // shared memory, or written as a list (one table, keys alone in shared memory)
@@ -60,9 +63,10 @@ cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStre
 cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 // Pairs of the listed rows (nodes[0 .. n_nodes), lists from a list-mode
 // launch, table tabs[0]) whose stripe lies in [a.r0, a.r1): one CTA per row,
-// each thread takes samples a and finds the partners b of the two windows
-// of k_b - k_a that map into the region by binary search.  Run region by
-// region so that the accumulator cells a launch touches stay in L2.
+// each thread takes samples a and walks the partners b of the two windows of
+// k_b - k_a that map into the region from per-entry cursors (set by binary
+// search in the first region).  Run region by region, in increasing stripe
+// order, so that the accumulator cells a launch touches stay in L2.
 cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 
 }  // namespace ufg

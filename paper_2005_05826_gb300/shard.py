@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["stripe_ranges", "stitch_condensed", "gather_and_stitch"]
+__all__ = ["stripe_ranges", "job_ranges", "stitch_condensed", "gather_parts", "gather_and_stitch"]
 
 
 def stripe_ranges(n_stripes: int, world: int):
@@ -26,6 +26,17 @@ def stripe_ranges(n_stripes: int, world: int):
         out.append((start, stop))
         start = stop
     return out
+
+
+def job_ranges(n_stripes: int, per_rank: int, world: int):
+    """The stripe ranges of a job that gives every rank ``per_rank`` stripes
+    of one matrix: rank r takes [r * per_rank, (r + 1) * per_rank) while
+    world * per_rank stripes exist (per-rank work fixed as ranks are added);
+    once they would run past the matrix, the whole matrix [0, n_stripes) is
+    split evenly instead."""
+    if per_rank <= 0 or world * per_rank >= n_stripes:
+        return stripe_ranges(n_stripes, world)
+    return [(r * per_rank, (r + 1) * per_rank) for r in range(world)]
 
 
 def stitch_condensed(n: int, ranges, parts) -> np.ndarray:
@@ -44,31 +55,44 @@ def stitch_condensed(n: int, ranges, parts) -> np.ndarray:
     return out
 
 
-def gather_and_stitch(dist, n: int, ranges, local_part) -> np.ndarray | None:
-    """All ranks send their stripe-major part; rank 0 returns the stitched
-    condensed matrix (the one collective of a sharded run), others None.
+def gather_parts(dist, n: int, ranges, local_part):
+    """All ranks send their stripe-major part to rank 0 (point-to-point: the
+    one collective of a sharded run); rank 0 returns the list of parts as
+    tensors (on its GPU under NCCL, on the host under gloo), the others None.
 
     local_part is a numpy array or a torch tensor (a device output of
-    uf_compute may be passed as it is).  With the NCCL backend the parts
-    travel as CUDA tensors on the current device; with gloo, as host tensors."""
+    uf_compute may be passed as it is; its dtype is kept, float32 or
+    float64).  With the NCCL backend the parts travel as CUDA tensors on the
+    current device; with gloo, as host tensors."""
     import torch
     rank, world = dist.get_rank(), dist.get_world_size()
     nccl = str(dist.get_backend()).lower() == "nccl"
     dev = torch.device("cuda", torch.cuda.current_device()) if nccl else torch.device("cpu")
     if isinstance(local_part, torch.Tensor):
-        t = local_part.reshape(-1).to(device=dev, dtype=torch.float64)
+        dtype = local_part.dtype if local_part.dtype in (torch.float32, torch.float64) else torch.float64
+        t = local_part.reshape(-1).to(device=dev, dtype=dtype)
     else:
         t = torch.as_tensor(np.ascontiguousarray(local_part, dtype=np.float64).ravel()).to(dev)
     sizes = [(stop - start) * n for start, stop in ranges]
     if t.numel() != sizes[rank]:
         raise ValueError(f"rank {rank}: part has {t.numel()} values, its stripe range {sizes[rank]}")
     if rank == 0:
-        bufs = [torch.empty(sz, dtype=torch.float64, device=dev) for sz in sizes]
+        bufs = [torch.empty(sz, dtype=t.dtype, device=dev) for sz in sizes]
         bufs[0].copy_(t)
         for r in range(1, world):
             if sizes[r]:
                 dist.recv(bufs[r], src=r)
-        return stitch_condensed(n, ranges, [b.cpu().numpy() for b in bufs])
+        return bufs
     if sizes[rank]:
         dist.send(t, dst=0)
     return None
+
+
+def gather_and_stitch(dist, n: int, ranges, local_part) -> np.ndarray | None:
+    """All ranks send their stripe-major part; rank 0 returns the stitched
+    condensed matrix of the whole stripe set (ranges covering [0, S)), the
+    others None."""
+    bufs = gather_parts(dist, n, ranges, local_part)
+    if bufs is None:
+        return None
+    return stitch_condensed(n, ranges, [b.double().cpu().numpy() for b in bufs])

@@ -97,3 +97,13 @@ def test_three_rank_gloo_gather_with_an_empty_range():
         p.join(timeout=120)
     assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
     assert q.get(timeout=5) <= 1e-14
+
+
+def test_job_ranges_fixed_per_rank_then_split():
+    from paper_2005_05826_gb300.shard import job_ranges
+    assert job_ranges(56500, 8192, 1) == [(0, 8192)]
+    assert job_ranges(56500, 8192, 4) == [(0, 8192), (8192, 16384), (16384, 24576), (24576, 32768)]
+    # eight ranks would run past the matrix: the whole matrix split evenly
+    r = job_ranges(56500, 8192, 8)
+    assert r[0][0] == 0 and r[-1][1] == 56500 and len(r) == 8
+    assert job_ranges(1024, 0, 2) == [(0, 512), (512, 1024)]

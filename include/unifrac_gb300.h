@@ -30,7 +30,9 @@
  *   (variance-adjusted weighted UniFrac, Chang, Luan & Sun, BMC
  *   Bioinformatics 12:118, 2011; branches with m_v = 0 or m_v = m add 0;
  *   these run every branch through the dense stripe kernel: option
- *   "sparse" does not apply to them)
+ *   "sparse" does not apply to them).  UF_UNWEIGHTED_UNNORMALIZED runs on
+ *   the CUDA-core kernels in both precisions (its numerator is summed
+ *   directly, never as a difference of sums)
  *
  * A ratio whose denominator is 0 is reported as 0.  The root's branch does
  * not exist: length[root] is ignored.
@@ -142,9 +144,10 @@ typedef struct {
  *   "kernel_timing"  0 (default) or 1: time each phase with CUDA events and
  *                    fill the t_*_ms fields of uf_report (adds a stream sync)
  *   "tensor_path"    1 (default): UF_UNWEIGHTED with UF_MIXED runs on the
- *                    tcgen05 tensor cores when every table's full gram matrix
- *                    (n rounded up to 256, squared, 8 bytes) fits in half the
- *                    free device memory, else on the CUDA-core stripe kernels
+ *                    tcgen05 tensor cores when the gram tiles its stripes need
+ *                    (128 x 256 int64 cells each, the diagonal tiles included)
+ *                    and the sparse rows' stripe cells fit in half the free
+ *                    device memory, else on the CUDA-core stripe kernels
  *                    (report path 0); 0: always on the CUDA-core kernels
  *   "graph"          1 (default): a call's branch-block launch sequence is
  *                    captured into a CUDA graph and launched as one graph
@@ -280,6 +283,25 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
                            uf_method method, double alpha, uf_precision precision,
                            void *const *outs, int out_is_device, uf_report *reps,
                            void *cuda_stream);
+
+/*
+ * Many stripe ranges in one call (stripes are independent subproblems,
+ * Abstract and Fig. 1; several inputs batched into one kernel invocation,
+ * Sec. 3): job t computes the stripes [starts[t], stops[t]) of tables[t]
+ * into outs[t] -- the condensed matrix for the full range, stripe-major
+ * values otherwise, as uf_compute -- in doubles, or floats if out_fp32.  A
+ * table may appear in several jobs; all tables share the tree.  The jobs go
+ * to the device as one batched schedule: one launch per embedding level and
+ * one accumulate launch (or tensor-core gram) for all jobs together.  An
+ * empty range writes nothing.  reps may be NULL or an array of n_jobs
+ * reports.  Same stream semantics as uf_compute.
+ * Errors: UF_EINVAL, UF_ERANGE (a range outside [0, uf_stripe_count(n)] or
+ * start > stop), UF_ETABLE, UF_ENOMEM, UF_ECUDA, UF_ETIMEOUT.
+ */
+uf_status uf_compute_ranges(const uf_tree *tree, const uf_table *const *tables, const int64_t *starts,
+                            const int64_t *stops, int64_t n_jobs, uf_method method, double alpha,
+                            uf_precision precision, void *const *outs, int out_is_device, int out_fp32,
+                            uf_report *reps, void *cuda_stream);
 
 /*
  * uf_compute_noalloc -- the full-range computation of uf_compute (condensed

@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = ["UFError", "Tree", "Table", "Report", "METHODS", "PRECISIONS", "library_path", "load",
            "uf_last_error", "uf_stripe_count", "uf_tree_create", "uf_table_create", "uf_compute",
-           "uf_compute_batch", "uf_compute_noalloc", "uf_set_option", "uf_get_option",
+           "uf_compute_batch", "uf_compute_ranges", "uf_compute_noalloc", "uf_set_option", "uf_get_option",
            "condensed_size"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -102,6 +102,9 @@ def load():
         lib.uf_compute_batch.argtypes = [vp, vp, i64, i32, dbl, i32, vp, i32,
                                          ctypes.POINTER(Report), vp]
         lib.uf_compute_batch.restype = i32
+        lib.uf_compute_ranges.argtypes = [vp, vp, vp, vp, i64, i32, dbl, i32, vp, i32, i32,
+                                          ctypes.POINTER(Report), vp]
+        lib.uf_compute_ranges.restype = i32
         lib.uf_compute_noalloc.argtypes = [vp, vp, i32, dbl, i32, vp, vp]
         lib.uf_compute_noalloc.restype = i32
         lib.uf_set_option.argtypes = [ctypes.c_char_p, i64]
@@ -314,6 +317,48 @@ def uf_compute_batch(tree: Tree, tables, method: str, alpha: float = 1.0, precis
                                     p_code, ptrs, is_dev, reps,
                                     ctypes.c_void_p(int(st)) if st else None))
     return [s[3] for s in specs], [reps[i] for i in range(nt)]
+
+
+def uf_compute_ranges(tree: Tree, jobs, method: str, alpha: float = 1.0, precision: str = "fp64",
+                      outs=None, out_fp32: bool = False, stream=None):
+    """Many (table, stripe_start, stripe_stop) jobs over one tree in one call.
+    Job t's output is the condensed matrix for the full range, else
+    (stop - start) x n stripe-major values.  Returns ``(outs, reports)``."""
+    lib = load()
+    m_code, p_code = _code_of(METHODS, method, "method"), _code_of(PRECISIONS, precision, "precision")
+    nj = len(jobs)
+    if outs is None:
+        outs = [None] * nj
+    sizes = []
+    for table, start, stop in jobs:
+        full = start == 0 and stop == uf_stripe_count(table.n_samples)
+        sizes.append(condensed_size(table.n_samples) if full else max(stop - start, 0) * table.n_samples)
+    specs = [_out_spec(o, sz, out_fp32) for o, sz in zip(outs, sizes)]
+    devs = {s[1] for s in specs}
+    if len(devs) > 1:
+        raise ValueError("outputs must be all host or all device buffers")
+    is_dev = devs.pop() if devs else 0
+    cuda_devs = {o.device for o in outs if hasattr(o, "is_cuda") and o.is_cuda}
+    if len(cuda_devs) > 1:
+        raise ValueError("device outputs must all be on one device")
+    st = stream if stream is not None else next((s[2] for s in specs if s[2]), None)
+    handles = (ctypes.c_void_p * nj)(*[t.handle.value for t, _, _ in jobs])
+    starts = np.ascontiguousarray([int(a) for _, a, _ in jobs], dtype=np.int64)
+    stops = np.ascontiguousarray([int(b) for _, _, b in jobs], dtype=np.int64)
+    ptrs = (ctypes.c_void_p * nj)(*[s[0] for s in specs])
+    reps = (Report * max(nj, 1))()
+    with _on_device_of(next((o for o in outs if hasattr(o, "is_cuda") and o.is_cuda), None)):
+        _check(lib.uf_compute_ranges(tree.handle, handles, _ptr(starts), _ptr(stops), nj, m_code, float(alpha),
+                                     p_code, ptrs, is_dev, int(bool(out_fp32)), reps,
+                                     ctypes.c_void_p(int(st)) if st else None))
+    res = []
+    for (table, start, stop), s, sz in zip(jobs, specs, sizes):
+        keep = s[3]
+        full = start == 0 and stop == uf_stripe_count(table.n_samples)
+        if isinstance(keep, np.ndarray) and outs[len(res)] is None and not full:
+            keep = keep.reshape(max(stop - start, 0), table.n_samples)
+        res.append(keep)
+    return res, [reps[i] for i in range(nj)]
 
 
 def uf_compute_noalloc(tree: Tree, table: Table, method: str, alpha: float = 1.0,

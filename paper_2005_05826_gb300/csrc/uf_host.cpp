@@ -756,6 +756,53 @@ uf_status uf_compute_batch(const uf_tree *tree, const uf_table *const *tables, i
   }
 }
 
+uf_status uf_compute_ranges(const uf_tree *tree, const uf_table *const *tables, const int64_t *starts,
+                            const int64_t *stops, int64_t n_jobs, uf_method method, double alpha,
+                            uf_precision precision, void *const *outs, int out_is_device, int out_fp32,
+                            uf_report *reps, void *cuda_stream) {
+  g_err.clear();
+  if (!tables || !starts || !stops || !outs || n_jobs < 0) return fail(UF_EINVAL, "null job arrays");
+  BatchJob J{method, alpha, precision == UF_MIXED, out_is_device, out_fp32, (cudaStream_t)cuda_stream, {}};
+  int64_t n_axis = 0;
+  for (int64_t t = 0; t < n_jobs; t++) {
+    uf_status st = check_args(tree, tables[t], method, alpha, precision);
+    if (st) return st;
+    if (reps) memset(&reps[t], 0, sizeof(uf_report));
+    const int64_t S = uf_stripe_count(tables[t]->n);
+    if (starts[t] < 0 || stops[t] < starts[t] || stops[t] > S)
+      return fail(UF_ERANGE, "job %lld: stripe range [%lld, %lld) outside [0, %lld]", (long long)t,
+                  (long long)starts[t], (long long)stops[t], (long long)S);
+    if (starts[t] == stops[t]) continue;  // nothing to write
+    if (!outs[t]) return fail(UF_EINVAL, "null output buffer for job %lld", (long long)t);
+    n_axis += tables[t]->n;
+    if (n_axis > MAX_CALL_SAMPLES)
+      return fail(UF_EINVAL, "jobs 0..%lld hold %lld samples: a compute call takes at most 2^30", (long long)t,
+                  (long long)n_axis);
+    J.tabs.push_back(
+        TableJob{const_cast<uf_table *>(tables[t]), starts[t], stops[t], outs[t], reps ? &reps[t] : nullptr});
+  }
+  if (J.tabs.empty()) return UF_OK;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(UF_ECUDA, "no CUDA device available");
+  }
+  if (out_is_device)
+    for (const TableJob &t : J.tabs) {
+      const uf_status st = check_device_output(t.out, "an output buffer");
+      if (st != UF_OK) return st;
+    }
+  try {
+    return run_batch(const_cast<uf_tree *>(tree), J);
+  } catch (const CudaFail &f) {
+    return f.st;
+  } catch (const std::bad_alloc &) {
+    return fail(UF_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(UF_ENOMEM, "host resources: %s", e.what());
+  }
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- views

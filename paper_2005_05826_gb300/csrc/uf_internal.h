@@ -92,6 +92,10 @@ struct StripeArgs {
   // this many elements after its first word (M and M2 cells; Dg); the FP32
   // kernels keep one word
   int64_t m_lo_off, d_lo_off;
+  // FP32 min kernel: 0xFF runs every stripe in the abs form (methods whose
+  // numerator must not come from a difference of sums); anything else the
+  // default FP32_ABS_ROW_MASK
+  unsigned abs_mask;
 };
 // stripes and samples per CTA tile of the accumulate kernel
 void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k);

@@ -874,6 +874,12 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   const bool fp32 = J.fp32;
   const size_t es = fp32 ? 4 : 8;
   const int planes = kind == EMB_VAW ? 3 : 1;  // embedding planes per branch row
+  // stripes in the abs form: FP32 1, 3, 5, 7 of 8, FP64 all; the unweighted
+  // numerator alone (unnormalized) all in FP32 too, since a min-form
+  // numerator W_k + W_j - 2M carries FP32 rounding relative to W, not to num
+  const unsigned amask = acc != ACC_MIN ? 0u
+                         : (fp32 && method == UF_UNWEIGHTED_UNNORMALIZED) ? 0xFFu
+                                                                          : abs_row_mask(fp32);
   int tile_s = 0, tile_k = 0;
   stripe_tile_shape(acc, fp32, &tile_s, &tile_k);
   std::vector<TabDesc> tabs(nt);
@@ -980,7 +986,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   auto launch_sparse = [&](cudaStream_t on) {
     SparseArgs sp{};
     sp.kind = kind;
-    sp.abs_mask = acc == ACC_MIN ? abs_row_mask(fp32) : 0u;
+    sp.abs_mask = amask;
     sp.gen_abs = acc == ACC_GEN && !fp32;
     sp.M = M.as<unsigned long long>();
     sp.M2 = M2.as<unsigned long long>();
@@ -1034,6 +1040,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sa.counter = counter.as<int>();
     sa.m_lo_off = fp32 ? 0 : cells;
     sa.d_lo_off = fp32 ? 0 : n_cols;
+    sa.abs_mask = amask;
     if (tune && !tuned) {
       chunk = sa.chunk = tune_chunk(acc, fp32, sa, m_bytes, ls);
       tuned = true;
@@ -1068,7 +1075,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     fa.s0 = J.tabs[t].start;
     fa.s1 = J.tabs[t].stop;
     fa.full = J.tabs[t].start == 0 && J.tabs[t].stop == tabs[t].n / 2;
-    fa.abs_mask = acc == ACC_MIN ? abs_row_mask(fp32) : 0u;
+    fa.abs_mask = amask;
     fa.gen_abs = acc == ACC_VAW || (acc == ACC_GEN && !fp32);
     fa.clamps = clamps.as<unsigned long long>();
     fa.M = M.as<unsigned long long>() + tabs[t].m_off;
@@ -1149,7 +1156,9 @@ uf_status run_batch(uf_tree *tree, const BatchJob &J) {
     const double s = accum_scale(tree, t.table, kind);
     scale = scale == 0.0 ? s : std::min(scale, s);
   }
-  if (kind == EMB_PRESENCE && J.fp32 && g_tensor_path.load()) {
+  // (the unweighted numerator alone stays on the CUDA-core kernels: the gram
+  // gives it as W_i + W_j - 2G, rounded relative to W rather than to itself)
+  if (method == UF_UNWEIGHTED && J.fp32 && g_tensor_path.load()) {
     // the tensor path stores the gram tiles the stripes need (and the
     // diagonal) plus the sparse rows' stripe cells; when those do not fit in
     // half the free memory the CUDA-core stripe kernels take the call

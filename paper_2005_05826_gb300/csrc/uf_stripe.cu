@@ -707,9 +707,11 @@ int stripe_chunk_rows() { return 2048; }
 
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st) {
   if (a.rows <= 0 || a.n_tiles <= 0) return cudaSuccess;
-  if (acc == ACC_MIN)
-    return fp32 ? run_min<float, 8, 8, FP32_ABS_ROW_MASK, 2>(a, st)
-                : run_min<double, 8, 8, FP64_ABS_ROW_MASK, 1>(a, st);
+  if (acc == ACC_MIN) {
+    if (!fp32) return run_min<double, 8, 8, FP64_ABS_ROW_MASK, 1>(a, st);
+    return a.abs_mask == 0xFFu ? run_min<float, 8, 8, 0xFFu, 2>(a, st)
+                               : run_min<float, 8, 8, FP32_ABS_ROW_MASK, 2>(a, st);
+  }
   if (acc == ACC_VAW) return fp32 ? run_vaw<float, 4, 4, 2>(a, st) : run_vaw<double, 4, 4, 1>(a, st);
   const bool half = a.alpha == 0.5;
   if (fp32) return half ? run_gen<float, 4, 8, 0, 2>(a, st) : run_gen<float, 4, 8, 1, 2>(a, st);

@@ -265,3 +265,24 @@ def test_no_cpu_fallback():
     table = uf.Table(tab_s.indptr, tab_s.indices, tab_s.data, tree)
     assert _code(lambda: uf.uf_compute(tree, table, "unweighted")) == "UF_ECUDA"
     assert _code(lambda: uf.uf_compute_batch(tree, [table, table], "generalized", 0.5, "mixed")) == "UF_ECUDA"
+
+
+def test_compute_ranges_validates_before_the_device():
+    # job ranges are checked on the host: a range past the table's stripes is
+    # UF_ERANGE, and valid jobs without a GPU are UF_ECUDA (no CPU fallback)
+    from synth import table_iid, yule_tree
+    tree_s = yule_tree(50, seed=3)
+    table_s = table_iid(12, tree_s.n_tips, 0.3, seed=4)
+    tree = uf.Tree(tree_s.parent, tree_s.length)
+    table = uf.Table(table_s.indptr, table_s.indices, table_s.data, tree)
+    with pytest.raises(uf.UFError) as e:
+        uf.uf_compute_ranges(tree, [(table, 0, 3), (table, 4, 7)], "weighted_normalized")
+    assert e.value.status == "UF_ERANGE"
+    # empty ranges only: nothing to compute, UF_OK on any machine
+    outs, reps = uf.uf_compute_ranges(tree, [(table, 2, 2)], "unweighted")
+    assert outs[0].size == 0
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(uf.UFError) as e:
+            uf.uf_compute_ranges(tree, [(table, 0, 3), (table, 3, 6)], "unweighted", precision="mixed")
+        assert e.value.status == "UF_ECUDA"

@@ -43,8 +43,8 @@ def test_variants_yule1k_n64_all_pairs(method, precision):
     exp = oracle.condensed(tree_s, table_s, method)
     assert_close(got, exp, method, precision, "variants yule1k_n64")
     assert rep.updates == 2016 * (tree_s.n_nodes - 1)
-    if method == "unweighted_unnormalized" and precision == "mixed":
-        assert rep.path == 1
+    if method == "unweighted_unnormalized":
+        assert rep.path == 0  # CUDA-core kernels, abs form on every stripe
 
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 7, 8, 31, 32, 33, 63, 64, 65, 127, 128, 129, 257])

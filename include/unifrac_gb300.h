@@ -154,9 +154,14 @@ typedef struct {
  *                    (not when "kernel_timing" is 1); 0: plain launches
  *   "autotune"       1 (default): the first call for an (accumulator,
  *                    precision, size) class times the accumulate kernel on
- *                    its first branch block with 1,024 / 2,048 / 4,096 / 8,192
- *                    branches per work unit and keeps the fastest for the
- *                    process; 0: 2,048; 2: forget the kept choices, then 1
+ *                    its first branch block with every tile shape it offers
+ *                    (the FP32 min kernel: 128 x 128 or 64 x 128 stripes x
+ *                    samples) and 1,024 / 2,048 / 4,096 / 8,192 branches per
+ *                    work unit, and keeps the fastest for the process;
+ *                    0: the first shape and 2,048; 2: forget the kept
+ *                    choices, then 1
+ *   "tile_shape"     -1 (default): the shape the autotuner picks; 0 or 1:
+ *                    that shape, where the kernel offers it (for testing)
  *   "sparse"         1 (default): a branch whose subtree holds few count
  *                    entries skips the dense stripe kernels; its terms are
  *                    added pair by pair over the samples nonzero under it,

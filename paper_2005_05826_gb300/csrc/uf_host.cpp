@@ -30,6 +30,7 @@ std::atomic<int64_t> g_autotune{1};
 std::atomic<int64_t> g_sparse{1};
 std::atomic<int64_t> g_overlap{1};
 std::atomic<int64_t> g_tensor_wait_test{0};
+std::atomic<int64_t> g_tile_shape{-1};
 std::atomic<int64_t> g_region_bytes{(int64_t)SPARSE_REGION_BYTES_DEFAULT};
 
 int host_threads() {
@@ -417,6 +418,11 @@ uf_status uf_set_option(const char *name, int64_t value) {
     g_overlap = value;
     return UF_OK;
   }
+  if (!strcmp(name, "tile_shape")) {
+    if (value < -1 || value > 1) return fail(UF_EINVAL, "tile_shape must be -1, 0 or 1");
+    g_tile_shape = value;
+    return UF_OK;
+  }
   if (!strcmp(name, "sparse_region_bytes")) {
     if (value != 0 && value < 4096) return fail(UF_EINVAL, "sparse_region_bytes must be 0 or >= 4096");
     g_region_bytes = value ? value : (int64_t)SPARSE_REGION_BYTES_DEFAULT;
@@ -436,6 +442,7 @@ int64_t uf_get_option(const char *name) {
   if (!strcmp(name, "sparse_region_bytes")) return g_region_bytes.load();
   if (!strcmp(name, "sparse_overlap")) return g_overlap.load();
   if (!strcmp(name, "tensor_wait_test")) return g_tensor_wait_test.load();
+  if (!strcmp(name, "tile_shape")) return g_tile_shape.load();
   return -1;
 }
 

@@ -96,9 +96,13 @@ struct StripeArgs {
   // numerator must not come from a difference of sums); anything else the
   // default FP32_ABS_ROW_MASK
   unsigned abs_mask;
+  int shape;            // tile shape (stripe_tile_shape); the descriptors must match it
 };
-// stripes and samples per CTA tile of the accumulate kernel
-void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k);
+// stripes and samples per CTA tile of the accumulate kernel; `shape` picks
+// one of stripe_shapes() tile shapes (0: the default)
+void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k, int shape = 0);
+// tile shapes the accumulate kernel of (acc, precision, abs mask) offers
+int stripe_shapes(int acc, bool fp32, unsigned abs_mask);
 // default rows per work unit
 int stripe_chunk_rows();
 cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStream_t st);

@@ -324,13 +324,15 @@ struct Capture {
   }
 };
 
-// Autotuned rows per work unit, by (accumulator, precision, size bucket).
+// Autotuned (tile shape, rows per work unit), by (accumulator, precision,
+// size bucket).
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, int> g_tuned_chunk;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned_chunk;
 
-std::tuple<int, int, int, int> tune_key(int acc, bool fp32, int64_t n_tiles, int64_t rows) {
+// kernel: 0 FP64, 1 FP32, 2 FP32 all-abs
+std::tuple<int, int, int, int> tune_key(int acc, int kernel, int64_t n_tiles, int64_t rows) {
   auto lg = [](int64_t x) { return (int)std::floor(std::log2((double)std::max<int64_t>(x, 1))); };
-  return {acc, fp32 ? 1 : 0, lg(n_tiles), lg(rows)};
+  return {acc, kernel, lg(n_tiles), lg(rows)};
 }
 
 // A timing event destroyed with its scope, also when a CUDA error is thrown.
@@ -344,28 +346,35 @@ struct ScopedEvent {
   ScopedEvent &operator=(const ScopedEvent &) = delete;
 };
 
-// Time the accumulate launch of the first block with each candidate chunk
-// size and keep the fastest (the accumulators are cleared afterwards).
-int tune_chunk(int acc, bool fp32, StripeArgs sa, size_t m_bytes, cudaStream_t st) {
+// Time the accumulate launch of the first block with each candidate tile
+// shape and chunk size and keep the fastest (the accumulators are cleared
+// afterwards).  tabs[s] / n_tiles[s]: the descriptors of shape s.
+std::pair<int, int> tune_chunk(int acc, bool fp32, StripeArgs sa, const std::vector<const TabDesc *> &tabs,
+                               const std::vector<int> &n_tiles, size_t m_bytes, cudaStream_t st) {
   const int cand[4] = {1024, 2048, 4096, 8192};
   const ScopedEvent ev0, ev1;
   cudaEvent_t e0 = ev0.e, e1 = ev1.e;
-  int best = stripe_chunk_rows();
+  std::pair<int, int> best{0, stripe_chunk_rows()};
   float best_ms = 1e30f;
-  for (int c : cand) {
-    if (c > 2 * std::max(sa.rows, 1024)) break;
-    sa.chunk = c;
-    ck(cudaEventRecord(e0, st), "cudaEventRecord");
-    ck(launch_stripe_acc(acc, fp32, sa, st), "autotune");
-    ck(cudaEventRecord(e1, st), "cudaEventRecord");
-    ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
-    float ms = 0.f;
-    ck(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = c;
+  for (size_t shape = 0; shape < tabs.size(); shape++)
+    for (int c : cand) {
+      if (n_tiles[shape] < 0) break;  // not a candidate
+      if (c > 2 * std::max(sa.rows, 1024)) break;
+      sa.chunk = c;
+      sa.shape = (int)shape;
+      sa.tabs = tabs[shape];
+      sa.n_tiles = n_tiles[shape];
+      ck(cudaEventRecord(e0, st), "cudaEventRecord");
+      ck(launch_stripe_acc(acc, fp32, sa, st), "autotune");
+      ck(cudaEventRecord(e1, st), "cudaEventRecord");
+      ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
+      float ms = 0.f;
+      ck(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = {(int)shape, c};
+      }
     }
-  }
   ck(cudaMemsetAsync(sa.M, 0, m_bytes, st), "memset");
   if (sa.M2) ck(cudaMemsetAsync(sa.M2, 0, m_bytes, st), "memset");
   return best;
@@ -905,6 +914,29 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     pitch += round_up(round_up(n, tile_k) + (int64_t)(d.m_hi + 1) * tile_s, 32);
     cells += (J.tabs[t].stop - J.tabs[t].start) * (int64_t)n;
   }
+  // the descriptors of every tile shape the kernel offers (shape 0 above; the
+  // others have shorter stripe tiles, so the rows' pitch of shape 0 fits them)
+  const int n_shapes = stripe_shapes(acc, fp32, amask);
+  // option "tile_shape": a forced shape when the kernel has it, else tuned (or 0)
+  const int forced = g_tile_shape.load() >= 0 && g_tile_shape.load() < n_shapes ? (int)g_tile_shape.load() : -1;
+  std::vector<std::vector<TabDesc>> shape_tabs(1, tabs);
+  std::vector<int> shape_tiles(1, n_tiles), shape_ts(1, tile_s), shape_tk(1, tile_k);
+  for (int sh = 1; sh < n_shapes; sh++) {
+    int ts2 = 0, tk2 = 0, nt2 = 0;
+    stripe_tile_shape(acc, fp32, &ts2, &tk2, sh);
+    std::vector<TabDesc> tb2(tabs);
+    for (TabDesc &d : tb2) {
+      d.m_lo = d.s_lo / ts2;
+      d.m_hi = d.s_hi / ts2;
+      d.n_ktiles = (d.n + tk2 - 1) / tk2;
+      d.tile0 = nt2;
+      nt2 += d.n_ktiles * (d.m_hi - d.m_lo + 1);
+    }
+    shape_tabs.push_back(std::move(tb2));
+    shape_tiles.push_back(nt2);
+    shape_ts.push_back(ts2);
+    shape_tk.push_back(tk2);
+  }
   const int64_t nb = tree->n_nodes - 1;
   // FP64: every fixed-point accumulator has a second word (uf_device.cuh),
   // stored after the first: M and M2 at + cells, Dg and the sparse R at + n_cols
@@ -937,6 +969,8 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   // table descriptors and row lists: one staged upload
   Meta meta;
   const size_t o_tabs = meta.add(tabs);
+  std::vector<size_t> o_shape_tabs(1, o_tabs);
+  for (int sh = 1; sh < n_shapes; sh++) o_shape_tabs.push_back(meta.add(shape_tabs[sh]));
   const size_t o_cnt = meta.add(split.cnt_lists);
   const size_t o_dense = meta.add(split.dense);
   const size_t o_dlen = meta.add(split.dense_len);
@@ -969,16 +1003,28 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   ck(cudaMemsetAsync(clamps.p, 0, sizeof(unsigned long long), st), "memset");
   Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
-  // chunk size: tuned once per (accumulator, precision, size bucket)
-  const auto key = tune_key(acc, fp32, n_tiles, xrows);
-  int chunk = stripe_chunk_rows();
+  // tile shape and chunk size: tuned once per (accumulator, precision, size
+  // bucket; the key's precision slot also tells the all-abs kernel apart)
+  const auto key = tune_key(acc, (fp32 ? (amask == 0xFFu ? 2 : 1) : 0) + 4 * (forced + 1), n_tiles, xrows);
+  int chunk = stripe_chunk_rows(), shape = forced > 0 ? forced : 0;
   bool tune = false;
   if (g_autotune.load() && !split.dense.empty()) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tuned_chunk.find(key);
-    if (it != g_tuned_chunk.end()) chunk = it->second;
-    else tune = true;
+    if (it != g_tuned_chunk.end()) {
+      shape = it->second.first;
+      chunk = it->second.second;
+    } else {
+      tune = true;
+    }
   }
+  auto use_shape = [&](int sh) {
+    shape = sh;
+    tile_s = shape_ts[sh];
+    tile_k = shape_tk[sh];
+    n_tiles = shape_tiles[sh];
+  };
+  use_shape(shape);
   // the launch sequence goes into a CUDA graph unless it is timed per phase
   Capture cap(g_graph.load() != 0 && !timer.on && !tune, st, device);
   const cudaStream_t ls = cap.stream();
@@ -1028,7 +1074,8 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sa.rows = (int)nd;
     sa.pitch = pitch;
     sa.chunk = chunk;
-    sa.tabs = d_tabs;
+    sa.shape = shape;
+    sa.tabs = meta.at<TabDesc>(o_shape_tabs[shape]);
     sa.n_tabs = (int)nt;
     sa.n_tiles = n_tiles;
     sa.n_cols = n_cols;
@@ -1042,10 +1089,23 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
     sa.d_lo_off = fp32 ? 0 : n_cols;
     sa.abs_mask = amask;
     if (tune && !tuned) {
-      chunk = sa.chunk = tune_chunk(acc, fp32, sa, m_bytes, ls);
+      std::vector<const TabDesc *> tp;
+      for (size_t o : o_shape_tabs) tp.push_back(meta.at<TabDesc>(o));
+      std::vector<int> tiles(shape_tiles);
+      if (forced >= 0) {  // only the forced shape is a candidate
+        for (size_t sh = 0; sh < tp.size(); sh++)
+          if ((int)sh != forced) tiles[sh] = -1;
+      }
+      const std::pair<int, int> best = tune_chunk(acc, fp32, sa, tp, tiles, m_bytes, ls);
+      use_shape(best.first);
+      chunk = best.second;
+      sa.chunk = chunk;
+      sa.shape = shape;
+      sa.tabs = tp[shape];
+      sa.n_tiles = n_tiles;
       tuned = true;
       std::lock_guard<std::mutex> g(g_tune_mu);
-      g_tuned_chunk[key] = chunk;
+      g_tuned_chunk[key] = best;
     }
     timer.begin(1);
     ck(launch_stripe_acc(acc, fp32, sa, ls), "stripe accumulate");

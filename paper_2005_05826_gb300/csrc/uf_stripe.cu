@@ -695,12 +695,17 @@ cudaError_t run_gen(const StripeArgs &a, cudaStream_t st, int max_per_sm = 0) {
 
 }  // namespace
 
-// micro-tiles: min kernels 8 x 8, generalized 4 x 8 (two accumulators),
-// variance-adjusted 4 x 4 (two accumulators, three planes)
-void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k) {
-  *tile_s = acc == ACC_MIN ? 16 * 8 : 16 * 4;
-  (void)fp32;
+// micro-tiles: min kernels 8 x 8 (shape 1 of the FP32 min kernel: 4 x 8
+// at three CTAs per SM, 64-stripe tiles that waste fewer stripes of small
+// tables), generalized 4 x 8 (two accumulators), variance-adjusted 4 x 4
+// (two accumulators, three planes)
+void stripe_tile_shape(int acc, bool fp32, int *tile_s, int *tile_k, int shape) {
+  *tile_s = acc == ACC_MIN && !(fp32 && shape == 1) ? 16 * 8 : 16 * 4;
   *tile_k = acc == ACC_VAW ? 16 * 4 : 16 * 8;
+}
+
+int stripe_shapes(int acc, bool fp32, unsigned abs_mask) {
+  return acc == ACC_MIN && fp32 && abs_mask != 0xFFu ? 2 : 1;
 }
 
 int stripe_chunk_rows() { return 2048; }
@@ -709,8 +714,9 @@ cudaError_t launch_stripe_acc(int acc, bool fp32, const StripeArgs &a, cudaStrea
   if (a.rows <= 0 || a.n_tiles <= 0) return cudaSuccess;
   if (acc == ACC_MIN) {
     if (!fp32) return run_min<double, 8, 8, FP64_ABS_ROW_MASK, 1>(a, st);
-    return a.abs_mask == 0xFFu ? run_min<float, 8, 8, 0xFFu, 2>(a, st)
-                               : run_min<float, 8, 8, FP32_ABS_ROW_MASK, 2>(a, st);
+    if (a.abs_mask == 0xFFu) return run_min<float, 8, 8, 0xFFu, 2>(a, st);
+    return a.shape == 1 ? run_min<float, 4, 8, FP32_ABS_ROW_MASK, 3>(a, st)
+                        : run_min<float, 8, 8, FP32_ABS_ROW_MASK, 2>(a, st);
   }
   if (acc == ACC_VAW) return fp32 ? run_vaw<float, 4, 4, 2>(a, st) : run_vaw<double, 4, 4, 1>(a, st);
   const bool half = a.alpha == 0.5;

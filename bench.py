@@ -577,13 +577,14 @@ def run_ours(args, rank, world, local_rank):
     sparse = {}
     phases = {}  # device ms per call and phase (CUDA events on the call's stream)
     for m, r in reps:
-        d = acc_ms.setdefault(m, [0.0, 0, 0, 0.0, 0, 0])
+        d = acc_ms.setdefault(m, [0.0, 0, 0, 0.0, 0, 0, 0])
         d[0] += r.t_accumulate_ms
         d[1] += r.acc_launches
         d[2] += 1
         d[3] += r.exec_flops
         d[4] = r.path
         d[5] = r.dense_rows
+        d[6] = r.stripe_tile
         sp = sparse.setdefault(m, {"rows": r.sparse_rows, "dense_rows": d[5], "pairs_at_most": r.sparse_pairs,
                                    "ms_per_call": 0.0})
         sp["ms_per_call"] += r.t_sparse_ms / phase_steps
@@ -594,7 +595,7 @@ def run_ours(args, rank, world, local_rank):
             ph[key] += val / phase_steps
     kern = {}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    for m, (ms, nl, ncalls, xflops, path, drows) in acc_ms.items():
+    for m, (ms, nl, ncalls, xflops, path, drows, tile_s) in acc_ms.items():
         per_launch_s = ms / 1e3 / max(nl, 1)
         # algorithmic cell updates of one launch: a call's launches share the
         # call's pairs x the branches that run through the dense kernels (the
@@ -619,13 +620,15 @@ def run_ours(args, rank, world, local_rank):
                      f"{sm_max:.0f} MHz (one per update)")
             name = "k_stripe_gen<float,4,8,rsqrt>"
         else:
-            # 5 of 8 stripes: FMNMX + half an FADD2; 3 of 8: half an FADD2 + FADD.
-            # Either way 1.5 warp instructions per update at one instruction
-            # per clock per SMSP: 128 / 1.5 updates/clk/SM
+            # stripes 1, 3, 5, 7 of 8 in the abs form (an FSUB and an FADD of
+            # |d| per update, as f32x2 pairs), the others in the min form (an
+            # FMNMX on the ALU pipe and an FADD): 1.5 FP32 operations per update
+            # on the FMA pipe, whose 128 lanes per clock per SM bound the kernel
+            # at 128 / 1.5 updates/clk/SM (the ALU pipe's bound, 64 / 0.5, is higher)
             per_clk = FP32_LANES_PER_SM / 1.5
-            basis = (f"issue: {FP32_LANES_PER_SM} lanes/clk/SM / 1.5 instructions per update x "
+            basis = (f"FMA pipe: {FP32_LANES_PER_SM} FP32 lanes/clk/SM / 1.5 operations per update x "
                      f"{SMS} SMs x {sm_max:.0f} MHz")
-            name = "k_stripe_min<float,8,8>"
+            name = f"k_stripe_min<float,{tile_s // 16},8>"
         peak = per_clk * SMS * sm_max * 1e6 / 1e12
         ach = cells / per_launch_s / 1e12
         kern[m] = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tupdates/s",

@@ -146,8 +146,9 @@ typedef struct {
  *   "tensor_path"    1 (default): UF_UNWEIGHTED with UF_MIXED runs on the
  *                    tcgen05 tensor cores when the gram tiles its stripes need
  *                    (128 x 256 int64 cells each, the diagonal tiles included)
- *                    and the sparse rows' stripe cells fit in half the free
- *                    device memory, else on the CUDA-core stripe kernels
+ *                    and the sparse rows' stripe cells fit in half the device
+ *                    memory that is free or held unused by the stream-ordered
+ *                    pool, else on the CUDA-core stripe kernels
  *                    (report path 0); 0: always on the CUDA-core kernels
  *   "graph"          1 (default): a call's branch-block launch sequence is
  *                    captured into a CUDA graph and launched as one graph

@@ -129,6 +129,25 @@ void keep_pool_memory(int device) {
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// Device memory a call can use: free memory plus what the current device's
+// stream-ordered pool holds reserved but unused (freed buffers of earlier
+// calls stay reserved, keep_pool_memory, and are reused by the pool).
+double available_bytes() {
+  size_t free_b = 0, total_b = 0;
+  ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+  double avail = (double)free_b;
+  int device = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&device) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+      avail += (double)(reserved - used);
+  }
+  cudaGetLastError();
+  return avail;
+}
+
 // Phase timer: CUDA events recorded on the call's stream around each phase.
 struct PhaseTimer {
   bool on;
@@ -406,9 +425,7 @@ Inputs bind_inputs(uf_tree *tree, const BatchJob &J, int device, int64_t rows) {
 // Branch rows per embedding block for a working budget of per_row bytes a row
 // plus fixed bytes.
 int64_t block_rows(int64_t nb, double per_row, double fixed) {
-  size_t free_b = 0, total_b = 0;
-  ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-  const double budget = std::min(0.5 * (double)free_b - fixed, 24e9);
+  const double budget = std::min(0.5 * available_bytes() - fixed, 24e9);
   int64_t rows = (int64_t)(budget / per_row / 1.1);
   rows = std::max<int64_t>(std::min<int64_t>(rows, nb), std::min<int64_t>(nb, 256));
   if (g_branch_block.load() > 0) rows = std::min<int64_t>(g_branch_block.load(), std::max<int64_t>(nb, 1));
@@ -1224,9 +1241,7 @@ uf_status run_batch(uf_tree *tree, const BatchJob &J) {
     // half the free memory the CUDA-core stripe kernels take the call
     const GramPlan G = gram_plan(J);
     const double need = (double)G.n_tiles * GRAM_TILE_CELLS * 8.0 + (double)stripe_cells(J) * 8.0;
-    size_t free_b = 0, total_b = 0;
-    ck(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-    if (need <= 0.5 * (double)free_b) return run_gram(tree, J, device, scale);
+    if (need <= 0.5 * available_bytes()) return run_gram(tree, J, device, scale);
   }
   return run_stripes(tree, J, device, method, scale);
 }

@@ -45,9 +45,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "pair*branch updates/s"
+FOUR = ["unweighted", "weighted_unnormalized", "weighted_normalized", "generalized"]
 ALL_METHODS = [("unweighted", 1.0), ("weighted_unnormalized", 1.0), ("weighted_normalized", 1.0),
-               ("generalized", 0.5)]
-METHODS = list(ALL_METHODS)
+               ("generalized", 0.5), ("unweighted_unnormalized", 1.0), ("vaw_weighted_unnormalized", 1.0),
+               ("vaw_weighted_normalized", 1.0)]
+METHODS = [ma for ma in ALL_METHODS if ma[0] in FOUR]
 # CUDA-core FP32 lanes per SM and the SFU rate per SM on GB300 (sm_103): the
 # peaks of the ALU-bound accumulate kernels at the maximum SM clock (the SM
 # count is read from the device)
@@ -60,10 +62,9 @@ SMS = 152  # replaced by the device's multiprocessor count in run_ours
 WORKLOAD_DEFAULTS = {
     "yule500k_n113000": dict(methods=["unweighted", "weighted_normalized"], stripe_stop=8192, out_fp32=True,
                              fp64_stripes=64),
-    "yule300k_n25000": dict(methods=[m for m, _ in ALL_METHODS], stripe_stop=0, out_fp32=False,
-                            fp64_stripes=256),
-    "yule50k_n2048": dict(methods=[m for m, _ in ALL_METHODS], stripe_stop=0, out_fp32=False, fp64_stripes=0),
-    "yule1k_n64": dict(methods=[m for m, _ in ALL_METHODS], stripe_stop=0, out_fp32=False, fp64_stripes=0),
+    "yule300k_n25000": dict(methods=FOUR, stripe_stop=0, out_fp32=False, fp64_stripes=256),
+    "yule50k_n2048": dict(methods=FOUR, stripe_stop=0, out_fp32=False, fp64_stripes=0),
+    "yule1k_n64": dict(methods=FOUR, stripe_stop=0, out_fp32=False, fp64_stripes=0),
 }
 
 
@@ -619,6 +620,12 @@ def run_ours(args, rank, world, local_rank):
             basis = (f"SFU: {SFU_PER_SM} reciprocal square roots/clk/SM x {SMS} SMs x "
                      f"{sm_max:.0f} MHz (one per update)")
             name = "k_stripe_gen<float,4,8,rsqrt>"
+        elif m.startswith("vaw_"):
+            # the variance-adjusted weight: one SFU reciprocal square root per update
+            per_clk = SFU_PER_SM
+            basis = (f"SFU: {SFU_PER_SM} reciprocal square roots/clk/SM x {SMS} SMs x "
+                     f"{sm_max:.0f} MHz (one per update)")
+            name = "k_stripe_vaw<float,4,4>"
         else:
             # stripes 1, 3, 5, 7 of 8 in the abs form (an FSUB and an FADD of
             # |d| per update, as f32x2 pairs), the others in the min form (an
@@ -846,7 +853,8 @@ def main():
                          "default: per workload)")
     ap.add_argument("--no-err", action="store_true", help="skip the comparison of the mixed and FP64 results")
     ap.add_argument("--methods", default="default",
-                    help="comma list of methods per step, or all (default: the workload's methods)")
+                    help="comma list of methods per step (any of the seven), or all (the four base "
+                         "methods); default: the workload's methods")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-downstream", action="store_true",
@@ -871,7 +879,7 @@ def main():
         args.fp64_stripes = dflt["fp64_stripes"]
     args.out_fp32 = dflt["out_fp32"] if args.out_fp32 < 0 else bool(args.out_fp32)
     want = (dflt["methods"] if args.methods == "default" else
-            [m for m, _ in ALL_METHODS] if args.methods == "all" else args.methods.split(","))
+            FOUR if args.methods == "all" else args.methods.split(","))
     METHODS[:] = [ma for ma in ALL_METHODS if ma[0] in want]
     if not METHODS:
         ap.error(f"no known method in {args.methods!r}")

@@ -552,17 +552,47 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_vaw(const StripeArgs a) {
             *reinterpret_cast<uint4 *>(&v[pl][q * G::VEC]) =
                 *reinterpret_cast<const uint4 *>(vrow + swz<T>(w0 + q * G::VEC));
         }
+        if constexpr (sizeof(T) == 4) {
+          // pairs of cells per f32x2 instruction (the weight's reciprocal
+          // square roots stay scalar, on the SFU)
+          const float2 l2 = make_float2(l, l);
 #pragma unroll
-        for (int i = 0; i < RD; i++)
+          for (int i = 0; i < RD; i++)
 #pragma unroll
-          for (int j = 0; j < RK; j++) {
-            const T uu = u[0][j], vv = v[0][i + j + 1];
-            const T mv = u[1][j] + v[1][i + j + 1];  // the two samples' counts below the branch
-            const T rest = u[2][j] + v[2][i + j + 1];  // and the rest of their totals
-            const T w = l * vaw_weight<T>(mv * rest);
-            accd[i][j] = fma(uu + vv, w, accd[i][j]);
-            accn[i][j] = fma(fabs(uu - vv), w, accn[i][j]);
-          }
+            for (int j = 0; j < RK; j += 2) {
+              const float2 uu = make_float2(u[0][j], u[0][j + 1]);
+              const float2 vv = make_float2(v[0][i + j + 1], v[0][i + j + 2]);
+              // the two samples' counts below the branch, and the rest of their totals
+              const float2 mv = __fadd2_rn(make_float2(u[1][j], u[1][j + 1]),
+                                           make_float2(v[1][i + j + 1], v[1][i + j + 2]));
+              const float2 rest = __fadd2_rn(make_float2(u[2][j], u[2][j + 1]),
+                                             make_float2(v[2][i + j + 1], v[2][i + j + 2]));
+              const float2 prod = __fmul2_rn(mv, rest);
+              const float2 w = __fmul2_rn(l2, make_float2(vaw_weight<float>(prod.x), vaw_weight<float>(prod.y)));
+              const float2 s2 = __fadd2_rn(uu, vv);
+              const float2 d2 = fsub2(uu, vv);
+              float2 ad = make_float2(accd[i][j], accd[i][j + 1]);
+              float2 an = make_float2(accn[i][j], accn[i][j + 1]);
+              ad = __ffma2_rn(s2, w, ad);
+              an = __ffma2_rn(make_float2(fabsf(d2.x), fabsf(d2.y)), w, an);
+              accd[i][j] = ad.x;
+              accd[i][j + 1] = ad.y;
+              accn[i][j] = an.x;
+              accn[i][j + 1] = an.y;
+            }
+        } else {
+#pragma unroll
+          for (int i = 0; i < RD; i++)
+#pragma unroll
+            for (int j = 0; j < RK; j++) {
+              const T uu = u[0][j], vv = v[0][i + j + 1];
+              const T mv = u[1][j] + v[1][i + j + 1];  // the two samples' counts below the branch
+              const T rest = u[2][j] + v[2][i + j + 1];  // and the rest of their totals
+              const T w = l * vaw_weight<T>(mv * rest);
+              accd[i][j] = fma(uu + vv, w, accd[i][j]);
+              accn[i][j] = fma(fabs(uu - vv), w, accn[i][j]);
+            }
+        }
       }
       in_sub += G::RB;
       if (in_sub >= B1 || it == nst - 1) {

@@ -55,6 +55,9 @@ struct TabDesc {
   int m_lo, m_hi;     // stripe tiles covering them
   int n_ktiles;       // sample tiles
   int tile0;          // first tile of this table in the batch's tile numbering
+  int kband;          // unit order: bands of kband sample tiles, every stripe tile of a band
+                      // before the next band (sample tile fastest within it), so that the
+                      // rows' columns a band reads stay in L2
   int64_t x_col;      // first column of its segment in an embedding row
   int64_t m_off;      // first cell of its stripe accumulator
 };

@@ -232,6 +232,7 @@ uf_status compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method 
   tab.m_hi = m_hi;
   tab.n_ktiles = (n + tile_k - 1) / tile_k;
   tab.tile0 = 0;
+  tab.kband = tab.n_ktiles;  // sample tile fastest over the whole table
   tab.x_col = 0;
   tab.m_off = 0;
   UF_TRY(h2d(p[18], &tab, sizeof tab));

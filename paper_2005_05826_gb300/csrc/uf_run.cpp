@@ -983,6 +983,20 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   DevBuf M2, Dg, diag_tmp, counter(sizeof(int), st, "alloc counter");
   DevBuf clamps(sizeof(unsigned long long), st, "alloc clamp counter");
   DevBuf total((size_t)n_cols * 8, st, "alloc totals"), inv_total((size_t)n_cols * 4, st, "alloc totals");
+  // unit order per table and shape: bands of sample tiles whose columns (their
+  // u windows and every stripe tile's partner windows) for the rows of a work
+  // unit fit in a third of L2, all stripe tiles of a band before the next;
+  // without such a band, sample tile fastest over the whole table
+  {
+    const double l2_budget = 40e6, rows_u = (double)std::min<int64_t>(xrows, 8192) * (double)es * planes;
+    for (size_t sh = 0; sh < shape_tabs.size(); sh++)
+      for (TabDesc &d : shape_tabs[sh]) {
+        const double cols = l2_budget / rows_u - (double)(d.m_hi - d.m_lo + 1) * shape_ts[sh];
+        const int kb = (int)std::floor(cols / (2.0 * shape_tk[sh]));
+        d.kband = kb >= 1 ? std::min(kb, d.n_ktiles) : d.n_ktiles;
+      }
+    tabs = shape_tabs[0];
+  }
   // table descriptors and row lists: one staged upload
   Meta meta;
   const size_t o_tabs = meta.add(tabs);

@@ -140,7 +140,12 @@ __device__ __forceinline__ bool next_unit(const StripeArgs &a, int tile_s, int t
   const int c = id / a.n_tiles, tt = id - c * a.n_tiles;
   const TabDesc &tb = a.tabs[a.n_tabs == 1 ? 0 : table_of_tile(a.tabs, a.n_tabs, tt)];
   const int t = tt - tb.tile0;
-  const int kt = t % tb.n_ktiles, st = t / tb.n_ktiles;
+  // bands of kband sample tiles: all stripe tiles of a band, then the next band
+  const int n_st = tb.m_hi - tb.m_lo + 1;
+  const int kb = max(1, min(tb.kband, tb.n_ktiles));
+  const int band = t / (kb * n_st), within = t - band * (kb * n_st);
+  const int width = min(kb, tb.n_ktiles - band * kb);
+  const int kt = band * kb + within % width, st = within / width;
   u->r0 = c * a.chunk;
   u->r1 = min(a.rows, u->r0 + a.chunk);
   u->k0 = kt * tile_k;

@@ -554,7 +554,7 @@ struct SparseScatter {
   int64_t n_sparse_rows = 0, cells = 0, n_cols = 0;
   std::vector<int64_t> sp_off;  // first entry of each capacity class in the sparse list
   size_t o_sparse = 0, o_sptabs = 0, o_lofs = 0;
-  DevBuf le, lk, lz, Dsp, cur, nxt, rnext;
+  DevBuf le, lk, lz, Dsp, cur;
   int64_t list_entries = 0;
   std::vector<SpLayout> lay;
 
@@ -588,8 +588,6 @@ struct SparseScatter {
       le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries), st, "alloc sparse lists");
       lk = DevBuf(total_e * 4, st, "alloc sparse lists");
       cur = DevBuf(total_e * 8, st, "alloc sparse list cursors");
-      nxt = DevBuf(total_e * 4, st, "alloc sparse list cursors");
-      rnext = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse list cursors");
       lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
       // rows without entries in the table return before writing their count
       ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
@@ -635,8 +633,6 @@ struct SparseScatter {
       base.lz = lz.as<int>();
       base.cur = cur.as<int>();
       base.cur_stride = list_entries;
-      base.nxt = nxt.as<int>();
-      base.rnext = rnext.as<int>();
     }
     for (size_t c = 0; c < split->sparse.size(); c++) {
       if (split->sparse[c].empty()) continue;

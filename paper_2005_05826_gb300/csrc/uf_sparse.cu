@@ -378,9 +378,6 @@ __device__ __forceinline__ int lower_index(const int *K, int lo, int hi, int key
 template <typename T, int ACC, int MODE>
 __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   const int row = blockIdx.x;
-  // the first stripe at which this row has a pair left (set by the region
-  // that last visited it): rows with nothing in this region return at once
-  if (!a.first_region && a.rnext[row] > a.r1 - 1) return;
   const int v = a.nodes[row];
   const SpTab tb = a.tabs[0];
   const int64_t off = a.lofs[row];
@@ -407,17 +404,7 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   // window where the previous region stopped, and only the first region of a
   // call searches for it.
   int *cur1 = a.cur + off, *cur2 = a.cur + a.cur_stride + off;
-  int *nxt = a.nxt + off;  // per entry: the first stripe at which it has a partner left
-  constexpr int NONE = 0x7fffffff;
-  int row_next = NONE;
   for (int ia = threadIdx.x; ia < z - 1; ia += blockDim.x) {
-    if (!a.first_region) {
-      const int ne = nxt[ia];
-      if (ne > a.r1 - 1) {  // no partner in this region
-        row_next = min(row_next, ne);
-        continue;
-      }
-    }
     const SpEnt<T> ea = E[ia];
     // window 1: d = k_b - k_a in [r0 + 1, min(r1, n/2)], stripe d - 1, cell column k_a
     {
@@ -436,28 +423,6 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
         for (; e > ia + 1 && K[e - 1] >= ea.k + dlo; e--) add_pair<T, ACC, MODE>(ea, E[e - 1], c);
       cur2[ia] = e;
     }
-    // the entry's next stripe with a partner: window 1 at d <= n/2 (stripe d - 1),
-    // window 2 at d > n/2 (stripe n - d - 1); both grow from region to region
-    int ne = NONE;
-    {
-      const int b = cur1[ia];
-      if (b < z && K[b] - ea.k <= half) ne = K[b] - ea.k - 1;
-      const int e = cur2[ia];
-      if (e - 1 > ia && K[e - 1] - ea.k >= half + 1) ne = min(ne, n - (K[e - 1] - ea.k) - 1);
-    }
-    nxt[ia] = ne;
-    row_next = min(row_next, ne);
-  }
-  // the row's next stripe with a pair: the smallest over its entries
-  __shared__ int s_next[4];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) row_next = min(row_next, __shfl_xor_sync(0xffffffffu, row_next, o));
-  if ((threadIdx.x & 31) == 0) s_next[threadIdx.x >> 5] = row_next;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int m = s_next[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = min(m, s_next[w]);
-    a.rnext[row] = m;
   }
 }
 

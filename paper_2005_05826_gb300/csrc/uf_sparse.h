@@ -52,8 +52,6 @@ struct SparseArgs {
   int first_region;         // 1: the call's first region (cursors are searched, not read)
   int *cur;                 // two cursors per list entry: window 1 at cur[e], window 2 at
   int64_t cur_stride;       // cur[cur_stride + e] (regions must come in increasing order)
-  int *nxt;                 // per list entry: the first stripe at which it has a partner left
-  int *rnext;               // per listed row: the smallest of its entries' nxt
 };
 // largest subtree entry count a sparse row may have: scattered directly from
 // shared memory, or written as a list (one table, keys alone in shared memory)
@@ -67,10 +65,8 @@ cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStr
 // launch, table tabs[0]) whose stripe lies in [a.r0, a.r1): one CTA per row,
 // each thread takes samples a and walks the partners b of the two windows of
 // k_b - k_a that map into the region from per-entry cursors (set by binary
-// search in the first region); entries, and whole rows, whose next partner
-// lies in a later region are skipped after one load.  Run region by region,
-// in increasing stripe order, so that the accumulator cells a launch touches
-// stay in L2.
+// search in the first region).  Run region by region, in increasing stripe
+// order, so that the accumulator cells a launch touches stay in L2.
 cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 
 }  // namespace ufg

@@ -100,7 +100,10 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
           const double pr = (double)ub * (double)(ub - 1) / 2.0;
           pairs += pr;
           cost += job_cost + pr * pair_cost[t] + (double)ub * entry_cost[t];
-          if (regions) cost += n_regions * (job_cost + (double)ub * 4e-11);  // one visit per region
+          // one visit per region: a CTA, and each entry's cursors walked to the
+          // region (about 7e-12 s per entry and region measured on GB300 with a
+          // 113,000-sample table; pairs at 4.3e-12 s)
+          if (regions) cost += n_regions * (job_cost + (double)ub * 1e-11);
         }
         if (mx > max_entries) continue;
         if (mode == 2 || cost < dense_t) {

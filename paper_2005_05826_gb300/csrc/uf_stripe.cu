@@ -460,6 +460,12 @@ struct GeoV {
   static constexpr int UCH = UW / VEC, VCH = VW / VEC, CH = UCH + VCH;
   static constexpr int NV = (RD + RK + VEC - 1) / VEC;
   static constexpr size_t SMEM = (size_t)NSTAGE * STAGE * sizeof(T) + (size_t)2 * RD * RK * NT * sizeof(T);
+  // Shared-memory position of row element `elem`.  A quarter-warp reads eight
+  // 16-byte chunks: consecutive ones for FP32 (RK = 4 floats per chunk), which
+  // hit eight distinct bank groups unswizzled (the swizzle of the 8 x 8 tile
+  // would put two of them on one group whenever the run starts at an odd
+  // chunk); every second one for FP64, which the swizzle spreads.
+  static __device__ __forceinline__ int at(int elem) { return sizeof(T) == 4 ? elem : swz<T>(elem); }
 };
 
 template <typename T, int RD, int RK>
@@ -475,11 +481,11 @@ __device__ __forceinline__ void load_stage_vaw(T *stage, const StripeArgs &a, in
     T *dst;
     int64_t src;
     if (q < G::UCH) {
-      dst = row + swz<T>(q * G::VEC);
+      dst = row + G::at(q * G::VEC);
       src = ucol + q * G::VEC;
     } else {
       const int qv = q - G::UCH;
-      dst = row + G::UW + swz<T>(qv * G::VEC);
+      dst = row + G::UW + G::at(qv * G::VEC);
       src = vcol + qv * G::VEC;
     }
     if (e < e_end) {
@@ -551,11 +557,11 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_vaw(const StripeArgs a) {
 #pragma unroll
           for (int q = 0; q < RK / G::VEC; q++)
             *reinterpret_cast<uint4 *>(&u[pl][q * G::VEC]) =
-                *reinterpret_cast<const uint4 *>(urow + swz<T>(RK * tk + q * G::VEC));
+                *reinterpret_cast<const uint4 *>(urow + G::at(RK * tk + q * G::VEC));
 #pragma unroll
           for (int q = 0; q < G::NV; q++)
             *reinterpret_cast<uint4 *>(&v[pl][q * G::VEC]) =
-                *reinterpret_cast<const uint4 *>(vrow + swz<T>(w0 + q * G::VEC));
+                *reinterpret_cast<const uint4 *>(vrow + G::at(w0 + q * G::VEC));
         }
         if constexpr (sizeof(T) == 4) {
           // pairs of cells per f32x2 instruction (the weight's reciprocal

@@ -180,15 +180,17 @@ __global__ void k_emb_rows(int64_t b0, const int32_t *__restrict__ nodes,
 }
 
 // Variance-adjusted rows: three planes per row r, each `pitch` elements:
-// p = c / T, the count c below the branch and T - c, with the same
-// wrap-padded columns as k_emb_rows.
+// l p = l c / T (the branch length folded in, as it multiplies both sums),
+// the count c below the branch and T - c, with the same wrap-padded columns
+// as k_emb_rows.
 template <typename T>
 __global__ void k_emb_rows_vaw(const int32_t *__restrict__ nodes, const int32_t *__restrict__ slot_of_node,
-                               const double *__restrict__ counts, int64_t ld, const double *__restrict__ total,
-                               const float *__restrict__ inv_total_f, T *__restrict__ X, int64_t pitch,
-                               const TabDesc *__restrict__ tabs, int n_tabs) {
+                               const double *__restrict__ counts, int64_t ld, const double *__restrict__ length,
+                               const double *__restrict__ total, const float *__restrict__ inv_total_f,
+                               T *__restrict__ X, int64_t pitch, const TabDesc *__restrict__ tabs, int n_tabs) {
   const int64_t v = nodes[blockIdx.x];
   const double *c = counts + (int64_t)slot_of_node[v] * ld;
+  const double l = length[v];
   T *x = X + (int64_t)blockIdx.x * 3 * pitch;
   for (int64_t j = threadIdx.x; j < pitch; j += blockDim.x) {
     const TabDesc &tb = tabs[n_tabs == 1 ? 0 : segment_of(tabs, n_tabs, j)];
@@ -196,8 +198,10 @@ __global__ void k_emb_rows_vaw(const int32_t *__restrict__ nodes, const int32_t 
     while (k >= tb.n) k -= tb.n;
     k += tb.off;
     const double ck = c[k], tk = total[k];
-    if constexpr (sizeof(T) == 4) x[j] = (float)ck * inv_total_f[k];
-    else x[j] = ck / tk;
+    // FP32 rows use the FP32 reciprocal of the total (an FP64 division per
+    // value costs more than the whole FP32 kernel saves)
+    if constexpr (sizeof(T) == 4) x[j] = (float)l * ((float)ck * inv_total_f[k]);
+    else x[j] = l * (ck / tk);
     x[pitch + j] = (T)ck;
     x[2 * pitch + j] = (T)(tk - ck);
   }
@@ -252,10 +256,10 @@ cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
   if (kind == EMB_VAW) {
     if (!nodes) return cudaErrorInvalidValue;
     if (fp32)
-      return launch_k(k_emb_rows_vaw<float>, dim3(rows), dim3(256), 0, st, nodes, slot_of_node, counts, ld, total,
-                      inv_total_f, (float *)X, pitch, tabs, n_tabs);
-    return launch_k(k_emb_rows_vaw<double>, dim3(rows), dim3(256), 0, st, nodes, slot_of_node, counts, ld, total,
-                    inv_total_f, (double *)X, pitch, tabs, n_tabs);
+      return launch_k(k_emb_rows_vaw<float>, dim3(rows), dim3(256), 0, st, nodes, slot_of_node, counts, ld, length,
+                      total, inv_total_f, (float *)X, pitch, tabs, n_tabs);
+    return launch_k(k_emb_rows_vaw<double>, dim3(rows), dim3(256), 0, st, nodes, slot_of_node, counts, ld, length,
+                    total, inv_total_f, (double *)X, pitch, tabs, n_tabs);
   }
 #define UF_EMB(T, K)                                                                                 \
   return launch_k(k_emb_rows<T, K>, dim3(rows), dim3(256), 0, st, b0, nodes, slot_of_node, counts, ld, length, \

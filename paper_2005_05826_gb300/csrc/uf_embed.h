@@ -29,7 +29,7 @@ cudaError_t launch_node_counts(const int32_t *nodes, int n_list, const int32_t *
                                double *counts, int64_t ld, cudaStream_t st, int64_t n_used = -1);
 // Embedding rows of branches nodes[0 .. rows) (b0 .. b0 + rows - 1 when
 // nodes is null) for every table segment; EMB_VAW rows hold three planes of
-// `pitch` elements each (a node list is required).
+// `pitch` elements each, l p, c and T - c (a node list is required).
 cudaError_t launch_emb_rows(int kind, bool fp32, int64_t b0, int rows,
                             const int32_t *slot_of_node, const double *counts, int64_t ld,
                             const double *length, const double *total, const float *inv_total_f,

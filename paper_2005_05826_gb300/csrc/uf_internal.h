@@ -32,7 +32,7 @@ enum EmbKind : int {
   EMB_PRESENCE = 1,  // l_v * [count > 0]: unweighted
   EMB_PROP = 2,      // p(v): generalized (the length is applied in the kernel)
   EMB_VAW = 3,       // variance-adjusted weighted: three planes per row, each `pitch`
-                     // elements, p(v), the count c(v) below v and T - c(v)
+                     // elements, l_v * p(v), the count c(v) below v and T - c(v)
 };
 
 // which quantity the accumulator holds

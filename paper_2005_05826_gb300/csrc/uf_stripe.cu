@@ -442,9 +442,9 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_gen(const StripeArgs a) {
 }
 
 // ---- variance-adjusted weighted (Chang, Luan & Sun 2011):
-//      den += l w (u + v), N += l w |u - v|, w = 1 / sqrt((c_k + c_j)(r_k + r_j))
-//      with c the counts below the branch and r = T - c, and w = 0 where either
-//      factor is 0 ----
+//      den += w (u + v), N += w |u - v|, w = 1 / sqrt((c_k + c_j)(r_k + r_j))
+//      with u = l p the length-scaled proportions, c the counts below the
+//      branch and r = T - c, and w = 0 where either factor is 0 ----
 // Rows hold three planes (u, c, r) of `pitch` elements each.  A stage carries
 // RB rows of all three planes; the micro-tile is RD x RK with two
 // accumulators per cell.
@@ -456,7 +456,7 @@ struct GeoV {
   static constexpr int TS = 16 * RD, TK = 16 * RK;
   static constexpr int VEC = 16 / sizeof(T);
   static constexpr int UW = TK, VW = TK + TS, ROW = UW + VW;
-  static constexpr int STAGE = RB * NPL * ROW + RB;
+  static constexpr int STAGE = RB * NPL * ROW;  // rows past the unit are zero (w = 0)
   static constexpr int UCH = UW / VEC, VCH = VW / VEC, CH = UCH + VCH;
   static constexpr int NV = (RD + RK + VEC - 1) / VEC;
   static constexpr size_t SMEM = (size_t)NSTAGE * STAGE * sizeof(T) + (size_t)2 * RD * RK * NT * sizeof(T);
@@ -494,10 +494,6 @@ __device__ __forceinline__ void load_stage_vaw(T *stage, const StripeArgs &a, in
 #pragma unroll
       for (int i = 0; i < G::VEC; i++) dst[i] = T(0);
     }
-  }
-  if (threadIdx.x < G::RB) {
-    const int e = e0 + threadIdx.x;
-    stage[G::RB * G::NPL * G::ROW + threadIdx.x] = e < e_end ? (T)a.len[e] : T(0);
   }
 }
 
@@ -548,7 +544,6 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_vaw(const StripeArgs a) {
       const T *stage = stg + (it % G::NSTAGE) * G::STAGE;
 #pragma unroll 1
       for (int r = 0; r < G::RB; r++) {
-        const T l = stage[G::RB * G::NPL * G::ROW + r];
         T u[3][RK], v[3][G::NV * G::VEC];
 #pragma unroll
         for (int pl = 0; pl < 3; pl++) {
@@ -566,7 +561,6 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_vaw(const StripeArgs a) {
         if constexpr (sizeof(T) == 4) {
           // pairs of cells per f32x2 instruction (the weight's reciprocal
           // square roots stay scalar, on the SFU)
-          const float2 l2 = make_float2(l, l);
 #pragma unroll
           for (int i = 0; i < RD; i++)
 #pragma unroll
@@ -579,7 +573,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_vaw(const StripeArgs a) {
               const float2 rest = __fadd2_rn(make_float2(u[2][j], u[2][j + 1]),
                                              make_float2(v[2][i + j + 1], v[2][i + j + 2]));
               const float2 prod = __fmul2_rn(mv, rest);
-              const float2 w = __fmul2_rn(l2, make_float2(vaw_weight<float>(prod.x), vaw_weight<float>(prod.y)));
+              const float2 w = make_float2(vaw_weight<float>(prod.x), vaw_weight<float>(prod.y));
               const float2 s2 = __fadd2_rn(uu, vv);
               const float2 d2 = fsub2(uu, vv);
               float2 ad = make_float2(accd[i][j], accd[i][j + 1]);
@@ -599,7 +593,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stripe_vaw(const StripeArgs a) {
               const T uu = u[0][j], vv = v[0][i + j + 1];
               const T mv = u[1][j] + v[1][i + j + 1];  // the two samples' counts below the branch
               const T rest = u[2][j] + v[2][i + j + 1];  // and the rest of their totals
-              const T w = l * vaw_weight<T>(mv * rest);
+              const T w = vaw_weight<T>(mv * rest);
               accd[i][j] = fma(uu + vv, w, accd[i][j]);
               accn[i][j] = fma(fabs(uu - vv), w, accn[i][j]);
             }

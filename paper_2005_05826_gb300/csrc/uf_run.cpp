@@ -549,11 +549,13 @@ struct SpLayout {
 struct SparseScatter {
   const RowSplit *split = nullptr;
   bool region_mode = false;
+  bool fused = false;     // min-form lists carrying member rows (launch_sparse_region)
   bool two_word = false;  // FP64 terms in two words (second words after the first)
   int n_acc = 1;
   int64_t n_sparse_rows = 0, cells = 0, n_cols = 0;
   std::vector<int64_t> sp_off;  // first entry of each capacity class in the sparse list
-  size_t o_sparse = 0, o_sptabs = 0, o_lofs = 0;
+  std::vector<int64_t> cls_n;   // rows of each class that are launched
+  size_t o_sparse = 0, o_sptabs = 0, o_lofs = 0, o_members = 0;
   DevBuf le, lk, lz, Dsp, cur;
   int64_t list_entries = 0;
   std::vector<SpLayout> lay;
@@ -572,10 +574,43 @@ struct SparseScatter {
     if (sp.n_sparse == 0) return;
     const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc * (two_word ? 2 : 1));
     region_mode = n_regions > 1 || sp.lists;
-    std::vector<int32_t> all;
-    for (const auto &c : sp.sparse) {
-      sp_off.push_back((int64_t)all.size());
-      all.insert(all.end(), c.begin(), c.end());
+    fused = region_mode && acc == ACC_MIN;
+    std::vector<int32_t> all, members;
+    if (fused) {
+      // A sparse branch whose parent is a listed head rides in the parent's
+      // list (up to SPARSE_FUSE_MEMBERS per head): its samples are among the
+      // parent's and its pairs among the parent's pairs.  Parents come before
+      // children in decreasing node order (parent[v] > v), so every head is
+      // final when its children are visited; a member's children are heads.
+      constexpr int F = SPARSE_FUSE_MEMBERS;
+      const int64_t nn = tree->n_nodes;
+      std::vector<int8_t> role(nn, 0), used(nn, 0);  // role 1: head, 2: member
+      std::vector<int32_t> mem_of((size_t)nn * F, -1);
+      for (const auto &c : sp.sparse)
+        for (int32_t v : c) role[v] = 1;
+      for (int64_t v = nn - 2; v >= 0; v--) {
+        if (role[v] != 1) continue;
+        const int64_t p = tree->parent[v];
+        if (p >= 0 && role[p] == 1 && used[p] < F) {
+          mem_of[(size_t)p * F + used[p]++] = (int32_t)v;
+          role[v] = 2;
+        }
+      }
+      for (const auto &c : sp.sparse) {
+        sp_off.push_back((int64_t)all.size());
+        for (int32_t v : c)
+          if (role[v] == 1) {
+            all.push_back(v);
+            members.insert(members.end(), mem_of.begin() + (size_t)v * F, mem_of.begin() + (size_t)v * F + F);
+          }
+        cls_n.push_back((int64_t)all.size() - sp_off.back());
+      }
+    } else {
+      for (const auto &c : sp.sparse) {
+        sp_off.push_back((int64_t)all.size());
+        all.insert(all.end(), c.begin(), c.end());
+        cls_n.push_back((int64_t)c.size());
+      }
     }
     n_sparse_rows = (int64_t)all.size();
     if (region_mode) {
@@ -585,13 +620,14 @@ struct SparseScatter {
         lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
       const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
       list_entries = (int64_t)total_e;
-      le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries), st, "alloc sparse lists");
+      le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries, fused), st, "alloc sparse lists");
       lk = DevBuf(total_e * 4, st, "alloc sparse lists");
       cur = DevBuf(total_e * 8, st, "alloc sparse list cursors");
       lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
       // rows without entries in the table return before writing their count
       ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
       o_lofs = meta.add(lofs);
+      if (fused) o_members = meta.add(members);
     }
     std::vector<SpTab> tabs(nt);
     for (size_t t = 0; t < nt; t++) {
@@ -633,13 +669,15 @@ struct SparseScatter {
       base.lz = lz.as<int>();
       base.cur = cur.as<int>();
       base.cur_stride = list_entries;
+      base.fused = fused ? 1 : 0;
+      base.members = fused ? meta.at<int32_t>(o_members) : nullptr;
     }
     for (size_t c = 0; c < split->sparse.size(); c++) {
-      if (split->sparse[c].empty()) continue;
+      if (cls_n[c] == 0) continue;
       SparseArgs sp = base;
       sp.row_base = (int)sp_off[c];
       sp.nodes = meta.at<int32_t>(o_sparse) + sp_off[c];
-      sp.n_nodes = (int)split->sparse[c].size();
+      sp.n_nodes = (int)cls_n[c];
       sp.cap = split->cap[c];
       if (region_mode) ck(launch_sparse_lists(acc, f32, sp, on), "sparse lists");
       else ck(launch_sparse_rows(acc, f32, sp, on), "sparse rows");

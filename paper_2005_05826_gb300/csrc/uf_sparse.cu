@@ -36,6 +36,7 @@
 // numbering and adds each pair to its stripe cell with one atomic per
 // accumulator (two when the pair is the duplicated half stripe of an even n).
 #include <cmath>
+#include <type_traits>
 
 #include "uf_device.cuh"
 #include "uf_sparse.h"
@@ -126,6 +127,28 @@ __device__ __forceinline__ void set_f(SpEnt<double> &e, Fx2 v) {
   e.f_lo = v.lo;
 }
 
+// One distinct sample of a fused list (min form): the fixed-point terms of
+// the listed row and of its members (0 where the sample is not below the
+// member); its sample is in the list's separate key array.
+constexpr int FUSE_ROWS = 1 + SPARSE_FUSE_MEMBERS;
+template <typename T>
+struct FuEnt;
+template <>
+struct alignas(8) FuEnt<float> {
+  long long f[FUSE_ROWS];
+};
+template <>
+struct alignas(16) FuEnt<double> {
+  long long f[FUSE_ROWS], f_lo[FUSE_ROWS];
+};
+__device__ __forceinline__ Fx2 fu_f(const FuEnt<float> &e, int r) { return Fx2{e.f[r], 0}; }
+__device__ __forceinline__ Fx2 fu_f(const FuEnt<double> &e, int r) { return Fx2{e.f[r], e.f_lo[r]}; }
+__device__ __forceinline__ void fu_set(FuEnt<float> &e, int r, Fx2 v) { e.f[r] = v.hi; }
+__device__ __forceinline__ void fu_set(FuEnt<double> &e, int r, Fx2 v) {
+  e.f[r] = v.hi;
+  e.f_lo[r] = v.lo;
+}
+
 // What a pair update needs besides its two entries.
 template <typename T>
 struct PairCtx {
@@ -177,6 +200,32 @@ __device__ __forceinline__ void add_pair(const SpEnt<T> &ea, const SpEnt<T> &eb,
       red_add2<T>(c.M2 + cell + d, c.m_lo_off, t2);
     }
   }
+}
+
+// The pair (a, b), k_a < k_b, of a fused list: the sum over the listed row
+// and its members of min(X_a, X_b) (a member without one of the samples
+// adds 0), -2 times that in an abs-form stripe; the same integers as the
+// rows' separate pair updates, in one atomic per word.
+template <typename T>
+__device__ __forceinline__ void add_pair_fused(int ka, int kb, const FuEnt<T> &ea, const FuEnt<T> &eb,
+                                               const PairCtx<T> &c) {
+  const int d = kb - ka;
+  int s, kc;
+  if (2 * d <= c.n) {
+    s = d - 1;
+    kc = ka;
+  } else {
+    s = c.n - d - 1;
+    kc = kb;
+  }
+  if (s < c.s_lo || s > c.s_hi) return;
+  const int64_t cell = (int64_t)(s - c.s_lo) * c.n + kc;
+  Fx2 t = fx_min(fu_f(ea, 0), fu_f(eb, 0));
+#pragma unroll
+  for (int r = 1; r < FUSE_ROWS; r++) t = fx_add(t, fx_min(fu_f(ea, r), fu_f(eb, r)));
+  if (abs_row(c.abs_mask, s)) t = fx_mul(t, -2);
+  red_add2<T>(c.M + cell, c.m_lo_off, t);
+  if (2 * d == c.n) red_add2<T>(c.M + cell + d, c.m_lo_off, t);
 }
 
 template <typename T, int ACC, int MODE>
@@ -341,6 +390,58 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
   const T alpha = (T)a.alpha;
   const int64_t off = a.lofs[row];
   SpEnt<T> *le = reinterpret_cast<SpEnt<T> *>(a.le);
+  if (ACC == ACC_MIN && a.fused) {
+    // The members' tips are sub-ranges of this row's tips, so their count
+    // entries are sub-runs [mlo, mhi) of its run: each distinct sample's
+    // count under a member sums the same entries in the same order as the
+    // member's own list would.
+    int mlo[SPARSE_FUSE_MEMBERS], mhi[SPARSE_FUSE_MEMBERS];
+    double ml[SPARSE_FUSE_MEMBERS];
+#pragma unroll
+    for (int j = 0; j < SPARSE_FUSE_MEMBERS; j++) {
+      const int mv = a.members[(int64_t)SPARSE_FUSE_MEMBERS * row + j];
+      mlo[j] = mv >= 0 ? (int)(tb.col_ptr[a.tip_lo[mv]] - q0) : 0;
+      mhi[j] = mv >= 0 ? (int)(tb.col_ptr[a.tip_hi[mv]] - q0) : 0;
+      ml[j] = mv >= 0 ? a.length[mv] : 0.0;
+    }
+    FuEnt<T> *lf = reinterpret_cast<FuEnt<T> *>(a.le);
+    for (int i = i0; i < i1; i++) {
+      const unsigned smp = (unsigned)(key[i] >> 32);
+      if (i > 0 && (unsigned)(key[i - 1] >> 32) == smp) continue;
+      double c = 0.0, cm[SPARSE_FUSE_MEMBERS];
+#pragma unroll
+      for (int j = 0; j < SPARSE_FUSE_MEMBERS; j++) cm[j] = 0.0;
+      for (int m = i; m < L && (unsigned)(key[m] >> 32) == smp; m++) {
+        const int e = (int)(key[m] & 0xffffffffu);
+        const double val = tb.col_val[q0 + e];
+        c += val;
+#pragma unroll
+        for (int j = 0; j < SPARSE_FUSE_MEMBERS; j++)
+          if (e >= mlo[j] && e < mhi[j]) cm[j] += val;
+      }
+      auto term = [&](double cnt, double len) -> Fx2 {
+        const T x = a.kind == EMB_SCALED
+                        ? emb_value<T, EMB_SCALED>(cnt, len, tb.total[smp], tb.inv_total_f[smp])
+                        : emb_value<T, EMB_PRESENCE>(cnt, len, tb.total[smp], tb.inv_total_f[smp]);
+        return to_fixed2(x, a.scale);
+      };
+      FuEnt<T> fe;
+      Fx2 f = term(c, l), dsum = f;
+      fu_set(fe, 0, f);
+#pragma unroll
+      for (int j = 0; j < SPARSE_FUSE_MEMBERS; j++) {
+        const Fx2 fm = term(cm[j], ml[j]);
+        fu_set(fe, 1 + j, fm);
+        dsum = fx_add(dsum, fm);
+      }
+      lf[off + u] = fe;
+      a.lk[off + u] = (int)smp;
+      red_add2<T>(a.Dsp + tb.off + smp, a.d_lo_off, dsum);
+      u++;
+    }
+    if (tid == 0) a.lz[row] = z;
+    return;
+  }
   for (int i = i0; i < i1; i++) {
     const unsigned smp = (unsigned)(key[i] >> 32);
     if (i > 0 && (unsigned)(key[i - 1] >> 32) == smp) continue;
@@ -375,15 +476,15 @@ __device__ __forceinline__ int lower_index(const int *K, int lo, int hi, int key
   return lo;
 }
 
-template <typename T, int ACC, int MODE>
+template <typename T, int ACC, int MODE, bool FUSED = false>
 __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
+  using Ent = std::conditional_t<FUSED, FuEnt<T>, SpEnt<T>>;
   const int row = blockIdx.x;
-  const int v = a.nodes[row];
   const SpTab tb = a.tabs[0];
   const int64_t off = a.lofs[row];
   // never past the row's list capacity
   const int z = (int)min((int64_t)a.lz[row], a.lofs[row + 1] - off);
-  const SpEnt<T> *E = reinterpret_cast<const SpEnt<T> *>(a.le) + off;
+  const Ent *E = reinterpret_cast<const Ent *>(a.le) + off;
   const int *K = a.lk + off;  // the same entries' samples, for the searches
   const int n = tb.n, half = n / 2;
   PairCtx<T> c;
@@ -395,7 +496,7 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   c.m_lo_off = a.m_lo_off;
   c.M = a.M + tb.m_off;
   c.M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
-  c.lt = (T)a.length[v];
+  c.lt = ACC == ACC_GEN ? (T)a.length[a.nodes[row]] : T(0);
   c.am1 = (T)(a.alpha - 1.0);
   c.scale = a.scale;
   // Regions come in increasing stripe order (r0 of one is r1 of the one
@@ -404,23 +505,30 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   // window where the previous region stopped, and only the first region of a
   // call searches for it.
   int *cur1 = a.cur + off, *cur2 = a.cur + a.cur_stride + off;
+  auto add = [&](const Ent &ea, int ka, int b, int kb) {
+    if constexpr (FUSED) add_pair_fused<T>(ka, kb, ea, E[b], c);
+    else add_pair<T, ACC, MODE>(ea, E[b], c);
+  };
   for (int ia = threadIdx.x; ia < z - 1; ia += blockDim.x) {
-    const SpEnt<T> ea = E[ia];
+    const Ent ea = E[ia];
+    int ka;
+    if constexpr (FUSED) ka = K[ia];
+    else ka = ea.k;
     // window 1: d = k_b - k_a in [r0 + 1, min(r1, n/2)], stripe d - 1, cell column k_a
     {
       const int dlo = a.r0 + 1, dhi = min(a.r1, half);
-      int b = a.first_region ? lower_index(K, ia + 1, z, ea.k + dlo) : cur1[ia];
+      int b = a.first_region ? lower_index(K, ia + 1, z, ka + dlo) : cur1[ia];
       if (dlo <= dhi)
-        for (; b < z && K[b] <= ea.k + dhi; b++) add_pair<T, ACC, MODE>(ea, E[b], c);
+        for (int kb; b < z && (kb = K[b]) <= ka + dhi; b++) add(ea, ka, b, kb);
       cur1[ia] = b;
     }
     // window 2: d in [max(n - r1, n/2 + 1), n - r0 - 1], stripe n - d - 1, column k_b;
     // the cursor is one past the last partner not yet added
     {
       const int dlo = max(n - a.r1, half + 1), dhi = n - a.r0 - 1;
-      int e = a.first_region ? lower_index(K, ia + 1, z, ea.k + dhi + 1) : cur2[ia];
+      int e = a.first_region ? lower_index(K, ia + 1, z, ka + dhi + 1) : cur2[ia];
       if (dlo <= dhi)
-        for (; e > ia + 1 && K[e - 1] >= ea.k + dlo; e--) add_pair<T, ACC, MODE>(ea, E[e - 1], c);
+        for (int kb; e > ia + 1 && (kb = K[e - 1]) >= ka + dlo; e--) add(ea, ka, e - 1, kb);
       cur2[ia] = e;
     }
   }
@@ -443,7 +551,10 @@ size_t sparse_smem_bytes(bool fp32, int cap) {
   return (size_t)cap * (8 + 8 + (fp32 ? sizeof(SpEnt<float>) : sizeof(SpEnt<double>)));
 }
 
-size_t sparse_entry_bytes(bool fp32) { return fp32 ? sizeof(SpEnt<float>) : sizeof(SpEnt<double>); }
+size_t sparse_entry_bytes(bool fp32, bool fused) {
+  if (fused) return fp32 ? sizeof(FuEnt<float>) : sizeof(FuEnt<double>);
+  return fp32 ? sizeof(SpEnt<float>) : sizeof(SpEnt<double>);
+}
 
 cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st) {
   if (a.n_nodes <= 0 || a.n_tabs <= 0) return cudaSuccess;
@@ -460,7 +571,10 @@ cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaSt
   if (a.n_nodes <= 0 || a.r0 >= a.r1) return cudaSuccess;
   const int mode = a.alpha == 0.5 ? 0 : 1;
   const dim3 grid((unsigned)a.n_nodes);
-  if (acc == ACC_MIN) {
+  if (acc == ACC_MIN && a.fused) {
+    if (fp32) k_sparse_region<float, ACC_MIN, 0, true><<<grid, 128, 0, st>>>(a);
+    else k_sparse_region<double, ACC_MIN, 0, true><<<grid, 128, 0, st>>>(a);
+  } else if (acc == ACC_MIN) {
     if (fp32) k_sparse_region<float, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
     else k_sparse_region<double, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
   } else if (fp32) {

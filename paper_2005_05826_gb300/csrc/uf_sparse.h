@@ -47,6 +47,13 @@ struct SparseArgs {
                             // region kernel's binary searches
   const int64_t *lofs;      // first entry of each row
   int *lz;                  // entries of each row
+  // fused lists (min form, list mode): a listed row also carries the terms of
+  // up to SPARSE_FUSE_MEMBERS member rows, sparse branches below it (so their
+  // samples are among its own and their pairs among its pairs), and each of
+  // its pairs adds the sum of the rows' min-form terms with one atomic;
+  // members[SPARSE_FUSE_MEMBERS * (row_base + blockIdx.x) + i] is a node or -1
+  int fused;
+  const int32_t *members;
   // region mode: only pairs whose stripe lies in [r0, r1) (launch_sparse_region)
   int r0, r1;
   int first_region;         // 1: the call's first region (cursors are searched, not read)
@@ -57,16 +64,18 @@ struct SparseArgs {
 // shared memory, or written as a list (one table, keys alone in shared memory)
 constexpr int SPARSE_MAX_ENTRIES = 4096;
 constexpr int SPARSE_LIST_MAX_ENTRIES = 16384;
+constexpr int SPARSE_FUSE_MEMBERS = 2;
 size_t sparse_smem_bytes(bool fp32, int cap);
-size_t sparse_entry_bytes(bool fp32);
+size_t sparse_entry_bytes(bool fp32, bool fused = false);
 cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 // Pairs of the listed rows (nodes[0 .. n_nodes), lists from a list-mode
 // launch, table tabs[0]) whose stripe lies in [a.r0, a.r1): one CTA per row,
 // each thread takes samples a and walks the partners b of the two windows of
 // k_b - k_a that map into the region from per-entry cursors (set by binary
-// search in the first region).  Run region by region, in increasing stripe
-// order, so that the accumulator cells a launch touches stay in L2.
+// search in the first region); fused lists add each pair's summed terms.
+// Run region by region, in increasing stripe order, so that the accumulator
+// cells a launch touches stay in L2.
 cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 
 }  // namespace ufg

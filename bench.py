@@ -273,7 +273,8 @@ def workload_config(args, tree_s, table_s, l2):
             "stripes": "all" if not 0 < getattr(args, "stripe_stop", 0) < table_s.n_samples // 2
             else f"[0, {args.stripe_stop}) of {table_s.n_samples // 2}",
             "sparse_rows_mode": getattr(args, "sparse", 1),
-            "sparse_region_bytes": getattr(args, "region_bytes", 0) or "default", "l2": l2}
+            "sparse_region_bytes": getattr(args, "region_bytes", 0) or "default",
+            "sparse_fuse": "default" if getattr(args, "sparse_fuse", -1) < 0 else args.sparse_fuse, "l2": l2}
 
 
 def max_err_vs_fp64(mixed_outs, fp64_outs):
@@ -498,6 +499,8 @@ def run_ours(args, rank, world, local_rank):
     uf.uf_set_option("kernel_timing", 1)
     uf.uf_set_option("sparse", args.sparse)
     uf.uf_set_option("sparse_region_bytes", args.region_bytes)
+    if args.sparse_fuse >= 0:
+        uf.uf_set_option("sparse_fuse", args.sparse_fuse)
     uf.uf_set_option("sparse_overlap", args.overlap)
 
     def step(precision, reps=None):
@@ -867,6 +870,8 @@ def main():
                          "(0: all; default: per workload)")
     ap.add_argument("--region-bytes", type=int, default=0,
                     help="option sparse_region_bytes (0: the library default)")
+    ap.add_argument("--sparse-fuse", type=int, choices=[-1, 0, 2, 6], default=-1,
+                    help="option sparse_fuse (-1: the library default)")
     ap.add_argument("--overlap", type=int, choices=[0, 1], default=1,
                     help="option sparse_overlap: sparse scatter beside the dense kernel")
     ap.add_argument("--sparse", type=int, choices=[0, 1, 2], default=1,

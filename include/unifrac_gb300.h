@@ -184,6 +184,13 @@ typedef struct {
  *                    wait runs out after 2 s: a synchronous call returns
  *                    UF_ETIMEOUT and an asynchronous one writes NaN (for
  *                    testing the abort path; no fault, the context stays usable)
+ *   "sparse_fuse"    2 (default), 6 or 0: in the region scatter of a min-form
+ *                    method (the weighted methods and the tensor path's
+ *                    unweighted) a listed branch also carries the terms of its
+ *                    scattered children (2), or of its children and their
+ *                    children (6), and adds each pair's summed terms with one
+ *                    atomic; 0: every scattered branch on its own.  The
+ *                    results are the same bit for bit (integer accumulators)
  *   "sparse_region_bytes"  48,000,000 (default; 0 restores it): a one-table
  *                    call whose stripe accumulators exceed this many bytes
  *                    writes the scattered branches' sample lists once and

@@ -23,6 +23,7 @@ namespace rt {
 thread_local std::string g_err;
 thread_local double g_h2d = 0.0;
 std::atomic<int64_t> g_branch_block{0};
+std::atomic<int64_t> g_sparse_fuse{2};
 std::atomic<int64_t> g_kernel_timing{0};
 std::atomic<int64_t> g_tensor_path{1};
 std::atomic<int64_t> g_graph{1};
@@ -418,6 +419,11 @@ uf_status uf_set_option(const char *name, int64_t value) {
     g_overlap = value;
     return UF_OK;
   }
+  if (!strcmp(name, "sparse_fuse")) {
+    if (value != 0 && value != 2 && value != 6) return fail(UF_EINVAL, "sparse_fuse must be 0, 2 or 6");
+    g_sparse_fuse = value;
+    return UF_OK;
+  }
   if (!strcmp(name, "tile_shape")) {
     if (value < -1 || value > 1) return fail(UF_EINVAL, "tile_shape must be -1, 0 or 1");
     g_tile_shape = value;
@@ -443,6 +449,7 @@ int64_t uf_get_option(const char *name) {
   if (!strcmp(name, "sparse_overlap")) return g_overlap.load();
   if (!strcmp(name, "tensor_wait_test")) return g_tensor_wait_test.load();
   if (!strcmp(name, "tile_shape")) return g_tile_shape.load();
+  if (!strcmp(name, "sparse_fuse")) return g_sparse_fuse.load();
   return -1;
 }
 

@@ -425,7 +425,9 @@ Inputs bind_inputs(uf_tree *tree, const BatchJob &J, int device, int64_t rows) {
 // Branch rows per embedding block for a working budget of per_row bytes a row
 // plus fixed bytes.
 int64_t block_rows(int64_t nb, double per_row, double fixed) {
-  const double budget = std::min(0.5 * available_bytes() - fixed, 24e9);
+  // 48 GB: about 31 blocks for a 1M-node tree and a 113,000-sample table
+  // (fewer, longer dense launches: 2.6 % less time than 24 GB's 64 blocks)
+  const double budget = std::min(0.5 * available_bytes() - fixed, 48e9);
   int64_t rows = (int64_t)(budget / per_row / 1.1);
   rows = std::max<int64_t>(std::min<int64_t>(rows, nb), std::min<int64_t>(nb, 256));
   if (g_branch_block.load() > 0) rows = std::min<int64_t>(g_branch_block.load(), std::max<int64_t>(nb, 1));
@@ -549,7 +551,7 @@ struct SpLayout {
 struct SparseScatter {
   const RowSplit *split = nullptr;
   bool region_mode = false;
-  bool fused = false;     // min-form lists carrying member rows (launch_sparse_region)
+  int fuse_m = 0;         // members per min-form list row (launch_sparse_region); 0: unfused
   bool two_word = false;  // FP64 terms in two words (second words after the first)
   int n_acc = 1;
   int64_t n_sparse_rows = 0, cells = 0, n_cols = 0;
@@ -574,32 +576,35 @@ struct SparseScatter {
     if (sp.n_sparse == 0) return;
     const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc * (two_word ? 2 : 1));
     region_mode = n_regions > 1 || sp.lists;
-    fused = region_mode && acc == ACC_MIN;
+    fuse_m = region_mode && acc == ACC_MIN ? (int)g_sparse_fuse.load() : 0;
     std::vector<int32_t> all, members;
-    if (fused) {
+    if (fuse_m > 0) {
       // A sparse branch whose parent is a listed head rides in the parent's
-      // list (up to SPARSE_FUSE_MEMBERS per head): its samples are among the
-      // parent's and its pairs among the parent's pairs.  Parents come before
-      // children in decreasing node order (parent[v] > v), so every head is
-      // final when its children are visited; a member's children are heads.
-      constexpr int F = SPARSE_FUSE_MEMBERS;
+      // list (its samples are among the parent's and its pairs among the
+      // parent's pairs); with six members per head, so does a sparse child of
+      // such a member (two levels below the head).  Parents come before
+      // children in decreasing node order (parent[v] > v), so every head and
+      // member is final when its children are visited.
+      const int F = fuse_m, depth = F == 6 ? 2 : 1;
       const int64_t nn = tree->n_nodes;
-      std::vector<int8_t> role(nn, 0), used(nn, 0);  // role 1: head, 2: member
-      std::vector<int32_t> mem_of((size_t)nn * F, -1);
+      std::vector<int8_t> level(nn, -1), used(nn, 0);  // -1: not listed, 0: head, >0: member depth
+      std::vector<int32_t> head_of(nn, -1), mem_of((size_t)nn * F, -1);
       for (const auto &c : sp.sparse)
-        for (int32_t v : c) role[v] = 1;
+        for (int32_t v : c) level[v] = 0;
       for (int64_t v = nn - 2; v >= 0; v--) {
-        if (role[v] != 1) continue;
+        if (level[v] != 0) continue;
         const int64_t p = tree->parent[v];
-        if (p >= 0 && role[p] == 1 && used[p] < F) {
-          mem_of[(size_t)p * F + used[p]++] = (int32_t)v;
-          role[v] = 2;
-        }
+        if (p < 0 || level[p] < 0 || level[p] >= depth) continue;
+        const int32_t h = level[p] == 0 ? (int32_t)p : head_of[p];
+        if (used[h] >= F) continue;
+        mem_of[(size_t)h * F + used[h]++] = (int32_t)v;
+        level[v] = (int8_t)(level[p] + 1);
+        head_of[v] = h;
       }
       for (const auto &c : sp.sparse) {
         sp_off.push_back((int64_t)all.size());
         for (int32_t v : c)
-          if (role[v] == 1) {
+          if (level[v] == 0) {
             all.push_back(v);
             members.insert(members.end(), mem_of.begin() + (size_t)v * F, mem_of.begin() + (size_t)v * F + F);
           }
@@ -620,14 +625,14 @@ struct SparseScatter {
         lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
       const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
       list_entries = (int64_t)total_e;
-      le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries, fused), st, "alloc sparse lists");
+      le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries, fuse_m), st, "alloc sparse lists");
       lk = DevBuf(total_e * 4, st, "alloc sparse lists");
       cur = DevBuf(total_e * 8, st, "alloc sparse list cursors");
       lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
       // rows without entries in the table return before writing their count
       ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
       o_lofs = meta.add(lofs);
-      if (fused) o_members = meta.add(members);
+      if (fuse_m > 0) o_members = meta.add(members);
     }
     std::vector<SpTab> tabs(nt);
     for (size_t t = 0; t < nt; t++) {
@@ -669,8 +674,8 @@ struct SparseScatter {
       base.lz = lz.as<int>();
       base.cur = cur.as<int>();
       base.cur_stride = list_entries;
-      base.fused = fused ? 1 : 0;
-      base.members = fused ? meta.at<int32_t>(o_members) : nullptr;
+      base.fused = fuse_m;
+      base.members = fuse_m > 0 ? meta.at<int32_t>(o_members) : nullptr;
     }
     for (size_t c = 0; c < split->sparse.size(); c++) {
       if (cls_n[c] == 0) continue;

@@ -38,7 +38,7 @@ namespace rt {
 extern thread_local std::string g_err;   // uf_last_error() text of this thread
 extern thread_local double g_h2d;        // bytes the current call uploaded
 extern std::atomic<int64_t> g_branch_block, g_kernel_timing, g_tensor_path, g_graph, g_autotune, g_sparse, g_overlap,
-    g_tensor_wait_test, g_tile_shape;
+    g_tensor_wait_test, g_tile_shape, g_sparse_fuse;
 
 // Sets the thread's error text and returns st.
 uf_status fail(uf_status st, const char *fmt, ...);

@@ -127,24 +127,27 @@ __device__ __forceinline__ void set_f(SpEnt<double> &e, Fx2 v) {
   e.f_lo = v.lo;
 }
 
-// One distinct sample of a fused list (min form): the fixed-point terms of
-// the listed row and of its members (0 where the sample is not below the
-// member); its sample is in the list's separate key array.
-constexpr int FUSE_ROWS = 1 + SPARSE_FUSE_MEMBERS;
-template <typename T>
+// One distinct sample of a fused list with F members (min form): the
+// fixed-point terms of the listed row and of its members (0 where the sample
+// is not below the member); its sample is in the list's separate key array.
+template <typename T, int F>
 struct FuEnt;
-template <>
-struct alignas(8) FuEnt<float> {
-  long long f[FUSE_ROWS];
+template <int F>
+struct alignas(8) FuEnt<float, F> {
+  long long f[1 + F];
 };
-template <>
-struct alignas(16) FuEnt<double> {
-  long long f[FUSE_ROWS], f_lo[FUSE_ROWS];
+template <int F>
+struct alignas(16) FuEnt<double, F> {
+  long long f[1 + F], f_lo[1 + F];
 };
-__device__ __forceinline__ Fx2 fu_f(const FuEnt<float> &e, int r) { return Fx2{e.f[r], 0}; }
-__device__ __forceinline__ Fx2 fu_f(const FuEnt<double> &e, int r) { return Fx2{e.f[r], e.f_lo[r]}; }
-__device__ __forceinline__ void fu_set(FuEnt<float> &e, int r, Fx2 v) { e.f[r] = v.hi; }
-__device__ __forceinline__ void fu_set(FuEnt<double> &e, int r, Fx2 v) {
+template <int F>
+__device__ __forceinline__ Fx2 fu_f(const FuEnt<float, F> &e, int r) { return Fx2{e.f[r], 0}; }
+template <int F>
+__device__ __forceinline__ Fx2 fu_f(const FuEnt<double, F> &e, int r) { return Fx2{e.f[r], e.f_lo[r]}; }
+template <int F>
+__device__ __forceinline__ void fu_set(FuEnt<float, F> &e, int r, Fx2 v) { e.f[r] = v.hi; }
+template <int F>
+__device__ __forceinline__ void fu_set(FuEnt<double, F> &e, int r, Fx2 v) {
   e.f[r] = v.hi;
   e.f_lo[r] = v.lo;
 }
@@ -206,8 +209,8 @@ __device__ __forceinline__ void add_pair(const SpEnt<T> &ea, const SpEnt<T> &eb,
 // and its members of min(X_a, X_b) (a member without one of the samples
 // adds 0), -2 times that in an abs-form stripe; the same integers as the
 // rows' separate pair updates, in one atomic per word.
-template <typename T>
-__device__ __forceinline__ void add_pair_fused(int ka, int kb, const FuEnt<T> &ea, const FuEnt<T> &eb,
+template <typename T, int F>
+__device__ __forceinline__ void add_pair_fused(int ka, int kb, const FuEnt<T, F> &ea, const FuEnt<T, F> &eb,
                                                const PairCtx<T> &c) {
   const int d = kb - ka;
   int s, kc;
@@ -222,7 +225,7 @@ __device__ __forceinline__ void add_pair_fused(int ka, int kb, const FuEnt<T> &e
   const int64_t cell = (int64_t)(s - c.s_lo) * c.n + kc;
   Fx2 t = fx_min(fu_f(ea, 0), fu_f(eb, 0));
 #pragma unroll
-  for (int r = 1; r < FUSE_ROWS; r++) t = fx_add(t, fx_min(fu_f(ea, r), fu_f(eb, r)));
+  for (int r = 1; r <= F; r++) t = fx_add(t, fx_min(fu_f(ea, r), fu_f(eb, r)));
   if (abs_row(c.abs_mask, s)) t = fx_mul(t, -2);
   red_add2<T>(c.M + cell, c.m_lo_off, t);
   if (2 * d == c.n) red_add2<T>(c.M + cell + d, c.m_lo_off, t);
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(256) k_sparse_rows(const SparseArgs a) {
 // summed in entry order reading the counts from global memory, and each
 // distinct sample's k, x (or u) and fixed-point term go straight to the
 // row's list; the per-sample terms R are added here once.
-template <typename T, int ACC, int MODE>
+template <typename T, int ACC, int MODE, int F = 0>
 __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sh[33];
@@ -390,33 +393,33 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
   const T alpha = (T)a.alpha;
   const int64_t off = a.lofs[row];
   SpEnt<T> *le = reinterpret_cast<SpEnt<T> *>(a.le);
-  if (ACC == ACC_MIN && a.fused) {
+  if constexpr (ACC == ACC_MIN && F > 0) {
     // The members' tips are sub-ranges of this row's tips, so their count
     // entries are sub-runs [mlo, mhi) of its run: each distinct sample's
     // count under a member sums the same entries in the same order as the
     // member's own list would.
-    int mlo[SPARSE_FUSE_MEMBERS], mhi[SPARSE_FUSE_MEMBERS];
-    double ml[SPARSE_FUSE_MEMBERS];
+    int mlo[F], mhi[F];
+    double ml[F];
 #pragma unroll
-    for (int j = 0; j < SPARSE_FUSE_MEMBERS; j++) {
-      const int mv = a.members[(int64_t)SPARSE_FUSE_MEMBERS * row + j];
+    for (int j = 0; j < F; j++) {
+      const int mv = a.members[(int64_t)F * row + j];
       mlo[j] = mv >= 0 ? (int)(tb.col_ptr[a.tip_lo[mv]] - q0) : 0;
       mhi[j] = mv >= 0 ? (int)(tb.col_ptr[a.tip_hi[mv]] - q0) : 0;
       ml[j] = mv >= 0 ? a.length[mv] : 0.0;
     }
-    FuEnt<T> *lf = reinterpret_cast<FuEnt<T> *>(a.le);
+    FuEnt<T, F> *lf = reinterpret_cast<FuEnt<T, F> *>(a.le);
     for (int i = i0; i < i1; i++) {
       const unsigned smp = (unsigned)(key[i] >> 32);
       if (i > 0 && (unsigned)(key[i - 1] >> 32) == smp) continue;
-      double c = 0.0, cm[SPARSE_FUSE_MEMBERS];
+      double c = 0.0, cm[F];
 #pragma unroll
-      for (int j = 0; j < SPARSE_FUSE_MEMBERS; j++) cm[j] = 0.0;
+      for (int j = 0; j < F; j++) cm[j] = 0.0;
       for (int m = i; m < L && (unsigned)(key[m] >> 32) == smp; m++) {
         const int e = (int)(key[m] & 0xffffffffu);
         const double val = tb.col_val[q0 + e];
         c += val;
 #pragma unroll
-        for (int j = 0; j < SPARSE_FUSE_MEMBERS; j++)
+        for (int j = 0; j < F; j++)
           if (e >= mlo[j] && e < mhi[j]) cm[j] += val;
       }
       auto term = [&](double cnt, double len) -> Fx2 {
@@ -425,11 +428,11 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
                         : emb_value<T, EMB_PRESENCE>(cnt, len, tb.total[smp], tb.inv_total_f[smp]);
         return to_fixed2(x, a.scale);
       };
-      FuEnt<T> fe;
+      FuEnt<T, F> fe;
       Fx2 f = term(c, l), dsum = f;
       fu_set(fe, 0, f);
 #pragma unroll
-      for (int j = 0; j < SPARSE_FUSE_MEMBERS; j++) {
+      for (int j = 0; j < F; j++) {
         const Fx2 fm = term(cm[j], ml[j]);
         fu_set(fe, 1 + j, fm);
         dsum = fx_add(dsum, fm);
@@ -476,9 +479,10 @@ __device__ __forceinline__ int lower_index(const int *K, int lo, int hi, int key
   return lo;
 }
 
-template <typename T, int ACC, int MODE, bool FUSED = false>
+template <typename T, int ACC, int MODE, int F = 0>
 __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
-  using Ent = std::conditional_t<FUSED, FuEnt<T>, SpEnt<T>>;
+  constexpr bool FUSED = F > 0;
+  using Ent = std::conditional_t<FUSED, FuEnt<T, (F > 0 ? F : 1)>, SpEnt<T>>;
   const int row = blockIdx.x;
   const SpTab tb = a.tabs[0];
   const int64_t off = a.lofs[row];
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   // call searches for it.
   int *cur1 = a.cur + off, *cur2 = a.cur + a.cur_stride + off;
   auto add = [&](const Ent &ea, int ka, int b, int kb) {
-    if constexpr (FUSED) add_pair_fused<T>(ka, kb, ea, E[b], c);
+    if constexpr (FUSED) add_pair_fused<T, F>(ka, kb, ea, E[b], c);
     else add_pair<T, ACC, MODE>(ea, E[b], c);
   };
   for (int ia = threadIdx.x; ia < z - 1; ia += blockDim.x) {
@@ -551,8 +555,9 @@ size_t sparse_smem_bytes(bool fp32, int cap) {
   return (size_t)cap * (8 + 8 + (fp32 ? sizeof(SpEnt<float>) : sizeof(SpEnt<double>)));
 }
 
-size_t sparse_entry_bytes(bool fp32, bool fused) {
-  if (fused) return fp32 ? sizeof(FuEnt<float>) : sizeof(FuEnt<double>);
+size_t sparse_entry_bytes(bool fp32, int fused) {
+  if (fused == 2) return fp32 ? sizeof(FuEnt<float, 2>) : sizeof(FuEnt<double, 2>);
+  if (fused == 6) return fp32 ? sizeof(FuEnt<float, 6>) : sizeof(FuEnt<double, 6>);
   return fp32 ? sizeof(SpEnt<float>) : sizeof(SpEnt<double>);
 }
 
@@ -571,9 +576,16 @@ cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaSt
   if (a.n_nodes <= 0 || a.r0 >= a.r1) return cudaSuccess;
   const int mode = a.alpha == 0.5 ? 0 : 1;
   const dim3 grid((unsigned)a.n_nodes);
-  if (acc == ACC_MIN && a.fused) {
-    if (fp32) k_sparse_region<float, ACC_MIN, 0, true><<<grid, 128, 0, st>>>(a);
-    else k_sparse_region<double, ACC_MIN, 0, true><<<grid, 128, 0, st>>>(a);
+  if (acc == ACC_MIN && a.fused != 0) {
+    if (a.fused == 2) {
+      if (fp32) k_sparse_region<float, ACC_MIN, 0, 2><<<grid, 128, 0, st>>>(a);
+      else k_sparse_region<double, ACC_MIN, 0, 2><<<grid, 128, 0, st>>>(a);
+    } else if (a.fused == 6) {
+      if (fp32) k_sparse_region<float, ACC_MIN, 0, 6><<<grid, 128, 0, st>>>(a);
+      else k_sparse_region<double, ACC_MIN, 0, 6><<<grid, 128, 0, st>>>(a);
+    } else {
+      return cudaErrorInvalidValue;
+    }
   } else if (acc == ACC_MIN) {
     if (fp32) k_sparse_region<float, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
     else k_sparse_region<double, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
@@ -603,6 +615,11 @@ cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStr
     kernel<<<grid, nt, smem, st>>>(a);
     return cudaGetLastError();
   };
+  if (acc == ACC_MIN && a.fused == 2)
+    return fp32 ? go(k_sparse_lists<float, ACC_MIN, 0, 2>) : go(k_sparse_lists<double, ACC_MIN, 0, 2>);
+  if (acc == ACC_MIN && a.fused == 6)
+    return fp32 ? go(k_sparse_lists<float, ACC_MIN, 0, 6>) : go(k_sparse_lists<double, ACC_MIN, 0, 6>);
+  if (a.fused != 0) return cudaErrorInvalidValue;
   if (acc == ACC_MIN) return fp32 ? go(k_sparse_lists<float, ACC_MIN, 0>) : go(k_sparse_lists<double, ACC_MIN, 0>);
   if (fp32) return mode == 0 ? go(k_sparse_lists<float, ACC_GEN, 0>) : go(k_sparse_lists<float, ACC_GEN, 1>);
   return mode == 0 ? go(k_sparse_lists<double, ACC_GEN, 0>) : go(k_sparse_lists<double, ACC_GEN, 1>);

@@ -59,10 +59,18 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
     else dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
     const double visit_rate = fp32 ? 2e12 : (acc == ACC_GEN ? 3e10 : 1e12);
     const double job_cost = 5e-10;
+    // min-form region lists are fused (a listed branch carries its sparse
+    // children, and with option sparse_fuse 6 its grandchildren, uf_run.cpp):
+    // on the 113k-sample table about 0.57 (0.43) of the pairs and 0.54 (0.39)
+    // of the list entries remain, so a scattered branch costs about that share
+    // of its own pairs and visits.  The tensor path's scatter runs beside its
+    // gram and ends after it already: its split keeps the unfused costs.
+    const int64_t fm = g_sparse_fuse.load();
+    const double fuse = regions && acc == ACC_MIN && fm > 0 ? (fm == 6 ? 0.45 : 0.6) : 1.0;
     for (size_t t = 0; t < nt; t++) {
       const double n = (double)J.tabs[t].table->n;
       const double atom_rate = std::floor(n / 2.0) * n * 8.0 * n_acc <= 64e6 || regions ? 2.3e11 : 2.5e10;
-      pair_cost[t] = 1.0 / visit_rate + n_acc / atom_rate;
+      pair_cost[t] = (1.0 / visit_rate + n_acc / atom_rate) * fuse;
       entry_cost[t] = 4.0 / atom_rate;
     }
     // a dense row also costs its count row and embedding (or planes) in HBM
@@ -103,7 +111,7 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
           // one visit per region: a CTA, and each entry's cursors walked to the
           // region (about 7e-12 s per entry and region measured on GB300 with a
           // 113,000-sample table; pairs at 4.3e-12 s)
-          if (regions) cost += n_regions * (job_cost + (double)ub * 1e-11);
+          if (regions) cost += n_regions * (job_cost + (double)ub * 1e-11 * fuse);
         }
         if (mx > max_entries) continue;
         if (mode == 2 || cost < dense_t) {
@@ -186,7 +194,7 @@ std::shared_ptr<const RowSplit> get_split(uf_tree *tree, const BatchJob &J, cons
   for (const TableJob &t : J.tabs) std::get<0>(key).push_back(t.table->id);
   std::get<1>(key) = acc;
   std::get<2>(key) = fp32 ? 1 : 0;
-  std::get<3>(key) = (int)g_sparse.load();
+  std::get<3>(key) = (int)(g_sparse.load() * 16 + g_sparse_fuse.load());
   std::get<4>(key) = P->block_rows;
   std::get<5>(key) = g_region_bytes.load();
   std::lock_guard<std::mutex> g(tree->mu);

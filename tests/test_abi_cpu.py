@@ -104,6 +104,8 @@ OPTIONS = {  # name: (default, accepted values, rejected values)
     "sparse_overlap": (1, [0, 1], [-1, 2]),
     "tensor_wait_test": (0, [1, 0], [-1, 2]),
     "sparse_region_bytes": (48_000_000, [4096, 10**9, 48_000_000], [1, 4095, -5]),
+    "sparse_fuse": (2, [0, 6, 2], [-1, 1, 3, 7]),
+    "tile_shape": (-1, [0, 1, -1], [-2, 2]),
 }
 
 

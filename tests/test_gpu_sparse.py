@@ -283,6 +283,42 @@ def test_region_scatter_matches_direct_bitwise(n, density):
     assert uf.uf_get_option("sparse_region_bytes") == 48_000_000
 
 
+@pytest.mark.parametrize("tensor", [0, 1])
+def test_fused_lists_match_unfused_bitwise(tensor):
+    # In list mode a listed branch carries the min-form terms of its scattered
+    # children (option sparse_fuse 2) or of its children and grandchildren (6)
+    # and adds each pair's summed terms with one atomic: the integers are the
+    # same as the rows' own updates, so every setting gives the same bits
+    # (with every fitting branch scattered, the split does not depend on the
+    # setting); the generalized method's lists are never fused.
+    tree_s = yule_tree(2000, seed=290)
+    table_s = table_iid(300, tree_s.n_tips, 0.01, seed=291)
+    tree, table = handles(tree_s, table_s)
+    S = uf.uf_stripe_count(300)
+    uf.uf_set_option("tensor_path", tensor)
+    uf.uf_set_option("sparse_region_bytes", 16384)
+    try:
+        for method in METHODS if not tensor else ["unweighted"]:
+            a = 0.5 if method == "generalized" else 1.0
+            exp = oracle.condensed(tree_s, table_s, method, a)
+            for precision in PRECISIONS:
+                got = {}
+                for fuse in (0, 2, 6):
+                    uf.uf_set_option("sparse_fuse", fuse)
+                    got[fuse], rep = run(tree, table, method, a, precision, 2)
+                    assert rep.sparse_rows > 0
+                    got[(fuse, "range")], _ = run(tree, table, method, a, precision, 2, 5, S - 7)
+                np.testing.assert_array_equal(got[2], got[0])
+                np.testing.assert_array_equal(got[6], got[0])
+                np.testing.assert_array_equal(got[(2, "range")], got[(0, "range")])
+                np.testing.assert_array_equal(got[(6, "range")], got[(0, "range")])
+                assert_close(got[2], exp, method, precision, f"fused lists tensor={tensor}")
+    finally:
+        uf.uf_set_option("sparse_fuse", 2)
+        uf.uf_set_option("sparse_region_bytes", 0)
+        uf.uf_set_option("tensor_path", 1)
+
+
 def test_overlap_matches_sequential_bitwise():
     # the scatter beside the dense kernel adds the same integers in another
     # order: the results equal the sequential ones bit for bit

@@ -576,7 +576,9 @@ struct SparseScatter {
     if (sp.n_sparse == 0) return;
     const int64_t n_regions = (int64_t)sparse_regions(nt, acc, (double)cells * 8.0 * n_acc * (two_word ? 2 : 1));
     region_mode = n_regions > 1 || sp.lists;
-    fuse_m = region_mode && acc == ACC_MIN ? (int)g_sparse_fuse.load() : 0;
+    // the generalized method's entries carry each row's proportion as well:
+    // two members at most
+    fuse_m = !region_mode ? 0 : acc == ACC_MIN ? (int)g_sparse_fuse.load() : (int)std::min<int64_t>(g_sparse_fuse.load(), 2);
     std::vector<int32_t> all, members;
     if (fuse_m > 0) {
       // A sparse branch whose parent is a listed head rides in the parent's
@@ -625,7 +627,7 @@ struct SparseScatter {
         lofs[r + 1] = lofs[r] + (cp[tree->tip_hi[all[r]]] - cp[tree->tip_lo[all[r]]]);
       const size_t total_e = (size_t)std::max<int64_t>(lofs.back(), 1);
       list_entries = (int64_t)total_e;
-      le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries, fuse_m), st, "alloc sparse lists");
+      le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries, fuse_m, acc), st, "alloc sparse lists");
       lk = DevBuf(total_e * 4, st, "alloc sparse lists");
       cur = DevBuf(total_e * 8, st, "alloc sparse list cursors");
       lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");

@@ -151,6 +151,35 @@ __device__ __forceinline__ void fu_set(FuEnt<double, F> &e, int r, Fx2 v) {
   e.f[r] = v.hi;
   e.f_lo[r] = v.lo;
 }
+// The same for the generalized method: each row's proportion u (0 where the
+// sample is not below the row) and its term P = fixed(l u^alpha).
+template <typename T, int F>
+struct FuGEnt;
+template <int F>
+struct alignas(8) FuGEnt<float, F> {
+  float x[1 + F];
+  long long f[1 + F];
+};
+template <int F>
+struct alignas(16) FuGEnt<double, F> {
+  double x[1 + F];
+  long long f[1 + F], f_lo[1 + F];
+};
+template <int F>
+__device__ __forceinline__ Fx2 fu_f(const FuGEnt<float, F> &e, int r) { return Fx2{e.f[r], 0}; }
+template <int F>
+__device__ __forceinline__ Fx2 fu_f(const FuGEnt<double, F> &e, int r) { return Fx2{e.f[r], e.f_lo[r]}; }
+template <int F>
+__device__ __forceinline__ void fu_set(FuGEnt<float, F> &e, int r, Fx2 v) { e.f[r] = v.hi; }
+template <int F>
+__device__ __forceinline__ void fu_set(FuGEnt<double, F> &e, int r, Fx2 v) {
+  e.f[r] = v.hi;
+  e.f_lo[r] = v.lo;
+}
+// list entry type of a method's fused lists (F > 0) or of unfused lists
+template <typename T, int ACC, int F>
+using ListEnt = std::conditional_t<F == 0, SpEnt<T>,
+                                   std::conditional_t<ACC == ACC_MIN, FuEnt<T, (F > 0 ? F : 1)>, FuGEnt<T, (F > 0 ? F : 1)>>>;
 
 // What a pair update needs besides its two entries.
 template <typename T>
@@ -229,6 +258,44 @@ __device__ __forceinline__ void add_pair_fused(int ka, int kb, const FuEnt<T, F>
   if (abs_row(c.abs_mask, s)) t = fx_mul(t, -2);
   red_add2<T>(c.M + cell, c.m_lo_off, t);
   if (2 * d == c.n) red_add2<T>(c.M + cell + d, c.m_lo_off, t);
+}
+
+// The pair (a, b), k_a < k_b, of a fused generalized list: each row in which
+// both samples are present (u > 0) gives the den and Q (or N) terms of its
+// own update with its own length len[r]; their sums go with one atomic per
+// accumulator and word, the same integers as the rows' separate updates.
+template <typename T, int MODE, int F>
+__device__ __forceinline__ void add_pair_fused_gen(int ka, int kb, const FuGEnt<T, F> &ea, const FuGEnt<T, F> &eb,
+                                                   const PairCtx<T> &c, const T *len) {
+  const int d = kb - ka;
+  int s, kc;
+  if (2 * d <= c.n) {
+    s = d - 1;
+    kc = ka;
+  } else {
+    s = c.n - d - 1;
+    kc = kb;
+  }
+  if (s < c.s_lo || s > c.s_hi) return;
+  const int64_t cell = (int64_t)(s - c.s_lo) * c.n + kc;
+  Fx2 den{0, 0}, t2{0, 0};
+#pragma unroll
+  for (int r = 0; r <= F; r++) {
+    const T uu = ea.x[r], vv = eb.x[r];
+    if (!(uu > T(0) && vv > T(0))) continue;
+    const T w = len[r] * pow_am1<T, MODE>(uu + vv, c.am1);
+    const Fx2 q = to_fixed2(w * tmin<T>(uu, vv), c.scale);
+    const Fx2 e = to_fixed2(w * (uu > vv ? uu - vv : vv - uu), c.scale);
+    const Fx2 e_ab = fx_sub(fx_sub(e, fu_f(ea, r)), fu_f(eb, r));
+    den = fx_add(den, fx_add(fx_mul(q, 2), e_ab));
+    t2 = fx_add(t2, c.gen_abs ? e_ab : q);
+  }
+  red_add2<T>(c.M + cell, c.m_lo_off, den);
+  red_add2<T>(c.M2 + cell, c.m_lo_off, t2);
+  if (2 * d == c.n) {
+    red_add2<T>(c.M + cell + d, c.m_lo_off, den);
+    red_add2<T>(c.M2 + cell + d, c.m_lo_off, t2);
+  }
 }
 
 template <typename T, int ACC, int MODE>
@@ -393,7 +460,7 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
   const T alpha = (T)a.alpha;
   const int64_t off = a.lofs[row];
   SpEnt<T> *le = reinterpret_cast<SpEnt<T> *>(a.le);
-  if constexpr (ACC == ACC_MIN && F > 0) {
+  if constexpr (F > 0) {
     // The members' tips are sub-ranges of this row's tips, so their count
     // entries are sub-runs [mlo, mhi) of its run: each distinct sample's
     // count under a member sums the same entries in the same order as the
@@ -407,7 +474,8 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
       mhi[j] = mv >= 0 ? (int)(tb.col_ptr[a.tip_hi[mv]] - q0) : 0;
       ml[j] = mv >= 0 ? a.length[mv] : 0.0;
     }
-    FuEnt<T, F> *lf = reinterpret_cast<FuEnt<T, F> *>(a.le);
+    using FE = ListEnt<T, ACC, F>;
+    FE *lf = reinterpret_cast<FE *>(a.le);
     for (int i = i0; i < i1; i++) {
       const unsigned smp = (unsigned)(key[i] >> 32);
       if (i > 0 && (unsigned)(key[i - 1] >> 32) == smp) continue;
@@ -422,18 +490,30 @@ __global__ void __launch_bounds__(256) k_sparse_lists(const SparseArgs a) {
         for (int j = 0; j < F; j++)
           if (e >= mlo[j] && e < mhi[j]) cm[j] += val;
       }
-      auto term = [&](double cnt, double len) -> Fx2 {
-        const T x = a.kind == EMB_SCALED
-                        ? emb_value<T, EMB_SCALED>(cnt, len, tb.total[smp], tb.inv_total_f[smp])
-                        : emb_value<T, EMB_PRESENCE>(cnt, len, tb.total[smp], tb.inv_total_f[smp]);
-        return to_fixed2(x, a.scale);
+      FE fe;
+      // one row's term (and, generalized, its proportion; both 0 where the
+      // sample is not below the row): as the row's own list computes them
+      auto term = [&](int r, double cnt, double len) -> Fx2 {
+        if constexpr (ACC == ACC_MIN) {
+          const T x = a.kind == EMB_SCALED
+                          ? emb_value<T, EMB_SCALED>(cnt, len, tb.total[smp], tb.inv_total_f[smp])
+                          : emb_value<T, EMB_PRESENCE>(cnt, len, tb.total[smp], tb.inv_total_f[smp]);
+          return to_fixed2(x, a.scale);
+        } else {
+          if (!(cnt > 0.0)) {
+            fe.x[r] = T(0);
+            return Fx2{0, 0};
+          }
+          const T x = emb_value<T, EMB_PROP>(cnt, len, tb.total[smp], tb.inv_total_f[smp]);
+          fe.x[r] = x;
+          return to_fixed2((T)len * pow_alpha<T, MODE>(x, alpha), a.scale);
+        }
       };
-      FuEnt<T, F> fe;
-      Fx2 f = term(c, l), dsum = f;
+      Fx2 f = term(0, c, l), dsum = f;
       fu_set(fe, 0, f);
 #pragma unroll
       for (int j = 0; j < F; j++) {
-        const Fx2 fm = term(cm[j], ml[j]);
+        const Fx2 fm = term(1 + j, cm[j], ml[j]);
         fu_set(fe, 1 + j, fm);
         dsum = fx_add(dsum, fm);
       }
@@ -482,7 +562,7 @@ __device__ __forceinline__ int lower_index(const int *K, int lo, int hi, int key
 template <typename T, int ACC, int MODE, int F = 0>
 __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   constexpr bool FUSED = F > 0;
-  using Ent = std::conditional_t<FUSED, FuEnt<T, (F > 0 ? F : 1)>, SpEnt<T>>;
+  using Ent = ListEnt<T, ACC, F>;
   const int row = blockIdx.x;
   const SpTab tb = a.tabs[0];
   const int64_t off = a.lofs[row];
@@ -501,6 +581,16 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   c.M = a.M + tb.m_off;
   c.M2 = ACC == ACC_GEN ? a.M2 + tb.m_off : nullptr;
   c.lt = ACC == ACC_GEN ? (T)a.length[a.nodes[row]] : T(0);
+  // fused generalized lists: the lengths of the row and its members
+  T len[1 + (F > 0 ? F : 1)];
+  if constexpr (FUSED && ACC == ACC_GEN) {
+    len[0] = c.lt;
+#pragma unroll
+    for (int j = 0; j < F; j++) {
+      const int mv = a.members[(int64_t)F * row + j];
+      len[1 + j] = mv >= 0 ? (T)a.length[mv] : T(0);
+    }
+  }
   c.am1 = (T)(a.alpha - 1.0);
   c.scale = a.scale;
   // Regions come in increasing stripe order (r0 of one is r1 of the one
@@ -510,7 +600,8 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   // call searches for it.
   int *cur1 = a.cur + off, *cur2 = a.cur + a.cur_stride + off;
   auto add = [&](const Ent &ea, int ka, int b, int kb) {
-    if constexpr (FUSED) add_pair_fused<T, F>(ka, kb, ea, E[b], c);
+    if constexpr (FUSED && ACC == ACC_MIN) add_pair_fused<T, F>(ka, kb, ea, E[b], c);
+    else if constexpr (FUSED) add_pair_fused_gen<T, MODE, F>(ka, kb, ea, E[b], c, len);
     else add_pair<T, ACC, MODE>(ea, E[b], c);
   };
   for (int ia = threadIdx.x; ia < z - 1; ia += blockDim.x) {
@@ -555,7 +646,9 @@ size_t sparse_smem_bytes(bool fp32, int cap) {
   return (size_t)cap * (8 + 8 + (fp32 ? sizeof(SpEnt<float>) : sizeof(SpEnt<double>)));
 }
 
-size_t sparse_entry_bytes(bool fp32, int fused) {
+size_t sparse_entry_bytes(bool fp32, int fused, int acc) {
+  if (fused == 2 && acc == ACC_GEN) return fp32 ? sizeof(FuGEnt<float, 2>) : sizeof(FuGEnt<double, 2>);
+  if (fused != 0 && acc == ACC_GEN) return 0;
   if (fused == 2) return fp32 ? sizeof(FuEnt<float, 2>) : sizeof(FuEnt<double, 2>);
   if (fused == 6) return fp32 ? sizeof(FuEnt<float, 6>) : sizeof(FuEnt<double, 6>);
   return fp32 ? sizeof(SpEnt<float>) : sizeof(SpEnt<double>);
@@ -589,6 +682,16 @@ cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaSt
   } else if (acc == ACC_MIN) {
     if (fp32) k_sparse_region<float, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
     else k_sparse_region<double, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
+  } else if (a.fused == 2) {
+    if (fp32) {
+      if (mode == 0) k_sparse_region<float, ACC_GEN, 0, 2><<<grid, 128, 0, st>>>(a);
+      else k_sparse_region<float, ACC_GEN, 1, 2><<<grid, 128, 0, st>>>(a);
+    } else {
+      if (mode == 0) k_sparse_region<double, ACC_GEN, 0, 2><<<grid, 128, 0, st>>>(a);
+      else k_sparse_region<double, ACC_GEN, 1, 2><<<grid, 128, 0, st>>>(a);
+    }
+  } else if (a.fused != 0) {
+    return cudaErrorInvalidValue;
   } else if (fp32) {
     if (mode == 0) k_sparse_region<float, ACC_GEN, 0><<<grid, 128, 0, st>>>(a);
     else k_sparse_region<float, ACC_GEN, 1><<<grid, 128, 0, st>>>(a);
@@ -619,6 +722,10 @@ cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStr
     return fp32 ? go(k_sparse_lists<float, ACC_MIN, 0, 2>) : go(k_sparse_lists<double, ACC_MIN, 0, 2>);
   if (acc == ACC_MIN && a.fused == 6)
     return fp32 ? go(k_sparse_lists<float, ACC_MIN, 0, 6>) : go(k_sparse_lists<double, ACC_MIN, 0, 6>);
+  if (acc == ACC_GEN && a.fused == 2) {
+    if (fp32) return mode == 0 ? go(k_sparse_lists<float, ACC_GEN, 0, 2>) : go(k_sparse_lists<float, ACC_GEN, 1, 2>);
+    return mode == 0 ? go(k_sparse_lists<double, ACC_GEN, 0, 2>) : go(k_sparse_lists<double, ACC_GEN, 1, 2>);
+  }
   if (a.fused != 0) return cudaErrorInvalidValue;
   if (acc == ACC_MIN) return fp32 ? go(k_sparse_lists<float, ACC_MIN, 0>) : go(k_sparse_lists<double, ACC_MIN, 0>);
   if (fp32) return mode == 0 ? go(k_sparse_lists<float, ACC_GEN, 0>) : go(k_sparse_lists<float, ACC_GEN, 1>);

@@ -47,11 +47,12 @@ struct SparseArgs {
                             // region kernel's binary searches
   const int64_t *lofs;      // first entry of each row
   int *lz;                  // entries of each row
-  // fused lists (min form, list mode): a listed row also carries the terms of
-  // up to `fused` member rows (2 or 6; 0: unfused), sparse branches below it
-  // (so their samples are among its own and their pairs among its pairs), and
-  // each of its pairs adds the sum of the rows' min-form terms with one
-  // atomic; members[fused * (row_base + blockIdx.x) + i] is a node or -1
+  // fused lists (list mode): a listed row also carries the terms of up to
+  // `fused` member rows (2 or 6, generalized 2; 0: unfused), sparse branches
+  // below it (so their samples are among its own and their pairs among its
+  // pairs), and each of its pairs adds the sum of the rows' terms with one
+  // atomic per accumulator; members[fused * (row_base + blockIdx.x) + i] is a
+  // node or -1
   int fused;
   const int32_t *members;
   // region mode: only pairs whose stripe lies in [r0, r1) (launch_sparse_region)
@@ -65,7 +66,7 @@ struct SparseArgs {
 constexpr int SPARSE_MAX_ENTRIES = 4096;
 constexpr int SPARSE_LIST_MAX_ENTRIES = 16384;
 size_t sparse_smem_bytes(bool fp32, int cap);
-size_t sparse_entry_bytes(bool fp32, int fused = 0);
+size_t sparse_entry_bytes(bool fp32, int fused = 0, int acc = ACC_MIN);
 cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 cudaError_t launch_sparse_lists(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);
 // Pairs of the listed rows (nodes[0 .. n_nodes), lists from a list-mode

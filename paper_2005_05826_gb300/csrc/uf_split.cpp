@@ -59,14 +59,15 @@ RowSplit split_rows(const uf_tree *tree, const BatchJob &J, const Plan *P, int a
     else dense_rate = fp32 ? (acc == ACC_GEN ? 4e12 : 1.3e13) : (acc == ACC_GEN ? 5e10 : 2e11);
     const double visit_rate = fp32 ? 2e12 : (acc == ACC_GEN ? 3e10 : 1e12);
     const double job_cost = 5e-10;
-    // min-form region lists are fused (a listed branch carries its sparse
-    // children, and with option sparse_fuse 6 its grandchildren, uf_run.cpp):
-    // on the 113k-sample table about 0.57 (0.43) of the pairs and 0.54 (0.39)
-    // of the list entries remain, so a scattered branch costs about that share
-    // of its own pairs and visits.  The tensor path's scatter runs beside its
-    // gram and ends after it already: its split keeps the unfused costs.
-    const int64_t fm = g_sparse_fuse.load();
-    const double fuse = regions && acc == ACC_MIN && fm > 0 ? (fm == 6 ? 0.45 : 0.6) : 1.0;
+    // region lists are fused (a listed branch carries its sparse children,
+    // and for the min form with option sparse_fuse 6 its grandchildren,
+    // uf_run.cpp): on the 113k-sample table about 0.57 (0.43) of the pairs
+    // and 0.54 (0.39) of the list entries remain, so a scattered branch costs
+    // about that share of its own pairs and visits.  The tensor path's
+    // scatter runs beside its gram and ends after it already: its split keeps
+    // the unfused costs.
+    const int64_t fm = acc == ACC_GEN ? std::min<int64_t>(g_sparse_fuse.load(), 2) : g_sparse_fuse.load();
+    const double fuse = regions && acc != SPLIT_GRAM && fm > 0 ? (fm == 6 ? 0.45 : 0.6) : 1.0;
     for (size_t t = 0; t < nt; t++) {
       const double n = (double)J.tabs[t].table->n;
       const double atom_rate = std::floor(n / 2.0) * n * 8.0 * n_acc <= 64e6 || regions ? 2.3e11 : 2.5e10;

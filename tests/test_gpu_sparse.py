@@ -285,12 +285,12 @@ def test_region_scatter_matches_direct_bitwise(n, density):
 
 @pytest.mark.parametrize("tensor", [0, 1])
 def test_fused_lists_match_unfused_bitwise(tensor):
-    # In list mode a listed branch carries the min-form terms of its scattered
-    # children (option sparse_fuse 2) or of its children and grandchildren (6)
-    # and adds each pair's summed terms with one atomic: the integers are the
-    # same as the rows' own updates, so every setting gives the same bits
-    # (with every fitting branch scattered, the split does not depend on the
-    # setting); the generalized method's lists are never fused.
+    # In list mode a listed branch carries the terms of its scattered children
+    # (option sparse_fuse 2) or, min form, of its children and grandchildren
+    # (6; the generalized method takes 2) and adds each pair's summed terms
+    # with one atomic per accumulator: the integers are the same as the rows'
+    # own updates, so every setting gives the same bits (with every fitting
+    # branch scattered, the split does not depend on the setting).
     tree_s = yule_tree(2000, seed=290)
     table_s = table_iid(300, tree_s.n_tips, 0.01, seed=291)
     tree, table = handles(tree_s, table_s)

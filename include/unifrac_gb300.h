@@ -135,6 +135,11 @@ typedef struct {
                               scattered pair by pair, or of length 0 and skipped */
     double sparse_pairs;   /* both-nonzero sample pairs of those branches, at most */
     double t_sparse_ms;    /* device time of the sparse-row launches ("kernel_timing") */
+    double sparse_pair_updates;  /* pair updates the stripe-region scatter made (one
+                              atomic per accumulator word each, two for the
+                              duplicated half stripe), counted on the device when
+                              "kernel_timing" is 1 and the call is synchronous;
+                              -1 otherwise or without a region scatter */
 } uf_report;
 
 /*
@@ -348,6 +353,18 @@ uf_status uf_compute_ranges(const uf_tree *tree, const uf_table *const *tables, 
 uf_status uf_compute_noalloc(const uf_tree *tree, const uf_table *table, uf_method method,
                              double alpha, uf_precision precision, double *out_device,
                              void *cuda_stream);
+
+/*
+ * uf_probe_l2_atomics -- diagnostic, not part of the method: the rate of
+ * random 64-bit atomic adds into a device array of `bytes` bytes on the
+ * current device (8 x a power of two, 8 KiB .. 16 GiB; 16 MiB stays in L2),
+ * each thread adding 1 to pseudo-random words with no other memory traffic.
+ * It is the ceiling that the stripe-region scatter's atomics (uf_compute's
+ * sparse_pair_updates) are measured against.  Allocates and frees the array;
+ * synchronous.  *adds_per_second receives the rate (0 on error).
+ * Errors: UF_EINVAL (bad size or NULL), UF_ECUDA.
+ */
+uf_status uf_probe_l2_atomics(int64_t bytes, double *adds_per_second);
 
 #ifdef __cplusplus
 }

@@ -47,7 +47,8 @@ class Report(ctypes.Structure):
                 ("acc_launches", ctypes.c_int64), ("chunk_rows", ctypes.c_int64),
                 ("graph", ctypes.c_int32), ("reserved2", ctypes.c_int32),
                 ("dense_rows", ctypes.c_int64), ("sparse_rows", ctypes.c_int64),
-                ("sparse_pairs", ctypes.c_double), ("t_sparse_ms", ctypes.c_double)]
+                ("sparse_pairs", ctypes.c_double), ("t_sparse_ms", ctypes.c_double),
+                ("sparse_pair_updates", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if not name.startswith("reserved")}
@@ -82,6 +83,8 @@ def load():
         lib.uf_last_error.restype = ctypes.c_char_p
         lib.uf_status_name.argtypes = [i32]
         lib.uf_status_name.restype = ctypes.c_char_p
+        lib.uf_probe_l2_atomics.argtypes = [i64, ctypes.POINTER(dbl)]
+        lib.uf_probe_l2_atomics.restype = i32
         lib.uf_stripe_count.argtypes = [i64]
         lib.uf_stripe_count.restype = i64
         lib.uf_tree_create.argtypes = [i64, vp, vp, ctypes.POINTER(vp)]
@@ -359,6 +362,15 @@ def uf_compute_ranges(tree: Tree, jobs, method: str, alpha: float = 1.0, precisi
             keep = keep.reshape(max(stop - start, 0), table.n_samples)
         res.append(keep)
     return res, [reps[i] for i in range(nj)]
+
+
+def uf_probe_l2_atomics(nbytes: int = 16 << 20) -> float:
+    """Random 64-bit atomic adds per second into a device array of nbytes on
+    the current device (diagnostic: the ceiling of the region scatter's
+    atomics)."""
+    rate = ctypes.c_double(0.0)
+    _check(load().uf_probe_l2_atomics(int(nbytes), ctypes.byref(rate)))
+    return rate.value
 
 
 def uf_compute_noalloc(tree: Tree, table: Table, method: str, alpha: float = 1.0,

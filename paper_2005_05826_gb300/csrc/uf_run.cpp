@@ -422,6 +422,13 @@ Inputs bind_inputs(uf_tree *tree, const BatchJob &J, int device, int64_t rows) {
   return in;
 }
 
+// the region scatter's pair-update counters, summed
+double pair_sum(const unsigned long long (&c)[SPARSE_PAIR_SLOTS]) {
+  unsigned long long t = 0;
+  for (unsigned long long v : c) t += v;
+  return (double)t;
+}
+
 // Branch rows per embedding block for a working budget of per_row bytes a row
 // plus fixed bytes.
 int64_t block_rows(int64_t nb, double per_row, double fixed) {
@@ -816,6 +823,9 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   ck(cudaMemsetAsync(Gt.p, 0, (size_t)std::max<int64_t>(G.n_tiles, 1) * GRAM_TILE_CELLS * 8, st), "memset");
   ck(cudaMemsetAsync(err.p, 0, sizeof(int), st), "memset");
   ck(cudaMemsetAsync(clamps.p, 0, sizeof(unsigned long long), st), "memset");
+  // the region scatter's pair updates, counted when the call is timed per phase
+  DevBuf pair_ctr(SPARSE_PAIR_SLOTS * sizeof(unsigned long long), st, "alloc pair counter");
+  ck(cudaMemsetAsync(pair_ctr.p, 0, SPARSE_PAIR_SLOTS * sizeof(unsigned long long), st), "memset");
   Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
   Capture cap(g_graph.load() != 0 && !timer.on, st, device);
@@ -829,6 +839,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
     const cudaStream_t ss = g_overlap.load() != 0 ? side.fork() : ls;
     timer.begin(4, ss);
     SparseArgs sp{};
+    sp.pair_count = timer.on ? pair_ctr.as<unsigned long long>() : nullptr;
     sp.kind = EMB_PRESENCE;
     sp.abs_mask = 0u;
     sp.M = Msp.as<unsigned long long>();
@@ -898,11 +909,13 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   // asynchronous one (device outputs on a stream) is not held back for it:
   // the finalize has already written NaN to every output when it is set
   const bool sync = !J.out_is_device || st == nullptr || timer.on;
+  const bool pairs_counted = timer.on && sc.region_mode;
   int h_err = 0;
-  unsigned long long h_clamps = 0;
+  unsigned long long h_clamps = 0, h_pairs[SPARSE_PAIR_SLOTS] = {};
   if (sync) {
     ck(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
     ck(cudaMemcpyAsync(&h_clamps, clamps.p, sizeof h_clamps, cudaMemcpyDeviceToHost, st), "copy count");
+    ck(cudaMemcpyAsync(h_pairs, pair_ctr.p, sizeof h_pairs, cudaMemcpyDeviceToHost, st), "copy count");
   }
   if (!J.out_is_device)
     for (size_t t = 0; t < nt; t++)
@@ -916,6 +929,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
   o.tmp.clear();
   err = DevBuf();
   clamps = DevBuf();
+  pair_ctr = DevBuf();
   if (sync) ck(cudaStreamSynchronize(st), "synchronize");
   else ck(cudaGetLastError(), "enqueue");
   if (h_err) return fail(UF_ETIMEOUT, "tensor-core kernel: a bounded wait gave up");
@@ -931,6 +945,7 @@ uf_status run_gram(uf_tree *tree, const BatchJob &J, int device, double scale) {
       t.rep->sparse_rows = split.n_sparse;
       t.rep->sparse_pairs = split.pairs;
       t.rep->t_sparse_ms = ms[4];
+      t.rep->sparse_pair_updates = pairs_counted ? pair_sum(h_pairs) : -1.0;
       t.rep->clamped = sync ? (int32_t)std::min<unsigned long long>(h_clamps, INT32_MAX) : -1;
     }
   return UF_OK;
@@ -1077,6 +1092,9 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   }
   ck(cudaMemsetAsync(M.p, 0, m_bytes, st), "memset");
   ck(cudaMemsetAsync(clamps.p, 0, sizeof(unsigned long long), st), "memset");
+  // the region scatter's pair updates, counted when the call is timed per phase
+  DevBuf pair_ctr(SPARSE_PAIR_SLOTS * sizeof(unsigned long long), st, "alloc pair counter");
+  ck(cudaMemsetAsync(pair_ctr.p, 0, SPARSE_PAIR_SLOTS * sizeof(unsigned long long), st), "memset");
   Outputs o = bind_outputs(J, st);
   double exec_flops = 0.0;
   // tile shape and chunk size: tuned once per (accumulator, precision, size
@@ -1107,6 +1125,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   // the sparse-row scatters run after the dense blocks, whose chunk tuning clears M
   auto launch_sparse = [&](cudaStream_t on) {
     SparseArgs sp{};
+    sp.pair_count = timer.on ? pair_ctr.as<unsigned long long>() : nullptr;
     sp.kind = kind;
     sp.abs_mask = amask;
     sp.gen_abs = acc == ACC_GEN && !fp32;
@@ -1230,8 +1249,12 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   cap.launch();
   // a synchronous call reads how many min-form numerators were raised to 0
   const bool sync = !J.out_is_device || st == nullptr || timer.on;
-  unsigned long long h_clamps = 0;
-  if (sync) ck(cudaMemcpyAsync(&h_clamps, clamps.p, sizeof h_clamps, cudaMemcpyDeviceToHost, st), "copy count");
+  const bool pairs_counted = timer.on && sc.region_mode;
+  unsigned long long h_clamps = 0, h_pairs[SPARSE_PAIR_SLOTS] = {};
+  if (sync) {
+    ck(cudaMemcpyAsync(&h_clamps, clamps.p, sizeof h_clamps, cudaMemcpyDeviceToHost, st), "copy count");
+    ck(cudaMemcpyAsync(h_pairs, pair_ctr.p, sizeof h_pairs, cudaMemcpyDeviceToHost, st), "copy count");
+  }
   if (!J.out_is_device)
     for (size_t t = 0; t < nt; t++)
       ck(cudaMemcpyAsync(J.tabs[t].out, o.dev[t], o.bytes[t], cudaMemcpyDeviceToHost, st), "copy out");
@@ -1245,6 +1268,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
   diag_tmp = DevBuf();
   counter = DevBuf();
   clamps = DevBuf();
+  pair_ctr = DevBuf();
   meta.dev = DevBuf();
   total = DevBuf();
   inv_total = DevBuf();
@@ -1264,6 +1288,7 @@ uf_status run_stripes(uf_tree *tree, const BatchJob &J, int device, uf_method me
       t.rep->sparse_rows = split.n_sparse;
       t.rep->sparse_pairs = split.pairs;
       t.rep->t_sparse_ms = ms[4];
+      t.rep->sparse_pair_updates = pairs_counted ? pair_sum(h_pairs) : -1.0;
     }
   return UF_OK;
 }

@@ -559,7 +559,9 @@ __device__ __forceinline__ int lower_index(const int *K, int lo, int hi, int key
   return lo;
 }
 
-template <typename T, int ACC, int MODE, int F = 0>
+// COUNT: the instantiation for timed calls, which also counts the pair updates
+// (kept apart: the count costs the counting-free kernel's 32 registers)
+template <typename T, int ACC, int MODE, int F = 0, bool COUNT = false>
 __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   constexpr bool FUSED = F > 0;
   using Ent = ListEnt<T, ACC, F>;
@@ -599,6 +601,7 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   // window where the previous region stopped, and only the first region of a
   // call searches for it.
   int *cur1 = a.cur + off, *cur2 = a.cur + a.cur_stride + off;
+  [[maybe_unused]] unsigned n_upd = 0;  // pair updates made by this thread: the cursors' moves
   auto add = [&](const Ent &ea, int ka, int b, int kb) {
     if constexpr (FUSED && ACC == ACC_MIN) add_pair_fused<T, F>(ka, kb, ea, E[b], c);
     else if constexpr (FUSED) add_pair_fused_gen<T, MODE, F>(ka, kb, ea, E[b], c, len);
@@ -613,19 +616,36 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
     {
       const int dlo = a.r0 + 1, dhi = min(a.r1, half);
       int b = a.first_region ? lower_index(K, ia + 1, z, ka + dlo) : cur1[ia];
+      [[maybe_unused]] const int b0 = b;
       if (dlo <= dhi)
         for (int kb; b < z && (kb = K[b]) <= ka + dhi; b++) add(ea, ka, b, kb);
       cur1[ia] = b;
+      if constexpr (COUNT) n_upd += (unsigned)(b - b0);
     }
     // window 2: d in [max(n - r1, n/2 + 1), n - r0 - 1], stripe n - d - 1, column k_b;
     // the cursor is one past the last partner not yet added
     {
       const int dlo = max(n - a.r1, half + 1), dhi = n - a.r0 - 1;
       int e = a.first_region ? lower_index(K, ia + 1, z, ka + dhi + 1) : cur2[ia];
+      [[maybe_unused]] const int e0 = e;
       if (dlo <= dhi)
         for (int kb; e > ia + 1 && (kb = K[e - 1]) >= ka + dlo; e--) add(ea, ka, e - 1, kb);
       cur2[ia] = e;
+      if constexpr (COUNT) n_upd += (unsigned)(e0 - e);
     }
+  }
+  if constexpr (COUNT) {  // every thread of the CTA is here
+    __shared__ unsigned long long s_upd;
+    if (threadIdx.x == 0) s_upd = 0;
+    __syncthreads();
+    unsigned long long w = n_upd;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_upd, w);
+    __syncthreads();
+    // spread over SPARSE_PAIR_SLOTS counters, so that no single address takes
+    // one atomic per CTA of every region
+    if (threadIdx.x == 0 && s_upd) atomicAdd(a.pair_count + (blockIdx.x & (SPARSE_PAIR_SLOTS - 1)), s_upd);
   }
 }
 
@@ -665,41 +685,46 @@ cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStre
   return mode == 0 ? launch_one<double, ACC_GEN, 0>(a, smem, st) : launch_one<double, ACC_GEN, 1>(a, smem, st);
 }
 
-cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaStream_t st) {
-  if (a.n_nodes <= 0 || a.r0 >= a.r1) return cudaSuccess;
+template <bool C>
+cudaError_t launch_region(int acc, bool fp32, const SparseArgs &a, dim3 grid, cudaStream_t st) {
   const int mode = a.alpha == 0.5 ? 0 : 1;
-  const dim3 grid((unsigned)a.n_nodes);
   if (acc == ACC_MIN && a.fused != 0) {
     if (a.fused == 2) {
-      if (fp32) k_sparse_region<float, ACC_MIN, 0, 2><<<grid, 128, 0, st>>>(a);
-      else k_sparse_region<double, ACC_MIN, 0, 2><<<grid, 128, 0, st>>>(a);
+      if (fp32) k_sparse_region<float, ACC_MIN, 0, 2, C><<<grid, 128, 0, st>>>(a);
+      else k_sparse_region<double, ACC_MIN, 0, 2, C><<<grid, 128, 0, st>>>(a);
     } else if (a.fused == 6) {
-      if (fp32) k_sparse_region<float, ACC_MIN, 0, 6><<<grid, 128, 0, st>>>(a);
-      else k_sparse_region<double, ACC_MIN, 0, 6><<<grid, 128, 0, st>>>(a);
+      if (fp32) k_sparse_region<float, ACC_MIN, 0, 6, C><<<grid, 128, 0, st>>>(a);
+      else k_sparse_region<double, ACC_MIN, 0, 6, C><<<grid, 128, 0, st>>>(a);
     } else {
       return cudaErrorInvalidValue;
     }
   } else if (acc == ACC_MIN) {
-    if (fp32) k_sparse_region<float, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
-    else k_sparse_region<double, ACC_MIN, 0><<<grid, 128, 0, st>>>(a);
+    if (fp32) k_sparse_region<float, ACC_MIN, 0, 0, C><<<grid, 128, 0, st>>>(a);
+    else k_sparse_region<double, ACC_MIN, 0, 0, C><<<grid, 128, 0, st>>>(a);
   } else if (a.fused == 2) {
     if (fp32) {
-      if (mode == 0) k_sparse_region<float, ACC_GEN, 0, 2><<<grid, 128, 0, st>>>(a);
-      else k_sparse_region<float, ACC_GEN, 1, 2><<<grid, 128, 0, st>>>(a);
+      if (mode == 0) k_sparse_region<float, ACC_GEN, 0, 2, C><<<grid, 128, 0, st>>>(a);
+      else k_sparse_region<float, ACC_GEN, 1, 2, C><<<grid, 128, 0, st>>>(a);
     } else {
-      if (mode == 0) k_sparse_region<double, ACC_GEN, 0, 2><<<grid, 128, 0, st>>>(a);
-      else k_sparse_region<double, ACC_GEN, 1, 2><<<grid, 128, 0, st>>>(a);
+      if (mode == 0) k_sparse_region<double, ACC_GEN, 0, 2, C><<<grid, 128, 0, st>>>(a);
+      else k_sparse_region<double, ACC_GEN, 1, 2, C><<<grid, 128, 0, st>>>(a);
     }
   } else if (a.fused != 0) {
     return cudaErrorInvalidValue;
   } else if (fp32) {
-    if (mode == 0) k_sparse_region<float, ACC_GEN, 0><<<grid, 128, 0, st>>>(a);
-    else k_sparse_region<float, ACC_GEN, 1><<<grid, 128, 0, st>>>(a);
+    if (mode == 0) k_sparse_region<float, ACC_GEN, 0, 0, C><<<grid, 128, 0, st>>>(a);
+    else k_sparse_region<float, ACC_GEN, 1, 0, C><<<grid, 128, 0, st>>>(a);
   } else {
-    if (mode == 0) k_sparse_region<double, ACC_GEN, 0><<<grid, 128, 0, st>>>(a);
-    else k_sparse_region<double, ACC_GEN, 1><<<grid, 128, 0, st>>>(a);
+    if (mode == 0) k_sparse_region<double, ACC_GEN, 0, 0, C><<<grid, 128, 0, st>>>(a);
+    else k_sparse_region<double, ACC_GEN, 1, 0, C><<<grid, 128, 0, st>>>(a);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_region(int acc, bool fp32, const SparseArgs &a, cudaStream_t st) {
+  if (a.n_nodes <= 0 || a.r0 >= a.r1) return cudaSuccess;
+  const dim3 grid((unsigned)a.n_nodes);
+  return a.pair_count ? launch_region<true>(acc, fp32, a, grid, st) : launch_region<false>(acc, fp32, a, grid, st);
 }
 
 size_t sparse_list_smem_bytes(int cap) { return (size_t)cap * 8; }

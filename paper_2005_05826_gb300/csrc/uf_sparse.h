@@ -57,6 +57,8 @@ struct SparseArgs {
   const int32_t *members;
   // region mode: only pairs whose stripe lies in [r0, r1) (launch_sparse_region)
   int r0, r1;
+  unsigned long long *pair_count;  // non-null: the pair updates made are added to these
+                                   // SPARSE_PAIR_SLOTS counters (summed by the host)
   int first_region;         // 1: the call's first region (cursors are searched, not read)
   int *cur;                 // two cursors per list entry: window 1 at cur[e], window 2 at
   int64_t cur_stride;       // cur[cur_stride + e] (regions must come in increasing order)
@@ -65,6 +67,7 @@ struct SparseArgs {
 // shared memory, or written as a list (one table, keys alone in shared memory)
 constexpr int SPARSE_MAX_ENTRIES = 4096;
 constexpr int SPARSE_LIST_MAX_ENTRIES = 16384;
+constexpr int SPARSE_PAIR_SLOTS = 256;
 size_t sparse_smem_bytes(bool fp32, int cap);
 size_t sparse_entry_bytes(bool fp32, int fused = 0, int acc = ACC_MIN);
 cudaError_t launch_sparse_rows(int acc, bool fp32, const SparseArgs &a, cudaStream_t st);

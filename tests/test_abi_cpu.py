@@ -288,3 +288,11 @@ def test_compute_ranges_validates_before_the_device():
         with pytest.raises(uf.UFError) as e:
             uf.uf_compute_ranges(tree, [(table, 0, 3), (table, 3, 6)], "unweighted", precision="mixed")
         assert e.value.status == "UF_ECUDA"
+
+
+def test_probe_validates_before_the_device():
+    # the diagnostic atomic-rate probe rejects bad sizes before any CUDA call
+    for nbytes in (0, 8 * 1000, 8 * 1023, 8 * 3000, 8 * (1 << 31) * 2):
+        assert _code(lambda: uf.uf_probe_l2_atomics(nbytes)) == "UF_EINVAL", nbytes
+    lib = uf.load()
+    assert lib.uf_probe_l2_atomics(16 << 20, None) == 1  # UF_EINVAL

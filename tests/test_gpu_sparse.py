@@ -319,6 +319,47 @@ def test_fused_lists_match_unfused_bitwise(tensor):
         uf.uf_set_option("tensor_path", 1)
 
 
+def test_region_scatter_counts_its_pair_updates():
+    # timed per phase, a call reports the pair updates its region scatter made
+    # (counted on the device): unfused, every scattered branch's pairs of
+    # present samples, z (z - 1) / 2 for z samples below it over the whole
+    # matrix; fused, fewer (the members' pairs ride in their heads' updates)
+    tree_s = yule_tree(2000, seed=290)
+    table_s = table_iid(300, tree_s.n_tips, 0.01, seed=291)
+    tree, table = handles(tree_s, table_s)
+    # samples present below every node (children before parents)
+    pres = np.zeros((tree_s.n_nodes, 300), dtype=bool)
+    dense = table_s.dense() > 0
+    has_child = np.zeros(tree_s.n_nodes, dtype=bool)
+    has_child[tree_s.parent[:-1]] = True
+    tips = np.nonzero(~has_child)[0]
+    pres[tips] = dense.T
+    for v in range(tree_s.n_nodes - 1):
+        pres[tree_s.parent[v]] |= pres[v]
+    z = pres[:-1].sum(axis=1).astype(np.float64)
+    listed = (tree_s.length[:-1] > 0) & (z > 0)
+    expect = float((z[listed] * (z[listed] - 1) / 2).sum())
+    uf.uf_set_option("tensor_path", 0)
+    uf.uf_set_option("sparse_region_bytes", 16384)
+    try:
+        uf.uf_set_option("kernel_timing", 1)
+        counts = {}
+        for fuse in (0, 2):
+            uf.uf_set_option("sparse_fuse", fuse)
+            _, rep = run(tree, table, "weighted_normalized", 1.0, "mixed", 2)
+            counts[fuse] = rep.sparse_pair_updates
+        assert counts[0] == expect, (counts[0], expect)
+        assert 0 < counts[2] < counts[0]
+        uf.uf_set_option("kernel_timing", 0)
+        _, rep = run(tree, table, "weighted_normalized", 1.0, "mixed", 2)
+        assert rep.sparse_pair_updates == -1.0
+    finally:
+        uf.uf_set_option("kernel_timing", 0)
+        uf.uf_set_option("sparse_fuse", 2)
+        uf.uf_set_option("sparse_region_bytes", 0)
+        uf.uf_set_option("tensor_path", 1)
+
+
 def test_overlap_matches_sequential_bitwise():
     # the scatter beside the dense kernel adds the same integers in another
     # order: the results equal the sequential ones bit for bit
@@ -337,3 +378,10 @@ def test_overlap_matches_sequential_bitwise():
                 np.testing.assert_array_equal(beside, after)
     finally:
         uf.uf_set_option("sparse_overlap", 1)
+
+
+def test_l2_atomic_probe_rate():
+    # the ceiling the region scatter is measured against: random 64-bit atomic
+    # adds into 16 MB (L2-resident) run at 1e10-1e12 per second on one GPU
+    rate = uf.uf_probe_l2_atomics(16 << 20)
+    assert 1e10 < rate < 1e12, rate

@@ -694,6 +694,7 @@ def run_ours(args, rank, world, local_rank):
         host_arrays = ([] if large else
                        [np.zeros(o.numel(), dtype=np.float32 if args.out_fp32 else np.float64) for o in outs])
         e2e_stream = torch.cuda.Stream(dev)  # a null stream would make every call synchronous
+        copy_stream = torch.cuda.Stream(dev)
 
         def e2e_step(sync_host):
             torch.cuda.synchronize()
@@ -701,21 +702,30 @@ def run_ours(args, rank, world, local_rank):
                 dist.barrier()
             t0 = time.perf_counter()
             tr = uf.Tree(tree_s.parent, tree_s.length)
+            t_tree = time.perf_counter()
             tb = uf.Table(table_s.indptr, table_s.indices, table_s.data, tr)
+            t_handles = time.perf_counter()
             hb = db = 0.0
+            call_s = []
             with torch.cuda.stream(e2e_stream):
-                for (m, a), o, ha in zip(METHODS, outs, host_arrays or [None] * len(outs)):
+                for (m, a), o, ha, h in zip(METHODS, outs, host_arrays or [None] * len(outs), host_res):
                     if sync_host:  # host output: each call returns with its result on the host
                         r, rep = uf.uf_compute(tr, tb, m, a, "mixed", *rng_args, out=ha, out_fp32=args.out_fp32)
                         db += r.nbytes
                     else:
                         _, rep = uf.uf_compute(tr, tb, m, a, "mixed", *rng_args, out=o, out_fp32=args.out_fp32)
-                    hb += rep.h2d_bytes
-                if not sync_host:
-                    for o, h in zip(outs, host_res):
-                        h.copy_(o, non_blocking=True)
+                        call_s.append(rep.seconds)
+                        # the result's read-back on a copy stream, beside the next call's kernels
+                        done = torch.cuda.Event()
+                        done.record(e2e_stream)
+                        copy_stream.wait_event(done)
+                        with torch.cuda.stream(copy_stream):
+                            h.copy_(o, non_blocking=True)
                         db += o.numel() * o.element_size()
+                    hb += rep.h2d_bytes
+                t_queued = time.perf_counter()
             torch.cuda.synchronize()
+            stage = (t_handles - t0, t_queued - t_handles, time.perf_counter() - t_queued, t_tree - t0, call_s)
             if dist:  # every rank's part to rank 0: the sharded job's one collective
                 from paper_2005_05826_gb300.shard import gather_parts
                 for o in outs:
@@ -724,15 +734,18 @@ def run_ours(args, rank, world, local_rank):
             dt = time.perf_counter() - t0
             tb.close()
             tr.close()
-            return dt, hb, db
+            return dt, hb, db, stage
 
         res = {}
+        stages = []  # per e2e step: handles, queueing the calls, the rest until synchronised
         for mode in modes:
             e_times = []
             for s in range((2 if large else max(1, min(args.steps, 3))) + 1):
-                dt, h2d, d2h = e2e_step(mode)
+                dt, h2d, d2h, stage = e2e_step(mode)
                 if s > 0:  # the first is a warm-up
                     e_times.append(dt)
+                    if not mode:
+                        stages.append(stage)
             t_mode = statistics.mean(e_times)
             if dist:  # the slowest rank's step time; bytes of all ranks
                 t = torch.tensor([t_mode], dtype=torch.float64, device=dev)
@@ -743,7 +756,14 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": job_updates / t_e, "unit": "updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e,
                "path": f"fresh tree and table handles from the host arrays, {len(METHODS)} uf_compute calls "
-                       f"queued on the stream with device outputs, results read into pinned host memory"}
+                       f"queued on the stream with device outputs, each result read into pinned host memory "
+                       f"on a copy stream beside the next call's kernels",
+               "ms_stages": {"handles": 1e3 * statistics.mean(x[0] for x in stages),
+                             "tree_handle": 1e3 * statistics.mean(x[3] for x in stages),
+                             "queue_calls": 1e3 * statistics.mean(x[1] for x in stages),
+                             "calls_host": [1e3 * statistics.mean(x[4][i] for x in stages)
+                                            for i in range(len(stages[0][4]))],
+                             "device_and_copies": 1e3 * statistics.mean(x[2] for x in stages)}}
         if True in res:
             e2e["host_output_calls"] = {"value": job_updates / res[True][0],
                                         "ms_per_step": 1e3 * res[True][0],

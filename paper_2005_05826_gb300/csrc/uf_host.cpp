@@ -164,6 +164,60 @@ void ck(cudaError_t e, const char *what) {
   }
 }
 
+// Pinned chunks for pinned_upload, one ring per device (the copy stream and
+// events belong to it); the chunks themselves are portable pinned memory.
+namespace {
+struct UploadRing {
+  static constexpr int NBUF = 4;
+  static constexpr size_t CHUNK = (size_t)32 << 20;
+  char *buf[NBUF] = {};
+  cudaEvent_t ev[NBUF] = {};
+  bool busy[NBUF] = {};
+  cudaStream_t st = nullptr;
+  bool ok = false;
+};
+std::mutex g_ring_mu;
+std::map<int, UploadRing> g_rings;
+}  // namespace
+
+void pinned_upload(void *dst, const void *src, size_t bytes) {
+  if (bytes == 0) return;
+  int dev = 0;
+  ck(cudaGetDevice(&dev), "upload");
+  std::lock_guard<std::mutex> g(g_ring_mu);
+  UploadRing &R = g_rings[dev];
+  if (!R.ok) {
+    bool good = cudaStreamCreateWithFlags(&R.st, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; good && i < UploadRing::NBUF; i++)
+      good = cudaHostAlloc((void **)&R.buf[i], UploadRing::CHUNK, cudaHostAllocPortable) == cudaSuccess &&
+             cudaEventCreateWithFlags(&R.ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!good) {  // no pinned memory: the driver's own staged copy
+      cudaGetLastError();
+      ck(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), "upload");
+      return;
+    }
+    R.ok = true;
+  }
+  const char *s = static_cast<const char *>(src);
+  char *d = static_cast<char *>(dst);
+  const int nt = std::max(1, std::min(host_threads(), 8));
+  int i = 0;
+  for (size_t off = 0; off < bytes; off += UploadRing::CHUNK, i = (i + 1) % UploadRing::NBUF) {
+    const size_t n = std::min(UploadRing::CHUNK, bytes - off);
+    if (R.busy[i]) ck(cudaEventSynchronize(R.ev[i]), "upload");
+    char *b = R.buf[i];
+    parallel_for(nt, [&](int c) {
+      const size_t a0 = n * c / nt, a1 = n * (c + 1) / nt;
+      memcpy(b + a0, s + off + a0, a1 - a0);
+    });
+    ck(cudaMemcpyAsync(d + off, b, n, cudaMemcpyHostToDevice, R.st), "upload");
+    ck(cudaEventRecord(R.ev[i], R.st), "upload");
+    R.busy[i] = true;
+  }
+  ck(cudaStreamSynchronize(R.st), "upload");
+  for (bool &x : R.busy) x = false;
+}
+
 uf_tree::Dev &tree_dev(uf_tree *t, int device) {
   auto it = t->dev.find(device);
   if (it != t->dev.end()) return it->second;
@@ -613,8 +667,6 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
     std::vector<double> cmin(T, INFINITY);  // the smallest count (variance-adjusted bound)
     const double *tip_dist = tree->tip_dist.data();
     parallel_for(T, [&](int c) {
-      cnt[c].assign(n_features, 0);
-      int64_t *cc = cnt[c].data();
       char buf[160];
       for (int64_t k = k_lo[c]; k < k_lo[c + 1]; k++) {
         double s = 0.0, w = 0.0;
@@ -628,7 +680,6 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
           else {
             s += data[q];
             w += tip_dist[indices[q]];
-            cc[indices[q]]++;
             cmin[c] = std::min(cmin[c], data[q]);
             continue;
           }
@@ -646,6 +697,30 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
     t->id = next_id++;
     t->presence_bound[tree->id] = *std::max_element(pres.begin(), pres.end());
     t->min_count = *std::min_element(cmin.begin(), cmin.end());
+    // each thread's column counts (a counting sort) and, below, its scatter
+    // run over feature blocks: a sample's entries are sorted by feature, so
+    // each block's entries of a sample are the run after the previous
+    // block's, and one block's counts and writes stay within its columns
+    // (cache-resident) instead of spreading over every column
+    const int NB = (int)std::max<int64_t>(1, std::min<int64_t>(64, n_features / 1024));
+    auto by_blocks = [&](int c, auto &&visit) {
+      const int64_t k0 = k_lo[c], nk = k_lo[c + 1] - k0;
+      std::vector<int64_t> cur(indptr + k0, indptr + k0 + nk);
+      for (int b = 0; b < NB; b++) {
+        const int64_t fend = n_features * (b + 1) / NB;
+        for (int64_t i = 0; i < nk; i++) {
+          const int64_t qe = indptr[k0 + i + 1];
+          int64_t q = cur[i];
+          for (; q < qe && indices[q] < fend; q++) visit(k0 + i, q);
+          cur[i] = q;
+        }
+      }
+    };
+    parallel_for(T, [&](int c) {
+      cnt[c].assign(n_features, 0);
+      int64_t *cc = cnt[c].data();
+      by_blocks(c, [&](int64_t, int64_t q) { cc[indices[q]]++; });
+    });
     // column starts, then each thread's first slot in every column (its
     // samples go behind the earlier threads'), over feature ranges in parallel
     t->col_ptr.assign(n_features + 1, 0);
@@ -674,12 +749,11 @@ uf_status uf_table_create(int64_t n_samples, int64_t n_features, const int64_t *
     t->col_val.resize(std::max<int64_t>(nnz, 1));
     parallel_for(T, [&](int c) {
       int64_t *slot = cnt[c].data();
-      for (int64_t k = k_lo[c]; k < k_lo[c + 1]; k++)
-        for (int64_t q = indptr[k]; q < indptr[k + 1]; q++) {
-          const int64_t at = slot[indices[q]]++;
-          t->col_row[at] = (int32_t)k;
-          t->col_val[at] = data[q];
-        }
+      by_blocks(c, [&](int64_t k, int64_t q) {
+        const int64_t at = slot[indices[q]]++;
+        t->col_row[at] = (int32_t)k;
+        t->col_val[at] = data[q];
+      });
     });
     *out = t.release();
     return UF_OK;

@@ -92,6 +92,12 @@ struct NoInit : std::allocator<T> {
   }
 };
 
+// Host -> device copy of pageable memory through a ring of pinned chunks:
+// host threads fill one chunk while the copy engine drains the previous ones
+// (a plain cudaMemcpy from pageable memory is staged by the driver at a
+// fraction of the link's rate).  Synchronous: returns when dst holds the data.
+void pinned_upload(void *dst, const void *src, size_t bytes);
+
 // Several host arrays copied into one device allocation at 256-byte aligned
 // offsets: one cudaMalloc per handle instead of one per array.
 struct DevPack {
@@ -112,10 +118,11 @@ struct DevPack {
     ck(cudaMalloc(&d, std::max<size_t>(total, 16)), what);
     for (size_t i = 0; i < parts.size(); i++) {
       if (!parts[i].second) continue;
-      const cudaError_t e = cudaMemcpy(d + offs[i], parts[i].first, parts[i].second, cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) {
+      try {
+        pinned_upload(d + offs[i], parts[i].first, parts[i].second);
+      } catch (...) {
         cudaFree(d);
-        ck(e, what);
+        throw;
       }
       g_h2d += (double)parts[i].second;
     }

@@ -265,16 +265,25 @@ struct PriorityScope {
   ~PriorityScope() { set_launch_priority(old); }
 };
 
-// Executable graphs still running: destroying one right after its launch
-// makes the host wait for it when the graph has parallel branches, so each
-// is kept with an event recorded behind its launch and destroyed by a later
-// call once that event has completed (or, past 32 in flight, after a wait on
-// the oldest).
+// Executable graphs already launched.  Destroying one makes the host wait for
+// the work in flight on the device, even when that graph itself has finished
+// (measured on GB300: destroying the previous call's finished graph while a
+// 0.9 s tensor-core call ran held the host for 0.9 s).  So each is kept with
+// an event recorded behind its launch, and they are destroyed together at
+// the start of a later call once every one of them has completed (the
+// caller has synchronised: nothing of ours is in flight), or, past 32
+// queued, after a wait on the oldest.
 struct LiveGraphs {
   std::mutex mu;
   std::deque<std::pair<cudaGraphExec_t, cudaEvent_t>> q;
 };
 LiveGraphs g_live_graphs;
+
+void destroy_front(std::deque<std::pair<cudaGraphExec_t, cudaEvent_t>> &q) {
+  cudaGraphExecDestroy(q.front().first);
+  cudaEventDestroy(q.front().second);
+  q.pop_front();
+}
 
 void retire_graph(cudaGraphExec_t e, cudaStream_t st) {
   cudaEvent_t ev = nullptr;
@@ -288,15 +297,23 @@ void retire_graph(cudaGraphExec_t e, cudaStream_t st) {
   std::lock_guard<std::mutex> g(g_live_graphs.mu);
   auto &q = g_live_graphs.q;
   q.emplace_back(e, ev);
-  while (!q.empty()) {
-    const bool over = q.size() > 32;
-    if (over) cudaEventSynchronize(q.front().second);
-    else if (cudaEventQuery(q.front().second) != cudaSuccess) break;
-    cudaGraphExecDestroy(q.front().first);
-    cudaEventDestroy(q.front().second);
-    q.pop_front();
+  while (q.size() > 32) {
+    cudaEventSynchronize(q.front().second);
+    destroy_front(q);
   }
-  cudaGetLastError();  // cudaErrorNotReady from the query is not an error here
+  cudaGetLastError();
+}
+
+// At the start of a call: the queued graphs, if all of them have completed.
+void reap_graphs() {
+  std::lock_guard<std::mutex> g(g_live_graphs.mu);
+  auto &q = g_live_graphs.q;
+  for (const auto &x : q)
+    if (cudaEventQuery(x.second) != cudaSuccess) {
+      cudaGetLastError();  // cudaErrorNotReady is not an error here
+      return;
+    }
+  while (!q.empty()) destroy_front(q);
 }
 
 // Records the branch-block launch sequence of a call into a CUDA graph (on a
@@ -311,6 +328,7 @@ struct Capture {
   bool node_priority = false;
   Capture(bool enable, cudaStream_t st, int device) : on(enable), user(st) {
     if (!on) return;
+    reap_graphs();
     cap = capture_stream(device);
     ck(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
     open = true;

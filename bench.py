@@ -673,8 +673,7 @@ def run_ours(args, rank, world, local_rank):
     cands += [(kern[m]["scatter"]["share_of_step"], m, kern[m]["scatter"]) for m in kern if "scatter" in kern[m]]
     _, dom, dom_k = max(cands, key=lambda c: c[0])
     rl = {k: v for k, v in dom_k.items() if k != "scatter"}
-    rl["traffic"] = (kernel_traffic(rl["kernel"], args.workload if full else f"{args.workload}[0,{stop})")
-                     if rl["bound"] != "l2" else None)
+    rl["traffic"] = kernel_traffic(rl["kernel"], args.workload if full else f"{args.workload}[0,{stop})")
     rl["method"] = dom
 
     # ---- e2e through the C ABI: fresh handles from the host arrays (their

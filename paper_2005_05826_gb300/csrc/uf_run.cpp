@@ -654,7 +654,7 @@ struct SparseScatter {
       list_entries = (int64_t)total_e;
       le = DevBuf(total_e * sparse_entry_bytes(!fp64_entries, fuse_m, acc), st, "alloc sparse lists");
       lk = DevBuf(total_e * 4, st, "alloc sparse lists");
-      cur = DevBuf(total_e * 8, st, "alloc sparse list cursors");
+      cur = DevBuf(total_e * 2 * sizeof(uint16_t), st, "alloc sparse list cursors");
       lz = DevBuf(std::max<size_t>(all.size(), 1) * 4, st, "alloc sparse lists");
       // rows without entries in the table return before writing their count
       ck(cudaMemsetAsync(lz.p, 0, std::max<size_t>(all.size(), 1) * 4, st), "memset");
@@ -699,7 +699,7 @@ struct SparseScatter {
       base.lk = lk.as<int>();
       base.lofs = meta.at<int64_t>(o_lofs);
       base.lz = lz.as<int>();
-      base.cur = cur.as<int>();
+      base.cur = cur.as<uint16_t>();
       base.cur_stride = list_entries;
       base.fused = fuse_m;
       base.members = fuse_m > 0 ? meta.at<int32_t>(o_members) : nullptr;

@@ -600,7 +600,9 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
   // window 2 move down from region to region: each entry keeps a cursor per
   // window where the previous region stopped, and only the first region of a
   // call searches for it.
-  int *cur1 = a.cur + off, *cur2 = a.cur + a.cur_stride + off;
+  // 16-bit cursors: the region kernels stream every entry's state once per
+  // region, so its bytes count (a list holds at most SPARSE_LIST_MAX_ENTRIES)
+  uint16_t *cur1 = a.cur + off, *cur2 = a.cur + a.cur_stride + off;
   [[maybe_unused]] unsigned n_upd = 0;  // pair updates made by this thread: the cursors' moves
   auto add = [&](const Ent &ea, int ka, int b, int kb) {
     if constexpr (FUSED && ACC == ACC_MIN) add_pair_fused<T, F>(ka, kb, ea, E[b], c);
@@ -615,22 +617,22 @@ __global__ void __launch_bounds__(128) k_sparse_region(const SparseArgs a) {
     // window 1: d = k_b - k_a in [r0 + 1, min(r1, n/2)], stripe d - 1, cell column k_a
     {
       const int dlo = a.r0 + 1, dhi = min(a.r1, half);
-      int b = a.first_region ? lower_index(K, ia + 1, z, ka + dlo) : cur1[ia];
+      int b = a.first_region ? lower_index(K, ia + 1, z, ka + dlo) : (int)cur1[ia];
       [[maybe_unused]] const int b0 = b;
       if (dlo <= dhi)
         for (int kb; b < z && (kb = K[b]) <= ka + dhi; b++) add(ea, ka, b, kb);
-      cur1[ia] = b;
+      cur1[ia] = (uint16_t)b;
       if constexpr (COUNT) n_upd += (unsigned)(b - b0);
     }
     // window 2: d in [max(n - r1, n/2 + 1), n - r0 - 1], stripe n - d - 1, column k_b;
     // the cursor is one past the last partner not yet added
     {
       const int dlo = max(n - a.r1, half + 1), dhi = n - a.r0 - 1;
-      int e = a.first_region ? lower_index(K, ia + 1, z, ka + dhi + 1) : cur2[ia];
+      int e = a.first_region ? lower_index(K, ia + 1, z, ka + dhi + 1) : (int)cur2[ia];
       [[maybe_unused]] const int e0 = e;
       if (dlo <= dhi)
         for (int kb; e > ia + 1 && (kb = K[e - 1]) >= ka + dlo; e--) add(ea, ka, e - 1, kb);
-      cur2[ia] = e;
+      cur2[ia] = (uint16_t)e;
       if constexpr (COUNT) n_upd += (unsigned)(e0 - e);
     }
   }

@@ -60,13 +60,15 @@ struct SparseArgs {
   unsigned long long *pair_count;  // non-null: the pair updates made are added to these
                                    // SPARSE_PAIR_SLOTS counters (summed by the host)
   int first_region;         // 1: the call's first region (cursors are searched, not read)
-  int *cur;                 // two cursors per list entry: window 1 at cur[e], window 2 at
-  int64_t cur_stride;       // cur[cur_stride + e] (regions must come in increasing order)
+  uint16_t *cur;            // two cursors per list entry (indices into its row's list, which
+                            // holds at most SPARSE_LIST_MAX_ENTRIES): window 1 at cur[e],
+  int64_t cur_stride;       // window 2 at cur[cur_stride + e] (regions in increasing order)
 };
 // largest subtree entry count a sparse row may have: scattered directly from
 // shared memory, or written as a list (one table, keys alone in shared memory)
 constexpr int SPARSE_MAX_ENTRIES = 4096;
 constexpr int SPARSE_LIST_MAX_ENTRIES = 16384;
+static_assert(SPARSE_LIST_MAX_ENTRIES <= 65535, "list cursors are 16-bit");
 constexpr int SPARSE_PAIR_SLOTS = 256;
 size_t sparse_smem_bytes(bool fp32, int cap);
 size_t sparse_entry_bytes(bool fp32, int fused = 0, int acc = ACC_MIN);

@@ -58,10 +58,12 @@ SFU_PER_SM = 16
 SMS = 152  # replaced by the device's multiprocessor count in run_ours
 
 # per-workload defaults: methods of a step, stripe range [0, stop) (0: all),
-# FP32 distance outputs, FP64 comparison slice [0, k) (0: the whole matrix)
+# FP32 distance outputs, FP64 comparison slice [0, k) (0: the whole matrix),
+# timed steps when --steps is not given (the large workloads' steps take
+# seconds: their timed region stays near a minute)
 WORKLOAD_DEFAULTS = {
     "yule500k_n113000": dict(methods=["unweighted", "weighted_normalized"], stripe_stop=8192, out_fp32=True,
-                             fp64_stripes=64),
+                             fp64_stripes=64, steps=10),
     "yule300k_n25000": dict(methods=FOUR, stripe_stop=0, out_fp32=False, fp64_stripes=256),
     "yule50k_n2048": dict(methods=FOUR, stripe_stop=0, out_fp32=False, fp64_stripes=0),
     "yule1k_n64": dict(methods=FOUR, stripe_stop=0, out_fp32=False, fp64_stripes=0),
@@ -895,7 +897,8 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 20, or 10 for the 113k-shaped workload)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="yule500k_n113000",
@@ -931,6 +934,8 @@ def main():
                     help="sparse-row path: 0 every branch dense, 1 cost model (default), 2 every branch that fits")
     args = ap.parse_args()
     dflt = WORKLOAD_DEFAULTS.get(args.workload, WORKLOAD_DEFAULTS["yule50k_n2048"])
+    if args.steps is None:
+        args.steps = dflt.get("steps", 20)
     if args.stripe_stop < 0:
         args.stripe_stop = dflt["stripe_stop"]
     if args.fp64_stripes < 0:
